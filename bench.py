@@ -1,0 +1,421 @@
+#!/usr/bin/env python
+"""Benchmark of the SPIIR hot path on GB300.
+
+Default workload: single-rate bank, 1024 templates x 512 complex filters,
+4096 Hz, 16 s of seeded white Gaussian strain pushed as one 16-block push per
+step (the plain FP32 recursion path). One JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload single|multirate]
+
+N > 1 (torchrun): every rank filters its own bank of the same shape (weak
+scaling, no collective on the data path); the timing is the max over ranks.
+--impl reference times the FP64 CPU oracle on the host cores instead, on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "real-time templates/GPU (filter-samples/s) & p99 block latency, chosen vs plain"
+UNIT = "filter-samples/s"
+FLOPS_PER_FS = 12          # Sec. 2.2 cost model: 12 flops per filter per sample
+LANE_OPS_PER_FS = 8        # 2 FMUL + 4 FFMA + 2 FADD per filter-sample
+FP32_LANES_PER_SM = 128
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.marks = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", self.gpu_id],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        threading.Thread(target=self._read, daemon=True).start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self):
+        self.marks.append(time.time())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = [l for (t, l) in self.lines if t0 - 0.25 <= t <= t1 + 0.25]
+        if not rows:
+            rows = [l for (_, l) in self.lines[-3:]]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            f = [x.strip() for x in r.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _gpu_id(torch, dev: int) -> str:
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        return "%08x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        return vis.split(",")[dev] if vis else str(dev)
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def _traffic(kernel_file: str, key: str):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel
+    source has not changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"{key}_traffic.txt")
+    try:
+        kv = dict(tok.split("=", 1) for tok in open(path).read().split() if "=" in tok)
+    except OSError:
+        return None
+    src = os.path.join(ROOT, "paper_1702_02256_gb300", "csrc", kernel_file)
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if kv.get("source_sha256_16") != h:
+        return None
+    return float(kv["dram_bytes_per_launch"])
+
+
+def _workload(name: str, rank: int, templates: int = 0):
+    from paper_1702_02256_gb300 import inputs
+    if name == "single":
+        T = templates or 1024
+        bank = inputs.single_rate_bank(T, 512, 4095, seed=rank)
+        return dict(bank=bank, x=inputs.strain(1, 16 * 4096, seed=1 + 100 * rank),
+                    block_len=4096, push_blocks=16,
+                    desc=f"single-rate {T} templates x 512 filters, 4096 Hz, 16 s per step "
+                         "(one 16-block push), delays 0-4095")
+    if name == "multirate":
+        T = templates or 4000
+        bank = inputs.multi_rate_bank(T, 7, seed=rank)
+        return dict(bank=bank, x=inputs.strain(1, 16 * 4096, seed=1 + 100 * rank),
+                    block_len=4096, push_blocks=1,
+                    desc=f"multi-rate {T} templates, 7 rates 4096-64 Hz, 16 s per step "
+                         "(16 pushes of 1 s)")
+    raise SystemExit(f"unknown workload {name}")
+
+
+def _cpu_sample(w, budget_s: float, n_templates_max: int):
+    """Time the oracle on the host cores over a bounded template sample sized
+    to about budget_s seconds. Returns (filter-samples/s, sample text, cores)."""
+    from oracle import oracle
+    bank = w["bank"]
+    x = w["x"][0]
+    threads = oracle.default_threads()
+    multi = bank.n_levels > 1
+
+    def run(sel):
+        t0 = time.perf_counter()
+        if multi:
+            oracle.spiir_multirate(bank, x, templates=sel, threads=threads)
+        else:
+            oracle.spiir_single(bank, x, templates=sel, threads=threads)
+        return time.perf_counter() - t0
+
+    def fs(sel):
+        cnt = np.bincount(bank.template_id, minlength=bank.n_templates)
+        lev_fs = 0
+        for t in sel:
+            m = bank.template_id == t
+            lev_fs += int(np.sum(x.shape[0] >> bank.level[m].astype(np.int64)))
+        return lev_fs
+
+    n0 = max(1, threads)
+    sel = np.arange(min(n0, bank.n_templates), dtype=np.int32)
+    dt = run(sel)
+    rate = fs(sel) / dt
+    per_t = dt / len(sel)
+    n = int(min(n_templates_max, bank.n_templates, max(len(sel), budget_s / per_t)))
+    n = max(threads, (n // threads) * threads) if n >= threads else n
+    sel = np.arange(n, dtype=np.int32)
+    dt = run(sel)
+    rate = fs(sel) / dt
+    sample = f"{n} of {bank.n_templates} templates, full {x.shape[0]} samples, {dt:.1f} s wall"
+    return rate, sample, threads
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    w = _workload(args.workload, 0, args.templates)
+    per_step = max(1.0, 150.0 / max(1, args.steps + args.warmup))
+    rates = []
+    sample = ""
+    threads = 1
+    for i in range(args.warmup + args.steps):
+        rate, sample, threads = _cpu_sample(w, per_step, 64)
+        if i >= args.warmup:
+            rates.append(rate)
+    value = float(np.mean(rates))
+    bank = w["bank"]
+    n = w["x"].shape[1]
+    fs_total = int(np.sum(n >> bank.level.astype(np.int64)))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * fs_total / value, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["desc"], "n_templates": bank.n_templates,
+                   "n_filters": bank.n_filters},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1702_02256_gb300 import spiir
+
+    w = _workload(args.workload, rank, args.templates)
+    bank = w["bank"]
+    n = w["x"].shape[1]
+    push_len = w["block_len"] * w["push_blocks"]
+    b = spiir.Bank(bank, n_streams=1, block_len=w["block_len"],
+                   max_push_blocks=w["push_blocks"], tune=args.tune)
+    info = b.info()
+    x = torch.from_numpy(w["x"]).to(dev)
+    pushes = [x[:, s:s + push_len].contiguous() for s in range(0, n, push_len)]
+    fs_per_step = int(np.sum(n >> bank.level.astype(np.int64)))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for p in pushes:
+            b.push(p)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(_gpu_id(torch, local)) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.5)
+    b.enable_timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    for i in range(args.steps):
+        flush.zero_()                      # L2 flushed between timed steps (untimed)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_wall1 = time.time()
+    kt = b.kernel_times()
+    b.enable_timing(False)
+    total_ms = sum(a.elapsed_time(c) for a, c in ev)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * fs_per_step * args.steps / (total_ms / 1e3)
+
+    # per-block latency: one 1 s block per push, push -> SNR copied out
+    blk = w["block_len"]
+    xb = x[:, :blk].contiguous()
+    zout = torch.empty((1, bank.n_templates, blk), dtype=torch.complex64, device=dev)
+    lat = []
+    for i in range(40):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.push(xb)
+        b.read(blk, stream_id=-1, out=zout)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= 5:
+            lat.append(e0.elapsed_time(e1))
+    lat = np.array(lat)
+
+    # end to end through the host-buffer entry point (copies inside)
+    xh = torch.from_numpy(w["x"]).pin_memory()
+    zh = torch.empty((1, bank.n_templates, push_len), dtype=torch.complex64).pin_memory()
+    xh_pushes = [xh[:, s:s + push_len].contiguous().pin_memory() for s in range(0, n, push_len)]
+    e2e_steps = max(3, min(args.steps, 20))
+    for p in xh_pushes:
+        b.push_host(p, z_out=zh)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for p in xh_pushes:
+            b.push_host(p, z_out=zh)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    b.sync_status()
+
+    if rank != 0:
+        b.close()
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    sampler.stop()
+    clocks = sampler.summary(t_wall0, t_wall1)
+    peaks = _peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_lane_ops = sms * FP32_LANES_PER_SM * sm_max * 1e6
+    peak_tflops = peak_lane_ops / LANE_OPS_PER_FS * FLOPS_PER_FS / 1e12
+    rec_ms, rec_n = kt.get("recur", (0.0, 0))
+    fs_per_launch = fs_per_step * args.steps / max(1, rec_n)
+    achieved = (FLOPS_PER_FS * fs_per_launch) / (rec_ms / max(1, rec_n) / 1e3) / 1e12 if rec_n else 0.0
+    traffic = _traffic("spiir_plain.cu", f"recur_{args.workload}")
+    launches = int(sum(c for _, c in kt.values()))
+    shares = {k: round(v[0] / max(1e-9, sum(u[0] for u in kt.values())), 4) for k, v in kt.items()}
+    cpu_rate, cpu_sample, cores = _cpu_sample(w, 10.0, 256)
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": w["desc"],
+            "n_templates": bank.n_templates,
+            "n_filters": bank.n_filters,
+            "samples_per_step": n,
+            "form": "plain FP32 recursion",
+            "kernel_variant": info["kernel_variant"],
+            "filters_per_lane": info["filters_per_lane"],
+            "time_tile": info["time_tile"],
+            "l2": "flushed between timed steps (256 MB write, untimed)",
+            "parallelism": f"{ws} independent bank replicas" if ws > 1 else "1 GPU",
+        },
+        "real_time_templates": ws * bank.n_templates * (n / 4096.0) / (ms_per_step / 1e3),
+        "p50_block_latency_ms": float(np.percentile(lat, 50)),
+        "p99_block_latency_ms": float(np.percentile(lat, 99)),
+        "kernel_share": shares,
+        "roofline": {
+            "bound": "alu",
+            "kernel": "recur_kernel",
+            "achieved": achieved,
+            "peak": peak_tflops,
+            "unit": "TFLOP/s",
+            "frac": achieved / peak_tflops if peak_tflops else None,
+            "traffic": traffic,
+            "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz "
+                          f"(sm_max_mhz of measured peaks) / {LANE_OPS_PER_FS} lane-ops x "
+                          f"{FLOPS_PER_FS} flops per filter-sample",
+        },
+        "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": cpu_sample},
+        "e2e": {"value": ws * fs_per_step / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(n * 4),
+                "d2h_bytes_per_step": int(bank.n_templates * n * 8)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    b.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="single", choices=["single", "multirate"])
+    ap.add_argument("--tune", type=int, default=0)
+    ap.add_argument("--templates", type=int, default=0,
+                    help="template count (0 = the workload's full size); small cases for ncu")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,224 @@
+/*
+ * spiir.h -- C ABI of libspiir, a GB300 (sm_103a) implementation of Summed
+ * Parallel IIR (SPIIR) filtering and its multi-rate scheme (arXiv:1702.02256).
+ *
+ * What is computed (Sec. 2.1, Eqs. iireq0 and iireq1): every template t is a
+ * bank of complex first-order filters k with pole a_k, gain b_k and integer
+ * delay d_k driven by the real strain x,
+ *
+ *     y_k[n] = a_k * y_k[n-1] + b_k * x[n - d_k],
+ *     z_t[n] = snr_scale * sum_{k in t} y_k[n],      snr_scale = 2*dt,
+ *
+ * and, when n_levels > 1, the multi-rate scheme of Sec. 2.2 (Fig. 1): the
+ * strain is decimated by 2 in succession (Kaiser-window low-pass, Eq.
+ * kaiser_window_filtering), a filter at level i runs at base_rate/2^i on the
+ * level-i strain, and from the lowest rate up each rate's sum is upsampled by
+ * 2 and added to the next rate's sum; level i's own sum is delayed by
+ * D_i = (T-1) + 2*D_{i+1} (D_H = 0) so that the levels line up.
+ *
+ * Conventions shared by every call:
+ *   - Complex arrays on the device are complex64: interleaved (re, im) float32.
+ *   - "Device pointer" means memory the caller allocated on the current CUDA
+ *     device (e.g. a torch tensor). The caller owns it; it must stay valid
+ *     until the work queued on `cuda_stream` has reached it.
+ *   - `cuda_stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *   - Calls do not throw. Each returns a spiir_status; spiir_last_error()
+ *     then holds a one-line message for the calling thread.
+ *   - A bank is used by one host thread at a time.
+ *   - Filter state, strain history and resampler history live on the device
+ *     in the bank between calls: a long series can be pushed in pieces and
+ *     gives the same SNR as one push of the whole series.
+ */
+#ifndef SPIIR_H
+#define SPIIR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spiir_bank *spiir_bank_t;
+
+typedef enum {
+    SPIIR_OK = 0,
+    SPIIR_EINVAL = 1,      /* bad argument: null pointer, size, ordering, range */
+    SPIIR_ENOMEM = 2,      /* a device or host allocation failed */
+    SPIIR_EBUDGET = 3,     /* footprint above desc->hbm_budget_bytes */
+    SPIIR_ECUDA = 4,       /* a CUDA runtime call failed (message has its name) */
+    SPIIR_ETIMEOUT = 5,    /* a bounded device-side wait gave up; results of
+                              that push are not valid, the bank stays usable */
+    SPIIR_ESTATE = 6,      /* call out of order (read before any push, ...) */
+    SPIIR_EUNSUPPORTED = 7 /* valid request this build does not provide */
+} spiir_status;
+
+/* Compute form. PLAIN_FP32 is the per-sample FP32 recursion (all n_levels).
+ * The TC_* forms are the block-parallel tensor-core form for single-rate
+ * banks: over chunks of chunk_len samples the bank is a dense contraction of
+ * the template impulse responses with a Toeplitz view of x, plus per-filter
+ * power panels a_k^j applied to filter states carried between chunks in FP64.
+ * TC_FP16 / TC_BF16 round the panel and strain operands to that type (FP32
+ * accumulation); TC_BF16X2 splits each operand into a bf16 high and low part. */
+typedef enum {
+    SPIIR_PLAIN_FP32 = 0,
+    SPIIR_TC_FP16 = 1,
+    SPIIR_TC_BF16 = 2,
+    SPIIR_TC_BF16X2 = 3
+} spiir_mode;
+
+/* Bank description. All arrays are host memory owned by the caller and are
+ * copied during spiir_bank_create; they may be freed when it returns. */
+typedef struct {
+    int32_t n_templates;    /* >= 1 */
+    int32_t n_levels;       /* 1 = single rate; up to 12 */
+    int32_t base_rate;      /* Hz of level 0 (the input rate), e.g. 4096 */
+    int32_t n_streams;      /* independent detector streams, >= 1 */
+    int32_t block_len;      /* samples per push unit at the base rate; a
+                               multiple of 2^(n_levels-1) */
+    int32_t max_push_blocks;/* largest push, in blocks (output ring size) */
+    int64_t n_filters;      /* >= 0; templates may have zero filters */
+    const float *a_re, *a_im;     /* pole a_k, at the filter's own rate */
+    const float *b_re, *b_im;     /* gain b_k */
+    const int32_t *delay;         /* d_k >= 0, samples at the filter's rate */
+    const int32_t *template_id;   /* in [0, n_templates) */
+    const int8_t *level;          /* in [0, n_levels); NULL = all level 0 */
+    const float *h_down, *h_up;   /* resampling taps, n_taps each; NULL =
+                                     built-in 60 dB Kaiser low-pass */
+    int32_t n_taps;               /* even, 2..64; 0 = 32 */
+    int32_t align;                /* 1 = delay level sums by D_i (default
+                                     when n_levels > 1), 0 = no delay */
+    float snr_scale;              /* 0 = 2/base_rate (2*dt, Eq. iireq1) */
+    spiir_mode mode;
+    int32_t chunk_len;            /* TC forms: chunk length L (0 = 256) */
+    int32_t tune;                 /* 0 = built-in tile choice, 1 = time the
+                                     compiled variants at create and keep
+                                     the fastest, -(v+1) = use variant v */
+    int64_t hbm_budget_bytes;     /* 0 = no limit; else create fails with
+                                     SPIIR_EBUDGET above it */
+} spiir_bank_desc;
+
+/* Read-only facts about a created bank. */
+typedef struct {
+    int64_t footprint_bytes;   /* device bytes the bank holds */
+    int64_t n_slots;           /* filter slots after packing (>= n_filters) */
+    int64_t filter_samples_per_block; /* sum over filters of own-rate samples
+                                         in one block, per stream */
+    int32_t n_warp_tasks;
+    int32_t n_cta_items;
+    int32_t filters_per_lane;  /* largest F chosen by the packer */
+    int32_t time_tile;         /* T of the recursion kernel */
+    int32_t kernel_variant;    /* index of the compiled recursion variant */
+    int32_t max_delay;         /* largest d_k (+ alignment) over levels */
+    int32_t tc_fir_len;        /* TC forms: F (> max delay), else 0 */
+    int32_t graph_captured;    /* 1 if pushes replay a CUDA graph */
+    int32_t n_units;           /* (template, level, part) units */
+    float smem_ways;           /* mean shared-memory wavefronts per round of
+                                  32 delayed-input reads (1 = no conflicts) */
+    float slot_fill;           /* n_filters / n_slots */
+} spiir_bank_info;
+
+/* Create a bank: validate the description, place filters into warp tasks
+ * (template-major per level, lane groups sized to the template's filter
+ * count), upload coefficients, allocate device state, history and output
+ * ring, and zero the state (Sec. 2.1: the recursion starts from y = 0 with
+ * x[n < 0] = 0). Work is queued on cuda_stream and synchronised before return.
+ * Errors: EINVAL (description), EBUDGET, ENOMEM, ECUDA, EUNSUPPORTED. */
+spiir_status spiir_bank_create(const spiir_bank_desc *desc, void *cuda_stream,
+                               spiir_bank_t *out);
+
+/* Filter n_samples more samples of one stream (stream_id in [0, n_streams))
+ * or of all streams (stream_id = -1; x_dev is then [n_streams][n_samples]).
+ * x_dev: device float32, contiguous. n_samples: a positive multiple of
+ * block_len, at most block_len * max_push_blocks. Asynchronous on
+ * cuda_stream; the SNR of these samples replaces the bank's output ring for
+ * the pushed stream(s). Errors: EINVAL; ETIMEOUT/ECUDA from an earlier push. */
+spiir_status spiir_push_block(spiir_bank_t bank, int32_t stream_id,
+                              const float *x_dev, int64_t n_samples,
+                              void *cuda_stream);
+
+/* Copy the SNR of the most recent push of stream_id (or of every stream for
+ * -1) into z_dev: complex64 [n_templates][n_samples] per stream, streams
+ * outermost, the last n_samples samples of that push, z = snr_scale * sum.
+ * Asynchronous device-to-device copy on cuda_stream.
+ * Errors: EINVAL, ESTATE (nothing pushed on that stream yet). */
+spiir_status spiir_read_snr(spiir_bank_t bank, int32_t stream_id, void *z_dev,
+                            int64_t n_samples, void *cuda_stream);
+
+/* Zero the filter state, strain history and resampler history of one stream
+ * (or all, -1): the next push behaves like the first push of a new bank. */
+spiir_status spiir_state_reset(spiir_bank_t bank, int32_t stream_id,
+                               void *cuda_stream);
+
+/* End-to-end call on host buffers: copy x_host [n_streams or 1][n_samples]
+ * to the device, push, and copy the SNR back into z_host (layout of
+ * spiir_read_snr). Pinned host memory makes the copies asynchronous; the
+ * call returns after the SNR is in z_host. */
+spiir_status spiir_push_block_host(spiir_bank_t bank, int32_t stream_id,
+                                   const float *x_host, int64_t n_samples,
+                                   void *z_host, void *cuda_stream);
+
+/* Device bytes a bank with this description would hold (filters, state,
+ * history, scratch, output ring), for admission control. -1 on a bad desc. */
+int64_t spiir_bank_footprint(const spiir_bank_desc *desc);
+
+/* Facts about a created bank. */
+spiir_status spiir_bank_get_info(spiir_bank_t bank, spiir_bank_info *info);
+
+/* The packing a description would get, computed on the host only (no device
+ * work, no CUDA call): the fields of spiir_bank_get_info for the variant that
+ * desc->tune selects (the built-in choice when tune >= 0). */
+spiir_status spiir_bank_plan(const spiir_bank_desc *desc, spiir_bank_info *info);
+
+/* Wait for the bank's queued work and report the device status word: OK, or
+ * ETIMEOUT if a bounded device wait gave up since the last call (the word is
+ * then cleared). */
+spiir_status spiir_bank_sync_status(spiir_bank_t bank);
+
+/* Kernel kinds for per-kernel timing. */
+typedef enum {
+    SPIIR_K_PROLOGUE = 0, /* strain history shift + new samples */
+    SPIIR_K_DECIMATE = 1, /* x2 decimation cascade */
+    SPIIR_K_RECUR = 2,    /* FP32 recursion + per-template sum */
+    SPIIR_K_COMBINE = 3,  /* parts + x2 upsample + upstream sum + scale */
+    SPIIR_K_TC_STAGE = 4, /* TC form: strain operand staging */
+    SPIIR_K_TC_FIR = 5,   /* TC form: impulse-response x Toeplitz(x) GEMM */
+    SPIIR_K_TC_CARRY = 6, /* TC form: power panels, FP64 carry, state GEMMs */
+    SPIIR_K_OTHER = 7,
+    SPIIR_K_COUNT = 8
+} spiir_kernel_kind;
+
+typedef struct {
+    double ms[SPIIR_K_COUNT];        /* summed device time per kind */
+    int64_t launches[SPIIR_K_COUNT]; /* launches per kind */
+} spiir_kernel_times;
+
+/* Tracing: while enabled, every push records a CUDA event pair on its own
+ * stream around each kernel it launches. */
+spiir_status spiir_bank_enable_timing(spiir_bank_t bank, int32_t enable);
+
+/* Wait for the recorded events, return the per-kind sums since the previous
+ * call (or since timing was enabled), and start a new count. */
+spiir_status spiir_bank_kernel_times(spiir_bank_t bank, spiir_kernel_times *out);
+
+/* Release everything the bank holds. NULL is ignored. */
+void spiir_bank_destroy(spiir_bank_t bank);
+
+/* The library's own resampling taps (Sec. 2.2): n_taps-tap Kaiser-window
+ * low-pass with cutoff at half the input Nyquist frequency, window parameter
+ * from Kaiser's formula for atten_db, unit DC gain, float32. */
+spiir_status spiir_kaiser_taps(int32_t n_taps, double atten_db, float *out);
+
+/* The rate-assignment rule of Sec. 2.2 on a base-rate pole a: the level
+ * whose rate base_rate/2^i is the smallest that is >= twice the filter's band
+ * edge |arg a| * base_rate / (2 pi). */
+int32_t spiir_assign_level(float a_re, float a_im, int32_t base_rate,
+                           int32_t n_levels);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *spiir_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPIIR_H */

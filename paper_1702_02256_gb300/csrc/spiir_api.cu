@@ -1,0 +1,1016 @@
+// spiir_api.cu -- host side of libspiir: the C ABI of include/spiir.h.
+//
+// Bank creation turns the filter list into warp tasks for the FP32 recursion
+// kernel (spiir_plain.cu):
+//   * per level, each template's filters form a unit (split into parts of at
+//     most 32*FMAX filters);
+//   * a unit gets a group of G = 2^g lanes (the smallest with G*FMAX >= its
+//     filter count) and F rounds, F = ceil(count/G) rounded up to even;
+//   * units of the same (level, G, F) share a warp, 32/G units per warp;
+//   * within a warp, each round's 32 filters are picked so that their strain
+//     window offsets fall in distinct shared-memory banks where the pools
+//     allow it (all lanes read x[n - d_k] in the same instruction);
+//   * up to SPIIR_CTA_WARPS warps of one level and F form a CTA item.
+// The level alignment delays D_i of the multi-rate scheme are folded into
+// the filter delays (a delayed sum is the sum of delayed filters), so the
+// upsample-and-add step needs no delay line.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "spiir.h"
+#include "spiir_internal.h"
+#include "spiir_tc.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+spiir_status fail(spiir_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CUDA_TRY(call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(e_ == cudaErrorMemoryAllocation ? SPIIR_ENOMEM : SPIIR_ECUDA,    \
+                        "%s: %s", #call, cudaGetErrorString(e_));                        \
+    } while (0)
+
+inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+constexpr int kSmemMax = 227 * 1024;
+constexpr int kWindowFloats = 12288;  // preferred strain window (48 KB)
+
+// The library's resampling taps: Kaiser-window-tapered ideal low-pass with
+// cutoff at half the input Nyquist frequency (Sec. 2.2). I0 by its series.
+double lib_i0(double x) {
+    const double q = 0.25 * x * x;
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 1000; ++k) {
+        term *= q / ((double)k * (double)k);
+        sum += term;
+        if (term <= sum * 1e-18) break;
+    }
+    return sum;
+}
+
+double lib_kaiser_beta(double A) {
+    if (A > 50.0) return 0.1102 * (A - 8.7);
+    if (A >= 21.0) return 0.5842 * std::pow(A - 21.0, 0.4) + 0.07886 * (A - 21.0);
+    return 0.0;
+}
+
+void lib_kaiser_taps(int n, double A, float *out) {
+    const double beta = lib_kaiser_beta(A), norm = lib_i0(beta);
+    std::vector<double> h(n);
+    double s = 0.0;
+    const double c = 0.5 * (n - 1);
+    for (int i = 0; i < n; ++i) {
+        const double m = i - c;
+        const double x = m * M_PI * 0.5;
+        const double ideal = (m == 0.0) ? 0.5 : std::sin(x) / (M_PI * m);
+        const double u = (i - c) / c;
+        const double w = lib_i0(beta * std::sqrt(std::max(0.0, 1.0 - u * u))) / norm;
+        h[i] = ideal * w;
+        s += h[i];
+    }
+    for (int i = 0; i < n; ++i) out[i] = (float)(h[i] / s);
+}
+
+// ---------------------------------------------------------------------------
+// Plan: sizes and packed arrays for one kernel variant
+// ---------------------------------------------------------------------------
+
+struct Plan {
+    int variant = 0, T = 32, FMAX = 8;
+    int n_levels = 1, H = 0, n_taps = 32, align = 0;
+    int hist[SPIIR_MAX_LEVELS] = {};
+    int seg[SPIIR_MAX_LEVELS] = {};
+    int64_t max_n[SPIIR_MAX_LEVELS] = {};
+    int64_t xbuf_off[SPIIR_MAX_LEVELS] = {};
+    int64_t part_rows[SPIIR_MAX_LEVELS] = {};
+    int64_t part_base[SPIIR_MAX_LEVELS] = {};
+    int64_t part_stride[SPIIR_MAX_LEVELS] = {};
+    int64_t ubuf_off[SPIIR_MAX_LEVELS] = {};
+    int32_t ubuf_stride[SPIIR_MAX_LEVELS] = {};
+    int64_t xbuf_stream_stride = 0, part_stream_stride = 0, ubuf_stream_stride = 0;
+    int64_t ring_len = 0;
+    int smem_bytes = 0;
+    bool need_combine = false;
+    int max_F = 0, max_delay = 0;
+    int64_t n_slots = 0;
+    int64_t fs_per_block = 0;
+    // packed arrays
+    std::vector<float> are, aim, bre, bim;
+    std::vector<int32_t> xoff;
+    std::vector<WarpTask> tasks;
+    std::vector<CtaItem> items;
+    std::vector<int32_t> task_out;
+    std::vector<int32_t> comb_ptr, comb_rows;
+    int64_t lds_rounds = 0, lds_wavefronts = 0;
+    int64_t n_units = 0;
+};
+
+struct Unit {
+    int level, tmpl;
+    std::vector<int64_t> filt;
+    int G, F;
+    int32_t dest;
+};
+
+int64_t align_delay(int level, int n_levels, int n_taps, int align) {
+    if (!align) return 0;
+    int64_t D = 0;
+    for (int i = n_levels - 2; i >= level; --i) D = (n_taps - 1) + 2 * D;
+    return D;
+}
+
+spiir_status validate(const spiir_bank_desc *d) {
+    if (!d) return fail(SPIIR_EINVAL, "desc is NULL");
+    if (d->n_templates < 1) return fail(SPIIR_EINVAL, "n_templates must be >= 1");
+    if (d->n_levels < 1 || d->n_levels > SPIIR_MAX_LEVELS)
+        return fail(SPIIR_EINVAL, "n_levels must be in [1, %d]", SPIIR_MAX_LEVELS);
+    if (d->base_rate <= 0) return fail(SPIIR_EINVAL, "base_rate must be > 0");
+    if (d->n_streams < 1) return fail(SPIIR_EINVAL, "n_streams must be >= 1");
+    if (d->block_len < 1) return fail(SPIIR_EINVAL, "block_len must be >= 1");
+    if (d->block_len % (1 << (d->n_levels - 1)) != 0)
+        return fail(SPIIR_EINVAL, "block_len must be a multiple of 2^(n_levels-1)");
+    if ((d->block_len >> (d->n_levels - 1)) % 4 != 0)
+        return fail(SPIIR_EINVAL, "block_len / 2^(n_levels-1) must be a multiple of 4");
+    if (d->max_push_blocks < 1) return fail(SPIIR_EINVAL, "max_push_blocks must be >= 1");
+    if ((int64_t)d->block_len * d->max_push_blocks > (1ll << 30))
+        return fail(SPIIR_EINVAL, "block_len * max_push_blocks too large");
+    if (d->n_filters < 0) return fail(SPIIR_EINVAL, "n_filters must be >= 0");
+    if (d->n_filters > 0 && (!d->a_re || !d->a_im || !d->b_re || !d->b_im || !d->delay ||
+                             !d->template_id))
+        return fail(SPIIR_EINVAL, "filter arrays must not be NULL");
+    const int nt = d->n_taps ? d->n_taps : 32;
+    if (nt < 2 || nt > SPIIR_MAX_TAPS || (nt & 1))
+        return fail(SPIIR_EINVAL, "n_taps must be even and in [2, %d]", SPIIR_MAX_TAPS);
+    if ((d->h_down == nullptr) != (d->h_up == nullptr))
+        return fail(SPIIR_EINVAL, "give both h_down and h_up or neither");
+    if (d->mode < SPIIR_PLAIN_FP32 || d->mode > SPIIR_TC_BF16X2)
+        return fail(SPIIR_EINVAL, "unknown mode %d", (int)d->mode);
+    if (d->mode != SPIIR_PLAIN_FP32 && d->n_levels != 1)
+        return fail(SPIIR_EUNSUPPORTED, "tensor-core forms take single-rate banks");
+    if (d->hbm_budget_bytes < 0) return fail(SPIIR_EINVAL, "hbm_budget_bytes must be >= 0");
+    for (int64_t k = 0; k < d->n_filters; ++k) {
+        if (d->template_id[k] < 0 || d->template_id[k] >= d->n_templates)
+            return fail(SPIIR_EINVAL, "template_id[%lld] out of range", (long long)k);
+        if (d->delay[k] < 0 || d->delay[k] > (1 << 20))
+            return fail(SPIIR_EINVAL, "delay[%lld] out of range", (long long)k);
+        if (d->level && (d->level[k] < 0 || d->level[k] >= d->n_levels))
+            return fail(SPIIR_EINVAL, "level[%lld] out of range", (long long)k);
+        if (!std::isfinite(d->a_re[k]) || !std::isfinite(d->a_im[k]) ||
+            !std::isfinite(d->b_re[k]) || !std::isfinite(d->b_im[k]))
+            return fail(SPIIR_EINVAL, "filter %lld has a non-finite coefficient", (long long)k);
+    }
+    return SPIIR_OK;
+}
+
+int default_variant(const spiir_bank_desc *d);
+
+// Variant requested by desc->tune < 0, or the built-in choice.
+int chosen_variant(const spiir_bank_desc *d) {
+    if (d->tune < 0) {
+        const int v = -d->tune - 1;
+        if (v < spiir_recur_variant_count()) return v;
+    }
+    return default_variant(d);
+}
+
+void plan_info(const spiir_bank_desc *d, const Plan &p, spiir_bank_info *info) {
+    info->n_slots = p.n_slots;
+    info->filter_samples_per_block = p.fs_per_block;
+    info->n_warp_tasks = (int32_t)p.tasks.size();
+    info->n_cta_items = (int32_t)p.items.size();
+    info->filters_per_lane = p.max_F;
+    info->time_tile = p.T;
+    info->kernel_variant = p.variant;
+    info->max_delay = p.max_delay;
+    info->tc_fir_len = 0;
+    info->graph_captured = 0;
+    info->n_units = (int32_t)p.n_units;
+    info->smem_ways = p.lds_rounds ? (float)p.lds_wavefronts / (float)p.lds_rounds : 1.f;
+    info->slot_fill = p.n_slots ? (float)d->n_filters / (float)p.n_slots : 1.f;
+}
+
+int default_variant(const spiir_bank_desc *d) {
+    // per (template, level) filter counts
+    const int L = d->n_levels;
+    std::vector<int64_t> cnt((size_t)d->n_templates * L, 0);
+    for (int64_t k = 0; k < d->n_filters; ++k)
+        cnt[(size_t)d->template_id[k] * L + (d->level ? d->level[k] : 0)]++;
+    int64_t mx = 0;
+    for (auto c : cnt) mx = std::max(mx, c);
+    return mx > 256 ? 1 : 0;
+}
+
+// Builds the plan. With arrays == false only the sizes are computed.
+spiir_status make_plan(const spiir_bank_desc *d, int variant, bool arrays, Plan &p) {
+    p = Plan();
+    p.variant = variant;
+    spiir_recur_variant_shape(variant, &p.T, &p.FMAX);
+    p.n_levels = d->n_levels;
+    p.H = d->n_levels - 1;
+    p.n_taps = d->n_taps ? d->n_taps : 32;
+    p.align = (d->n_levels > 1) ? (d->align != 0) : 0;
+    const int L = p.n_levels;
+    const int64_t push_max = (int64_t)d->block_len * d->max_push_blocks;
+
+    // filters per (level, template)
+    std::vector<std::vector<int64_t>> lists((size_t)L * d->n_templates);
+    std::vector<int> maxd(L, 0);
+    for (int64_t k = 0; k < d->n_filters; ++k) {
+        const int lv = d->level ? d->level[k] : 0;
+        lists[(size_t)lv * d->n_templates + d->template_id[k]].push_back(k);
+        maxd[lv] = std::max(maxd[lv], d->delay[k]);
+    }
+    int64_t off = 0;
+    for (int i = 0; i < L; ++i) {
+        const int64_t D = align_delay(i, L, p.n_taps, p.align);
+        int64_t h = (int64_t)maxd[i] + D;
+        if (i < p.H) h = std::max<int64_t>(h, p.n_taps - 1);
+        h = round_up(h, 4);
+        if (h + p.T + 8 > (kSmemMax - 64) / 4)
+            return fail(SPIIR_EUNSUPPORTED, "delay %lld at level %d does not fit shared memory",
+                        (long long)h, i);
+        p.hist[i] = (int)h;
+        p.max_delay = std::max<int>(p.max_delay, (int)(maxd[i] + D));
+        p.max_n[i] = push_max >> i;
+        int64_t W = std::max<int64_t>(kWindowFloats, h + 4 * p.T);
+        W = std::min<int64_t>(W, (kSmemMax - 64) / 4);
+        int64_t sg = (W - h) / p.T * p.T;
+        if (sg < p.T) sg = p.T;
+        if (sg >= p.max_n[i]) sg = round_up(p.max_n[i], 4);
+        p.seg[i] = (int)sg;
+        p.smem_bytes = std::max<int>(p.smem_bytes, (int)(16 + 4 * (h + sg) + 64));
+        p.xbuf_off[i] = off;
+        off += round_up(h + p.max_n[i] + 64, 4);
+    }
+    p.xbuf_stream_stride = off;
+    p.ring_len = round_up(push_max, 2);
+
+    // units
+    std::vector<Unit> units;
+    int64_t rows[SPIIR_MAX_LEVELS] = {};
+    bool all_single = true;
+    for (int i = 0; i < L; ++i)
+        for (int t = 0; t < d->n_templates; ++t) {
+            const auto &f = lists[(size_t)i * d->n_templates + t];
+            if ((int64_t)f.size() > 32ll * p.FMAX) all_single = false;
+        }
+    p.need_combine = (L > 1) || !all_single;
+    p.comb_ptr.assign((size_t)d->n_templates * L + 1, 0);
+    std::vector<std::vector<int32_t>> comb((size_t)d->n_templates * L);
+    for (int i = 0; i < L; ++i) {
+        for (int t = 0; t < d->n_templates; ++t) {
+            const auto &f = lists[(size_t)i * d->n_templates + t];
+            const int64_t M = (int64_t)f.size();
+            p.fs_per_block += M * (d->block_len >> i);
+            if (M == 0) continue;
+            const int64_t cap = 32ll * p.FMAX;
+            const int64_t parts = (M + cap - 1) / cap;
+            for (int64_t q = 0; q < parts; ++q) {
+                const int64_t b0 = M * q / parts, b1 = M * (q + 1) / parts;
+                Unit u;
+                u.level = i;
+                u.tmpl = t;
+                u.filt.assign(f.begin() + b0, f.begin() + b1);
+                const int64_t m = b1 - b0;
+                int G = 1;
+                while ((int64_t)G * p.FMAX < m) G *= 2;
+                int F = (int)((m + G - 1) / G);
+                F += F & 1;
+                if (F < 2) F = 2;
+                u.G = G;
+                u.F = F;
+                if (!p.need_combine) {
+                    u.dest = t;
+                } else {
+                    const int64_t row = rows[i]++;
+                    u.dest = -(int32_t)(row + 1);
+                    comb[(size_t)t * L + i].push_back((int32_t)row);
+                }
+                units.push_back(std::move(u));
+            }
+        }
+    }
+    for (size_t j = 0; j < comb.size(); ++j) {
+        p.comb_ptr[j + 1] = p.comb_ptr[j] + (int32_t)comb[j].size();
+        for (auto r : comb[j]) p.comb_rows.push_back(r);
+    }
+    int64_t poff = 0, uoff = 0;
+    for (int i = 0; i < L; ++i) {
+        p.part_rows[i] = rows[i];
+        p.part_stride[i] = round_up(p.max_n[i], 2);
+        p.part_base[i] = poff;
+        poff += rows[i] * p.part_stride[i];
+        if (i > 0) {
+            p.ubuf_stride[i] = (int32_t)round_up(SPIIR_UHIST + p.max_n[i], 2);
+            p.ubuf_off[i] = uoff;
+            uoff += (int64_t)d->n_templates * p.ubuf_stride[i];
+        }
+    }
+    p.part_stream_stride = poff;
+    p.ubuf_stream_stride = uoff;
+
+    // warps: classes (level, G, F)
+    std::stable_sort(units.begin(), units.end(), [](const Unit &a, const Unit &b) {
+        if (a.level != b.level) return a.level < b.level;
+        if (a.F != b.F) return a.F > b.F;
+        return a.G < b.G;
+    });
+    struct WarpPlan {
+        int level, G, F;
+        std::vector<int> units;
+    };
+    std::vector<WarpPlan> warps;
+    for (size_t u = 0; u < units.size();) {
+        WarpPlan w{units[u].level, units[u].G, units[u].F, {}};
+        const int per = 32 / w.G;
+        while (u < units.size() && (int)w.units.size() < per && units[u].level == w.level &&
+               units[u].G == w.G && units[u].F == w.F)
+            w.units.push_back((int)u++);
+        warps.push_back(std::move(w));
+    }
+    // CTA items: warps of one (level, F), heaviest first
+    std::vector<int> order(warps.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const int64_t wa = (int64_t)warps[a].F * p.max_n[warps[a].level];
+        const int64_t wb = (int64_t)warps[b].F * p.max_n[warps[b].level];
+        if (wa != wb) return wa > wb;
+        return warps[a].level < warps[b].level;
+    });
+    std::vector<std::vector<int>> item_warps;
+    for (size_t i = 0; i < order.size();) {
+        std::vector<int> it;
+        const int lv = warps[order[i]].level, F = warps[order[i]].F;
+        while (i < order.size() && (int)it.size() < SPIIR_CTA_WARPS &&
+               warps[order[i]].level == lv && warps[order[i]].F == F)
+            it.push_back(order[i++]);
+        item_warps.push_back(std::move(it));
+    }
+
+    p.n_units = (int64_t)units.size();
+    int64_t n_slots = 0;
+    for (auto &w : warps) n_slots += 32ll * w.F;
+    p.n_slots = n_slots;
+    for (auto &w : warps) p.max_F = std::max(p.max_F, w.F);
+    if (!arrays) {
+        p.tasks.resize(warps.size());
+        p.items.resize(item_warps.size());
+        return SPIIR_OK;
+    }
+
+    p.are.assign(n_slots, 0.f);
+    p.aim.assign(n_slots, 0.f);
+    p.bre.assign(n_slots, 0.f);
+    p.bim.assign(n_slots, 0.f);
+    p.xoff.assign(n_slots, 0);
+    int64_t slot_base = 0;
+    for (auto &iw : item_warps) {
+        CtaItem ci;
+        ci.level = warps[iw[0]].level;
+        ci.task_begin = (int32_t)p.tasks.size();
+        ci.task_count = (int32_t)iw.size();
+        ci.F = warps[iw[0]].F;
+        for (int wi : iw) {
+            const WarpPlan &w = warps[wi];
+            const int g = w.G, F = w.F, lv = w.level;
+            const int64_t D = align_delay(lv, L, p.n_taps, p.align);
+            const int hist = p.hist[lv];
+            WarpTask wt;
+            wt.slot_base = (int32_t)slot_base;
+            wt.F = (int16_t)F;
+            int gl = 0;
+            while ((1 << gl) < g) ++gl;
+            wt.g_log2 = (int8_t)gl;
+            wt.level = (int8_t)lv;
+            wt.out_base = (int32_t)p.task_out.size();
+            wt.n_groups = (int32_t)w.units.size();
+            for (int u : w.units) p.task_out.push_back(units[u].dest);
+            // per-group pools bucketed by shared-memory bank of the offset
+            const int ng = (int)w.units.size();
+            std::vector<std::vector<std::vector<int64_t>>> pool(ng,
+                                                                std::vector<std::vector<int64_t>>(32));
+            std::vector<int> rot(ng, 0);
+            for (int q = 0; q < ng; ++q)
+                for (int64_t k : units[w.units[q]].filt) {
+                    const int64_t xo = hist - (d->delay[k] + D);
+                    pool[q][xo & 31].push_back(k);
+                }
+            for (int r = 0; r < F; ++r) {
+                uint32_t used = 0;
+                int wave = 0;
+                int per_bank[32] = {};
+                for (int l = 0; l < 32; ++l) {
+                    const int64_t s = slot_base + (int64_t)r * 32 + l;
+                    const int q = l / g;
+                    int64_t pick = -1;
+                    if (q < ng) {
+                        // fullest bank not yet read this round, else the fullest
+                        // bank (a conflict); drawing from the fullest keeps the
+                        // pools even so later rounds still find free banks
+                        auto &pl = pool[q];
+                        int best = -1;
+                        for (int pass = 0; pass < 2 && best < 0; ++pass) {
+                            size_t most = 0;
+                            for (int c = 0; c < 32; ++c) {
+                                const int b = (rot[q] + c) & 31;
+                                if (pass == 0 && (used >> b & 1u)) continue;
+                                if (pl[b].size() > most) {
+                                    most = pl[b].size();
+                                    best = b;
+                                }
+                            }
+                        }
+                        if (best >= 0) {
+                            pick = pl[best].back();
+                            pl[best].pop_back();
+                            rot[q] = (best + 1) & 31;
+                        }
+                    }
+                    int32_t xo;
+                    if (pick >= 0) {
+                        p.are[s] = d->a_re[pick];
+                        p.aim[s] = d->a_im[pick];
+                        p.bre[s] = d->b_re[pick];
+                        p.bim[s] = d->b_im[pick];
+                        xo = (int32_t)(hist - (d->delay[pick] + D));
+                    } else {
+                        // inert padding slot: read a free bank inside the window
+                        int b = 0;
+                        while (b < 32 && (used >> b & 1u)) ++b;
+                        b &= 31;
+                        xo = hist - ((hist - b) & 31);
+                        if (xo < 0) xo = hist;
+                    }
+                    p.xoff[s] = xo;
+                    used |= 1u << (xo & 31);
+                    per_bank[xo & 31]++;
+                }
+                for (int b = 0; b < 32; ++b) wave = std::max(wave, per_bank[b]);
+                p.lds_rounds++;
+                p.lds_wavefronts += wave;
+            }
+            slot_base += 32ll * F;
+            p.tasks.push_back(wt);
+        }
+        p.items.push_back(ci);
+    }
+    return SPIIR_OK;
+}
+
+int64_t plan_footprint(const spiir_bank_desc *d, const Plan &p) {
+    const int64_t S = d->n_streams;
+    int64_t b = 0;
+    b += p.n_slots * (4 * 4 + 4);                        // coefficients + offsets
+    b += (int64_t)p.tasks.size() * sizeof(WarpTask);
+    b += (int64_t)p.items.size() * sizeof(CtaItem);
+    b += (int64_t)p.tasks.size() * 32 * 4;               // task_out (upper bound)
+    b += ((int64_t)d->n_templates * p.n_levels + 1) * 4 + p.n_slots * 4;  // comb lists (bound)
+    b += S * p.n_slots * 8;                              // state
+    b += S * p.xbuf_stream_stride * 4;                   // strain windows
+    b += S * p.part_stream_stride * 8;                   // partial sums
+    b += S * p.ubuf_stream_stride * 8;                   // upsampler rows
+    b += S * (int64_t)d->n_templates * p.ring_len * 8;   // output ring
+    b += S * p.ring_len * 4;                             // host-call staging
+    b += 256;
+    return b;
+}
+
+template <typename T>
+spiir_status upload(T **dst, const std::vector<T> &src, cudaStream_t s) {
+    *dst = nullptr;
+    if (src.empty()) return SPIIR_OK;
+    CUDA_TRY(cudaMalloc((void **)dst, src.size() * sizeof(T)));
+    CUDA_TRY(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return SPIIR_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// The bank
+// ---------------------------------------------------------------------------
+
+struct spiir_bank {
+    spiir_bank_desc d;
+    Plan p;
+    float scale = 0.f;
+    std::vector<float> h_down, h_up;
+    int device = 0;
+    // device arrays
+    float *are = nullptr, *aim = nullptr, *bre = nullptr, *bim = nullptr;
+    int32_t *xoff = nullptr;
+    WarpTask *tasks = nullptr;
+    CtaItem *items = nullptr;
+    int32_t *task_out = nullptr, *comb_ptr = nullptr, *comb_rows = nullptr;
+    float2 *state = nullptr, *partial = nullptr, *ubuf = nullptr, *z = nullptr;
+    float *xbuf = nullptr, *xstage = nullptr;
+    unsigned int *status = nullptr;
+    std::vector<int64_t> last_n;
+    int64_t footprint = 0;
+    int64_t n_filters = 0;
+    TcBank *tc = nullptr;
+    KernelTimer *timer = nullptr;
+
+    void free_device() {
+        void *ptrs[] = {are, aim, bre, bim, xoff, tasks, items, task_out, comb_ptr, comb_rows,
+                        state, partial, ubuf, z, xbuf, xstage, status};
+        for (void *q : ptrs)
+            if (q) cudaFree(q);
+        are = aim = bre = bim = nullptr;
+        xoff = nullptr;
+        tasks = nullptr;
+        items = nullptr;
+        task_out = comb_ptr = comb_rows = nullptr;
+        state = partial = ubuf = z = nullptr;
+        xbuf = xstage = nullptr;
+        status = nullptr;
+        if (tc) {
+            spiir_tc_destroy(tc);
+            tc = nullptr;
+        }
+        if (timer) {
+            timer->release();
+            delete timer;
+            timer = nullptr;
+        }
+    }
+};
+
+namespace {
+
+spiir_status alloc_plain(spiir_bank *b, cudaStream_t s) {
+    const Plan &p = b->p;
+    const int64_t S = b->d.n_streams;
+    spiir_status st;
+    if ((st = upload(&b->are, p.are, s))) return st;
+    if ((st = upload(&b->aim, p.aim, s))) return st;
+    if ((st = upload(&b->bre, p.bre, s))) return st;
+    if ((st = upload(&b->bim, p.bim, s))) return st;
+    if ((st = upload(&b->xoff, p.xoff, s))) return st;
+    if ((st = upload(&b->tasks, p.tasks, s))) return st;
+    if ((st = upload(&b->items, p.items, s))) return st;
+    if ((st = upload(&b->task_out, p.task_out, s))) return st;
+    if ((st = upload(&b->comb_ptr, p.comb_ptr, s))) return st;
+    if ((st = upload(&b->comb_rows, p.comb_rows, s))) return st;
+    CUDA_TRY(cudaMalloc((void **)&b->state, std::max<int64_t>(1, S * p.n_slots) * sizeof(float2)));
+    CUDA_TRY(cudaMalloc((void **)&b->xbuf, S * p.xbuf_stream_stride * sizeof(float)));
+    if (p.part_stream_stride)
+        CUDA_TRY(cudaMalloc((void **)&b->partial, S * p.part_stream_stride * sizeof(float2)));
+    if (p.ubuf_stream_stride)
+        CUDA_TRY(cudaMalloc((void **)&b->ubuf, S * p.ubuf_stream_stride * sizeof(float2)));
+    CUDA_TRY(cudaMalloc((void **)&b->z, S * (int64_t)b->d.n_templates * p.ring_len * sizeof(float2)));
+    CUDA_TRY(cudaMalloc((void **)&b->xstage, S * p.ring_len * sizeof(float)));
+    CUDA_TRY(cudaMalloc((void **)&b->status, sizeof(unsigned int)));
+    CUDA_TRY(cudaMemsetAsync(b->state, 0, std::max<int64_t>(1, S * p.n_slots) * sizeof(float2), s));
+    CUDA_TRY(cudaMemsetAsync(b->xbuf, 0, S * p.xbuf_stream_stride * sizeof(float), s));
+    if (b->ubuf) CUDA_TRY(cudaMemsetAsync(b->ubuf, 0, S * p.ubuf_stream_stride * sizeof(float2), s));
+    CUDA_TRY(cudaMemsetAsync(b->z, 0, S * (int64_t)b->d.n_templates * p.ring_len * sizeof(float2), s));
+    CUDA_TRY(cudaMemsetAsync(b->status, 0, sizeof(unsigned int), s));
+    CUDA_TRY(spiir_recur_prepare(p.variant, p.smem_bytes));
+    return SPIIR_OK;
+}
+
+void level_args(const spiir_bank *b, int64_t n, int64_t n_prev, LevelArgs *lev) {
+    const Plan &p = b->p;
+    for (int i = 0; i < p.n_levels; ++i) {
+        LevelArgs &L = lev[i];
+        L.hist = p.hist[i];
+        L.n = (int32_t)(n >> i);
+        L.seg = p.seg[i];
+        L.n_prev = (int32_t)(n_prev >> i);
+        L.part_base = p.part_base[i];
+        L.part_stride = p.part_stride[i];
+        L.xbuf_off = p.xbuf_off[i];
+        L.ubuf_off = p.ubuf_off[i];
+        L.ubuf_stride = p.ubuf_stride[i];
+        L.pad = 0;
+    }
+}
+
+spiir_status push_plain(spiir_bank *b, int s0, int count, const float *x, int64_t x_stride,
+                        int64_t n, cudaStream_t st) {
+    const Plan &p = b->p;
+    const int64_t n_prev = b->last_n[s0];
+    PrologueArgs pa{};
+    pa.xbuf = b->xbuf;
+    pa.xbuf_stream_stride = p.xbuf_stream_stride;
+    pa.x_in = x;
+    pa.x_in_stream_stride = x_stride;
+    pa.stream0 = s0;
+    pa.n_levels = p.n_levels;
+    level_args(b, n, n_prev, pa.lev);
+    KernelTimer &tm = *b->timer;
+    tm.begin(SPIIR_K_PROLOGUE, st);
+    CUDA_TRY(spiir_launch_prologue(pa, count, st));
+    tm.end(st);
+    if (p.n_levels > 1) {
+        DecimArgs da{};
+        da.xbuf = b->xbuf;
+        da.xbuf_stream_stride = p.xbuf_stream_stride;
+        da.stream0 = s0;
+        da.n_levels = p.n_levels;
+        da.n_taps = p.n_taps;
+        for (int j = 0; j < p.n_taps; ++j) da.h_down[j] = b->h_down[j];
+        level_args(b, n, n_prev, da.lev);
+        tm.begin(SPIIR_K_DECIMATE, st);
+        CUDA_TRY(spiir_launch_decimate(da, count, st));
+        tm.end(st);
+    }
+    if (!p.items.empty()) {
+        RecurArgs ra{};
+        ra.tasks = b->tasks;
+        ra.items = b->items;
+        ra.task_out = b->task_out;
+        ra.a_re = b->are;
+        ra.a_im = b->aim;
+        ra.b_re = b->bre;
+        ra.b_im = b->bim;
+        ra.xoff = b->xoff;
+        ra.state = b->state;
+        ra.n_slots = p.n_slots;
+        ra.xbuf = b->xbuf;
+        ra.xbuf_stream_stride = p.xbuf_stream_stride;
+        ra.partial = b->partial;
+        ra.partial_stream_stride = p.part_stream_stride;
+        ra.z = b->z;
+        ra.z_row_stride = p.ring_len;
+        ra.z_stream_stride = (int64_t)b->d.n_templates * p.ring_len;
+        ra.scale = b->scale;
+        ra.stream0 = s0;
+        ra.n_levels = p.n_levels;
+        ra.status = b->status;
+        level_args(b, n, n_prev, ra.lev);
+        tm.begin(SPIIR_K_RECUR, st);
+        CUDA_TRY(spiir_launch_recur(ra, p.variant, (int)p.items.size(), count, p.smem_bytes, st));
+        tm.end(st);
+    }
+    if (p.need_combine) {
+        CombineArgs ca{};
+        ca.comb_ptr = b->comb_ptr;
+        ca.comb_rows = b->comb_rows;
+        ca.partial = b->partial;
+        ca.partial_stream_stride = p.part_stream_stride;
+        ca.ubuf = b->ubuf;
+        ca.ubuf_stream_stride = p.ubuf_stream_stride;
+        ca.z = b->z;
+        ca.z_row_stride = p.ring_len;
+        ca.z_stream_stride = (int64_t)b->d.n_templates * p.ring_len;
+        ca.scale = b->scale;
+        ca.n_templates = b->d.n_templates;
+        ca.n_levels = p.n_levels;
+        ca.n_taps = p.n_taps;
+        ca.stream0 = s0;
+        for (int j = 0; j < p.n_taps; ++j) ca.h_up2[j] = 2.0f * b->h_up[j];
+        level_args(b, n, n_prev, ca.lev);
+        tm.begin(SPIIR_K_COMBINE, st);
+        CUDA_TRY(spiir_launch_combine(ca, count, st));
+        tm.end(st);
+    }
+    for (int s = s0; s < s0 + count; ++s) b->last_n[s] = n;
+    return SPIIR_OK;
+}
+
+spiir_status build_bank(const spiir_bank_desc *desc, int variant, cudaStream_t s,
+                        spiir_bank *b) {
+    b->d = *desc;
+    b->n_filters = desc->n_filters;
+    b->d.a_re = b->d.a_im = b->d.b_re = b->d.b_im = nullptr;
+    b->d.delay = b->d.template_id = nullptr;
+    b->d.level = nullptr;
+    b->d.h_down = b->d.h_up = nullptr;
+    if (b->d.n_taps == 0) b->d.n_taps = 32;
+    if (b->d.chunk_len == 0) b->d.chunk_len = 256;
+    b->scale = desc->snr_scale != 0.f ? desc->snr_scale : 2.0f / (float)desc->base_rate;
+    const int nt = b->d.n_taps;
+    b->h_down.resize(nt);
+    b->h_up.resize(nt);
+    if (desc->h_down) {
+        std::copy(desc->h_down, desc->h_down + nt, b->h_down.begin());
+        std::copy(desc->h_up, desc->h_up + nt, b->h_up.begin());
+    } else {
+        lib_kaiser_taps(nt, 60.0, b->h_down.data());
+        lib_kaiser_taps(nt, 60.0, b->h_up.data());
+    }
+    b->last_n.assign(desc->n_streams, 0);
+    if (!b->timer) b->timer = new KernelTimer();
+    spiir_status st;
+    if (desc->mode != SPIIR_PLAIN_FP32) {
+        st = spiir_tc_create(desc, b->scale, s, &b->tc, &b->footprint);
+        if (st) return fail(st, "%s", spiir_tc_last_error());
+        return SPIIR_OK;
+    }
+    if ((st = make_plan(desc, variant, true, b->p))) return st;
+    b->footprint = plan_footprint(desc, b->p);
+    if (desc->hbm_budget_bytes > 0 && b->footprint > desc->hbm_budget_bytes)
+        return fail(SPIIR_EBUDGET, "bank needs %lld bytes, budget %lld",
+                    (long long)b->footprint, (long long)desc->hbm_budget_bytes);
+    if ((st = alloc_plain(b, s))) return st;
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SPIIR_OK;
+}
+
+// Time a few pushes of zeros through each compiled variant; return the best.
+spiir_status autotune(const spiir_bank_desc *desc, cudaStream_t s, int *best) {
+    float best_ms = 1e30f;
+    *best = default_variant(desc);
+    const int nv = spiir_recur_variant_count();
+    for (int v = 0; v < nv; ++v) {
+        spiir_bank tmp;
+        spiir_status st = build_bank(desc, v, s, &tmp);
+        if (st) {
+            tmp.free_device();
+            if (st == SPIIR_ENOMEM || st == SPIIR_EBUDGET) return st;
+            continue;
+        }
+        const int64_t n = (int64_t)desc->block_len * std::min(desc->max_push_blocks, 4);
+        cudaMemsetAsync(tmp.xstage, 0, desc->n_streams * tmp.p.ring_len * sizeof(float), s);
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        push_plain(&tmp, 0, desc->n_streams, tmp.xstage, tmp.p.ring_len, n, s);
+        cudaEventRecord(e0, s);
+        const int reps = 3;
+        for (int r = 0; r < reps; ++r) push_plain(&tmp, 0, desc->n_streams, tmp.xstage, tmp.p.ring_len, n, s);
+        cudaEventRecord(e1, s);
+        cudaError_t e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        tmp.free_device();
+        if (e != cudaSuccess) return fail(SPIIR_ECUDA, "autotune: %s", cudaGetErrorString(e));
+        if (ms < best_ms) {
+            best_ms = ms;
+            *best = v;
+        }
+    }
+    return SPIIR_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+spiir_status spiir_bank_create(const spiir_bank_desc *desc, void *cuda_stream, spiir_bank_t *out) {
+    if (!out) return fail(SPIIR_EINVAL, "out is NULL");
+    *out = nullptr;
+    spiir_status st = validate(desc);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int variant = chosen_variant(desc);
+    if (desc->tune > 0 && desc->mode == SPIIR_PLAIN_FP32) {
+        if ((st = autotune(desc, s, &variant))) return st;
+    }
+    spiir_bank *b = new (std::nothrow) spiir_bank();
+    if (!b) return fail(SPIIR_ENOMEM, "host allocation failed");
+    cudaGetDevice(&b->device);
+    st = build_bank(desc, variant, s, b);
+    if (st) {
+        b->free_device();
+        delete b;
+        return st;
+    }
+    *out = b;
+    g_err.clear();
+    return SPIIR_OK;
+}
+
+spiir_status spiir_push_block(spiir_bank_t b, int32_t stream_id, const float *x_dev,
+                              int64_t n_samples, void *cuda_stream) {
+    if (!b) return fail(SPIIR_EINVAL, "bank is NULL");
+    if (!x_dev) return fail(SPIIR_EINVAL, "x_dev is NULL");
+    if (stream_id < -1 || stream_id >= b->d.n_streams)
+        return fail(SPIIR_EINVAL, "stream_id %d out of range", stream_id);
+    if (n_samples <= 0 || n_samples % b->d.block_len != 0 ||
+        n_samples > (int64_t)b->d.block_len * b->d.max_push_blocks)
+        return fail(SPIIR_EINVAL, "n_samples must be a positive multiple of block_len, at most "
+                                  "block_len * max_push_blocks");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int s0 = stream_id < 0 ? 0 : stream_id;
+    const int cnt = stream_id < 0 ? b->d.n_streams : 1;
+    if (b->tc) {
+        spiir_status st = spiir_tc_push(b->tc, s0, cnt, x_dev, n_samples, n_samples, s, b->timer);
+        if (st) return fail(st, "%s", spiir_tc_last_error());
+        for (int q = s0; q < s0 + cnt; ++q) b->last_n[q] = n_samples;
+        return SPIIR_OK;
+    }
+    bool same = true;
+    for (int q = s0; q < s0 + cnt; ++q) same &= (b->last_n[q] == b->last_n[s0]);
+    if (same) return push_plain(b, s0, cnt, x_dev, n_samples, n_samples, s);
+    for (int q = 0; q < cnt; ++q) {
+        spiir_status st = push_plain(b, s0 + q, 1, x_dev + q * n_samples, n_samples, n_samples, s);
+        if (st) return st;
+    }
+    return SPIIR_OK;
+}
+
+spiir_status spiir_read_snr(spiir_bank_t b, int32_t stream_id, void *z_dev, int64_t n_samples,
+                            void *cuda_stream) {
+    if (!b) return fail(SPIIR_EINVAL, "bank is NULL");
+    if (!z_dev) return fail(SPIIR_EINVAL, "z_dev is NULL");
+    if (stream_id < -1 || stream_id >= b->d.n_streams)
+        return fail(SPIIR_EINVAL, "stream_id %d out of range", stream_id);
+    const int s0 = stream_id < 0 ? 0 : stream_id;
+    const int cnt = stream_id < 0 ? b->d.n_streams : 1;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    for (int q = s0; q < s0 + cnt; ++q) {
+        if (b->last_n[q] == 0) return fail(SPIIR_ESTATE, "nothing pushed on stream %d", q);
+        if (n_samples <= 0 || n_samples > b->last_n[q])
+            return fail(SPIIR_EINVAL, "n_samples must be in [1, samples of the last push]");
+    }
+    const int T = b->d.n_templates;
+    for (int q = s0; q < s0 + cnt; ++q) {
+        const float2 *src;
+        int64_t ring;
+        if (b->tc) {
+            src = spiir_tc_output(b->tc, q, &ring);
+        } else {
+            ring = b->p.ring_len;
+            src = b->z + (int64_t)q * T * ring;
+        }
+        src += b->last_n[q] - n_samples;
+        char *dst = (char *)z_dev + (int64_t)(q - s0) * T * n_samples * sizeof(float2);
+        CUDA_TRY(cudaMemcpy2DAsync(dst, n_samples * sizeof(float2), src, ring * sizeof(float2),
+                                   n_samples * sizeof(float2), T, cudaMemcpyDeviceToDevice, s));
+    }
+    return SPIIR_OK;
+}
+
+spiir_status spiir_state_reset(spiir_bank_t b, int32_t stream_id, void *cuda_stream) {
+    if (!b) return fail(SPIIR_EINVAL, "bank is NULL");
+    if (stream_id < -1 || stream_id >= b->d.n_streams)
+        return fail(SPIIR_EINVAL, "stream_id %d out of range", stream_id);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int s0 = stream_id < 0 ? 0 : stream_id;
+    const int cnt = stream_id < 0 ? b->d.n_streams : 1;
+    if (b->tc) {
+        spiir_status st = spiir_tc_reset(b->tc, s0, cnt, s);
+        if (st) return fail(st, "%s", spiir_tc_last_error());
+    } else {
+        const Plan &p = b->p;
+        if (p.n_slots)
+            CUDA_TRY(cudaMemsetAsync(b->state + (int64_t)s0 * p.n_slots, 0,
+                                     cnt * p.n_slots * sizeof(float2), s));
+        CUDA_TRY(cudaMemsetAsync(b->xbuf + (int64_t)s0 * p.xbuf_stream_stride, 0,
+                                 cnt * p.xbuf_stream_stride * sizeof(float), s));
+        if (b->ubuf)
+            CUDA_TRY(cudaMemsetAsync(b->ubuf + (int64_t)s0 * p.ubuf_stream_stride, 0,
+                                     cnt * p.ubuf_stream_stride * sizeof(float2), s));
+    }
+    for (int q = s0; q < s0 + cnt; ++q) b->last_n[q] = 0;
+    return SPIIR_OK;
+}
+
+spiir_status spiir_push_block_host(spiir_bank_t b, int32_t stream_id, const float *x_host,
+                                   int64_t n_samples, void *z_host, void *cuda_stream) {
+    if (!b) return fail(SPIIR_EINVAL, "bank is NULL");
+    if (!x_host || !z_host) return fail(SPIIR_EINVAL, "host buffers must not be NULL");
+    if (stream_id < -1 || stream_id >= b->d.n_streams)
+        return fail(SPIIR_EINVAL, "stream_id %d out of range", stream_id);
+    if (n_samples <= 0 || n_samples % b->d.block_len != 0 ||
+        n_samples > (int64_t)b->d.block_len * b->d.max_push_blocks)
+        return fail(SPIIR_EINVAL, "bad n_samples");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int cnt = stream_id < 0 ? b->d.n_streams : 1;
+    float *stage = b->tc ? spiir_tc_stage(b->tc) : b->xstage;
+    CUDA_TRY(cudaMemcpyAsync(stage, x_host, cnt * n_samples * sizeof(float),
+                             cudaMemcpyHostToDevice, s));
+    spiir_status st = spiir_push_block(b, stream_id, stage, n_samples, cuda_stream);
+    if (st) return st;
+    const int s0 = stream_id < 0 ? 0 : stream_id;
+    const int T = b->d.n_templates;
+    for (int q = s0; q < s0 + cnt; ++q) {
+        const float2 *src;
+        int64_t ring;
+        if (b->tc) {
+            src = spiir_tc_output(b->tc, q, &ring);
+        } else {
+            ring = b->p.ring_len;
+            src = b->z + (int64_t)q * T * ring;
+        }
+        char *dst = (char *)z_host + (int64_t)(q - s0) * T * n_samples * sizeof(float2);
+        CUDA_TRY(cudaMemcpy2DAsync(dst, n_samples * sizeof(float2), src, ring * sizeof(float2),
+                                   n_samples * sizeof(float2), T, cudaMemcpyDeviceToHost, s));
+    }
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SPIIR_OK;
+}
+
+int64_t spiir_bank_footprint(const spiir_bank_desc *desc) {
+    if (validate(desc)) return -1;
+    if (desc->mode != SPIIR_PLAIN_FP32) return spiir_tc_footprint(desc);
+    Plan p;
+    if (make_plan(desc, chosen_variant(desc), false, p)) return -1;
+    return plan_footprint(desc, p);
+}
+
+spiir_status spiir_bank_plan(const spiir_bank_desc *desc, spiir_bank_info *info) {
+    if (!info) return fail(SPIIR_EINVAL, "info is NULL");
+    spiir_status st = validate(desc);
+    if (st) return st;
+    if (desc->mode != SPIIR_PLAIN_FP32) return fail(SPIIR_EUNSUPPORTED, "plan of the plain form only");
+    Plan p;
+    if ((st = make_plan(desc, chosen_variant(desc), true, p))) return st;
+    std::memset(info, 0, sizeof(*info));
+    info->footprint_bytes = plan_footprint(desc, p);
+    plan_info(desc, p, info);
+    return SPIIR_OK;
+}
+
+spiir_status spiir_bank_get_info(spiir_bank_t b, spiir_bank_info *info) {
+    if (!b || !info) return fail(SPIIR_EINVAL, "NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    info->footprint_bytes = b->footprint;
+    if (b->tc) {
+        spiir_tc_info(b->tc, info);
+        return SPIIR_OK;
+    }
+    plan_info(&b->d, b->p, info);
+    info->slot_fill = b->p.n_slots ? (float)b->n_filters / (float)b->p.n_slots : 1.f;
+    return SPIIR_OK;
+}
+
+spiir_status spiir_bank_sync_status(spiir_bank_t b) {
+    if (!b) return fail(SPIIR_EINVAL, "bank is NULL");
+    CUDA_TRY(cudaDeviceSynchronize());
+    unsigned int *dst = b->tc ? spiir_tc_status(b->tc) : b->status;
+    unsigned int v = 0;
+    CUDA_TRY(cudaMemcpy(&v, dst, sizeof(v), cudaMemcpyDeviceToHost));
+    if (v != SPIIR_DEV_OK) {
+        CUDA_TRY(cudaMemset(dst, 0, sizeof(unsigned int)));
+        return fail(SPIIR_ETIMEOUT, "a device-side wait timed out (status %u)", v);
+    }
+    return SPIIR_OK;
+}
+
+spiir_status spiir_bank_enable_timing(spiir_bank_t b, int32_t enable) {
+    if (!b) return fail(SPIIR_EINVAL, "bank is NULL");
+    b->timer->flush();
+    b->timer->on = enable != 0;
+    for (int k = 0; k < SPIIR_K_COUNT; ++k) {
+        b->timer->ms[k] = 0.0;
+        b->timer->launches[k] = 0;
+    }
+    return SPIIR_OK;
+}
+
+spiir_status spiir_bank_kernel_times(spiir_bank_t b, spiir_kernel_times *out) {
+    if (!b || !out) return fail(SPIIR_EINVAL, "NULL argument");
+    b->timer->flush();
+    for (int k = 0; k < SPIIR_K_COUNT; ++k) {
+        out->ms[k] = b->timer->ms[k];
+        out->launches[k] = b->timer->launches[k];
+        b->timer->ms[k] = 0.0;
+        b->timer->launches[k] = 0;
+    }
+    return SPIIR_OK;
+}
+
+void spiir_bank_destroy(spiir_bank_t b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    b->free_device();
+    delete b;
+}
+
+spiir_status spiir_kaiser_taps(int32_t n_taps, double atten_db, float *out) {
+    if (!out || n_taps < 2 || n_taps > 4096) return fail(SPIIR_EINVAL, "bad n_taps or out");
+    lib_kaiser_taps(n_taps, atten_db, out);
+    return SPIIR_OK;
+}
+
+int32_t spiir_assign_level(float a_re, float a_im, int32_t base_rate, int32_t n_levels) {
+    const double f = std::fabs(std::atan2((double)a_im, (double)a_re)) * base_rate / (2.0 * M_PI);
+    int32_t lv = 0;
+    for (int32_t i = 0; i < n_levels; ++i)
+        if ((double)base_rate / (double)(1 << i) >= 2.0 * f) lv = i;
+    return lv;
+}
+
+const char *spiir_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

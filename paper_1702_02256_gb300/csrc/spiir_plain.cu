@@ -1,0 +1,483 @@
+// spiir_plain.cu -- FP32 per-sample SPIIR kernels for sm_103a.
+//
+//   prologue   move each level's strain history to the front of its buffer
+//              and append the pushed base-rate samples;
+//   decimate   the x2 decimation cascade (Sec. 2.2, Eq. kaiser_window_filtering,
+//              causal T-tap form);
+//   recur      the filter recursion y_k[n] = a_k y_k[n-1] + b_k x[n-d_k]
+//              (Eq. iireq0) and the sum over a template's filters
+//              (Eq. iireq1), every level in one launch;
+//   combine    sum of a unit's parts, x2 upsampling of the next lower rate
+//              and the upstream sum, level by level (Sec. 2.2, Fig. 1), and
+//              the 2*dt scale.
+//
+// Recursion kernel layout. A CTA stages its level's strain window (history
+// plus a segment of the push) into shared memory with one bulk async copy
+// (cp.async.bulk + mbarrier). Each lane owns F filter slots whose state
+// (y), pole and gain sit in registers for the whole push; two slots are
+// updated together with packed f32x2 FMA. Each filter reads its delayed input
+// straight from the window at its own offset (the packer spreads the offsets
+// of one round over the 32 shared-memory banks). Every lane accumulates its
+// filters' sum for T consecutive samples, then the lanes of a unit reduce
+// those T sums with a butterfly reduce-scatter (shuffles in a fixed order,
+// no atomics), which leaves each lane holding whole sums for T/G samples.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "spiir_internal.h"
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// mbarrier / bulk-copy helpers (inline PTX)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *m, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *m, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *m, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(m)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *m) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(m))
+        : "memory");
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for an mbarrier phase for at most ~2 s; on timeout record it in the
+// status word and report failure instead of hanging.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *m, uint32_t parity,
+                                                  unsigned int *status) {
+    if (mbar_try_wait(m, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (true) {
+        if (mbar_try_wait(m, parity)) return true;
+        if (globaltimer_ns() - t0 > 2000000000ull) {
+            atomicExch(status, SPIIR_DEV_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Prologue: strain history + new base-rate samples
+// ---------------------------------------------------------------------------
+
+__global__ void prologue_kernel(const PrologueArgs a) {
+    const int lev = blockIdx.x;
+    const int s = a.stream0 + blockIdx.y;
+    const LevelArgs L = a.lev[lev];
+    float *buf = a.xbuf + (int64_t)s * a.xbuf_stream_stride + L.xbuf_off;
+    const int hist = L.hist, np = L.n_prev;
+    if (np > 0 && hist > 0) {
+        // buf[0, hist) <- buf[np, np + hist); chunks of np samples so that a
+        // chunk's sources are read before the next chunk overwrites them.
+        for (int c0 = 0; c0 < hist; c0 += np) {
+            const int len = min(np, hist - c0);
+            for (int k = threadIdx.x; k < len; k += blockDim.x) buf[c0 + k] = buf[c0 + np + k];
+            __syncthreads();
+        }
+    }
+    if (lev == 0) {
+        const float *src = a.x_in + (int64_t)blockIdx.y * a.x_in_stream_stride;
+        for (int k = threadIdx.x; k < L.n; k += blockDim.x) buf[hist + k] = src[k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Decimation cascade: x_{i+1}[m] = sum_j h[j] x_i[2m - j]
+// ---------------------------------------------------------------------------
+
+__global__ void decimate_kernel(const DecimArgs a) {
+    const int s = a.stream0 + blockIdx.x;
+    float *base = a.xbuf + (int64_t)s * a.xbuf_stream_stride;
+    __shared__ float h[SPIIR_MAX_TAPS];
+    if (threadIdx.x < a.n_taps) h[threadIdx.x] = a.h_down[threadIdx.x];
+    __syncthreads();
+    for (int i = 1; i < a.n_levels; ++i) {
+        const LevelArgs Ls = a.lev[i - 1], Ld = a.lev[i];
+        const float *src = base + Ls.xbuf_off + Ls.hist;
+        float *dst = base + Ld.xbuf_off + Ld.hist;
+        for (int m = threadIdx.x; m < Ld.n; m += blockDim.x) {
+            const float *p = src + 2 * m;
+            float acc = 0.f;
+            for (int j = 0; j < a.n_taps; ++j) acc = fmaf(h[j], p[-j], acc);
+            dst[m] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Recursion kernel
+// ---------------------------------------------------------------------------
+
+template <int PMAX>
+struct Regs {
+    float2 are[PMAX], aim[PMAX], naim[PMAX], bre[PMAX], bim[PMAX], yre[PMAX], yim[PMAX];
+    int off0[PMAX], off1[PMAX];
+};
+
+// One time tile of T samples for P slot pairs; sre/sim receive this lane's
+// per-sample sums over its filters. tl < T marks a ragged last tile.
+template <int T, int PMAX, int P, bool FULL>
+__device__ __forceinline__ void tile(const float *__restrict__ xs, int tb, int tl,
+                                     Regs<PMAX> &r, float (&sre)[T], float (&sim)[T]) {
+#pragma unroll
+    for (int j = 0; j < T; ++j) {
+        if (FULL || j < tl) {
+            float2 accr, acci;
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const float2 X = make_float2(xs[r.off0[p] + tb + j], xs[r.off1[p] + tb + j]);
+                const float2 tr = __fmul2_rn(r.bre[p], X);
+                const float2 ti = __fmul2_rn(r.bim[p], X);
+                float2 nr = __ffma2_rn(r.are[p], r.yre[p], tr);
+                nr = __ffma2_rn(r.naim[p], r.yim[p], nr);
+                float2 ni = __ffma2_rn(r.are[p], r.yim[p], ti);
+                ni = __ffma2_rn(r.aim[p], r.yre[p], ni);
+                r.yre[p] = nr;
+                r.yim[p] = ni;
+                if (p == 0) {
+                    accr = nr;
+                    acci = ni;
+                } else {
+                    accr = __fadd2_rn(accr, nr);
+                    acci = __fadd2_rn(acci, ni);
+                }
+            }
+            sre[j] = accr.x + accr.y;
+            sim[j] = acci.x + acci.y;
+        } else {
+            sre[j] = 0.f;
+            sim[j] = 0.f;
+        }
+    }
+}
+
+// Butterfly reduce-scatter over lane groups: round with stride S exchanges
+// half of the LEN live values with lane^S and adds; once one value is left
+// the remaining rounds are plain pairwise sums.
+template <int T, int LEN, int S>
+__device__ __forceinline__ void rs_round(float (&re)[T], float (&im)[T], int lane) {
+    if constexpr (S >= 1) {
+        if constexpr (LEN >= 2) {
+            const bool up = (lane & S) != 0;
+#pragma unroll
+            for (int i = 0; i < LEN / 2; ++i) {
+                const float sr = up ? re[i] : re[i + LEN / 2];
+                const float kr = up ? re[i + LEN / 2] : re[i];
+                const float si = up ? im[i] : im[i + LEN / 2];
+                const float ki = up ? im[i + LEN / 2] : im[i];
+                re[i] = kr + __shfl_xor_sync(0xffffffffu, sr, S);
+                im[i] = ki + __shfl_xor_sync(0xffffffffu, si, S);
+            }
+            rs_round<T, LEN / 2, S / 2>(re, im, lane);
+        } else {
+            re[0] += __shfl_xor_sync(0xffffffffu, re[0], S);
+            im[0] += __shfl_xor_sync(0xffffffffu, im[0], S);
+            rs_round<T, 1, S / 2>(re, im, lane);
+        }
+    }
+}
+
+constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
+
+// After the reduce-scatter for group size G a lane holds CH = max(T/G, 1)
+// consecutive sums; when G > T, 2^NR lanes hold the same sums and the first
+// of them writes.
+template <int T, int G>
+__device__ __forceinline__ void reduce_write(float (&re)[T], float (&im)[T], int lane,
+                                             int tl, float2 *row, float scale, bool valid) {
+    rs_round<T, T, G / 2>(re, im, lane);
+    constexpr int NS = ilog2(G < T ? G : T);
+    constexpr int NR = ilog2(G) - NS;
+    constexpr int CH = (T / G) > 1 ? (T / G) : 1;
+    if (!valid) return;
+    if ((lane & ((1 << NR) - 1)) != 0) return;
+    const int t0 = ((lane & (G - 1)) >> NR) * CH;
+#pragma unroll
+    for (int i = 0; i < CH; ++i)
+        if (t0 + i < tl) row[t0 + i] = make_float2(scale * re[i], scale * im[i]);
+}
+
+template <int T, int PMAX, int P>
+__device__ __forceinline__ void run_segment(const float *__restrict__ xs, int seg_len,
+                                            Regs<PMAX> &r, int lane, int g, float2 *row,
+                                            float scale, bool valid) {
+    for (int t0 = 0; t0 < seg_len; t0 += T) {
+        const int tl = min(T, seg_len - t0);
+        float sre[T], sim[T];
+        if (tl == T)
+            tile<T, PMAX, P, true>(xs, t0, T, r, sre, sim);
+        else
+            tile<T, PMAX, P, false>(xs, t0, tl, r, sre, sim);
+        float2 *rw = row + t0;
+        switch (g) {
+            case 0: reduce_write<T, 1>(sre, sim, lane, tl, rw, scale, valid); break;
+            case 1: reduce_write<T, 2>(sre, sim, lane, tl, rw, scale, valid); break;
+            case 2: reduce_write<T, 4>(sre, sim, lane, tl, rw, scale, valid); break;
+            case 3: reduce_write<T, 8>(sre, sim, lane, tl, rw, scale, valid); break;
+            case 4: reduce_write<T, 16>(sre, sim, lane, tl, rw, scale, valid); break;
+            default: reduce_write<T, 32>(sre, sim, lane, tl, rw, scale, valid); break;
+        }
+    }
+}
+
+template <int T, int PMAX, int P>
+__device__ __forceinline__ void dispatch_segment(int p_runtime, const float *xs, int seg_len,
+                                                 Regs<PMAX> &r, int lane, int g, float2 *row,
+                                                 float scale, bool valid) {
+    if constexpr (P <= PMAX) {
+        if (p_runtime == P)
+            run_segment<T, PMAX, P>(xs, seg_len, r, lane, g, row, scale, valid);
+        else
+            dispatch_segment<T, PMAX, P + 1>(p_runtime, xs, seg_len, r, lane, g, row, scale,
+                                             valid);
+    }
+}
+
+template <int T, int FMAX>
+__global__ void __launch_bounds__(SPIIR_CTA_WARPS * 32) recur_kernel(const RecurArgs a) {
+    constexpr int PMAX = FMAX / 2;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
+    float *xs = reinterpret_cast<float *>(smem + 16);
+
+    const int stream = a.stream0 + blockIdx.y;
+    const CtaItem item = a.items[blockIdx.x];
+    const LevelArgs L = a.lev[item.level];
+    const float *xlev = a.xbuf + (int64_t)stream * a.xbuf_stream_stride + L.xbuf_off;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool active = warp < item.task_count;
+
+    WarpTask wt;
+    wt.slot_base = 0; wt.F = 0; wt.g_log2 = 0; wt.level = 0; wt.out_base = 0; wt.n_groups = 0;
+    if (active) wt = a.tasks[item.task_begin + warp];
+    const int P = active ? wt.F / 2 : 0;
+
+    Regs<PMAX> r;
+    float2 *st = a.state + (int64_t)stream * a.n_slots;
+#pragma unroll
+    for (int p = 0; p < PMAX; ++p) {
+        if (p < P) {
+            const int64_t s0 = wt.slot_base + (int64_t)(2 * p) * 32 + lane, s1 = s0 + 32;
+            r.are[p] = make_float2(a.a_re[s0], a.a_re[s1]);
+            r.aim[p] = make_float2(a.a_im[s0], a.a_im[s1]);
+            r.naim[p] = make_float2(-r.aim[p].x, -r.aim[p].y);
+            r.bre[p] = make_float2(a.b_re[s0], a.b_re[s1]);
+            r.bim[p] = make_float2(a.b_im[s0], a.b_im[s1]);
+            const float2 y0 = st[s0], y1 = st[s1];
+            r.yre[p] = make_float2(y0.x, y1.x);
+            r.yim[p] = make_float2(y0.y, y1.y);
+            r.off0[p] = a.xoff[s0];
+            r.off1[p] = a.xoff[s1];
+        } else {
+            r.are[p] = r.aim[p] = r.naim[p] = r.bre[p] = r.bim[p] = make_float2(0.f, 0.f);
+            r.yre[p] = r.yim[p] = make_float2(0.f, 0.f);
+            r.off0[p] = r.off1[p] = 0;
+        }
+    }
+
+    // Destination of this lane's group.
+    bool valid = false;
+    float2 *row = nullptr;
+    float scale = 1.f;
+    if (active) {
+        const int grp = lane >> wt.g_log2;
+        if (grp < wt.n_groups) {
+            const int dst = a.task_out[wt.out_base + grp];
+            valid = true;
+            if (dst >= 0) {
+                row = a.z + (int64_t)stream * a.z_stream_stride + (int64_t)dst * a.z_row_stride;
+                scale = a.scale;
+            } else {
+                row = a.partial + (int64_t)stream * a.partial_stream_stride + L.part_base +
+                      (int64_t)(-dst - 1) * L.part_stride;
+            }
+        }
+    }
+
+    if (threadIdx.x == 0) {
+        mbar_init(mbar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    uint32_t phase = 0;
+    for (int s0 = 0; s0 < L.n; s0 += L.seg) {
+        const int sl = min(L.seg, L.n - s0);
+        if (threadIdx.x == 0) {
+            const uint32_t bytes = (uint32_t)(((L.hist + sl) * 4 + 15) & ~15);
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(mbar, bytes);
+            bulk_g2s(xs, xlev + s0, bytes, mbar);
+        }
+        const bool ok = mbar_wait_bounded(mbar, phase, a.status);
+        phase ^= 1u;
+        if (!ok) break;
+        if (active && P > 0)
+            dispatch_segment<T, PMAX, 1>(P, xs, sl, r, lane, wt.g_log2,
+                                         row ? row + s0 : nullptr, scale, valid);
+        __syncthreads();
+    }
+
+#pragma unroll
+    for (int p = 0; p < PMAX; ++p) {
+        if (p < P) {
+            const int64_t s0 = wt.slot_base + (int64_t)(2 * p) * 32 + lane, s1 = s0 + 32;
+            st[s0] = make_float2(r.yre[p].x, r.yim[p].x);
+            st[s1] = make_float2(r.yre[p].y, r.yim[p].y);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Combine: parts + upsample(next lower rate) + scale
+// ---------------------------------------------------------------------------
+
+__global__ void combine_kernel(const CombineArgs a) {
+    const int t = blockIdx.x;
+    const int s = a.stream0 + blockIdx.y;
+    const int H = a.n_levels - 1;
+    const int half = a.n_taps / 2;
+    __shared__ float h2[SPIIR_MAX_TAPS];
+    if (threadIdx.x < a.n_taps) h2[threadIdx.x] = a.h_up2[threadIdx.x];
+    __syncthreads();
+    float2 *part = a.partial + (int64_t)s * a.partial_stream_stride;
+    float2 *ub = a.ubuf + (int64_t)s * a.ubuf_stream_stride;
+    for (int i = H; i >= 0; --i) {
+        const LevelArgs L = a.lev[i];
+        const int r0 = a.comb_ptr[t * a.n_levels + i], r1 = a.comb_ptr[t * a.n_levels + i + 1];
+        float2 *urow = (i > 0) ? ub + L.ubuf_off + (int64_t)t * L.ubuf_stride : nullptr;
+        float2 *ulow = nullptr;
+        int n_low = 0;
+        if (i < H) {
+            const LevelArgs Ll = a.lev[i + 1];
+            ulow = ub + Ll.ubuf_off + (int64_t)t * Ll.ubuf_stride;
+            n_low = Ll.n;
+        }
+        float2 *zrow = a.z + (int64_t)s * a.z_stream_stride + (int64_t)t * a.z_row_stride;
+        for (int n = threadIdx.x; n < L.n; n += blockDim.x) {
+            float re = 0.f, im = 0.f;
+            for (int q = r0; q < r1; ++q) {
+                const float2 v = part[L.part_base + (int64_t)a.comb_rows[q] * L.part_stride + n];
+                re += v.x;
+                im += v.y;
+            }
+            if (ulow) {
+                const float2 *u = ulow + SPIIR_UHIST + (n >> 1);
+                const int ph = n & 1;
+                for (int j = 0; j < half; ++j) {
+                    const float w = h2[2 * j + ph];
+                    const float2 v = u[-j];
+                    re = fmaf(w, v.x, re);
+                    im = fmaf(w, v.y, im);
+                }
+            }
+            if (i > 0)
+                urow[SPIIR_UHIST + n] = make_float2(re, im);
+            else
+                zrow[n] = make_float2(a.scale * re, a.scale * im);
+        }
+        __syncthreads();
+        if (ulow) {
+            // keep the last SPIIR_UHIST samples of the lower rate as history
+            for (int c0 = 0; c0 < SPIIR_UHIST; c0 += n_low) {
+                const int len = min(n_low, SPIIR_UHIST - c0);
+                for (int k = threadIdx.x; k < len; k += blockDim.x) ulow[c0 + k] = ulow[c0 + n_low + k];
+                __syncthreads();
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Variants
+// ---------------------------------------------------------------------------
+
+struct Variant {
+    int T, FMAX;
+    void (*fn)(const RecurArgs);
+};
+
+const Variant kVariants[] = {
+    {32, 8, recur_kernel<32, 8>},
+    {16, 16, recur_kernel<16, 16>},
+    {32, 4, recur_kernel<32, 4>},
+    {16, 8, recur_kernel<16, 8>},
+};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+}  // namespace
+
+int spiir_recur_variant_count() { return kNumVariants; }
+
+void spiir_recur_variant_shape(int v, int *time_tile, int *fmax) {
+    *time_tile = kVariants[v].T;
+    *fmax = kVariants[v].FMAX;
+}
+
+cudaError_t spiir_recur_prepare(int v, int smem_bytes) {
+    return cudaFuncSetAttribute(kVariants[v].fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem_bytes);
+}
+
+cudaError_t spiir_launch_prologue(const PrologueArgs &a, int n_streams, cudaStream_t s) {
+    prologue_kernel<<<dim3(a.n_levels, n_streams), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t spiir_launch_decimate(const DecimArgs &a, int n_streams, cudaStream_t s) {
+    decimate_kernel<<<n_streams, 512, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t spiir_launch_recur(const RecurArgs &a, int variant, int n_items, int n_streams,
+                               int smem_bytes, cudaStream_t s) {
+    kVariants[variant].fn<<<dim3(n_items, n_streams), SPIIR_CTA_WARPS * 32, smem_bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t spiir_launch_combine(const CombineArgs &a, int n_streams, cudaStream_t s) {
+    combine_kernel<<<dim3(a.n_templates, n_streams), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}

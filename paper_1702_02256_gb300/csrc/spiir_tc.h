@@ -1,0 +1,24 @@
+// spiir_tc.h -- block-parallel tensor-core form of single-rate SPIIR banks
+// (internal interface between spiir_api.cu and spiir_tc.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "spiir.h"
+
+struct TcBank;
+
+spiir_status spiir_tc_create(const spiir_bank_desc *desc, float scale, cudaStream_t s,
+                             TcBank **out, int64_t *footprint);
+struct KernelTimer;
+spiir_status spiir_tc_push(TcBank *b, int s0, int count, const float *x, int64_t x_stride,
+                           int64_t n, cudaStream_t s, KernelTimer *timer);
+spiir_status spiir_tc_reset(TcBank *b, int s0, int count, cudaStream_t s);
+const float2 *spiir_tc_output(TcBank *b, int stream, int64_t *ring_len);
+float *spiir_tc_stage(TcBank *b);
+unsigned int *spiir_tc_status(TcBank *b);
+void spiir_tc_info(TcBank *b, spiir_bank_info *info);
+int64_t spiir_tc_footprint(const spiir_bank_desc *desc);
+void spiir_tc_destroy(TcBank *b);
+const char *spiir_tc_last_error();

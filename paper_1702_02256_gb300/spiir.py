@@ -1,0 +1,266 @@
+"""Thin ctypes binding of libspiir (include/spiir.h).
+
+Argument marshalling only: every step of the filtering runs in the library's
+CUDA kernels. PyTorch supplies device memory (tensors) and the CUDA stream.
+If the shared library is missing the import fails loudly; there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libspiir.so")
+
+OK, EINVAL, ENOMEM, EBUDGET, ECUDA, ETIMEOUT, ESTATE, EUNSUPPORTED = range(8)
+PLAIN_FP32, TC_FP16, TC_BF16, TC_BF16X2 = range(4)
+MODES = {"plain": PLAIN_FP32, "fp16": TC_FP16, "bf16": TC_BF16, "bf16x2": TC_BF16X2}
+
+_c_void_p = ctypes.c_void_p
+_i32, _i64, _f32, _f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double
+
+
+class BankDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_templates", _i32), ("n_levels", _i32), ("base_rate", _i32),
+        ("n_streams", _i32), ("block_len", _i32), ("max_push_blocks", _i32),
+        ("n_filters", _i64),
+        ("a_re", _c_void_p), ("a_im", _c_void_p), ("b_re", _c_void_p), ("b_im", _c_void_p),
+        ("delay", _c_void_p), ("template_id", _c_void_p), ("level", _c_void_p),
+        ("h_down", _c_void_p), ("h_up", _c_void_p),
+        ("n_taps", _i32), ("align", _i32), ("snr_scale", _f32), ("mode", _i32),
+        ("chunk_len", _i32), ("tune", _i32), ("hbm_budget_bytes", _i64),
+    ]
+
+
+class BankInfo(ctypes.Structure):
+    _fields_ = [
+        ("footprint_bytes", _i64), ("n_slots", _i64), ("filter_samples_per_block", _i64),
+        ("n_warp_tasks", _i32), ("n_cta_items", _i32), ("filters_per_lane", _i32),
+        ("time_tile", _i32), ("kernel_variant", _i32), ("max_delay", _i32),
+        ("tc_fir_len", _i32), ("graph_captured", _i32), ("n_units", _i32),
+        ("smem_ways", _f32), ("slot_fill", _f32),
+    ]
+
+
+K_PROLOGUE, K_DECIMATE, K_RECUR, K_COMBINE, K_TC_STAGE, K_TC_FIR, K_TC_CARRY, K_OTHER = range(8)
+KERNEL_NAMES = ["prologue", "decimate", "recur", "combine", "tc_stage", "tc_fir", "tc_carry", "other"]
+
+
+class KernelTimes(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_int64 * 8)]
+
+
+class SpiirError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"spiir status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "spiir_bank_create": (_i32, [ctypes.POINTER(BankDesc), _c_void_p, ctypes.POINTER(_c_void_p)]),
+    "spiir_push_block": (_i32, [_c_void_p, _i32, _c_void_p, _i64, _c_void_p]),
+    "spiir_read_snr": (_i32, [_c_void_p, _i32, _c_void_p, _i64, _c_void_p]),
+    "spiir_state_reset": (_i32, [_c_void_p, _i32, _c_void_p]),
+    "spiir_push_block_host": (_i32, [_c_void_p, _i32, _c_void_p, _i64, _c_void_p, _c_void_p]),
+    "spiir_bank_footprint": (_i64, [ctypes.POINTER(BankDesc)]),
+    "spiir_bank_get_info": (_i32, [_c_void_p, ctypes.POINTER(BankInfo)]),
+    "spiir_bank_plan": (_i32, [ctypes.POINTER(BankDesc), ctypes.POINTER(BankInfo)]),
+    "spiir_bank_sync_status": (_i32, [_c_void_p]),
+    "spiir_bank_destroy": (None, [_c_void_p]),
+    "spiir_kaiser_taps": (_i32, [_i32, _f64, _c_void_p]),
+    "spiir_assign_level": (_i32, [_f32, _f32, _i32, _i32]),
+    "spiir_last_error": (ctypes.c_char_p, []),
+    "spiir_bank_enable_timing": (_i32, [_c_void_p, _i32]),
+    "spiir_bank_kernel_times": (_i32, [_c_void_p, ctypes.POINTER(KernelTimes)]),
+}
+
+
+def lib():
+    """Load libspiir.so (built by __graft_entry__.build()); fail loudly if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().spiir_last_error().decode()
+
+
+def check(status: int):
+    if status != OK:
+        raise SpiirError(status, last_error())
+
+
+def _arr(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def kaiser_taps(n_taps: int = 32, atten_db: float = 60.0) -> np.ndarray:
+    out = np.zeros(n_taps, np.float32)
+    check(lib().spiir_kaiser_taps(n_taps, atten_db, out.ctypes.data))
+    return out
+
+
+def assign_level(a_re: float, a_im: float, base_rate: int, n_levels: int) -> int:
+    return int(lib().spiir_assign_level(a_re, a_im, base_rate, n_levels))
+
+
+def make_desc(bank, n_streams: int = 1, block_len: int = 4096, max_push_blocks: int = 1,
+              mode: str = "plain", chunk_len: int = 0, tune: int = 0,
+              hbm_budget_bytes: int = 0, align: Optional[bool] = None,
+              h_down: Optional[np.ndarray] = None, h_up: Optional[np.ndarray] = None,
+              snr_scale: float = 0.0):
+    """Fill a BankDesc from an inputs.Bank. Returns (desc, keepalive arrays)."""
+    keep = dict(
+        a_re=_arr(bank.a_re, np.float32), a_im=_arr(bank.a_im, np.float32),
+        b_re=_arr(bank.b_re, np.float32), b_im=_arr(bank.b_im, np.float32),
+        delay=_arr(bank.delay, np.int32), template_id=_arr(bank.template_id, np.int32),
+        level=_arr(bank.level, np.int8),
+    )
+    d = BankDesc()
+    d.n_templates = bank.n_templates
+    d.n_levels = bank.n_levels
+    d.base_rate = bank.base_rate
+    d.n_streams = n_streams
+    d.block_len = block_len
+    d.max_push_blocks = max_push_blocks
+    d.n_filters = bank.n_filters
+    for k, v in keep.items():
+        setattr(d, k, v.ctypes.data if v.size else None)
+    if h_down is not None:
+        keep["h_down"] = _arr(h_down, np.float32)
+        keep["h_up"] = _arr(h_up, np.float32)
+        d.h_down = keep["h_down"].ctypes.data
+        d.h_up = keep["h_up"].ctypes.data
+        d.n_taps = int(keep["h_down"].shape[0])
+    d.align = int(bank.n_levels > 1 if align is None else align)
+    d.snr_scale = snr_scale
+    d.mode = MODES[mode] if isinstance(mode, str) else int(mode)
+    d.chunk_len = chunk_len
+    d.tune = tune
+    d.hbm_budget_bytes = hbm_budget_bytes
+    return d, keep
+
+
+def footprint(bank, **kw) -> int:
+    d, _keep = make_desc(bank, **kw)
+    return int(lib().spiir_bank_footprint(ctypes.byref(d)))
+
+
+def plan(bank, **kw) -> dict:
+    """Host-only packing facts for a bank description (no GPU needed)."""
+    d, _keep = make_desc(bank, **kw)
+    inf = BankInfo()
+    check(lib().spiir_bank_plan(ctypes.byref(d), ctypes.byref(inf)))
+    return {k: getattr(inf, k) for k, _ in BankInfo._fields_}
+
+
+def _stream_handle(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class Bank:
+    """A device-resident SPIIR bank (spiir_bank_t)."""
+
+    def __init__(self, bank, n_streams: int = 1, block_len: int = 4096,
+                 max_push_blocks: int = 1, stream=None, **kw):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libspiir needs a CUDA device")
+        d, keep = make_desc(bank, n_streams=n_streams, block_len=block_len,
+                            max_push_blocks=max_push_blocks, **kw)
+        h = _c_void_p()
+        check(lib().spiir_bank_create(ctypes.byref(d), _stream_handle(stream), ctypes.byref(h)))
+        self._h = h
+        self.n_templates = bank.n_templates
+        self.n_streams = n_streams
+        self.block_len = block_len
+        self.max_push_blocks = max_push_blocks
+
+    @property
+    def handle(self):
+        return self._h
+
+    def push(self, x, stream_id: int = -1, stream=None):
+        """x: float32 CUDA tensor [n] (one stream) or [n_streams, n] (stream_id=-1)."""
+        assert x.is_cuda and x.dtype.is_floating_point and x.is_contiguous()
+        n = int(x.shape[-1])
+        check(lib().spiir_push_block(self._h, stream_id, x.data_ptr(), n, _stream_handle(stream)))
+
+    def read(self, n_samples: int, stream_id: int = -1, out=None, stream=None):
+        """SNR of the last push: complex64 [n_streams, T, n] (or [T, n])."""
+        import torch
+        shape = ((self.n_streams if stream_id < 0 else 1), self.n_templates, n_samples)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.complex64, device="cuda")
+        check(lib().spiir_read_snr(self._h, stream_id, out.data_ptr(), n_samples,
+                                   _stream_handle(stream)))
+        return out if stream_id < 0 else out[0]
+
+    def push_host(self, x, stream_id: int = -1, z_out=None, stream=None):
+        """Host buffers in and out (copies inside the call). x and z_out are
+        numpy arrays or (pinned) CPU torch tensors."""
+        if hasattr(x, "data_ptr"):
+            n = int(x.shape[-1])
+            xp = x.data_ptr()
+        else:
+            x = np.ascontiguousarray(x, np.float32)
+            n = int(x.shape[-1])
+            xp = x.ctypes.data
+        cnt = self.n_streams if stream_id < 0 else 1
+        if z_out is None:
+            z_out = np.empty((cnt, self.n_templates, n), np.complex64)
+        zp = z_out.data_ptr() if hasattr(z_out, "data_ptr") else z_out.ctypes.data
+        check(lib().spiir_push_block_host(self._h, stream_id, xp, n, zp, _stream_handle(stream)))
+        return z_out
+
+    def reset(self, stream_id: int = -1, stream=None):
+        check(lib().spiir_state_reset(self._h, stream_id, _stream_handle(stream)))
+
+    def info(self) -> dict:
+        inf = BankInfo()
+        check(lib().spiir_bank_get_info(self._h, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in BankInfo._fields_}
+
+    def enable_timing(self, on: bool = True):
+        check(lib().spiir_bank_enable_timing(self._h, int(on)))
+
+    def kernel_times(self) -> dict:
+        """{kernel name: (ms summed, launches)} since the last call."""
+        kt = KernelTimes()
+        check(lib().spiir_bank_kernel_times(self._h, ctypes.byref(kt)))
+        return {KERNEL_NAMES[k]: (kt.ms[k], int(kt.launches[k])) for k in range(8)
+                if kt.launches[k]}
+
+    def sync_status(self):
+        check(lib().spiir_bank_sync_status(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().spiir_bank_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

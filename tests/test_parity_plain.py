@@ -1,0 +1,157 @@
+"""GPU parity of the FP32 path (single-rate and multi-rate) against the FP64
+oracle, through the C ABI. Tolerance: per-template RMS error / RMS SNR <= 1e-5
+(the plain FP32 path's bound). Integer and layout facts are checked exactly."""
+import numpy as np
+import pytest
+
+from paper_1702_02256_gb300 import inputs
+from tests._util import TOL_PLAIN, gpu_snr, rel_rms
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_config0_all_templates(torch_cuda, oracle_mod, variant):
+    w = inputs.workload(0)
+    z = gpu_snr(w["bank"], w["x"], tune=-(variant + 1))[0]
+    ref = oracle_mod.spiir_single(w["bank"], w["x"][0])
+    err = rel_rms(z, ref)
+    assert err.max() <= TOL_PLAIN, err
+
+
+def test_uneven_templates_ragged_tail(torch_cuda, oracle_mod):
+    """Uneven filter counts (0 .. 1100, so some templates split into parts),
+    and a block length that leaves a ragged last time tile."""
+    counts = [0, 1, 2, 3, 5, 17, 31, 33, 64, 129, 300, 513, 1100]
+    bank = inputs.single_rate_bank(len(counts), counts, 700, seed=21)
+    x = inputs.strain(1, 3 * 4100, seed=3)
+    for variant in (0, 1):
+        z = gpu_snr(bank, x, block_len=4100, push_blocks=2, tune=-(variant + 1))[0]
+        ref = oracle_mod.spiir_single(bank, x[0])
+        assert np.all(z[0] == 0)            # template without filters
+        err = rel_rms(z[1:], ref[1:])
+        assert err.max() <= TOL_PLAIN, err
+
+
+def test_block_split_invariance_and_reset(torch_cuda):
+    """Pushing 4 blocks at once equals 4 pushes of one block, bit for bit, and
+    state_reset gives a fresh bank."""
+    import torch
+    from paper_1702_02256_gb300 import spiir
+    bank = inputs.single_rate_bank(6, 100, 900, seed=5)
+    x = inputs.strain(1, 4 * 1024, seed=8)
+    z4 = gpu_snr(bank, x, block_len=1024, push_blocks=4)
+    z1 = gpu_snr(bank, x, block_len=1024, push_blocks=1)
+    assert np.array_equal(z4, z1)
+    b = spiir.Bank(bank, n_streams=1, block_len=1024, max_push_blocks=4)
+    xd = torch.from_numpy(x).cuda()
+    b.push(xd)
+    first = b.read(4096).cpu().numpy()
+    b.push(xd)
+    b.reset()
+    b.push(xd)
+    again = b.read(4096).cpu().numpy()
+    b.sync_status()
+    assert np.array_equal(first, again)
+    assert np.array_equal(first, z4)
+
+
+def test_two_streams_match_separate_banks(torch_cuda, oracle_mod):
+    bank = inputs.single_rate_bank(5, 40, 300, seed=9)
+    x = inputs.strain(2, 2 * 2048, seed=4)
+    z = gpu_snr(bank, x, block_len=2048, n_streams=2)
+    for s in range(2):
+        zs = gpu_snr(bank, x[s:s + 1], block_len=2048, n_streams=1)[0]
+        assert np.array_equal(z[s], zs)
+        ref = oracle_mod.spiir_single(bank, x[s])
+        assert rel_rms(z[s], ref).max() <= TOL_PLAIN
+
+
+def test_config1_scaled_all_templates(torch_cuda, oracle_mod):
+    """Config-1 filters (512 per template, delays to 4095) on 48 templates x 4 s."""
+    w = inputs.workload(1, scale_templates=48, n_samples=4 * 4096)
+    z = gpu_snr(w["bank"], w["x"], push_blocks=4)[0]
+    ref = oracle_mod.spiir_single(w["bank"], w["x"][0])
+    err = rel_rms(z, ref)
+    assert err.max() <= TOL_PLAIN, err.max()
+
+
+def test_config1_full_size_sampled(torch_cuda, oracle_mod):
+    """The benchmark's configuration: 1024 templates x 512 filters, 16 s in one
+    push of 16 blocks; 24 seeded templates checked against the oracle."""
+    w = inputs.workload(1)
+    z = gpu_snr(w["bank"], w["x"], push_blocks=16)[0]
+    sel = np.random.default_rng(0).choice(1024, 24, replace=False)
+    ref = oracle_mod.spiir_single(w["bank"], w["x"][0], templates=sel)
+    err = rel_rms(z[sel], ref)
+    assert err.max() <= TOL_PLAIN, err.max()
+    # every template produced a finite, non-trivial series
+    assert np.all(np.isfinite(z))
+    assert np.all(np.abs(z).max(axis=1) > 0)
+
+
+@pytest.mark.parametrize("align", [True, False])
+def test_multirate_scaled(torch_cuda, oracle_mod, align):
+    w = inputs.workload(2, scale_templates=12, n_samples=4 * 4096)
+    z = gpu_snr(w["bank"], w["x"], push_blocks=1, align=align)[0]
+    ref = oracle_mod.spiir_multirate(w["bank"], w["x"][0], align=align)
+    err = rel_rms(z, ref)
+    assert err.max() <= TOL_PLAIN, err
+
+
+def test_multirate_custom_taps_and_empty_levels(torch_cuda, oracle_mod):
+    counts = np.array([[3, 0, 2, 0], [0, 0, 0, 5], [1, 2, 3, 4], [0, 0, 0, 0]])
+    bank = inputs.multi_rate_bank(4, 4, seed=2, counts=counts, delay_max=200)
+    hd = oracle_mod.kaiser_taps(16, 50.0)
+    hu = oracle_mod.kaiser_taps(16, 40.0)
+    x = inputs.strain(1, 3 * 1024, seed=6)
+    z = gpu_snr(bank, x, block_len=1024, push_blocks=1, h_down=hd, h_up=hu)[0]
+    ref = oracle_mod.spiir_multirate(bank, x[0], h_down=hd, h_up=hu)
+    assert np.all(z[3] == 0)
+    err = rel_rms(z[:3], ref[:3])
+    assert err.max() <= TOL_PLAIN, err
+
+
+def test_multirate_full_size_sampled(torch_cuda, oracle_mod):
+    """Config 2 at full size (4000 templates, 7 rates), 4 s pushed in 1 s
+    blocks; 12 seeded templates against the oracle."""
+    w = inputs.workload(2, n_samples=4 * 4096)
+    z = gpu_snr(w["bank"], w["x"], push_blocks=1)[0]
+    sel = np.random.default_rng(1).choice(4000, 12, replace=False)
+    ref = oracle_mod.spiir_multirate(w["bank"], w["x"][0], templates=sel)
+    err = rel_rms(z[sel], ref)
+    assert err.max() <= TOL_PLAIN, err.max()
+
+
+def test_host_entry_point_matches_device_path(torch_cuda):
+    from paper_1702_02256_gb300 import spiir
+    bank = inputs.single_rate_bank(4, 30, 100, seed=3)
+    x = inputs.strain(1, 2048, seed=2)
+    zd = gpu_snr(bank, x, block_len=2048)
+    b = spiir.Bank(bank, n_streams=1, block_len=2048)
+    zh = b.push_host(x)
+    b.close()
+    assert np.array_equal(zh.astype(np.complex128), zd)
+
+
+def test_kernel_timing_counts_launches(torch_cuda):
+    import torch
+    from paper_1702_02256_gb300 import spiir
+    bank = inputs.multi_rate_bank(8, 3, seed=1)
+    b = spiir.Bank(bank, n_streams=1, block_len=1024)
+    b.enable_timing(True)
+    xd = torch.from_numpy(inputs.strain(1, 1024)).cuda()
+    for _ in range(3):
+        b.push(xd)
+    kt = b.kernel_times()
+    assert kt["recur"][1] == 3 and kt["combine"][1] == 3 and kt["decimate"][1] == 3
+    assert all(ms >= 0 for ms, _ in kt.values())
+    b.close()
