@@ -214,6 +214,31 @@ spiir_status spiir_kaiser_taps(int32_t n_taps, double atten_db, float *out);
 int32_t spiir_assign_level(float a_re, float a_im, int32_t base_rate,
                            int32_t n_levels);
 
+/* One-shot filtering that allocates no device memory. The paper has no
+ * counterpart: this is for callers that cannot call cudaMalloc, such as code
+ * that runs while a CUDA graph is being captured on its stream, or a host
+ * framework whose real-time thread must not allocate device memory.
+ *
+ * Filters x_dev (device float32 [n_samples], one stream) with the bank that
+ * desc describes (plain FP32 form, n_streams = 1), starting from zero filter
+ * state and zero strain history, and writes z_dev (device complex64
+ * [n_templates][n_samples], the layout of spiir_read_snr) -- the SNR that
+ * spiir_bank_create + spiir_push_block + spiir_read_snr would give for the
+ * same description and samples. n_samples: a positive multiple of
+ * 4 * 2^(n_levels-1). The caller owns x_dev and z_dev.
+ *
+ * All device memory it uses is one fixed 32 MiB __device__ array that every
+ * GPU loading the library reserves until the process exits. A bank and length
+ * whose packed coefficients, state and buffers need more fail with EINVAL and a
+ * message giving both sizes. Every call shares that array and leaves its
+ * contents behind (it clears what must start at zero), so calls whose work
+ * overlaps on the GPU -- on two streams, or from two host threads -- race and
+ * must be serialised by the caller. The first call on a device looks up the
+ * array's device address; make that first call before any stream capture.
+ * Host-side packing uses ordinary host memory. */
+spiir_status spiir_filter_noalloc(const spiir_bank_desc *desc, const float *x_dev,
+                                  int64_t n_samples, void *z_dev, void *cuda_stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *spiir_last_error(void);
 

@@ -1014,3 +1014,178 @@ int32_t spiir_assign_level(float a_re, float a_im, int32_t base_rate, int32_t n_
 const char *spiir_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// One-shot filtering without device allocation (spiir_filter_noalloc).
+//
+// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
+// being captured on its stream, a host framework that hands the library a
+// real-time thread on which device allocation is forbidden, or a process whose
+// device memory is carved up in advance by someone else. This entry point
+// serves them: all the device memory it needs lives in one file-scope
+// __device__ array of fixed size, which the module reserves on every GPU that
+// loads the library and keeps until the process exits.
+// ---------------------------------------------------------------------------
+
+#define SPIIR_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+static __device__ __align__(256) unsigned char g_spiir_noalloc_scratch[SPIIR_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+void *g_noalloc_ptr[kMaxDevices] = {};
+KernelTimer g_noalloc_timer;  // stays off: pushes record no events
+
+// Device address of the scratch array on the current device. The array's
+// name is only a host-side stand-in; the address comes from the runtime, once
+// per device, with that device current.
+spiir_status noalloc_scratch(void **out) {
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(SPIIR_EUNSUPPORTED, "device %d out of range", dev);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        CUDA_TRY(cudaGetSymbolAddress(&p, g_spiir_noalloc_scratch));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return SPIIR_OK;
+}
+
+struct Carve {
+    char *base;
+    size_t off = 0;
+    template <typename T>
+    T *take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T *p = reinterpret_cast<T *>(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+template <typename T>
+spiir_status put(T *dst, const std::vector<T> &src, cudaStream_t s) {
+    if (src.empty()) return SPIIR_OK;
+    CUDA_TRY(cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return SPIIR_OK;
+}
+
+}  // namespace
+
+extern "C" spiir_status spiir_filter_noalloc(const spiir_bank_desc *desc, const float *x_dev,
+                                             int64_t n_samples, void *z_dev, void *cuda_stream) {
+    if (!x_dev || !z_dev) return fail(SPIIR_EINVAL, "x_dev and z_dev must not be NULL");
+    spiir_status st = validate(desc);
+    if (st) return st;
+    if (desc->mode != SPIIR_PLAIN_FP32)
+        return fail(SPIIR_EUNSUPPORTED, "spiir_filter_noalloc runs the plain FP32 form only");
+    if (desc->n_streams != 1) return fail(SPIIR_EINVAL, "spiir_filter_noalloc takes one stream");
+    const int H = desc->n_levels - 1;
+    if (n_samples <= 0 || n_samples % (4ll << H) != 0 || n_samples > (1ll << 30))
+        return fail(SPIIR_EINVAL, "n_samples must be a positive multiple of 4*2^(n_levels-1)");
+
+    // Plan for one push of n_samples from zero state.
+    spiir_bank_desc d = *desc;
+    d.block_len = (int32_t)n_samples;
+    d.max_push_blocks = 1;
+    d.tune = desc->tune < 0 ? desc->tune : 0;
+    spiir_bank b;
+    b.d = d;
+    b.n_filters = d.n_filters;
+    if ((st = make_plan(&d, chosen_variant(&d), true, b.p))) return st;
+    const Plan &p = b.p;
+
+    // Size check before any device work.
+    size_t need = 0;
+    {
+        Carve c{nullptr};
+        c.take<float>(p.n_slots);
+        c.take<float>(p.n_slots);
+        c.take<float>(p.n_slots);
+        c.take<float>(p.n_slots);
+        c.take<int32_t>(p.n_slots);
+        c.take<WarpTask>(p.tasks.size());
+        c.take<CtaItem>(p.items.size());
+        c.take<int32_t>(p.task_out.size());
+        c.take<int32_t>(p.comb_ptr.size());
+        c.take<int32_t>(p.comb_rows.size());
+        c.take<float2>(std::max<int64_t>(1, p.n_slots));
+        c.take<float>(p.xbuf_stream_stride);
+        c.take<float2>(p.part_stream_stride);
+        c.take<float2>(p.ubuf_stream_stride);
+        c.take<unsigned int>(1);
+        need = c.off;
+    }
+    if (need > SPIIR_NOALLOC_SCRATCH_BYTES)
+        return fail(SPIIR_EINVAL,
+                    "spiir_filter_noalloc: this bank and length need %zu bytes of scratch, above "
+                    "the fixed %u bytes; use spiir_bank_create instead",
+                    need, (unsigned)SPIIR_NOALLOC_SCRATCH_BYTES);
+
+    void *base = nullptr;
+    if ((st = noalloc_scratch(&base))) return st;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    Carve c{static_cast<char *>(base)};
+    b.are = c.take<float>(p.n_slots);
+    b.aim = c.take<float>(p.n_slots);
+    b.bre = c.take<float>(p.n_slots);
+    b.bim = c.take<float>(p.n_slots);
+    b.xoff = c.take<int32_t>(p.n_slots);
+    b.tasks = c.take<WarpTask>(p.tasks.size());
+    b.items = c.take<CtaItem>(p.items.size());
+    b.task_out = c.take<int32_t>(p.task_out.size());
+    b.comb_ptr = c.take<int32_t>(p.comb_ptr.size());
+    b.comb_rows = c.take<int32_t>(p.comb_rows.size());
+    b.state = c.take<float2>(std::max<int64_t>(1, p.n_slots));
+    b.xbuf = c.take<float>(p.xbuf_stream_stride);
+    b.partial = p.part_stream_stride ? c.take<float2>(p.part_stream_stride) : nullptr;
+    b.ubuf = p.ubuf_stream_stride ? c.take<float2>(p.ubuf_stream_stride) : nullptr;
+    b.status = c.take<unsigned int>(1);
+    b.z = static_cast<float2 *>(z_dev);   // row stride p.ring_len == n_samples
+
+    if ((st = put(b.are, p.are, s)) || (st = put(b.aim, p.aim, s)) || (st = put(b.bre, p.bre, s)) ||
+        (st = put(b.bim, p.bim, s)) || (st = put(b.xoff, p.xoff, s)) ||
+        (st = put(b.tasks, p.tasks, s)) || (st = put(b.items, p.items, s)) ||
+        (st = put(b.task_out, p.task_out, s)) || (st = put(b.comb_ptr, p.comb_ptr, s)) ||
+        (st = put(b.comb_rows, p.comb_rows, s)))
+        return st;
+    // The array keeps the previous call's contents: zero the state, the strain
+    // history, the upsampler history and the status word.
+    CUDA_TRY(cudaMemsetAsync(b.state, 0, std::max<int64_t>(1, p.n_slots) * sizeof(float2), s));
+    CUDA_TRY(cudaMemsetAsync(b.xbuf, 0, p.xbuf_stream_stride * sizeof(float), s));
+    if (b.ubuf) CUDA_TRY(cudaMemsetAsync(b.ubuf, 0, p.ubuf_stream_stride * sizeof(float2), s));
+    CUDA_TRY(cudaMemsetAsync(b.status, 0, sizeof(unsigned int), s));
+    // Templates without filters are never written by the kernels.
+    CUDA_TRY(cudaMemsetAsync(z_dev, 0, (size_t)d.n_templates * n_samples * sizeof(float2), s));
+    CUDA_TRY(spiir_recur_prepare(p.variant, p.smem_bytes));
+
+    b.scale = desc->snr_scale != 0.f ? desc->snr_scale : 2.0f / (float)desc->base_rate;
+    const int nt = d.n_taps ? d.n_taps : 32;
+    b.d.n_taps = nt;
+    b.h_down.resize(nt);
+    b.h_up.resize(nt);
+    if (desc->h_down) {
+        std::copy(desc->h_down, desc->h_down + nt, b.h_down.begin());
+        std::copy(desc->h_up, desc->h_up + nt, b.h_up.begin());
+    } else {
+        lib_kaiser_taps(nt, 60.0, b.h_down.data());
+        lib_kaiser_taps(nt, 60.0, b.h_up.data());
+    }
+    b.last_n.assign(1, 0);
+    b.timer = &g_noalloc_timer;
+    st = push_plain(&b, 0, 1, x_dev, n_samples, n_samples, s);
+    // The bank object only borrows these pointers: clear them so that it
+    // frees nothing when it goes out of scope.
+    b.are = b.aim = b.bre = b.bim = nullptr;
+    b.xoff = nullptr;
+    b.tasks = nullptr;
+    b.items = nullptr;
+    b.task_out = b.comb_ptr = b.comb_rows = nullptr;
+    b.state = b.partial = b.ubuf = b.z = nullptr;
+    b.xbuf = nullptr;
+    b.status = nullptr;
+    b.timer = nullptr;
+    return st;
+}

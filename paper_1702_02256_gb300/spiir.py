@@ -78,6 +78,7 @@ _SIGS = {
     "spiir_kaiser_taps": (_i32, [_i32, _f64, _c_void_p]),
     "spiir_assign_level": (_i32, [_f32, _f32, _i32, _i32]),
     "spiir_last_error": (ctypes.c_char_p, []),
+    "spiir_filter_noalloc": (_i32, [ctypes.POINTER(BankDesc), _c_void_p, _i64, _c_void_p, _c_void_p]),
     "spiir_bank_enable_timing": (_i32, [_c_void_p, _i32]),
     "spiir_bank_kernel_times": (_i32, [_c_void_p, ctypes.POINTER(KernelTimes)]),
 }
@@ -170,6 +171,20 @@ def plan(bank, **kw) -> dict:
     inf = BankInfo()
     check(lib().spiir_bank_plan(ctypes.byref(d), ctypes.byref(inf)))
     return {k: getattr(inf, k) for k, _ in BankInfo._fields_}
+
+
+def filter_noalloc(bank, x, z_out=None, stream=None, **kw):
+    """spiir_filter_noalloc: one-shot filtering of a CUDA tensor x [n] from
+    zero state into z_out (complex64 [T, n]) without any device allocation by
+    the library. Returns z_out."""
+    import torch
+    n = int(x.shape[-1])
+    if z_out is None:
+        z_out = torch.empty((bank.n_templates, n), dtype=torch.complex64, device=x.device)
+    d, _keep = make_desc(bank, n_streams=1, block_len=n, max_push_blocks=1, **kw)
+    check(lib().spiir_filter_noalloc(ctypes.byref(d), x.data_ptr(), n, z_out.data_ptr(),
+                                     _stream_handle(stream)))
+    return z_out
 
 
 def _stream_handle(stream=None) -> int:
