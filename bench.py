@@ -137,22 +137,24 @@ def _traffic(kernel_file: str, key: str):
     return float(kv["dram_bytes_per_launch"])
 
 
-def _workload(name: str, rank: int, templates: int = 0):
+def _workload(name: str, rank: int, templates: int = 0, seconds: int = 0):
     from paper_1702_02256_gb300 import inputs
     if name == "single":
         T = templates or 1024
+        sec = seconds or 16
         bank = inputs.single_rate_bank(T, 512, 4095, seed=rank)
-        return dict(bank=bank, x=inputs.strain(1, 16 * 4096, seed=1 + 100 * rank),
-                    block_len=4096, push_blocks=16,
-                    desc=f"single-rate {T} templates x 512 filters, 4096 Hz, 16 s per step "
-                         "(one 16-block push), delays 0-4095")
+        return dict(bank=bank, x=inputs.strain(1, sec * 4096, seed=1 + 100 * rank),
+                    block_len=4096, push_blocks=sec,
+                    desc=f"single-rate {T} templates x 512 filters, 4096 Hz, {sec} s per step "
+                         f"(one {sec}-block push), delays 0-4095")
     if name == "multirate":
         T = templates or 4000
+        sec = seconds or 16
         bank = inputs.multi_rate_bank(T, 7, seed=rank)
-        return dict(bank=bank, x=inputs.strain(1, 16 * 4096, seed=1 + 100 * rank),
+        return dict(bank=bank, x=inputs.strain(1, sec * 4096, seed=1 + 100 * rank),
                     block_len=4096, push_blocks=1,
-                    desc=f"multi-rate {T} templates, 7 rates 4096-64 Hz, 16 s per step "
-                         "(16 pushes of 1 s)")
+                    desc=f"multi-rate {T} templates, 7 rates 4096-64 Hz, {sec} s per step "
+                         f"({sec} pushes of 1 s)")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -199,7 +201,7 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    w = _workload(args.workload, 0, args.templates)
+    w = _workload(args.workload, 0, args.templates, args.seconds)
     per_step = max(1.0, 150.0 / max(1, args.steps + args.warmup))
     rates = []
     sample = ""
@@ -238,7 +240,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     from paper_1702_02256_gb300 import spiir
 
-    w = _workload(args.workload, rank, args.templates)
+    w = _workload(args.workload, rank, args.templates, args.seconds)
     bank = w["bank"]
     n = w["x"].shape[1]
     push_len = w["block_len"] * w["push_blocks"]
@@ -409,6 +411,8 @@ def main():
     ap.add_argument("--tune", type=int, default=0)
     ap.add_argument("--templates", type=int, default=0,
                     help="template count (0 = the workload's full size); small cases for ncu")
+    ap.add_argument("--seconds", type=int, default=0,
+                    help="seconds of strain per step (0 = the workload's 16 s)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -53,7 +53,6 @@ spiir_status fail(spiir_status st, const char *fmt, ...) {
 inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
 constexpr int kSmemMax = 227 * 1024;
-constexpr int kWindowFloats = 12288;  // preferred strain window (48 KB)
 
 // The library's resampling taps: Kaiser-window-tapered ideal low-pass with
 // cutoff at half the input Nyquist frequency (Sec. 2.2). I0 by its series.
@@ -121,6 +120,7 @@ struct Plan {
     std::vector<CtaItem> items;
     std::vector<int32_t> task_out;
     std::vector<int32_t> comb_ptr, comb_rows;
+    std::vector<int32_t> order;
     int64_t lds_rounds = 0, lds_wavefronts = 0;
     int64_t n_units = 0;
 };
@@ -210,14 +210,11 @@ void plan_info(const spiir_bank_desc *d, const Plan &p, spiir_bank_info *info) {
 }
 
 int default_variant(const spiir_bank_desc *d) {
-    // per (template, level) filter counts
-    const int L = d->n_levels;
-    std::vector<int64_t> cnt((size_t)d->n_templates * L, 0);
-    for (int64_t k = 0; k < d->n_filters; ++k)
-        cnt[(size_t)d->template_id[k] * L + (d->level ? d->level[k] : 0)]++;
-    int64_t mx = 0;
-    for (auto c : cnt) mx = std::max(mx, c);
-    return mx > 256 ? 1 : 0;
+    // T = 32, FMAX = 8: units above 256 filters span 2-4 warps, which gives the
+    // persistent scheduler twice as many independent chains as FMAX = 16, and
+    // the 32-sample tile halves the reduction's share per sample
+    (void)d;
+    return 3;
 }
 
 // Builds the plan. With arrays == false only the sizes are computed.
@@ -252,13 +249,12 @@ spiir_status make_plan(const spiir_bank_desc *d, int variant, bool arrays, Plan 
         p.hist[i] = (int)h;
         p.max_delay = std::max<int>(p.max_delay, (int)(maxd[i] + D));
         p.max_n[i] = push_max >> i;
-        int64_t W = std::max<int64_t>(kWindowFloats, h + 4 * p.T);
-        W = std::min<int64_t>(W, (kSmemMax - 64) / 4);
-        int64_t sg = (W - h) / p.T * p.T;
-        if (sg < p.T) sg = p.T;
-        if (sg >= p.max_n[i]) sg = round_up(p.max_n[i], 4);
+        // a push is cut into time segments of at most ~4096 base-rate samples
+        // (see push_plain); the window holds the history plus one segment
+        const int64_t sg = std::min<int64_t>(round_up(p.max_n[i], 4), (4096 >> i) + 8);
         p.seg[i] = (int)sg;
-        p.smem_bytes = std::max<int>(p.smem_bytes, (int)(16 + 4 * (h + sg) + 64));
+        p.smem_bytes = std::max<int>(p.smem_bytes,
+                                     (int)(16 + spiir_recur_red_bytes() + 4 * (h + sg) + 64));
         p.xbuf_off[i] = off;
         off += round_up(h + p.max_n[i] + 64, 4);
     }
@@ -272,7 +268,7 @@ spiir_status make_plan(const spiir_bank_desc *d, int variant, bool arrays, Plan 
     for (int i = 0; i < L; ++i)
         for (int t = 0; t < d->n_templates; ++t) {
             const auto &f = lists[(size_t)i * d->n_templates + t];
-            if ((int64_t)f.size() > 32ll * p.FMAX) all_single = false;
+            if ((int64_t)f.size() > 32ll * SPIIR_CTA_WARPS * p.FMAX) all_single = false;
         }
     p.need_combine = (L > 1) || !all_single;
     p.comb_ptr.assign((size_t)d->n_templates * L + 1, 0);
@@ -283,7 +279,7 @@ spiir_status make_plan(const spiir_bank_desc *d, int variant, bool arrays, Plan 
             const int64_t M = (int64_t)f.size();
             p.fs_per_block += M * (d->block_len >> i);
             if (M == 0) continue;
-            const int64_t cap = 32ll * p.FMAX;
+            const int64_t cap = 32ll * SPIIR_CTA_WARPS * p.FMAX;
             const int64_t parts = (M + cap - 1) / cap;
             for (int64_t q = 0; q < parts; ++q) {
                 const int64_t b0 = M * q / parts, b1 = M * (q + 1) / parts;
@@ -321,7 +317,7 @@ spiir_status make_plan(const spiir_bank_desc *d, int variant, bool arrays, Plan 
         p.part_base[i] = poff;
         poff += rows[i] * p.part_stride[i];
         if (i > 0) {
-            p.ubuf_stride[i] = (int32_t)round_up(SPIIR_UHIST + p.max_n[i], 2);
+            p.ubuf_stride[i] = (int32_t)round_up(SPIIR_UHIST + p.max_n[i] + 8, 2);
             p.ubuf_off[i] = uoff;
             uoff += (int64_t)d->n_templates * p.ubuf_stride[i];
         }
@@ -329,52 +325,77 @@ spiir_status make_plan(const spiir_bank_desc *d, int variant, bool arrays, Plan 
     p.part_stream_stride = poff;
     p.ubuf_stream_stride = uoff;
 
-    // warps: classes (level, G, F)
+    // Bundles: one warp of small units (32/G units of G <= 32 lanes), or the
+    // 2^xw warps of one unit larger than a warp; all of one (level, G, F).
     std::stable_sort(units.begin(), units.end(), [](const Unit &a, const Unit &b) {
         if (a.level != b.level) return a.level < b.level;
         if (a.F != b.F) return a.F > b.F;
         return a.G < b.G;
     });
-    struct WarpPlan {
-        int level, G, F;
+    struct Bundle {
+        int level, G, F, W;       // W warps; G <= 32 when W == 1
         std::vector<int> units;
     };
-    std::vector<WarpPlan> warps;
+    std::vector<Bundle> bundles;
     for (size_t u = 0; u < units.size();) {
-        WarpPlan w{units[u].level, units[u].G, units[u].F, {}};
-        const int per = 32 / w.G;
-        while (u < units.size() && (int)w.units.size() < per && units[u].level == w.level &&
-               units[u].G == w.G && units[u].F == w.F)
-            w.units.push_back((int)u++);
-        warps.push_back(std::move(w));
+        if (units[u].G > 32) {
+            bundles.push_back(Bundle{units[u].level, 32, units[u].F, units[u].G / 32, {(int)u}});
+            ++u;
+            continue;
+        }
+        Bundle b{units[u].level, units[u].G, units[u].F, 1, {}};
+        const int per = 32 / b.G;
+        while (u < units.size() && (int)b.units.size() < per && units[u].level == b.level &&
+               units[u].G == b.G && units[u].F == b.F)
+            b.units.push_back((int)u++);
+        bundles.push_back(std::move(b));
     }
-    // CTA items: warps of one (level, F), heaviest first
-    std::vector<int> order(warps.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        const int64_t wa = (int64_t)warps[a].F * p.max_n[warps[a].level];
-        const int64_t wb = (int64_t)warps[b].F * p.max_n[warps[b].level];
-        if (wa != wb) return wa > wb;
-        return warps[a].level < warps[b].level;
+    // CTA items: bundles of one (level, F, W) filling SPIIR_CTA_WARPS warps
+    std::vector<int> bo(bundles.size());
+    for (size_t i = 0; i < bo.size(); ++i) bo[i] = (int)i;
+    std::stable_sort(bo.begin(), bo.end(), [&](int a, int b) {
+        const Bundle &x = bundles[a], &y = bundles[b];
+        if (x.level != y.level) return x.level < y.level;
+        if (x.F != y.F) return x.F > y.F;
+        return x.W > y.W;
     });
-    std::vector<std::vector<int>> item_warps;
-    for (size_t i = 0; i < order.size();) {
+    std::vector<std::vector<int>> item_bundles;
+    for (size_t i = 0; i < bo.size();) {
         std::vector<int> it;
-        const int lv = warps[order[i]].level, F = warps[order[i]].F;
-        while (i < order.size() && (int)it.size() < SPIIR_CTA_WARPS &&
-               warps[order[i]].level == lv && warps[order[i]].F == F)
-            it.push_back(order[i++]);
-        item_warps.push_back(std::move(it));
+        const Bundle &b0 = bundles[bo[i]];
+        int warps_used = 0;
+        while (i < bo.size() && warps_used + bundles[bo[i]].W <= SPIIR_CTA_WARPS &&
+               bundles[bo[i]].level == b0.level && bundles[bo[i]].F == b0.F &&
+               bundles[bo[i]].W == b0.W) {
+            warps_used += bundles[bo[i]].W;
+            it.push_back(bo[i++]);
+        }
+        item_bundles.push_back(std::move(it));
     }
 
     p.n_units = (int64_t)units.size();
     int64_t n_slots = 0;
-    for (auto &w : warps) n_slots += 32ll * w.F;
+    size_t n_warps = 0;
+    for (auto &b : bundles) {
+        n_slots += 32ll * b.F * b.W;
+        n_warps += b.W;
+        p.max_F = std::max(p.max_F, b.F);
+    }
     p.n_slots = n_slots;
-    for (auto &w : warps) p.max_F = std::max(p.max_F, w.F);
+    // queue order of the items: most work first
+    p.order.resize(item_bundles.size());
+    {
+        std::vector<int64_t> work(item_bundles.size(), 0);
+        for (size_t i = 0; i < item_bundles.size(); ++i)
+            for (int bi : item_bundles[i])
+                work[i] += (int64_t)bundles[bi].F * bundles[bi].W * p.max_n[bundles[bi].level];
+        for (size_t i = 0; i < p.order.size(); ++i) p.order[i] = (int32_t)i;
+        std::stable_sort(p.order.begin(), p.order.end(),
+                         [&](int32_t a, int32_t b) { return work[a] > work[b]; });
+    }
     if (!arrays) {
-        p.tasks.resize(warps.size());
-        p.items.resize(item_warps.size());
+        p.tasks.resize(n_warps);
+        p.items.resize(item_bundles.size());
         return SPIIR_OK;
     }
 
@@ -384,93 +405,107 @@ spiir_status make_plan(const spiir_bank_desc *d, int variant, bool arrays, Plan 
     p.bim.assign(n_slots, 0.f);
     p.xoff.assign(n_slots, 0);
     int64_t slot_base = 0;
-    for (auto &iw : item_warps) {
+    for (auto &ib : item_bundles) {
         CtaItem ci;
-        ci.level = warps[iw[0]].level;
+        ci.level = bundles[ib[0]].level;
         ci.task_begin = (int32_t)p.tasks.size();
-        ci.task_count = (int32_t)iw.size();
-        ci.F = warps[iw[0]].F;
-        for (int wi : iw) {
-            const WarpPlan &w = warps[wi];
-            const int g = w.G, F = w.F, lv = w.level;
+        ci.task_count = 0;
+        ci.F = bundles[ib[0]].F;
+        for (int bi : ib) {
+            const Bundle &b = bundles[bi];
+            const int g = b.G, F = b.F, lv = b.level, W = b.W;
             const int64_t D = align_delay(lv, L, p.n_taps, p.align);
             const int hist = p.hist[lv];
-            WarpTask wt;
-            wt.slot_base = (int32_t)slot_base;
-            wt.F = (int16_t)F;
             int gl = 0;
             while ((1 << gl) < g) ++gl;
-            wt.g_log2 = (int8_t)gl;
-            wt.level = (int8_t)lv;
-            wt.out_base = (int32_t)p.task_out.size();
-            wt.n_groups = (int32_t)w.units.size();
-            for (int u : w.units) p.task_out.push_back(units[u].dest);
-            // per-group pools bucketed by shared-memory bank of the offset
-            const int ng = (int)w.units.size();
-            std::vector<std::vector<std::vector<int64_t>>> pool(ng,
-                                                                std::vector<std::vector<int64_t>>(32));
+            int xw = 0;
+            while ((1 << xw) < W) ++xw;
+            const int out_base = (int32_t)p.task_out.size();
+            for (int u : b.units) p.task_out.push_back(units[u].dest);
+            // pools bucketed by the shared-memory bank of the window offset:
+            // one per group (W == 1) or one shared by the unit's warps
+            const int ng = (int)b.units.size();
+            std::vector<std::vector<std::vector<int64_t>>> pool(
+                ng, std::vector<std::vector<int64_t>>(32));
             std::vector<int> rot(ng, 0);
             for (int q = 0; q < ng; ++q)
-                for (int64_t k : units[w.units[q]].filt) {
+                for (int64_t k : units[b.units[q]].filt) {
                     const int64_t xo = hist - (d->delay[k] + D);
                     pool[q][xo & 31].push_back(k);
                 }
+            const int64_t base0 = slot_base;
+            for (int w = 0; w < W; ++w) {
+                WarpTask wt;
+                wt.slot_base = (int32_t)(base0 + 32ll * F * w);
+                wt.F = (int8_t)F;
+                wt.g_log2 = (int8_t)gl;
+                wt.level = (int8_t)lv;
+                wt.xw_log2 = (int8_t)xw;
+                wt.out_base = out_base;
+                wt.n_groups = (int16_t)(W > 1 ? 1 : ng);
+                wt.xw_rank = (int8_t)w;
+                wt.pad = 0;
+                p.tasks.push_back(wt);
+                ci.task_count++;
+            }
+            // rounds of all warps interleaved so the shared pool drains evenly
             for (int r = 0; r < F; ++r) {
-                uint32_t used = 0;
-                int wave = 0;
-                int per_bank[32] = {};
-                for (int l = 0; l < 32; ++l) {
-                    const int64_t s = slot_base + (int64_t)r * 32 + l;
-                    const int q = l / g;
-                    int64_t pick = -1;
-                    if (q < ng) {
-                        // fullest bank not yet read this round, else the fullest
-                        // bank (a conflict); drawing from the fullest keeps the
-                        // pools even so later rounds still find free banks
-                        auto &pl = pool[q];
-                        int best = -1;
-                        for (int pass = 0; pass < 2 && best < 0; ++pass) {
-                            size_t most = 0;
-                            for (int c = 0; c < 32; ++c) {
-                                const int b = (rot[q] + c) & 31;
-                                if (pass == 0 && (used >> b & 1u)) continue;
-                                if (pl[b].size() > most) {
-                                    most = pl[b].size();
-                                    best = b;
+                for (int w = 0; w < W; ++w) {
+                    uint32_t used = 0;
+                    int per_bank[32] = {};
+                    for (int l = 0; l < 32; ++l) {
+                        const int64_t s = base0 + 32ll * F * w + (int64_t)r * 32 + l;
+                        const int q = W > 1 ? 0 : l / g;
+                        int64_t pick = -1;
+                        if (q < ng) {
+                            // fullest bank not yet read this round, else the
+                            // fullest bank (a conflict); drawing from the fullest
+                            // keeps the pools even for the later rounds
+                            auto &pl = pool[q];
+                            int best = -1;
+                            for (int pass = 0; pass < 2 && best < 0; ++pass) {
+                                size_t most = 0;
+                                for (int c = 0; c < 32; ++c) {
+                                    const int bk = (rot[q] + c) & 31;
+                                    if (pass == 0 && (used >> bk & 1u)) continue;
+                                    if (pl[bk].size() > most) {
+                                        most = pl[bk].size();
+                                        best = bk;
+                                    }
                                 }
                             }
+                            if (best >= 0) {
+                                pick = pl[best].back();
+                                pl[best].pop_back();
+                                rot[q] = (best + 1) & 31;
+                            }
                         }
-                        if (best >= 0) {
-                            pick = pl[best].back();
-                            pl[best].pop_back();
-                            rot[q] = (best + 1) & 31;
+                        int32_t xo;
+                        if (pick >= 0) {
+                            p.are[s] = d->a_re[pick];
+                            p.aim[s] = d->a_im[pick];
+                            p.bre[s] = d->b_re[pick];
+                            p.bim[s] = d->b_im[pick];
+                            xo = (int32_t)(hist - (d->delay[pick] + D));
+                        } else {
+                            // inert padding slot: read a free bank inside the window
+                            int bk = 0;
+                            while (bk < 32 && (used >> bk & 1u)) ++bk;
+                            bk &= 31;
+                            xo = hist - ((hist - bk) & 31);
+                            if (xo < 0) xo = hist;
                         }
+                        p.xoff[s] = xo;
+                        used |= 1u << (xo & 31);
+                        per_bank[xo & 31]++;
                     }
-                    int32_t xo;
-                    if (pick >= 0) {
-                        p.are[s] = d->a_re[pick];
-                        p.aim[s] = d->a_im[pick];
-                        p.bre[s] = d->b_re[pick];
-                        p.bim[s] = d->b_im[pick];
-                        xo = (int32_t)(hist - (d->delay[pick] + D));
-                    } else {
-                        // inert padding slot: read a free bank inside the window
-                        int b = 0;
-                        while (b < 32 && (used >> b & 1u)) ++b;
-                        b &= 31;
-                        xo = hist - ((hist - b) & 31);
-                        if (xo < 0) xo = hist;
-                    }
-                    p.xoff[s] = xo;
-                    used |= 1u << (xo & 31);
-                    per_bank[xo & 31]++;
+                    int wave = 0;
+                    for (int bk = 0; bk < 32; ++bk) wave = std::max(wave, per_bank[bk]);
+                    p.lds_rounds++;
+                    p.lds_wavefronts += wave;
                 }
-                for (int b = 0; b < 32; ++b) wave = std::max(wave, per_bank[b]);
-                p.lds_rounds++;
-                p.lds_wavefronts += wave;
             }
-            slot_base += 32ll * F;
-            p.tasks.push_back(wt);
+            slot_base += 32ll * F * W;
         }
         p.items.push_back(ci);
     }
@@ -485,6 +520,7 @@ int64_t plan_footprint(const spiir_bank_desc *d, const Plan &p) {
     b += (int64_t)p.items.size() * sizeof(CtaItem);
     b += (int64_t)p.tasks.size() * 32 * 4;               // task_out (upper bound)
     b += ((int64_t)d->n_templates * p.n_levels + 1) * 4 + p.n_slots * 4;  // comb lists (bound)
+    b += (int64_t)p.items.size() * 4 * (1 + S) + S * 4;   // queue order, progress
     b += S * p.n_slots * 8;                              // state
     b += S * p.xbuf_stream_stride * 4;                   // strain windows
     b += S * p.part_stream_stride * 8;                   // partial sums
@@ -525,6 +561,9 @@ struct spiir_bank {
     float2 *state = nullptr, *partial = nullptr, *ubuf = nullptr, *z = nullptr;
     float *xbuf = nullptr, *xstage = nullptr;
     unsigned int *status = nullptr;
+    int32_t *order = nullptr;
+    unsigned int *queue = nullptr, *prog = nullptr;
+    int ctas_per_sm = 1, n_sms = 1;
     std::vector<int64_t> last_n;
     int64_t footprint = 0;
     int64_t n_filters = 0;
@@ -533,7 +572,7 @@ struct spiir_bank {
 
     void free_device() {
         void *ptrs[] = {are, aim, bre, bim, xoff, tasks, items, task_out, comb_ptr, comb_rows,
-                        state, partial, ubuf, z, xbuf, xstage, status};
+                        state, partial, ubuf, z, xbuf, xstage, status, order, queue, prog};
         for (void *q : ptrs)
             if (q) cudaFree(q);
         are = aim = bre = bim = nullptr;
@@ -544,6 +583,8 @@ struct spiir_bank {
         state = partial = ubuf = z = nullptr;
         xbuf = xstage = nullptr;
         status = nullptr;
+        order = nullptr;
+        queue = prog = nullptr;
         if (tc) {
             spiir_tc_destroy(tc);
             tc = nullptr;
@@ -572,6 +613,10 @@ spiir_status alloc_plain(spiir_bank *b, cudaStream_t s) {
     if ((st = upload(&b->task_out, p.task_out, s))) return st;
     if ((st = upload(&b->comb_ptr, p.comb_ptr, s))) return st;
     if ((st = upload(&b->comb_rows, p.comb_rows, s))) return st;
+    if ((st = upload(&b->order, p.order, s))) return st;
+    CUDA_TRY(cudaMalloc((void **)&b->queue, S * sizeof(unsigned int)));
+    CUDA_TRY(cudaMalloc((void **)&b->prog, std::max<int64_t>(1, S * (int64_t)p.items.size()) *
+                                              sizeof(unsigned int)));
     CUDA_TRY(cudaMalloc((void **)&b->state, std::max<int64_t>(1, S * p.n_slots) * sizeof(float2)));
     CUDA_TRY(cudaMalloc((void **)&b->xbuf, S * p.xbuf_stream_stride * sizeof(float)));
     if (p.part_stream_stride)
@@ -586,17 +631,28 @@ spiir_status alloc_plain(spiir_bank *b, cudaStream_t s) {
     if (b->ubuf) CUDA_TRY(cudaMemsetAsync(b->ubuf, 0, S * p.ubuf_stream_stride * sizeof(float2), s));
     CUDA_TRY(cudaMemsetAsync(b->z, 0, S * (int64_t)b->d.n_templates * p.ring_len * sizeof(float2), s));
     CUDA_TRY(cudaMemsetAsync(b->status, 0, sizeof(unsigned int), s));
-    CUDA_TRY(spiir_recur_prepare(p.variant, p.smem_bytes));
+    CUDA_TRY(spiir_recur_prepare(p.variant, p.smem_bytes, &b->ctas_per_sm));
+    CUDA_TRY(cudaDeviceGetAttribute(&b->n_sms, cudaDevAttrMultiProcessorCount, b->device));
     return SPIIR_OK;
+}
+
+// Time segments per push: about 4096 base-rate samples each, a power of two,
+// at least 4 samples at the lowest level.
+int push_segments(const Plan &p, int64_t n) {
+    int S = 1;
+    while ((int64_t)S * 4096 < n) S *= 2;
+    while (S > 1 && ((n >> p.H) / S) < 4) S /= 2;
+    return S;
 }
 
 void level_args(const spiir_bank *b, int64_t n, int64_t n_prev, LevelArgs *lev) {
     const Plan &p = b->p;
+    const int S = push_segments(p, n);
     for (int i = 0; i < p.n_levels; ++i) {
         LevelArgs &L = lev[i];
         L.hist = p.hist[i];
         L.n = (int32_t)(n >> i);
-        L.seg = p.seg[i];
+        L.seg = (int32_t)round_up(((n >> i) + S - 1) / S, 4);
         L.n_prev = (int32_t)(n_prev >> i);
         L.part_base = p.part_base[i];
         L.part_stride = p.part_stride[i];
@@ -612,6 +668,9 @@ spiir_status push_plain(spiir_bank *b, int s0, int count, const float *x, int64_
     const Plan &p = b->p;
     const int64_t n_prev = b->last_n[s0];
     PrologueArgs pa{};
+    pa.queue = b->queue;
+    pa.prog = b->prog;
+    pa.n_items = (int32_t)p.items.size();
     pa.xbuf = b->xbuf;
     pa.xbuf_stream_stride = p.xbuf_stream_stride;
     pa.x_in = x;
@@ -640,6 +699,11 @@ spiir_status push_plain(spiir_bank *b, int s0, int count, const float *x, int64_
         RecurArgs ra{};
         ra.tasks = b->tasks;
         ra.items = b->items;
+        ra.order = b->order;
+        ra.n_items = (int32_t)p.items.size();
+        ra.n_segs = push_segments(p, n);
+        ra.queue = b->queue;
+        ra.prog = b->prog;
         ra.task_out = b->task_out;
         ra.a_re = b->are;
         ra.a_im = b->aim;
@@ -661,7 +725,10 @@ spiir_status push_plain(spiir_bank *b, int s0, int count, const float *x, int64_
         ra.status = b->status;
         level_args(b, n, n_prev, ra.lev);
         tm.begin(SPIIR_K_RECUR, st);
-        CUDA_TRY(spiir_launch_recur(ra, p.variant, (int)p.items.size(), count, p.smem_bytes, st));
+        const int64_t total = (int64_t)ra.n_segs * ra.n_items;
+        const int64_t resident = std::max<int64_t>(1, (int64_t)b->ctas_per_sm * b->n_sms / count);
+        const int ctas = (int)std::min<int64_t>(total, resident);
+        CUDA_TRY(spiir_launch_recur(ra, p.variant, ctas, count, p.smem_bytes, st));
         tm.end(st);
     }
     if (p.need_combine) {
@@ -1111,6 +1178,9 @@ extern "C" spiir_status spiir_filter_noalloc(const spiir_bank_desc *desc, const 
         c.take<int32_t>(p.task_out.size());
         c.take<int32_t>(p.comb_ptr.size());
         c.take<int32_t>(p.comb_rows.size());
+        c.take<int32_t>(p.order.size());
+        c.take<unsigned int>(1);
+        c.take<unsigned int>(std::max<size_t>(1, p.items.size()));
         c.take<float2>(std::max<int64_t>(1, p.n_slots));
         c.take<float>(p.xbuf_stream_stride);
         c.take<float2>(p.part_stream_stride);
@@ -1138,6 +1208,9 @@ extern "C" spiir_status spiir_filter_noalloc(const spiir_bank_desc *desc, const 
     b.task_out = c.take<int32_t>(p.task_out.size());
     b.comb_ptr = c.take<int32_t>(p.comb_ptr.size());
     b.comb_rows = c.take<int32_t>(p.comb_rows.size());
+    b.order = c.take<int32_t>(p.order.size());
+    b.queue = c.take<unsigned int>(1);
+    b.prog = c.take<unsigned int>(std::max<size_t>(1, p.items.size()));
     b.state = c.take<float2>(std::max<int64_t>(1, p.n_slots));
     b.xbuf = c.take<float>(p.xbuf_stream_stride);
     b.partial = p.part_stream_stride ? c.take<float2>(p.part_stream_stride) : nullptr;
@@ -1149,7 +1222,7 @@ extern "C" spiir_status spiir_filter_noalloc(const spiir_bank_desc *desc, const 
         (st = put(b.bim, p.bim, s)) || (st = put(b.xoff, p.xoff, s)) ||
         (st = put(b.tasks, p.tasks, s)) || (st = put(b.items, p.items, s)) ||
         (st = put(b.task_out, p.task_out, s)) || (st = put(b.comb_ptr, p.comb_ptr, s)) ||
-        (st = put(b.comb_rows, p.comb_rows, s)))
+        (st = put(b.comb_rows, p.comb_rows, s)) || (st = put(b.order, p.order, s)))
         return st;
     // The array keeps the previous call's contents: zero the state, the strain
     // history, the upsampler history and the status word.
@@ -1159,7 +1232,9 @@ extern "C" spiir_status spiir_filter_noalloc(const spiir_bank_desc *desc, const 
     CUDA_TRY(cudaMemsetAsync(b.status, 0, sizeof(unsigned int), s));
     // Templates without filters are never written by the kernels.
     CUDA_TRY(cudaMemsetAsync(z_dev, 0, (size_t)d.n_templates * n_samples * sizeof(float2), s));
-    CUDA_TRY(spiir_recur_prepare(p.variant, p.smem_bytes));
+    CUDA_TRY(spiir_recur_prepare(p.variant, p.smem_bytes, &b.ctas_per_sm));
+    CUDA_TRY(cudaGetDevice(&b.device));
+    CUDA_TRY(cudaDeviceGetAttribute(&b.n_sms, cudaDevAttrMultiProcessorCount, b.device));
 
     b.scale = desc->snr_scale != 0.f ? desc->snr_scale : 2.0f / (float)desc->base_rate;
     const int nt = d.n_taps ? d.n_taps : 32;
@@ -1186,6 +1261,8 @@ extern "C" spiir_status spiir_filter_noalloc(const spiir_bank_desc *desc, const 
     b.state = b.partial = b.ubuf = b.z = nullptr;
     b.xbuf = nullptr;
     b.status = nullptr;
+    b.order = nullptr;
+    b.queue = b.prog = nullptr;
     b.timer = nullptr;
     return st;
 }

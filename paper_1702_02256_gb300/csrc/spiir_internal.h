@@ -17,14 +17,19 @@
 // One warp's work in the FP32 recursion kernel: 32 lanes x F rounds of
 // filter slots (slot = slot_base + round*32 + lane). Lanes form groups of
 // 2^g_log2 consecutive lanes; each group is one unit (a template's filters at
-// one level, or a part of them) whose per-sample sum the group reduces.
+// one level, or a part of them) whose per-sample sum the group reduces. A unit
+// larger than one warp spans 2^xw_log2 consecutive warps of the CTA (then
+// g_log2 = 5); its warps add their sums in shared memory and rank 0 writes.
 struct WarpTask {
     int32_t slot_base;
-    int16_t F;        // rounds, even, <= the kernel variant's FMAX
-    int8_t g_log2;    // lane group size = 1 << g_log2
+    int8_t F;         // rounds, even, <= the kernel variant's FMAX
+    int8_t g_log2;    // lane group size = 1 << g_log2 (<= 32)
     int8_t level;
+    int8_t xw_log2;   // warps per unit (0 = unit inside this warp)
     int32_t out_base; // task_out[out_base + group] = destination of the group
-    int32_t n_groups; // groups that hold a unit (the rest are padding)
+    int16_t n_groups; // groups that hold a unit (the rest are padding)
+    int8_t xw_rank;   // this warp's rank in its multi-warp unit
+    int8_t pad;
 };
 
 // One CTA's work: up to SPIIR_CTA_WARPS warp tasks of the same level.
@@ -39,7 +44,7 @@ struct CtaItem {
 struct LevelArgs {
     int32_t hist;     // strain history samples in front of the block (mult. of 4)
     int32_t n;        // samples of this level in this push
-    int32_t seg;      // samples per SMEM window (multiple of 4)
+    int32_t seg;      // samples per time segment (multiple of 4)
     int32_t n_prev;   // samples of the previous push at this level
     int64_t part_base;   // float2 offset of this level's partial rows
     int64_t part_stride; // float2 per partial row
@@ -52,6 +57,11 @@ struct LevelArgs {
 struct RecurArgs {
     const WarpTask *tasks;
     const CtaItem *items;
+    const int32_t *order;      // queue order of the CTA items (heaviest first)
+    int32_t n_items;           // CTA items (groups) per stream
+    int32_t n_segs;            // time segments per push; queue = n_segs * n_items
+    unsigned int *queue;       // [stream] work counter, zeroed by the prologue
+    unsigned int *prog;        // [stream][n_items] segments finished this push
     const int32_t *task_out;   // >= 0: direct z row; < 0: partial row -(v+1)
     const float *a_re, *a_im, *b_re, *b_im;
     const int32_t *xoff;       // per slot: hist - delay (window offset)
@@ -72,6 +82,10 @@ struct RecurArgs {
 };
 
 struct PrologueArgs {
+    unsigned int *queue;        // zeroed for the recursion kernel's work queue
+    unsigned int *prog;         // [stream][n_items] zeroed
+    int32_t n_items;
+    int32_t pad;
     float *xbuf;
     int64_t xbuf_stream_stride;
     const float *x_in;          // [n_streams_in_push][n] device, level 0 samples
@@ -173,9 +187,11 @@ struct KernelTimer {
 // Kernel launchers (spiir_plain.cu).
 cudaError_t spiir_launch_prologue(const PrologueArgs &a, int n_streams, cudaStream_t s);
 cudaError_t spiir_launch_decimate(const DecimArgs &a, int n_streams, cudaStream_t s);
-cudaError_t spiir_launch_recur(const RecurArgs &a, int variant, int n_items,
+cudaError_t spiir_launch_recur(const RecurArgs &a, int variant, int n_ctas,
                                int n_streams, int smem_bytes, cudaStream_t s);
 cudaError_t spiir_launch_combine(const CombineArgs &a, int n_streams, cudaStream_t s);
 int spiir_recur_variant_count();
 void spiir_recur_variant_shape(int variant, int *time_tile, int *fmax);
-cudaError_t spiir_recur_prepare(int variant, int smem_bytes);
+// Sets the dynamic shared memory limit and returns resident CTAs per SM.
+cudaError_t spiir_recur_prepare(int variant, int smem_bytes, int *ctas_per_sm);
+int spiir_recur_red_bytes();

@@ -104,6 +104,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *m, uint32_t parity,
 __global__ void prologue_kernel(const PrologueArgs a) {
     const int lev = blockIdx.x;
     const int s = a.stream0 + blockIdx.y;
+    if (lev == 0 && a.prog) {
+        // fresh work queue and segment progress for this push
+        if (threadIdx.x == 0) a.queue[s] = 0u;
+        for (int k = threadIdx.x; k < a.n_items; k += blockDim.x)
+            a.prog[(int64_t)s * a.n_items + k] = 0u;
+    }
     const LevelArgs L = a.lev[lev];
     float *buf = a.xbuf + (int64_t)s * a.xbuf_stream_stride + L.xbuf_off;
     const int hist = L.hist, np = L.n_prev;
@@ -147,14 +153,68 @@ __global__ void decimate_kernel(const DecimArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Recursion kernel
+// Recursion kernel (persistent, dynamically scheduled)
+//
+// Work items are (CTA item, time segment) pairs taken from a per-stream
+// atomic queue in segment-major order. Segment s of an item starts only after
+// segment s-1 of the same item has finished (a progress counter with
+// acquire/release ordering); the filter state travels through global memory
+// between segments, so an item's segments may run on different SMs. This
+// keeps every SM busy whatever the number and size of the items, and every
+// wait is on an item that a running CTA took earlier from the queue.
 // ---------------------------------------------------------------------------
+
+constexpr int kRedBytes = 2 * SPIIR_CTA_WARPS * 32 * 2 * 4;   // cross-warp sums, 2 buffers
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned int *p, unsigned int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void named_bar(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void named_arrive(int id, int n) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// Wait (at most ~2 s) until *p >= want; on timeout record it and go on.
+__device__ __forceinline__ bool wait_counter(const unsigned int *p, unsigned int want,
+                                             unsigned int *status) {
+    if (ld_acquire(p) >= want) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (true) {
+        __nanosleep(100);
+        if (ld_acquire(p) >= want) return true;
+        if (globaltimer_ns() - t0 > 2000000000ull) {
+            atomicExch(status, SPIIR_DEV_TIMEOUT);
+            return false;
+        }
+    }
+}
 
 template <int PMAX>
 struct Regs {
     float2 are[PMAX], aim[PMAX], naim[PMAX], bre[PMAX], bim[PMAX], yre[PMAX], yim[PMAX];
     int off0[PMAX], off1[PMAX];
 };
+
+// Pairwise (tree-ordered) sum of v[LO..HI): a log-depth dependency chain.
+template <int LO, int HI>
+__device__ __forceinline__ float2 tree_sum(const float2 *v) {
+    if constexpr (HI - LO == 1) {
+        return v[LO];
+    } else {
+        constexpr int MID = (LO + HI) / 2;
+        return __fadd2_rn(tree_sum<LO, MID>(v), tree_sum<MID, HI>(v));
+    }
+}
 
 // One time tile of T samples for P slot pairs; sre/sim receive this lane's
 // per-sample sums over its filters. tl < T marks a ragged last tile.
@@ -164,26 +224,23 @@ __device__ __forceinline__ void tile(const float *__restrict__ xs, int tb, int t
 #pragma unroll
     for (int j = 0; j < T; ++j) {
         if (FULL || j < tl) {
-            float2 accr, acci;
+            float2 nr[P], ni[P];
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 const float2 X = make_float2(xs[r.off0[p] + tb + j], xs[r.off1[p] + tb + j]);
                 const float2 tr = __fmul2_rn(r.bre[p], X);
                 const float2 ti = __fmul2_rn(r.bim[p], X);
-                float2 nr = __ffma2_rn(r.are[p], r.yre[p], tr);
-                nr = __ffma2_rn(r.naim[p], r.yim[p], nr);
-                float2 ni = __ffma2_rn(r.are[p], r.yim[p], ti);
-                ni = __ffma2_rn(r.aim[p], r.yre[p], ni);
-                r.yre[p] = nr;
-                r.yim[p] = ni;
-                if (p == 0) {
-                    accr = nr;
-                    acci = ni;
-                } else {
-                    accr = __fadd2_rn(accr, nr);
-                    acci = __fadd2_rn(acci, ni);
-                }
+                float2 a = __ffma2_rn(r.are[p], r.yre[p], tr);
+                a = __ffma2_rn(r.naim[p], r.yim[p], a);
+                float2 b = __ffma2_rn(r.are[p], r.yim[p], ti);
+                b = __ffma2_rn(r.aim[p], r.yre[p], b);
+                r.yre[p] = a;
+                r.yim[p] = b;
+                nr[p] = a;
+                ni[p] = b;
             }
+            const float2 accr = tree_sum<0, P>(nr);
+            const float2 acci = tree_sum<0, P>(ni);
             sre[j] = accr.x + accr.y;
             sim[j] = acci.x + acci.y;
         } else {
@@ -219,153 +276,211 @@ __device__ __forceinline__ void rs_round(float (&re)[T], float (&im)[T], int lan
     }
 }
 
-constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
+__host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
+
+// Where one warp's reduction ends up and what it spans.
+struct OutCtx {
+    float2 *row;      // destination row at this segment's first sample
+    float scale;
+    bool valid;
+    int xw_log2, xw_rank, warp;
+    int n_tiles;      // tiles in this segment (for the cross-warp hand-off)
+    float *red;       // cross-warp buffers in shared memory
+};
 
 // After the reduce-scatter for group size G a lane holds CH = max(T/G, 1)
 // consecutive sums; when G > T, 2^NR lanes hold the same sums and the first
-// of them writes.
+// of them writes. Units spanning several warps hand their sums to rank 0
+// through two shared-memory buffers: the other ranks arrive on FULL[b]
+// without waiting, rank 0 waits on FULL[b], adds in rank order, and arrives on
+// EMPTY[b]; a rank waits on EMPTY[b] only before reusing buffer b.
 template <int T, int G>
-__device__ __forceinline__ void reduce_write(float (&re)[T], float (&im)[T], int lane,
-                                             int tl, float2 *row, float scale, bool valid) {
+__device__ __forceinline__ void reduce_write(float (&re)[T], float (&im)[T], int lane, int tl,
+                                             int t0, int tile, const OutCtx &o) {
     rs_round<T, T, G / 2>(re, im, lane);
     constexpr int NS = ilog2(G < T ? G : T);
     constexpr int NR = ilog2(G) - NS;
     constexpr int CH = (T / G) > 1 ? (T / G) : 1;
-    if (!valid) return;
+    if constexpr (G == 32) {
+        if (o.xw_log2 > 0) {
+            const int nw = 1 << o.xw_log2;
+            const int first = o.warp - o.xw_rank;
+            const int b = tile & 1;
+            const int base = 1 + 4 * (first >> 1);     // FULL0, FULL1, EMPTY0, EMPTY1
+            const int n = 32 * nw;
+            if (o.xw_rank > 0) {
+                if (tile >= 2) named_bar(base + 2 + b, n);      // buffer b free again
+                float *mine = o.red + ((b * SPIIR_CTA_WARPS + o.warp) * 32 + lane) * (2 * CH);
+#pragma unroll
+                for (int i = 0; i < CH; ++i) {
+                    mine[2 * i] = re[i];
+                    mine[2 * i + 1] = im[i];
+                }
+                named_arrive(base + b, n);
+                return;
+            }
+            named_bar(base + b, n);
+            for (int w = 1; w < nw; ++w) {
+                const float *other =
+                    o.red + ((b * SPIIR_CTA_WARPS + first + w) * 32 + lane) * (2 * CH);
+#pragma unroll
+                for (int i = 0; i < CH; ++i) {
+                    re[i] += other[2 * i];
+                    im[i] += other[2 * i + 1];
+                }
+            }
+            if (tile + 2 < o.n_tiles) named_arrive(base + 2 + b, n);
+        }
+    }
+    if (!o.valid) return;
     if ((lane & ((1 << NR) - 1)) != 0) return;
-    const int t0 = ((lane & (G - 1)) >> NR) * CH;
+    const int tc = ((lane & (G - 1)) >> NR) * CH;
+    float2 *row = o.row + t0;
 #pragma unroll
     for (int i = 0; i < CH; ++i)
-        if (t0 + i < tl) row[t0 + i] = make_float2(scale * re[i], scale * im[i]);
+        if (tc + i < tl) row[tc + i] = make_float2(o.scale * re[i], o.scale * im[i]);
 }
 
 template <int T, int PMAX, int P>
 __device__ __forceinline__ void run_segment(const float *__restrict__ xs, int seg_len,
-                                            Regs<PMAX> &r, int lane, int g, float2 *row,
-                                            float scale, bool valid) {
-    for (int t0 = 0; t0 < seg_len; t0 += T) {
+                                            Regs<PMAX> &r, int lane, int g, const OutCtx &o) {
+    int k = 0;
+    for (int t0 = 0; t0 < seg_len; t0 += T, ++k) {
         const int tl = min(T, seg_len - t0);
         float sre[T], sim[T];
         if (tl == T)
             tile<T, PMAX, P, true>(xs, t0, T, r, sre, sim);
         else
             tile<T, PMAX, P, false>(xs, t0, tl, r, sre, sim);
-        float2 *rw = row + t0;
         switch (g) {
-            case 0: reduce_write<T, 1>(sre, sim, lane, tl, rw, scale, valid); break;
-            case 1: reduce_write<T, 2>(sre, sim, lane, tl, rw, scale, valid); break;
-            case 2: reduce_write<T, 4>(sre, sim, lane, tl, rw, scale, valid); break;
-            case 3: reduce_write<T, 8>(sre, sim, lane, tl, rw, scale, valid); break;
-            case 4: reduce_write<T, 16>(sre, sim, lane, tl, rw, scale, valid); break;
-            default: reduce_write<T, 32>(sre, sim, lane, tl, rw, scale, valid); break;
+            case 0: reduce_write<T, 1>(sre, sim, lane, tl, t0, k, o); break;
+            case 1: reduce_write<T, 2>(sre, sim, lane, tl, t0, k, o); break;
+            case 2: reduce_write<T, 4>(sre, sim, lane, tl, t0, k, o); break;
+            case 3: reduce_write<T, 8>(sre, sim, lane, tl, t0, k, o); break;
+            case 4: reduce_write<T, 16>(sre, sim, lane, tl, t0, k, o); break;
+            default: reduce_write<T, 32>(sre, sim, lane, tl, t0, k, o); break;
         }
     }
 }
 
 template <int T, int PMAX, int P>
 __device__ __forceinline__ void dispatch_segment(int p_runtime, const float *xs, int seg_len,
-                                                 Regs<PMAX> &r, int lane, int g, float2 *row,
-                                                 float scale, bool valid) {
+                                                 Regs<PMAX> &r, int lane, int g,
+                                                 const OutCtx &o) {
     if constexpr (P <= PMAX) {
         if (p_runtime == P)
-            run_segment<T, PMAX, P>(xs, seg_len, r, lane, g, row, scale, valid);
+            run_segment<T, PMAX, P>(xs, seg_len, r, lane, g, o);
         else
-            dispatch_segment<T, PMAX, P + 1>(p_runtime, xs, seg_len, r, lane, g, row, scale,
-                                             valid);
+            dispatch_segment<T, PMAX, P + 1>(p_runtime, xs, seg_len, r, lane, g, o);
     }
 }
 
-template <int T, int FMAX>
-__global__ void __launch_bounds__(SPIIR_CTA_WARPS * 32) recur_kernel(const RecurArgs a) {
+template <int T, int FMAX, int MINB>
+__global__ void __launch_bounds__(SPIIR_CTA_WARPS * 32, MINB) recur_kernel(const RecurArgs a) {
     constexpr int PMAX = FMAX / 2;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
-    float *xs = reinterpret_cast<float *>(smem + 16);
+    float *red = reinterpret_cast<float *>(smem + 16);
+    float *xs = reinterpret_cast<float *>(smem + 16 + kRedBytes);
+    __shared__ int s_item;
 
     const int stream = a.stream0 + blockIdx.y;
-    const CtaItem item = a.items[blockIdx.x];
-    const LevelArgs L = a.lev[item.level];
-    const float *xlev = a.xbuf + (int64_t)stream * a.xbuf_stream_stride + L.xbuf_off;
+    unsigned int *queue = a.queue + stream;
+    unsigned int *prog = a.prog + (int64_t)stream * a.n_items;
+    const int total = a.n_segs * a.n_items;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool active = warp < item.task_count;
-
-    WarpTask wt;
-    wt.slot_base = 0; wt.F = 0; wt.g_log2 = 0; wt.level = 0; wt.out_base = 0; wt.n_groups = 0;
-    if (active) wt = a.tasks[item.task_begin + warp];
-    const int P = active ? wt.F / 2 : 0;
-
-    Regs<PMAX> r;
     float2 *st = a.state + (int64_t)stream * a.n_slots;
-#pragma unroll
-    for (int p = 0; p < PMAX; ++p) {
-        if (p < P) {
-            const int64_t s0 = wt.slot_base + (int64_t)(2 * p) * 32 + lane, s1 = s0 + 32;
-            r.are[p] = make_float2(a.a_re[s0], a.a_re[s1]);
-            r.aim[p] = make_float2(a.a_im[s0], a.a_im[s1]);
-            r.naim[p] = make_float2(-r.aim[p].x, -r.aim[p].y);
-            r.bre[p] = make_float2(a.b_re[s0], a.b_re[s1]);
-            r.bim[p] = make_float2(a.b_im[s0], a.b_im[s1]);
-            const float2 y0 = st[s0], y1 = st[s1];
-            r.yre[p] = make_float2(y0.x, y1.x);
-            r.yim[p] = make_float2(y0.y, y1.y);
-            r.off0[p] = a.xoff[s0];
-            r.off1[p] = a.xoff[s1];
-        } else {
-            r.are[p] = r.aim[p] = r.naim[p] = r.bre[p] = r.bim[p] = make_float2(0.f, 0.f);
-            r.yre[p] = r.yim[p] = make_float2(0.f, 0.f);
-            r.off0[p] = r.off1[p] = 0;
-        }
-    }
-
-    // Destination of this lane's group.
-    bool valid = false;
-    float2 *row = nullptr;
-    float scale = 1.f;
-    if (active) {
-        const int grp = lane >> wt.g_log2;
-        if (grp < wt.n_groups) {
-            const int dst = a.task_out[wt.out_base + grp];
-            valid = true;
-            if (dst >= 0) {
-                row = a.z + (int64_t)stream * a.z_stream_stride + (int64_t)dst * a.z_row_stride;
-                scale = a.scale;
-            } else {
-                row = a.partial + (int64_t)stream * a.partial_stream_stride + L.part_base +
-                      (int64_t)(-dst - 1) * L.part_stride;
-            }
-        }
-    }
 
     if (threadIdx.x == 0) {
         mbar_init(mbar, 1);
         fence_mbar_init();
     }
-    __syncthreads();
-
     uint32_t phase = 0;
-    for (int s0 = 0; s0 < L.n; s0 += L.seg) {
-        const int sl = min(L.seg, L.n - s0);
-        if (threadIdx.x == 0) {
-            const uint32_t bytes = (uint32_t)(((L.hist + sl) * 4 + 15) & ~15);
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(mbar, bytes);
-            bulk_g2s(xs, xlev + s0, bytes, mbar);
-        }
-        const bool ok = mbar_wait_bounded(mbar, phase, a.status);
-        phase ^= 1u;
-        if (!ok) break;
-        if (active && P > 0)
-            dispatch_segment<T, PMAX, 1>(P, xs, sl, r, lane, wt.g_log2,
-                                         row ? row + s0 : nullptr, scale, valid);
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(queue, 1u);
         __syncthreads();
-    }
-
+        const int q = s_item;
+        if (q >= total) break;
+        const int seg = q / a.n_items;
+        const int gi = a.order[q - seg * a.n_items];
+        const CtaItem item = a.items[gi];
+        const LevelArgs L = a.lev[item.level];
+        const int s0 = seg * L.seg;
+        const int sl = min(L.seg, L.n - s0);
+        if (seg > 0 && threadIdx.x == 0) wait_counter(prog + gi, (unsigned)seg, a.status);
+        __syncthreads();
+        if (sl > 0) {
+            const float *xlev = a.xbuf + (int64_t)stream * a.xbuf_stream_stride + L.xbuf_off;
+            if (threadIdx.x == 0) {
+                const uint32_t bytes = (uint32_t)(((L.hist + sl) * 4 + 15) & ~15);
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(mbar, bytes);
+                bulk_g2s(xs, xlev + s0, bytes, mbar);
+            }
+            const bool ok = mbar_wait_bounded(mbar, phase, a.status);
+            phase ^= 1u;
+            const bool active = ok && warp < item.task_count;
+            if (active) {
+                const WarpTask wt = a.tasks[item.task_begin + warp];
+                const int P = wt.F / 2;
+                Regs<PMAX> r;
 #pragma unroll
-    for (int p = 0; p < PMAX; ++p) {
-        if (p < P) {
-            const int64_t s0 = wt.slot_base + (int64_t)(2 * p) * 32 + lane, s1 = s0 + 32;
-            st[s0] = make_float2(r.yre[p].x, r.yim[p].x);
-            st[s1] = make_float2(r.yre[p].y, r.yim[p].y);
+                for (int p = 0; p < PMAX; ++p) {
+                    if (p < P) {
+                        const int64_t i0 = wt.slot_base + (int64_t)(2 * p) * 32 + lane, i1 = i0 + 32;
+                        r.are[p] = make_float2(a.a_re[i0], a.a_re[i1]);
+                        r.aim[p] = make_float2(a.a_im[i0], a.a_im[i1]);
+                        r.naim[p] = make_float2(-r.aim[p].x, -r.aim[p].y);
+                        r.bre[p] = make_float2(a.b_re[i0], a.b_re[i1]);
+                        r.bim[p] = make_float2(a.b_im[i0], a.b_im[i1]);
+                        const float2 y0 = __ldcg(st + i0), y1 = __ldcg(st + i1);
+                        r.yre[p] = make_float2(y0.x, y1.x);
+                        r.yim[p] = make_float2(y0.y, y1.y);
+                        r.off0[p] = a.xoff[i0];
+                        r.off1[p] = a.xoff[i1];
+                    } else {
+                        r.are[p] = r.aim[p] = r.naim[p] = r.bre[p] = r.bim[p] = make_float2(0.f, 0.f);
+                        r.yre[p] = r.yim[p] = make_float2(0.f, 0.f);
+                        r.off0[p] = r.off1[p] = 0;
+                    }
+                }
+                OutCtx o;
+                o.row = nullptr;
+                o.scale = 1.f;
+                o.valid = false;
+                o.xw_log2 = wt.xw_log2;
+                o.xw_rank = wt.xw_rank;
+                o.warp = warp;
+                o.n_tiles = (sl + T - 1) / T;
+                o.red = red;
+                const int grp = lane >> wt.g_log2;
+                if (grp < wt.n_groups && wt.xw_rank == 0) {
+                    const int dst = a.task_out[wt.out_base + grp];
+                    o.valid = true;
+                    if (dst >= 0) {
+                        o.row = a.z + (int64_t)stream * a.z_stream_stride + (int64_t)dst * a.z_row_stride;
+                        o.scale = a.scale;
+                    } else {
+                        o.row = a.partial + (int64_t)stream * a.partial_stream_stride + L.part_base +
+                                (int64_t)(-dst - 1) * L.part_stride;
+                    }
+                    o.row += s0;
+                }
+                if (P > 0) dispatch_segment<T, PMAX, 1>(P, xs, sl, r, lane, wt.g_log2, o);
+#pragma unroll
+                for (int p = 0; p < PMAX; ++p) {
+                    if (p < P) {
+                        const int64_t i0 = wt.slot_base + (int64_t)(2 * p) * 32 + lane, i1 = i0 + 32;
+                        st[i0] = make_float2(r.yre[p].x, r.yim[p].x);
+                        st[i1] = make_float2(r.yre[p].y, r.yim[p].y);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release(prog + gi, (unsigned)(seg + 1));
         }
     }
 }
@@ -374,11 +489,41 @@ __global__ void __launch_bounds__(SPIIR_CTA_WARPS * 32) recur_kernel(const Recur
 // Combine: parts + upsample(next lower rate) + scale
 // ---------------------------------------------------------------------------
 
+// Each thread makes 8 consecutive outputs of a level from a register window
+// of 19 lower-rate samples (the 16-tap polyphase branches of the x2
+// interpolator overlap), plus the unit's partial sums.
+constexpr int kCombOut = 8;
+
+template <int HT>
+__device__ __forceinline__ void combine_chunk(const float2 *__restrict__ ulow, const float *h2,
+                                              int n0, float (&re)[kCombOut],
+                                              float (&im)[kCombOut]) {
+    // window w[k] = u[n0/2 - (HT-1) + k], k < HT - 1 + kCombOut/2
+    constexpr int NW = HT - 1 + kCombOut / 2;
+    float2 w[NW];
+    const float2 *u = ulow + SPIIR_UHIST + (n0 >> 1) - (HT - 1);
+#pragma unroll
+    for (int k = 0; k < NW; ++k) w[k] = u[k];
+#pragma unroll
+    for (int r = 0; r < kCombOut; ++r) {
+        const int ph = r & 1;
+        const int c = HT - 1 + (r >> 1);   // window index of u[m], m = (n0 + r) >> 1
+        float ar = re[r], ai = im[r];
+#pragma unroll
+        for (int j = 0; j < HT; ++j) {
+            const float hw = h2[2 * j + ph];
+            ar = fmaf(hw, w[c - j].x, ar);
+            ai = fmaf(hw, w[c - j].y, ai);
+        }
+        re[r] = ar;
+        im[r] = ai;
+    }
+}
+
 __global__ void combine_kernel(const CombineArgs a) {
     const int t = blockIdx.x;
     const int s = a.stream0 + blockIdx.y;
     const int H = a.n_levels - 1;
-    const int half = a.n_taps / 2;
     __shared__ float h2[SPIIR_MAX_TAPS];
     if (threadIdx.x < a.n_taps) h2[threadIdx.x] = a.h_up2[threadIdx.x];
     __syncthreads();
@@ -396,27 +541,49 @@ __global__ void combine_kernel(const CombineArgs a) {
             n_low = Ll.n;
         }
         float2 *zrow = a.z + (int64_t)s * a.z_stream_stride + (int64_t)t * a.z_row_stride;
-        for (int n = threadIdx.x; n < L.n; n += blockDim.x) {
-            float re = 0.f, im = 0.f;
+        for (int n0 = threadIdx.x * kCombOut; n0 < L.n; n0 += blockDim.x * kCombOut) {
+            const int cnt = min(kCombOut, L.n - n0);
+            float re[kCombOut], im[kCombOut];
+#pragma unroll
+            for (int r = 0; r < kCombOut; ++r) re[r] = im[r] = 0.f;
             for (int q = r0; q < r1; ++q) {
-                const float2 v = part[L.part_base + (int64_t)a.comb_rows[q] * L.part_stride + n];
-                re += v.x;
-                im += v.y;
+                const float2 *pr = part + L.part_base + (int64_t)a.comb_rows[q] * L.part_stride + n0;
+#pragma unroll
+                for (int r = 0; r < kCombOut; ++r)
+                    if (r < cnt) {
+                        const float2 v = pr[r];
+                        re[r] += v.x;
+                        im[r] += v.y;
+                    }
             }
             if (ulow) {
-                const float2 *u = ulow + SPIIR_UHIST + (n >> 1);
-                const int ph = n & 1;
-                for (int j = 0; j < half; ++j) {
-                    const float w = h2[2 * j + ph];
-                    const float2 v = u[-j];
-                    re = fmaf(w, v.x, re);
-                    im = fmaf(w, v.y, im);
+                switch (a.n_taps / 2) {
+                    case 16: combine_chunk<16>(ulow, h2, n0, re, im); break;
+                    case 8: combine_chunk<8>(ulow, h2, n0, re, im); break;
+                    case 32: combine_chunk<32>(ulow, h2, n0, re, im); break;
+                    default: {
+                        // other tap counts: direct form
+                        const int half = a.n_taps / 2;
+                        for (int r = 0; r < kCombOut; ++r) {
+                            const float2 *u = ulow + SPIIR_UHIST + ((n0 + r) >> 1);
+                            const int ph = (n0 + r) & 1;
+                            for (int j = 0; j < half; ++j) {
+                                re[r] = fmaf(h2[2 * j + ph], u[-j].x, re[r]);
+                                im[r] = fmaf(h2[2 * j + ph], u[-j].y, im[r]);
+                            }
+                        }
+                    }
                 }
             }
-            if (i > 0)
-                urow[SPIIR_UHIST + n] = make_float2(re, im);
-            else
-                zrow[n] = make_float2(a.scale * re, a.scale * im);
+            if (i > 0) {
+#pragma unroll
+                for (int r = 0; r < kCombOut; ++r)
+                    if (r < cnt) urow[SPIIR_UHIST + n0 + r] = make_float2(re[r], im[r]);
+            } else {
+#pragma unroll
+                for (int r = 0; r < kCombOut; ++r)
+                    if (r < cnt) zrow[n0 + r] = make_float2(a.scale * re[r], a.scale * im[r]);
+            }
         }
         __syncthreads();
         if (ulow) {
@@ -440,10 +607,12 @@ struct Variant {
 };
 
 const Variant kVariants[] = {
-    {32, 8, recur_kernel<32, 8>},
-    {16, 16, recur_kernel<16, 16>},
-    {32, 4, recur_kernel<32, 4>},
-    {16, 8, recur_kernel<16, 8>},
+    {16, 8, recur_kernel<16, 8, 3>},
+    {16, 16, recur_kernel<16, 16, 2>},
+    {32, 4, recur_kernel<32, 4, 3>},
+    {32, 8, recur_kernel<32, 8, 2>},
+    {16, 4, recur_kernel<16, 4, 4>},
+    {32, 8, recur_kernel<32, 8, 3>},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
@@ -456,10 +625,18 @@ void spiir_recur_variant_shape(int v, int *time_tile, int *fmax) {
     *fmax = kVariants[v].FMAX;
 }
 
-cudaError_t spiir_recur_prepare(int v, int smem_bytes) {
-    return cudaFuncSetAttribute(kVariants[v].fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem_bytes);
+cudaError_t spiir_recur_prepare(int v, int smem_bytes, int *ctas_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(kVariants[v].fn,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (e != cudaSuccess) return e;
+    int n = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kVariants[v].fn, SPIIR_CTA_WARPS * 32,
+                                                      smem_bytes);
+    *ctas_per_sm = n > 0 ? n : 1;
+    return e;
 }
+
+int spiir_recur_red_bytes() { return kRedBytes; }
 
 cudaError_t spiir_launch_prologue(const PrologueArgs &a, int n_streams, cudaStream_t s) {
     prologue_kernel<<<dim3(a.n_levels, n_streams), 256, 0, s>>>(a);
@@ -471,13 +648,13 @@ cudaError_t spiir_launch_decimate(const DecimArgs &a, int n_streams, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t spiir_launch_recur(const RecurArgs &a, int variant, int n_items, int n_streams,
+cudaError_t spiir_launch_recur(const RecurArgs &a, int variant, int n_ctas, int n_streams,
                                int smem_bytes, cudaStream_t s) {
-    kVariants[variant].fn<<<dim3(n_items, n_streams), SPIIR_CTA_WARPS * 32, smem_bytes, s>>>(a);
+    kVariants[variant].fn<<<dim3(n_ctas, n_streams), SPIIR_CTA_WARPS * 32, smem_bytes, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t spiir_launch_combine(const CombineArgs &a, int n_streams, cudaStream_t s) {
-    combine_kernel<<<dim3(a.n_templates, n_streams), 256, 0, s>>>(a);
+    combine_kernel<<<dim3(a.n_templates, n_streams), 128, 0, s>>>(a);
     return cudaGetLastError();
 }
