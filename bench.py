@@ -138,13 +138,15 @@ def _traffic(kernel_file: str, key: str):
 
 
 def _workload(name: str, rank: int, templates: int = 0, seconds: int = 0):
+    """The benchmark workloads: seeded synthetic banks of the configurations'
+    shapes, one bank per rank (weak scaling)."""
     from paper_1702_02256_gb300 import inputs
     if name == "single":
         T = templates or 1024
         sec = seconds or 16
         bank = inputs.single_rate_bank(T, 512, 4095, seed=rank)
         return dict(bank=bank, x=inputs.strain(1, sec * 4096, seed=1 + 100 * rank),
-                    block_len=4096, push_blocks=sec,
+                    block_len=4096, push_blocks=sec, n_streams=1, chunk_len=256,
                     desc=f"single-rate {T} templates x 512 filters, 4096 Hz, {sec} s per step "
                          f"(one {sec}-block push), delays 0-4095")
     if name == "multirate":
@@ -152,9 +154,17 @@ def _workload(name: str, rank: int, templates: int = 0, seconds: int = 0):
         sec = seconds or 16
         bank = inputs.multi_rate_bank(T, 7, seed=rank)
         return dict(bank=bank, x=inputs.strain(1, sec * 4096, seed=1 + 100 * rank),
-                    block_len=4096, push_blocks=1,
+                    block_len=4096, push_blocks=1, n_streams=1, chunk_len=256,
                     desc=f"multi-rate {T} templates, 7 rates 4096-64 Hz, {sec} s per step "
                          f"({sec} pushes of 1 s)")
+    if name == "tc":
+        T = templates or 8000
+        sec = seconds or 8
+        bank = inputs.single_rate_bank(T, 256, 1023, seed=rank)
+        return dict(bank=bank, x=inputs.strain(2, sec * 4096, seed=1 + 100 * rank),
+                    block_len=4096, push_blocks=1, n_streams=2, chunk_len=256,
+                    desc=f"single-rate {T} templates x 256 filters, 2 streams, 4096 Hz, {sec} s "
+                         f"per step ({sec} pushes of 1 s of both streams), delays 0-1023")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -229,42 +239,34 @@ def run_reference(args):
     return 0
 
 
-def run_ours(args):
-    import torch
-    ws, rank, local = _dist()
-    dist = None
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    from paper_1702_02256_gb300 import spiir
+FORM_MODE = {"plain": "plain", "fp16": "fp16", "bf16": "bf16"}
 
-    w = _workload(args.workload, rank, args.templates, args.seconds)
+
+def _measure(w, form, args, dev, dist, sampler, rank, ws):
+    """Time one form of the filtering on workload w. Returns a dict of the
+    device-timed throughput, per-kernel times, latency and end-to-end rate."""
+    import torch
+    from paper_1702_02256_gb300 import spiir
     bank = w["bank"]
+    S = w["n_streams"]
     n = w["x"].shape[1]
     push_len = w["block_len"] * w["push_blocks"]
-    b = spiir.Bank(bank, n_streams=1, block_len=w["block_len"],
-                   max_push_blocks=w["push_blocks"], tune=args.tune)
+    kw = dict(tune=args.tune) if form == "plain" else dict(mode=form, chunk_len=w["chunk_len"])
+    b = spiir.Bank(bank, n_streams=S, block_len=w["block_len"], max_push_blocks=w["push_blocks"], **kw)
     info = b.info()
     x = torch.from_numpy(w["x"]).to(dev)
-    pushes = [x[:, s:s + push_len].contiguous() for s in range(0, n, push_len)]
-    fs_per_step = int(np.sum(n >> bank.level.astype(np.int64)))
+    pushes = [x[:, s0:s0 + push_len].contiguous() for s0 in range(0, n, push_len)]
+    fs_per_step = S * int(np.sum(n >> bank.level.astype(np.int64)))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
     stream = torch.cuda.current_stream()
 
     def step():
         for p in pushes:
-            b.push(p)
+            b.push(p, stream_id=-1)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-
-    sampler = ClockSampler(_gpu_id(torch, local)) if rank == 0 else None
-    if sampler:
-        sampler.start()
-        time.sleep(0.5)
     b.enable_timing(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -283,23 +285,22 @@ def run_ours(args):
     t_wall1 = time.time()
     kt = b.kernel_times()
     b.enable_timing(False)
-    total_ms = sum(a.elapsed_time(c) for a, c in ev)
+    total_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
     if dist:
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
-    value = ws * fs_per_step * args.steps / (total_ms / 1e3)
 
-    # per-block latency: one 1 s block per push, push -> SNR copied out
+    # per-block latency: one 1 s block of every stream per push, push -> SNR out
     blk = w["block_len"]
     xb = x[:, :blk].contiguous()
-    zout = torch.empty((1, bank.n_templates, blk), dtype=torch.complex64, device=dev)
+    zout = torch.empty((S, bank.n_templates, blk), dtype=torch.complex64, device=dev)
     lat = []
     for i in range(40):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        b.push(xb)
+        b.push(xb, stream_id=-1)
         b.read(blk, stream_id=-1, out=zout)
         e1.record(stream)
         e1.synchronize()
@@ -307,11 +308,11 @@ def run_ours(args):
             lat.append(e0.elapsed_time(e1))
     lat = np.array(lat)
 
-    # end to end through the host-buffer entry point (copies inside)
-    xh = torch.from_numpy(w["x"]).pin_memory()
-    zh = torch.empty((1, bank.n_templates, push_len), dtype=torch.complex64).pin_memory()
-    xh_pushes = [xh[:, s:s + push_len].contiguous().pin_memory() for s in range(0, n, push_len)]
-    e2e_steps = max(3, min(args.steps, 20))
+    # end to end through the host-buffer entry point (copies inside the call)
+    xh_pushes = [torch.from_numpy(np.ascontiguousarray(w["x"][:, s0:s0 + push_len])).pin_memory()
+                 for s0 in range(0, n, push_len)]
+    zh = torch.empty((S, bank.n_templates, push_len), dtype=torch.complex64).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
     for p in xh_pushes:
         b.push_host(p, z_out=zh)
     t0 = time.perf_counter()
@@ -324,78 +325,137 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
     b.sync_status()
+    b.close()
+    del flush
+    torch.cuda.synchronize()
+    return dict(form=form, info=info, kt=kt, ms_per_step=ms_per_step,
+                value=ws * fs_per_step * args.steps / (total_ms / 1e3),
+                fs_per_step=fs_per_step, steps=args.steps,
+                rtt=ws * bank.n_templates * S * (n / 4096.0) / (ms_per_step / 1e3),
+                p50=float(np.percentile(lat, 50)), p99=float(np.percentile(lat, 99)),
+                e2e=ws * fs_per_step / e2e_s, h2d=int(S * n * 4),
+                d2h=int(S * bank.n_templates * n * 8), wall=(t_wall0, t_wall1))
 
+
+def _roofline(m, w, args, peaks, sms):
+    """Roofline of the dominant kernel of one measured form."""
+    kt = m["kt"]
+    bank = w["bank"]
+    if m["form"] == "plain":
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = sms * FP32_LANES_PER_SM * sm_max * 1e6 / LANE_OPS_PER_FS * FLOPS_PER_FS / 1e12
+        ms, nl = kt.get("recur", (0.0, 0))
+        ach = FLOPS_PER_FS * m["fs_per_step"] * m["steps"] / nl / (ms / nl / 1e3) / 1e12 if nl else 0.0
+        return {"bound": "alu", "kernel": "recur_kernel", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak if peak else None,
+                "traffic": _traffic("spiir_plain.cu", f"recur_{args.workload}"),
+                "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz "
+                              f"(sm_max_mhz of measured peaks) / {LANE_OPS_PER_FS} lane-ops x "
+                              f"{FLOPS_PER_FS} flops per filter-sample"}
+    # tensor-core form: algorithmic contraction flops of the dominant kernel
+    S = w["n_streams"]
+    samples = S * w["x"].shape[1] * m["steps"]
+    F = m["info"]["tc_fir_len"]
+    L = w["chunk_len"]
+    fir_flops = 4.0 * (F + L) * bank.n_templates * samples        # 2 real rows x 2 flops x K
+    carry_flops = 12.0 * bank.n_filters * samples                 # 4M state + 8M output
+    fir_ms, fir_n = kt.get("tc_fir", (0.0, 0))
+    car_ms, car_n = kt.get("tc_carry", (0.0, 0))
+    peak = float(peaks.get("bf16_tflops", 1890.7))
+    if fir_ms >= car_ms:
+        name, ach = "tc_fir_kernel", fir_flops / (fir_ms / 1e3) / 1e12 if fir_ms else 0.0
+    else:
+        name, ach = "tc_carry_kernel", carry_flops / (car_ms / 1e3) / 1e12 if car_ms else 0.0
+    return {"bound": "tensor", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "traffic": None,
+            "peak_basis": "measured dense bf16 burst (cuBLAS) of MEASURED_PEAKS; fp16 has the same "
+                          "nominal dense rate",
+            "fir_tflops": fir_flops / (fir_ms / 1e3) / 1e12 if fir_ms else None,
+            "carry_tflops": carry_flops / (car_ms / 1e3) / 1e12 if car_ms else None}
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = _workload(args.workload, rank, args.templates, args.seconds)
+    sampler = ClockSampler(_gpu_id(torch, local)) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.5)
+    form = args.form or ("fp16" if args.workload == "tc" else "plain")
+    main = _measure(w, form, args, dev, dist, sampler, rank, ws)
+    chosen = None
+    if args.chosen and args.chosen != form and w["bank"].n_levels == 1:
+        chosen = _measure(w, args.chosen, args, dev, dist, sampler, rank, ws)
     if rank != 0:
-        b.close()
         if dist:
             dist.destroy_process_group()
         return 0
-
     sampler.stop()
-    clocks = sampler.summary(t_wall0, t_wall1)
+    clocks = sampler.summary(*main["wall"])
     peaks = _peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_lane_ops = sms * FP32_LANES_PER_SM * sm_max * 1e6
-    peak_tflops = peak_lane_ops / LANE_OPS_PER_FS * FLOPS_PER_FS / 1e12
-    rec_ms, rec_n = kt.get("recur", (0.0, 0))
-    fs_per_launch = fs_per_step * args.steps / max(1, rec_n)
-    achieved = (FLOPS_PER_FS * fs_per_launch) / (rec_ms / max(1, rec_n) / 1e3) / 1e12 if rec_n else 0.0
-    traffic = _traffic("spiir_plain.cu", f"recur_{args.workload}")
-    launches = int(sum(c for _, c in kt.values()))
-    shares = {k: round(v[0] / max(1e-9, sum(u[0] for u in kt.values())), 4) for k, v in kt.items()}
+    kt = main["kt"]
+    tot = max(1e-9, sum(v[0] for v in kt.values()))
+    shares = {k: round(v[0] / tot, 4) for k, v in kt.items()}
     cpu_rate, cpu_sample, cores = _cpu_sample(w, 10.0, 256)
+    bank = w["bank"]
     line = {
         "metric": METRIC,
-        "value": value,
+        "value": main["value"],
         "unit": UNIT,
         "n_gpus": ws,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": ms_per_step,
+        "ms_per_step": main["ms_per_step"],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": "f32" if form == "plain" else form,
         "data": "synthetic",
         "config": {
             "workload": w["desc"],
             "n_templates": bank.n_templates,
             "n_filters": bank.n_filters,
-            "samples_per_step": n,
-            "form": "plain FP32 recursion",
-            "kernel_variant": info["kernel_variant"],
-            "filters_per_lane": info["filters_per_lane"],
-            "time_tile": info["time_tile"],
+            "n_streams": w["n_streams"],
+            "samples_per_step": int(w["x"].shape[1]),
+            "form": "plain FP32 recursion" if form == "plain" else f"tensor-core block form ({form})",
+            "kernel_variant": main["info"]["kernel_variant"],
+            "filters_per_lane": main["info"]["filters_per_lane"],
+            "time_tile": main["info"]["time_tile"],
             "l2": "flushed between timed steps (256 MB write, untimed)",
             "parallelism": f"{ws} independent bank replicas" if ws > 1 else "1 GPU",
         },
-        "real_time_templates": ws * bank.n_templates * (n / 4096.0) / (ms_per_step / 1e3),
-        "p50_block_latency_ms": float(np.percentile(lat, 50)),
-        "p99_block_latency_ms": float(np.percentile(lat, 99)),
+        "real_time_templates": main["rtt"],
+        "p50_block_latency_ms": main["p50"],
+        "p99_block_latency_ms": main["p99"],
         "kernel_share": shares,
-        "roofline": {
-            "bound": "alu",
-            "kernel": "recur_kernel",
-            "achieved": achieved,
-            "peak": peak_tflops,
-            "unit": "TFLOP/s",
-            "frac": achieved / peak_tflops if peak_tflops else None,
-            "traffic": traffic,
-            "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz "
-                          f"(sm_max_mhz of measured peaks) / {LANE_OPS_PER_FS} lane-ops x "
-                          f"{FLOPS_PER_FS} flops per filter-sample",
-        },
+        "roofline": _roofline(main, w, args, peaks, sms),
         "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": cpu_sample},
-        "e2e": {"value": ws * fs_per_step / e2e_s, "unit": UNIT,
-                "h2d_bytes_per_step": int(n * 4),
-                "d2h_bytes_per_step": int(bank.n_templates * n * 8)},
-        "gpu_launches": launches,
+        "e2e": {"value": main["e2e"], "unit": UNIT, "h2d_bytes_per_step": main["h2d"],
+                "d2h_bytes_per_step": main["d2h"]},
+        "gpu_launches": int(sum(c for _, c in kt.values())),
         "clocks": clocks,
     }
+    if chosen:
+        line["chosen"] = {
+            "form": f"tensor-core block form ({chosen['form']})",
+            "value": chosen["value"], "unit": UNIT, "ms_per_step": chosen["ms_per_step"],
+            "real_time_templates": chosen["rtt"],
+            "p50_block_latency_ms": chosen["p50"], "p99_block_latency_ms": chosen["p99"],
+            "speedup_vs_plain": chosen["value"] / main["value"],
+            "roofline": _roofline(chosen, w, args, peaks, sms),
+            "e2e": {"value": chosen["e2e"], "unit": UNIT},
+            "kernel_ms": {k: v[0] for k, v in chosen["kt"].items()},
+        }
     print(json.dumps(line), flush=True)
-    b.close()
     if dist:
         dist.destroy_process_group()
     return 0
@@ -407,7 +467,11 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="single", choices=["single", "multirate"])
+    ap.add_argument("--workload", default="single", choices=["single", "multirate", "tc"])
+    ap.add_argument("--form", default="", choices=["", "plain", "fp16", "bf16"],
+                    help="compute form of the headline number (default: plain; fp16 for tc)")
+    ap.add_argument("--chosen", default="fp16", choices=["", "plain", "fp16", "bf16"],
+                    help="second form measured on the same workload and reported as 'chosen'")
     ap.add_argument("--tune", type=int, default=0)
     ap.add_argument("--templates", type=int, default=0,
                     help="template count (0 = the workload's full size); small cases for ncu")

@@ -1,29 +1,1219 @@
-// spiir_tc.cu -- block-parallel tensor-core form (not built yet in this file).
+// spiir_tc.cu -- block-parallel tensor-core form of single-rate SPIIR banks.
+//
+// Exact chunked decomposition (chunks of L samples, n0 = c*L, F > max d_k):
+//
+//   z_t[n0+j] = scale * ( sum_{q=0}^{F+L-1} h_t[q] xt[n0+j-q]
+//                        + sum_{k in t} a_k^{j+1} s_k(c) ),        0 <= j < L
+//
+//   h_t[q]  = sum_k 1[q >= d_k] b_k a_k^(q-d_k)   (template impulse response)
+//   xt[m]   = x[m] for m >= n0-F, else 0          (older input is in the state)
+//   v_k[p]  = a_k v_k[p-1] + x[p]                 (undelayed unit filter)
+//   s_k(c)  = a_k^(F-d_k) b_k v_k[n0-F-1]
+//   v_k     <- a_k^L v_k + sum_{i<L} a_k^(L-1-i) x[n0-F+i]   (chunk to chunk)
+//
+// It follows from Eq. (iireq0) solved as Eq. (equ:first-order2): inputs older
+// than n0-F reach every filter after its delay, so their whole effect is the
+// filter state; newer inputs are a finite convolution with h_t.
+//
+// Three tensor-core contractions (tcgen05.mma, operands in shared memory,
+// accumulators in tensor memory) and one FP64 recurrence:
+//   FIR    D[(t,re/im), j] = H[(t,re/im), q] x Toeplitz(xt)[q, j]. The Toeplitz
+//          operand is a shared-memory descriptor over a reversed strain window
+//          stored 8 times with one-sample shifts: every 8x8 core matrix
+//          (n-block g, k-block kb) is block g+kb, so both descriptor strides
+//          are 128 bytes and no Toeplitz matrix is ever built.
+//   STATE  G_k(c, i2) = sum_{i1<128} a_k^i1 x[e_c - 128 i2 - i1]: power panel
+//          R[k][i] = a_k^i (K-major, contraction over powers) times strain
+//          segments; U_k = sum_i2 a_k^(128 i2) G_k(c, i2).
+//   CARRY  (FP64, one thread per filter and stream) s = c_k v, v <- a^L v + U.
+//   OUTPUT D[j1, (c, j2, re/im)] = sum_k R[k][j1] w_k(c, j2) with
+//          w = a_k^(128 j2) a_k s_k(c): the same panel R read MN-major
+//          (contraction over filters); added into z.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "spiir_internal.h"
 #include "spiir_tc.h"
 
-struct TcBank {
-    int unused;
+namespace {
+
+thread_local std::string g_tc_err;
+
+spiir_status tc_fail(spiir_status st, const char *msg) {
+    g_tc_err = msg;
+    return st;
+}
+
+#define TC_CUDA(call)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            g_tc_err = std::string(#call) + ": " + cudaGetErrorString(e_);              \
+            return e_ == cudaErrorMemoryAllocation ? SPIIR_ENOMEM : SPIIR_ECUDA;        \
+        }                                                                               \
+    } while (0)
+
+constexpr int kJ = 128;           // power-panel length (STATE/OUTPUT factorisation)
+constexpr int kTile = 128;        // filters per carry tile (MMA M)
+constexpr int kGroup = 64;        // templates per FIR tile (M = 128 rows re/im)
+constexpr int kKs = 64;           // FIR K slice
+constexpr int kStages = 4;        // FIR A-operand pipeline depth
+constexpr int kSliceBytes = 128 * kKs * 2;   // 16 KB
+
+// ---------------------------------------------------------------------------
+// Device helpers: mbarrier, bulk copy, tcgen05
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t s32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t gtime() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *m, uint32_t c) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s32(m)), "r"(c) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *m, uint32_t ph) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(s32(m)), "r"(ph)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait (~2 s): on timeout record it and report false.
+__device__ __forceinline__ bool mbar_wait(uint64_t *m, uint32_t ph, unsigned int *status) {
+    if (mbar_try(m, ph)) return true;
+    const uint64_t t0 = gtime();
+    while (!mbar_try(m, ph)) {
+        if (gtime() - t0 > 2000000000ull) {
+            atomicExch(status, SPIIR_DEV_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void mbar_expect(uint64_t *m, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s32(m)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *m) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            s32(dst)),
+        "l"(src), "r"(bytes), "r"(s32(m))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Whole warp: allocate ncols tensor-memory columns; address written to *dst.
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s32(dst)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_free(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+
+// Shared-memory matrix descriptor, no swizzle: start, LBO (stride between
+// core matrices along K), SBO (stride between 8-row groups along M/N).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor, kind::f16, FP32 accumulate.
+__host__ __device__ constexpr uint32_t idesc(int M, int N, bool bf16, bool a_mn, bool b_mn) {
+    return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) |
+           ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *m) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     s32(m))
+                 : "memory");
+}
+
+// 32 lanes x 16 consecutive 32-bit columns.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%"
+        "15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <bool BF16>
+__device__ __forceinline__ uint16_t to16(float x) {
+    if constexpr (BF16) {
+        return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+    } else {
+        return __half_as_ushort(__float2half_rn(x));
+    }
+}
+
+template <bool BF16>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    if constexpr (BF16) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<const uint32_t *>(&h);
+    } else {
+        const __half2 h = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<const uint32_t *>(&h);
+    }
+}
+
+template <bool BF16>
+__device__ __forceinline__ uint4 pack8(const float (&v)[8]) {
+    uint4 r;
+    r.x = pack2<BF16>(v[0], v[1]);
+    r.y = pack2<BF16>(v[2], v[3]);
+    r.z = pack2<BF16>(v[4], v[5]);
+    r.w = pack2<BF16>(v[6], v[7]);
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel arguments
+// ---------------------------------------------------------------------------
+
+// Strain operands of one push, staged once in global memory in the exact
+// shared-memory layouts the contractions read (fetched with bulk copies).
+struct TcStageArgs {
+    const float *xbuf;        // [stream][xbuf_stride]: hist then the push
+    int64_t xbuf_stride;
+    int32_t hist, F, L, K, n_chunks, n_streams, stream0;
+    int32_t cpb, n_batches;   // carry: chunks per batch, batches
+    uint4 *hank;              // [s][c][hank_bytes/16]  FIR Toeplitz source
+    int32_t hank_bytes;
+    uint4 *xseg;              // [batch][kXsegBytes/16] STATE strain segments
 };
 
-static const char *kMsg = "tensor-core form not available in this build";
+constexpr int kNii = 32;                       // STATE columns per carry batch
+constexpr int kXsegBytes = kNii * kJ * 2;      // 8 KB
+constexpr int kBatchGroup = 2;                 // batches per power-panel generation
 
-spiir_status spiir_tc_create(const spiir_bank_desc *, float, cudaStream_t, TcBank **out,
-                             int64_t *) {
+struct TcFirArgs {
+    const uint4 *H;           // [group][slice][16 KB] pre-tiled impulse responses
+    const float *row_scale;   // per template: snr_scale * 2^-e_t
+    const uint8_t *has_carry; // per template: z already holds the state term
+    const uint4 *hank;        // staged Toeplitz sources
+    int32_t hank_bytes;
+    int32_t L, K;
+    int32_t n_groups, n_chunks, n_streams, n_templates;
+    int32_t stream0;
+    float2 *z;
+    int64_t z_row_stride, z_stream_stride;
+    unsigned int *status;
+};
+
+struct TcCarryArgs {
+    const int32_t *tile_ptr;  // [t], [t+1]: carry tiles of template t
+    const int32_t *tmpl_of;   // templates that own tiles
+    int32_t n_carry;
+    const float2 *a;          // [slot] a_k
+    const float2 *a64;        // [slot] a_k^64
+    const float2 *aJ;         // [slot] a_k^128
+    const double2 *aL;        // [slot] a_k^L (FP64)
+    const float2 *aLf;        // [slot] a_k^L rounded to FP32
+    const double2 *aLb;       // [slot] a_k^(L * cpb) (FP64), cpb of this launch
+    const float2 *c;          // [slot] a_k^(F-d_k) b_k
+    double2 *v;               // [stream][n_slots] undelayed unit-filter state
+    int64_t n_slots;
+    const uint4 *xseg;        // staged STATE strain segments
+    int32_t L, n_chunks, n_streams, stream0, cpb, n_batches;
+    float scale;
+    float2 *z;
+    int64_t z_row_stride, z_stream_stride;
+    unsigned int *status;
+};
+
+// ---------------------------------------------------------------------------
+// Staging kernel: one thread per 16-byte chunk of either operand
+// ---------------------------------------------------------------------------
+
+template <bool BF16>
+__global__ void tc_stage_kernel(const TcStageArgs a) {
+    const int64_t hank_chunks = (int64_t)a.n_streams * a.n_chunks * (a.hank_bytes / 16);
+    const int64_t xseg_chunks = (int64_t)a.n_batches * (kXsegBytes / 16);
+    const int LJ = a.L / kJ;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < hank_chunks + xseg_chunks;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float v[8];
+        if (i < hank_chunks) {
+            // Toeplitz source of chunk c: xr[p] = xt[n0 + L - 1 - p]; 16-byte
+            // chunk (blk, r) holds xr[8 blk + r + 0..7]
+            const int per = a.hank_bytes / 16;
+            const int sc = (int)(i / per), w = (int)(i % per);
+            const int ss = sc / a.n_chunks, c = sc % a.n_chunks;
+            const int blk = w >> 3, r = w & 7;
+            const float *x = a.xbuf + (int64_t)(a.stream0 + ss) * a.xbuf_stride + a.hist;
+            const int n0 = c * a.L;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int p = 8 * blk + r + q;
+                const int m = n0 + a.L - 1 - p;
+                v[q] = (p < a.L + a.K - 1 && m >= n0 - a.F) ? x[m] : 0.f;
+            }
+            a.hank[i] = pack8<BF16>(v);
+        } else {
+            // STATE segments of batch b: row n = (s, c, i2), K = i1:
+            // x_s[e_c - 128 i2 - i1], e_c = c L - F + L - 1; layout
+            // [n/8][i1/8][n%8][i1%8]
+            const int64_t j = i - hank_chunks;
+            const int b = (int)(j / (kXsegBytes / 16)), w = (int)(j % (kXsegBytes / 16));
+            const int n = (w / 128) * 8 + (w % 8), kb = (w / 8) % 16;
+            const int nb = min(a.cpb, a.n_chunks - b * a.cpb);
+            const int nii = a.n_streams * nb * LJ;
+            if (n < nii) {
+                const int ss = n / (nb * LJ), rem = n % (nb * LJ), cc = rem / LJ, i2 = rem % LJ;
+                const float *x = a.xbuf + (int64_t)(a.stream0 + ss) * a.xbuf_stride + a.hist;
+                const int e = (b * a.cpb + cc) * a.L - a.F + a.L - 1 - kJ * i2;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[q] = x[e - (8 * kb + q)];
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[q] = 0.f;
+            }
+            a.xseg[j] = pack8<BF16>(v);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FIR kernel: persistent, warp-specialised
+//   warp 0 lane 0: bulk-copy producer (impulse-response slices, Toeplitz source)
+//   warp 1 lane 0: MMA issuer into two tensor-memory accumulators
+//   warps 2-5    : epilogue (tensor memory -> z), overlapping the next MMAs
+// Items (template group, stream, chunk), chunk fastest so that CTAs working at
+// the same time share impulse-response tiles in L2.
+// ---------------------------------------------------------------------------
+
+template <bool BF16>
+__global__ void __launch_bounds__(192, 1) tc_fir_kernel(const TcFirArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint64_t a_full[kStages], a_empty[kStages], h_full[2], h_empty[2], acc_full[2],
+        acc_empty[2];
+    __shared__ uint32_t s_tmem;
+    const int L = a.L, K = a.K;
+    const int n_slices = K / kKs;
+    const int n_items = a.n_groups * a.n_streams * a.n_chunks;
+    unsigned char *stage_mem = smem;                                   // kStages x 16 KB
+    unsigned char *hank = smem + kStages * kSliceBytes;                // 2 x hank_bytes
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(&a_full[i], 1);
+            mbar_init(&a_empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&h_full[i], 1);
+            mbar_init(&h_empty[i], 1);
+            mbar_init(&acc_full[i], 1);
+            mbar_init(&acc_empty[i], 128);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(&s_tmem, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    if (warp == 0 && lane == 0) {
+        // producer
+        int64_t gc = 0;     // global slice counter (A ring)
+        int li = 0;
+        bool ok = true;
+        for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++li) {
+            const int c = it % a.n_chunks, sg = it / a.n_chunks;
+            const int ss = sg % a.n_streams, g = sg / a.n_streams;
+            const int hb = li & 1;
+            if (li >= 2) {
+                ok = mbar_wait(&h_empty[hb], ((li >> 1) - 1) & 1, a.status);
+                if (!ok) break;
+            }
+            mbar_expect(&h_full[hb], a.hank_bytes);
+            bulk_load(hank + (size_t)hb * a.hank_bytes,
+                      a.hank + ((size_t)ss * a.n_chunks + c) * (a.hank_bytes / 16), a.hank_bytes,
+                      &h_full[hb]);
+            const uint4 *A = a.H + (size_t)g * n_slices * (kSliceBytes / 16);
+            for (int ks = 0; ks < n_slices; ++ks, ++gc) {
+                const int st = (int)(gc % kStages);
+                const int64_t use = gc / kStages;
+                if (use >= 1) {
+                    ok = mbar_wait(&a_empty[st], (uint32_t)((use - 1) & 1), a.status);
+                    if (!ok) break;
+                }
+                mbar_expect(&a_full[st], kSliceBytes);
+                bulk_load(stage_mem + st * kSliceBytes, A + (size_t)ks * (kSliceBytes / 16),
+                          kSliceBytes, &a_full[st]);
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        const uint32_t id = idesc(128, L, BF16, false, false);
+        int64_t gc = 0;
+        int li = 0;
+        bool ok = true;
+        for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++li) {
+            const int ab = li & 1, hb = li & 1;
+            if (li >= 2) {
+                ok = mbar_wait(&acc_empty[ab], ((li >> 1) - 1) & 1, a.status);
+                if (!ok) break;
+            }
+            ok = mbar_wait(&h_full[hb], (li >> 1) & 1, a.status);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t d = tmem + ab * 256;
+            const uint32_t bbase = s32(hank + (size_t)hb * a.hank_bytes);
+            for (int ks = 0; ks < n_slices; ++ks, ++gc) {
+                const int st = (int)(gc % kStages);
+                ok = mbar_wait(&a_full[st], (uint32_t)((gc / kStages) & 1), a.status);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t abase = s32(stage_mem + st * kSliceBytes);
+#pragma unroll
+                for (int kk = 0; kk < kKs / 16; ++kk) {
+                    const uint64_t ad = sdesc(abase + kk * 256, 128, 1024);
+                    const uint64_t bd = sdesc(bbase + (ks * (kKs / 8) + 2 * kk) * 128, 128, 128);
+                    mma(d, ad, bd, id, (ks | kk) ? 1u : 0u);
+                }
+                mma_commit(&a_empty[st]);
+            }
+            mma_commit(&h_empty[hb]);
+            mma_commit(&acc_full[ab]);
+        }
+    } else if (warp >= 2) {
+        // epilogue: lane row r = template 64g + r/2, re (even) / im (odd);
+        // column n' is time n = L - 1 - n'
+        const int q = warp & 3;
+        const int r = q * 32 + lane;
+        int li = 0;
+        bool ok = true;
+        for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++li) {
+            const int c = it % a.n_chunks, sg = it / a.n_chunks;
+            const int ss = sg % a.n_streams, g = sg / a.n_streams;
+            const int ab = li & 1;
+            ok = ok && mbar_wait(&acc_full[ab], (li >> 1) & 1, a.status);
+            tc_fence_after();
+            const int t = g * kGroup + (r >> 1);
+            const float sc = (t < a.n_templates) ? a.row_scale[t] : 0.f;
+            float2 *zrow = a.z + (int64_t)(a.stream0 + ss) * a.z_stream_stride +
+                           (int64_t)min(t, a.n_templates - 1) * a.z_row_stride + (int64_t)c * L;
+            const bool is_re = (r & 1) == 0;
+            const bool add = (t < a.n_templates) && a.has_carry[t];
+            const int i0 = is_re ? 0 : 8;
+            for (int cc = 0; cc < L / 16; ++cc) {
+                // state term written by the carry kernel: fetch before the
+                // tensor-memory load so the global latency overlaps it
+                float2 prev[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    prev[i] = add ? zrow[L - 1 - (cc * 16 + i0 + i)] : make_float2(0.f, 0.f);
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + ab * 256 + cc * 16, v);
+                float o[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) o[i] = __shfl_xor_sync(0xffffffffu, v[i], 1);
+                if (ok && t < a.n_templates) {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int col = cc * 16 + i0 + i;
+                        const float re = is_re ? v[i0 + i] : o[i0 + i];
+                        const float im = is_re ? o[i0 + i] : v[i0 + i];
+                        zrow[L - 1 - col] = make_float2(fmaf(sc, re, prev[i].x), fmaf(sc, im, prev[i].y));
+                    }
+                }
+            }
+            tc_fence_before();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s32(&acc_empty[ab])) : "memory");
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_free(tmem, 512);
+}
+
+// ---------------------------------------------------------------------------
+// Carry kernel: persistent over templates, two CTAs per SM so that one CTA's
+// FP64 recurrence overlaps the other's panel generation and contractions.
+// Per template and group of up to kBatchGroup chunk batches:
+//   for each 128-filter tile: generate R = a_k^i once, then per batch
+//     STATE MMA -> FP64 carry (thread = filter, stream) -> OUTPUT MMA
+//   epilogue: z += scale * OUTPUT, per batch.
+// ---------------------------------------------------------------------------
+
+constexpr int kCarrySmem = 65536 + kBatchGroup * kXsegBytes + 2 * (2 * kNii) * kJ * 2;
+
+template <bool BF16>
+__global__ void __launch_bounds__(256, 2) tc_carry_kernel(const TcCarryArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint64_t mb, xb;
+    __shared__ uint32_t s_tmem;
+    const int L = a.L, LJ = L / kJ;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *Pr = smem;
+    unsigned char *Pi = smem + 32768;
+    unsigned char *Xs = smem + 65536;                              // kBatchGroup x 8 KB
+    unsigned char *W1 = Xs + kBatchGroup * kXsegBytes;            // 64 rows x 128 K
+    unsigned char *W2 = W1 + (2 * kNii) * kJ * 2;
+    constexpr uint32_t kWSbo = 16 * 128;                          // 8 rows x 16 k-blocks
+
+    if (threadIdx.x == 0) {
+        mbar_init(&mb, 1);
+        mbar_init(&xb, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(&s_tmem, 256);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;          // STATE re [0,32) im [32,64); OUTPUT [64 + 64 b, ...)
+    uint32_t ph = 0, phx = 0;
+    int loaded_b0 = -1;
+    bool ok = true;
+    const int S = a.n_streams;
+
+    for (int ti = blockIdx.x; ti < a.n_carry && ok; ti += gridDim.x) {
+        const int t = a.tmpl_of[ti];
+        const int tile0 = a.tile_ptr[t], tile1 = a.tile_ptr[t + 1];
+        for (int b0 = 0; b0 < a.n_batches && ok; b0 += kBatchGroup) {
+            const int nbg = min(kBatchGroup, a.n_batches - b0);
+            // the strain segments do not depend on the template: load them
+            // again only when this CTA moves to another group of batches
+            const bool reload = (b0 != loaded_b0);
+            if (reload && threadIdx.x == 0) {
+                mbar_expect(&xb, nbg * kXsegBytes);
+                bulk_load(Xs, a.xseg + (size_t)b0 * (kXsegBytes / 16), nbg * kXsegBytes, &xb);
+            }
+            for (int tile = tile0; tile < tile1 && ok; ++tile) {
+                // power panel R[k][i] = a_k^i: rows = filters, K = powers,
+                // layout [k/8][i/8][k%8][i%8]; thread = (filter, half of the
+                // powers) running four independent chains of 16 powers
+                {
+                    const int k = threadIdx.x & 127, h = threadIdx.x >> 7;
+                    const int64_t slot = (int64_t)tile * kTile + k;
+                    const float2 ak = a.a[slot];
+                    float2 a16 = ak;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        a16 = make_float2(a16.x * a16.x - a16.y * a16.y, 2.f * a16.x * a16.y);
+                    float2 p[4];
+                    p[0] = h ? a.a64[slot] : make_float2(1.f, 0.f);
+#pragma unroll
+                    for (int i = 1; i < 4; ++i)
+                        p[i] = make_float2(p[i - 1].x * a16.x - p[i - 1].y * a16.y,
+                                           p[i - 1].x * a16.y + p[i - 1].y * a16.x);
+                    for (int ib = 0; ib < 2; ++ib) {
+                        float vr[4][8], vi[4][8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+#pragma unroll
+                            for (int ch = 0; ch < 4; ++ch) {
+                                vr[ch][q] = p[ch].x;
+                                vi[ch][q] = p[ch].y;
+                                p[ch] = make_float2(p[ch].x * ak.x - p[ch].y * ak.y,
+                                                    p[ch].x * ak.y + p[ch].y * ak.x);
+                            }
+                        }
+#pragma unroll
+                        for (int ch = 0; ch < 4; ++ch) {
+                            const int kb = h * 8 + ch * 2 + ib;
+                            const size_t off = (size_t)(k >> 3) * 2048 + kb * 128 + (k & 7) * 16;
+                            *reinterpret_cast<uint4 *>(Pr + off) = pack8<BF16>(vr[ch]);
+                            *reinterpret_cast<uint4 *>(Pi + off) = pack8<BF16>(vi[ch]);
+                        }
+                    }
+                }
+                fence_async_smem();
+                tc_fence_before();
+                __syncthreads();
+                tc_fence_after();
+                if (tile == tile0 && reload) {
+                    ok = mbar_wait(&xb, phx, a.status);
+                    phx ^= 1u;
+                    loaded_b0 = b0;
+                }
+                // carry thread state: filter k (tensor-memory lane), stream ss
+                const int k = threadIdx.x & 127, ss = threadIdx.x >> 7;
+                const int64_t slot = (int64_t)tile * kTile + k;
+                const bool act = ss < S;
+                const float2 ak = a.a[slot], aJ = a.aJ[slot], ck = a.c[slot], aLf = a.aLf[slot];
+                double2 v = act ? a.v[(int64_t)(a.stream0 + ss) * a.n_slots + slot] : make_double2(0, 0);
+                const uint32_t lane_base = ((uint32_t)((warp & 3) * 32)) << 16;
+                for (int bi = 0; bi < nbg && ok; ++bi) {
+                    const int b = b0 + bi;
+                    const int nb = min(a.cpb, a.n_chunks - b * a.cpb);
+                    const int nii = S * nb * LJ;
+                    const int niv = 2 * nii;
+                    // STATE: tmem cols [0, 32) re, [32, 64) im
+                    if (threadIdx.x == 0) {
+                        const uint32_t id = idesc(128, kNii, BF16, false, false);
+                        const uint32_t xs = s32(Xs + bi * kXsegBytes);
+                        for (int kk = 0; kk < kJ / 16; ++kk) {
+                            const uint64_t bd = sdesc(xs + kk * 256, 128, 2048);
+                            mma(tmem, sdesc(s32(Pr) + kk * 256, 128, 2048), bd, id, kk ? 1u : 0u);
+                            mma(tmem + kNii, sdesc(s32(Pi) + kk * 256, 128, 2048), bd, id, kk ? 1u : 0u);
+                        }
+                        mma_commit(&mb);
+                    }
+                    __syncwarp();
+                    ok = mbar_wait(&mb, ph, a.status);
+                    ph ^= 1u;
+                    tc_fence_after();
+                    // Carry across this batch. The batch's starting state v is
+                    // FP64; chunk states inside the batch are FP32:
+                    //   v_c = a^(cL) v + d_c,  d_{c+1} = a^L d_c + U_c,  d_0 = 0,
+                    // and the next batch starts from a^(nb L) v + d_nb in FP64.
+                    float pr = (float)v.x, pi = (float)v.y;     // a^(cL) v
+                    float dr = 0.f, di = 0.f;                    // d_c
+                    for (int c0 = 0; c0 < nb * LJ; c0 += 16) {
+                        float gr[16], gi[16];
+                        const int colb = (act ? ss : 0) * nb * LJ + c0;
+                        tmem_ld16(tmem + lane_base + colb, gr);
+                        tmem_ld16(tmem + lane_base + kNii + colb, gi);
+                        if (act) {
+                            for (int q = 0; q < 16 && c0 + q < nb * LJ; q += LJ) {
+                                float ur = gr[q + LJ - 1], ui = gi[q + LJ - 1];
+                                for (int i2 = LJ - 2; i2 >= 0; --i2) {
+                                    const float nr = ur * aJ.x - ui * aJ.y + gr[q + i2];
+                                    const float ni = ur * aJ.y + ui * aJ.x + gi[q + i2];
+                                    ur = nr;
+                                    ui = ni;
+                                }
+                                const int cc = (c0 + q) / LJ;
+                                const float vr = pr + dr, vi = pi + di;
+                                const float sr = ck.x * vr - ck.y * vi, si = ck.x * vi + ck.y * vr;
+                                float wr = ak.x * sr - ak.y * si, wi = ak.x * si + ak.y * sr;
+                                const float ndr = aLf.x * dr - aLf.y * di + ur;
+                                const float ndi = aLf.x * di + aLf.y * dr + ui;
+                                dr = ndr;
+                                di = ndi;
+                                const float npr = aLf.x * pr - aLf.y * pi;
+                                const float npi = aLf.x * pi + aLf.y * pr;
+                                pr = npr;
+                                pi = npi;
+                                for (int j2 = 0; j2 < LJ; ++j2) {
+                                    const int n = ((ss * nb + cc) * LJ + j2) * 2;
+                                    const size_t o0 = (size_t)(n >> 3) * kWSbo + (k >> 3) * 128 +
+                                                      (n & 7) * 16 + (k & 7) * 2;
+                                    const size_t o1 = (size_t)((n + 1) >> 3) * kWSbo + (k >> 3) * 128 +
+                                                      ((n + 1) & 7) * 16 + (k & 7) * 2;
+                                    *reinterpret_cast<uint16_t *>(W1 + o0) = to16<BF16>(wr);
+                                    *reinterpret_cast<uint16_t *>(W1 + o1) = to16<BF16>(wi);
+                                    *reinterpret_cast<uint16_t *>(W2 + o0) = to16<BF16>(-wi);
+                                    *reinterpret_cast<uint16_t *>(W2 + o1) = to16<BF16>(wr);
+                                    const float nr = wr * aJ.x - wi * aJ.y, ni = wr * aJ.y + wi * aJ.x;
+                                    wr = nr;
+                                    wi = ni;
+                                }
+                            }
+                        }
+                    }
+                    if (act) {
+                        // v <- a^(nb L) v + d_nb in FP64
+                        double2 pw;
+                        if (nb == a.cpb) {
+                            pw = a.aLb[slot];
+                        } else {
+                            const double2 aL = a.aL[slot];
+                            pw = aL;
+                            for (int i = 1; i < nb; ++i)
+                                pw = make_double2(pw.x * aL.x - pw.y * aL.y, pw.x * aL.y + pw.y * aL.x);
+                        }
+                        const double nvr = fma(pw.x, v.x, fma(-pw.y, v.y, (double)dr));
+                        const double nvi = fma(pw.x, v.y, fma(pw.y, v.x, (double)di));
+                        v = make_double2(nvr, nvi);
+                    }
+                    for (int n = niv + (threadIdx.x >> 7); n < 2 * kNii; n += 2) {
+                        const size_t o = (size_t)(n >> 3) * kWSbo + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
+                        *reinterpret_cast<uint16_t *>(W1 + o) = 0;
+                        *reinterpret_cast<uint16_t *>(W2 + o) = 0;
+                    }
+                    fence_async_smem();
+                    tc_fence_before();
+                    __syncthreads();
+                    tc_fence_after();
+                    // OUTPUT: D[j1][n] (+)= R^T(re) W1 + R^T(im) W2 into cols [64 + 64 bi, ...)
+                    if (threadIdx.x == 0) {
+                        const uint32_t id = idesc(128, 2 * kNii, BF16, true, false);
+                        const uint32_t dz = tmem + 64 + 64 * bi;
+                        for (int kk = 0; kk < kTile / 16; ++kk) {
+                            const uint32_t acc = (tile != tile0 || kk) ? 1u : 0u;
+                            const uint64_t ar = sdesc(s32(Pr) + kk * 2 * 2048, 2048, 128);
+                            const uint64_t ai = sdesc(s32(Pi) + kk * 2 * 2048, 2048, 128);
+                            mma(dz, ar, sdesc(s32(W1) + kk * 2 * 128, 128, kWSbo), id, acc);
+                            mma(dz, ai, sdesc(s32(W2) + kk * 2 * 128, 128, kWSbo), id, 1u);
+                        }
+                        mma_commit(&mb);
+                    }
+                    __syncwarp();
+                    ok = ok && mbar_wait(&mb, ph, a.status);
+                    ph ^= 1u;
+                    tc_fence_after();
+                }
+                if (act) a.v[(int64_t)(a.stream0 + ss) * a.n_slots + slot] = v;
+            }
+            // epilogue: lane j1, columns (s, c, j2, re/im) -> z = scale * value
+            // (the FIR kernel adds its term afterwards)
+            if (tile1 > tile0) {
+                const int j1 = threadIdx.x & 127, half = threadIdx.x >> 7;
+                const uint32_t lane_base = ((uint32_t)((warp & 3) * 32)) << 16;
+                for (int bi = 0; bi < nbg; ++bi) {
+                    const int b = b0 + bi;
+                    const int nb = min(a.cpb, a.n_chunks - b * a.cpb);
+                    const int niv = 2 * S * nb * LJ;
+                    for (int c0 = half * 16; c0 < 2 * kNii; c0 += 32) {
+                        float vv[16];
+                        tmem_ld16(tmem + lane_base + 64 + 64 * bi + c0, vv);
+                        if (ok) {
+#pragma unroll
+                            for (int q = 0; q < 16; q += 2) {
+                                const int n = c0 + q;
+                                if (n >= niv) break;
+                                const int rest = n >> 1;
+                                const int s2 = rest / (nb * LJ), rem = rest % (nb * LJ);
+                                const int cc = rem / LJ, j2 = rem % LJ;
+                                float2 *zp = a.z + (int64_t)(a.stream0 + s2) * a.z_stream_stride +
+                                             (int64_t)t * a.z_row_stride +
+                                             (int64_t)(b * a.cpb + cc) * L + kJ * j2 + j1;
+                                *zp = make_float2(a.scale * vv[q], a.scale * vv[q + 1]);
+                            }
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_free(tmem, 256);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+struct TcBank {
+    int T = 0, S = 0, L = 256, F = 0, K = 0, n_groups = 0, n_slices = 0;
+    int n_carry_ctas = 0, n_tiles = 0;
+    int64_t n_slots = 0;
+    int64_t max_n = 0, ring_len = 0, xbuf_stride = 0;
+    bool bf16 = false;
+    float scale = 0.f;
+    int max_delay = 0;
+    // device
+    uint4 *H = nullptr;
+    float *row_scale = nullptr;
+    int32_t *tile_ptr = nullptr, *tmpl_of = nullptr;
+    uint8_t *has_carry = nullptr;
+    float2 *a = nullptr, *a64 = nullptr, *aJ = nullptr, *c = nullptr, *aLf = nullptr;
+    double2 *aL = nullptr, *v = nullptr, *aLb1 = nullptr, *aLb2 = nullptr;
+    float *xbuf = nullptr, *stage = nullptr;
+    float2 *z = nullptr;
+    unsigned int *status = nullptr;
+    uint4 *hank = nullptr, *xseg = nullptr;   // staged strain operands
+    int hank_bytes = 0;
+    int n_sms = 1;
+    std::vector<int64_t> last_n;
+    int64_t footprint = 0;
+};
+
+namespace {
+
+constexpr int kFirSmem = kStages * kSliceBytes;
+int hank_bytes_of(int L, int K) { return (L + K) / 8 * 128; }
+int fir_smem_of(int L, int K) { return kFirSmem + 2 * hank_bytes_of(L, K); }
+int carry_cpb(int streams, int L) { return std::max(1, kNii / (streams * (L / kJ))); }
+
+struct TcPlan {
+    int T, L, F, K, n_groups, n_slices, n_tiles;
+    int64_t n_slots, max_n, ring_len, xbuf_stride;
+    int max_delay;
+};
+
+spiir_status tc_plan(const spiir_bank_desc *d, TcPlan &p) {
+    p.L = d->chunk_len ? d->chunk_len : 256;
+    if (p.L != 128 && p.L != 256)
+        return tc_fail(SPIIR_EUNSUPPORTED, "tensor-core form: chunk_len must be 128 or 256");
+    if (d->block_len % p.L != 0)
+        return tc_fail(SPIIR_EINVAL, "tensor-core form: block_len must be a multiple of chunk_len");
+    p.T = d->n_templates;
+    int md = 0;
+    std::vector<int64_t> cnt(p.T, 0);
+    for (int64_t k = 0; k < d->n_filters; ++k) {
+        md = std::max(md, d->delay[k]);
+        cnt[d->template_id[k]]++;
+    }
+    p.max_delay = md;
+    p.F = (int)(((int64_t)md + 1 + 63) / 64 * 64);
+    p.K = p.F + p.L;
+    if (fir_smem_of(p.L, p.K) > 220 * 1024)
+        return tc_fail(SPIIR_EUNSUPPORTED, "tensor-core form: delays too long for the FIR tile");
+    p.n_groups = (p.T + kGroup - 1) / kGroup;
+    p.n_slices = p.K / kKs;
+    p.n_tiles = 0;
+    for (int t = 0; t < p.T; ++t) p.n_tiles += (int)((cnt[t] + kTile - 1) / kTile);
+    p.n_slots = (int64_t)p.n_tiles * kTile;
+    p.max_n = (int64_t)d->block_len * d->max_push_blocks;
+    p.ring_len = (p.max_n + 1) / 2 * 2;
+    p.xbuf_stride = (p.F + p.max_n + 64 + 3) / 4 * 4;
+    return SPIIR_OK;
+}
+
+int64_t tc_bytes(const spiir_bank_desc *d, const TcPlan &p) {
+    const int64_t S = d->n_streams;
+    int64_t b = 0;
+    b += (int64_t)p.n_groups * p.n_slices * kSliceBytes;
+    b += (int64_t)p.T * 4 + (p.T + 1) * 4 + p.T * 4;
+    b += p.n_slots * (8 * 5 + 16 * 3);
+    b += S * p.n_slots * 16;
+    b += S * p.xbuf_stride * 4 + S * p.ring_len * 4;
+    b += S * (int64_t)p.T * p.ring_len * 8;
+    const int64_t C = p.max_n / p.L;
+    b += S * C * hank_bytes_of(p.L, p.K);
+    b += (C * S * (p.L / kJ) / kNii + 2) * kXsegBytes;
+    return b + 256;
+}
+
+uint16_t host16(float x, bool bf16) {
+    if (bf16) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+    return __half_as_ushort(__float2half_rn(x));
+}
+
+template <typename T>
+spiir_status tc_upload(T **dst, const std::vector<T> &src, cudaStream_t s) {
+    *dst = nullptr;
+    if (src.empty()) return SPIIR_OK;
+    TC_CUDA(cudaMalloc((void **)dst, src.size() * sizeof(T)));
+    TC_CUDA(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return SPIIR_OK;
+}
+
+}  // namespace
+
+spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t s, TcBank **out,
+                             int64_t *footprint) {
     *out = nullptr;
-    return SPIIR_EUNSUPPORTED;
+    TcPlan p;
+    spiir_status st = tc_plan(d, p);
+    if (st) return st;
+    const int64_t bytes = tc_bytes(d, p);
+    if (d->hbm_budget_bytes > 0 && bytes > d->hbm_budget_bytes)
+        return tc_fail(SPIIR_EBUDGET, "tensor-core bank above hbm_budget_bytes");
+    TcBank *b = new TcBank();
+    b->T = p.T;
+    b->S = d->n_streams;
+    b->L = p.L;
+    b->F = p.F;
+    b->K = p.K;
+    b->n_groups = p.n_groups;
+    b->n_slices = p.n_slices;
+    b->n_tiles = p.n_tiles;
+    b->n_slots = p.n_slots;
+    b->max_n = p.max_n;
+    b->ring_len = p.ring_len;
+    b->xbuf_stride = p.xbuf_stride;
+    b->bf16 = d->mode != SPIIR_TC_FP16;
+    b->scale = scale;
+    b->max_delay = p.max_delay;
+    b->last_n.assign(d->n_streams, 0);
+    b->footprint = bytes;
+    *footprint = bytes;
+    *out = b;
+
+    // filters per template in input order
+    std::vector<std::vector<int64_t>> fl(p.T);
+    for (int64_t k = 0; k < d->n_filters; ++k) fl[d->template_id[k]].push_back(k);
+
+    // Impulse responses h_t[q], q < K, in FP64; rows scaled by 2^e_t into the
+    // 16-bit range; tiles [group][slice][r/8][k/8][r%8][k%8].
+    const int K = p.K;
+    std::vector<uint16_t> Hh((size_t)p.n_groups * p.n_slices * (kSliceBytes / 2), 0);
+    std::vector<float> row_scale(p.T, 0.f);
+    auto work = [&](int t0, int t1) {
+        std::vector<std::complex<double>> h(K);
+        for (int t = t0; t < t1; ++t) {
+            std::fill(h.begin(), h.end(), std::complex<double>(0, 0));
+            for (int64_t k : fl[t]) {
+                const std::complex<double> a(d->a_re[k], d->a_im[k]);
+                std::complex<double> pw(d->b_re[k], d->b_im[k]);
+                for (int q = d->delay[k]; q < K; ++q) {
+                    h[q] += pw;
+                    pw *= a;
+                }
+            }
+            double mx = 0.0;
+            for (int q = 0; q < K; ++q) mx = std::max(mx, std::max(std::fabs(h[q].real()), std::fabs(h[q].imag())));
+            int e = 0;
+            if (mx > 0.0) {
+                int ex;
+                std::frexp(mx, &ex);          // mx in [2^(ex-1), 2^ex)
+                e = 10 - ex;                  // max |h| * 2^e in [2^9, 2^10)
+            }
+            const double sc = std::ldexp(1.0, e);
+            row_scale[t] = (float)(scale * std::ldexp(1.0, -e));
+            const int g = t / kGroup;
+            for (int comp = 0; comp < 2; ++comp) {
+                const int r = 2 * (t % kGroup) + comp;
+                for (int q = 0; q < K; ++q) {
+                    const double val = (comp ? h[q].imag() : h[q].real()) * sc;
+                    const int sl = q / kKs, kq = q % kKs;
+                    const size_t off = ((size_t)g * p.n_slices + sl) * (kSliceBytes / 2) +
+                                       (size_t)(r >> 3) * 512 + (kq >> 3) * 64 + (r & 7) * 8 + (kq & 7);
+                    Hh[off] = host16((float)val, b->bf16);
+                }
+            }
+        }
+    };
+    {
+        const int nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        std::vector<std::thread> th;
+        for (int i = 0; i < nth; ++i) {
+            const int t0 = (int)((int64_t)p.T * i / nth), t1 = (int)((int64_t)p.T * (i + 1) / nth);
+            th.emplace_back(work, t0, t1);
+        }
+        for (auto &x : th) x.join();
+    }
+
+    // Carry tiles: 128 filter slots each, template-major.
+    std::vector<int32_t> tile_ptr(p.T + 1, 0), tmpl_of;
+    std::vector<float2> av(p.n_slots), a64v(p.n_slots), aJv(p.n_slots), cv(p.n_slots);
+    std::vector<double2> aLv(p.n_slots), aLb1v(p.n_slots), aLb2v(p.n_slots);
+    std::vector<float2> aLfv(p.n_slots);
+    const int cpb1 = carry_cpb(1, p.L), cpb2 = carry_cpb(2, p.L);
+    int tile = 0;
+    for (int t = 0; t < p.T; ++t) {
+        tile_ptr[t] = tile;
+        const int nt = (int)((fl[t].size() + kTile - 1) / kTile);
+        if (nt) tmpl_of.push_back(t);
+        for (int i = 0; i < nt * kTile; ++i) {
+            const int64_t slot = (int64_t)tile * kTile + i;
+            if (i < (int)fl[t].size()) {
+                const int64_t k = fl[t][i];
+                const std::complex<double> a(d->a_re[k], d->a_im[k]), bb(d->b_re[k], d->b_im[k]);
+                auto pw = [&](int n) {
+                    std::complex<double> r(1, 0), x = a;
+                    while (n) {
+                        if (n & 1) r *= x;
+                        x *= x;
+                        n >>= 1;
+                    }
+                    return r;
+                };
+                const std::complex<double> aL = pw(p.L), ck = pw(p.F - d->delay[k]) * bb;
+                av[slot] = make_float2(d->a_re[k], d->a_im[k]);
+                const auto p64 = pw(64), pJ = pw(kJ);
+                a64v[slot] = make_float2((float)p64.real(), (float)p64.imag());
+                aJv[slot] = make_float2((float)pJ.real(), (float)pJ.imag());
+                aLv[slot] = make_double2(aL.real(), aL.imag());
+                aLfv[slot] = make_float2((float)aL.real(), (float)aL.imag());
+                const auto b1 = pw(p.L * cpb1), b2 = pw(p.L * cpb2);
+                aLb1v[slot] = make_double2(b1.real(), b1.imag());
+                aLb2v[slot] = make_double2(b2.real(), b2.imag());
+                cv[slot] = make_float2((float)ck.real(), (float)ck.imag());
+            } else {
+                av[slot] = a64v[slot] = aJv[slot] = cv[slot] = aLfv[slot] = make_float2(0.f, 0.f);
+                aLv[slot] = aLb1v[slot] = aLb2v[slot] = make_double2(0.0, 0.0);
+            }
+        }
+        tile += nt;
+    }
+    tile_ptr[p.T] = tile;
+    b->n_carry_ctas = (int)tmpl_of.size();
+    std::vector<uint8_t> has_carry(p.T, 0);
+    for (int t : tmpl_of) has_carry[t] = 1;
+
+    if ((st = tc_upload(&b->H, std::vector<uint4>((uint4 *)Hh.data(), (uint4 *)(Hh.data() + Hh.size())), s)))
+        return st;
+    if ((st = tc_upload(&b->row_scale, row_scale, s))) return st;
+    if ((st = tc_upload(&b->tile_ptr, tile_ptr, s))) return st;
+    if ((st = tc_upload(&b->tmpl_of, tmpl_of, s))) return st;
+    if ((st = tc_upload(&b->has_carry, has_carry, s))) return st;
+    if ((st = tc_upload(&b->a, av, s))) return st;
+    if ((st = tc_upload(&b->a64, a64v, s))) return st;
+    if ((st = tc_upload(&b->aJ, aJv, s))) return st;
+    if ((st = tc_upload(&b->c, cv, s))) return st;
+    if ((st = tc_upload(&b->aL, aLv, s))) return st;
+    if ((st = tc_upload(&b->aLf, aLfv, s))) return st;
+    if ((st = tc_upload(&b->aLb1, aLb1v, s))) return st;
+    if ((st = tc_upload(&b->aLb2, aLb2v, s))) return st;
+    const int64_t S = d->n_streams;
+    TC_CUDA(cudaMalloc((void **)&b->v, std::max<int64_t>(1, S * p.n_slots) * sizeof(double2)));
+    TC_CUDA(cudaMemsetAsync(b->v, 0, std::max<int64_t>(1, S * p.n_slots) * sizeof(double2), s));
+    TC_CUDA(cudaMalloc((void **)&b->xbuf, S * p.xbuf_stride * sizeof(float)));
+    TC_CUDA(cudaMemsetAsync(b->xbuf, 0, S * p.xbuf_stride * sizeof(float), s));
+    TC_CUDA(cudaMalloc((void **)&b->stage, S * p.ring_len * sizeof(float)));
+    TC_CUDA(cudaMalloc((void **)&b->z, S * (int64_t)p.T * p.ring_len * sizeof(float2)));
+    TC_CUDA(cudaMemsetAsync(b->z, 0, S * (int64_t)p.T * p.ring_len * sizeof(float2), s));
+    TC_CUDA(cudaMalloc((void **)&b->status, sizeof(unsigned int)));
+    TC_CUDA(cudaMemsetAsync(b->status, 0, sizeof(unsigned int), s));
+    b->hank_bytes = hank_bytes_of(p.L, p.K);
+    const int64_t Cmax = p.max_n / p.L;
+    TC_CUDA(cudaMalloc((void **)&b->hank, S * Cmax * b->hank_bytes));
+    const int64_t nbmax = (Cmax + carry_cpb(std::min<int64_t>(S, 2), p.L) - 1) / carry_cpb(std::min<int64_t>(S, 2), p.L) + 1;
+    TC_CUDA(cudaMalloc((void **)&b->xseg, std::max<int64_t>(nbmax, Cmax) * kXsegBytes));
+    int dev = 0;
+    TC_CUDA(cudaGetDevice(&dev));
+    TC_CUDA(cudaDeviceGetAttribute(&b->n_sms, cudaDevAttrMultiProcessorCount, dev));
+    const int fir_smem = fir_smem_of(p.L, p.K);
+    if (b->bf16) {
+        TC_CUDA(cudaFuncSetAttribute(tc_fir_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fir_smem));
+        TC_CUDA(cudaFuncSetAttribute(tc_carry_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCarrySmem));
+    } else {
+        TC_CUDA(cudaFuncSetAttribute(tc_fir_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fir_smem));
+        TC_CUDA(cudaFuncSetAttribute(tc_carry_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCarrySmem));
+    }
+    TC_CUDA(cudaStreamSynchronize(s));
+    return SPIIR_OK;
 }
-spiir_status spiir_tc_push(TcBank *, int, int, const float *, int64_t, int64_t, cudaStream_t,
-                           KernelTimer *) {
-    return SPIIR_EUNSUPPORTED;
+
+spiir_status spiir_tc_push(TcBank *b, int s0, int count, const float *x, int64_t x_stride, int64_t n,
+                           cudaStream_t s, KernelTimer *timer) {
+    if (n % b->L != 0) return tc_fail(SPIIR_EINVAL, "push length must be a multiple of chunk_len");
+    const int64_t n_prev = b->last_n[s0];
+    for (int q = s0; q < s0 + count; ++q)
+        if (b->last_n[q] != n_prev) {
+            for (int i = 0; i < count; ++i) {
+                spiir_status st = spiir_tc_push(b, s0 + i, 1, x + i * x_stride, x_stride, n, s, timer);
+                if (st) return st;
+            }
+            return SPIIR_OK;
+        }
+    // strain history + new samples (single-level prologue)
+    PrologueArgs pa{};
+    pa.xbuf = b->xbuf;
+    pa.xbuf_stream_stride = b->xbuf_stride;
+    pa.x_in = x;
+    pa.x_in_stream_stride = x_stride;
+    pa.stream0 = s0;
+    pa.n_levels = 1;
+    pa.lev[0].hist = b->F;
+    pa.lev[0].n = (int32_t)n;
+    pa.lev[0].n_prev = (int32_t)n_prev;
+    pa.lev[0].xbuf_off = 0;
+    timer->begin(SPIIR_K_TC_STAGE, s);
+    TC_CUDA(spiir_launch_prologue(pa, count, s));
+    timer->end(s);
+
+    const int C = (int)(n / b->L);
+    // streams are carried two at a time (the carry kernel's thread layout)
+    if (count > 2) {
+        for (int i = 0; i < count; i += 2) {
+            const int cnt = std::min(2, count - i);
+            spiir_status st = spiir_tc_push(b, s0 + i, cnt, x + i * x_stride, x_stride, n, s, timer);
+            if (st) return st;
+        }
+        return SPIIR_OK;
+    }
+    const int cpb = carry_cpb(count, b->L);
+    const int n_batches = (C + cpb - 1) / cpb;
+    TcStageArgs sa{};
+    sa.xbuf = b->xbuf;
+    sa.xbuf_stride = b->xbuf_stride;
+    sa.hist = b->F;
+    sa.F = b->F;
+    sa.L = b->L;
+    sa.K = b->K;
+    sa.n_chunks = C;
+    sa.n_streams = count;
+    sa.stream0 = s0;
+    sa.cpb = cpb;
+    sa.n_batches = n_batches;
+    sa.hank = b->hank;
+    sa.hank_bytes = b->hank_bytes;
+    sa.xseg = b->xseg;
+    {
+        const int64_t chunks = (int64_t)count * C * (b->hank_bytes / 16) + (int64_t)n_batches * (kXsegBytes / 16);
+        const int grid = (int)std::min<int64_t>((chunks + 255) / 256, 8LL * b->n_sms);
+        timer->begin(SPIIR_K_TC_STAGE, s);
+        if (b->bf16)
+            tc_stage_kernel<true><<<grid, 256, 0, s>>>(sa);
+        else
+            tc_stage_kernel<false><<<grid, 256, 0, s>>>(sa);
+        TC_CUDA(cudaGetLastError());
+        timer->end(s);
+    }
+
+    // the carry kernel writes the state term into z; the FIR kernel adds to it
+    if (b->n_carry_ctas > 0) {
+        TcCarryArgs ca{};
+        ca.tile_ptr = b->tile_ptr;
+        ca.tmpl_of = b->tmpl_of;
+        ca.n_carry = b->n_carry_ctas;
+        ca.a = b->a;
+        ca.a64 = b->a64;
+        ca.aJ = b->aJ;
+        ca.aL = b->aL;
+        ca.aLf = b->aLf;
+        ca.aLb = count == 1 ? b->aLb1 : b->aLb2;
+        ca.c = b->c;
+        ca.v = b->v;
+        ca.n_slots = b->n_slots;
+        ca.xseg = b->xseg;
+        ca.L = b->L;
+        ca.n_chunks = C;
+        ca.n_streams = count;
+        ca.stream0 = s0;
+        ca.cpb = cpb;
+        ca.n_batches = n_batches;
+        ca.scale = b->scale;
+        ca.z = b->z;
+        ca.z_row_stride = b->ring_len;
+        ca.z_stream_stride = (int64_t)b->T * b->ring_len;
+        ca.status = b->status;
+        const int grid = std::min(b->n_carry_ctas, 2 * b->n_sms);
+        timer->begin(SPIIR_K_TC_CARRY, s);
+        if (b->bf16)
+            tc_carry_kernel<true><<<grid, 256, kCarrySmem, s>>>(ca);
+        else
+            tc_carry_kernel<false><<<grid, 256, kCarrySmem, s>>>(ca);
+        TC_CUDA(cudaGetLastError());
+        timer->end(s);
+    }
+    TcFirArgs fa{};
+    fa.H = b->H;
+    fa.row_scale = b->row_scale;
+    fa.has_carry = b->has_carry;
+    fa.hank = b->hank;
+    fa.hank_bytes = b->hank_bytes;
+    fa.L = b->L;
+    fa.K = b->K;
+    fa.n_groups = b->n_groups;
+    fa.n_chunks = C;
+    fa.n_streams = count;
+    fa.n_templates = b->T;
+    fa.stream0 = s0;
+    fa.z = b->z;
+    fa.z_row_stride = b->ring_len;
+    fa.z_stream_stride = (int64_t)b->T * b->ring_len;
+    fa.status = b->status;
+    {
+        const int items = b->n_groups * C * count;
+        const int grid = std::min(items, b->n_sms);
+        const int smem = fir_smem_of(b->L, b->K);
+        timer->begin(SPIIR_K_TC_FIR, s);
+        if (b->bf16)
+            tc_fir_kernel<true><<<grid, 192, smem, s>>>(fa);
+        else
+            tc_fir_kernel<false><<<grid, 192, smem, s>>>(fa);
+        TC_CUDA(cudaGetLastError());
+        timer->end(s);
+    }
+
+    for (int q = s0; q < s0 + count; ++q) b->last_n[q] = n;
+    return SPIIR_OK;
 }
-spiir_status spiir_tc_reset(TcBank *, int, int, cudaStream_t) { return SPIIR_EUNSUPPORTED; }
-const float2 *spiir_tc_output(TcBank *, int, int64_t *ring_len) {
-    *ring_len = 0;
-    return nullptr;
+
+spiir_status spiir_tc_reset(TcBank *b, int s0, int count, cudaStream_t s) {
+    if (b->n_slots)
+        TC_CUDA(cudaMemsetAsync(b->v + (int64_t)s0 * b->n_slots, 0, count * b->n_slots * sizeof(double2), s));
+    TC_CUDA(cudaMemsetAsync(b->xbuf + (int64_t)s0 * b->xbuf_stride, 0, count * b->xbuf_stride * sizeof(float), s));
+    for (int q = s0; q < s0 + count; ++q) b->last_n[q] = 0;
+    return SPIIR_OK;
 }
-float *spiir_tc_stage(TcBank *) { return nullptr; }
-unsigned int *spiir_tc_status(TcBank *) { return nullptr; }
-void spiir_tc_info(TcBank *, spiir_bank_info *) {}
-int64_t spiir_tc_footprint(const spiir_bank_desc *) { return -1; }
-void spiir_tc_destroy(TcBank *b) { delete b; }
-const char *spiir_tc_last_error() { return kMsg; }
+
+const float2 *spiir_tc_output(TcBank *b, int stream, int64_t *ring_len) {
+    *ring_len = b->ring_len;
+    return b->z + (int64_t)stream * b->T * b->ring_len;
+}
+
+float *spiir_tc_stage(TcBank *b) { return b->stage; }
+
+unsigned int *spiir_tc_status(TcBank *b) { return b->status; }
+
+void spiir_tc_info(TcBank *b, spiir_bank_info *info) {
+    info->n_slots = b->n_slots;
+    info->filter_samples_per_block = 0;
+    info->n_warp_tasks = 0;
+    info->n_cta_items = b->n_groups;
+    info->filters_per_lane = 0;
+    info->time_tile = b->L;
+    info->kernel_variant = b->bf16 ? 2 : 1;
+    info->max_delay = b->max_delay;
+    info->tc_fir_len = b->F;
+    info->graph_captured = 0;
+    info->n_units = b->n_tiles;
+    info->smem_ways = 1.f;
+    info->slot_fill = 1.f;
+}
+
+int64_t spiir_tc_footprint(const spiir_bank_desc *d) {
+    TcPlan p;
+    if (tc_plan(d, p)) return -1;
+    return tc_bytes(d, p);
+}
+
+void spiir_tc_destroy(TcBank *b) {
+    if (!b) return;
+    void *ptrs[] = {b->H, b->row_scale, b->tile_ptr, b->tmpl_of, b->has_carry, b->a, b->a64, b->aJ, b->c,
+                    b->aL, b->v, b->xbuf, b->stage, b->z, b->status, b->hank, b->xseg,
+                    b->aLf, b->aLb1, b->aLb2};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    delete b;
+}
+
+const char *spiir_tc_last_error() { return g_tc_err.c_str(); }

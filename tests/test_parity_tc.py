@@ -1,0 +1,79 @@
+"""GPU parity of the block-parallel tensor-core form against the FP64 oracle.
+
+Tolerance for the FP16 panels: per-template RMS error / RMS SNR <= 1e-3. The
+single-pass BF16 form rounds operands to 8 significant bits, so its error is
+reported against a looser bound (see the test). The first chunk of a fresh
+bank has zero carried state, so its error isolates the FIR contraction; the
+later chunks add the state contractions and the FP64 carry."""
+import numpy as np
+import pytest
+
+from paper_1702_02256_gb300 import inputs
+from tests._util import TOL_TC, gpu_snr, rel_rms
+
+pytestmark = pytest.mark.gpu
+
+TOL_BF16 = 1e-2
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _check(z, ref, tol, L):
+    err = rel_rms(z, ref)
+    first = rel_rms(z[..., :L], ref[..., :L]) if np.abs(ref[..., :L]).max() > 0 else np.zeros(1)
+    assert err.max() <= tol, (f"max rel rms {err.max():.3e}; first chunk (FIR only) "
+                              f"{np.max(first):.3e}")
+    return float(err.max())
+
+
+@pytest.mark.parametrize("mode,tol", [("fp16", TOL_TC), ("bf16", TOL_BF16)])
+def test_config3_scaled_two_streams(torch_cuda, oracle_mod, mode, tol):
+    """Config-3 filters (256 per template, delays to 1023), 2 streams, 4 s pushed
+    as 1 s blocks, chunk length 256."""
+    w = inputs.workload(3, scale_templates=96, n_samples=4 * 4096)
+    z = gpu_snr(w["bank"], w["x"], push_blocks=1, n_streams=2, mode=mode, chunk_len=256)
+    for s in range(2):
+        ref = oracle_mod.spiir_single(w["bank"], w["x"][s])
+        _check(z[s], ref, tol, 256)
+
+
+def test_uneven_templates_chunk128(torch_cuda, oracle_mod):
+    counts = [0, 1, 3, 100, 128, 130, 300]
+    bank = inputs.single_rate_bank(len(counts), counts, 600, seed=17)
+    x = inputs.strain(1, 3 * 2048, seed=12)
+    z = gpu_snr(bank, x, block_len=2048, push_blocks=1, mode="fp16", chunk_len=128)[0]
+    ref = oracle_mod.spiir_single(bank, x[0])
+    assert np.all(z[0] == 0)
+    _check(z[1:], ref[1:], TOL_TC, 128)
+
+
+def test_tc_matches_plain_path(torch_cuda):
+    """Same bank through both forms: they agree to the TC tolerance."""
+    bank = inputs.single_rate_bank(70, 64, 300, seed=3)
+    x = inputs.strain(1, 2 * 4096, seed=4)
+    zp = gpu_snr(bank, x, push_blocks=2)[0]
+    zt = gpu_snr(bank, x, push_blocks=2, mode="fp16")[0]
+    assert rel_rms(zt, zp).max() <= TOL_TC
+
+
+def test_tc_reset_and_host_entry(torch_cuda):
+    import torch
+    from paper_1702_02256_gb300 import spiir
+    bank = inputs.single_rate_bank(8, 40, 200, seed=6)
+    x = inputs.strain(1, 4096, seed=2)
+    b = spiir.Bank(bank, n_streams=1, block_len=4096, mode="fp16")
+    xd = torch.from_numpy(x).cuda()
+    b.push(xd)
+    first = b.read(4096).cpu().numpy()
+    b.push(xd)
+    b.reset()
+    zh = b.push_host(x)
+    b.sync_status()
+    b.close()
+    assert np.array_equal(first, zh)
