@@ -30,6 +30,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1702_02256_gb300 import replicas  # noqa: E402
+
 METRIC = "real-time templates/GPU (filter-samples/s) & p99 block latency, chosen vs plain"
 UNIT = "filter-samples/s"
 FLOPS_PER_FS = 12          # Sec. 2.2 cost model: 12 flops per filter per sample
@@ -38,10 +40,8 @@ FP32_LANES_PER_SM = 128
 
 
 def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_1702_02256_gb300 import replicas
+    return replicas.world()
 
 
 class ClockSampler:
@@ -144,7 +144,7 @@ def _workload(name: str, rank: int, templates: int = 0, seconds: int = 0):
     if name == "single":
         T = templates or 1024
         sec = seconds or 16
-        bank = inputs.single_rate_bank(T, 512, 4095, seed=rank)
+        bank = inputs.single_rate_bank(T, 512, 4095, seed=replicas.rank_seed(0, rank))
         return dict(bank=bank, x=inputs.strain(1, sec * 4096, seed=1 + 100 * rank),
                     block_len=4096, push_blocks=sec, n_streams=1, chunk_len=256,
                     desc=f"single-rate {T} templates x 512 filters, 4096 Hz, {sec} s per step "
@@ -152,7 +152,7 @@ def _workload(name: str, rank: int, templates: int = 0, seconds: int = 0):
     if name == "multirate":
         T = templates or 4000
         sec = seconds or 16
-        bank = inputs.multi_rate_bank(T, 7, seed=rank)
+        bank = inputs.multi_rate_bank(T, 7, seed=replicas.rank_seed(0, rank))
         return dict(bank=bank, x=inputs.strain(1, sec * 4096, seed=1 + 100 * rank),
                     block_len=4096, push_blocks=1, n_streams=1, chunk_len=256,
                     desc=f"multi-rate {T} templates, 7 rates 4096-64 Hz, {sec} s per step "
@@ -160,7 +160,7 @@ def _workload(name: str, rank: int, templates: int = 0, seconds: int = 0):
     if name == "tc":
         T = templates or 8000
         sec = seconds or 8
-        bank = inputs.single_rate_bank(T, 256, 1023, seed=rank)
+        bank = inputs.single_rate_bank(T, 256, 1023, seed=replicas.rank_seed(0, rank))
         return dict(bank=bank, x=inputs.strain(2, sec * 4096, seed=1 + 100 * rank),
                     block_len=4096, push_blocks=1, n_streams=2, chunk_len=256,
                     desc=f"single-rate {T} templates x 256 filters, 2 streams, 4096 Hz, {sec} s "
@@ -285,11 +285,7 @@ def _measure(w, form, args, dev, dist, sampler, rank, ws):
     t_wall1 = time.time()
     kt = b.kernel_times()
     b.enable_timing(False)
-    total_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = replicas.max_over_ranks(sum(e0.elapsed_time(e1) for e0, e1 in ev), dist, dev)
     ms_per_step = total_ms / args.steps
 
     # per-block latency: one 1 s block of every stream per push, push -> SNR out
@@ -319,17 +315,13 @@ def _measure(w, form, args, dev, dist, sampler, rank, ws):
     for _ in range(e2e_steps):
         for p in xh_pushes:
             b.push_host(p, z_out=zh)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = replicas.max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist, dev)
     b.sync_status()
     b.close()
     del flush
     torch.cuda.synchronize()
     return dict(form=form, info=info, kt=kt, ms_per_step=ms_per_step,
-                value=ws * fs_per_step * args.steps / (total_ms / 1e3),
+                value=replicas.job_rate(fs_per_step * args.steps, ws, total_ms / 1e3),
                 fs_per_step=fs_per_step, steps=args.steps,
                 rtt=ws * bank.n_templates * S * (n / 4096.0) / (ms_per_step / 1e3),
                 p50=float(np.percentile(lat, 50)), p99=float(np.percentile(lat, 99)),
@@ -461,13 +453,97 @@ def run_ours(args):
     return 0
 
 
+def _serve_trial(kind, form, scale, n_blocks, seed, budget):
+    """One serving run: config-4 request process with template counts scaled by
+    `scale`, started from the steady-state population. Returns the summary."""
+    import torch
+    from paper_1702_02256_gb300 import inputs, serve
+    block = 4096
+    reqs = inputs.serving_requests(400, seed=seed)
+    t0 = 40.0     # requests arriving in the 40 s before block 0 may still be alive
+    make, fp = serve.device_bank_factory(form, block_len=block, n_streams=3)
+    srv = serve.Server(budget, 3, block, make, fp)
+    for i, r in enumerate(reqs):
+        t = r["arrival_s"] - t0
+        if t >= n_blocks:
+            break
+        first = max(0, int(np.ceil(t)))
+        # a request that arrived before block 0 has already served part of
+        # its lifetime
+        life = r["lifetime"] - (int(np.ceil(-t)) if t < 0 else 0)
+        if life <= 0:
+            continue
+        T = max(1, int(round(r["n_templates"] * scale)))
+        q = dict(r, n_templates=T)
+        if kind == "multirate":
+            bank = inputs.request_bank(q)
+        else:
+            bank = inputs.single_rate_bank(T, r["filters"], 1023, seed=r["seed"])
+        srv.submit(serve.Request(i, bank, first, life))
+    x = torch.from_numpy(inputs.strain(3, n_blocks * block, seed=seed + 1)).cuda()
+    for b in range(n_blocks):
+        srv.step(x[:, b * block:(b + 1) * block].contiguous())
+    srv.drain()
+    out = serve.summarize(srv, warm_blocks=2)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_serve(args):
+    """Largest sustained load (real-time templates, 3 streams) with p99 block
+    latency under 10 ms, plain form versus tensor-core form."""
+    import torch
+    torch.cuda.set_device(0)
+    budget = int(torch.cuda.get_device_properties(0).total_memory * 0.8)
+    res = {}
+    for form, kind in (("plain", args.serve_kind), ("fp16", "single")):
+        best = None
+        trials = []
+        scale = args.serve_scale0
+        for _ in range(args.serve_trials):
+            r = _serve_trial(kind, form, scale, args.serve_blocks, 7, budget)
+            r["scale"] = scale
+            trials.append(r)
+            if r.get("blocks", 0) and r["p99_block_latency_ms"] < 10.0:
+                best = r
+                scale *= 2.0
+            else:
+                break
+        res[form] = {"at_slo": best, "trials": trials}
+    def rtt(r):
+        return 3 * r["mean_active_templates"] if r else 0.0
+    line = {
+        "metric": "real-time templates/GPU at p99 block latency < 10 ms (3 streams, 1 s blocks)",
+        "value": rtt(res["fp16"]["at_slo"]), "unit": "templates", "higher_is_better": True,
+        "n_gpus": 1, "data": "synthetic",
+        "config": {"workload": "serving loop: Poisson bank requests 2/s, template counts "
+                               "log-uniform 50-20000 x scale, 128-512 filters, lifetimes 10-60 "
+                               "blocks, 3 streams, 1 s blocks, HBM budget 80% of the device",
+                   "plain_requests": args.serve_kind, "tc_requests": "single"},
+        "plain": {"real_time_templates": rtt(res["plain"]["at_slo"]), **(res["plain"]["at_slo"] or {})},
+        "chosen": {"form": "tensor-core block form (fp16)",
+                   "real_time_templates": rtt(res["fp16"]["at_slo"]), **(res["fp16"]["at_slo"] or {})},
+        "trials": {k: v["trials"] for k, v in res.items()},
+    }
+    if line["plain"]["real_time_templates"]:
+        line["chosen"]["ratio_vs_plain"] = line["chosen"]["real_time_templates"] / line["plain"]["real_time_templates"]
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="single", choices=["single", "multirate", "tc"])
+    ap.add_argument("--workload", default="single", choices=["single", "multirate", "tc", "serve"])
+    ap.add_argument("--serve-kind", default="single", choices=["single", "multirate"],
+                    help="serving: banks of the plain-form run (multi-rate is config 4)")
+    ap.add_argument("--serve-blocks", type=int, default=24)
+    ap.add_argument("--serve-trials", type=int, default=6)
+    ap.add_argument("--serve-scale0", type=float, default=0.02)
     ap.add_argument("--form", default="", choices=["", "plain", "fp16", "bf16"],
                     help="compute form of the headline number (default: plain; fp16 for tc)")
     ap.add_argument("--chosen", default="fp16", choices=["", "plain", "fp16", "bf16"],
@@ -482,6 +558,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

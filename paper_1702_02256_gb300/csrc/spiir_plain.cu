@@ -626,8 +626,19 @@ void spiir_recur_variant_shape(int v, int *time_tile, int *fmax) {
 }
 
 cudaError_t spiir_recur_prepare(int v, int smem_bytes, int *ctas_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(kVariants[v].fn,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    // The limit is a property of the kernel shared by every bank: set it once
+    // to the device maximum; each launch passes its own (smaller) size.
+    int dev = 0, max_optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kVariants[v].fn);
+    if (e != cudaSuccess) return e;
+    const int dyn_max = max_optin - (int)fa.sharedSizeBytes;
+    if (smem_bytes > dyn_max) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(kVariants[v].fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
     if (e != cudaSuccess) return e;
     int n = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kVariants[v].fn, SPIIR_CTA_WARPS * 32,

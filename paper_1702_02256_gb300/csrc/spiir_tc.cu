@@ -1018,13 +1018,21 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
     int dev = 0;
     TC_CUDA(cudaGetDevice(&dev));
     TC_CUDA(cudaDeviceGetAttribute(&b->n_sms, cudaDevAttrMultiProcessorCount, dev));
-    const int fir_smem = fir_smem_of(p.L, p.K);
-    if (b->bf16) {
-        TC_CUDA(cudaFuncSetAttribute(tc_fir_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fir_smem));
-        TC_CUDA(cudaFuncSetAttribute(tc_carry_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCarrySmem));
-    } else {
-        TC_CUDA(cudaFuncSetAttribute(tc_fir_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fir_smem));
-        TC_CUDA(cudaFuncSetAttribute(tc_carry_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCarrySmem));
+    // kernel-wide limits shared by every bank: the device maximum, set once
+    int max_optin = 0;
+    TC_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    {
+        const void *fns[4] = {(const void *)tc_fir_kernel<true>, (const void *)tc_carry_kernel<true>,
+                              (const void *)tc_fir_kernel<false>, (const void *)tc_carry_kernel<false>};
+        const int need[4] = {fir_smem_of(p.L, p.K), kCarrySmem, fir_smem_of(p.L, p.K), kCarrySmem};
+        for (int i = 0; i < 4; ++i) {
+            cudaFuncAttributes fa;
+            TC_CUDA(cudaFuncGetAttributes(&fa, fns[i]));
+            const int dyn_max = max_optin - (int)fa.sharedSizeBytes;
+            if (need[i] > dyn_max)
+                return tc_fail(SPIIR_EUNSUPPORTED, "tensor-core form: shared memory above the device limit");
+            TC_CUDA(cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
+        }
     }
     TC_CUDA(cudaStreamSynchronize(s));
     return SPIIR_OK;
