@@ -58,7 +58,8 @@ typedef enum {
  * the template impulse responses with a Toeplitz view of x, plus per-filter
  * power panels a_k^j applied to filter states carried between chunks in FP64.
  * TC_FP16 / TC_BF16 round the panel and strain operands to that type (FP32
- * accumulation); TC_BF16X2 splits each operand into a bf16 high and low part. */
+ * accumulation). TC_BF16X2 (each operand split into a bf16 high and low part)
+ * is reserved: this build returns SPIIR_EUNSUPPORTED for it. */
 typedef enum {
     SPIIR_PLAIN_FP32 = 0,
     SPIIR_TC_FP16 = 1,
@@ -199,6 +200,16 @@ spiir_status spiir_bank_enable_timing(spiir_bank_t bank, int32_t enable);
 /* Wait for the recorded events, return the per-kind sums since the previous
  * call (or since timing was enabled), and start a new count. */
 spiir_status spiir_bank_kernel_times(spiir_bank_t bank, spiir_kernel_times *out);
+
+/* Failure-detection test (plain form): one push of the first stream in which
+ * the first work item of the recursion kernel neither runs nor publishes its
+ * progress, so the item that depends on it waits until the bounded device
+ * wait (about 2 s) gives up and records SPIIR_ETIMEOUT in the status word.
+ * No fault, trap or hang: the kernel finishes, the SNR of that push is not
+ * valid, the next spiir_bank_sync_status returns SPIIR_ETIMEOUT and clears
+ * it, and the bank keeps working. n_samples >= 8192 (two time segments). */
+spiir_status spiir_bank_test_stall(spiir_bank_t bank, const float *x_dev, int64_t n_samples,
+                                   void *cuda_stream);
 
 /* Release everything the bank holds. NULL is ignored. */
 void spiir_bank_destroy(spiir_bank_t bank);

@@ -167,6 +167,8 @@ spiir_status validate(const spiir_bank_desc *d) {
         return fail(SPIIR_EINVAL, "unknown mode %d", (int)d->mode);
     if (d->mode != SPIIR_PLAIN_FP32 && d->n_levels != 1)
         return fail(SPIIR_EUNSUPPORTED, "tensor-core forms take single-rate banks");
+    if (d->mode == SPIIR_TC_BF16X2)
+        return fail(SPIIR_EUNSUPPORTED, "split-bf16 operands are not built; use SPIIR_TC_FP16");
     if (d->hbm_budget_bytes < 0) return fail(SPIIR_EINVAL, "hbm_budget_bytes must be >= 0");
     for (int64_t k = 0; k < d->n_filters; ++k) {
         if (d->template_id[k] < 0 || d->template_id[k] >= d->n_templates)
@@ -546,6 +548,12 @@ spiir_status upload(T **dst, const std::vector<T> &src, cudaStream_t s) {
 // The bank
 // ---------------------------------------------------------------------------
 
+struct GraphEntry {
+    int s0, count;
+    int64_t n, n_prev;
+    cudaGraphExec_t exec;
+};
+
 struct spiir_bank {
     spiir_bank_desc d;
     Plan p;
@@ -564,6 +572,8 @@ struct spiir_bank {
     int32_t *order = nullptr;
     unsigned int *queue = nullptr, *prog = nullptr;
     int ctas_per_sm = 1, n_sms = 1;
+    cudaStream_t cap = nullptr;             // private stream for graph capture
+    std::vector<GraphEntry> graphs;
     std::vector<int64_t> last_n;
     int64_t footprint = 0;
     int64_t n_filters = 0;
@@ -593,6 +603,12 @@ struct spiir_bank {
             timer->release();
             delete timer;
             timer = nullptr;
+        }
+        for (auto &g : graphs) cudaGraphExecDestroy(g.exec);
+        graphs.clear();
+        if (cap) {
+            cudaStreamDestroy(cap);
+            cap = nullptr;
         }
     }
 };
@@ -633,6 +649,7 @@ spiir_status alloc_plain(spiir_bank *b, cudaStream_t s) {
     CUDA_TRY(cudaMemsetAsync(b->status, 0, sizeof(unsigned int), s));
     CUDA_TRY(spiir_recur_prepare(p.variant, p.smem_bytes, &b->ctas_per_sm));
     CUDA_TRY(cudaDeviceGetAttribute(&b->n_sms, cudaDevAttrMultiProcessorCount, b->device));
+    CUDA_TRY(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
     return SPIIR_OK;
 }
 
@@ -663,10 +680,10 @@ void level_args(const spiir_bank *b, int64_t n, int64_t n_prev, LevelArgs *lev) 
     }
 }
 
-spiir_status push_plain(spiir_bank *b, int s0, int count, const float *x, int64_t x_stride,
-                        int64_t n, cudaStream_t st) {
+// The kernels of one push (no host state changes).
+spiir_status launch_sequence(spiir_bank *b, int s0, int count, const float *x, int64_t x_stride,
+                             int64_t n, int64_t n_prev, cudaStream_t st, bool stall_test) {
     const Plan &p = b->p;
-    const int64_t n_prev = b->last_n[s0];
     PrologueArgs pa{};
     pa.queue = b->queue;
     pa.prog = b->prog;
@@ -704,6 +721,7 @@ spiir_status push_plain(spiir_bank *b, int s0, int count, const float *x, int64_
         ra.n_segs = push_segments(p, n);
         ra.queue = b->queue;
         ra.prog = b->prog;
+        ra.stall_test = stall_test ? 1 : 0;
         ra.task_out = b->task_out;
         ra.a_re = b->are;
         ra.a_im = b->aim;
@@ -753,7 +771,62 @@ spiir_status push_plain(spiir_bank *b, int s0, int count, const float *x, int64_
         CUDA_TRY(spiir_launch_combine(ca, count, st));
         tm.end(st);
     }
-    for (int s = s0; s < s0 + count; ++s) b->last_n[s] = n;
+    return SPIIR_OK;
+}
+
+// A push replayed from a CUDA graph: the strain is copied into the bank's
+// staging buffer on the caller's stream and one graph (captured once per
+// stream set, length and previous length) launches all kernels.
+spiir_status push_graph(spiir_bank *b, int s0, int count, const float *x, int64_t x_stride,
+                        int64_t n, cudaStream_t st) {
+    const int64_t n_prev = b->last_n[s0];
+    GraphEntry *ge = nullptr;
+    for (auto &g : b->graphs)
+        if (g.s0 == s0 && g.count == count && g.n == n && g.n_prev == n_prev) ge = &g;
+    if (!ge) {
+        if (b->graphs.size() >= 16) {
+            cudaGraphExecDestroy(b->graphs.front().exec);
+            b->graphs.erase(b->graphs.begin());
+        }
+        cudaGraph_t g = nullptr;
+        CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+        spiir_status stc = launch_sequence(b, s0, count, b->xstage + (int64_t)s0 * n, n, n, n_prev,
+                                           b->cap, false);
+        cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+        if (stc) {
+            if (g) cudaGraphDestroy(g);
+            return stc;
+        }
+        if (e != cudaSuccess) return fail(SPIIR_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(SPIIR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        b->graphs.push_back(GraphEntry{s0, count, n, n_prev, exec});
+        ge = &b->graphs.back();
+    }
+    float *dst = b->xstage + (int64_t)s0 * n;
+    if (x != dst) {
+        if (x_stride == n) {
+            CUDA_TRY(cudaMemcpyAsync(dst, x, count * n * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        } else {
+            CUDA_TRY(cudaMemcpy2DAsync(dst, n * sizeof(float), x, x_stride * sizeof(float),
+                                       n * sizeof(float), count, cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    CUDA_TRY(cudaGraphLaunch(ge->exec, st));
+    return SPIIR_OK;
+}
+
+spiir_status push_plain(spiir_bank *b, int s0, int count, const float *x, int64_t x_stride,
+                        int64_t n, cudaStream_t st, bool stall_test = false) {
+    spiir_status r;
+    if (b->cap && !b->timer->on && !stall_test)
+        r = push_graph(b, s0, count, x, x_stride, n, st);
+    else
+        r = launch_sequence(b, s0, count, x, x_stride, n, b->last_n[s0], st, stall_test);
+    if (r) return r;
+    for (int q = s0; q < s0 + count; ++q) b->last_n[q] = n;
     return SPIIR_OK;
 }
 
@@ -1018,6 +1091,7 @@ spiir_status spiir_bank_get_info(spiir_bank_t b, spiir_bank_info *info) {
     }
     plan_info(&b->d, b->p, info);
     info->slot_fill = b->p.n_slots ? (float)b->n_filters / (float)b->p.n_slots : 1.f;
+    info->graph_captured = b->graphs.empty() ? 0 : 1;
     return SPIIR_OK;
 }
 
@@ -1032,6 +1106,16 @@ spiir_status spiir_bank_sync_status(spiir_bank_t b) {
         return fail(SPIIR_ETIMEOUT, "a device-side wait timed out (status %u)", v);
     }
     return SPIIR_OK;
+}
+
+spiir_status spiir_bank_test_stall(spiir_bank_t b, const float *x_dev, int64_t n_samples,
+                                   void *cuda_stream) {
+    if (!b || !x_dev) return fail(SPIIR_EINVAL, "NULL argument");
+    if (b->tc) return fail(SPIIR_EUNSUPPORTED, "stall test runs on the plain form");
+    if (n_samples < 8192 || n_samples % b->d.block_len != 0 ||
+        n_samples > (int64_t)b->d.block_len * b->d.max_push_blocks)
+        return fail(SPIIR_EINVAL, "stall test needs a push of at least two 4096-sample segments");
+    return push_plain(b, 0, 1, x_dev, n_samples, n_samples, (cudaStream_t)cuda_stream, true);
 }
 
 spiir_status spiir_bank_enable_timing(spiir_bank_t b, int32_t enable) {

@@ -62,6 +62,8 @@ struct RecurArgs {
     int32_t n_segs;            // time segments per push; queue = n_segs * n_items
     unsigned int *queue;       // [stream] work counter, zeroed by the prologue
     unsigned int *prog;        // [stream][n_items] segments finished this push
+    int32_t stall_test;        // 1: queue item 0 neither works nor publishes
+                               // its progress (failure-detection test)
     const int32_t *task_out;   // >= 0: direct z row; < 0: partial row -(v+1)
     const float *a_re, *a_im, *b_re, *b_im;
     const int32_t *xoff;       // per slot: hist - delay (window offset)

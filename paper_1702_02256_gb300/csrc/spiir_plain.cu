@@ -407,9 +407,12 @@ __global__ void __launch_bounds__(SPIIR_CTA_WARPS * 32, MINB) recur_kernel(const
         const LevelArgs L = a.lev[item.level];
         const int s0 = seg * L.seg;
         const int sl = min(L.seg, L.n - s0);
+        // in the failure-detection test the first item is dropped, so the
+        // wait of the item after it has to give up
+        const bool dropped = a.stall_test && q == 0;
         if (seg > 0 && threadIdx.x == 0) wait_counter(prog + gi, (unsigned)seg, a.status);
         __syncthreads();
-        if (sl > 0) {
+        if (sl > 0 && !dropped) {
             const float *xlev = a.xbuf + (int64_t)stream * a.xbuf_stream_stride + L.xbuf_off;
             if (threadIdx.x == 0) {
                 const uint32_t bytes = (uint32_t)(((L.hist + sl) * 4 + 15) & ~15);
@@ -478,7 +481,7 @@ __global__ void __launch_bounds__(SPIIR_CTA_WARPS * 32, MINB) recur_kernel(const
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && !dropped) {
             __threadfence();
             st_release(prog + gi, (unsigned)(seg + 1));
         }
@@ -520,13 +523,20 @@ __device__ __forceinline__ void combine_chunk(const float2 *__restrict__ ulow, c
     }
 }
 
-__global__ void combine_kernel(const CombineArgs a) {
-    const int t = blockIdx.x;
+// One warp per template: the warp walks the levels from the lowest rate up,
+// so levels are ordered by __syncwarp alone and a CTA keeps 8 templates in
+// flight.
+constexpr int kCombWarps = 8;
+
+__global__ void __launch_bounds__(kCombWarps * 32) combine_kernel(const CombineArgs a) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x * kCombWarps + warp;
     const int s = a.stream0 + blockIdx.y;
     const int H = a.n_levels - 1;
     __shared__ float h2[SPIIR_MAX_TAPS];
     if (threadIdx.x < a.n_taps) h2[threadIdx.x] = a.h_up2[threadIdx.x];
     __syncthreads();
+    if (t >= a.n_templates) return;
     float2 *part = a.partial + (int64_t)s * a.partial_stream_stride;
     float2 *ub = a.ubuf + (int64_t)s * a.ubuf_stream_stride;
     for (int i = H; i >= 0; --i) {
@@ -541,7 +551,7 @@ __global__ void combine_kernel(const CombineArgs a) {
             n_low = Ll.n;
         }
         float2 *zrow = a.z + (int64_t)s * a.z_stream_stride + (int64_t)t * a.z_row_stride;
-        for (int n0 = threadIdx.x * kCombOut; n0 < L.n; n0 += blockDim.x * kCombOut) {
+        for (int n0 = lane * kCombOut; n0 < L.n; n0 += 32 * kCombOut) {
             const int cnt = min(kCombOut, L.n - n0);
             float re[kCombOut], im[kCombOut];
 #pragma unroll
@@ -562,7 +572,6 @@ __global__ void combine_kernel(const CombineArgs a) {
                     case 8: combine_chunk<8>(ulow, h2, n0, re, im); break;
                     case 32: combine_chunk<32>(ulow, h2, n0, re, im); break;
                     default: {
-                        // other tap counts: direct form
                         const int half = a.n_taps / 2;
                         for (int r = 0; r < kCombOut; ++r) {
                             const float2 *u = ulow + SPIIR_UHIST + ((n0 + r) >> 1);
@@ -585,13 +594,24 @@ __global__ void combine_kernel(const CombineArgs a) {
                     if (r < cnt) zrow[n0 + r] = make_float2(a.scale * re[r], a.scale * im[r]);
             }
         }
-        __syncthreads();
+        __syncwarp();
         if (ulow) {
             // keep the last SPIIR_UHIST samples of the lower rate as history
             for (int c0 = 0; c0 < SPIIR_UHIST; c0 += n_low) {
                 const int len = min(n_low, SPIIR_UHIST - c0);
-                for (int k = threadIdx.x; k < len; k += blockDim.x) ulow[c0 + k] = ulow[c0 + n_low + k];
-                __syncthreads();
+                float2 v[(SPIIR_UHIST + 31) / 32];
+#pragma unroll
+                for (int j = 0; j < (SPIIR_UHIST + 31) / 32; ++j) {
+                    const int k = lane + 32 * j;
+                    if (k < len) v[j] = ulow[c0 + n_low + k];
+                }
+                __syncwarp();
+#pragma unroll
+                for (int j = 0; j < (SPIIR_UHIST + 31) / 32; ++j) {
+                    const int k = lane + 32 * j;
+                    if (k < len) ulow[c0 + k] = v[j];
+                }
+                __syncwarp();
             }
         }
     }
@@ -666,6 +686,7 @@ cudaError_t spiir_launch_recur(const RecurArgs &a, int variant, int n_ctas, int 
 }
 
 cudaError_t spiir_launch_combine(const CombineArgs &a, int n_streams, cudaStream_t s) {
-    combine_kernel<<<dim3(a.n_templates, n_streams), 128, 0, s>>>(a);
+    combine_kernel<<<dim3((a.n_templates + kCombWarps - 1) / kCombWarps, n_streams), kCombWarps * 32,
+                     0, s>>>(a);
     return cudaGetLastError();
 }

@@ -80,6 +80,7 @@ _SIGS = {
     "spiir_last_error": (ctypes.c_char_p, []),
     "spiir_filter_noalloc": (_i32, [ctypes.POINTER(BankDesc), _c_void_p, _i64, _c_void_p, _c_void_p]),
     "spiir_bank_enable_timing": (_i32, [_c_void_p, _i32]),
+    "spiir_bank_test_stall": (_i32, [_c_void_p, _c_void_p, _i64, _c_void_p]),
     "spiir_bank_kernel_times": (_i32, [_c_void_p, ctypes.POINTER(KernelTimes)]),
 }
 
@@ -265,6 +266,14 @@ class Bank:
         check(lib().spiir_bank_kernel_times(self._h, ctypes.byref(kt)))
         return {KERNEL_NAMES[k]: (kt.ms[k], int(kt.launches[k])) for k in range(8)
                 if kt.launches[k]}
+
+    def test_stall(self, x, stream=None) -> int:
+        """Failure-detection push (see spiir_bank_test_stall); returns its status."""
+        return int(lib().spiir_bank_test_stall(self._h, x.data_ptr(), int(x.shape[-1]),
+                                               _stream_handle(stream)))
+
+    def sync_status_code(self) -> int:
+        return int(lib().spiir_bank_sync_status(self._h))
 
     def sync_status(self):
         check(lib().spiir_bank_sync_status(self._h))
