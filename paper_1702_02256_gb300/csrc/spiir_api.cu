@@ -319,7 +319,7 @@ spiir_status make_plan(const spiir_bank_desc *d, int variant, bool arrays, Plan 
         p.part_base[i] = poff;
         poff += rows[i] * p.part_stride[i];
         if (i > 0) {
-            p.ubuf_stride[i] = (int32_t)round_up(SPIIR_UHIST + p.max_n[i] + 8, 2);
+            p.ubuf_stride[i] = SPIIR_UHIST;
             p.ubuf_off[i] = uoff;
             uoff += (int64_t)d->n_templates * p.ubuf_stride[i];
         }
@@ -648,6 +648,7 @@ spiir_status alloc_plain(spiir_bank *b, cudaStream_t s) {
     CUDA_TRY(cudaMemsetAsync(b->z, 0, S * (int64_t)b->d.n_templates * p.ring_len * sizeof(float2), s));
     CUDA_TRY(cudaMemsetAsync(b->status, 0, sizeof(unsigned int), s));
     CUDA_TRY(spiir_recur_prepare(p.variant, p.smem_bytes, &b->ctas_per_sm));
+    if (p.need_combine) CUDA_TRY(spiir_combine_prepare());
     CUDA_TRY(cudaDeviceGetAttribute(&b->n_sms, cudaDevAttrMultiProcessorCount, b->device));
     CUDA_TRY(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
     return SPIIR_OK;
@@ -765,10 +766,11 @@ spiir_status launch_sequence(spiir_bank *b, int s0, int count, const float *x, i
         ca.n_levels = p.n_levels;
         ca.n_taps = p.n_taps;
         ca.stream0 = s0;
+        ca.status = b->status;
         for (int j = 0; j < p.n_taps; ++j) ca.h_up2[j] = 2.0f * b->h_up[j];
         level_args(b, n, n_prev, ca.lev);
         tm.begin(SPIIR_K_COMBINE, st);
-        CUDA_TRY(spiir_launch_combine(ca, count, st));
+        CUDA_TRY(spiir_launch_combine(ca, spiir_combine_chunk(p.n_levels, p.ring_len), count, st));
         tm.end(st);
     }
     return SPIIR_OK;
@@ -1317,6 +1319,7 @@ extern "C" spiir_status spiir_filter_noalloc(const spiir_bank_desc *desc, const 
     // Templates without filters are never written by the kernels.
     CUDA_TRY(cudaMemsetAsync(z_dev, 0, (size_t)d.n_templates * n_samples * sizeof(float2), s));
     CUDA_TRY(spiir_recur_prepare(p.variant, p.smem_bytes, &b.ctas_per_sm));
+    if (p.need_combine) CUDA_TRY(spiir_combine_prepare());
     CUDA_TRY(cudaGetDevice(&b.device));
     CUDA_TRY(cudaDeviceGetAttribute(&b.n_sms, cudaDevAttrMultiProcessorCount, b.device));
 

@@ -50,7 +50,7 @@ struct LevelArgs {
     int64_t part_stride; // float2 per partial row
     int64_t xbuf_off;    // float offset of this level's strain buffer (per stream)
     int64_t ubuf_off;    // float2 offset of this level's upsampler rows
-    int32_t ubuf_stride; // float2 per row (SPIIR_UHIST + max samples)
+    int32_t ubuf_stride; // float2 per upsampler history row (SPIIR_UHIST)
     int32_t pad;
 };
 
@@ -112,7 +112,7 @@ struct CombineArgs {
     const int32_t *comb_rows;  // partial rows per (template, level), fixed order
     float2 *partial;
     int64_t partial_stream_stride;
-    float2 *ubuf;              // upsampler rows [stream][level][template][...]
+    float2 *ubuf;              // upsampler histories [stream][level][template][SPIIR_UHIST]
     int64_t ubuf_stream_stride;
     float2 *z;
     int64_t z_row_stride;
@@ -122,6 +122,7 @@ struct CombineArgs {
     int32_t n_levels;
     int32_t n_taps;
     int32_t stream0;
+    unsigned int *status;          // device status word (bounded waits)
     float h_up2[SPIIR_MAX_TAPS];   // 2 * h_up (gain 2 of the zero-stuffed series)
     LevelArgs lev[SPIIR_MAX_LEVELS];
 };
@@ -131,6 +132,7 @@ struct KernelTimer {
     bool on = false;
     struct Rec {
         int kind;
+        int n;                 // kernels launched between the two events
         cudaEvent_t a, b;
     };
     Rec recs[4096];
@@ -156,8 +158,9 @@ struct KernelTimer {
         cudaEventRecord(recs[n_recs].a, s);
         open_kind = kind;
     }
-    void end(cudaStream_t s) {
+    void end(cudaStream_t s, int n_launches = 1) {
         if (!on || open_kind < 0) return;
+        recs[n_recs].n = n_launches;
         cudaEventRecord(recs[n_recs].b, s);
         ++n_recs;
         open_kind = -1;
@@ -168,7 +171,7 @@ struct KernelTimer {
             float t = 0.f;
             cudaEventElapsedTime(&t, recs[i].a, recs[i].b);
             ms[recs[i].kind] += t;
-            launches[recs[i].kind] += 1;
+            launches[recs[i].kind] += recs[i].n;
             if (n_pool < 8190) {
                 pool[n_pool++] = recs[i].a;
                 pool[n_pool++] = recs[i].b;
@@ -191,7 +194,11 @@ cudaError_t spiir_launch_prologue(const PrologueArgs &a, int n_streams, cudaStre
 cudaError_t spiir_launch_decimate(const DecimArgs &a, int n_streams, cudaStream_t s);
 cudaError_t spiir_launch_recur(const RecurArgs &a, int variant, int n_ctas,
                                int n_streams, int smem_bytes, cudaStream_t s);
-cudaError_t spiir_launch_combine(const CombineArgs &a, int n_streams, cudaStream_t s);
+cudaError_t spiir_launch_combine(const CombineArgs &a, int chunk, int n_streams, cudaStream_t s);
+// Base-rate samples per combine time chunk, and the combine CTA's shared memory.
+int spiir_combine_chunk(int n_levels, int64_t push_max);
+int spiir_combine_smem(int n_levels, int chunk);
+cudaError_t spiir_combine_prepare();
 int spiir_recur_variant_count();
 void spiir_recur_variant_shape(int variant, int *time_tile, int *fmax);
 // Sets the dynamic shared memory limit and returns resident CTAs per SM.

@@ -22,6 +22,8 @@
 // those T sums with a butterfly reduce-scatter (shuffles in a fixed order,
 // no atomics), which leaves each lane holding whole sums for T/G samples.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 #include "spiir_internal.h"
@@ -492,128 +494,194 @@ __global__ void __launch_bounds__(SPIIR_CTA_WARPS * 32, MINB) recur_kernel(const
 // Combine: parts + upsample(next lower rate) + scale
 // ---------------------------------------------------------------------------
 
-// Each thread makes 8 consecutive outputs of a level from a register window
-// of 19 lower-rate samples (the 16-tap polyphase branches of the x2
-// interpolator overlap), plus the unit's partial sums.
-constexpr int kCombOut = 8;
+// One CTA per (template, stream) runs the whole level chain of a push in
+// time chunks of C base-rate samples (C >> H a multiple of 4). Level i >= 1
+// keeps its upsampler input in shared memory as [SPIIR_UHIST history |
+// C >> i samples]; the history carries across chunks in shared memory and
+// across pushes in a SPIIR_UHIST-long global row. At the start of a chunk one
+// thread stages the first unit part of every level into shared memory with
+// bulk async copies (all levels in flight at once); then, from the lowest
+// rate up:
+//   u_H[n] = sum of the unit parts
+//   u_i[n] = sum of the unit parts + 2 sum_j h_up[2j + (n&1)] u_{i+1}[n/2 - j]
+//   z[n]   = scale * u_0[n]
+// A thread makes 4 consecutive outputs 4q..4q+3 (lower-rate samples 2q and
+// 2q+1) from one window of the lower level held in registers, so only the
+// unit parts and z touch HBM.
+constexpr int kCombThreads = 256;
 
+// Shared-memory layout of the combine CTA, in float2 units after a 16-byte
+// mbarrier slot: the upsampler buffers of levels 1..H, each SPIIR_UHIST + 2 +
+// (C >> i) long, then the part stage of levels 0..H, C >> i each. C is a
+// multiple of 4 << H, so every length is a multiple of 2 (16-byte aligned).
+__host__ __device__ __forceinline__ int comb_ubuf_off(int chunk, int i) {   // i >= 1
+    return (i - 1) * (SPIIR_UHIST + 2) + chunk - (chunk >> (i - 1));
+}
+__host__ __device__ __forceinline__ int comb_stage_off(int chunk, int H, int i) {
+    return comb_ubuf_off(chunk, H + 1) + 2 * chunk - 2 * (chunk >> i);
+}
+
+// u_lo: lower-level buffer at its sample 0 (history at negative indices).
 template <int HT>
-__device__ __forceinline__ void combine_chunk(const float2 *__restrict__ ulow, const float *h2,
-                                              int n0, float (&re)[kCombOut],
-                                              float (&im)[kCombOut]) {
-    // window w[k] = u[n0/2 - (HT-1) + k], k < HT - 1 + kCombOut/2
-    constexpr int NW = HT - 1 + kCombOut / 2;
-    float2 w[NW];
-    const float2 *u = ulow + SPIIR_UHIST + (n0 >> 1) - (HT - 1);
+__device__ __forceinline__ void upsample_quad(const float2 *u_lo, int q, const float (&h0)[32],
+                                              const float (&h1)[32], int ht,
+                                              float2 (&o)[4]) {
+    if constexpr (HT > 0 && (HT % 2) == 0) {
+        // w[k] = u[2q - HT + k], k < HT + 2, loaded two samples at a time
+        float2 w[HT + 2];
+        const float4 *src = reinterpret_cast<const float4 *>(u_lo + 2 * q - HT);
 #pragma unroll
-    for (int k = 0; k < NW; ++k) w[k] = u[k];
-#pragma unroll
-    for (int r = 0; r < kCombOut; ++r) {
-        const int ph = r & 1;
-        const int c = HT - 1 + (r >> 1);   // window index of u[m], m = (n0 + r) >> 1
-        float ar = re[r], ai = im[r];
+        for (int k = 0; k < HT / 2 + 1; ++k) {
+            const float4 v = src[k];
+            w[2 * k] = make_float2(v.x, v.y);
+            w[2 * k + 1] = make_float2(v.z, v.w);
+        }
 #pragma unroll
         for (int j = 0; j < HT; ++j) {
-            const float hw = h2[2 * j + ph];
-            ar = fmaf(hw, w[c - j].x, ar);
-            ai = fmaf(hw, w[c - j].y, ai);
+            const float2 a0 = w[HT - j], a1 = w[HT + 1 - j];   // u[2q - j], u[2q + 1 - j]
+            o[0].x = fmaf(h0[j], a0.x, o[0].x);
+            o[0].y = fmaf(h0[j], a0.y, o[0].y);
+            o[1].x = fmaf(h1[j], a0.x, o[1].x);
+            o[1].y = fmaf(h1[j], a0.y, o[1].y);
+            o[2].x = fmaf(h0[j], a1.x, o[2].x);
+            o[2].y = fmaf(h0[j], a1.y, o[2].y);
+            o[3].x = fmaf(h1[j], a1.x, o[3].x);
+            o[3].y = fmaf(h1[j], a1.y, o[3].y);
         }
-        re[r] = ar;
-        im[r] = ai;
+    } else {
+        for (int j = 0; j < ht; ++j) {
+            const float2 a0 = u_lo[2 * q - j], a1 = u_lo[2 * q + 1 - j];
+            o[0].x = fmaf(h0[j], a0.x, o[0].x);
+            o[0].y = fmaf(h0[j], a0.y, o[0].y);
+            o[1].x = fmaf(h1[j], a0.x, o[1].x);
+            o[1].y = fmaf(h1[j], a0.y, o[1].y);
+            o[2].x = fmaf(h0[j], a1.x, o[2].x);
+            o[2].y = fmaf(h0[j], a1.y, o[2].y);
+            o[3].x = fmaf(h1[j], a1.x, o[3].x);
+            o[3].y = fmaf(h1[j], a1.y, o[3].y);
+        }
     }
 }
 
-// One warp per template: the warp walks the levels from the lowest rate up,
-// so levels are ordered by __syncwarp alone and a CTA keeps 8 templates in
-// flight.
-constexpr int kCombWarps = 8;
+template <int HT>
+__global__ void __launch_bounds__(kCombThreads, 4) combine_kernel(const CombineArgs a, int chunk) {
+    extern __shared__ __align__(16) unsigned char csm[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(csm);
+    float2 *cbuf = reinterpret_cast<float2 *>(csm + 16);
+    const int t = blockIdx.x, s = a.stream0 + blockIdx.y, tid = threadIdx.x;
+    const int H = a.n_levels - 1, ht = a.n_taps / 2;
+    const float2 *part = a.partial + (int64_t)s * a.partial_stream_stride;
+    float2 *hist = a.ubuf + (int64_t)s * a.ubuf_stream_stride;
+    float2 *zrow = a.z + (int64_t)s * a.z_stream_stride + (int64_t)t * a.z_row_stride;
+    const int32_t *cptr = a.comb_ptr + t * a.n_levels;
 
-__global__ void __launch_bounds__(kCombWarps * 32) combine_kernel(const CombineArgs a) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int t = blockIdx.x * kCombWarps + warp;
-    const int s = a.stream0 + blockIdx.y;
-    const int H = a.n_levels - 1;
-    __shared__ float h2[SPIIR_MAX_TAPS];
-    if (threadIdx.x < a.n_taps) h2[threadIdx.x] = a.h_up2[threadIdx.x];
+    float h0[32], h1[32];   // even / odd polyphase branches of 2 h_up
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        h0[j] = (j < ht) ? a.h_up2[2 * j] : 0.f;
+        h1[j] = (j < ht) ? a.h_up2[2 * j + 1] : 0.f;
+    }
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        fence_mbar_init();
+    }
+    for (int k = tid; k < H * SPIIR_UHIST; k += kCombThreads) {
+        const int i = 1 + k / SPIIR_UHIST, j = k % SPIIR_UHIST;
+        cbuf[comb_ubuf_off(chunk, i) + j] = hist[a.lev[i].ubuf_off + (int64_t)t * SPIIR_UHIST + j];
+    }
     __syncthreads();
-    if (t >= a.n_templates) return;
-    float2 *part = a.partial + (int64_t)s * a.partial_stream_stride;
-    float2 *ub = a.ubuf + (int64_t)s * a.ubuf_stream_stride;
-    for (int i = H; i >= 0; --i) {
-        const LevelArgs L = a.lev[i];
-        const int r0 = a.comb_ptr[t * a.n_levels + i], r1 = a.comb_ptr[t * a.n_levels + i + 1];
-        float2 *urow = (i > 0) ? ub + L.ubuf_off + (int64_t)t * L.ubuf_stride : nullptr;
-        float2 *ulow = nullptr;
-        int n_low = 0;
-        if (i < H) {
-            const LevelArgs Ll = a.lev[i + 1];
-            ulow = ub + Ll.ubuf_off + (int64_t)t * Ll.ubuf_stride;
-            n_low = Ll.n;
-        }
-        float2 *zrow = a.z + (int64_t)s * a.z_stream_stride + (int64_t)t * a.z_row_stride;
-        for (int n0 = lane * kCombOut; n0 < L.n; n0 += 32 * kCombOut) {
-            const int cnt = min(kCombOut, L.n - n0);
-            float re[kCombOut], im[kCombOut];
-#pragma unroll
-            for (int r = 0; r < kCombOut; ++r) re[r] = im[r] = 0.f;
-            for (int q = r0; q < r1; ++q) {
-                const float2 *pr = part + L.part_base + (int64_t)a.comb_rows[q] * L.part_stride + n0;
-#pragma unroll
-                for (int r = 0; r < kCombOut; ++r)
-                    if (r < cnt) {
-                        const float2 v = pr[r];
-                        re[r] += v.x;
-                        im[r] += v.y;
+
+    const int n0 = a.lev[0].n;
+    uint32_t phase = 0;
+    for (int c0 = 0; c0 < n0; c0 += chunk) {
+        const int cn = min(chunk, n0 - c0);
+        uint32_t bytes = 0;
+        for (int i = 0; i <= H; ++i)
+            if (cptr[i + 1] > cptr[i]) bytes += (uint32_t)(cn >> i) * 8u;
+        bool ok = true;
+        if (bytes) {
+            if (tid == 0) {
+                mbar_arrive_expect_tx(mbar, bytes);
+                for (int i = 0; i <= H; ++i)
+                    if (cptr[i + 1] > cptr[i]) {
+                        const LevelArgs &L = a.lev[i];
+                        bulk_g2s(cbuf + comb_stage_off(chunk, H, i),
+                                 part + L.part_base + (int64_t)a.comb_rows[cptr[i]] * L.part_stride +
+                                     (c0 >> i),
+                                 (uint32_t)(cn >> i) * 8u, mbar);
                     }
             }
-            if (ulow) {
-                switch (a.n_taps / 2) {
-                    case 16: combine_chunk<16>(ulow, h2, n0, re, im); break;
-                    case 8: combine_chunk<8>(ulow, h2, n0, re, im); break;
-                    case 32: combine_chunk<32>(ulow, h2, n0, re, im); break;
-                    default: {
-                        const int half = a.n_taps / 2;
-                        for (int r = 0; r < kCombOut; ++r) {
-                            const float2 *u = ulow + SPIIR_UHIST + ((n0 + r) >> 1);
-                            const int ph = (n0 + r) & 1;
-                            for (int j = 0; j < half; ++j) {
-                                re[r] = fmaf(h2[2 * j + ph], u[-j].x, re[r]);
-                                im[r] = fmaf(h2[2 * j + ph], u[-j].y, im[r]);
-                            }
-                        }
-                    }
+            ok = mbar_wait_bounded(mbar, phase, a.status);
+            phase ^= 1u;
+        }
+        if (!__syncthreads_and(ok)) {
+            // a copy did not land in time (status word set): wait once more,
+            // bounded, so that no copy is left writing this CTA's memory
+            mbar_wait_bounded(mbar, phase ^ 1u, a.status);
+            return;
+        }
+        for (int i = H; i >= 0; --i) {
+            const LevelArgs &L = a.lev[i];
+            const int ni = cn >> i, off = c0 >> i;
+            const int r0 = cptr[i], r1 = cptr[i + 1];
+            const float2 *pl = part + L.part_base + off;
+            const float4 *stg = reinterpret_cast<const float4 *>(cbuf + comb_stage_off(chunk, H, i));
+            float2 *u_hi = (i > 0) ? cbuf + comb_ubuf_off(chunk, i) + SPIIR_UHIST : nullptr;
+            const float2 *u_lo = (i < H) ? cbuf + comb_ubuf_off(chunk, i + 1) + SPIIR_UHIST : nullptr;
+            for (int q = tid; 4 * q < ni; q += kCombThreads) {
+                float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f), p1 = p0;
+                if (r1 > r0) {
+                    p0 = stg[2 * q];
+                    p1 = stg[2 * q + 1];
+                }
+                for (int r = r0 + 1; r < r1; ++r) {   // further parts (large units)
+                    const float4 *pr = reinterpret_cast<const float4 *>(
+                        pl + (int64_t)a.comb_rows[r] * L.part_stride + 4 * q);
+                    const float4 v0 = __ldg(pr), v1 = __ldg(pr + 1);
+                    p0.x += v0.x; p0.y += v0.y; p0.z += v0.z; p0.w += v0.w;
+                    p1.x += v1.x; p1.y += v1.y; p1.z += v1.z; p1.w += v1.w;
+                }
+                float2 o[4] = {make_float2(p0.x, p0.y), make_float2(p0.z, p0.w),
+                               make_float2(p1.x, p1.y), make_float2(p1.z, p1.w)};
+                if (u_lo) upsample_quad<HT>(u_lo, q, h0, h1, ht, o);
+                if (u_hi) {
+                    float4 *d = reinterpret_cast<float4 *>(u_hi + 4 * q);
+                    d[0] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+                    d[1] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
+                } else {
+                    const float sc = a.scale;
+                    float4 *d = reinterpret_cast<float4 *>(zrow + c0 + 4 * q);
+                    d[0] = make_float4(sc * o[0].x, sc * o[0].y, sc * o[1].x, sc * o[1].y);
+                    d[1] = make_float4(sc * o[2].x, sc * o[2].y, sc * o[3].x, sc * o[3].y);
                 }
             }
-            if (i > 0) {
+            __syncthreads();
+        }
+        // keep the last SPIIR_UHIST samples of every level as its history
+        constexpr int kPer = (SPIIR_MAX_LEVELS * SPIIR_UHIST + kCombThreads - 1) / kCombThreads;
+        float2 keep[kPer];
 #pragma unroll
-                for (int r = 0; r < kCombOut; ++r)
-                    if (r < cnt) urow[SPIIR_UHIST + n0 + r] = make_float2(re[r], im[r]);
-            } else {
-#pragma unroll
-                for (int r = 0; r < kCombOut; ++r)
-                    if (r < cnt) zrow[n0 + r] = make_float2(a.scale * re[r], a.scale * im[r]);
+        for (int e = 0; e < kPer; ++e) {
+            const int k = tid + e * kCombThreads;
+            if (k < H * SPIIR_UHIST) {
+                const int i = 1 + k / SPIIR_UHIST, j = k % SPIIR_UHIST;
+                keep[e] = cbuf[comb_ubuf_off(chunk, i) + (cn >> i) + j];
             }
         }
-        __syncwarp();
-        if (ulow) {
-            // keep the last SPIIR_UHIST samples of the lower rate as history
-            for (int c0 = 0; c0 < SPIIR_UHIST; c0 += n_low) {
-                const int len = min(n_low, SPIIR_UHIST - c0);
-                float2 v[(SPIIR_UHIST + 31) / 32];
+        __syncthreads();
 #pragma unroll
-                for (int j = 0; j < (SPIIR_UHIST + 31) / 32; ++j) {
-                    const int k = lane + 32 * j;
-                    if (k < len) v[j] = ulow[c0 + n_low + k];
-                }
-                __syncwarp();
-#pragma unroll
-                for (int j = 0; j < (SPIIR_UHIST + 31) / 32; ++j) {
-                    const int k = lane + 32 * j;
-                    if (k < len) ulow[c0 + k] = v[j];
-                }
-                __syncwarp();
+        for (int e = 0; e < kPer; ++e) {
+            const int k = tid + e * kCombThreads;
+            if (k < H * SPIIR_UHIST) {
+                const int i = 1 + k / SPIIR_UHIST, j = k % SPIIR_UHIST;
+                cbuf[comb_ubuf_off(chunk, i) + j] = keep[e];
             }
         }
+        __syncthreads();
+    }
+    for (int k = tid; k < H * SPIIR_UHIST; k += kCombThreads) {
+        const int i = 1 + k / SPIIR_UHIST, j = k % SPIIR_UHIST;
+        hist[a.lev[i].ubuf_off + (int64_t)t * SPIIR_UHIST + j] = cbuf[comb_ubuf_off(chunk, i) + j];
     }
 }
 
@@ -685,8 +753,37 @@ cudaError_t spiir_launch_recur(const RecurArgs &a, int variant, int n_ctas, int 
     return cudaGetLastError();
 }
 
-cudaError_t spiir_launch_combine(const CombineArgs &a, int n_streams, cudaStream_t s) {
-    combine_kernel<<<dim3((a.n_templates + kCombWarps - 1) / kCombWarps, n_streams), kCombWarps * 32,
-                     0, s>>>(a);
+int spiir_combine_chunk(int n_levels, int64_t push_max) {
+    const int64_t c = std::max<int64_t>(2048, (int64_t)4 << (n_levels - 1));
+    return (int)std::min<int64_t>(c, push_max);
+}
+
+int spiir_combine_smem(int n_levels, int chunk) {
+    const int H = n_levels - 1;
+    return 16 + comb_stage_off(chunk, H, H + 1) * (int)sizeof(float2);
+}
+
+cudaError_t spiir_launch_combine(const CombineArgs &a, int chunk, int n_streams, cudaStream_t s) {
+    const int smem = spiir_combine_smem(a.n_levels, chunk);
+    const dim3 grid(a.n_templates, n_streams);
+    const int ht = a.n_taps / 2;
+    switch (a.n_levels > 1 ? ht : 0) {
+        case 8: combine_kernel<8><<<grid, kCombThreads, smem, s>>>(a, chunk); break;
+        case 16: combine_kernel<16><<<grid, kCombThreads, smem, s>>>(a, chunk); break;
+        case 32: combine_kernel<32><<<grid, kCombThreads, smem, s>>>(a, chunk); break;
+        default: combine_kernel<-1><<<grid, kCombThreads, smem, s>>>(a, chunk); break;
+    }
     return cudaGetLastError();
+}
+
+cudaError_t spiir_combine_prepare() {
+    // like the recursion kernel: one kernel-wide limit, the device maximum
+    int dev = 0, optin = 0;
+    cudaError_t r = cudaGetDevice(&dev);
+    if (r == cudaSuccess) r = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const void *fns[] = {(const void *)combine_kernel<8>, (const void *)combine_kernel<16>,
+                         (const void *)combine_kernel<32>, (const void *)combine_kernel<-1>};
+    for (const void *f : fns)
+        if (r == cudaSuccess) r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    return r;
 }
