@@ -132,6 +132,18 @@ struct Unit {
     int32_t dest;
 };
 
+// A push of n base-rate samples is cut into S time segments (S the smallest
+// power of two with S * 4096 >= n); level i's segments are segment_len
+// samples long (a multiple of 4, at most max(4096 >> i, 4)), so at the lower
+// rates the last segments may be short or empty.
+int push_segments_n(int64_t n) {
+    int S = 1;
+    while ((int64_t)S * 4096 < n) S *= 2;
+    return S;
+}
+
+int64_t segment_len(int64_t n, int i, int S) { return round_up(((n >> i) + S - 1) / S, 4); }
+
 int64_t align_delay(int level, int n_levels, int n_taps, int align) {
     if (!align) return 0;
     int64_t D = 0;
@@ -251,9 +263,8 @@ spiir_status make_plan(const spiir_bank_desc *d, int variant, bool arrays, Plan 
         p.hist[i] = (int)h;
         p.max_delay = std::max<int>(p.max_delay, (int)(maxd[i] + D));
         p.max_n[i] = push_max >> i;
-        // a push is cut into time segments of at most ~4096 base-rate samples
-        // (see push_plain); the window holds the history plus one segment
-        const int64_t sg = std::min<int64_t>(round_up(p.max_n[i], 4), (4096 >> i) + 8);
+        // the window holds the history plus the longest segment
+        const int64_t sg = std::min<int64_t>(round_up(p.max_n[i], 4), round_up(std::max(4096 >> i, 4), 4));
         p.seg[i] = (int)sg;
         p.smem_bytes = std::max<int>(p.smem_bytes,
                                      (int)(16 + spiir_recur_red_bytes() + 4 * (h + sg) + 64));
@@ -656,12 +667,7 @@ spiir_status alloc_plain(spiir_bank *b, cudaStream_t s) {
 
 // Time segments per push: about 4096 base-rate samples each, a power of two,
 // at least 4 samples at the lowest level.
-int push_segments(const Plan &p, int64_t n) {
-    int S = 1;
-    while ((int64_t)S * 4096 < n) S *= 2;
-    while (S > 1 && ((n >> p.H) / S) < 4) S /= 2;
-    return S;
-}
+int push_segments(const Plan &, int64_t n) { return push_segments_n(n); }
 
 void level_args(const spiir_bank *b, int64_t n, int64_t n_prev, LevelArgs *lev) {
     const Plan &p = b->p;
@@ -670,7 +676,7 @@ void level_args(const spiir_bank *b, int64_t n, int64_t n_prev, LevelArgs *lev) 
         LevelArgs &L = lev[i];
         L.hist = p.hist[i];
         L.n = (int32_t)(n >> i);
-        L.seg = (int32_t)round_up(((n >> i) + S - 1) / S, 4);
+        L.seg = (int32_t)segment_len(n, i, S);
         L.n_prev = (int32_t)(n_prev >> i);
         L.part_base = p.part_base[i];
         L.part_stride = p.part_stride[i];

@@ -120,6 +120,44 @@ def test_multirate_custom_taps_and_empty_levels(torch_cuda, oracle_mod):
     assert err.max() <= TOL_PLAIN, err
 
 
+def test_multirate_twelve_rates(torch_cuda, oracle_mod):
+    """The deepest cascade (12 rates, 4096 Hz down to 2 Hz): the combine
+    works in time chunks of 8192 samples, one per push here. Without the
+    alignment delays: aligned, the base rate would wait 31 * (2^11 - 1)
+    samples, more than a shared-memory strain window holds."""
+    bank = inputs.multi_rate_bank(6, 12, seed=4, count_range=(2.0, 60.0), delay_max=300)
+    x = inputs.strain(1, 3 * 8192, seed=9)
+    z = gpu_snr(bank, x, block_len=8192, push_blocks=1, align=False)[0]
+    ref = oracle_mod.spiir_multirate(bank, x[0], align=False)
+    err = rel_rms(z, ref)
+    assert err.max() <= TOL_PLAIN, err
+
+
+def test_multirate_uneven_pushes_span_chunks(torch_cuda, oracle_mod):
+    """Pushes of 3 and 2 blocks of 1024: the first push spans two combine
+    time chunks (2048 + 1024 samples), so the upsampler history carries both
+    inside a push and across pushes."""
+    bank = inputs.multi_rate_bank(10, 5, seed=8, delay_max=400)
+    x = inputs.strain(1, 5 * 1024, seed=10)
+    z = gpu_snr(bank, x, block_len=1024, push_blocks=3)[0]
+    ref = oracle_mod.spiir_multirate(bank, x[0])
+    err = rel_rms(z, ref)
+    assert err.max() <= TOL_PLAIN, err
+
+
+@pytest.mark.parametrize("n_taps", [6, 64])
+def test_multirate_interpolator_lengths(torch_cuda, oracle_mod, n_taps):
+    """Interpolators of 3 and 32 taps per polyphase branch (the generic and the
+    longest unrolled combine paths)."""
+    bank = inputs.multi_rate_bank(8, 4, seed=5, delay_max=300)
+    h = oracle_mod.kaiser_taps(n_taps, 60.0)
+    x = inputs.strain(1, 3 * 1024, seed=11)
+    z = gpu_snr(bank, x, block_len=1024, push_blocks=1, h_down=h, h_up=h)[0]
+    ref = oracle_mod.spiir_multirate(bank, x[0], h_down=h, h_up=h)
+    err = rel_rms(z, ref)
+    assert err.max() <= TOL_PLAIN, err
+
+
 def test_multirate_full_size_sampled(torch_cuda, oracle_mod):
     """Config 2 at full size (4000 templates, 7 rates), 4 s pushed in 1 s
     blocks; 12 seeded templates against the oracle."""
