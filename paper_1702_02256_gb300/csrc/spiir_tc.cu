@@ -492,262 +492,417 @@ __global__ void __launch_bounds__(192, 1) tc_fir_kernel(const TcFirArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Carry kernel: persistent over templates, two CTAs per SM so that one CTA's
-// FP64 recurrence overlaps the other's panel generation and contractions.
-// Per template and group of up to kBatchGroup chunk batches:
-//   for each 128-filter tile: generate R = a_k^i once, then per batch
-//     STATE MMA -> FP64 carry (thread = filter, stream) -> OUTPUT MMA
-//   epilogue: z += scale * OUTPUT, per batch.
+// Carry kernel: one CTA per SM, persistent over templates. A CTA's work is a
+// sequence of jobs (template, group of up to kBatchGroup chunk batches,
+// 128-filter tile), pipelined over warp roles:
+//   warp 0, lane 0   issues the STATE and OUTPUT contractions, running one job
+//                    ahead (STATE of job j before OUTPUT of job j-1), and the
+//                    bulk copies of the strain segments
+//   warps 1-4        power panel R[k][i] = a_k^i of job j into buffer j % 2
+//   warps 5-8, 9-12  carry groups 0 and 1: jobs with j % 2 = group; STATE
+//                    (tensor memory) -> FP32 carry inside a batch, FP64 from
+//                    batch to batch -> OUTPUT operand W in shared memory
+//   warps 13-16      epilogue: OUTPUT accumulators -> z, per (template, group)
+// Every hand-off is an mbarrier: tcgen05.commit for contractions, one arrive
+// per thread for the 128-thread roles; every wait is bounded and gives up at
+// once when another role has given up.
+// Tensor memory (512 columns): STATE of carry group g at 128 g (64 columns
+// per batch: 32 re, 32 im); OUTPUT of (template, group) e at 256 + 128 (e%2)
+// (64 columns per batch).
 // ---------------------------------------------------------------------------
 
-constexpr int kCarrySmem = 65536 + kBatchGroup * kXsegBytes + 2 * (2 * kNii) * kJ * 2;
+constexpr int kCarryWarps = 17;
+constexpr int kPanelBytes = 2 * kTile * kJ * 2;                 // Pr + Pi: 64 KB
+constexpr int kWBytes = 2 * (2 * kNii) * kJ * 2;                // W1 + W2: 32 KB
+constexpr int kCarrySmem = 2 * kPanelBytes + kBatchGroup * kXsegBytes + 2 * kWBytes;   // 208 KB
 
-template <bool BF16>
-__global__ void __launch_bounds__(256, 2) tc_carry_kernel(const TcCarryArgs a) {
+__device__ __forceinline__ void mbar_arrive(uint64_t *m) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s32(m)) : "memory");
+}
+
+// Bounded wait that also gives up when *abort is set; a timeout sets *abort.
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t *m, uint32_t ph, unsigned int *status,
+                                             volatile int *abort) {
+    if (mbar_try(m, ph)) return true;
+    const uint64_t t0 = gtime();
+    while (!mbar_try(m, ph)) {
+        if (*abort) return false;
+        if (gtime() - t0 > 2000000000ull) {
+            atomicExch(status, SPIIR_DEV_TIMEOUT);
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+struct CarryJob {
+    int t, b0, nbg, tile;
+    bool first_tile, last_tile;
+    int j, e;   // job index and (template, group) index within this CTA
+    int g;      // pipeline slot: panel buffer, carry group, STATE columns, W buffer
+};
+
+// The job sequence of this CTA; fn returns false to stop. Jobs alternate
+// between the two pipeline slots. When a template has several groups of
+// batches, the filter state v of a tile passes from one group to the next, so
+// a tile keeps its slot (and so its carry threads) for all of them.
+template <class Fn>
+__device__ __forceinline__ void carry_jobs(const TcCarryArgs &a, Fn &&fn) {
+    int j = 0, e = 0;
+    const bool multi = a.n_batches > kBatchGroup;
+    for (int ti = blockIdx.x; ti < a.n_carry; ti += gridDim.x) {
+        const int t = a.tmpl_of[ti];
+        const int tile0 = a.tile_ptr[t], tile1 = a.tile_ptr[t + 1];
+        for (int b0 = 0; b0 < a.n_batches; b0 += kBatchGroup, ++e) {
+            const int nbg = min(kBatchGroup, a.n_batches - b0);
+            for (int tile = tile0; tile < tile1; ++tile, ++j) {
+                const int g = multi ? ((tile - tile0) & 1) : (j & 1);
+                if (!fn(CarryJob{t, b0, nbg, tile, tile == tile0, tile == tile1 - 1, j, e, g})) return;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ float2 cmul(float2 x, float2 y) {
+    return make_float2(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x);
+}
+
+template <bool BF16, int LJ>
+__global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcCarryArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t mb, xb;
+    __shared__ uint64_t panel_full[2], panel_free[2], state_full[2], state_free[2], w_full[2],
+        w_free[2], out_full[2], out_free[2], xs_bar, drain;
     __shared__ uint32_t s_tmem;
-    const int L = a.L, LJ = L / kJ;
+    __shared__ int s_abort;
+    unsigned char *Xs = smem + 2 * kPanelBytes;                    // kBatchGroup x 8 KB
+    unsigned char *Wb = Xs + kBatchGroup * kXsegBytes;             // 2 x (W1, W2)
+    constexpr uint32_t kWSbo = 16 * 128;                           // 8 rows x 16 k-blocks
+    const int L = LJ * kJ;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char *Pr = smem;
-    unsigned char *Pi = smem + 32768;
-    unsigned char *Xs = smem + 65536;                              // kBatchGroup x 8 KB
-    unsigned char *W1 = Xs + kBatchGroup * kXsegBytes;            // 64 rows x 128 K
-    unsigned char *W2 = W1 + (2 * kNii) * kJ * 2;
-    constexpr uint32_t kWSbo = 16 * 128;                          // 8 rows x 16 k-blocks
+    const int S = a.n_streams;
+    volatile int *abort = &s_abort;
 
     if (threadIdx.x == 0) {
-        mbar_init(&mb, 1);
-        mbar_init(&xb, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&panel_full[i], 128);
+            mbar_init(&panel_free[i], 1);
+            mbar_init(&state_full[i], 1);
+            mbar_init(&state_free[i], 128);
+            mbar_init(&w_full[i], 128);
+            mbar_init(&w_free[i], 1);
+            mbar_init(&out_full[i], 1);
+            mbar_init(&out_free[i], 128);
+        }
+        mbar_init(&xs_bar, 1);
+        mbar_init(&drain, 1);
+        s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) tmem_alloc(&s_tmem, 256);
+    if (warp == 0) tmem_alloc(&s_tmem, 512);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = s_tmem;          // STATE re [0,32) im [32,64); OUTPUT [64 + 64 b, ...)
-    uint32_t ph = 0, phx = 0;
-    int loaded_b0 = -1;
-    bool ok = true;
-    const int S = a.n_streams;
+    const uint32_t tmem = s_tmem;
 
-    for (int ti = blockIdx.x; ti < a.n_carry && ok; ti += gridDim.x) {
-        const int t = a.tmpl_of[ti];
-        const int tile0 = a.tile_ptr[t], tile1 = a.tile_ptr[t + 1];
-        for (int b0 = 0; b0 < a.n_batches && ok; b0 += kBatchGroup) {
-            const int nbg = min(kBatchGroup, a.n_batches - b0);
-            // the strain segments do not depend on the template: load them
-            // again only when this CTA moves to another group of batches
-            const bool reload = (b0 != loaded_b0);
-            if (reload && threadIdx.x == 0) {
-                mbar_expect(&xb, nbg * kXsegBytes);
-                bulk_load(Xs, a.xseg + (size_t)b0 * (kXsegBytes / 16), nbg * kXsegBytes, &xb);
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            uint32_t n_pf[2] = {0, 0}, n_sf[2] = {0, 0}, n_wf[2] = {0, 0}, n_of[2] = {0, 0};
+            uint32_t ph_x = 0, ph_d = 0;
+            int loaded_b0 = -1;
+            bool ok = true, have_prev = false;
+            CarryJob prev{};
+            bool issued = false;
+            auto output = [&](const CarryJob &P) -> bool {
+                const int g = P.g, ob = P.e & 1;
+                if (P.first_tile && P.e >= 2) {
+                    if (!mbar_wait_ab(&out_free[ob], n_of[ob] & 1, a.status, abort)) return false;
+                    ++n_of[ob];
+                }
+                const unsigned char *Pr = smem + g * kPanelBytes, *Pi = Pr + kPanelBytes / 2;
+                const unsigned char *W1 = Wb + g * kWBytes, *W2 = W1 + kWBytes / 2;
+                const uint32_t id = idesc(128, 2 * kNii, BF16, true, false);
+                for (int bi = 0; bi < P.nbg; ++bi) {
+                    if (!mbar_wait_ab(&w_full[g], n_wf[g] & 1, a.status, abort)) return false;
+                    ++n_wf[g];
+                    tc_fence_after();
+                    const uint32_t dz = tmem + 256 + 128 * ob + 64 * bi;
+                    for (int kk = 0; kk < kTile / 16; ++kk) {
+                        const uint32_t acc = (!P.first_tile || kk) ? 1u : 0u;
+                        const uint64_t ar = sdesc(s32(Pr) + kk * 2 * 2048, 2048, 128);
+                        const uint64_t ai = sdesc(s32(Pi) + kk * 2 * 2048, 2048, 128);
+                        mma(dz, ar, sdesc(s32(W1) + kk * 2 * 128, 128, kWSbo), id, acc);
+                        mma(dz, ai, sdesc(s32(W2) + kk * 2 * 128, 128, kWSbo), id, 1u);
+                    }
+                    mma_commit(&w_free[g]);
+                }
+                mma_commit(&panel_free[g]);
+                if (P.last_tile) mma_commit(&out_full[ob]);
+                return true;
+            };
+            carry_jobs(a, [&](const CarryJob &J) -> bool {
+                const int g = J.g;
+                if (J.b0 != loaded_b0) {
+                    // the STATE contractions that read the old segments are done
+                    if (issued) {
+                        mma_commit(&drain);
+                        ok = mbar_wait_ab(&drain, ph_d, a.status, abort);
+                        ph_d ^= 1u;
+                        if (!ok) return false;
+                    }
+                    mbar_expect(&xs_bar, J.nbg * kXsegBytes);
+                    bulk_load(Xs, a.xseg + (size_t)J.b0 * (kXsegBytes / 16), J.nbg * kXsegBytes, &xs_bar);
+                    ok = mbar_wait_ab(&xs_bar, ph_x, a.status, abort);
+                    ph_x ^= 1u;
+                    if (!ok) return false;
+                    loaded_b0 = J.b0;
+                }
+                // two jobs in a row on one slot: the earlier one's OUTPUT frees
+                // the slot's panel, so it cannot wait behind this job's STATE
+                if (have_prev && prev.g == g) {
+                    have_prev = false;
+                    if (!(ok = output(prev))) return false;
+                }
+                ok = mbar_wait_ab(&panel_full[g], n_pf[g] & 1, a.status, abort);
+                ++n_pf[g];
+                if (ok && n_pf[g] >= 2) {       // slot g was used before
+                    ok = mbar_wait_ab(&state_free[g], n_sf[g] & 1, a.status, abort);
+                    ++n_sf[g];
+                }
+                if (!ok) return false;
+                tc_fence_after();
+                const unsigned char *Pr = smem + g * kPanelBytes, *Pi = Pr + kPanelBytes / 2;
+                const uint32_t id = idesc(128, kNii, BF16, false, false);
+                for (int bi = 0; bi < J.nbg; ++bi) {
+                    const uint32_t xs = s32(Xs + bi * kXsegBytes);
+                    const uint32_t d = tmem + 128 * g + 64 * bi;
+                    for (int kk = 0; kk < kJ / 16; ++kk) {
+                        const uint64_t bd = sdesc(xs + kk * 256, 128, 2048);
+                        mma(d, sdesc(s32(Pr) + kk * 256, 128, 2048), bd, id, kk ? 1u : 0u);
+                        mma(d + kNii, sdesc(s32(Pi) + kk * 256, 128, 2048), bd, id, kk ? 1u : 0u);
+                    }
+                }
+                mma_commit(&state_full[g]);
+                issued = true;
+                if (have_prev && !(ok = output(prev))) return false;
+                prev = J;
+                have_prev = true;
+                return true;
+            });
+            if (ok && have_prev) ok = output(prev);
+            // nothing may still run when the tensor memory is released
+            if (issued) {
+                mma_commit(&drain);
+                mbar_wait(&drain, ph_d, a.status);
             }
-            for (int tile = tile0; tile < tile1 && ok; ++tile) {
-                // power panel R[k][i] = a_k^i: rows = filters, K = powers,
-                // layout [k/8][i/8][k%8][i%8]; thread = (filter, half of the
-                // powers) running four independent chains of 16 powers
-                {
-                    const int k = threadIdx.x & 127, h = threadIdx.x >> 7;
-                    const int64_t slot = (int64_t)tile * kTile + k;
-                    const float2 ak = a.a[slot];
-                    float2 a16 = ak;
+        }
+    } else if (warp <= 4) {
+        // ---------------- power panels ----------------
+        // thread = filter k: R[k][i] = a_k^i, i < 128, as four chains of 16
+        // powers per half (the second half starts from a_k^64); layout
+        // [k/8][i/8][k%8][i%8]
+        const int k = threadIdx.x - 32;
+        uint32_t use[2] = {0, 0};
+        carry_jobs(a, [&](const CarryJob &J) -> bool {
+            const int g = J.g;
+            if (use[g] > 0 && !mbar_wait_ab(&panel_free[g], (use[g] - 1) & 1, a.status, abort))
+                return false;
+            ++use[g];
+            unsigned char *Pr = smem + g * kPanelBytes, *Pi = Pr + kPanelBytes / 2;
+            const int64_t slot = (int64_t)J.tile * kTile + k;
+            const float2 ak = a.a[slot], a64 = a.a64[slot];
+            float2 a16 = ak;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        a16 = make_float2(a16.x * a16.x - a16.y * a16.y, 2.f * a16.x * a16.y);
-                    float2 p[4];
-                    p[0] = h ? a.a64[slot] : make_float2(1.f, 0.f);
+            for (int i = 0; i < 4; ++i) a16 = cmul(a16, a16);
 #pragma unroll
-                    for (int i = 1; i < 4; ++i)
-                        p[i] = make_float2(p[i - 1].x * a16.x - p[i - 1].y * a16.y,
-                                           p[i - 1].x * a16.y + p[i - 1].y * a16.x);
-                    for (int ib = 0; ib < 2; ++ib) {
-                        float vr[4][8], vi[4][8];
+            for (int h = 0; h < 2; ++h) {
+                float2 p[4];
+                p[0] = h ? a64 : make_float2(1.f, 0.f);
+#pragma unroll
+                for (int i = 1; i < 4; ++i) p[i] = cmul(p[i - 1], a16);
+#pragma unroll
+                for (int ib = 0; ib < 2; ++ib) {
+#pragma unroll
+                    for (int c2 = 0; c2 < 4; c2 += 2) {     // two chains at a time
+                        float vr[2][8], vi[2][8];
 #pragma unroll
                         for (int q = 0; q < 8; ++q) {
 #pragma unroll
-                            for (int ch = 0; ch < 4; ++ch) {
-                                vr[ch][q] = p[ch].x;
-                                vi[ch][q] = p[ch].y;
-                                p[ch] = make_float2(p[ch].x * ak.x - p[ch].y * ak.y,
-                                                    p[ch].x * ak.y + p[ch].y * ak.x);
+                            for (int ch = 0; ch < 2; ++ch) {
+                                vr[ch][q] = p[c2 + ch].x;
+                                vi[ch][q] = p[c2 + ch].y;
+                                p[c2 + ch] = cmul(p[c2 + ch], ak);
                             }
                         }
 #pragma unroll
-                        for (int ch = 0; ch < 4; ++ch) {
-                            const int kb = h * 8 + ch * 2 + ib;
+                        for (int ch = 0; ch < 2; ++ch) {
+                            const int kb = h * 8 + (c2 + ch) * 2 + ib;
                             const size_t off = (size_t)(k >> 3) * 2048 + kb * 128 + (k & 7) * 16;
                             *reinterpret_cast<uint4 *>(Pr + off) = pack8<BF16>(vr[ch]);
                             *reinterpret_cast<uint4 *>(Pi + off) = pack8<BF16>(vi[ch]);
                         }
                     }
                 }
-                fence_async_smem();
-                tc_fence_before();
-                __syncthreads();
-                tc_fence_after();
-                if (tile == tile0 && reload) {
-                    ok = mbar_wait(&xb, phx, a.status);
-                    phx ^= 1u;
-                    loaded_b0 = b0;
-                }
-                // carry thread state: filter k (tensor-memory lane), stream ss
-                const int k = threadIdx.x & 127, ss = threadIdx.x >> 7;
-                const int64_t slot = (int64_t)tile * kTile + k;
-                const bool act = ss < S;
-                const float2 ak = a.a[slot], aJ = a.aJ[slot], ck = a.c[slot], aLf = a.aLf[slot];
-                double2 v = act ? a.v[(int64_t)(a.stream0 + ss) * a.n_slots + slot] : make_double2(0, 0);
-                const uint32_t lane_base = ((uint32_t)((warp & 3) * 32)) << 16;
-                for (int bi = 0; bi < nbg && ok; ++bi) {
-                    const int b = b0 + bi;
-                    const int nb = min(a.cpb, a.n_chunks - b * a.cpb);
-                    const int nii = S * nb * LJ;
-                    const int niv = 2 * nii;
-                    // STATE: tmem cols [0, 32) re, [32, 64) im
-                    if (threadIdx.x == 0) {
-                        const uint32_t id = idesc(128, kNii, BF16, false, false);
-                        const uint32_t xs = s32(Xs + bi * kXsegBytes);
-                        for (int kk = 0; kk < kJ / 16; ++kk) {
-                            const uint64_t bd = sdesc(xs + kk * 256, 128, 2048);
-                            mma(tmem, sdesc(s32(Pr) + kk * 256, 128, 2048), bd, id, kk ? 1u : 0u);
-                            mma(tmem + kNii, sdesc(s32(Pi) + kk * 256, 128, 2048), bd, id, kk ? 1u : 0u);
-                        }
-                        mma_commit(&mb);
-                    }
-                    __syncwarp();
-                    ok = mbar_wait(&mb, ph, a.status);
-                    ph ^= 1u;
-                    tc_fence_after();
-                    // Carry across this batch. The batch's starting state v is
-                    // FP64; chunk states inside the batch are FP32:
-                    //   v_c = a^(cL) v + d_c,  d_{c+1} = a^L d_c + U_c,  d_0 = 0,
-                    // and the next batch starts from a^(nb L) v + d_nb in FP64.
-                    float pr = (float)v.x, pi = (float)v.y;     // a^(cL) v
-                    float dr = 0.f, di = 0.f;                    // d_c
-                    for (int c0 = 0; c0 < nb * LJ; c0 += 16) {
-                        float gr[16], gi[16];
-                        const int colb = (act ? ss : 0) * nb * LJ + c0;
-                        tmem_ld16(tmem + lane_base + colb, gr);
-                        tmem_ld16(tmem + lane_base + kNii + colb, gi);
-                        if (act) {
-                            for (int q = 0; q < 16 && c0 + q < nb * LJ; q += LJ) {
-                                float ur = gr[q + LJ - 1], ui = gi[q + LJ - 1];
-                                for (int i2 = LJ - 2; i2 >= 0; --i2) {
-                                    const float nr = ur * aJ.x - ui * aJ.y + gr[q + i2];
-                                    const float ni = ur * aJ.y + ui * aJ.x + gi[q + i2];
-                                    ur = nr;
-                                    ui = ni;
-                                }
-                                const int cc = (c0 + q) / LJ;
-                                const float vr = pr + dr, vi = pi + di;
-                                const float sr = ck.x * vr - ck.y * vi, si = ck.x * vi + ck.y * vr;
-                                float wr = ak.x * sr - ak.y * si, wi = ak.x * si + ak.y * sr;
-                                const float ndr = aLf.x * dr - aLf.y * di + ur;
-                                const float ndi = aLf.x * di + aLf.y * dr + ui;
-                                dr = ndr;
-                                di = ndi;
-                                const float npr = aLf.x * pr - aLf.y * pi;
-                                const float npi = aLf.x * pi + aLf.y * pr;
-                                pr = npr;
-                                pi = npi;
-                                for (int j2 = 0; j2 < LJ; ++j2) {
-                                    const int n = ((ss * nb + cc) * LJ + j2) * 2;
-                                    const size_t o0 = (size_t)(n >> 3) * kWSbo + (k >> 3) * 128 +
-                                                      (n & 7) * 16 + (k & 7) * 2;
-                                    const size_t o1 = (size_t)((n + 1) >> 3) * kWSbo + (k >> 3) * 128 +
-                                                      ((n + 1) & 7) * 16 + (k & 7) * 2;
-                                    *reinterpret_cast<uint16_t *>(W1 + o0) = to16<BF16>(wr);
-                                    *reinterpret_cast<uint16_t *>(W1 + o1) = to16<BF16>(wi);
-                                    *reinterpret_cast<uint16_t *>(W2 + o0) = to16<BF16>(-wi);
-                                    *reinterpret_cast<uint16_t *>(W2 + o1) = to16<BF16>(wr);
-                                    const float nr = wr * aJ.x - wi * aJ.y, ni = wr * aJ.y + wi * aJ.x;
-                                    wr = nr;
-                                    wi = ni;
-                                }
-                            }
-                        }
-                    }
-                    if (act) {
-                        // v <- a^(nb L) v + d_nb in FP64
-                        double2 pw;
-                        if (nb == a.cpb) {
-                            pw = a.aLb[slot];
-                        } else {
-                            const double2 aL = a.aL[slot];
-                            pw = aL;
-                            for (int i = 1; i < nb; ++i)
-                                pw = make_double2(pw.x * aL.x - pw.y * aL.y, pw.x * aL.y + pw.y * aL.x);
-                        }
-                        const double nvr = fma(pw.x, v.x, fma(-pw.y, v.y, (double)dr));
-                        const double nvi = fma(pw.x, v.y, fma(pw.y, v.x, (double)di));
-                        v = make_double2(nvr, nvi);
-                    }
-                    for (int n = niv + (threadIdx.x >> 7); n < 2 * kNii; n += 2) {
-                        const size_t o = (size_t)(n >> 3) * kWSbo + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
-                        *reinterpret_cast<uint16_t *>(W1 + o) = 0;
-                        *reinterpret_cast<uint16_t *>(W2 + o) = 0;
-                    }
-                    fence_async_smem();
-                    tc_fence_before();
-                    __syncthreads();
-                    tc_fence_after();
-                    // OUTPUT: D[j1][n] (+)= R^T(re) W1 + R^T(im) W2 into cols [64 + 64 bi, ...)
-                    if (threadIdx.x == 0) {
-                        const uint32_t id = idesc(128, 2 * kNii, BF16, true, false);
-                        const uint32_t dz = tmem + 64 + 64 * bi;
-                        for (int kk = 0; kk < kTile / 16; ++kk) {
-                            const uint32_t acc = (tile != tile0 || kk) ? 1u : 0u;
-                            const uint64_t ar = sdesc(s32(Pr) + kk * 2 * 2048, 2048, 128);
-                            const uint64_t ai = sdesc(s32(Pi) + kk * 2 * 2048, 2048, 128);
-                            mma(dz, ar, sdesc(s32(W1) + kk * 2 * 128, 128, kWSbo), id, acc);
-                            mma(dz, ai, sdesc(s32(W2) + kk * 2 * 128, 128, kWSbo), id, 1u);
-                        }
-                        mma_commit(&mb);
-                    }
-                    __syncwarp();
-                    ok = ok && mbar_wait(&mb, ph, a.status);
-                    ph ^= 1u;
-                    tc_fence_after();
-                }
-                if (act) a.v[(int64_t)(a.stream0 + ss) * a.n_slots + slot] = v;
             }
-            // epilogue: lane j1, columns (s, c, j2, re/im) -> z = scale * value
-            // (the FIR kernel adds its term afterwards)
-            if (tile1 > tile0) {
-                const int j1 = threadIdx.x & 127, half = threadIdx.x >> 7;
-                const uint32_t lane_base = ((uint32_t)((warp & 3) * 32)) << 16;
-                for (int bi = 0; bi < nbg; ++bi) {
-                    const int b = b0 + bi;
-                    const int nb = min(a.cpb, a.n_chunks - b * a.cpb);
-                    const int niv = 2 * S * nb * LJ;
-                    for (int c0 = half * 16; c0 < 2 * kNii; c0 += 32) {
-                        float vv[16];
-                        tmem_ld16(tmem + lane_base + 64 + 64 * bi + c0, vv);
-                        if (ok) {
+            fence_async_smem();
+            mbar_arrive(&panel_full[g]);
+            return true;
+        });
+    } else if (warp <= 12) {
+        // ---------------- carry groups ----------------
+        const int grp = (warp - 5) >> 2;
+        const int k = (warp & 3) * 32 + lane;                 // tensor-memory lane = filter
+        const uint32_t lane_base = ((uint32_t)((warp & 3) * 32)) << 16;
+        const size_t kofs = (size_t)(k >> 3) * 128 + (k & 7) * 2;
+        uint32_t n_state = 0, n_w = 0;
+        carry_jobs(a, [&](const CarryJob &J) -> bool {
+            if (J.g != grp) return true;
+            const int64_t slot = (int64_t)J.tile * kTile + k;
+            const float2 ak = a.a[slot], aJ = a.aJ[slot], ck = a.c[slot], aLf = a.aLf[slot];
+            double2 v0 = a.v[(int64_t)a.stream0 * a.n_slots + slot];
+            double2 v1 = S > 1 ? a.v[(int64_t)(a.stream0 + 1) * a.n_slots + slot] : make_double2(0, 0);
+            if (!mbar_wait_ab(&state_full[grp], n_state & 1, a.status, abort)) return false;
+            ++n_state;
+            tc_fence_after();
+            unsigned char *W1 = Wb + grp * kWBytes, *W2 = W1 + kWBytes / 2;
+            for (int bi = 0; bi < J.nbg; ++bi) {
+                const int b = J.b0 + bi;
+                const int nb = min(a.cpb, a.n_chunks - b * a.cpb);
+                const int nsteps = S * nb;                          // (stream, chunk) steps
+                // STATE columns: (stream, chunk, i2) -> (s nb + c) LJ + i2, read
+                // 16 at a time (16 / LJ steps)
+                const uint32_t tb = tmem + lane_base + 128 * grp + 64 * bi;
+                if (n_w > 0 && !mbar_wait_ab(&w_free[grp], (n_w - 1) & 1, a.status, abort)) return false;
+                ++n_w;
+                // Carry across this batch. The batch's starting state v is
+                // FP64; chunk states inside the batch are FP32:
+                //   v_c = a^(cL) v + d_c,  d_{c+1} = a^L d_c + U_c,  d_0 = 0,
+                // and the next batch starts from a^(nb L) v + d_nb in FP64.
+                float2 p = make_float2((float)v0.x, (float)v0.y);   // a^(cL) v
+                float2 dd = make_float2(0.f, 0.f);                   // d_c
+                float2 d_s0 = dd;
+                constexpr int kSteps = 16 / LJ;                       // steps per 16 columns
 #pragma unroll
-                            for (int q = 0; q < 16; q += 2) {
-                                const int n = c0 + q;
-                                if (n >= niv) break;
-                                const int rest = n >> 1;
-                                const int s2 = rest / (nb * LJ), rem = rest % (nb * LJ);
-                                const int cc = rem / LJ, j2 = rem % LJ;
-                                float2 *zp = a.z + (int64_t)(a.stream0 + s2) * a.z_stream_stride +
-                                             (int64_t)t * a.z_row_stride +
-                                             (int64_t)(b * a.cpb + cc) * L + kJ * j2 + j1;
-                                *zp = make_float2(a.scale * vv[q], a.scale * vv[q + 1]);
+                for (int half = 0; half < 2; ++half) {
+                    float gr[16], gi[16];
+                    tmem_ld16(tb + 16 * half, gr);
+                    tmem_ld16(tb + kNii + 16 * half, gi);
+                    if (half == 1 && bi == J.nbg - 1) {
+                        tc_fence_before();
+                        mbar_arrive(&state_free[grp]);
+                    }
+#pragma unroll
+                    for (int qq = 0; qq < kSteps; ++qq) {
+                        const int q = half * kSteps + qq;
+                        if (q < nsteps) {
+                            if (q == nb) {                            // stream 1 starts
+                                d_s0 = dd;
+                                p = make_float2((float)v1.x, (float)v1.y);
+                                dd = make_float2(0.f, 0.f);
                             }
+                            float2 u = make_float2(gr[qq * LJ + LJ - 1], gi[qq * LJ + LJ - 1]);
+#pragma unroll
+                            for (int i2 = LJ - 2; i2 >= 0; --i2)
+                                u = make_float2(u.x * aJ.x - u.y * aJ.y + gr[qq * LJ + i2],
+                                                u.x * aJ.y + u.y * aJ.x + gi[qq * LJ + i2]);
+                            const float2 vv = make_float2(p.x + dd.x, p.y + dd.y);
+                            float2 w = cmul(ak, cmul(ck, vv));
+                            const float2 ndd = cmul(aLf, dd);
+                            dd = make_float2(ndd.x + u.x, ndd.y + u.y);
+                            p = cmul(aLf, p);
+#pragma unroll
+                            for (int j2 = 0; j2 < LJ; ++j2) {
+                                const int n = (q * LJ + j2) * 2;
+                                const size_t o0 = (size_t)(n >> 3) * kWSbo + (n & 7) * 16 + kofs;
+                                const size_t o1 = (size_t)((n + 1) >> 3) * kWSbo + ((n + 1) & 7) * 16 + kofs;
+                                *reinterpret_cast<uint16_t *>(W1 + o0) = to16<BF16>(w.x);
+                                *reinterpret_cast<uint16_t *>(W1 + o1) = to16<BF16>(w.y);
+                                *reinterpret_cast<uint16_t *>(W2 + o0) = to16<BF16>(-w.y);
+                                *reinterpret_cast<uint16_t *>(W2 + o1) = to16<BF16>(w.x);
+                                w = cmul(w, aJ);
+                            }
+                        } else {
+                            // columns past this batch contribute nothing
+#pragma unroll
+                            for (int j2 = 0; j2 < LJ; ++j2) {
+                                const int n = (q * LJ + j2) * 2;
+                                const size_t o0 = (size_t)(n >> 3) * kWSbo + (n & 7) * 16 + kofs;
+                                const size_t o1 = (size_t)((n + 1) >> 3) * kWSbo + ((n + 1) & 7) * 16 + kofs;
+                                *reinterpret_cast<uint16_t *>(W1 + o0) = 0;
+                                *reinterpret_cast<uint16_t *>(W1 + o1) = 0;
+                                *reinterpret_cast<uint16_t *>(W2 + o0) = 0;
+                                *reinterpret_cast<uint16_t *>(W2 + o1) = 0;
+                            }
+                        }
+                    }
+                }
+                if (S == 1) d_s0 = dd;
+                fence_async_smem();
+                mbar_arrive(&w_full[grp]);
+                // v <- a^(nb L) v + d_nb in FP64, per stream
+                double2 pw;
+                if (nb == a.cpb) {
+                    pw = a.aLb[slot];
+                } else {
+                    const double2 aL = a.aL[slot];
+                    pw = aL;
+                    for (int i = 1; i < nb; ++i)
+                        pw = make_double2(pw.x * aL.x - pw.y * aL.y, pw.x * aL.y + pw.y * aL.x);
+                }
+                v0 = make_double2(fma(pw.x, v0.x, fma(-pw.y, v0.y, (double)d_s0.x)),
+                                  fma(pw.x, v0.y, fma(pw.y, v0.x, (double)d_s0.y)));
+                if (S > 1)
+                    v1 = make_double2(fma(pw.x, v1.x, fma(-pw.y, v1.y, (double)dd.x)),
+                                      fma(pw.x, v1.y, fma(pw.y, v1.x, (double)dd.y)));
+            }
+            a.v[(int64_t)a.stream0 * a.n_slots + slot] = v0;
+            if (S > 1) a.v[(int64_t)(a.stream0 + 1) * a.n_slots + slot] = v1;
+            return true;
+        });
+    } else {
+        // ---------------- epilogue ----------------
+        // lane j1, columns (s, c, j2, re/im) -> z = scale * value (the FIR
+        // kernel adds its term afterwards)
+        const int j1 = (warp & 3) * 32 + lane;
+        const uint32_t lane_base = ((uint32_t)((warp & 3) * 32)) << 16;
+        carry_jobs(a, [&](const CarryJob &J) -> bool {
+            if (!J.last_tile) return true;
+            const int ob = J.e & 1;
+            if (!mbar_wait_ab(&out_full[ob], (J.e >> 1) & 1, a.status, abort)) return false;
+            tc_fence_after();
+            for (int bi = 0; bi < J.nbg; ++bi) {
+                const int b = J.b0 + bi;
+                const int nb = min(a.cpb, a.n_chunks - b * a.cpb);
+                const int niv = 2 * S * nb * LJ;
+#pragma unroll
+                for (int c0 = 0; c0 < 2 * kNii; c0 += 16) {
+                    float vv[16];
+                    tmem_ld16(tmem + lane_base + 256 + 128 * ob + 64 * bi + c0, vv);
+#pragma unroll
+                    for (int q = 0; q < 16; q += 2) {
+                        const int n = c0 + q;
+                        if (n < niv) {
+                            const int rest = n >> 1;
+                            const int s2 = rest / (nb * LJ), rem = rest - s2 * (nb * LJ);
+                            const int cc = rem / LJ, j2 = rem - cc * LJ;
+                            float2 *zp = a.z + (int64_t)(a.stream0 + s2) * a.z_stream_stride +
+                                         (int64_t)J.t * a.z_row_stride +
+                                         (int64_t)(b * a.cpb + cc) * L + kJ * j2 + j1;
+                            *zp = make_float2(a.scale * vv[q], a.scale * vv[q + 1]);
                         }
                     }
                 }
             }
             tc_fence_before();
-            __syncthreads();
-            tc_fence_after();
-        }
+            mbar_arrive(&out_free[ob]);
+            return true;
+        });
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_free(tmem, 256);
+    tc_fence_after();
+    if (warp == 0) tmem_free(tmem, 512);
 }
 
 }  // namespace
@@ -1022,10 +1177,12 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
     int max_optin = 0;
     TC_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     {
-        const void *fns[4] = {(const void *)tc_fir_kernel<true>, (const void *)tc_carry_kernel<true>,
-                              (const void *)tc_fir_kernel<false>, (const void *)tc_carry_kernel<false>};
-        const int need[4] = {fir_smem_of(p.L, p.K), kCarrySmem, fir_smem_of(p.L, p.K), kCarrySmem};
-        for (int i = 0; i < 4; ++i) {
+        const void *fns[6] = {(const void *)tc_fir_kernel<true>, (const void *)tc_fir_kernel<false>,
+                              (const void *)tc_carry_kernel<true, 1>, (const void *)tc_carry_kernel<true, 2>,
+                              (const void *)tc_carry_kernel<false, 1>, (const void *)tc_carry_kernel<false, 2>};
+        const int need[6] = {fir_smem_of(p.L, p.K), fir_smem_of(p.L, p.K), kCarrySmem, kCarrySmem,
+                             kCarrySmem, kCarrySmem};
+        for (int i = 0; i < 6; ++i) {
             cudaFuncAttributes fa;
             TC_CUDA(cudaFuncGetAttributes(&fa, fns[i]));
             const int dyn_max = max_optin - (int)fa.sharedSizeBytes;
@@ -1132,12 +1289,20 @@ spiir_status spiir_tc_push(TcBank *b, int s0, int count, const float *x, int64_t
         ca.z_row_stride = b->ring_len;
         ca.z_stream_stride = (int64_t)b->T * b->ring_len;
         ca.status = b->status;
-        const int grid = std::min(b->n_carry_ctas, 2 * b->n_sms);
+        const int grid = std::min(b->n_carry_ctas, b->n_sms);
+        const int thr = kCarryWarps * 32;
         timer->begin(SPIIR_K_TC_CARRY, s);
-        if (b->bf16)
-            tc_carry_kernel<true><<<grid, 256, kCarrySmem, s>>>(ca);
-        else
-            tc_carry_kernel<false><<<grid, 256, kCarrySmem, s>>>(ca);
+        if (b->bf16) {
+            if (b->L == kJ)
+                tc_carry_kernel<true, 1><<<grid, thr, kCarrySmem, s>>>(ca);
+            else
+                tc_carry_kernel<true, 2><<<grid, thr, kCarrySmem, s>>>(ca);
+        } else {
+            if (b->L == kJ)
+                tc_carry_kernel<false, 1><<<grid, thr, kCarrySmem, s>>>(ca);
+            else
+                tc_carry_kernel<false, 2><<<grid, thr, kCarrySmem, s>>>(ca);
+        }
         TC_CUDA(cudaGetLastError());
         timer->end(s);
     }

@@ -53,6 +53,19 @@ def test_uneven_templates_chunk128(torch_cuda, oracle_mod):
     _check(z[1:], ref[1:], TOL_TC, 128)
 
 
+def test_several_batch_groups_per_push(torch_cuda, oracle_mod):
+    """Two streams, pushes of 2 s: 32 chunks of 256 in 4 carry batches, so the
+    filter state passes between batch groups inside one push; templates of 1,
+    2 and 3 filter tiles (odd tile counts put consecutive jobs on one slot)."""
+    counts = [60, 128, 200, 256, 300, 1, 383]
+    bank = inputs.single_rate_bank(len(counts), counts, 700, seed=23)
+    x = inputs.strain(2, 3 * 8192, seed=14)
+    z = gpu_snr(bank, x, push_blocks=2, n_streams=2, mode="fp16", chunk_len=256)
+    for s in range(2):
+        ref = oracle_mod.spiir_single(bank, x[s])
+        _check(z[s], ref, TOL_TC, 256)
+
+
 def test_tc_matches_plain_path(torch_cuda):
     """Same bank through both forms: they agree to the TC tolerance."""
     bank = inputs.single_rate_bank(70, 64, 300, seed=3)
