@@ -494,30 +494,45 @@ __global__ void __launch_bounds__(192, 1) tc_fir_kernel(const TcFirArgs a) {
 // ---------------------------------------------------------------------------
 // Carry kernel: one CTA per SM, persistent over templates. A CTA's work is a
 // sequence of jobs (template, group of up to kBatchGroup chunk batches,
-// 128-filter tile), pipelined over warp roles:
-//   warp 0, lane 0   issues the STATE and OUTPUT contractions, running one job
-//                    ahead (STATE of job j before OUTPUT of job j-1), and the
-//                    bulk copies of the strain segments
-//   warps 1-4        power panel R[k][i] = a_k^i of job j into buffer j % 2
-//   warps 5-8, 9-12  carry groups 0 and 1: jobs with j % 2 = group; STATE
-//                    (tensor memory) -> FP32 carry inside a batch, FP64 from
-//                    batch to batch -> OUTPUT operand W in shared memory
-//   warps 13-16      epilogue: OUTPUT accumulators -> z, per (template, group)
+// 128-filter tile) on two pipeline slots, spread over warp roles:
+//   warp 0, lane 0   issues the STATE and OUTPUT contractions as soon as each
+//                    one's inputs are ready (STATE of later jobs may overtake
+//                    the OUTPUT of earlier ones), and the strain-segment copies
+//   warps 1-4        power panel R[k][i] = a_k^i of each job into its slot, and
+//                    the epilogue of each (template, group): OUTPUT
+//                    accumulators -> z, taken up two jobs after its last tile,
+//                    when that tile's contractions have finished
+//   warps 5-8, 9-12  carry groups of slots 0 and 1: STATE (tensor memory) ->
+//                    FP32 carry inside a batch, FP64 from batch to batch ->
+//                    OUTPUT operands W1, W2 in shared memory
 // Every hand-off is an mbarrier: tcgen05.commit for contractions, one arrive
 // per thread for the 128-thread roles; every wait is bounded and gives up at
 // once when another role has given up.
-// Tensor memory (512 columns): STATE of carry group g at 128 g (64 columns
-// per batch: 32 re, 32 im); OUTPUT of (template, group) e at 256 + 128 (e%2)
-// (64 columns per batch).
+// Tensor memory (512 columns): STATE of slot g at 128 g (64 columns per
+// batch: 32 re, 32 im); OUTPUT of (template, group) e at 256 + 128 (e%2)
+// (64 columns per batch: re and im of chunk column c at 2c and 2c + 1).
 // ---------------------------------------------------------------------------
 
-constexpr int kCarryWarps = 17;
+constexpr int kCarryWarps = 13;
 constexpr int kPanelBytes = 2 * kTile * kJ * 2;                 // Pr + Pi: 64 KB
-constexpr int kWBytes = 2 * (2 * kNii) * kJ * 2;                // W1 + W2: 32 KB
+constexpr int kWHalf = 2 * kNii * kTile * 2;                    // W1 or W2: 16 KB
+constexpr int kWBytes = 2 * kWHalf;
 constexpr int kCarrySmem = 2 * kPanelBytes + kBatchGroup * kXsegBytes + 2 * kWBytes;   // 208 KB
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *m) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s32(m)) : "memory");
+}
+
+// Non-blocking test of an mbarrier phase.
+__device__ __forceinline__ bool mbar_test(uint64_t *m, uint32_t ph) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(s32(m)), "r"(ph)
+        : "memory");
+    return ok != 0;
 }
 
 // Bounded wait that also gives up when *abort is set; a timeout sets *abort.
@@ -536,6 +551,22 @@ __device__ __forceinline__ bool mbar_wait_ab(uint64_t *m, uint32_t ph, unsigned 
     return true;
 }
 
+// 32 lanes x 16 columns, without waiting (tmem_wait_ld completes the loads).
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%"
+        "15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 struct CarryJob {
     int t, b0, nbg, tile;
     bool first_tile, last_tile;
@@ -543,25 +574,49 @@ struct CarryJob {
     int g;      // pipeline slot: panel buffer, carry group, STATE columns, W buffer
 };
 
-// The job sequence of this CTA; fn returns false to stop. Jobs alternate
-// between the two pipeline slots. When a template has several groups of
-// batches, the filter state v of a tile passes from one group to the next, so
-// a tile keeps its slot (and so its carry threads) for all of them.
-template <class Fn>
-__device__ __forceinline__ void carry_jobs(const TcCarryArgs &a, Fn &&fn) {
-    int j = 0, e = 0;
-    const bool multi = a.n_batches > kBatchGroup;
-    for (int ti = blockIdx.x; ti < a.n_carry; ti += gridDim.x) {
-        const int t = a.tmpl_of[ti];
-        const int tile0 = a.tile_ptr[t], tile1 = a.tile_ptr[t + 1];
-        for (int b0 = 0; b0 < a.n_batches; b0 += kBatchGroup, ++e) {
-            const int nbg = min(kBatchGroup, a.n_batches - b0);
-            for (int tile = tile0; tile < tile1; ++tile, ++j) {
-                const int g = multi ? ((tile - tile0) & 1) : (j & 1);
-                if (!fn(CarryJob{t, b0, nbg, tile, tile == tile0, tile == tile1 - 1, j, e, g})) return;
-            }
+// The job sequence of this CTA. Jobs alternate between the two slots. When a
+// template has several groups of batches, the filter state v of a tile passes
+// from one group to the next, so a tile keeps its slot (and so its carry
+// threads) for all of them. Every listed template owns at least one tile.
+struct CarryJobs {
+    const TcCarryArgs *a;
+    int ti, b0, tile, tile0, tile1, t, j, e;
+    bool multi, valid;
+    __device__ explicit CarryJobs(const TcCarryArgs &A)
+        : a(&A), ti(blockIdx.x), j(0), e(0), multi(A.n_batches > kBatchGroup) {
+        start();
+    }
+    __device__ void start() {
+        valid = ti < a->n_carry;
+        if (valid) {
+            t = a->tmpl_of[ti];
+            tile0 = a->tile_ptr[t];
+            tile1 = a->tile_ptr[t + 1];
+            b0 = 0;
+            tile = tile0;
         }
     }
+    __device__ CarryJob cur() const {
+        const int g = multi ? ((tile - tile0) & 1) : (j & 1);
+        return CarryJob{t, b0, min(kBatchGroup, a->n_batches - b0), tile, tile == tile0,
+                        tile == tile1 - 1, j, e, g};
+    }
+    __device__ void next() {
+        ++j;
+        if (++tile < tile1) return;
+        tile = tile0;
+        ++e;
+        b0 += kBatchGroup;
+        if (b0 < a->n_batches) return;
+        ti += gridDim.x;
+        start();
+    }
+};
+
+template <class Fn>
+__device__ __forceinline__ void carry_jobs(const TcCarryArgs &a, Fn &&fn) {
+    for (CarryJobs it(a); it.valid; it.next())
+        if (!fn(it.cur())) return;
 }
 
 __device__ __forceinline__ float2 cmul(float2 x, float2 y) {
@@ -577,7 +632,11 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
     __shared__ int s_abort;
     unsigned char *Xs = smem + 2 * kPanelBytes;                    // kBatchGroup x 8 KB
     unsigned char *Wb = Xs + kBatchGroup * kXsegBytes;             // 2 x (W1, W2)
-    constexpr uint32_t kWSbo = 16 * 128;                           // 8 rows x 16 k-blocks
+    // OUTPUT operands, MN-major [k/8][n/8][k%8][n%8] (n = column, k =
+    // filter): 8-column groups 128 bytes apart, 8-filter groups kWK apart;
+    // column 2c = re, 2c + 1 = im of chunk column c:
+    //   W1 = [w_re, w_im],  W2 = [-w_im, w_re]  (D = Rr^T W1 + Ri^T W2)
+    constexpr uint32_t kWK = (2 * kNii / 8) * 128;
     const int L = LJ * kJ;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = a.n_streams;
@@ -608,89 +667,134 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            uint32_t n_pf[2] = {0, 0}, n_sf[2] = {0, 0}, n_wf[2] = {0, 0}, n_of[2] = {0, 0};
-            uint32_t ph_x = 0, ph_d = 0;
+            // STATE runs in job order; OUTPUT runs in job order (the first
+            // tile of a (template, group) overwrites the accumulator); each is
+            // issued as soon as its barriers have completed. All bookkeeping
+            // is in registers: phase parities and slot-use flags as bits of
+            // ph, the OUTPUT queue as 8-bit entries of oq.
+            constexpr uint32_t kPF = 0, kSF = 2, kWF = 4, kOF = 6, kUsed = 8;
+            uint32_t ph = 0, ph_x = 0, ph_d = 0;
+            // queue entry: bit 0 slot, 1 OUTPUT buffer, 2 first tile, 3 last
+            // tile, 4 two batches, 5 buffer used before
+            uint32_t oq = 0;
+            int oq_n = 0, ob_bi = 0;          // queue length; next batch of the head
             int loaded_b0 = -1;
-            bool ok = true, have_prev = false;
-            CarryJob prev{};
-            bool issued = false;
-            auto output = [&](const CarryJob &P) -> bool {
-                const int g = P.g, ob = P.e & 1;
-                if (P.first_tile && P.e >= 2) {
-                    if (!mbar_wait_ab(&out_free[ob], n_of[ob] & 1, a.status, abort)) return false;
-                    ++n_of[ob];
-                }
-                const unsigned char *Pr = smem + g * kPanelBytes, *Pi = Pr + kPanelBytes / 2;
-                const unsigned char *W1 = Wb + g * kWBytes, *W2 = W1 + kWBytes / 2;
-                const uint32_t id = idesc(128, 2 * kNii, BF16, true, false);
-                for (int bi = 0; bi < P.nbg; ++bi) {
-                    if (!mbar_wait_ab(&w_full[g], n_wf[g] & 1, a.status, abort)) return false;
-                    ++n_wf[g];
-                    tc_fence_after();
-                    const uint32_t dz = tmem + 256 + 128 * ob + 64 * bi;
-                    for (int kk = 0; kk < kTile / 16; ++kk) {
-                        const uint32_t acc = (!P.first_tile || kk) ? 1u : 0u;
-                        const uint64_t ar = sdesc(s32(Pr) + kk * 2 * 2048, 2048, 128);
-                        const uint64_t ai = sdesc(s32(Pi) + kk * 2 * 2048, 2048, 128);
-                        mma(dz, ar, sdesc(s32(W1) + kk * 2 * 128, 128, kWSbo), id, acc);
-                        mma(dz, ai, sdesc(s32(W2) + kk * 2 * 128, 128, kWSbo), id, 1u);
-                    }
-                    mma_commit(&w_free[g]);
-                }
-                mma_commit(&panel_free[g]);
-                if (P.last_tile) mma_commit(&out_full[ob]);
-                return true;
-            };
-            carry_jobs(a, [&](const CarryJob &J) -> bool {
-                const int g = J.g;
-                if (J.b0 != loaded_b0) {
-                    // the STATE contractions that read the old segments are done
-                    if (issued) {
-                        mma_commit(&drain);
-                        ok = mbar_wait_ab(&drain, ph_d, a.status, abort);
-                        ph_d ^= 1u;
-                        if (!ok) return false;
-                    }
-                    mbar_expect(&xs_bar, J.nbg * kXsegBytes);
-                    bulk_load(Xs, a.xseg + (size_t)J.b0 * (kXsegBytes / 16), J.nbg * kXsegBytes, &xs_bar);
-                    ok = mbar_wait_ab(&xs_bar, ph_x, a.status, abort);
-                    ph_x ^= 1u;
-                    if (!ok) return false;
-                    loaded_b0 = J.b0;
-                }
-                // two jobs in a row on one slot: the earlier one's OUTPUT frees
-                // the slot's panel, so it cannot wait behind this job's STATE
-                if (have_prev && prev.g == g) {
-                    have_prev = false;
-                    if (!(ok = output(prev))) return false;
-                }
-                ok = mbar_wait_ab(&panel_full[g], n_pf[g] & 1, a.status, abort);
-                ++n_pf[g];
-                if (ok && n_pf[g] >= 2) {       // slot g was used before
-                    ok = mbar_wait_ab(&state_free[g], n_sf[g] & 1, a.status, abort);
-                    ++n_sf[g];
-                }
-                if (!ok) return false;
-                tc_fence_after();
-                const unsigned char *Pr = smem + g * kPanelBytes, *Pi = Pr + kPanelBytes / 2;
-                const uint32_t id = idesc(128, kNii, BF16, false, false);
-                for (int bi = 0; bi < J.nbg; ++bi) {
-                    const uint32_t xs = s32(Xs + bi * kXsegBytes);
-                    const uint32_t d = tmem + 128 * g + 64 * bi;
-                    for (int kk = 0; kk < kJ / 16; ++kk) {
-                        const uint64_t bd = sdesc(xs + kk * 256, 128, 2048);
-                        mma(d, sdesc(s32(Pr) + kk * 256, 128, 2048), bd, id, kk ? 1u : 0u);
-                        mma(d + kNii, sdesc(s32(Pi) + kk * 256, 128, 2048), bd, id, kk ? 1u : 0u);
+            bool issued = false, ok = true;
+            CarryJobs st(a);                  // next job for STATE
+            const uint32_t id_state = idesc(128, kNii, BF16, false, false);
+            const uint32_t id_out = idesc(128, 2 * kNii, BF16, true, true);
+            const uint32_t smem0 = s32(smem), wb0 = s32(Wb), xs0 = s32(Xs);
+            uint64_t idle0 = 0;
+            while (ok && (st.valid || oq_n > 0)) {
+                bool progressed = false;
+                // STATE of the next job: panel ready, slot's STATE columns
+                // free, and no earlier job of this slot still without OUTPUT
+                if (st.valid && oq_n < 4) {
+                    const CarryJob J = st.cur();
+                    const uint32_t g = (uint32_t)J.g;
+                    bool same = false;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        same |= (i < oq_n) && (((oq >> (8 * i)) & 1u) == g);
+                    const bool used = (ph >> (kUsed + g)) & 1u;
+                    if (!same && (!used || mbar_test(&state_free[g], (ph >> (kSF + g)) & 1u)) &&
+                        mbar_test(&panel_full[g], (ph >> (kPF + g)) & 1u)) {
+                        if (used) ph ^= 1u << (kSF + g);
+                        ph ^= 1u << (kPF + g);
+                        ph |= 1u << (kUsed + g);
+                        if (J.b0 != loaded_b0) {
+                            // the STATE contractions that read the old segments are done
+                            if (issued) {
+                                mma_commit(&drain);
+                                ok = mbar_wait_ab(&drain, ph_d, a.status, abort);
+                                ph_d ^= 1u;
+                            }
+                            if (ok) {
+                                mbar_expect(&xs_bar, J.nbg * kXsegBytes);
+                                bulk_load(Xs, a.xseg + (size_t)J.b0 * (kXsegBytes / 16), J.nbg * kXsegBytes,
+                                          &xs_bar);
+                                ok = mbar_wait_ab(&xs_bar, ph_x, a.status, abort);
+                                ph_x ^= 1u;
+                            }
+                            if (!ok) break;
+                            loaded_b0 = J.b0;
+                        }
+                        tc_fence_after();
+                        // descriptors advance by 16-byte units in their low bits
+                        const uint64_t dr0 = sdesc(smem0 + g * kPanelBytes, 128, 2048);
+                        const uint64_t di0 = dr0 + ((kPanelBytes / 2) >> 4);
+                        for (int bi = 0; bi < J.nbg; ++bi) {
+                            const uint64_t dx0 = sdesc(xs0 + bi * kXsegBytes, 128, 2048);
+                            const uint32_t d = tmem + 128 * g + 64 * bi;
+#pragma unroll
+                            for (int kk = 0; kk < kJ / 16; ++kk) {
+                                const uint64_t o = (uint64_t)(kk * 256) >> 4;
+                                mma(d, dr0 + o, dx0 + o, id_state, kk ? 1u : 0u);
+                                mma(d + kNii, di0 + o, dx0 + o, id_state, kk ? 1u : 0u);
+                            }
+                        }
+                        mma_commit(&state_full[g]);
+                        issued = true;
+                        const uint32_t ent = g | ((uint32_t)(J.e & 1) << 1) | ((uint32_t)J.first_tile << 2) |
+                                             ((uint32_t)J.last_tile << 3) | ((uint32_t)(J.nbg == 2) << 4) |
+                                             ((uint32_t)(J.e >= 2) << 5);
+                        oq |= ent << (8 * oq_n);
+                        ++oq_n;
+                        st.next();
+                        progressed = true;
                     }
                 }
-                mma_commit(&state_full[g]);
-                issued = true;
-                if (have_prev && !(ok = output(prev))) return false;
-                prev = J;
-                have_prev = true;
-                return true;
-            });
-            if (ok && have_prev) ok = output(prev);
+                // OUTPUT of the oldest job, batch by batch:
+                //   D = Rr^T W1 + Ri^T W2
+                if (oq_n > 0) {
+                    const uint32_t ent = oq & 0xFFu;
+                    const uint32_t g = ent & 1u, ob = (ent >> 1) & 1u;
+                    const bool first = (ent >> 2) & 1u, last = (ent >> 3) & 1u;
+                    const int nbg = ((ent >> 4) & 1u) ? 2 : 1;
+                    const bool need_of = first && ob_bi == 0 && ((ent >> 5) & 1u);
+                    const bool of_ok = !need_of || mbar_test(&out_free[ob], (ph >> (kOF + ob)) & 1u);
+                    if (of_ok && mbar_test(&w_full[g], (ph >> (kWF + g)) & 1u)) {
+                        if (need_of) ph ^= 1u << (kOF + ob);
+                        ph ^= 1u << (kWF + g);
+                        tc_fence_after();
+                        const uint64_t ar0 = sdesc(smem0 + g * kPanelBytes, 2048, 128);
+                        const uint64_t ai0 = ar0 + ((kPanelBytes / 2) >> 4);
+                        const uint64_t b10 = sdesc(wb0 + g * kWBytes, kWK, 128);
+                        const uint64_t b20 = b10 + (kWHalf >> 4);
+                        const uint32_t dz = tmem + 256 + 128 * ob + 64 * ob_bi;
+                        const uint32_t acc0 = first ? 0u : 1u;
+#pragma unroll
+                        for (int kk = 0; kk < kTile / 16; ++kk) {
+                            const uint64_t oa = (uint64_t)(kk * 2 * 2048) >> 4;
+                            const uint64_t ow = (uint64_t)(kk * 2 * kWK) >> 4;
+                            mma(dz, ar0 + oa, b10 + ow, id_out, kk ? 1u : acc0);
+                            mma(dz, ai0 + oa, b20 + ow, id_out, 1u);
+                        }
+                        mma_commit(&w_free[g]);
+                        if (++ob_bi == nbg) {
+                            mma_commit(&panel_free[g]);
+                            if (last) mma_commit(&out_full[ob]);
+                            oq >>= 8;
+                            --oq_n;
+                            ob_bi = 0;
+                        }
+                        progressed = true;
+                    }
+                }
+                if (progressed) {
+                    idle0 = 0;
+                } else {
+                    const uint64_t now = gtime();
+                    if (idle0 == 0) {
+                        idle0 = now;
+                    } else if (now - idle0 > 2000000000ull) {
+                        atomicExch(a.status, SPIIR_DEV_TIMEOUT);
+                        *abort = 1;
+                        ok = false;
+                    }
+                    if (*abort) ok = false;
+                }
+            }
             // nothing may still run when the tensor memory is released
             if (issued) {
                 mma_commit(&drain);
@@ -698,20 +802,81 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             }
         }
     } else if (warp <= 4) {
-        // ---------------- power panels ----------------
-        // thread = filter k: R[k][i] = a_k^i, i < 128, as four chains of 16
-        // powers per half (the second half starts from a_k^64); layout
+        // ---------------- power panels and epilogue ----------------
+        // panel: thread = filter k: R[k][i] = a_k^i, i < 128, as four chains of
+        // 16 powers per half (the second half starts from a_k^64); layout
         // [k/8][i/8][k%8][i%8]
         const int k = threadIdx.x - 32;
-        uint32_t use[2] = {0, 0};
+        // epilogue: lane j1; column c = (s, chunk, j2) of the re and im
+        // halves -> z = scale * value (the FIR kernel adds its term afterwards)
+        const int j1 = (warp & 3) * 32 + lane;
+        const uint32_t lane_base = ((uint32_t)((warp & 3) * 32)) << 16;
+        // (template, group)s awaiting the epilogue, oldest first (at most 3)
+        struct Ep {
+            int t, b0, nbg, e, j;
+        };
+        Ep ep0{}, ep1{}, ep2{};
+        int ep_n = 0;
+        auto epilogue = [&](const Ep &J) -> bool {
+            const int ob = J.e & 1;
+            if (!mbar_wait_ab(&out_full[ob], (J.e >> 1) & 1, a.status, abort)) return false;
+            tc_fence_after();
+            for (int bi = 0; bi < J.nbg; ++bi) {
+                const int b = J.b0 + bi;
+                const int nb = min(a.cpb, a.n_chunks - b * a.cpb);
+                const int nii = S * nb * LJ;
+                const uint32_t tb = tmem + lane_base + 256 + 128 * ob + 64 * bi;
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {       // chunk columns 16 hh .. 16 hh + 15
+                    uint32_t vv[2][16];
+                    tmem_ld16_nw(tb + 32 * hh, vv[0]);
+                    tmem_ld16_nw(tb + 32 * hh + 16, vv[1]);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int c16 = 0; c16 < 16; ++c16) {
+                        const int c = 16 * hh + c16;
+                        if (c < nii) {
+                            const int s2 = c / (nb * LJ), rem = c - s2 * (nb * LJ);
+                            const int cc = rem / LJ, j2 = rem - cc * LJ;
+                            float2 *zp = a.z + (int64_t)(a.stream0 + s2) * a.z_stream_stride +
+                                         (int64_t)J.t * a.z_row_stride +
+                                         (int64_t)(b * a.cpb + cc) * L + kJ * j2 + j1;
+                            *zp = make_float2(a.scale * __uint_as_float(vv[c16 >> 3][(2 * c16) & 15]),
+                                              a.scale * __uint_as_float(vv[c16 >> 3][(2 * c16 + 1) & 15]));
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&out_free[ob]);
+            return true;
+        };
+        uint32_t used = 0, pfp = 0;           // slot used before; panel_free parity
+        bool ok = true;
         carry_jobs(a, [&](const CarryJob &J) -> bool {
             const int g = J.g;
-            if (use[g] > 0 && !mbar_wait_ab(&panel_free[g], (use[g] - 1) & 1, a.status, abort))
-                return false;
-            ++use[g];
-            unsigned char *Pr = smem + g * kPanelBytes, *Pi = Pr + kPanelBytes / 2;
             const int64_t slot = (int64_t)J.tile * kTile + k;
             const float2 ak = a.a[slot], a64 = a.a64[slot];
+            // epilogues whose last tile is at least two jobs back
+            while (ep_n > 0 && ep0.j <= J.j - 2) {
+                if (!(ok = epilogue(ep0))) return false;
+                ep0 = ep1;
+                ep1 = ep2;
+                --ep_n;
+            }
+            if (J.last_tile) {
+                const Ep n{J.t, J.b0, J.nbg, J.e, J.j};
+                if (ep_n == 0) ep0 = n;
+                else if (ep_n == 1) ep1 = n;
+                else ep2 = n;
+                ++ep_n;
+            }
+            if ((used >> g) & 1u) {
+                if (!(ok = mbar_wait_ab(&panel_free[g], (pfp >> g) & 1u, a.status, abort))) return false;
+                pfp ^= 1u << g;
+            }
+            used |= 1u << g;
+            unsigned char *Pr = smem + g * kPanelBytes, *Pi = Pr + kPanelBytes / 2;
             float2 a16 = ak;
 #pragma unroll
             for (int i = 0; i < 4; ++i) a16 = cmul(a16, a16);
@@ -723,25 +888,22 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                 for (int i = 1; i < 4; ++i) p[i] = cmul(p[i - 1], a16);
 #pragma unroll
                 for (int ib = 0; ib < 2; ++ib) {
+                    float vr[4][8], vi[4][8];
 #pragma unroll
-                    for (int c2 = 0; c2 < 4; c2 += 2) {     // two chains at a time
-                        float vr[2][8], vi[2][8];
+                    for (int q = 0; q < 8; ++q) {
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-#pragma unroll
-                            for (int ch = 0; ch < 2; ++ch) {
-                                vr[ch][q] = p[c2 + ch].x;
-                                vi[ch][q] = p[c2 + ch].y;
-                                p[c2 + ch] = cmul(p[c2 + ch], ak);
-                            }
+                        for (int ch = 0; ch < 4; ++ch) {
+                            vr[ch][q] = p[ch].x;
+                            vi[ch][q] = p[ch].y;
+                            p[ch] = cmul(p[ch], ak);
                         }
+                    }
 #pragma unroll
-                        for (int ch = 0; ch < 2; ++ch) {
-                            const int kb = h * 8 + (c2 + ch) * 2 + ib;
-                            const size_t off = (size_t)(k >> 3) * 2048 + kb * 128 + (k & 7) * 16;
-                            *reinterpret_cast<uint4 *>(Pr + off) = pack8<BF16>(vr[ch]);
-                            *reinterpret_cast<uint4 *>(Pi + off) = pack8<BF16>(vi[ch]);
-                        }
+                    for (int ch = 0; ch < 4; ++ch) {
+                        const int kb = h * 8 + ch * 2 + ib;
+                        const size_t off = (size_t)(k >> 3) * 2048 + kb * 128 + (k & 7) * 16;
+                        *reinterpret_cast<uint4 *>(Pr + off) = pack8<BF16>(vr[ch]);
+                        *reinterpret_cast<uint4 *>(Pi + off) = pack8<BF16>(vi[ch]);
                     }
                 }
             }
@@ -749,12 +911,15 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             mbar_arrive(&panel_full[g]);
             return true;
         });
+        if (ok && ep_n > 0) ok = epilogue(ep0);
+        if (ok && ep_n > 1) ok = epilogue(ep1);
+        if (ok && ep_n > 2) ok = epilogue(ep2);
     } else if (warp <= 12) {
         // ---------------- carry groups ----------------
         const int grp = (warp - 5) >> 2;
         const int k = (warp & 3) * 32 + lane;                 // tensor-memory lane = filter
         const uint32_t lane_base = ((uint32_t)((warp & 3) * 32)) << 16;
-        const size_t kofs = (size_t)(k >> 3) * 128 + (k & 7) * 2;
+        const uint32_t kofs = (uint32_t)(k >> 3) * kWK + (k & 7) * 16;
         uint32_t n_state = 0, n_w = 0;
         carry_jobs(a, [&](const CarryJob &J) -> bool {
             if (J.g != grp) return true;
@@ -765,14 +930,12 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             if (!mbar_wait_ab(&state_full[grp], n_state & 1, a.status, abort)) return false;
             ++n_state;
             tc_fence_after();
-            unsigned char *W1 = Wb + grp * kWBytes, *W2 = W1 + kWBytes / 2;
+            unsigned char *W1 = Wb + grp * kWBytes, *W2 = W1 + kWHalf;
+            const double2 aLb = a.aLb[slot];
             for (int bi = 0; bi < J.nbg; ++bi) {
                 const int b = J.b0 + bi;
                 const int nb = min(a.cpb, a.n_chunks - b * a.cpb);
                 const int nsteps = S * nb;                          // (stream, chunk) steps
-                // STATE columns: (stream, chunk, i2) -> (s nb + c) LJ + i2, read
-                // 16 at a time (16 / LJ steps)
-                const uint32_t tb = tmem + lane_base + 128 * grp + 64 * bi;
                 if (n_w > 0 && !mbar_wait_ab(&w_free[grp], (n_w - 1) & 1, a.status, abort)) return false;
                 ++n_w;
                 // Carry across this batch. The batch's starting state v is
@@ -782,12 +945,18 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                 float2 p = make_float2((float)v0.x, (float)v0.y);   // a^(cL) v
                 float2 dd = make_float2(0.f, 0.f);                   // d_c
                 float2 d_s0 = dd;
-                constexpr int kSteps = 16 / LJ;                       // steps per 16 columns
+                // STATE columns: (stream, chunk, i2) -> (s nb + c) LJ + i2, read
+                // 16 at a time (16 / LJ steps). One step writes columns
+                // 2 q LJ .. 2 q LJ + 2 LJ - 1 of W1 and W2: 4 LJ contiguous bytes
+                // at (k/8) kWK + (n/8) 128 + (k%8) 16 + (n%8) 2
+                const uint32_t tb = tmem + lane_base + 128 * grp + 64 * bi;
+                constexpr int kSteps = 16 / LJ;
 #pragma unroll
                 for (int half = 0; half < 2; ++half) {
-                    float gr[16], gi[16];
-                    tmem_ld16(tb + 16 * half, gr);
-                    tmem_ld16(tb + kNii + 16 * half, gi);
+                    uint32_t rr[16], ri[16];
+                    tmem_ld16_nw(tb + 16 * half, rr);
+                    tmem_ld16_nw(tb + kNii + 16 * half, ri);
+                    tmem_wait_ld();
                     if (half == 1 && bi == J.nbg - 1) {
                         tc_fence_before();
                         mbar_arrive(&state_free[grp]);
@@ -795,17 +964,23 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
 #pragma unroll
                     for (int qq = 0; qq < kSteps; ++qq) {
                         const int q = half * kSteps + qq;
+                        const int n = 2 * q * LJ;
+                        const uint32_t off = kofs + (uint32_t)(n >> 3) * 128 + (n & 7) * 2;
+                        float wr[LJ], wi[LJ];
                         if (q < nsteps) {
                             if (q == nb) {                            // stream 1 starts
                                 d_s0 = dd;
                                 p = make_float2((float)v1.x, (float)v1.y);
                                 dd = make_float2(0.f, 0.f);
                             }
-                            float2 u = make_float2(gr[qq * LJ + LJ - 1], gi[qq * LJ + LJ - 1]);
+                            const int c1 = qq * LJ + LJ - 1;
+                            float2 u = make_float2(__uint_as_float(rr[c1]), __uint_as_float(ri[c1]));
 #pragma unroll
-                            for (int i2 = LJ - 2; i2 >= 0; --i2)
-                                u = make_float2(u.x * aJ.x - u.y * aJ.y + gr[qq * LJ + i2],
-                                                u.x * aJ.y + u.y * aJ.x + gi[qq * LJ + i2]);
+                            for (int i2 = LJ - 2; i2 >= 0; --i2) {
+                                const int c = qq * LJ + i2;
+                                u = make_float2(u.x * aJ.x - u.y * aJ.y + __uint_as_float(rr[c]),
+                                                u.x * aJ.y + u.y * aJ.x + __uint_as_float(ri[c]));
+                            }
                             const float2 vv = make_float2(p.x + dd.x, p.y + dd.y);
                             float2 w = cmul(ak, cmul(ck, vv));
                             const float2 ndd = cmul(aLf, dd);
@@ -813,27 +988,23 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                             p = cmul(aLf, p);
 #pragma unroll
                             for (int j2 = 0; j2 < LJ; ++j2) {
-                                const int n = (q * LJ + j2) * 2;
-                                const size_t o0 = (size_t)(n >> 3) * kWSbo + (n & 7) * 16 + kofs;
-                                const size_t o1 = (size_t)((n + 1) >> 3) * kWSbo + ((n + 1) & 7) * 16 + kofs;
-                                *reinterpret_cast<uint16_t *>(W1 + o0) = to16<BF16>(w.x);
-                                *reinterpret_cast<uint16_t *>(W1 + o1) = to16<BF16>(w.y);
-                                *reinterpret_cast<uint16_t *>(W2 + o0) = to16<BF16>(-w.y);
-                                *reinterpret_cast<uint16_t *>(W2 + o1) = to16<BF16>(w.x);
+                                wr[j2] = w.x;
+                                wi[j2] = w.y;
                                 w = cmul(w, aJ);
                             }
                         } else {
                             // columns past this batch contribute nothing
 #pragma unroll
-                            for (int j2 = 0; j2 < LJ; ++j2) {
-                                const int n = (q * LJ + j2) * 2;
-                                const size_t o0 = (size_t)(n >> 3) * kWSbo + (n & 7) * 16 + kofs;
-                                const size_t o1 = (size_t)((n + 1) >> 3) * kWSbo + ((n + 1) & 7) * 16 + kofs;
-                                *reinterpret_cast<uint16_t *>(W1 + o0) = 0;
-                                *reinterpret_cast<uint16_t *>(W1 + o1) = 0;
-                                *reinterpret_cast<uint16_t *>(W2 + o0) = 0;
-                                *reinterpret_cast<uint16_t *>(W2 + o1) = 0;
-                            }
+                            for (int j2 = 0; j2 < LJ; ++j2) wr[j2] = wi[j2] = 0.f;
+                        }
+                        if constexpr (LJ == 2) {
+                            *reinterpret_cast<uint2 *>(W1 + off) =
+                                make_uint2(pack2<BF16>(wr[0], wi[0]), pack2<BF16>(wr[1], wi[1]));
+                            *reinterpret_cast<uint2 *>(W2 + off) =
+                                make_uint2(pack2<BF16>(-wi[0], wr[0]), pack2<BF16>(-wi[1], wr[1]));
+                        } else {
+                            *reinterpret_cast<uint32_t *>(W1 + off) = pack2<BF16>(wr[0], wi[0]);
+                            *reinterpret_cast<uint32_t *>(W2 + off) = pack2<BF16>(-wi[0], wr[0]);
                         }
                     }
                 }
@@ -843,7 +1014,7 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                 // v <- a^(nb L) v + d_nb in FP64, per stream
                 double2 pw;
                 if (nb == a.cpb) {
-                    pw = a.aLb[slot];
+                    pw = aLb;
                 } else {
                     const double2 aL = a.aL[slot];
                     pw = aL;
@@ -858,44 +1029,6 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             }
             a.v[(int64_t)a.stream0 * a.n_slots + slot] = v0;
             if (S > 1) a.v[(int64_t)(a.stream0 + 1) * a.n_slots + slot] = v1;
-            return true;
-        });
-    } else {
-        // ---------------- epilogue ----------------
-        // lane j1, columns (s, c, j2, re/im) -> z = scale * value (the FIR
-        // kernel adds its term afterwards)
-        const int j1 = (warp & 3) * 32 + lane;
-        const uint32_t lane_base = ((uint32_t)((warp & 3) * 32)) << 16;
-        carry_jobs(a, [&](const CarryJob &J) -> bool {
-            if (!J.last_tile) return true;
-            const int ob = J.e & 1;
-            if (!mbar_wait_ab(&out_full[ob], (J.e >> 1) & 1, a.status, abort)) return false;
-            tc_fence_after();
-            for (int bi = 0; bi < J.nbg; ++bi) {
-                const int b = J.b0 + bi;
-                const int nb = min(a.cpb, a.n_chunks - b * a.cpb);
-                const int niv = 2 * S * nb * LJ;
-#pragma unroll
-                for (int c0 = 0; c0 < 2 * kNii; c0 += 16) {
-                    float vv[16];
-                    tmem_ld16(tmem + lane_base + 256 + 128 * ob + 64 * bi + c0, vv);
-#pragma unroll
-                    for (int q = 0; q < 16; q += 2) {
-                        const int n = c0 + q;
-                        if (n < niv) {
-                            const int rest = n >> 1;
-                            const int s2 = rest / (nb * LJ), rem = rest - s2 * (nb * LJ);
-                            const int cc = rem / LJ, j2 = rem - cc * LJ;
-                            float2 *zp = a.z + (int64_t)(a.stream0 + s2) * a.z_stream_stride +
-                                         (int64_t)J.t * a.z_row_stride +
-                                         (int64_t)(b * a.cpb + cc) * L + kJ * j2 + j1;
-                            *zp = make_float2(a.scale * vv[q], a.scale * vv[q + 1]);
-                        }
-                    }
-                }
-            }
-            tc_fence_before();
-            mbar_arrive(&out_free[ob]);
             return true;
         });
     }
