@@ -358,8 +358,9 @@ def _roofline(m, w, args, peaks, sms):
         name, ach = "tc_fir_kernel", fir_flops / (fir_ms / 1e3) / 1e12 if fir_ms else 0.0
     else:
         name, ach = "tc_carry_kernel", carry_flops / (car_ms / 1e3) / 1e12 if car_ms else 0.0
+    key = ("tc_fir" if name == "tc_fir_kernel" else "tc_carry") + f"_{args.workload}"
     return {"bound": "tensor", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-            "frac": ach / peak, "traffic": None,
+            "frac": ach / peak, "traffic": _traffic("spiir_tc.cu", key),
             "peak_basis": "measured dense bf16 burst (cuBLAS) of MEASURED_PEAKS; fp16 has the same "
                           "nominal dense rate",
             "fir_tflops": fir_flops / (fir_ms / 1e3) / 1e12 if fir_ms else None,
@@ -501,15 +502,17 @@ def run_serve(args):
         best = None
         trials = []
         scale = args.serve_scale0
+        lo, hi = None, None            # largest passing / smallest failing scale
         for _ in range(args.serve_trials):
             r = _serve_trial(kind, form, scale, args.serve_blocks, 7, budget)
             r["scale"] = scale
             trials.append(r)
             if r.get("blocks", 0) and r["p99_block_latency_ms"] < 10.0:
-                best = r
-                scale *= 2.0
+                best, lo = r, scale
             else:
-                break
+                hi = scale
+            # double until the SLO is missed, then bisect (geometrically)
+            scale = scale * 2.0 if hi is None else (lo * hi) ** 0.5 if lo else hi / 2.0
         res[form] = {"at_slo": best, "trials": trials}
     def rtt(r):
         return 3 * r["mean_active_templates"] if r else 0.0
@@ -542,7 +545,7 @@ def main():
     ap.add_argument("--serve-kind", default="single", choices=["single", "multirate"],
                     help="serving: banks of the plain-form run (multi-rate is config 4)")
     ap.add_argument("--serve-blocks", type=int, default=24)
-    ap.add_argument("--serve-trials", type=int, default=6)
+    ap.add_argument("--serve-trials", type=int, default=8)
     ap.add_argument("--serve-scale0", type=float, default=0.02)
     ap.add_argument("--form", default="", choices=["", "plain", "fp16", "bf16"],
                     help="compute form of the headline number (default: plain; fp16 for tc)")
