@@ -63,7 +63,7 @@ spiir_status tc_fail(spiir_status st, const char *msg) {
         }                                                                               \
     } while (0)
 
-constexpr int kJ = 128;           // power-panel length (STATE/OUTPUT factorisation)
+constexpr int kJ = 64;            // power-panel length (STATE/OUTPUT factorisation)
 constexpr int kTile = 128;        // filters per carry tile (MMA M)
 constexpr int kGroup = 64;        // templates per FIR tile (M = 128 rows re/im)
 constexpr int kKs = 64;           // FIR K slice
@@ -244,9 +244,8 @@ struct TcStageArgs {
     uint4 *xseg;              // [batch][kXsegBytes/16] STATE strain segments
 };
 
-constexpr int kNii = 32;                       // STATE columns per carry batch
+constexpr int kNii = 64;                       // STATE columns per carry batch
 constexpr int kXsegBytes = kNii * kJ * 2;      // 8 KB
-constexpr int kBatchGroup = 2;                 // batches per power-panel generation
 
 struct TcFirArgs {
     const uint4 *H;           // [group][slice][16 KB] pre-tiled impulse responses
@@ -267,8 +266,7 @@ struct TcCarryArgs {
     const int32_t *tmpl_of;   // templates that own tiles
     int32_t n_carry;
     const float2 *a;          // [slot] a_k
-    const float2 *a64;        // [slot] a_k^64
-    const float2 *aJ;         // [slot] a_k^128
+    const float2 *aJ;         // [slot] a_k^kJ
     const double2 *aL;        // [slot] a_k^L (FP64)
     const float2 *aLf;        // [slot] a_k^L rounded to FP32
     const double2 *aLb;       // [slot] a_k^(L * cpb) (FP64), cpb of this launch
@@ -313,11 +311,12 @@ __global__ void tc_stage_kernel(const TcStageArgs a) {
             a.hank[i] = pack8<BF16>(v);
         } else {
             // STATE segments of batch b: row n = (s, c, i2), K = i1:
-            // x_s[e_c - 128 i2 - i1], e_c = c L - F + L - 1; layout
+            // x_s[e_c - kJ i2 - i1], e_c = c L - F + L - 1; layout
             // [n/8][i1/8][n%8][i1%8]
             const int64_t j = i - hank_chunks;
             const int b = (int)(j / (kXsegBytes / 16)), w = (int)(j % (kXsegBytes / 16));
-            const int n = (w / 128) * 8 + (w % 8), kb = (w / 8) % 16;
+            constexpr int kKB = kJ / 8;
+            const int n = (w / (8 * kKB)) * 8 + (w % 8), kb = (w / 8) % kKB;
             const int nb = min(a.cpb, a.n_chunks - b * a.cpb);
             const int nii = a.n_streams * nb * LJ;
             if (n < nii) {
@@ -493,31 +492,41 @@ __global__ void __launch_bounds__(192, 1) tc_fir_kernel(const TcFirArgs a) {
 
 // ---------------------------------------------------------------------------
 // Carry kernel: one CTA per SM, persistent over templates. A CTA's work is a
-// sequence of jobs (template, group of up to kBatchGroup chunk batches,
-// 128-filter tile) on two pipeline slots, spread over warp roles:
+// sequence of jobs (template, chunk batch, 128-filter tile) on three pipeline
+// slots (power panel and OUTPUT operand in shared memory) and two carry
+// groups, spread over warp roles:
 //   warp 0, lane 0   issues the STATE and OUTPUT contractions as soon as each
 //                    one's inputs are ready (STATE of later jobs may overtake
 //                    the OUTPUT of earlier ones), and the strain-segment copies
-//   warps 1-4        power panel R[k][i] = a_k^i of each job into its slot, and
-//                    the epilogue of each (template, group): OUTPUT
-//                    accumulators -> z, taken up two jobs after its last tile,
-//                    when that tile's contractions have finished
-//   warps 5-8, 9-12  carry groups of slots 0 and 1: STATE (tensor memory) ->
-//                    FP32 carry inside a batch, FP64 from batch to batch ->
-//                    OUTPUT operands W1, W2 in shared memory
-// Every hand-off is an mbarrier: tcgen05.commit for contractions, one arrive
-// per thread for the 128-thread roles; every wait is bounded and gives up at
-// once when another role has given up.
-// Tensor memory (512 columns): STATE of slot g at 128 g (64 columns per
-// batch: 32 re, 32 im); OUTPUT of (template, group) e at 256 + 128 (e%2)
-// (64 columns per batch: re and im of chunk column c at 2c and 2c + 1).
+//   warps 1-4        power panel of each job into its slot, and the epilogue
+//                    of each (template, batch): OUTPUT accumulators -> z,
+//                    taken up two jobs after its last tile
+//   warps 5-8, 9-12  carry groups 0 and 1: STATE (tensor memory) -> FP32
+//                    carry inside a batch, FP64 from batch to batch -> OUTPUT
+//                    operand W of the job's slot
+// Panel of a 128-filter tile: R[k][m] = Re a_k^m (m < 64), Im a_k^(m-64)
+// (m >= 64), layout [k/8][m/8][k%8][m%8]. STATE reads it K-major (filters x
+// powers, re and im halves separately); OUTPUT reads it MN-major with the re
+// and im powers stacked along M = 128:
+//   D[m][2c]     = sum_k R[k][m] Re w_k(c),  D[m][2c + 1] = sum_k R[k][m] Im w_k(c)
+//   z_re(j) = D[j][2c] - D[64 + j][2c + 1],  z_im(j) = D[j][2c + 1] + D[64 + j][2c]
+// so the epilogue pairs row j with row 64 + j (another warp) through a small
+// double-buffered shared-memory exchange under the panel role's own barrier.
+// Every hand-off between roles is an mbarrier: tcgen05.commit for
+// contractions, one arrive per thread for the 128-thread roles; every wait is
+// bounded and gives up at once when another role has given up (the panel role
+// agrees on it with a barrier reduction, so it leaves as a whole).
+// Tensor memory (512 columns): STATE of carry group g at 128 g (re 64, im 64
+// columns); OUTPUT of (template, batch) e at 256 + 128 (e % 2).
 // ---------------------------------------------------------------------------
 
 constexpr int kCarryWarps = 13;
-constexpr int kPanelBytes = 2 * kTile * kJ * 2;                 // Pr + Pi: 64 KB
-constexpr int kWHalf = 2 * kNii * kTile * 2;                    // W1 or W2: 16 KB
-constexpr int kWBytes = 2 * kWHalf;
-constexpr int kCarrySmem = 2 * kPanelBytes + kBatchGroup * kXsegBytes + 2 * kWBytes;   // 208 KB
+constexpr int kSlots = 3;
+constexpr int kPanelBytes = kTile * 2 * kJ * 2;                 // 32 KB
+constexpr int kWBytes = kTile * 2 * kNii * 2;                   // 32 KB
+constexpr int kExStride = 17;                                   // floats per exchange row
+constexpr int kExBytes = 2 * 64 * kExStride * 4;                // two rounds in flight
+constexpr int kCarrySmem = kSlots * (kPanelBytes + kWBytes) + 2 * kXsegBytes + kExBytes;   // 212 KB
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *m) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s32(m)) : "memory");
@@ -567,23 +576,42 @@ __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// The 128 threads of the panel role (named barrier 1): synchronise, and
+// agree on v (true only if every thread passes true), so that the role
+// leaves its loop as a whole.
+__device__ __forceinline__ bool panel_role_all(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 1, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void panel_role_sync() {
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+}
+
 struct CarryJob {
-    int t, b0, nbg, tile;
+    int t, b0, tile;
     bool first_tile, last_tile;
-    int j, e;   // job index and (template, group) index within this CTA
-    int g;      // pipeline slot: panel buffer, carry group, STATE columns, W buffer
+    int j, e;   // job index and (template, batch) index within this CTA
+    int s, g;   // pipeline slot (panel, W) and carry group (STATE columns)
 };
 
-// The job sequence of this CTA. Jobs alternate between the two slots. When a
-// template has several groups of batches, the filter state v of a tile passes
-// from one group to the next, so a tile keeps its slot (and so its carry
-// threads) for all of them. Every listed template owns at least one tile.
+// The job sequence of this CTA: jobs cycle through the three slots and
+// alternate between the two carry groups. When a template has several
+// batches, the filter state v of a tile passes from one batch to the next,
+// so a tile keeps its carry group for all of them. Every listed template
+// owns at least one tile.
 struct CarryJobs {
     const TcCarryArgs *a;
     int ti, b0, tile, tile0, tile1, t, j, e;
     bool multi, valid;
     __device__ explicit CarryJobs(const TcCarryArgs &A)
-        : a(&A), ti(blockIdx.x), j(0), e(0), multi(A.n_batches > kBatchGroup) {
+        : a(&A), ti(blockIdx.x), j(0), e(0), multi(A.n_batches > 1) {
         start();
     }
     __device__ void start() {
@@ -598,16 +626,14 @@ struct CarryJobs {
     }
     __device__ CarryJob cur() const {
         const int g = multi ? ((tile - tile0) & 1) : (j & 1);
-        return CarryJob{t, b0, min(kBatchGroup, a->n_batches - b0), tile, tile == tile0,
-                        tile == tile1 - 1, j, e, g};
+        return CarryJob{t, b0, tile, tile == tile0, tile == tile1 - 1, j, e, j % kSlots, g};
     }
     __device__ void next() {
         ++j;
         if (++tile < tile1) return;
         tile = tile0;
         ++e;
-        b0 += kBatchGroup;
-        if (b0 < a->n_batches) return;
+        if (++b0 < a->n_batches) return;
         ti += gridDim.x;
         start();
     }
@@ -626,16 +652,17 @@ __device__ __forceinline__ float2 cmul(float2 x, float2 y) {
 template <bool BF16, int LJ>
 __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcCarryArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t panel_full[2], panel_free[2], state_full[2], state_free[2], w_full[2],
-        w_free[2], out_full[2], out_free[2], xs_bar, drain;
+    __shared__ uint64_t panel_full[kSlots], panel_free[kSlots], w_full[kSlots], w_free[kSlots],
+        state_full[2], state_free[2], out_full[2], out_free[2], xs_bar, drain;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
-    unsigned char *Xs = smem + 2 * kPanelBytes;                    // kBatchGroup x 8 KB
-    unsigned char *Wb = Xs + kBatchGroup * kXsegBytes;             // 2 x (W1, W2)
-    // OUTPUT operands, MN-major [k/8][n/8][k%8][n%8] (n = column, k =
-    // filter): 8-column groups 128 bytes apart, 8-filter groups kWK apart;
-    // column 2c = re, 2c + 1 = im of chunk column c:
-    //   W1 = [w_re, w_im],  W2 = [-w_im, w_re]  (D = Rr^T W1 + Ri^T W2)
+    // slot s: panel at s * kPanelBytes, W at kSlots * kPanelBytes + s * kWBytes
+    unsigned char *Wb = smem + kSlots * kPanelBytes;
+    unsigned char *Xs = Wb + kSlots * kWBytes;                     // strain segments of batches b % 2
+    float *ex = reinterpret_cast<float *>(Xs + 2 * kXsegBytes);
+    // OUTPUT operand W, MN-major [k/8][n/8][k%8][n%8] (n = column, k = filter):
+    // 8-column groups 128 bytes apart, 8-filter groups kWK apart; column 2c =
+    // Re w(c), 2c + 1 = Im w(c) of chunk column c = (stream, chunk, j2)
     constexpr uint32_t kWK = (2 * kNii / 8) * 128;
     const int L = LJ * kJ;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -643,13 +670,15 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
     volatile int *abort = &s_abort;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < kSlots; ++i) {
             mbar_init(&panel_full[i], 128);
             mbar_init(&panel_free[i], 1);
-            mbar_init(&state_full[i], 1);
-            mbar_init(&state_free[i], 128);
             mbar_init(&w_full[i], 128);
             mbar_init(&w_free[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&state_full[i], 1);
+            mbar_init(&state_free[i], 128);
             mbar_init(&out_full[i], 1);
             mbar_init(&out_free[i], 128);
         }
@@ -668,17 +697,18 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
             // STATE runs in job order; OUTPUT runs in job order (the first
-            // tile of a (template, group) overwrites the accumulator); each is
+            // tile of a (template, batch) overwrites the accumulator); each is
             // issued as soon as its barriers have completed. All bookkeeping
-            // is in registers: phase parities and slot-use flags as bits of
-            // ph, the OUTPUT queue as 8-bit entries of oq.
-            constexpr uint32_t kPF = 0, kSF = 2, kWF = 4, kOF = 6, kUsed = 8;
+            // is in registers: phase parities and use flags as bits of ph,
+            // the OUTPUT queue as 8-bit entries of oq. Slot phases follow from
+            // the job index (slot use j / kSlots).
+            constexpr uint32_t kSF = 0, kOF = 2, kUsed = 4;
             uint32_t ph = 0, ph_x = 0, ph_d = 0;
-            // queue entry: bit 0 slot, 1 OUTPUT buffer, 2 first tile, 3 last
-            // tile, 4 two batches, 5 buffer used before
+            // queue entry: bits 0-1 slot, 2 OUTPUT buffer, 3 first tile,
+            // 4 last tile, 5 buffer used before
             uint32_t oq = 0;
-            int oq_n = 0, ob_bi = 0;          // queue length; next batch of the head
-            int loaded_b0 = -1;
+            int oq_n = 0, oq_j = 0;           // queue length; job index of the head
+            int loaded0 = -1, loaded1 = -1;   // batch held by segment buffer 0 / 1
             bool issued = false, ok = true;
             CarryJobs st(a);                  // next job for STATE
             const uint32_t id_state = idesc(128, kNii, BF16, false, false);
@@ -687,22 +717,18 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             uint64_t idle0 = 0;
             while (ok && (st.valid || oq_n > 0)) {
                 bool progressed = false;
-                // STATE of the next job: panel ready, slot's STATE columns
-                // free, and no earlier job of this slot still without OUTPUT
+                // STATE of the next job: panel ready and the carry group's
+                // STATE columns free
                 if (st.valid && oq_n < 4) {
                     const CarryJob J = st.cur();
-                    const uint32_t g = (uint32_t)J.g;
-                    bool same = false;
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        same |= (i < oq_n) && (((oq >> (8 * i)) & 1u) == g);
+                    const uint32_t g = (uint32_t)J.g, sl = (uint32_t)J.s;
                     const bool used = (ph >> (kUsed + g)) & 1u;
-                    if (!same && (!used || mbar_test(&state_free[g], (ph >> (kSF + g)) & 1u)) &&
-                        mbar_test(&panel_full[g], (ph >> (kPF + g)) & 1u)) {
+                    if ((!used || mbar_test(&state_free[g], (ph >> (kSF + g)) & 1u)) &&
+                        mbar_test(&panel_full[sl], (uint32_t)(J.j / kSlots) & 1u)) {
                         if (used) ph ^= 1u << (kSF + g);
-                        ph ^= 1u << (kPF + g);
                         ph |= 1u << (kUsed + g);
-                        if (J.b0 != loaded_b0) {
+                        const int xb = J.b0 & 1;
+                        if (J.b0 != (xb ? loaded1 : loaded0)) {
                             // the STATE contractions that read the old segments are done
                             if (issued) {
                                 mma_commit(&drain);
@@ -710,74 +736,66 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                                 ph_d ^= 1u;
                             }
                             if (ok) {
-                                mbar_expect(&xs_bar, J.nbg * kXsegBytes);
-                                bulk_load(Xs, a.xseg + (size_t)J.b0 * (kXsegBytes / 16), J.nbg * kXsegBytes,
-                                          &xs_bar);
+                                mbar_expect(&xs_bar, kXsegBytes);
+                                bulk_load(Xs + xb * kXsegBytes, a.xseg + (size_t)J.b0 * (kXsegBytes / 16),
+                                          kXsegBytes, &xs_bar);
                                 ok = mbar_wait_ab(&xs_bar, ph_x, a.status, abort);
                                 ph_x ^= 1u;
                             }
                             if (!ok) break;
-                            loaded_b0 = J.b0;
+                            if (xb) loaded1 = J.b0;
+                            else loaded0 = J.b0;
                         }
                         tc_fence_after();
-                        // descriptors advance by 16-byte units in their low bits
-                        const uint64_t dr0 = sdesc(smem0 + g * kPanelBytes, 128, 2048);
-                        const uint64_t di0 = dr0 + ((kPanelBytes / 2) >> 4);
-                        for (int bi = 0; bi < J.nbg; ++bi) {
-                            const uint64_t dx0 = sdesc(xs0 + bi * kXsegBytes, 128, 2048);
-                            const uint32_t d = tmem + 128 * g + 64 * bi;
+                        // descriptors advance by 16-byte units in their low bits;
+                        // re powers are panel k-blocks 0..7, im powers 8..15
+                        const uint64_t dr0 = sdesc(smem0 + sl * kPanelBytes, 128, 2048);
+                        const uint64_t di0 = dr0 + ((kJ / 8 * 128) >> 4);
+                        const uint64_t dx0 = sdesc(xs0 + xb * kXsegBytes, 128, (kJ / 8) * 128);
+                        const uint32_t d = tmem + 128 * g;
 #pragma unroll
-                            for (int kk = 0; kk < kJ / 16; ++kk) {
-                                const uint64_t o = (uint64_t)(kk * 256) >> 4;
-                                mma(d, dr0 + o, dx0 + o, id_state, kk ? 1u : 0u);
-                                mma(d + kNii, di0 + o, dx0 + o, id_state, kk ? 1u : 0u);
-                            }
+                        for (int kk = 0; kk < kJ / 16; ++kk) {
+                            const uint64_t o = (uint64_t)(kk * 256) >> 4;
+                            mma(d, dr0 + o, dx0 + o, id_state, kk ? 1u : 0u);
+                            mma(d + kNii, di0 + o, dx0 + o, id_state, kk ? 1u : 0u);
                         }
                         mma_commit(&state_full[g]);
                         issued = true;
-                        const uint32_t ent = g | ((uint32_t)(J.e & 1) << 1) | ((uint32_t)J.first_tile << 2) |
-                                             ((uint32_t)J.last_tile << 3) | ((uint32_t)(J.nbg == 2) << 4) |
-                                             ((uint32_t)(J.e >= 2) << 5);
+                        const uint32_t ent = sl | ((uint32_t)(J.e & 1) << 2) | ((uint32_t)J.first_tile << 3) |
+                                             ((uint32_t)J.last_tile << 4) | ((uint32_t)(J.e >= 2) << 5);
+                        if (oq_n == 0) oq_j = J.j;
                         oq |= ent << (8 * oq_n);
                         ++oq_n;
                         st.next();
                         progressed = true;
                     }
                 }
-                // OUTPUT of the oldest job, batch by batch:
-                //   D = Rr^T W1 + Ri^T W2
+                // OUTPUT of the oldest job: D = R^T W over the tile's filters
                 if (oq_n > 0) {
                     const uint32_t ent = oq & 0xFFu;
-                    const uint32_t g = ent & 1u, ob = (ent >> 1) & 1u;
-                    const bool first = (ent >> 2) & 1u, last = (ent >> 3) & 1u;
-                    const int nbg = ((ent >> 4) & 1u) ? 2 : 1;
-                    const bool need_of = first && ob_bi == 0 && ((ent >> 5) & 1u);
+                    const uint32_t sl = ent & 3u, ob = (ent >> 2) & 1u;
+                    const bool first = (ent >> 3) & 1u, last = (ent >> 4) & 1u;
+                    const bool need_of = first && ((ent >> 5) & 1u);
                     const bool of_ok = !need_of || mbar_test(&out_free[ob], (ph >> (kOF + ob)) & 1u);
-                    if (of_ok && mbar_test(&w_full[g], (ph >> (kWF + g)) & 1u)) {
+                    if (of_ok && mbar_test(&w_full[sl], (uint32_t)(oq_j / kSlots) & 1u)) {
                         if (need_of) ph ^= 1u << (kOF + ob);
-                        ph ^= 1u << (kWF + g);
                         tc_fence_after();
-                        const uint64_t ar0 = sdesc(smem0 + g * kPanelBytes, 2048, 128);
-                        const uint64_t ai0 = ar0 + ((kPanelBytes / 2) >> 4);
-                        const uint64_t b10 = sdesc(wb0 + g * kWBytes, kWK, 128);
-                        const uint64_t b20 = b10 + (kWHalf >> 4);
-                        const uint32_t dz = tmem + 256 + 128 * ob + 64 * ob_bi;
+                        const uint64_t a0 = sdesc(smem0 + sl * kPanelBytes, 2048, 128);
+                        const uint64_t b0 = sdesc(wb0 + sl * kWBytes, kWK, 128);
+                        const uint32_t dz = tmem + 256 + 128 * ob;
                         const uint32_t acc0 = first ? 0u : 1u;
 #pragma unroll
                         for (int kk = 0; kk < kTile / 16; ++kk) {
                             const uint64_t oa = (uint64_t)(kk * 2 * 2048) >> 4;
                             const uint64_t ow = (uint64_t)(kk * 2 * kWK) >> 4;
-                            mma(dz, ar0 + oa, b10 + ow, id_out, kk ? 1u : acc0);
-                            mma(dz, ai0 + oa, b20 + ow, id_out, 1u);
+                            mma(dz, a0 + oa, b0 + ow, id_out, kk ? 1u : acc0);
                         }
-                        mma_commit(&w_free[g]);
-                        if (++ob_bi == nbg) {
-                            mma_commit(&panel_free[g]);
-                            if (last) mma_commit(&out_full[ob]);
-                            oq >>= 8;
-                            --oq_n;
-                            ob_bi = 0;
-                        }
+                        mma_commit(&w_free[sl]);
+                        mma_commit(&panel_free[sl]);
+                        if (last) mma_commit(&out_full[ob]);
+                        oq >>= 8;
+                        --oq_n;
+                        ++oq_j;
                         progressed = true;
                     }
                 }
@@ -803,46 +821,61 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
         }
     } else if (warp <= 4) {
         // ---------------- power panels and epilogue ----------------
-        // panel: thread = filter k: R[k][i] = a_k^i, i < 128, as four chains of
-        // 16 powers per half (the second half starts from a_k^64); layout
-        // [k/8][i/8][k%8][i%8]
+        // panel: thread = filter k: a_k^i, i < 64, as four chains of 16
+        // powers (starting from a^0, a^16, a^32, a^48)
         const int k = threadIdx.x - 32;
-        // epilogue: lane j1; column c = (s, chunk, j2) of the re and im
-        // halves -> z = scale * value (the FIR kernel adds its term afterwards)
-        const int j1 = (warp & 3) * 32 + lane;
+        // epilogue: thread = tensor-memory lane m; rows 0..63 (warps 4 and 1)
+        // combine with rows 64..127 (warps 2 and 3) through the exchange rows
+        const int m = (warp & 3) * 32 + lane;
+        const bool top = m < 64;
         const uint32_t lane_base = ((uint32_t)((warp & 3) * 32)) << 16;
-        // (template, group)s awaiting the epilogue, oldest first (at most 3)
         struct Ep {
-            int t, b0, nbg, e, j;
+            int t, b0, e, j;
         };
-        Ep ep0{}, ep1{}, ep2{};
+        Ep ep0{}, ep1{}, ep2{}, ep3{}, ep4{};   // pending epilogues, oldest first (at most 5)
         int ep_n = 0;
         auto epilogue = [&](const Ep &J) -> bool {
             const int ob = J.e & 1;
-            if (!mbar_wait_ab(&out_full[ob], (J.e >> 1) & 1, a.status, abort)) return false;
+            if (!panel_role_all(mbar_wait_ab(&out_full[ob], (J.e >> 1) & 1, a.status, abort))) return false;
             tc_fence_after();
-            for (int bi = 0; bi < J.nbg; ++bi) {
-                const int b = J.b0 + bi;
-                const int nb = min(a.cpb, a.n_chunks - b * a.cpb);
-                const int nii = S * nb * LJ;
-                const uint32_t tb = tmem + lane_base + 256 + 128 * ob + 64 * bi;
+            const int b = J.b0;
+            const int nb = min(a.cpb, a.n_chunks - b * a.cpb);
+            const int nc = nb * LJ, nii = S * nc;        // columns per stream, in all
+            const uint32_t tb = tmem + lane_base + 256 + 128 * ob;
+            const int j1 = m & 63;
+            // z of stream 0 and 1 at this batch's first sample and lane j1
+            float2 *zb0 = a.z + (int64_t)a.stream0 * a.z_stream_stride + (int64_t)J.t * a.z_row_stride +
+                          (int64_t)b * a.cpb * L + j1;
+            float2 *zb1 = zb0 + a.z_stream_stride;
+            // 64 columns per tensor-memory round trip, exchanged 16 at a time
+            for (int hh = 0; hh < 2 * kNii / 64; ++hh) {
+                uint32_t v[4][16];
 #pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {       // chunk columns 16 hh .. 16 hh + 15
-                    uint32_t vv[2][16];
-                    tmem_ld16_nw(tb + 32 * hh, vv[0]);
-                    tmem_ld16_nw(tb + 32 * hh + 16, vv[1]);
-                    tmem_wait_ld();
+                for (int i = 0; i < 4; ++i) tmem_ld16_nw(tb + 64 * hh + 16 * i, v[i]);
+                tmem_wait_ld();
 #pragma unroll
-                    for (int c16 = 0; c16 < 16; ++c16) {
-                        const int c = 16 * hh + c16;
-                        if (c < nii) {
-                            const int s2 = c / (nb * LJ), rem = c - s2 * (nb * LJ);
-                            const int cc = rem / LJ, j2 = rem - cc * LJ;
-                            float2 *zp = a.z + (int64_t)(a.stream0 + s2) * a.z_stream_stride +
-                                         (int64_t)J.t * a.z_row_stride +
-                                         (int64_t)(b * a.cpb + cc) * L + kJ * j2 + j1;
-                            *zp = make_float2(a.scale * __uint_as_float(vv[c16 >> 3][(2 * c16) & 15]),
-                                              a.scale * __uint_as_float(vv[c16 >> 3][(2 * c16 + 1) & 15]));
+                for (int i4 = 0; i4 < 4; ++i4) {
+                    const int h = 4 * hh + i4;          // 16 columns = 8 chunk columns
+                    float *row = ex + (h & 1) * (64 * kExStride) + j1 * kExStride;
+                    if (!top) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) row[i] = __uint_as_float(v[i4][i]);
+                    }
+                    // rows of round h are written, and every top thread read
+                    // the other buffer (round h - 1) before arriving here
+                    panel_role_sync();
+                    if (top) {
+#pragma unroll
+                        for (int i = 0; i < 16; i += 2) {
+                            const int c = 8 * h + i / 2;
+                            if (c < nii) {
+                                const float zr = __uint_as_float(v[i4][i]) - row[i + 1];
+                                const float zi = __uint_as_float(v[i4][i + 1]) + row[i];
+                                const bool s1 = c >= nc;                // at most two streams
+                                const int rem = s1 ? c - nc : c;
+                                float2 *zp = (s1 ? zb1 : zb0) + (rem / LJ) * L + kJ * (rem % LJ);
+                                *zp = make_float2(a.scale * zr, a.scale * zi);
+                            }
                         }
                     }
                 }
@@ -851,184 +884,204 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             mbar_arrive(&out_free[ob]);
             return true;
         };
-        uint32_t used = 0, pfp = 0;           // slot used before; panel_free parity
         bool ok = true;
         carry_jobs(a, [&](const CarryJob &J) -> bool {
-            const int g = J.g;
+            const int sl = J.s;
             const int64_t slot = (int64_t)J.tile * kTile + k;
-            const float2 ak = a.a[slot], a64 = a.a64[slot];
-            // epilogues whose last tile is at least two jobs back
+            const float2 ak = a.a[slot];
+            // Epilogues whose last tile is at least two jobs back, taken
+            // when their contractions have finished; one five or more jobs
+            // back is waited for, since the OUTPUT that frees this job's slot
+            // may need its accumulator (first tile of the (template, batch)
+            // two after it).
             while (ep_n > 0 && ep0.j <= J.j - 2) {
+                if (ep0.j > J.j - 5 &&
+                    !panel_role_all(mbar_test(&out_full[ep0.e & 1], (ep0.e >> 1) & 1)))
+                    break;
                 if (!(ok = epilogue(ep0))) return false;
                 ep0 = ep1;
                 ep1 = ep2;
+                ep2 = ep3;
+                ep3 = ep4;
                 --ep_n;
             }
             if (J.last_tile) {
-                const Ep n{J.t, J.b0, J.nbg, J.e, J.j};
+                const Ep n{J.t, J.b0, J.e, J.j};
                 if (ep_n == 0) ep0 = n;
                 else if (ep_n == 1) ep1 = n;
-                else ep2 = n;
+                else if (ep_n == 2) ep2 = n;
+                else if (ep_n == 3) ep3 = n;
+                else ep4 = n;
                 ++ep_n;
             }
-            if ((used >> g) & 1u) {
-                if (!(ok = mbar_wait_ab(&panel_free[g], (pfp >> g) & 1u, a.status, abort))) return false;
-                pfp ^= 1u << g;
-            }
-            used |= 1u << g;
-            unsigned char *Pr = smem + g * kPanelBytes, *Pi = Pr + kPanelBytes / 2;
+            const int use = J.j / kSlots;
+            if (!(ok = panel_role_all(use == 0 || mbar_wait_ab(&panel_free[sl], (use - 1) & 1, a.status, abort))))
+                return false;
+            unsigned char *P = smem + sl * kPanelBytes;
             float2 a16 = ak;
 #pragma unroll
             for (int i = 0; i < 4; ++i) a16 = cmul(a16, a16);
+            float2 p[4];
+            p[0] = make_float2(1.f, 0.f);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                float2 p[4];
-                p[0] = h ? a64 : make_float2(1.f, 0.f);
+            for (int i = 1; i < 4; ++i) p[i] = cmul(p[i - 1], a16);
 #pragma unroll
-                for (int i = 1; i < 4; ++i) p[i] = cmul(p[i - 1], a16);
+            for (int ib = 0; ib < 2; ++ib) {
+                float vr[4][8], vi[4][8];
 #pragma unroll
-                for (int ib = 0; ib < 2; ++ib) {
-                    float vr[4][8], vi[4][8];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-#pragma unroll
-                        for (int ch = 0; ch < 4; ++ch) {
-                            vr[ch][q] = p[ch].x;
-                            vi[ch][q] = p[ch].y;
-                            p[ch] = cmul(p[ch], ak);
-                        }
-                    }
+                for (int q = 0; q < 8; ++q) {
 #pragma unroll
                     for (int ch = 0; ch < 4; ++ch) {
-                        const int kb = h * 8 + ch * 2 + ib;
-                        const size_t off = (size_t)(k >> 3) * 2048 + kb * 128 + (k & 7) * 16;
-                        *reinterpret_cast<uint4 *>(Pr + off) = pack8<BF16>(vr[ch]);
-                        *reinterpret_cast<uint4 *>(Pi + off) = pack8<BF16>(vi[ch]);
+                        vr[ch][q] = p[ch].x;
+                        vi[ch][q] = p[ch].y;
+                        p[ch] = cmul(p[ch], ak);
                     }
+                }
+#pragma unroll
+                for (int ch = 0; ch < 4; ++ch) {
+                    const int kb = ch * 2 + ib;                 // powers 8 kb .. 8 kb + 7
+                    const size_t off = (size_t)(k >> 3) * 2048 + kb * 128 + (k & 7) * 16;
+                    *reinterpret_cast<uint4 *>(P + off) = pack8<BF16>(vr[ch]);
+                    *reinterpret_cast<uint4 *>(P + off + 8 * 128) = pack8<BF16>(vi[ch]);
                 }
             }
             fence_async_smem();
-            mbar_arrive(&panel_full[g]);
+            mbar_arrive(&panel_full[sl]);
             return true;
         });
         if (ok && ep_n > 0) ok = epilogue(ep0);
         if (ok && ep_n > 1) ok = epilogue(ep1);
         if (ok && ep_n > 2) ok = epilogue(ep2);
+        if (ok && ep_n > 3) ok = epilogue(ep3);
+        if (ok && ep_n > 4) ok = epilogue(ep4);
     } else if (warp <= 12) {
         // ---------------- carry groups ----------------
         const int grp = (warp - 5) >> 2;
         const int k = (warp & 3) * 32 + lane;                 // tensor-memory lane = filter
         const uint32_t lane_base = ((uint32_t)((warp & 3) * 32)) << 16;
         const uint32_t kofs = (uint32_t)(k >> 3) * kWK + (k & 7) * 16;
-        uint32_t n_state = 0, n_w = 0;
+        uint32_t n_state = 0;
         carry_jobs(a, [&](const CarryJob &J) -> bool {
             if (J.g != grp) return true;
+            const int sl = J.s;
             const int64_t slot = (int64_t)J.tile * kTile + k;
             const float2 ak = a.a[slot], aJ = a.aJ[slot], ck = a.c[slot], aLf = a.aLf[slot];
+            const double2 aLb = a.aLb[slot];
+            // per job: aJ^i2 for the state sums, a^(kJ j2) a c for the outputs
+            float2 pj[LJ], cj[LJ];
+            pj[0] = make_float2(1.f, 0.f);
+            cj[0] = cmul(ak, ck);
+#pragma unroll
+            for (int i = 1; i < LJ; ++i) {
+                pj[i] = cmul(pj[i - 1], aJ);
+                cj[i] = cmul(cj[i - 1], aJ);
+            }
             double2 v0 = a.v[(int64_t)a.stream0 * a.n_slots + slot];
             double2 v1 = S > 1 ? a.v[(int64_t)(a.stream0 + 1) * a.n_slots + slot] : make_double2(0, 0);
             if (!mbar_wait_ab(&state_full[grp], n_state & 1, a.status, abort)) return false;
             ++n_state;
             tc_fence_after();
-            unsigned char *W1 = Wb + grp * kWBytes, *W2 = W1 + kWHalf;
-            const double2 aLb = a.aLb[slot];
-            for (int bi = 0; bi < J.nbg; ++bi) {
-                const int b = J.b0 + bi;
-                const int nb = min(a.cpb, a.n_chunks - b * a.cpb);
-                const int nsteps = S * nb;                          // (stream, chunk) steps
-                if (n_w > 0 && !mbar_wait_ab(&w_free[grp], (n_w - 1) & 1, a.status, abort)) return false;
-                ++n_w;
-                // Carry across this batch. The batch's starting state v is
-                // FP64; chunk states inside the batch are FP32:
-                //   v_c = a^(cL) v + d_c,  d_{c+1} = a^L d_c + U_c,  d_0 = 0,
-                // and the next batch starts from a^(nb L) v + d_nb in FP64.
-                float2 p = make_float2((float)v0.x, (float)v0.y);   // a^(cL) v
-                float2 dd = make_float2(0.f, 0.f);                   // d_c
-                float2 d_s0 = dd;
-                // STATE columns: (stream, chunk, i2) -> (s nb + c) LJ + i2, read
-                // 16 at a time (16 / LJ steps). One step writes columns
-                // 2 q LJ .. 2 q LJ + 2 LJ - 1 of W1 and W2: 4 LJ contiguous bytes
-                // at (k/8) kWK + (n/8) 128 + (k%8) 16 + (n%8) 2
-                const uint32_t tb = tmem + lane_base + 128 * grp + 64 * bi;
-                constexpr int kSteps = 16 / LJ;
+            const int use = J.j / kSlots;
+            if (use > 0 && !mbar_wait_ab(&w_free[sl], (use - 1) & 1, a.status, abort)) return false;
+            unsigned char *W = Wb + sl * kWBytes;
+            const int b = J.b0;
+            const int nb = min(a.cpb, a.n_chunks - b * a.cpb);
+            const int nsteps = S * nb;                          // (stream, chunk) steps
+            // Carry across this batch. The batch's starting state v is FP64;
+            // chunk states inside the batch are FP32:
+            //   v_c = a^(cL) v + d_c,  d_{c+1} = a^L d_c + U_c,  d_0 = 0,
+            // and the next batch starts from a^(nb L) v + d_nb in FP64.
+            float2 p = make_float2((float)v0.x, (float)v0.y);   // a^(cL) v
+            float2 dd = make_float2(0.f, 0.f);                   // d_c
+            float2 d_s0 = dd;
+            // STATE columns: (stream, chunk, i2) -> (s nb + c) LJ + i2, read 32
+            // at a time (32 / LJ steps). Step q writes W columns 2 q LJ ..
+            // 2 q LJ + 2 LJ - 1: 4 LJ contiguous bytes at (k/8) kWK + q LJ / 4 * 128
+            // + (2 q LJ % 8) * 2 + (k%8) 16.
+            const uint32_t tb = tmem + lane_base + 128 * grp;
+            constexpr int kSteps = 16 / LJ;
 #pragma unroll
-                for (int half = 0; half < 2; ++half) {
-                    uint32_t rr[16], ri[16];
-                    tmem_ld16_nw(tb + 16 * half, rr);
-                    tmem_ld16_nw(tb + kNii + 16 * half, ri);
-                    tmem_wait_ld();
-                    if (half == 1 && bi == J.nbg - 1) {
-                        tc_fence_before();
-                        mbar_arrive(&state_free[grp]);
+            for (int pp = 0; pp < kNii / 32; ++pp) {          // 32 columns per round trip
+                uint32_t rr[2][16], ri[2][16];
+                tmem_ld16_nw(tb + 32 * pp, rr[0]);
+                tmem_ld16_nw(tb + 32 * pp + 16, rr[1]);
+                tmem_ld16_nw(tb + kNii + 32 * pp, ri[0]);
+                tmem_ld16_nw(tb + kNii + 32 * pp + 16, ri[1]);
+                tmem_wait_ld();
+                if (pp == kNii / 32 - 1) {
+                    tc_fence_before();
+                    mbar_arrive(&state_free[grp]);
+                }
+#pragma unroll
+                for (int qq = 0; qq < 2 * kSteps; ++qq) {
+                    const int q = pp * 2 * kSteps + qq;
+                    const int n = 2 * q * LJ;
+                    const uint32_t off = kofs + (uint32_t)(n >> 3) * 128 + (n & 7) * 2;
+                    float wr[LJ], wi[LJ];
+                    if (q < nsteps) {
+                        if (q == nb) {                            // stream 1 starts
+                            d_s0 = dd;
+                            p = make_float2((float)v1.x, (float)v1.y);
+                            dd = make_float2(0.f, 0.f);
+                        }
+                        // U = sum_i2 aJ^i2 G(i2)
+                        const int c0 = qq * LJ;
+                        float ur = __uint_as_float(rr[c0 >> 4][c0 & 15]);
+                        float ui = __uint_as_float(ri[c0 >> 4][c0 & 15]);
+#pragma unroll
+                        for (int i2 = 1; i2 < LJ; ++i2) {
+                            const int c = c0 + i2;
+                            const float gr = __uint_as_float(rr[c >> 4][c & 15]);
+                            const float gi = __uint_as_float(ri[c >> 4][c & 15]);
+                            ur = fmaf(pj[i2].x, gr, fmaf(-pj[i2].y, gi, ur));
+                            ui = fmaf(pj[i2].x, gi, fmaf(pj[i2].y, gr, ui));
+                        }
+                        const float2 vv = make_float2(p.x + dd.x, p.y + dd.y);
+#pragma unroll
+                        for (int j2 = 0; j2 < LJ; ++j2) {
+                            const float2 w = cmul(cj[j2], vv);
+                            wr[j2] = w.x;
+                            wi[j2] = w.y;
+                        }
+                        dd = make_float2(fmaf(aLf.x, dd.x, fmaf(-aLf.y, dd.y, ur)),
+                                         fmaf(aLf.x, dd.y, fmaf(aLf.y, dd.x, ui)));
+                        p = cmul(aLf, p);
+                    } else {
+                        // columns past this batch contribute nothing
+#pragma unroll
+                        for (int j2 = 0; j2 < LJ; ++j2) wr[j2] = wi[j2] = 0.f;
                     }
-#pragma unroll
-                    for (int qq = 0; qq < kSteps; ++qq) {
-                        const int q = half * kSteps + qq;
-                        const int n = 2 * q * LJ;
-                        const uint32_t off = kofs + (uint32_t)(n >> 3) * 128 + (n & 7) * 2;
-                        float wr[LJ], wi[LJ];
-                        if (q < nsteps) {
-                            if (q == nb) {                            // stream 1 starts
-                                d_s0 = dd;
-                                p = make_float2((float)v1.x, (float)v1.y);
-                                dd = make_float2(0.f, 0.f);
-                            }
-                            const int c1 = qq * LJ + LJ - 1;
-                            float2 u = make_float2(__uint_as_float(rr[c1]), __uint_as_float(ri[c1]));
-#pragma unroll
-                            for (int i2 = LJ - 2; i2 >= 0; --i2) {
-                                const int c = qq * LJ + i2;
-                                u = make_float2(u.x * aJ.x - u.y * aJ.y + __uint_as_float(rr[c]),
-                                                u.x * aJ.y + u.y * aJ.x + __uint_as_float(ri[c]));
-                            }
-                            const float2 vv = make_float2(p.x + dd.x, p.y + dd.y);
-                            float2 w = cmul(ak, cmul(ck, vv));
-                            const float2 ndd = cmul(aLf, dd);
-                            dd = make_float2(ndd.x + u.x, ndd.y + u.y);
-                            p = cmul(aLf, p);
-#pragma unroll
-                            for (int j2 = 0; j2 < LJ; ++j2) {
-                                wr[j2] = w.x;
-                                wi[j2] = w.y;
-                                w = cmul(w, aJ);
-                            }
-                        } else {
-                            // columns past this batch contribute nothing
-#pragma unroll
-                            for (int j2 = 0; j2 < LJ; ++j2) wr[j2] = wi[j2] = 0.f;
-                        }
-                        if constexpr (LJ == 2) {
-                            *reinterpret_cast<uint2 *>(W1 + off) =
-                                make_uint2(pack2<BF16>(wr[0], wi[0]), pack2<BF16>(wr[1], wi[1]));
-                            *reinterpret_cast<uint2 *>(W2 + off) =
-                                make_uint2(pack2<BF16>(-wi[0], wr[0]), pack2<BF16>(-wi[1], wr[1]));
-                        } else {
-                            *reinterpret_cast<uint32_t *>(W1 + off) = pack2<BF16>(wr[0], wi[0]);
-                            *reinterpret_cast<uint32_t *>(W2 + off) = pack2<BF16>(-wi[0], wr[0]);
-                        }
+                    if constexpr (LJ == 4) {
+                        *reinterpret_cast<uint4 *>(W + off) =
+                            make_uint4(pack2<BF16>(wr[0], wi[0]), pack2<BF16>(wr[1], wi[1]),
+                                       pack2<BF16>(wr[2], wi[2]), pack2<BF16>(wr[3], wi[3]));
+                    } else {
+                        *reinterpret_cast<uint2 *>(W + off) =
+                            make_uint2(pack2<BF16>(wr[0], wi[0]), pack2<BF16>(wr[1], wi[1]));
                     }
                 }
-                if (S == 1) d_s0 = dd;
-                fence_async_smem();
-                mbar_arrive(&w_full[grp]);
-                // v <- a^(nb L) v + d_nb in FP64, per stream
-                double2 pw;
-                if (nb == a.cpb) {
-                    pw = aLb;
-                } else {
-                    const double2 aL = a.aL[slot];
-                    pw = aL;
-                    for (int i = 1; i < nb; ++i)
-                        pw = make_double2(pw.x * aL.x - pw.y * aL.y, pw.x * aL.y + pw.y * aL.x);
-                }
-                v0 = make_double2(fma(pw.x, v0.x, fma(-pw.y, v0.y, (double)d_s0.x)),
-                                  fma(pw.x, v0.y, fma(pw.y, v0.x, (double)d_s0.y)));
-                if (S > 1)
-                    v1 = make_double2(fma(pw.x, v1.x, fma(-pw.y, v1.y, (double)dd.x)),
-                                      fma(pw.x, v1.y, fma(pw.y, v1.x, (double)dd.y)));
             }
+            if (S == 1) d_s0 = dd;
+            // v <- a^(nb L) v + d_nb in FP64, per stream
+            double2 pw;
+            if (nb == a.cpb) {
+                pw = aLb;
+            } else {
+                const double2 aL = a.aL[slot];
+                pw = aL;
+                for (int i = 1; i < nb; ++i)
+                    pw = make_double2(pw.x * aL.x - pw.y * aL.y, pw.x * aL.y + pw.y * aL.x);
+            }
+            v0 = make_double2(fma(pw.x, v0.x, fma(-pw.y, v0.y, (double)d_s0.x)),
+                              fma(pw.x, v0.y, fma(pw.y, v0.x, (double)d_s0.y)));
             a.v[(int64_t)a.stream0 * a.n_slots + slot] = v0;
-            if (S > 1) a.v[(int64_t)(a.stream0 + 1) * a.n_slots + slot] = v1;
+            if (S > 1) {
+                v1 = make_double2(fma(pw.x, v1.x, fma(-pw.y, v1.y, (double)dd.x)),
+                                  fma(pw.x, v1.y, fma(pw.y, v1.x, (double)dd.y)));
+                a.v[(int64_t)(a.stream0 + 1) * a.n_slots + slot] = v1;
+            }
+            fence_async_smem();
+            mbar_arrive(&w_full[sl]);
             return true;
         });
     }
@@ -1057,7 +1110,7 @@ struct TcBank {
     float *row_scale = nullptr;
     int32_t *tile_ptr = nullptr, *tmpl_of = nullptr;
     uint8_t *has_carry = nullptr;
-    float2 *a = nullptr, *a64 = nullptr, *aJ = nullptr, *c = nullptr, *aLf = nullptr;
+    float2 *a = nullptr, *aJ = nullptr, *c = nullptr, *aLf = nullptr;
     double2 *aL = nullptr, *v = nullptr, *aLb1 = nullptr, *aLb2 = nullptr;
     float *xbuf = nullptr, *stage = nullptr;
     float2 *z = nullptr;
@@ -1116,7 +1169,7 @@ int64_t tc_bytes(const spiir_bank_desc *d, const TcPlan &p) {
     int64_t b = 0;
     b += (int64_t)p.n_groups * p.n_slices * kSliceBytes;
     b += (int64_t)p.T * 4 + (p.T + 1) * 4 + p.T * 4;
-    b += p.n_slots * (8 * 5 + 16 * 3);
+    b += p.n_slots * (8 * 4 + 16 * 3);
     b += S * p.n_slots * 16;
     b += S * p.xbuf_stride * 4 + S * p.ring_len * 4;
     b += S * (int64_t)p.T * p.ring_len * 8;
@@ -1228,7 +1281,7 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
 
     // Carry tiles: 128 filter slots each, template-major.
     std::vector<int32_t> tile_ptr(p.T + 1, 0), tmpl_of;
-    std::vector<float2> av(p.n_slots), a64v(p.n_slots), aJv(p.n_slots), cv(p.n_slots);
+    std::vector<float2> av(p.n_slots), aJv(p.n_slots), cv(p.n_slots);
     std::vector<double2> aLv(p.n_slots), aLb1v(p.n_slots), aLb2v(p.n_slots);
     std::vector<float2> aLfv(p.n_slots);
     const int cpb1 = carry_cpb(1, p.L), cpb2 = carry_cpb(2, p.L);
@@ -1253,8 +1306,7 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
                 };
                 const std::complex<double> aL = pw(p.L), ck = pw(p.F - d->delay[k]) * bb;
                 av[slot] = make_float2(d->a_re[k], d->a_im[k]);
-                const auto p64 = pw(64), pJ = pw(kJ);
-                a64v[slot] = make_float2((float)p64.real(), (float)p64.imag());
+                const auto pJ = pw(kJ);
                 aJv[slot] = make_float2((float)pJ.real(), (float)pJ.imag());
                 aLv[slot] = make_double2(aL.real(), aL.imag());
                 aLfv[slot] = make_float2((float)aL.real(), (float)aL.imag());
@@ -1263,7 +1315,7 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
                 aLb2v[slot] = make_double2(b2.real(), b2.imag());
                 cv[slot] = make_float2((float)ck.real(), (float)ck.imag());
             } else {
-                av[slot] = a64v[slot] = aJv[slot] = cv[slot] = aLfv[slot] = make_float2(0.f, 0.f);
+                av[slot] = aJv[slot] = cv[slot] = aLfv[slot] = make_float2(0.f, 0.f);
                 aLv[slot] = aLb1v[slot] = aLb2v[slot] = make_double2(0.0, 0.0);
             }
         }
@@ -1281,7 +1333,6 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
     if ((st = tc_upload(&b->tmpl_of, tmpl_of, s))) return st;
     if ((st = tc_upload(&b->has_carry, has_carry, s))) return st;
     if ((st = tc_upload(&b->a, av, s))) return st;
-    if ((st = tc_upload(&b->a64, a64v, s))) return st;
     if ((st = tc_upload(&b->aJ, aJv, s))) return st;
     if ((st = tc_upload(&b->c, cv, s))) return st;
     if ((st = tc_upload(&b->aL, aLv, s))) return st;
@@ -1311,8 +1362,8 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
     TC_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     {
         const void *fns[6] = {(const void *)tc_fir_kernel<true>, (const void *)tc_fir_kernel<false>,
-                              (const void *)tc_carry_kernel<true, 1>, (const void *)tc_carry_kernel<true, 2>,
-                              (const void *)tc_carry_kernel<false, 1>, (const void *)tc_carry_kernel<false, 2>};
+                              (const void *)tc_carry_kernel<true, 2>, (const void *)tc_carry_kernel<true, 4>,
+                              (const void *)tc_carry_kernel<false, 2>, (const void *)tc_carry_kernel<false, 4>};
         const int need[6] = {fir_smem_of(p.L, p.K), fir_smem_of(p.L, p.K), kCarrySmem, kCarrySmem,
                              kCarrySmem, kCarrySmem};
         for (int i = 0; i < 6; ++i) {
@@ -1402,7 +1453,6 @@ spiir_status spiir_tc_push(TcBank *b, int s0, int count, const float *x, int64_t
         ca.tmpl_of = b->tmpl_of;
         ca.n_carry = b->n_carry_ctas;
         ca.a = b->a;
-        ca.a64 = b->a64;
         ca.aJ = b->aJ;
         ca.aL = b->aL;
         ca.aLf = b->aLf;
@@ -1426,15 +1476,15 @@ spiir_status spiir_tc_push(TcBank *b, int s0, int count, const float *x, int64_t
         const int thr = kCarryWarps * 32;
         timer->begin(SPIIR_K_TC_CARRY, s);
         if (b->bf16) {
-            if (b->L == kJ)
-                tc_carry_kernel<true, 1><<<grid, thr, kCarrySmem, s>>>(ca);
-            else
+            if (b->L == 2 * kJ)
                 tc_carry_kernel<true, 2><<<grid, thr, kCarrySmem, s>>>(ca);
-        } else {
-            if (b->L == kJ)
-                tc_carry_kernel<false, 1><<<grid, thr, kCarrySmem, s>>>(ca);
             else
+                tc_carry_kernel<true, 4><<<grid, thr, kCarrySmem, s>>>(ca);
+        } else {
+            if (b->L == 2 * kJ)
                 tc_carry_kernel<false, 2><<<grid, thr, kCarrySmem, s>>>(ca);
+            else
+                tc_carry_kernel<false, 4><<<grid, thr, kCarrySmem, s>>>(ca);
         }
         TC_CUDA(cudaGetLastError());
         timer->end(s);
@@ -1514,7 +1564,7 @@ int64_t spiir_tc_footprint(const spiir_bank_desc *d) {
 
 void spiir_tc_destroy(TcBank *b) {
     if (!b) return;
-    void *ptrs[] = {b->H, b->row_scale, b->tile_ptr, b->tmpl_of, b->has_carry, b->a, b->a64, b->aJ, b->c,
+    void *ptrs[] = {b->H, b->row_scale, b->tile_ptr, b->tmpl_of, b->has_carry, b->a, b->aJ, b->c,
                     b->aL, b->v, b->xbuf, b->stage, b->z, b->status, b->hank, b->xseg,
                     b->aLf, b->aLb1, b->aLb2};
     for (void *q : ptrs)
