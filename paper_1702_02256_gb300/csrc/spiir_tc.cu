@@ -310,7 +310,8 @@ __global__ void tc_stage_kernel(const TcStageArgs a) {
             }
             a.hank[i] = pack8<BF16>(v);
         } else {
-            // STATE segments of batch b: row n = (s, c, i2), K = i1:
+            // STATE segments of batch b: row n = (c, s, i2) (streams of a
+            // chunk adjacent), K = i1:
             // x_s[e_c - kJ i2 - i1], e_c = c L - F + L - 1; layout
             // [n/8][i1/8][n%8][i1%8]
             const int64_t j = i - hank_chunks;
@@ -320,7 +321,7 @@ __global__ void tc_stage_kernel(const TcStageArgs a) {
             const int nb = min(a.cpb, a.n_chunks - b * a.cpb);
             const int nii = a.n_streams * nb * LJ;
             if (n < nii) {
-                const int ss = n / (nb * LJ), rem = n % (nb * LJ), cc = rem / LJ, i2 = rem % LJ;
+                const int q = n / LJ, i2 = n % LJ, cc = q / a.n_streams, ss = q % a.n_streams;
                 const float *x = a.xbuf + (int64_t)(a.stream0 + ss) * a.xbuf_stride + a.hist;
                 const int e = (b * a.cpb + cc) * a.L - a.F + a.L - 1 - kJ * i2;
 #pragma unroll
@@ -649,7 +650,7 @@ __device__ __forceinline__ float2 cmul(float2 x, float2 y) {
     return make_float2(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x);
 }
 
-template <bool BF16, int LJ>
+template <bool BF16, int LJ, int S>
 __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcCarryArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t panel_full[kSlots], panel_free[kSlots], w_full[kSlots], w_free[kSlots],
@@ -666,8 +667,7 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
     constexpr uint32_t kWK = (2 * kNii / 8) * 128;
     const int L = LJ * kJ;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int S = a.n_streams;
-    volatile int *abort = &s_abort;
+    volatile int *abort = &s_abort;     // S (1 or 2) = a.n_streams
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < kSlots; ++i) {
@@ -840,7 +840,7 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             tc_fence_after();
             const int b = J.b0;
             const int nb = min(a.cpb, a.n_chunks - b * a.cpb);
-            const int nc = nb * LJ, nii = S * nc;        // columns per stream, in all
+            const int nii = S * nb * LJ;                // columns of this batch
             const uint32_t tb = tmem + lane_base + 256 + 128 * ob;
             const int j1 = m & 63;
             // z of stream 0 and 1 at this batch's first sample and lane j1
@@ -871,9 +871,8 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                             if (c < nii) {
                                 const float zr = __uint_as_float(v[i4][i]) - row[i + 1];
                                 const float zi = __uint_as_float(v[i4][i + 1]) + row[i];
-                                const bool s1 = c >= nc;                // at most two streams
-                                const int rem = s1 ? c - nc : c;
-                                float2 *zp = (s1 ? zb1 : zb0) + (rem / LJ) * L + kJ * (rem % LJ);
+                                const int q = c / LJ;                   // c = (chunk S + stream) LJ + j2
+                                float2 *zp = ((q % S) ? zb1 : zb0) + (q / S) * L + kJ * (c % LJ);
                                 *zp = make_float2(a.scale * zr, a.scale * zi);
                             }
                         }
@@ -991,11 +990,16 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             // chunk states inside the batch are FP32:
             //   v_c = a^(cL) v + d_c,  d_{c+1} = a^L d_c + U_c,  d_0 = 0,
             // and the next batch starts from a^(nb L) v + d_nb in FP64.
-            float2 p = make_float2((float)v0.x, (float)v0.y);   // a^(cL) v
-            float2 dd = make_float2(0.f, 0.f);                   // d_c
-            float2 d_s0 = dd;
-            // STATE columns: (stream, chunk, i2) -> (s nb + c) LJ + i2, read 32
-            // at a time (32 / LJ steps). Step q writes W columns 2 q LJ ..
+            // per stream: a^(cL) v and d_c; the streams' chains interleave
+            float2 p[S], dd[S];
+#pragma unroll
+            for (int i = 0; i < S; ++i) {
+                const double2 vi = i ? v1 : v0;
+                p[i] = make_float2((float)vi.x, (float)vi.y);
+                dd[i] = make_float2(0.f, 0.f);
+            }
+            // STATE columns: (chunk, stream, i2) -> (c S + s) LJ + i2, read 32
+            // at a time (32 / LJ steps); step q = c S + s. Step q writes W columns 2 q LJ ..
             // 2 q LJ + 2 LJ - 1: 4 LJ contiguous bytes at (k/8) kWK + q LJ / 4 * 128
             // + (2 q LJ % 8) * 2 + (k%8) 16.
             const uint32_t tb = tmem + lane_base + 128 * grp;
@@ -1019,11 +1023,7 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                     const uint32_t off = kofs + (uint32_t)(n >> 3) * 128 + (n & 7) * 2;
                     float wr[LJ], wi[LJ];
                     if (q < nsteps) {
-                        if (q == nb) {                            // stream 1 starts
-                            d_s0 = dd;
-                            p = make_float2((float)v1.x, (float)v1.y);
-                            dd = make_float2(0.f, 0.f);
-                        }
+                        const int ss = q % S;   // resolved at compile time (unrolled)
                         // U = sum_i2 aJ^i2 G(i2)
                         const int c0 = qq * LJ;
                         float ur = __uint_as_float(rr[c0 >> 4][c0 & 15]);
@@ -1036,16 +1036,16 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                             ur = fmaf(pj[i2].x, gr, fmaf(-pj[i2].y, gi, ur));
                             ui = fmaf(pj[i2].x, gi, fmaf(pj[i2].y, gr, ui));
                         }
-                        const float2 vv = make_float2(p.x + dd.x, p.y + dd.y);
+                        const float2 vv = make_float2(p[ss].x + dd[ss].x, p[ss].y + dd[ss].y);
 #pragma unroll
                         for (int j2 = 0; j2 < LJ; ++j2) {
                             const float2 w = cmul(cj[j2], vv);
                             wr[j2] = w.x;
                             wi[j2] = w.y;
                         }
-                        dd = make_float2(fmaf(aLf.x, dd.x, fmaf(-aLf.y, dd.y, ur)),
-                                         fmaf(aLf.x, dd.y, fmaf(aLf.y, dd.x, ui)));
-                        p = cmul(aLf, p);
+                        dd[ss] = make_float2(fmaf(aLf.x, dd[ss].x, fmaf(-aLf.y, dd[ss].y, ur)),
+                                             fmaf(aLf.x, dd[ss].y, fmaf(aLf.y, dd[ss].x, ui)));
+                        p[ss] = cmul(aLf, p[ss]);
                     } else {
                         // columns past this batch contribute nothing
 #pragma unroll
@@ -1061,7 +1061,6 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                     }
                 }
             }
-            if (S == 1) d_s0 = dd;
             // v <- a^(nb L) v + d_nb in FP64, per stream
             double2 pw;
             if (nb == a.cpb) {
@@ -1072,12 +1071,12 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                 for (int i = 1; i < nb; ++i)
                     pw = make_double2(pw.x * aL.x - pw.y * aL.y, pw.x * aL.y + pw.y * aL.x);
             }
-            v0 = make_double2(fma(pw.x, v0.x, fma(-pw.y, v0.y, (double)d_s0.x)),
-                              fma(pw.x, v0.y, fma(pw.y, v0.x, (double)d_s0.y)));
+            v0 = make_double2(fma(pw.x, v0.x, fma(-pw.y, v0.y, (double)dd[0].x)),
+                              fma(pw.x, v0.y, fma(pw.y, v0.x, (double)dd[0].y)));
             a.v[(int64_t)a.stream0 * a.n_slots + slot] = v0;
-            if (S > 1) {
-                v1 = make_double2(fma(pw.x, v1.x, fma(-pw.y, v1.y, (double)dd.x)),
-                                  fma(pw.x, v1.y, fma(pw.y, v1.x, (double)dd.y)));
+            if constexpr (S > 1) {
+                v1 = make_double2(fma(pw.x, v1.x, fma(-pw.y, v1.y, (double)dd[1].x)),
+                                  fma(pw.x, v1.y, fma(pw.y, v1.x, (double)dd[1].y)));
                 a.v[(int64_t)(a.stream0 + 1) * a.n_slots + slot] = v1;
             }
             fence_async_smem();
@@ -1361,12 +1360,14 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
     int max_optin = 0;
     TC_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     {
-        const void *fns[6] = {(const void *)tc_fir_kernel<true>, (const void *)tc_fir_kernel<false>,
-                              (const void *)tc_carry_kernel<true, 2>, (const void *)tc_carry_kernel<true, 4>,
-                              (const void *)tc_carry_kernel<false, 2>, (const void *)tc_carry_kernel<false, 4>};
-        const int need[6] = {fir_smem_of(p.L, p.K), fir_smem_of(p.L, p.K), kCarrySmem, kCarrySmem,
-                             kCarrySmem, kCarrySmem};
-        for (int i = 0; i < 6; ++i) {
+        const void *fns[10] = {(const void *)tc_fir_kernel<true>, (const void *)tc_fir_kernel<false>,
+                               (const void *)tc_carry_kernel<true, 2, 1>, (const void *)tc_carry_kernel<true, 4, 1>,
+                               (const void *)tc_carry_kernel<false, 2, 1>, (const void *)tc_carry_kernel<false, 4, 1>,
+                               (const void *)tc_carry_kernel<true, 2, 2>, (const void *)tc_carry_kernel<true, 4, 2>,
+                               (const void *)tc_carry_kernel<false, 2, 2>, (const void *)tc_carry_kernel<false, 4, 2>};
+        const int need[10] = {fir_smem_of(p.L, p.K), fir_smem_of(p.L, p.K), kCarrySmem, kCarrySmem,
+                              kCarrySmem, kCarrySmem, kCarrySmem, kCarrySmem, kCarrySmem, kCarrySmem};
+        for (int i = 0; i < 10; ++i) {
             cudaFuncAttributes fa;
             TC_CUDA(cudaFuncGetAttributes(&fa, fns[i]));
             const int dyn_max = max_optin - (int)fa.sharedSizeBytes;
@@ -1475,16 +1476,23 @@ spiir_status spiir_tc_push(TcBank *b, int s0, int count, const float *x, int64_t
         const int grid = std::min(b->n_carry_ctas, b->n_sms);
         const int thr = kCarryWarps * 32;
         timer->begin(SPIIR_K_TC_CARRY, s);
+        const bool l2 = b->L == 2 * kJ, two = count == 2;
         if (b->bf16) {
-            if (b->L == 2 * kJ)
-                tc_carry_kernel<true, 2><<<grid, thr, kCarrySmem, s>>>(ca);
-            else
-                tc_carry_kernel<true, 4><<<grid, thr, kCarrySmem, s>>>(ca);
+            if (two) {
+                if (l2) tc_carry_kernel<true, 2, 2><<<grid, thr, kCarrySmem, s>>>(ca);
+                else tc_carry_kernel<true, 4, 2><<<grid, thr, kCarrySmem, s>>>(ca);
+            } else {
+                if (l2) tc_carry_kernel<true, 2, 1><<<grid, thr, kCarrySmem, s>>>(ca);
+                else tc_carry_kernel<true, 4, 1><<<grid, thr, kCarrySmem, s>>>(ca);
+            }
         } else {
-            if (b->L == 2 * kJ)
-                tc_carry_kernel<false, 2><<<grid, thr, kCarrySmem, s>>>(ca);
-            else
-                tc_carry_kernel<false, 4><<<grid, thr, kCarrySmem, s>>>(ca);
+            if (two) {
+                if (l2) tc_carry_kernel<false, 2, 2><<<grid, thr, kCarrySmem, s>>>(ca);
+                else tc_carry_kernel<false, 4, 2><<<grid, thr, kCarrySmem, s>>>(ca);
+            } else {
+                if (l2) tc_carry_kernel<false, 2, 1><<<grid, thr, kCarrySmem, s>>>(ca);
+                else tc_carry_kernel<false, 4, 1><<<grid, thr, kCarrySmem, s>>>(ca);
+            }
         }
         TC_CUDA(cudaGetLastError());
         timer->end(s);
