@@ -460,13 +460,23 @@ __global__ void __launch_bounds__(192, 1) tc_fir_kernel(const TcFirArgs a) {
             const bool is_re = (r & 1) == 0;
             const bool add = (t < a.n_templates) && a.has_carry[t];
             const int i0 = is_re ? 0 : 8;
+            // state term written by the carry kernel, fetched two 16-column
+            // steps ahead so that its global latency overlaps two steps
+            float2 pf0[8], pf1[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                pf0[i] = add ? zrow[L - 1 - (i0 + i)] : make_float2(0.f, 0.f);
+                pf1[i] = add ? zrow[L - 1 - (16 + i0 + i)] : make_float2(0.f, 0.f);
+            }
             for (int cc = 0; cc < L / 16; ++cc) {
-                // state term written by the carry kernel: fetch before the
-                // tensor-memory load so the global latency overlaps it
                 float2 prev[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    prev[i] = add ? zrow[L - 1 - (cc * 16 + i0 + i)] : make_float2(0.f, 0.f);
+                for (int i = 0; i < 8; ++i) {
+                    prev[i] = pf0[i];
+                    pf0[i] = pf1[i];
+                    pf1[i] = (add && cc + 2 < L / 16) ? zrow[L - 1 - ((cc + 2) * 16 + i0 + i)]
+                                                       : make_float2(0.f, 0.f);
+                }
                 float v[16];
                 tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + ab * 256 + cc * 16, v);
                 float o[16];
@@ -476,8 +486,10 @@ __global__ void __launch_bounds__(192, 1) tc_fir_kernel(const TcFirArgs a) {
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const int col = cc * 16 + i0 + i;
-                        const float re = is_re ? v[i0 + i] : o[i0 + i];
-                        const float im = is_re ? o[i0 + i] : v[i0 + i];
+                        // even lanes own columns 0..7 of the step, odd lanes 8..15
+                        // (compile-time register indices on both sides)
+                        const float re = is_re ? v[i] : o[8 + i];
+                        const float im = is_re ? o[i] : v[8 + i];
                         zrow[L - 1 - col] = make_float2(fmaf(sc, re, prev[i].x), fmaf(sc, im, prev[i].y));
                     }
                 }
@@ -1392,6 +1404,16 @@ spiir_status spiir_tc_push(TcBank *b, int s0, int count, const float *x, int64_t
             }
             return SPIIR_OK;
         }
+    // streams are carried two at a time (the carry kernel's thread layout);
+    // each pair runs its own prologue
+    if (count > 2) {
+        for (int i = 0; i < count; i += 2) {
+            const int cnt = std::min(2, count - i);
+            spiir_status st = spiir_tc_push(b, s0 + i, cnt, x + i * x_stride, x_stride, n, s, timer);
+            if (st) return st;
+        }
+        return SPIIR_OK;
+    }
     // strain history + new samples (single-level prologue)
     PrologueArgs pa{};
     pa.xbuf = b->xbuf;
@@ -1409,15 +1431,6 @@ spiir_status spiir_tc_push(TcBank *b, int s0, int count, const float *x, int64_t
     timer->end(s);
 
     const int C = (int)(n / b->L);
-    // streams are carried two at a time (the carry kernel's thread layout)
-    if (count > 2) {
-        for (int i = 0; i < count; i += 2) {
-            const int cnt = std::min(2, count - i);
-            spiir_status st = spiir_tc_push(b, s0 + i, cnt, x + i * x_stride, x_stride, n, s, timer);
-            if (st) return st;
-        }
-        return SPIIR_OK;
-    }
     const int cpb = carry_cpb(count, b->L);
     const int n_batches = (C + cpb - 1) / cpb;
     TcStageArgs sa{};

@@ -66,6 +66,17 @@ def test_several_batch_groups_per_push(torch_cuda, oracle_mod):
         _check(z[s], ref, TOL_TC, 256)
 
 
+def test_three_streams_pair_and_single(torch_cuda, oracle_mod):
+    """Three detector streams: the carry runs them as a pair plus a single
+    stream (two kernel instantiations); each stream against the oracle."""
+    bank = inputs.single_rate_bank(9, [40, 128, 200, 5, 300, 64, 129, 256, 90], 500, seed=31)
+    x = inputs.strain(3, 3 * 4096, seed=21)
+    z = gpu_snr(bank, x, push_blocks=1, n_streams=3, mode="fp16", chunk_len=256)
+    for s in range(3):
+        ref = oracle_mod.spiir_single(bank, x[s])
+        _check(z[s], ref, TOL_TC, 256)
+
+
 def test_tc_matches_plain_path(torch_cuda):
     """Same bank through both forms: they agree to the TC tolerance."""
     bank = inputs.single_rate_bank(70, 64, 300, seed=3)
