@@ -223,7 +223,7 @@ def run_reference(args):
     value = float(np.mean(rates))
     bank = w["bank"]
     n = w["x"].shape[1]
-    fs_total = int(np.sum(n >> bank.level.astype(np.int64)))
+    fs_total = w["n_streams"] * int(np.sum(n >> bank.level.astype(np.int64)))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
