@@ -666,7 +666,7 @@ template <bool BF16, int LJ, int S>
 __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcCarryArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t panel_full[kSlots], panel_free[kSlots], w_full[kSlots], w_free[kSlots],
-        state_full[2], state_free[2], out_full[2], out_free[2], xs_bar, drain;
+        state_full[2], state_free[2], out_full[2], out_free[2], xs_full[2], drain;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
     // slot s: panel at s * kPanelBytes, W at kSlots * kPanelBytes + s * kWBytes
@@ -694,7 +694,8 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             mbar_init(&out_full[i], 1);
             mbar_init(&out_free[i], 128);
         }
-        mbar_init(&xs_bar, 1);
+        mbar_init(&xs_full[0], 1);
+        mbar_init(&xs_full[1], 1);
         mbar_init(&drain, 1);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -715,12 +716,26 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             // the OUTPUT queue as 8-bit entries of oq. Slot phases follow from
             // the job index (slot use j / kSlots).
             constexpr uint32_t kSF = 0, kOF = 2, kUsed = 4;
-            uint32_t ph = 0, ph_x = 0, ph_d = 0;
+            uint32_t ph = 0, ph_d = 0;
             // queue entry: bits 0-1 slot, 2 OUTPUT buffer, 3 first tile,
             // 4 last tile, 5 buffer used before
             uint32_t oq = 0;
             int oq_n = 0, oq_j = 0;           // queue length; job index of the head
-            int loaded0 = -1, loaded1 = -1;   // batch held by segment buffer 0 / 1
+            // strain-segment buffers (batch b in buffer b % 2): batch held or
+            // being loaded, job of the last STATE that read it, load in flight,
+            // and the phase of the next load's completion
+            int held0 = -1, held1 = -1, last0 = -1000, last1 = -1000;
+            uint32_t loading = 0, xs_ph = 0;
+            int last_pf = -1;   // latest job whose panel was seen ready: every
+                                // STATE up to three jobs before it has finished
+            auto start_load = [&](int x, int batch) {
+                mbar_expect(&xs_full[x], kXsegBytes);
+                bulk_load(Xs + x * kXsegBytes, a.xseg + (size_t)batch * (kXsegBytes / 16), kXsegBytes,
+                          &xs_full[x]);
+                if (x) held1 = batch;
+                else held0 = batch;
+                loading |= 1u << x;
+            };
             bool issued = false, ok = true;
             CarryJobs st(a);                  // next job for STATE
             const uint32_t id_state = idesc(128, kNii, BF16, false, false);
@@ -735,29 +750,31 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                     const CarryJob J = st.cur();
                     const uint32_t g = (uint32_t)J.g, sl = (uint32_t)J.s;
                     const bool used = (ph >> (kUsed + g)) & 1u;
-                    if ((!used || mbar_test(&state_free[g], (ph >> (kSF + g)) & 1u)) &&
+                    const int xb = J.b0 & 1;
+                    if ((xb ? held1 : held0) != J.b0 && !((loading >> xb) & 1u)) {
+                        // the buffer's readers must be done before it is refilled:
+                        // certain three jobs on, else drain the tensor pipe (rare:
+                        // one-tile templates with several batches)
+                        if (issued && (xb ? last1 : last0) > last_pf - 3) {
+                            mma_commit(&drain);
+                            ok = mbar_wait_ab(&drain, ph_d, a.status, abort);
+                            ph_d ^= 1u;
+                            if (!ok) break;
+                        }
+                        start_load(xb, J.b0);
+                    }
+                    if (((loading >> xb) & 1u) && mbar_test(&xs_full[xb], (xs_ph >> xb) & 1u)) {
+                        loading &= ~(1u << xb);
+                        xs_ph ^= 1u << xb;
+                    }
+                    if (!((loading >> xb) & 1u) &&
+                        (!used || mbar_test(&state_free[g], (ph >> (kSF + g)) & 1u)) &&
                         mbar_test(&panel_full[sl], (uint32_t)(J.j / kSlots) & 1u)) {
                         if (used) ph ^= 1u << (kSF + g);
                         ph |= 1u << (kUsed + g);
-                        const int xb = J.b0 & 1;
-                        if (J.b0 != (xb ? loaded1 : loaded0)) {
-                            // the STATE contractions that read the old segments are done
-                            if (issued) {
-                                mma_commit(&drain);
-                                ok = mbar_wait_ab(&drain, ph_d, a.status, abort);
-                                ph_d ^= 1u;
-                            }
-                            if (ok) {
-                                mbar_expect(&xs_bar, kXsegBytes);
-                                bulk_load(Xs + xb * kXsegBytes, a.xseg + (size_t)J.b0 * (kXsegBytes / 16),
-                                          kXsegBytes, &xs_bar);
-                                ok = mbar_wait_ab(&xs_bar, ph_x, a.status, abort);
-                                ph_x ^= 1u;
-                            }
-                            if (!ok) break;
-                            if (xb) loaded1 = J.b0;
-                            else loaded0 = J.b0;
-                        }
+                        last_pf = J.j;
+                        if (xb) last1 = J.j;
+                        else last0 = J.j;
                         tc_fence_after();
                         // descriptors advance by 16-byte units in their low bits;
                         // re powers are panel k-blocks 0..7, im powers 8..15
@@ -778,6 +795,12 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                         if (oq_n == 0) oq_j = J.j;
                         oq |= ent << (8 * oq_n);
                         ++oq_n;
+                        // prefetch the template's next batch into the other buffer
+                        // once that buffer's readers are certainly done
+                        const int nb2 = J.b0 + 1, x2 = nb2 & 1;
+                        if (nb2 < a.n_batches && (x2 ? held1 : held0) != nb2 && !((loading >> x2) & 1u) &&
+                            (x2 ? last1 : last0) <= last_pf - 3)
+                            start_load(x2, nb2);
                         st.next();
                         progressed = true;
                     }
@@ -825,11 +848,14 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                     if (*abort) ok = false;
                 }
             }
-            // nothing may still run when the tensor memory is released
+            // nothing may still run when the tensor memory is released, and no
+            // copy may still be writing shared memory
             if (issued) {
                 mma_commit(&drain);
                 mbar_wait(&drain, ph_d, a.status);
             }
+            for (int x = 0; x < 2; ++x)
+                if ((loading >> x) & 1u) mbar_wait(&xs_full[x], (xs_ph >> x) & 1u, a.status);
         }
     } else if (warp <= 4) {
         // ---------------- power panels and epilogue ----------------
