@@ -420,6 +420,8 @@ def run_ours(args):
             "samples_per_step": int(w["x"].shape[1]),
             "form": "plain FP32 recursion" if form == "plain" else f"tensor-core block form ({form})",
             "kernel_variant": main["info"]["kernel_variant"],
+            "variant_choice": {1: "autotuned at bank creation", 0: "default"}.get(
+                args.tune, f"forced {-args.tune - 1}") if form == "plain" else "n/a",
             "filters_per_lane": main["info"]["filters_per_lane"],
             "time_tile": main["info"]["time_tile"],
             "l2": "flushed between timed steps (256 MB write, untimed)",
@@ -551,12 +553,16 @@ def main():
                     help="compute form of the headline number (default: plain; fp16 for tc)")
     ap.add_argument("--chosen", default="fp16", choices=["", "plain", "fp16", "bf16"],
                     help="second form measured on the same workload and reported as 'chosen'")
-    ap.add_argument("--tune", type=int, default=0)
+    ap.add_argument("--tune", type=int, default=None,
+                    help="plain-form kernel variant: 1 = autotune at bank creation, 0 = default, "
+                         "-(v+1) = variant v (default: autotune for multirate, else 0)")
     ap.add_argument("--templates", type=int, default=0,
                     help="template count (0 = the workload's full size); small cases for ncu")
     ap.add_argument("--seconds", type=int, default=0,
                     help="seconds of strain per step (0 = the workload's 16 s)")
     args = ap.parse_args()
+    if args.tune is None:
+        args.tune = 1 if args.workload == "multirate" else 0
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
