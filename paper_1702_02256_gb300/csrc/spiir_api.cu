@@ -294,20 +294,21 @@ spiir_status make_plan(const spiir_bank_desc *d, int variant, bool arrays, Plan 
             if (M == 0) continue;
             const int64_t cap = 32ll * SPIIR_CTA_WARPS * p.FMAX;
             const int64_t parts = (M + cap - 1) / cap;
-            for (int64_t q = 0; q < parts; ++q) {
-                const int64_t b0 = M * q / parts, b1 = M * (q + 1) / parts;
+            // lanes x slots of a unit of m filters: G = smallest power of two
+            // with G FMAX >= m, F = ceil(m / G) rounded up to even
+            auto shape = [&](int64_t m, int &G, int &F) {
+                G = 1;
+                while ((int64_t)G * p.FMAX < m) G *= 2;
+                F = (int)((m + G - 1) / G);
+                F += F & 1;
+                if (F < 2) F = 2;
+            };
+            auto add_unit = [&](int64_t b0, int64_t b1) {
                 Unit u;
                 u.level = i;
                 u.tmpl = t;
                 u.filt.assign(f.begin() + b0, f.begin() + b1);
-                const int64_t m = b1 - b0;
-                int G = 1;
-                while ((int64_t)G * p.FMAX < m) G *= 2;
-                int F = (int)((m + G - 1) / G);
-                F += F & 1;
-                if (F < 2) F = 2;
-                u.G = G;
-                u.F = F;
+                shape(b1 - b0, u.G, u.F);
                 if (!p.need_combine) {
                     u.dest = t;
                 } else {
@@ -316,6 +317,29 @@ spiir_status make_plan(const spiir_bank_desc *d, int variant, bool arrays, Plan 
                     comb[(size_t)t * L + i].push_back((int32_t)row);
                 }
                 units.push_back(std::move(u));
+            };
+            for (int64_t q = 0; q < parts; ++q) {
+                const int64_t b0 = M * q / parts, b1 = M * (q + 1) / parts;
+                const int64_t m = b1 - b0;
+                int G, F;
+                shape(m, G, F);
+                // Where a combine pass runs anyway, split off the filters above
+                // the largest full block of G' lanes x FMAX slots when that saves
+                // more padded slots than an extra partial row costs: a row is
+                // 16 bytes of HBM traffic per sample (written, read back), about
+                // 12 slot-updates of FP32 time at the measured peaks.
+                int64_t full = 0;
+                for (int64_t g2 = 1; g2 * p.FMAX <= m; g2 *= 2) full = g2 * p.FMAX;
+                if (p.need_combine && full > 0 && full < m) {
+                    int Gr, Fr;
+                    shape(m - full, Gr, Fr);
+                    if ((int64_t)G * F - (full + (int64_t)Gr * Fr) > 12) {
+                        add_unit(b0, b0 + full);
+                        add_unit(b0 + full, b1);
+                        continue;
+                    }
+                }
+                add_unit(b0, b1);
             }
         }
     }
