@@ -962,16 +962,26 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             p[0] = make_float2(1.f, 0.f);
 #pragma unroll
             for (int i = 1; i < 4; ++i) p[i] = cmul(p[i - 1], a16);
+            // chains (0, 1) and (2, 3) advance together in packed f32x2:
+            // re' = re ak.x - im ak.y, im' = re ak.y + im ak.x
+            float2 pr[2] = {make_float2(p[0].x, p[1].x), make_float2(p[2].x, p[3].x)};
+            float2 pi[2] = {make_float2(p[0].y, p[1].y), make_float2(p[2].y, p[3].y)};
+            const float2 akr = make_float2(ak.x, ak.x), aki = make_float2(ak.y, ak.y);
+            const float2 naki = make_float2(-ak.y, -ak.y);
 #pragma unroll
             for (int ib = 0; ib < 2; ++ib) {
                 float vr[4][8], vi[4][8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
 #pragma unroll
-                    for (int ch = 0; ch < 4; ++ch) {
-                        vr[ch][q] = p[ch].x;
-                        vi[ch][q] = p[ch].y;
-                        p[ch] = cmul(p[ch], ak);
+                    for (int h2 = 0; h2 < 2; ++h2) {
+                        vr[2 * h2][q] = pr[h2].x;
+                        vr[2 * h2 + 1][q] = pr[h2].y;
+                        vi[2 * h2][q] = pi[h2].x;
+                        vi[2 * h2 + 1][q] = pi[h2].y;
+                        const float2 nr = __ffma2_rn(pi[h2], naki, __fmul2_rn(pr[h2], akr));
+                        pi[h2] = __ffma2_rn(pi[h2], akr, __fmul2_rn(pr[h2], aki));
+                        pr[h2] = nr;
                     }
                 }
 #pragma unroll
@@ -1012,6 +1022,14 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             for (int i = 1; i < LJ; ++i) {
                 pj[i] = cmul(pj[i - 1], aJ);
                 cj[i] = cmul(cj[i - 1], aJ);
+            }
+            // the same factors as packed pairs (j2, j2 + 1) for f32x2 products
+            float2 cjr[LJ / 2], cji[LJ / 2], ncji[LJ / 2];
+#pragma unroll
+            for (int i = 0; i < LJ / 2; ++i) {
+                cjr[i] = make_float2(cj[2 * i].x, cj[2 * i + 1].x);
+                cji[i] = make_float2(cj[2 * i].y, cj[2 * i + 1].y);
+                ncji[i] = make_float2(-cj[2 * i].y, -cj[2 * i + 1].y);
             }
             double2 v0 = a.v[(int64_t)a.stream0 * a.n_slots + slot];
             double2 v1 = S > 1 ? a.v[(int64_t)(a.stream0 + 1) * a.n_slots + slot] : make_double2(0, 0);
@@ -1075,11 +1093,15 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                             ui = fmaf(pj[i2].x, gi, fmaf(pj[i2].y, gr, ui));
                         }
                         const float2 vv = make_float2(p[ss].x + dd[ss].x, p[ss].y + dd[ss].y);
+                        const float2 vx = make_float2(vv.x, vv.x), vy = make_float2(vv.y, vv.y);
 #pragma unroll
-                        for (int j2 = 0; j2 < LJ; ++j2) {
-                            const float2 w = cmul(cj[j2], vv);
-                            wr[j2] = w.x;
-                            wi[j2] = w.y;
+                        for (int i = 0; i < LJ / 2; ++i) {      // w = a^(kJ j2) a c vv
+                            const float2 r = __ffma2_rn(ncji[i], vy, __fmul2_rn(cjr[i], vx));
+                            const float2 m = __ffma2_rn(cji[i], vx, __fmul2_rn(cjr[i], vy));
+                            wr[2 * i] = r.x;
+                            wr[2 * i + 1] = r.y;
+                            wi[2 * i] = m.x;
+                            wi[2 * i + 1] = m.y;
                         }
                         dd[ss] = make_float2(fmaf(aLf.x, dd[ss].x, fmaf(-aLf.y, dd[ss].y, ur)),
                                              fmaf(aLf.x, dd[ss].y, fmaf(aLf.y, dd[ss].x, ui)));
