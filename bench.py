@@ -122,17 +122,24 @@ def _peaks():
         return {}
 
 
+def _source_hash(kernel_file: str) -> str:
+    """First 16 hex digits of the sha256 of the kernel file followed by the
+    planner (spiir_api.cu): the traffic depends on both."""
+    h = hashlib.sha256()
+    for f in (kernel_file, "spiir_api.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1702_02256_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def _traffic(kernel_file: str, key: str):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel
-    source has not changed since it was taken."""
+    """DRAM bytes per launch from a committed ncu summary, if the kernel and
+    planner sources have not changed since it was taken."""
     path = os.path.join(ROOT, "profiles", f"{key}_traffic.txt")
     try:
         kv = dict(tok.split("=", 1) for tok in open(path).read().split() if "=" in tok)
     except OSError:
         return None
-    src = os.path.join(ROOT, "paper_1702_02256_gb300", "csrc", kernel_file)
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if kv.get("source_sha256_16") != h:
+    if kv.get("source_sha256_16") != _source_hash(kernel_file):
         return None
     return float(kv["dram_bytes_per_launch"])
 
