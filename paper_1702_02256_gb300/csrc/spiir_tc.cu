@@ -339,13 +339,18 @@ __global__ void tc_stage_kernel(const TcStageArgs a) {
 // FIR kernel: persistent, warp-specialised
 //   warp 0 lane 0: bulk-copy producer (impulse-response slices, Toeplitz source)
 //   warp 1 lane 0: MMA issuer into two tensor-memory accumulators
-//   warps 2-5    : epilogue (tensor memory -> z), overlapping the next MMAs
+//   warps 2-9    : epilogue (tensor memory -> z), overlapping the next MMAs;
+//                  two warps per tensor-memory lane quadrant, each taking
+//                  every other 16-column step
 // Items (template group, stream, chunk), chunk fastest so that CTAs working at
 // the same time share impulse-response tiles in L2.
 // ---------------------------------------------------------------------------
 
+constexpr int kFirEpiWarps = 8;
+constexpr int kFirThreads = (2 + kFirEpiWarps) * 32;
+
 template <bool BF16>
-__global__ void __launch_bounds__(192, 1) tc_fir_kernel(const TcFirArgs a) {
+__global__ void __launch_bounds__(kFirThreads, 1) tc_fir_kernel(const TcFirArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t a_full[kStages], a_empty[kStages], h_full[2], h_empty[2], acc_full[2],
         acc_empty[2];
@@ -366,7 +371,7 @@ __global__ void __launch_bounds__(192, 1) tc_fir_kernel(const TcFirArgs a) {
             mbar_init(&h_full[i], 1);
             mbar_init(&h_empty[i], 1);
             mbar_init(&acc_full[i], 1);
-            mbar_init(&acc_empty[i], 128);
+            mbar_init(&acc_empty[i], kFirEpiWarps * 32);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -444,6 +449,7 @@ __global__ void __launch_bounds__(192, 1) tc_fir_kernel(const TcFirArgs a) {
         // epilogue: lane row r = template 64g + r/2, re (even) / im (odd);
         // column n' is time n = L - 1 - n'
         const int q = warp & 3;
+        const int half = (warp - 2) >> 2;      // steps half, half + 2, ...
         const int r = q * 32 + lane;
         int li = 0;
         bool ok = true;
@@ -460,22 +466,28 @@ __global__ void __launch_bounds__(192, 1) tc_fir_kernel(const TcFirArgs a) {
             const bool is_re = (r & 1) == 0;
             const bool add = (t < a.n_templates) && a.has_carry[t];
             const int i0 = is_re ? 0 : 8;
-            // state term written by the carry kernel, fetched two 16-column
-            // steps ahead so that its global latency overlaps two steps
-            float2 pf0[8], pf1[8];
+            // A lane writes the 8 samples of its 8 columns of a 16-column step:
+            // column c is sample L - 1 - c, so they are the contiguous samples
+            // from L - 8 - (16 cc + i0), moved as four 16-byte vectors. The
+            // state term (written by the carry kernel) is fetched two steps
+            // ahead so its global latency overlaps two steps.
+            const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            auto zv = [&](int cc) {
+                return reinterpret_cast<float4 *>(zrow + (L - 8 - (cc * 16 + i0)));
+            };
+            float4 pf0[4], pf1[4];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                pf0[i] = add ? zrow[L - 1 - (i0 + i)] : make_float2(0.f, 0.f);
-                pf1[i] = add ? zrow[L - 1 - (16 + i0 + i)] : make_float2(0.f, 0.f);
+            for (int i = 0; i < 4; ++i) {
+                pf0[i] = add ? zv(half)[i] : zero4;
+                pf1[i] = (add && half + 2 < L / 16) ? zv(half + 2)[i] : zero4;
             }
-            for (int cc = 0; cc < L / 16; ++cc) {
-                float2 prev[8];
+            for (int cc = half; cc < L / 16; cc += 2) {
+                float4 prev[4];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
+                for (int i = 0; i < 4; ++i) {
                     prev[i] = pf0[i];
                     pf0[i] = pf1[i];
-                    pf1[i] = (add && cc + 2 < L / 16) ? zrow[L - 1 - ((cc + 2) * 16 + i0 + i)]
-                                                       : make_float2(0.f, 0.f);
+                    pf1[i] = (add && cc + 4 < L / 16) ? zv(cc + 4)[i] : zero4;
                 }
                 float v[16];
                 tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + ab * 256 + cc * 16, v);
@@ -483,14 +495,21 @@ __global__ void __launch_bounds__(192, 1) tc_fir_kernel(const TcFirArgs a) {
 #pragma unroll
                 for (int i = 0; i < 16; ++i) o[i] = __shfl_xor_sync(0xffffffffu, v[i], 1);
                 if (ok && t < a.n_templates) {
+                    // even lanes own columns 0..7 of the step, odd lanes 8..15
+                    // (compile-time register indices on both sides); sample
+                    // sb + u holds column 7 - u
+                    float re[8], im[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
-                        const int col = cc * 16 + i0 + i;
-                        // even lanes own columns 0..7 of the step, odd lanes 8..15
-                        // (compile-time register indices on both sides)
-                        const float re = is_re ? v[i] : o[8 + i];
-                        const float im = is_re ? o[i] : v[8 + i];
-                        zrow[L - 1 - col] = make_float2(fmaf(sc, re, prev[i].x), fmaf(sc, im, prev[i].y));
+                        re[i] = is_re ? v[i] : o[8 + i];
+                        im[i] = is_re ? o[i] : v[8 + i];
+                    }
+                    float4 *dst = zv(cc);
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        const int i_lo = 7 - 2 * w, i_hi = 6 - 2 * w;   // samples 2w, 2w + 1
+                        dst[w] = make_float4(fmaf(sc, re[i_lo], prev[w].x), fmaf(sc, im[i_lo], prev[w].y),
+                                             fmaf(sc, re[i_hi], prev[w].z), fmaf(sc, im[i_hi], prev[w].w));
                     }
                 }
             }
@@ -1581,9 +1600,9 @@ spiir_status spiir_tc_push(TcBank *b, int s0, int count, const float *x, int64_t
         const int smem = fir_smem_of(b->L, b->K);
         timer->begin(SPIIR_K_TC_FIR, s);
         if (b->bf16)
-            tc_fir_kernel<true><<<grid, 192, smem, s>>>(fa);
+            tc_fir_kernel<true><<<grid, kFirThreads, smem, s>>>(fa);
         else
-            tc_fir_kernel<false><<<grid, 192, smem, s>>>(fa);
+            tc_fir_kernel<false><<<grid, kFirThreads, smem, s>>>(fa);
         TC_CUDA(cudaGetLastError());
         timer->end(s);
     }
