@@ -175,13 +175,14 @@ def _workload(name: str, rank: int, templates: int = 0, seconds: int = 0):
     raise SystemExit(f"unknown workload {name}")
 
 
-def _cpu_sample(w, budget_s: float, n_templates_max: int):
-    """Time the oracle on the host cores over a bounded template sample sized
-    to about budget_s seconds. Returns (filter-samples/s, sample text, cores)."""
+def _cpu_sample(w, budget_s: float, n_templates_max: int, threads: int = 0):
+    """Time the oracle on the host cores (all of them, or `threads`) over a
+    bounded template sample sized to about budget_s seconds. Returns
+    (filter-samples/s, sample text, cores)."""
     from oracle import oracle
     bank = w["bank"]
     x = w["x"][0]
-    threads = oracle.default_threads()
+    threads = threads or oracle.default_threads()
     multi = bank.n_levels > 1
 
     def run(sel):
@@ -212,6 +213,41 @@ def _cpu_sample(w, budget_s: float, n_templates_max: int):
     rate = fs(sel) / dt
     sample = f"{n} of {bank.n_templates} templates, full {x.shape[0]} samples, {dt:.1f} s wall"
     return rate, sample, threads
+
+
+def run_sweep(args):
+    """Throughput against filters per template (the paper's speed-up table,
+    Table tab:spiir_speedup): single-rate banks of about 2^19 filters,
+    M = 4 .. 512 filters per template, 1 s pushes of 1 s blocks, plain form
+    and the fp16 block form; fraction of the FP32 roofline for the plain form."""
+    import torch
+    from paper_1702_02256_gb300 import inputs
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    peaks = _peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_fs = sms * FP32_LANES_PER_SM * sm_max * 1e6 / LANE_OPS_PER_FS
+    rows = []
+    for M in (4, 8, 16, 32, 64, 128, 256, 512):
+        T = (1 << 19) // M
+        bank = inputs.single_rate_bank(T, M, 1023, seed=5)
+        w = dict(bank=bank, x=inputs.strain(1, 4 * 4096, seed=3), block_len=4096, push_blocks=1,
+                 n_streams=1, chunk_len=256, desc=f"{T} templates x {M} filters")
+        row = {"filters_per_template": M, "templates": T}
+        for form in ("plain", "fp16"):
+            m = _measure(w, form, args, dev, None, None, 0, 1)
+            row[form] = {"filter_samples_per_s": m["value"], "p99_block_latency_ms": m["p99"]}
+            if form == "plain":
+                row[form]["roofline_frac"] = m["value"] / peak_fs
+                row[form]["kernel_variant"] = m["info"]["kernel_variant"]
+        rows.append(row)
+    line = {"metric": "filter-samples/s by filters per template (plain and fp16 block form)",
+            "value": rows[-1]["plain"]["filter_samples_per_s"], "unit": UNIT, "higher_is_better": True,
+            "n_gpus": 1, "data": "synthetic", "rows": rows,
+            "config": {"workload": "single-rate banks of 2^19 filters, delays 0-1023, 4 s in 1 s pushes"}}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_reference(args):
@@ -405,6 +441,7 @@ def run_ours(args):
     tot = max(1e-9, sum(v[0] for v in kt.values()))
     shares = {k: round(v[0] / tot, 4) for k, v in kt.items()}
     cpu_rate, cpu_sample, cores = _cpu_sample(w, 10.0, 256)
+    cpu1_rate, cpu1_sample, _ = _cpu_sample(w, 3.0, 64, threads=1)
     bank = w["bank"]
     line = {
         "metric": METRIC,
@@ -441,6 +478,8 @@ def run_ours(args):
         "roofline": _roofline(main, w, args, peaks, sms),
         "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": cpu_sample},
+        "cpu_baseline_single_thread": {"value": cpu1_rate, "unit": UNIT, "cores": 1,
+                                       "kind": "oracle", "sample": cpu1_sample},
         "e2e": {"value": main["e2e"], "unit": UNIT, "h2d_bytes_per_step": main["h2d"],
                 "d2h_bytes_per_step": main["d2h"]},
         "gpu_launches": int(sum(c for _, c in kt.values())),
@@ -550,7 +589,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="single", choices=["single", "multirate", "tc", "serve"])
+    ap.add_argument("--workload", default="single", choices=["single", "multirate", "tc", "serve", "sweep"])
     ap.add_argument("--serve-kind", default="single", choices=["single", "multirate"],
                     help="serving: banks of the plain-form run (multi-rate is config 4)")
     ap.add_argument("--serve-blocks", type=int, default=24)
@@ -576,6 +615,8 @@ def main():
         return run_reference(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     return run_ours(args)
 
 
