@@ -53,7 +53,7 @@ def lib():
         _lib.spiir_oracle_assign_level.restype = i32
         _lib.spiir_oracle_assign_level.argtypes = [d, d, i32, i32]
         _lib.spiir_oracle_align_delay.restype = i64
-        _lib.spiir_oracle_align_delay.argtypes = [i32, i32, i32, i32]
+        _lib.spiir_oracle_align_delay.argtypes = [i32, i32, i32, i32, i32]
         _lib.spiir_oracle_single.restype = ctypes.c_int
         _lib.spiir_oracle_single.argtypes = [i32, p, p, p, p, p, p, p, i64, d,
                                              p, i32, p, i32]
@@ -63,7 +63,7 @@ def lib():
         _lib.spiir_oracle_upsample_add.argtypes = [p, i64, p, i32, p]
         _lib.spiir_oracle_multirate.restype = ctypes.c_int
         _lib.spiir_oracle_multirate.argtypes = [i32, p, p, p, p, p, p, p, i32,
-                                                p, p, i32, i32, p, i64, d, p,
+                                                p, p, i32, i32, i32, p, i64, d, p,
                                                 i32, p, i32]
     return _lib
 
@@ -97,8 +97,12 @@ def assign_level(a_re: float, a_im: float, base_rate: int, n_levels: int) -> int
                                                int(base_rate), int(n_levels)))
 
 
-def align_delay(level: int, n_levels: int, n_taps: int = 32, align: bool = True) -> int:
-    return int(lib().spiir_oracle_align_delay(level, n_levels, n_taps, int(align)))
+def align_delay(level: int, n_levels: int, n_taps: int = 32, align: bool = True,
+                n_taps_up: Optional[int] = None) -> int:
+    """Alignment delay of level `level`: decimator of n_taps taps, interpolator
+    of n_taps_up taps (default: the same)."""
+    tu = n_taps if n_taps_up is None else n_taps_up
+    return int(lib().spiir_oracle_align_delay(level, n_levels, n_taps, tu, int(align)))
 
 
 def _csr(bank):
@@ -171,7 +175,6 @@ def spiir_multirate(bank, x: np.ndarray, h_down: Optional[np.ndarray] = None,
         h_up = kaiser_taps(n_taps, 60.0)
     h_down = np.ascontiguousarray(h_down, np.float32)
     h_up = np.ascontiguousarray(h_up, np.float32)
-    assert h_down.shape[0] == h_up.shape[0]
     scale = 2.0 / bank.base_rate if scale is None else float(scale)
     ptr = _csr(bank)
     tsel, n_sel = _sel(bank, templates)
@@ -181,7 +184,8 @@ def spiir_multirate(bank, x: np.ndarray, h_down: Optional[np.ndarray] = None,
     lev = np.ascontiguousarray(bank.level, np.int8)
     rc = lib().spiir_oracle_multirate(bank.n_templates, _ptr(ptr), *[_ptr(v) for v in arrs],
                                       _ptr(lev), bank.n_levels, _ptr(h_down), _ptr(h_up),
-                                      int(h_down.shape[0]), int(bool(align)), _ptr(x), n,
+                                      int(h_down.shape[0]), int(h_up.shape[0]),
+                                      int(bool(align)), _ptr(x), n,
                                       scale, _ptr(tsel), n_sel, _ptr(z),
                                       threads or default_threads())
     if rc:

@@ -33,9 +33,12 @@
  *   - x is real; a, b, y and z are complex;
  *   - d_k counts samples at the filter's own rate;
  *   - z = scale * (sum over filters), scale = 2*dt = 2/base_rate by default;
- *   - the level-i sum is delayed by D_i = (T-1) + 2*D_{i+1} (D_H = 0) so that
- *     a down/up round trip (delay T-1 at the higher rate) lines up with it;
- *     align = 0 sets every D_i to 0.
+ *   - the level-i sum is delayed by D_i = R + 2*D_{i+1} (D_H = 0) so that a
+ *     down/up round trip lines up with it; R = (Td-1)/2 + (Tu-1)/2 is the
+ *     sum of the two linear-phase filters' group delays at the higher rate
+ *     (T-1 when both have T taps; the decimator may be longer, e.g. the
+ *     paper's 100 dB design, and Td + Tu must be even); align = 0 sets every
+ *     D_i to 0.
  */
 #include <math.h>
 #include <stdint.h>
@@ -208,12 +211,15 @@ int spiir_oracle_upsample_add(const double *u, int64_t n_low, const float *h,
     return 0;
 }
 
-/* Alignment delay of level i's sum, in level-i samples (reading above). */
+/* Alignment delay of level i's sum, in level-i samples (reading above), for
+ * a decimator of n_taps_down and an interpolator of n_taps_up taps. */
 int64_t spiir_oracle_align_delay(int32_t level, int32_t n_levels,
-                                 int32_t n_taps, int32_t align) {
+                                 int32_t n_taps_down, int32_t n_taps_up,
+                                 int32_t align) {
     if (!align) return 0;
+    const int64_t R = (n_taps_down + n_taps_up) / 2 - 1; /* round trip */
     int64_t D = 0; /* D_H = 0 */
-    for (int32_t i = n_levels - 2; i >= level; --i) D = (n_taps - 1) + 2 * D;
+    for (int32_t i = n_levels - 2; i >= level; --i) D = R + 2 * D;
     return D;
 }
 
@@ -234,11 +240,13 @@ int spiir_oracle_multirate(int32_t n_templates, const int64_t *tmpl_ptr,
                            const float *b_re, const float *b_im,
                            const int32_t *delay, const int8_t *level,
                            int32_t n_levels, const float *h_down,
-                           const float *h_up, int32_t n_taps, int32_t align,
+                           const float *h_up, int32_t n_taps_down,
+                           int32_t n_taps_up, int32_t align,
                            const float *x, int64_t n_samples, double scale,
                            const int32_t *tsel, int32_t n_sel, double *z,
                            int32_t n_threads) {
     if (n_levels < 1 || n_levels > 16 || !tmpl_ptr || !z) return 1;
+    if ((n_taps_down + n_taps_up) % 2 != 0) return 1;
     int64_t H = n_levels - 1;
     if (n_samples % ((int64_t)1 << H) != 0) return 1;
     if (!tsel) n_sel = n_templates;
@@ -252,8 +260,8 @@ int spiir_oracle_multirate(int32_t n_templates, const int64_t *tmpl_ptr,
     }
     for (int64_t n = 0; n < n_samples; ++n) xl[0][n] = (double)x[n];
     for (int32_t i = 1; i < n_levels; ++i)
-        spiir_oracle_decimate(xl[i - 1], n_samples >> (i - 1), h_down, n_taps,
-                              xl[i]);
+        spiir_oracle_decimate(xl[i - 1], n_samples >> (i - 1), h_down,
+                              n_taps_down, xl[i]);
 
     int bad = 0;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads > 0 ? n_threads : 1)
@@ -269,7 +277,8 @@ int spiir_oracle_multirate(int32_t n_templates, const int64_t *tmpl_ptr,
                 if (level[k] == i)
                     filter_into(a_re[k], a_im[k], b_re[k], b_im[k], delay[k],
                                 xl[i], Ni, s);
-            int64_t D = spiir_oracle_align_delay(i, n_levels, n_taps, align);
+            int64_t D = spiir_oracle_align_delay(i, n_levels, n_taps_down,
+                                                 n_taps_up, align);
             for (int64_t n = 0; n < Ni; ++n) {
                 if (n - D >= 0) {
                     u[2 * n] = s[2 * (n - D)];
@@ -277,7 +286,7 @@ int spiir_oracle_multirate(int32_t n_templates, const int64_t *tmpl_ptr,
                 }
             }
             if (u_low) {
-                spiir_oracle_upsample_add(u_low, Ni / 2, h_up, n_taps, u);
+                spiir_oracle_upsample_add(u_low, Ni / 2, h_up, n_taps_up, u);
                 free(u_low);
             }
             free(s);

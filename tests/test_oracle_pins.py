@@ -226,12 +226,15 @@ def test_multirate_all_level0_equals_single_rate(oracle_mod):
     assert np.array_equal(za[:, D:], z1[:, :1024 - D])
 
 
-def _scipy_multirate(bank, x, h, align=True):
+def _scipy_multirate(bank, x, h, align=True, h_up=None):
     """The whole multi-rate chain from scipy routines: lfilter for the Kaiser
-    decimator and each IIR filter, upfirdn for the interpolator."""
+    decimator and each IIR filter, upfirdn for the interpolator. The level
+    delay per round trip is the sum of the two linear-phase filters' group
+    delays, (Td - 1)/2 + (Tu - 1)/2."""
     a, b = _complex(bank)
     H = bank.n_levels - 1
-    T = h.shape[0]
+    hu = (h if h_up is None else h_up).astype(np.float64)
+    R = (h.shape[0] + hu.shape[0]) // 2 - 1        # group delays; measured in the round-trip pins
     hd = h.astype(np.float64)
     xs = [x.astype(np.float64)]
     for i in range(1, bank.n_levels):
@@ -249,10 +252,10 @@ def _scipy_multirate(bank, x, h, align=True):
             D = 0
             if align:
                 for _ in range(H - i):
-                    D = (T - 1) + 2 * D
+                    D = R + 2 * D
             cur = np.concatenate([np.zeros(D, np.complex128), s])[:Ni]
             if u is not None:
-                cur = cur + ss.upfirdn(2.0 * hd, u, up=2)[:Ni]
+                cur = cur + ss.upfirdn(2.0 * hu, u, up=2)[:Ni]
             u = cur
         out.append(u * 2.0 / 4096)
     return np.array(out)
@@ -267,6 +270,36 @@ def test_multirate_matches_scipy_chain(oracle_mod, align):
     z = oracle_mod.spiir_multirate(bank, x, align=align)
     ref = _scipy_multirate(bank, x, h, align=align)
     assert _rel(z, ref) < 1e-11
+
+
+@pytest.mark.parametrize("align", [True, False])
+def test_multirate_long_decimator_matches_scipy_chain(oracle_mod, align):
+    """The paper's resampler variant: a 384-tap 100 dB decimator with the
+    32-tap 60 dB interpolator (Sec. 2.2)."""
+    counts = np.array([[3, 1, 2], [1, 2, 0], [0, 2, 4]])
+    bank = inputs.multi_rate_bank(3, 3, seed=13, counts=counts, delay_max=40)
+    x = inputs.strain(1, 4096, seed=5)[0]
+    hd = oracle_mod.kaiser_taps(384, 100.0)
+    hu = oracle_mod.kaiser_taps(32, 60.0)
+    z = oracle_mod.spiir_multirate(bank, x, h_down=hd, h_up=hu, align=align)
+    ref = _scipy_multirate(bank, x, hd, align=align, h_up=hu)
+    assert _rel(z, ref) < 1e-11
+
+
+def test_round_trip_delay_long_decimator(oracle_mod):
+    """Down through the 384-tap decimator and up through the 32-tap
+    interpolator: a band-limited tone comes back delayed by the two group
+    delays, (384 - 1)/2 + (32 - 1)/2 = 207 samples; the oracle's alignment for
+    the next level up is the same 207."""
+    hd = oracle_mod.kaiser_taps(384, 100.0)
+    hu = oracle_mod.kaiser_taps(32, 60.0)
+    n = 8192
+    x = np.cos(0.05 * math.pi * np.arange(n))
+    back = oracle_mod.upsample_add(oracle_mod.decimate(x, hd).astype(np.complex128), hu).real
+    ref = np.concatenate([np.zeros(207), x])[:n]
+    assert np.max(np.abs(back[600:] - ref[600:])) < 5e-3
+    assert oracle_mod.align_delay(1, 3, 384, n_taps_up=32) == 207
+    assert oracle_mod.align_delay(0, 3, 384, n_taps_up=32) == 207 + 2 * 207
 
 
 def test_lower_rate_filter_approximates_base_rate(oracle_mod):
