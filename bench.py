@@ -188,7 +188,8 @@ def _cpu_sample(w, budget_s: float, n_templates_max: int, threads: int = 0):
     def run(sel):
         t0 = time.perf_counter()
         if multi:
-            oracle.spiir_multirate(bank, x, templates=sel, threads=threads)
+            oracle.spiir_multirate(bank, x, h_down=w.get("h_down"), h_up=w.get("h_up"),
+                                   templates=sel, threads=threads)
         else:
             oracle.spiir_single(bank, x, templates=sel, threads=threads)
         return time.perf_counter() - t0
@@ -295,6 +296,8 @@ def _measure(w, form, args, dev, dist, sampler, rank, ws):
     n = w["x"].shape[1]
     push_len = w["block_len"] * w["push_blocks"]
     kw = dict(tune=args.tune) if form == "plain" else dict(mode=form, chunk_len=w["chunk_len"])
+    if w.get("h_down") is not None:
+        kw.update(h_down=w["h_down"], h_up=w["h_up"])
     b = spiir.Bank(bank, n_streams=S, block_len=w["block_len"], max_push_blocks=w["push_blocks"], **kw)
     info = b.info()
     x = torch.from_numpy(w["x"]).to(dev)
@@ -420,6 +423,11 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = _workload(args.workload, rank, args.templates, args.seconds)
+    if args.resampler == "paper":
+        # Sec. 2.2's pair: a 384-tap 100 dB decimator, a 32-tap 60 dB interpolator
+        from paper_1702_02256_gb300 import spiir
+        w["h_down"], w["h_up"] = spiir.kaiser_taps(384, 100.0), spiir.kaiser_taps(32, 60.0)
+        w["desc"] += ", resampler: 384-tap 100 dB decimator, 32-tap 60 dB interpolator"
     sampler = ClockSampler(_gpu_id(torch, local)) if rank == 0 else None
     if sampler:
         sampler.start()
@@ -599,6 +607,9 @@ def main():
                     help="compute form of the headline number (default: plain; fp16 for tc)")
     ap.add_argument("--chosen", default="fp16", choices=["", "plain", "fp16", "bf16"],
                     help="second form measured on the same workload and reported as 'chosen'")
+    ap.add_argument("--resampler", default="default", choices=["default", "paper"],
+                    help="multi-rate: 32/32-tap 60 dB pair (default) or the paper's "
+                         "384-tap 100 dB decimator with the 32-tap interpolator")
     ap.add_argument("--tune", type=int, default=None,
                     help="plain-form kernel variant: 1 = autotune at bank creation, 0 = default, "
                          "-(v+1) = variant v (default: autotune for multirate, else 0)")

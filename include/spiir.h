@@ -83,9 +83,10 @@ typedef struct {
     const int32_t *delay;         /* d_k >= 0, samples at the filter's rate */
     const int32_t *template_id;   /* in [0, n_templates) */
     const int8_t *level;          /* in [0, n_levels); NULL = all level 0 */
-    const float *h_down, *h_up;   /* resampling taps, n_taps each; NULL =
-                                     built-in 60 dB Kaiser low-pass */
-    int32_t n_taps;               /* even, 2..64; 0 = 32 */
+    const float *h_down, *h_up;   /* decimator taps (n_taps of them) and
+                                     interpolator taps (n_taps_up); NULL =
+                                     built-in 60 dB Kaiser low-passes */
+    int32_t n_taps;               /* decimator length: even, 2..512; 0 = 32 */
     int32_t align;                /* 1 = delay level sums by D_i (default
                                      when n_levels > 1), 0 = no delay */
     float snr_scale;              /* 0 = 2/base_rate (2*dt, Eq. iireq1) */
@@ -96,6 +97,9 @@ typedef struct {
                                      the fastest, -(v+1) = use variant v */
     int64_t hbm_budget_bytes;     /* 0 = no limit; else create fails with
                                      SPIIR_EBUDGET above it */
+    int32_t n_taps_up;            /* interpolator length: even, 2..64; 0 =
+                                     n_taps (Sec. 2.2 pairs a long 100 dB
+                                     decimator with a 32-tap interpolator) */
 } spiir_bank_desc;
 
 /* Read-only facts about a created bank. */

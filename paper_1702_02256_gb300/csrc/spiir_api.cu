@@ -96,7 +96,7 @@ void lib_kaiser_taps(int n, double A, float *out) {
 
 struct Plan {
     int variant = 0, T = 32, FMAX = 8;
-    int n_levels = 1, H = 0, n_taps = 32, align = 0;
+    int n_levels = 1, H = 0, n_taps = 32, n_taps_up = 32, align = 0;   // decimator, interpolator
     int hist[SPIIR_MAX_LEVELS] = {};
     int seg[SPIIR_MAX_LEVELS] = {};
     int64_t max_n[SPIIR_MAX_LEVELS] = {};
@@ -144,10 +144,12 @@ int push_segments_n(int64_t n) {
 
 int64_t segment_len(int64_t n, int i, int S) { return round_up(((n >> i) + S - 1) / S, 4); }
 
-int64_t align_delay(int level, int n_levels, int n_taps, int align) {
+int64_t align_delay(int level, int n_levels, int n_taps, int n_taps_up, int align) {
     if (!align) return 0;
     int64_t D = 0;
-    for (int i = n_levels - 2; i >= level; --i) D = (n_taps - 1) + 2 * D;
+    // a down/up round trip: the two linear-phase group delays at the higher rate
+    const int64_t R = (n_taps + n_taps_up) / 2 - 1;
+    for (int i = n_levels - 2; i >= level; --i) D = R + 2 * D;
     return D;
 }
 
@@ -171,8 +173,11 @@ spiir_status validate(const spiir_bank_desc *d) {
                              !d->template_id))
         return fail(SPIIR_EINVAL, "filter arrays must not be NULL");
     const int nt = d->n_taps ? d->n_taps : 32;
-    if (nt < 2 || nt > SPIIR_MAX_TAPS || (nt & 1))
-        return fail(SPIIR_EINVAL, "n_taps must be even and in [2, %d]", SPIIR_MAX_TAPS);
+    if (nt < 2 || nt > SPIIR_MAX_DOWN_TAPS || (nt & 1))
+        return fail(SPIIR_EINVAL, "n_taps must be even and in [2, %d]", SPIIR_MAX_DOWN_TAPS);
+    const int ntu = d->n_taps_up ? d->n_taps_up : nt;
+    if (ntu < 2 || ntu > SPIIR_MAX_TAPS || (ntu & 1))
+        return fail(SPIIR_EINVAL, "interpolator taps must be even and in [2, %d]", SPIIR_MAX_TAPS);
     if ((d->h_down == nullptr) != (d->h_up == nullptr))
         return fail(SPIIR_EINVAL, "give both h_down and h_up or neither");
     if (d->mode < SPIIR_PLAIN_FP32 || d->mode > SPIIR_TC_BF16X2)
@@ -239,6 +244,7 @@ spiir_status make_plan(const spiir_bank_desc *d, int variant, bool arrays, Plan 
     p.n_levels = d->n_levels;
     p.H = d->n_levels - 1;
     p.n_taps = d->n_taps ? d->n_taps : 32;
+    p.n_taps_up = d->n_taps_up ? d->n_taps_up : p.n_taps;
     p.align = (d->n_levels > 1) ? (d->align != 0) : 0;
     const int L = p.n_levels;
     const int64_t push_max = (int64_t)d->block_len * d->max_push_blocks;
@@ -253,7 +259,7 @@ spiir_status make_plan(const spiir_bank_desc *d, int variant, bool arrays, Plan 
     }
     int64_t off = 0;
     for (int i = 0; i < L; ++i) {
-        const int64_t D = align_delay(i, L, p.n_taps, p.align);
+        const int64_t D = align_delay(i, L, p.n_taps, p.n_taps_up, p.align);
         int64_t h = (int64_t)maxd[i] + D;
         if (i < p.H) h = std::max<int64_t>(h, p.n_taps - 1);
         h = round_up(h, 4);
@@ -451,7 +457,7 @@ spiir_status make_plan(const spiir_bank_desc *d, int variant, bool arrays, Plan 
         for (int bi : ib) {
             const Bundle &b = bundles[bi];
             const int g = b.G, F = b.F, lv = b.level, W = b.W;
-            const int64_t D = align_delay(lv, L, p.n_taps, p.align);
+            const int64_t D = align_delay(lv, L, p.n_taps, p.n_taps_up, p.align);
             const int hist = p.hist[lv];
             int gl = 0;
             while ((1 << gl) < g) ++gl;
@@ -794,10 +800,10 @@ spiir_status launch_sequence(spiir_bank *b, int s0, int count, const float *x, i
         ca.scale = b->scale;
         ca.n_templates = b->d.n_templates;
         ca.n_levels = p.n_levels;
-        ca.n_taps = p.n_taps;
+        ca.n_taps = p.n_taps_up;
         ca.stream0 = s0;
         ca.status = b->status;
-        for (int j = 0; j < p.n_taps; ++j) ca.h_up2[j] = 2.0f * b->h_up[j];
+        for (int j = 0; j < p.n_taps_up; ++j) ca.h_up2[j] = 2.0f * b->h_up[j];
         level_args(b, n, n_prev, ca.lev);
         tm.begin(SPIIR_K_COMBINE, st);
         CUDA_TRY(spiir_launch_combine(ca, spiir_combine_chunk(p.n_levels, p.ring_len), count, st));
@@ -871,17 +877,18 @@ spiir_status build_bank(const spiir_bank_desc *desc, int variant, cudaStream_t s
     b->d.level = nullptr;
     b->d.h_down = b->d.h_up = nullptr;
     if (b->d.n_taps == 0) b->d.n_taps = 32;
+    if (b->d.n_taps_up == 0) b->d.n_taps_up = b->d.n_taps;
     if (b->d.chunk_len == 0) b->d.chunk_len = 256;
     b->scale = desc->snr_scale != 0.f ? desc->snr_scale : 2.0f / (float)desc->base_rate;
-    const int nt = b->d.n_taps;
+    const int nt = b->d.n_taps, ntu = b->d.n_taps_up;
     b->h_down.resize(nt);
-    b->h_up.resize(nt);
+    b->h_up.resize(ntu);
     if (desc->h_down) {
         std::copy(desc->h_down, desc->h_down + nt, b->h_down.begin());
-        std::copy(desc->h_up, desc->h_up + nt, b->h_up.begin());
+        std::copy(desc->h_up, desc->h_up + ntu, b->h_up.begin());
     } else {
         lib_kaiser_taps(nt, 60.0, b->h_down.data());
-        lib_kaiser_taps(nt, 60.0, b->h_up.data());
+        lib_kaiser_taps(ntu, 60.0, b->h_up.data());
     }
     b->last_n.assign(desc->n_streams, 0);
     if (!b->timer) b->timer = new KernelTimer();
@@ -1355,15 +1362,17 @@ extern "C" spiir_status spiir_filter_noalloc(const spiir_bank_desc *desc, const 
 
     b.scale = desc->snr_scale != 0.f ? desc->snr_scale : 2.0f / (float)desc->base_rate;
     const int nt = d.n_taps ? d.n_taps : 32;
+    const int ntu = d.n_taps_up ? d.n_taps_up : nt;
     b.d.n_taps = nt;
+    b.d.n_taps_up = ntu;
     b.h_down.resize(nt);
-    b.h_up.resize(nt);
+    b.h_up.resize(ntu);
     if (desc->h_down) {
         std::copy(desc->h_down, desc->h_down + nt, b.h_down.begin());
-        std::copy(desc->h_up, desc->h_up + nt, b.h_up.begin());
+        std::copy(desc->h_up, desc->h_up + ntu, b.h_up.begin());
     } else {
         lib_kaiser_taps(nt, 60.0, b.h_down.data());
-        lib_kaiser_taps(nt, 60.0, b.h_up.data());
+        lib_kaiser_taps(ntu, 60.0, b.h_up.data());
     }
     b.last_n.assign(1, 0);
     b.timer = &g_noalloc_timer;

@@ -6,7 +6,8 @@
 #include <stdint.h>
 
 #define SPIIR_MAX_LEVELS 12
-#define SPIIR_MAX_TAPS 64
+#define SPIIR_MAX_TAPS 64        // interpolator taps
+#define SPIIR_MAX_DOWN_TAPS 512  // decimator taps
 #define SPIIR_UHIST 32   // history kept per upsampler input row (>= n_taps/2)
 #define SPIIR_CTA_WARPS 4
 
@@ -103,7 +104,7 @@ struct DecimArgs {
     int32_t stream0;
     int32_t n_levels;
     int32_t n_taps;
-    float h_down[SPIIR_MAX_TAPS];
+    float h_down[SPIIR_MAX_DOWN_TAPS];
     LevelArgs lev[SPIIR_MAX_LEVELS];
 };
 

@@ -137,8 +137,8 @@ __global__ void prologue_kernel(const PrologueArgs a) {
 __global__ void decimate_kernel(const DecimArgs a) {
     const int s = a.stream0 + blockIdx.x;
     float *base = a.xbuf + (int64_t)s * a.xbuf_stream_stride;
-    __shared__ float h[SPIIR_MAX_TAPS];
-    if (threadIdx.x < a.n_taps) h[threadIdx.x] = a.h_down[threadIdx.x];
+    __shared__ float h[SPIIR_MAX_DOWN_TAPS];
+    for (int j = threadIdx.x; j < a.n_taps; j += blockDim.x) h[j] = a.h_down[j];
     __syncthreads();
     for (int i = 1; i < a.n_levels; ++i) {
         const LevelArgs Ls = a.lev[i - 1], Ld = a.lev[i];
@@ -146,9 +146,14 @@ __global__ void decimate_kernel(const DecimArgs a) {
         float *dst = base + Ld.xbuf_off + Ld.hist;
         for (int m = threadIdx.x; m < Ld.n; m += blockDim.x) {
             const float *p = src + 2 * m;
-            float acc = 0.f;
-            for (int j = 0; j < a.n_taps; ++j) acc = fmaf(h[j], p[-j], acc);
-            dst[m] = acc;
+            // two interleaved partial sums (taps are even in number): shorter
+            // dependency chains for long decimators
+            float acc0 = 0.f, acc1 = 0.f;
+            for (int j = 0; j < a.n_taps; j += 2) {
+                acc0 = fmaf(h[j], p[-j], acc0);
+                acc1 = fmaf(h[j + 1], p[-j - 1], acc1);
+            }
+            dst[m] = acc0 + acc1;
         }
         __syncthreads();
     }

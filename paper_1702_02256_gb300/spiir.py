@@ -33,7 +33,7 @@ class BankDesc(ctypes.Structure):
         ("delay", _c_void_p), ("template_id", _c_void_p), ("level", _c_void_p),
         ("h_down", _c_void_p), ("h_up", _c_void_p),
         ("n_taps", _i32), ("align", _i32), ("snr_scale", _f32), ("mode", _i32),
-        ("chunk_len", _i32), ("tune", _i32), ("hbm_budget_bytes", _i64),
+        ("chunk_len", _i32), ("tune", _i32), ("hbm_budget_bytes", _i64), ("n_taps_up", _i32),
     ]
 
 
@@ -152,6 +152,7 @@ def make_desc(bank, n_streams: int = 1, block_len: int = 4096, max_push_blocks: 
         d.h_down = keep["h_down"].ctypes.data
         d.h_up = keep["h_up"].ctypes.data
         d.n_taps = int(keep["h_down"].shape[0])
+        d.n_taps_up = int(keep["h_up"].shape[0])
     d.align = int(bank.n_levels > 1 if align is None else align)
     d.snr_scale = snr_scale
     d.mode = MODES[mode] if isinstance(mode, str) else int(mode)

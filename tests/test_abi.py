@@ -76,6 +76,12 @@ def test_validation_rejects_bad_descriptions():
     mr = inputs.multi_rate_bank(2, 3, seed=1)
     assert _status(mr, block_len=4098) == spiir.EINVAL  # not a multiple of 4
     assert _status(mr, block_len=4096, mode="fp16") == spiir.EUNSUPPORTED
+    # resampler lengths: decimator up to 512 taps, interpolator up to 64, even
+    hd, hu = spiir.kaiser_taps(384, 100.0), spiir.kaiser_taps(32, 60.0)
+    assert _status(mr, block_len=4096, h_down=hd, h_up=hu) == spiir.OK
+    assert _status(mr, block_len=4096, h_down=spiir.kaiser_taps(514, 100.0), h_up=hu) == spiir.EINVAL
+    assert _status(mr, block_len=4096, h_down=hd, h_up=spiir.kaiser_taps(66, 60.0)) == spiir.EINVAL
+    assert _status(mr, block_len=4096, h_down=hd, h_up=spiir.kaiser_taps(31, 60.0)) == spiir.EINVAL
     d, _k = spiir.make_desc(bank)
     assert spiir.lib().spiir_bank_create(None, None, ctypes.byref(ctypes.c_void_p())) == spiir.EINVAL
     assert "NULL" in spiir.last_error()

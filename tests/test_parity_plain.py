@@ -158,6 +158,19 @@ def test_multirate_interpolator_lengths(torch_cuda, oracle_mod, n_taps):
     assert err.max() <= TOL_PLAIN, err
 
 
+def test_multirate_paper_resampler(torch_cuda, oracle_mod):
+    """The paper's resampler pair (Sec. 2.2): a 384-tap 100 dB Kaiser decimator
+    with a 32-tap 60 dB interpolator, aligned levels, 7 rates."""
+    bank = inputs.multi_rate_bank(10, 7, seed=19, delay_max=500)
+    hd = oracle_mod.kaiser_taps(384, 100.0)
+    hu = oracle_mod.kaiser_taps(32, 60.0)
+    x = inputs.strain(1, 3 * 4096, seed=23)
+    z = gpu_snr(bank, x, push_blocks=1, h_down=hd, h_up=hu)[0]
+    ref = oracle_mod.spiir_multirate(bank, x[0], h_down=hd, h_up=hu)
+    err = rel_rms(z, ref)
+    assert err.max() <= TOL_PLAIN, err
+
+
 def test_multirate_full_size_sampled(torch_cuda, oracle_mod):
     """Config 2 at full size (4000 templates, 7 rates), 4 s pushed in 1 s
     blocks; 12 seeded templates against the oracle."""
