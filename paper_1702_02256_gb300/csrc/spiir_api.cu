@@ -263,14 +263,14 @@ spiir_status make_plan(const spiir_bank_desc *d, int variant, bool arrays, Plan 
         int64_t h = (int64_t)maxd[i] + D;
         if (i < p.H) h = std::max<int64_t>(h, p.n_taps - 1);
         h = round_up(h, 4);
-        if (h + p.T + 8 > (kSmemMax - 64) / 4)
-            return fail(SPIIR_EUNSUPPORTED, "delay %lld at level %d does not fit shared memory",
-                        (long long)h, i);
         p.hist[i] = (int)h;
         p.max_delay = std::max<int>(p.max_delay, (int)(maxd[i] + D));
         p.max_n[i] = push_max >> i;
         // the window holds the history plus the longest segment
         const int64_t sg = std::min<int64_t>(round_up(p.max_n[i], 4), round_up(std::max(4096 >> i, 4), 4));
+        if (16 + spiir_recur_red_bytes() + 4 * (h + sg) + 64 > kSmemMax - 1024)
+            return fail(SPIIR_EUNSUPPORTED, "delay %lld at level %d does not fit shared memory",
+                        (long long)h, i);
         p.seg[i] = (int)sg;
         p.smem_bytes = std::max<int>(p.smem_bytes,
                                      (int)(16 + spiir_recur_red_bytes() + 4 * (h + sg) + 64));

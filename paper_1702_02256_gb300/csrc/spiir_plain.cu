@@ -172,6 +172,8 @@ __global__ void decimate_kernel(const DecimArgs a) {
 // ---------------------------------------------------------------------------
 
 constexpr int kRedBytes = 2 * SPIIR_CTA_WARPS * 32 * 2 * 4;   // cross-warp sums, 2 buffers
+constexpr int kRowPitch = 33;                                  // float2 per staged row (padded)
+constexpr int kScratchBytes = SPIIR_CTA_WARPS * 32 * kRowPitch * 8;   // small-unit output rows
 
 __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
     unsigned int v;
@@ -293,6 +295,7 @@ struct OutCtx {
     int xw_log2, xw_rank, warp;
     int n_tiles;      // tiles in this segment (for the cross-warp hand-off)
     float *red;       // cross-warp buffers in shared memory
+    float2 *scratch;  // per-warp staging of small units' output rows
 };
 
 // After the reduce-scatter for group size G a lane holds CH = max(T/G, 1)
@@ -338,6 +341,27 @@ __device__ __forceinline__ void reduce_write(float (&re)[T], float (&im)[T], int
             }
             if (tile + 2 < o.n_tiles) named_arrive(base + 2 + b, n);
         }
+    }
+    if constexpr (T == 32 && G <= 4) {
+        // Small groups: a lane holds CH = 32 / G consecutive sums of its
+        // group's row, so a direct store would touch 32 / G rows per
+        // instruction. Stage the warp's rows in shared memory and write each
+        // row with one 256-byte store of the whole warp.
+        float2 *sc = o.scratch + o.warp * (32 * kRowPitch);
+        const int grp = lane / G, tcs = (lane & (G - 1)) * CH;
+#pragma unroll
+        for (int i = 0; i < CH; ++i)
+            sc[grp * kRowPitch + tcs + i] = make_float2(o.scale * re[i], o.scale * im[i]);
+        __syncwarp();
+        const unsigned long long rowbits = reinterpret_cast<unsigned long long>(o.row);
+#pragma unroll
+        for (int r = 0; r < 32 / G; ++r) {
+            const unsigned long long rb = __shfl_sync(0xffffffffu, rowbits, r * G);
+            const int v = __shfl_sync(0xffffffffu, (int)o.valid, r * G);
+            if (v && lane < tl) reinterpret_cast<float2 *>(rb)[t0 + lane] = sc[r * kRowPitch + lane];
+        }
+        __syncwarp();
+        return;
     }
     if (!o.valid) return;
     if ((lane & ((1 << NR) - 1)) != 0) return;
@@ -388,7 +412,8 @@ __global__ void __launch_bounds__(SPIIR_CTA_WARPS * 32, MINB) recur_kernel(const
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
     float *red = reinterpret_cast<float *>(smem + 16);
-    float *xs = reinterpret_cast<float *>(smem + 16 + kRedBytes);
+    float2 *scratch = reinterpret_cast<float2 *>(smem + 16 + kRedBytes);
+    float *xs = reinterpret_cast<float *>(smem + 16 + kRedBytes + kScratchBytes);
     __shared__ int s_item;
 
     const int stream = a.stream0 + blockIdx.y;
@@ -463,6 +488,7 @@ __global__ void __launch_bounds__(SPIIR_CTA_WARPS * 32, MINB) recur_kernel(const
                 o.warp = warp;
                 o.n_tiles = (sl + T - 1) / T;
                 o.red = red;
+                o.scratch = scratch;
                 const int grp = lane >> wt.g_log2;
                 if (grp < wt.n_groups && wt.xw_rank == 0) {
                     const int dst = a.task_out[wt.out_base + grp];
@@ -740,7 +766,7 @@ cudaError_t spiir_recur_prepare(int v, int smem_bytes, int *ctas_per_sm) {
     return e;
 }
 
-int spiir_recur_red_bytes() { return kRedBytes; }
+int spiir_recur_red_bytes() { return kRedBytes + kScratchBytes; }
 
 cudaError_t spiir_launch_prologue(const PrologueArgs &a, int n_streams, cudaStream_t s) {
     prologue_kernel<<<dim3(a.n_levels, n_streams), 256, 0, s>>>(a);
