@@ -343,10 +343,11 @@ __device__ __forceinline__ void reduce_write(float (&re)[T], float (&im)[T], int
         }
     }
     if constexpr (T == 32 && G <= 4) {
-        // Small groups: a lane holds CH = 32 / G consecutive sums of its
-        // group's row, so a direct store would touch 32 / G rows per
-        // instruction. Stage the warp's rows in shared memory and write each
-        // row with one 256-byte store of the whole warp.
+        // Groups of up to 4 lanes: a lane holds CH = 32 / G consecutive sums
+        // of its group's row, so a direct store would scatter over 8 to 32
+        // rows at a stride of CH samples. Stage the warp's rows in shared
+        // memory and write each row with one 256-byte store of the whole
+        // warp. (Larger groups gain nothing from it.)
         float2 *sc = o.scratch + o.warp * (32 * kRowPitch);
         const int grp = lane / G, tcs = (lane & (G - 1)) * CH;
 #pragma unroll
