@@ -131,15 +131,18 @@ def _source_hash(kernel_file: str) -> str:
     return h.hexdigest()[:16]
 
 
-def _traffic(kernel_file: str, key: str):
+def _traffic(kernel_file: str, key: str, variant=None):
     """DRAM bytes per launch from a committed ncu summary, if the kernel and
-    planner sources have not changed since it was taken."""
+    planner sources have not changed since it was taken and, where the
+    summary names a kernel variant, the run used that variant."""
     path = os.path.join(ROOT, "profiles", f"{key}_traffic.txt")
     try:
         kv = dict(tok.split("=", 1) for tok in open(path).read().split() if "=" in tok)
     except OSError:
         return None
     if kv.get("source_sha256_16") != _source_hash(kernel_file):
+        return None
+    if "kernel_variant" in kv and (variant is None or int(kv["kernel_variant"]) != int(variant)):
         return None
     return float(kv["dram_bytes_per_launch"])
 
@@ -386,7 +389,8 @@ def _roofline(m, w, args, peaks, sms):
         ach = FLOPS_PER_FS * m["fs_per_step"] * m["steps"] / nl / (ms / nl / 1e3) / 1e12 if nl else 0.0
         return {"bound": "alu", "kernel": "recur_kernel", "achieved": ach, "peak": peak,
                 "unit": "TFLOP/s", "frac": ach / peak if peak else None,
-                "traffic": _traffic("spiir_plain.cu", f"recur_{args.workload}"),
+                "traffic": _traffic("spiir_plain.cu", f"recur_{args.workload}",
+                                    m["info"].get("kernel_variant")),
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz "
                               f"(sm_max_mhz of measured peaks) / {LANE_OPS_PER_FS} lane-ops x "
                               f"{FLOPS_PER_FS} flops per filter-sample"}

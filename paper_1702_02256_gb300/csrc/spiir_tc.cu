@@ -99,6 +99,20 @@ __device__ __forceinline__ bool mbar_try(uint64_t *m, uint32_t ph) {
     return ok != 0;
 }
 
+// As mbar_try, with a hint (ns) for how long the thread may be suspended
+// while the phase is incomplete: a polling loop that does not take issue
+// slots from the warps doing the work.
+__device__ __forceinline__ bool mbar_try_ns(uint64_t *m, uint32_t ph, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(s32(m)), "r"(ph), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait (~2 s): on timeout record it and report false.
 __device__ __forceinline__ bool mbar_wait(uint64_t *m, uint32_t ph, unsigned int *status) {
     if (mbar_try(m, ph)) return true;
@@ -532,18 +546,21 @@ __global__ void __launch_bounds__(kFirThreads, 1) tc_fir_kernel(const TcFirArgs 
 //                    the OUTPUT of earlier ones), and the strain-segment copies
 //   warps 1-4        power panel of each job into its slot, and the epilogue
 //                    of each (template, batch): OUTPUT accumulators -> z,
-//                    taken up two jobs after its last tile
+//                    taken while the next panel's slot is still in use (or
+//                    at the latest five jobs after its last tile)
 //   warps 5-8, 9-12  carry groups 0 and 1: STATE (tensor memory) -> FP32
 //                    carry inside a batch, FP64 from batch to batch -> OUTPUT
 //                    operand W of the job's slot
-// Panel of a 128-filter tile: R[k][m] = Re a_k^m (m < 64), Im a_k^(m-64)
-// (m >= 64), layout [k/8][m/8][k%8][m%8]. STATE reads it K-major (filters x
-// powers, re and im halves separately); OUTPUT reads it MN-major with the re
-// and im powers stacked along M = 128:
+// Panel of a 128-filter tile: 128 rows m of powers, layout
+// [k/8][m/8][k%8][m%8]; row m = 32 q + r holds Re a_k^j for r < 16 and
+// Im a_k^j for r >= 16, with j = 16 q + (r % 16). STATE reads it K-major
+// (filters x powers: the re powers 16 i .. 16 i + 15 are row groups 4 i and
+// 4 i + 1, the im powers groups 4 i + 2 and 4 i + 3); OUTPUT reads it
+// MN-major along M = 128:
 //   D[m][2c]     = sum_k R[k][m] Re w_k(c),  D[m][2c + 1] = sum_k R[k][m] Im w_k(c)
-//   z_re(j) = D[j][2c] - D[64 + j][2c + 1],  z_im(j) = D[j][2c + 1] + D[64 + j][2c]
-// so the epilogue pairs row j with row 64 + j (another warp) through a small
-// double-buffered shared-memory exchange under the panel role's own barrier.
+//   z_re(j) = D[re j][2c] - D[im j][2c + 1],  z_im(j) = D[re j][2c + 1] + D[im j][2c]
+// The two rows of power j are lanes r and r + 16 of one warp's tensor-memory
+// quadrant, so the epilogue pairs them with warp shuffles.
 // Every hand-off between roles is an mbarrier: tcgen05.commit for
 // contractions, one arrive per thread for the 128-thread roles; every wait is
 // bounded and gives up at once when another role has given up (the panel role
@@ -556,9 +573,7 @@ constexpr int kCarryWarps = 13;
 constexpr int kSlots = 3;
 constexpr int kPanelBytes = kTile * 2 * kJ * 2;                 // 32 KB
 constexpr int kWBytes = kTile * 2 * kNii * 2;                   // 32 KB
-constexpr int kExStride = 17;                                   // floats per exchange row
-constexpr int kExBytes = 2 * 64 * kExStride * 4;                // two rounds in flight
-constexpr int kCarrySmem = kSlots * (kPanelBytes + kWBytes) + 2 * kXsegBytes + kExBytes;   // 212 KB
+constexpr int kCarrySmem = kSlots * (kPanelBytes + kWBytes) + 2 * kXsegBytes;   // 208 KB
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *m) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s32(m)) : "memory");
@@ -620,10 +635,6 @@ __device__ __forceinline__ bool panel_role_all(bool v) {
         : "r"((uint32_t)v)
         : "memory");
     return r != 0;
-}
-
-__device__ __forceinline__ void panel_role_sync() {
-    asm volatile("bar.sync 1, 128;" ::: "memory");
 }
 
 struct CarryJob {
@@ -691,7 +702,6 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
     // slot s: panel at s * kPanelBytes, W at kSlots * kPanelBytes + s * kWBytes
     unsigned char *Wb = smem + kSlots * kPanelBytes;
     unsigned char *Xs = Wb + kSlots * kWBytes;                     // strain segments of batches b % 2
-    float *ex = reinterpret_cast<float *>(Xs + 2 * kXsegBytes);
     // OUTPUT operand W, MN-major [k/8][n/8][k%8][n%8] (n = column, k = filter):
     // 8-column groups 128 bytes apart, 8-filter groups kWK apart; column 2c =
     // Re w(c), 2c + 1 = Im w(c) of chunk column c = (stream, chunk, j2)
@@ -796,16 +806,18 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                         else last0 = J.j;
                         tc_fence_after();
                         // descriptors advance by 16-byte units in their low bits;
-                        // re powers are panel k-blocks 0..7, im powers 8..15
+                        // re powers 16 kk .. 16 kk + 15 are panel row groups 4 kk and
+                        // 4 kk + 1, the im powers the two groups after them
                         const uint64_t dr0 = sdesc(smem0 + sl * kPanelBytes, 128, 2048);
-                        const uint64_t di0 = dr0 + ((kJ / 8 * 128) >> 4);
+                        const uint64_t di0 = dr0 + (256 >> 4);
                         const uint64_t dx0 = sdesc(xs0 + xb * kXsegBytes, 128, (kJ / 8) * 128);
                         const uint32_t d = tmem + 128 * g;
 #pragma unroll
                         for (int kk = 0; kk < kJ / 16; ++kk) {
-                            const uint64_t o = (uint64_t)(kk * 256) >> 4;
-                            mma(d, dr0 + o, dx0 + o, id_state, kk ? 1u : 0u);
-                            mma(d + kNii, di0 + o, dx0 + o, id_state, kk ? 1u : 0u);
+                            const uint64_t o = (uint64_t)(kk * 512) >> 4;
+                            const uint64_t ox = (uint64_t)(kk * 256) >> 4;
+                            mma(d, dr0 + o, dx0 + ox, id_state, kk ? 1u : 0u);
+                            mma(d + kNii, di0 + o, dx0 + ox, id_state, kk ? 1u : 0u);
                         }
                         mma_commit(&state_full[g]);
                         issued = true;
@@ -881,10 +893,10 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
         // panel: thread = filter k: a_k^i, i < 64, as four chains of 16
         // powers (starting from a^0, a^16, a^32, a^48)
         const int k = threadIdx.x - 32;
-        // epilogue: thread = tensor-memory lane m; rows 0..63 (warps 4 and 1)
-        // combine with rows 64..127 (warps 2 and 3) through the exchange rows
-        const int m = (warp & 3) * 32 + lane;
-        const bool top = m < 64;
+        // epilogue: thread = lane r of its warp's tensor-memory quadrant q;
+        // lanes r and r + 16 hold the re and im rows of power j = 16 q + r % 16
+        const bool hi = lane >= 16;
+        const int jj = (warp & 3) * 16 + (lane & 15);
         const uint32_t lane_base = ((uint32_t)((warp & 3) * 32)) << 16;
         struct Ep {
             int t, b0, e, j;
@@ -899,12 +911,13 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             const int nb = min(a.cpb, a.n_chunks - b * a.cpb);
             const int nii = S * nb * LJ;                // columns of this batch
             const uint32_t tb = tmem + lane_base + 256 + 128 * ob;
-            const int j1 = m & 63;
-            // z of stream 0 and 1 at this batch's first sample and lane j1
+            // z of stream 0 and 1 at this batch's first sample and power jj
             float2 *zb0 = a.z + (int64_t)a.stream0 * a.z_stream_stride + (int64_t)J.t * a.z_row_stride +
-                          (int64_t)b * a.cpb * L + j1;
+                          (int64_t)b * a.cpb * L + jj;
             float2 *zb1 = zb0 + a.z_stream_stride;
-            // 64 columns per tensor-memory round trip, exchanged 16 at a time
+            // 64 columns per tensor-memory round trip; of the 8 chunk columns in
+            // 16 of them the re-row lane writes the first four, the im-row lane
+            // the last four, each taking the other row from its partner lane
             for (int hh = 0; hh < 2 * kNii / 64; ++hh) {
                 uint32_t v[4][16];
 #pragma unroll
@@ -912,26 +925,26 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                 tmem_wait_ld();
 #pragma unroll
                 for (int i4 = 0; i4 < 4; ++i4) {
-                    const int h = 4 * hh + i4;          // 16 columns = 8 chunk columns
-                    float *row = ex + (h & 1) * (64 * kExStride) + j1 * kExStride;
-                    if (!top) {
+                    const int h = 4 * hh + i4;
+                    float own[8], oth[8];               // own and partner row, this lane's columns
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) row[i] = __uint_as_float(v[i4][i]);
+                    for (int i = 0; i < 8; ++i) {
+                        const float lo_v = __uint_as_float(v[i4][i]), hi_v = __uint_as_float(v[i4][8 + i]);
+                        own[i] = hi ? hi_v : lo_v;
+                        oth[i] = __shfl_xor_sync(0xffffffffu, hi ? lo_v : hi_v, 16);
                     }
-                    // rows of round h are written, and every top thread read
-                    // the other buffer (round h - 1) before arriving here
-                    panel_role_sync();
-                    if (top) {
 #pragma unroll
-                        for (int i = 0; i < 16; i += 2) {
-                            const int c = 8 * h + i / 2;
-                            if (c < nii) {
-                                const float zr = __uint_as_float(v[i4][i]) - row[i + 1];
-                                const float zi = __uint_as_float(v[i4][i + 1]) + row[i];
-                                const int q = c / LJ;                   // c = (chunk S + stream) LJ + j2
-                                float2 *zp = ((q % S) ? zb1 : zb0) + (q / S) * L + kJ * (c % LJ);
-                                *zp = make_float2(a.scale * zr, a.scale * zi);
-                            }
+                    for (int cc = 0; cc < 4; ++cc) {
+                        const float rr = hi ? oth[2 * cc] : own[2 * cc];           // D[re j][2c]
+                        const float ri = hi ? oth[2 * cc + 1] : own[2 * cc + 1];   // D[re j][2c + 1]
+                        const float ir = hi ? own[2 * cc] : oth[2 * cc];           // D[im j][2c]
+                        const float ii = hi ? own[2 * cc + 1] : oth[2 * cc + 1];   // D[im j][2c + 1]
+                        if (8 * h + (hi ? 4 : 0) + cc < nii) {
+                            // c = (chunk S + stream) LJ + j2; the im-row lane's
+                            // columns are 4 / LJ steps on
+                            const int q = (8 * h + cc) / LJ + (hi ? 4 / LJ : 0);
+                            float2 *zp = ((q % S) ? zb1 : zb0) + (q / S) * L + kJ * ((8 * h + cc) % LJ);
+                            *zp = make_float2(a.scale * (rr - ii), a.scale * (ri + ir));
                         }
                     }
                 }
@@ -945,21 +958,19 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             const int sl = J.s;
             const int64_t slot = (int64_t)J.tile * kTile + k;
             const float2 ak = a.a[slot];
-            // Epilogues whose last tile is at least two jobs back, taken
-            // when their contractions have finished; one five or more jobs
-            // back is waited for, since the OUTPUT that frees this job's slot
-            // may need its accumulator (first tile of the (template, batch)
-            // two after it).
-            while (ep_n > 0 && ep0.j <= J.j - 2) {
-                if (ep0.j > J.j - 5 &&
-                    !panel_role_all(mbar_test(&out_full[ep0.e & 1], (ep0.e >> 1) & 1)))
-                    break;
-                if (!(ok = epilogue(ep0))) return false;
+            // Epilogues five or more jobs back are taken first: the OUTPUT
+            // that frees this job's slot may need their accumulator (first
+            // tile of the (template, batch) two after them).
+            auto pop = [&]() {
                 ep0 = ep1;
                 ep1 = ep2;
                 ep2 = ep3;
                 ep3 = ep4;
                 --ep_n;
+            };
+            while (ep_n > 0 && ep0.j <= J.j - 5) {
+                if (!(ok = epilogue(ep0))) return false;
+                pop();
             }
             if (J.last_tile) {
                 const Ep n{J.t, J.b0, J.e, J.j};
@@ -970,9 +981,30 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                 else ep4 = n;
                 ++ep_n;
             }
+            // While this job's slot is still in use, take the epilogues whose
+            // contractions have finished (bounded like every other wait; the
+            // slot test suspends the threads for up to 1 us at a time).
             const int use = J.j / kSlots;
-            if (!(ok = panel_role_all(use == 0 || mbar_wait_ab(&panel_free[sl], (use - 1) & 1, a.status, abort))))
-                return false;
+            if (use > 0) {
+                uint64_t t0 = 0;
+                while (!panel_role_all(mbar_try_ns(&panel_free[sl], (use - 1) & 1, 1000u))) {
+                    if (ep_n > 0 && ep0.j < J.j &&
+                        panel_role_all(mbar_test(&out_full[ep0.e & 1], (ep0.e >> 1) & 1))) {
+                        if (!(ok = epilogue(ep0))) return false;
+                        pop();
+                        t0 = 0;
+                        continue;
+                    }
+                    const uint64_t now = gtime();
+                    if (t0 == 0) {
+                        t0 = now;
+                    } else if (now - t0 > 2000000000ull) {
+                        atomicExch(a.status, SPIIR_DEV_TIMEOUT);
+                        *abort = 1;
+                    }
+                    if (!(ok = panel_role_all(*abort == 0))) return false;
+                }
+            }
             unsigned char *P = smem + sl * kPanelBytes;
             float2 a16 = ak;
 #pragma unroll
@@ -1005,10 +1037,10 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                 }
 #pragma unroll
                 for (int ch = 0; ch < 4; ++ch) {
-                    const int kb = ch * 2 + ib;                 // powers 8 kb .. 8 kb + 7
-                    const size_t off = (size_t)(k >> 3) * 2048 + kb * 128 + (k & 7) * 16;
+                    // powers 16 ch + 8 ib .. + 7: re in row group 4 ch + ib, im two groups on
+                    const size_t off = (size_t)(k >> 3) * 2048 + (4 * ch + ib) * 128 + (k & 7) * 16;
                     *reinterpret_cast<uint4 *>(P + off) = pack8<BF16>(vr[ch]);
-                    *reinterpret_cast<uint4 *>(P + off + 8 * 128) = pack8<BF16>(vi[ch]);
+                    *reinterpret_cast<uint4 *>(P + off + 2 * 128) = pack8<BF16>(vi[ch]);
                 }
             }
             fence_async_smem();
@@ -1140,6 +1172,10 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                     }
                 }
             }
+            // W is complete: the OUTPUT contraction may start while the state
+            // update below runs on the (slow) FP64 pipe
+            fence_async_smem();
+            mbar_arrive(&w_full[sl]);
             // v <- a^(nb L) v + d_nb in FP64, per stream
             double2 pw;
             if (nb == a.cpb) {
@@ -1158,8 +1194,6 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                                   fma(pw.x, v1.y, fma(pw.y, v1.x, (double)dd[1].y)));
                 a.v[(int64_t)(a.stream0 + 1) * a.n_slots + slot] = v1;
             }
-            fence_async_smem();
-            mbar_arrive(&w_full[sl]);
             return true;
         });
     }
