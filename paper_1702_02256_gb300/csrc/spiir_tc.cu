@@ -281,11 +281,11 @@ struct TcCarryArgs {
     int32_t n_carry;
     const float2 *a;          // [slot] a_k
     const float2 *aJ;         // [slot] a_k^kJ
-    const double2 *aL;        // [slot] a_k^L (FP64)
+    const float4 *aL;         // [slot] a_k^L, double-float {re hi, im hi, re lo, im lo}
     const float2 *aLf;        // [slot] a_k^L rounded to FP32
-    const double2 *aLb;       // [slot] a_k^(L * cpb) (FP64), cpb of this launch
+    const float4 *aLb;        // [slot] a_k^(L * cpb), double-float, cpb of this launch
     const float2 *c;          // [slot] a_k^(F-d_k) b_k
-    double2 *v;               // [stream][n_slots] undelayed unit-filter state
+    float4 *v;                // [stream][n_slots] undelayed unit-filter state, double-float
     int64_t n_slots;
     const uint4 *xseg;        // staged STATE strain segments
     int32_t L, n_chunks, n_streams, stream0, cpb, n_batches;
@@ -541,26 +541,28 @@ __global__ void __launch_bounds__(kFirThreads, 1) tc_fir_kernel(const TcFirArgs 
 // sequence of jobs (template, chunk batch, 128-filter tile) on three pipeline
 // slots (power panel and OUTPUT operand in shared memory) and two carry
 // groups, spread over warp roles:
-//   warp 0, lane 0   issues the STATE and OUTPUT contractions as soon as each
-//                    one's inputs are ready (STATE of later jobs may overtake
-//                    the OUTPUT of earlier ones), and the strain-segment copies
+//   warp 0, lane 0   issues the STATE contractions in job order as soon as
+//                    each one's inputs are ready, and the strain-segment copies
+//   warp 13, lane 0  issues the OUTPUT contractions in job order (a separate
+//                    warp, on another scheduler: a single issuer sharing a
+//                    scheduler with the arithmetic warps was slow to react)
 //   warps 1-4        power panel of each job into its slot, and the epilogue
 //                    of each (template, batch): OUTPUT accumulators -> z,
 //                    taken while the next panel's slot is still in use (or
 //                    at the latest five jobs after its last tile)
 //   warps 5-8, 9-12  carry groups 0 and 1: STATE (tensor memory) -> FP32
-//                    carry inside a batch, FP64 from batch to batch -> OUTPUT
-//                    operand W of the job's slot
+//                    carry inside a batch, double-float from batch to batch
+//                    -> OUTPUT operand W of the job's slot
 // Panel of a 128-filter tile: 128 rows m of powers, layout
-// [k/8][m/8][k%8][m%8]; row m = 32 q + r holds Re a_k^j for r < 16 and
-// Im a_k^j for r >= 16, with j = 16 q + (r % 16). STATE reads it K-major
-// (filters x powers: the re powers 16 i .. 16 i + 15 are row groups 4 i and
-// 4 i + 1, the im powers groups 4 i + 2 and 4 i + 3); OUTPUT reads it
+// [k/8][m/8][k%8][m%8], in row groups of 8: group 2 p holds Re a_k^j and
+// group 2 p + 1 Im a_k^j for the powers j = 8 p .. 8 p + 7. STATE reads it
+// K-major (filters x powers: the re powers 16 i .. 16 i + 15 are groups 4 i
+// and 4 i + 2, the im powers groups 4 i + 1 and 4 i + 3); OUTPUT reads it
 // MN-major along M = 128:
 //   D[m][2c]     = sum_k R[k][m] Re w_k(c),  D[m][2c + 1] = sum_k R[k][m] Im w_k(c)
 //   z_re(j) = D[re j][2c] - D[im j][2c + 1],  z_im(j) = D[re j][2c + 1] + D[im j][2c]
-// The two rows of power j are lanes r and r + 16 of one warp's tensor-memory
-// quadrant, so the epilogue pairs them with warp shuffles.
+// The two rows of power j are tensor-memory lanes 8 apart, so one 16-lane
+// load (shape 16x256b) gives each epilogue thread all four terms of z(j, c).
 // Every hand-off between roles is an mbarrier: tcgen05.commit for
 // contractions, one arrive per thread for the 128-thread roles; every wait is
 // bounded and gives up at once when another role has given up (the panel role
@@ -569,7 +571,7 @@ __global__ void __launch_bounds__(kFirThreads, 1) tc_fir_kernel(const TcFirArgs 
 // columns); OUTPUT of (template, batch) e at 256 + 128 (e % 2).
 // ---------------------------------------------------------------------------
 
-constexpr int kCarryWarps = 13;
+constexpr int kCarryWarps = 14;
 constexpr int kSlots = 3;
 constexpr int kPanelBytes = kTile * 2 * kJ * 2;                 // 32 KB
 constexpr int kWBytes = kTile * 2 * kNii * 2;                   // 32 KB
@@ -615,6 +617,26 @@ __device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t (&r)[16]) 
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
           "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+// 16 lanes x 256 bits, 16 times along the columns: thread t gets rows
+// t / 4 and t / 4 + 8, columns 2 (t % 4) and 2 (t % 4) + 1 of each 8.
+__device__ __forceinline__ void tmem_ld16x256_x16(uint32_t taddr, uint32_t (&r)[64]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x256b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+        "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+          "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+          "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+          "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+          "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
         : "r"(taddr)
         : "memory");
 }
@@ -692,11 +714,51 @@ __device__ __forceinline__ float2 cmul(float2 x, float2 y) {
     return make_float2(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x);
 }
 
+// Double-float complex numbers: float4 {re hi, im hi, re lo, im lo}, value
+// hi + lo with |lo| <= ulp(hi) / 2 (about 48 significant bits), on the FP32
+// pipe: GB300's FP64 rate is 2 DFMA per SM and clock. Built from the
+// error-free sum (Knuth's TwoSum), product (FMA residual) and the
+// normalising fast sum (Dekker); the _rn intrinsics keep the compiler from
+// contracting or reassociating them.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// One component of x y + d: x1 y1 + sg x2 y2 + d (x, y double-float parts
+// (hi, lo); sg = +1 or -1), returned as (hi, lo).
+__device__ __forceinline__ float2 df_dot2_add(float x1h, float x1l, float y1h, float y1l, float x2h,
+                                              float x2l, float y2h, float y2l, float sg, float d) {
+    const float p1 = __fmul_rn(x1h, y1h);
+    const float e1 = __fmaf_rn(x1h, y1h, -p1);
+    const float nx2h = sg * x2h, nx2l = sg * x2l;
+    const float p2 = __fmul_rn(nx2h, y2h);
+    const float e2 = __fmaf_rn(nx2h, y2h, -p2);
+    float s, t1, t2;
+    two_sum(p1, p2, s, t1);
+    two_sum(s, d, s, t2);
+    float lo = __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(t1, t2));
+    lo = __fmaf_rn(x1h, y1l, lo);
+    lo = __fmaf_rn(x1l, y1h, lo);
+    lo = __fmaf_rn(nx2h, y2l, lo);
+    lo = __fmaf_rn(nx2l, y2h, lo);
+    const float hi = __fadd_rn(s, lo);
+    return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, s)));
+}
+
+// x y + d for double-float x, y and FP32 d.
+__device__ __forceinline__ float4 cdf_mul_add(float4 x, float4 y, float2 d) {
+    const float2 re = df_dot2_add(x.x, x.z, y.x, y.z, x.y, x.w, y.y, y.w, -1.f, d.x);
+    const float2 im = df_dot2_add(x.x, x.z, y.y, y.w, x.y, x.w, y.x, y.z, 1.f, d.y);
+    return make_float4(re.x, im.x, re.y, im.y);
+}
+
 template <bool BF16, int LJ, int S>
 __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcCarryArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t panel_full[kSlots], panel_free[kSlots], w_full[kSlots], w_free[kSlots],
-        state_full[2], state_free[2], out_full[2], out_free[2], xs_full[2], drain;
+        state_full[2], state_free[2], out_full[2], out_free[2], xs_full[2], drain, drain_o;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
     // slot s: panel at s * kPanelBytes, W at kSlots * kPanelBytes + s * kWBytes
@@ -726,6 +788,7 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
         mbar_init(&xs_full[0], 1);
         mbar_init(&xs_full[1], 1);
         mbar_init(&drain, 1);
+        mbar_init(&drain_o, 1);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -737,26 +800,20 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------- MMA issuer ----------------
-            // STATE runs in job order; OUTPUT runs in job order (the first
-            // tile of a (template, batch) overwrites the accumulator); each is
-            // issued as soon as its barriers have completed. All bookkeeping
-            // is in registers: phase parities and use flags as bits of ph,
-            // the OUTPUT queue as 8-bit entries of oq. Slot phases follow from
-            // the job index (slot use j / kSlots).
-            constexpr uint32_t kSF = 0, kOF = 2, kUsed = 4;
+            // ---------------- STATE issuer ----------------
+            // STATE of each job in job order, as soon as its strain segment,
+            // its carry group's STATE columns and its panel are ready; the
+            // strain-segment copies. Phase parities and use flags are bits
+            // of ph; slot phases follow from the job index (use j / kSlots).
+            constexpr uint32_t kSF = 0, kUsed = 2;
             uint32_t ph = 0, ph_d = 0;
-            // queue entry: bits 0-1 slot, 2 OUTPUT buffer, 3 first tile,
-            // 4 last tile, 5 buffer used before
-            uint32_t oq = 0;
-            int oq_n = 0, oq_j = 0;           // queue length; job index of the head
             // strain-segment buffers (batch b in buffer b % 2): batch held or
             // being loaded, job of the last STATE that read it, load in flight,
             // and the phase of the next load's completion
             int held0 = -1, held1 = -1, last0 = -1000, last1 = -1000;
             uint32_t loading = 0, xs_ph = 0;
-            int last_pf = -1;   // latest job whose panel was seen ready: every
-                                // STATE up to three jobs before it has finished
+            int last_pf = -1;   // latest job whose panel was ready: every STATE
+                                // up to three jobs before it has finished
             auto start_load = [&](int x, int batch) {
                 mbar_expect(&xs_full[x], kXsegBytes);
                 bulk_load(Xs + x * kXsegBytes, a.xseg + (size_t)batch * (kXsegBytes / 16), kXsegBytes,
@@ -766,118 +823,61 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                 loading |= 1u << x;
             };
             bool issued = false, ok = true;
-            CarryJobs st(a);                  // next job for STATE
             const uint32_t id_state = idesc(128, kNii, BF16, false, false);
-            const uint32_t id_out = idesc(128, 2 * kNii, BF16, true, true);
-            const uint32_t smem0 = s32(smem), wb0 = s32(Wb), xs0 = s32(Xs);
-            uint64_t idle0 = 0;
-            while (ok && (st.valid || oq_n > 0)) {
-                bool progressed = false;
-                // STATE of the next job: panel ready and the carry group's
-                // STATE columns free
-                if (st.valid && oq_n < 4) {
-                    const CarryJob J = st.cur();
-                    const uint32_t g = (uint32_t)J.g, sl = (uint32_t)J.s;
-                    const bool used = (ph >> (kUsed + g)) & 1u;
-                    const int xb = J.b0 & 1;
-                    if ((xb ? held1 : held0) != J.b0 && !((loading >> xb) & 1u)) {
-                        // the buffer's readers must be done before it is refilled:
-                        // certain three jobs on, else drain the tensor pipe (rare:
-                        // one-tile templates with several batches)
-                        if (issued && (xb ? last1 : last0) > last_pf - 3) {
-                            mma_commit(&drain);
-                            ok = mbar_wait_ab(&drain, ph_d, a.status, abort);
-                            ph_d ^= 1u;
-                            if (!ok) break;
-                        }
-                        start_load(xb, J.b0);
+            const uint32_t smem0 = s32(smem), xs0 = s32(Xs);
+            for (CarryJobs st(a); ok && st.valid; st.next()) {
+                const CarryJob J = st.cur();
+                const uint32_t g = (uint32_t)J.g, sl = (uint32_t)J.s;
+                const int xb = J.b0 & 1;
+                if ((xb ? held1 : held0) != J.b0 && !((loading >> xb) & 1u)) {
+                    // the buffer's readers must be done before it is refilled:
+                    // certain three jobs on, else drain the tensor pipe (rare:
+                    // one-tile templates with several batches)
+                    if (issued && (xb ? last1 : last0) > last_pf - 3) {
+                        mma_commit(&drain);
+                        ok = mbar_wait_ab(&drain, ph_d, a.status, abort);
+                        ph_d ^= 1u;
+                        if (!ok) break;
                     }
-                    if (((loading >> xb) & 1u) && mbar_test(&xs_full[xb], (xs_ph >> xb) & 1u)) {
-                        loading &= ~(1u << xb);
-                        xs_ph ^= 1u << xb;
-                    }
-                    if (!((loading >> xb) & 1u) &&
-                        (!used || mbar_test(&state_free[g], (ph >> (kSF + g)) & 1u)) &&
-                        mbar_test(&panel_full[sl], (uint32_t)(J.j / kSlots) & 1u)) {
-                        if (used) ph ^= 1u << (kSF + g);
-                        ph |= 1u << (kUsed + g);
-                        last_pf = J.j;
-                        if (xb) last1 = J.j;
-                        else last0 = J.j;
-                        tc_fence_after();
-                        // descriptors advance by 16-byte units in their low bits;
-                        // re powers 16 kk .. 16 kk + 15 are panel row groups 4 kk and
-                        // 4 kk + 1, the im powers the two groups after them
-                        const uint64_t dr0 = sdesc(smem0 + sl * kPanelBytes, 128, 2048);
-                        const uint64_t di0 = dr0 + (256 >> 4);
-                        const uint64_t dx0 = sdesc(xs0 + xb * kXsegBytes, 128, (kJ / 8) * 128);
-                        const uint32_t d = tmem + 128 * g;
+                    start_load(xb, J.b0);
+                }
+                if ((loading >> xb) & 1u) {
+                    if (!(ok = mbar_wait_ab(&xs_full[xb], (xs_ph >> xb) & 1u, a.status, abort))) break;
+                    loading &= ~(1u << xb);
+                    xs_ph ^= 1u << xb;
+                }
+                if ((ph >> (kUsed + g)) & 1u) {
+                    if (!(ok = mbar_wait_ab(&state_free[g], (ph >> (kSF + g)) & 1u, a.status, abort))) break;
+                    ph ^= 1u << (kSF + g);
+                }
+                ph |= 1u << (kUsed + g);
+                if (!(ok = mbar_wait_ab(&panel_full[sl], (uint32_t)(J.j / kSlots) & 1u, a.status, abort))) break;
+                last_pf = J.j;
+                if (xb) last1 = J.j;
+                else last0 = J.j;
+                tc_fence_after();
+                // descriptors advance by 16-byte units in their low bits;
+                // re powers 16 kk .. 16 kk + 15 are panel row groups 4 kk and
+                // 4 kk + 2, the im powers groups 4 kk + 1 and 4 kk + 3
+                const uint64_t dr0 = sdesc(smem0 + sl * kPanelBytes, 256, 2048);
+                const uint64_t di0 = dr0 + (128 >> 4);
+                const uint64_t dx0 = sdesc(xs0 + xb * kXsegBytes, 128, (kJ / 8) * 128);
+                const uint32_t d = tmem + 128 * g;
 #pragma unroll
-                        for (int kk = 0; kk < kJ / 16; ++kk) {
-                            const uint64_t o = (uint64_t)(kk * 512) >> 4;
-                            const uint64_t ox = (uint64_t)(kk * 256) >> 4;
-                            mma(d, dr0 + o, dx0 + ox, id_state, kk ? 1u : 0u);
-                            mma(d + kNii, di0 + o, dx0 + ox, id_state, kk ? 1u : 0u);
-                        }
-                        mma_commit(&state_full[g]);
-                        issued = true;
-                        const uint32_t ent = sl | ((uint32_t)(J.e & 1) << 2) | ((uint32_t)J.first_tile << 3) |
-                                             ((uint32_t)J.last_tile << 4) | ((uint32_t)(J.e >= 2) << 5);
-                        if (oq_n == 0) oq_j = J.j;
-                        oq |= ent << (8 * oq_n);
-                        ++oq_n;
-                        // prefetch the template's next batch into the other buffer
-                        // once that buffer's readers are certainly done
-                        const int nb2 = J.b0 + 1, x2 = nb2 & 1;
-                        if (nb2 < a.n_batches && (x2 ? held1 : held0) != nb2 && !((loading >> x2) & 1u) &&
-                            (x2 ? last1 : last0) <= last_pf - 3)
-                            start_load(x2, nb2);
-                        st.next();
-                        progressed = true;
-                    }
+                for (int kk = 0; kk < kJ / 16; ++kk) {
+                    const uint64_t o = (uint64_t)(kk * 512) >> 4;
+                    const uint64_t ox = (uint64_t)(kk * 256) >> 4;
+                    mma(d, dr0 + o, dx0 + ox, id_state, kk ? 1u : 0u);
+                    mma(d + kNii, di0 + o, dx0 + ox, id_state, kk ? 1u : 0u);
                 }
-                // OUTPUT of the oldest job: D = R^T W over the tile's filters
-                if (oq_n > 0) {
-                    const uint32_t ent = oq & 0xFFu;
-                    const uint32_t sl = ent & 3u, ob = (ent >> 2) & 1u;
-                    const bool first = (ent >> 3) & 1u, last = (ent >> 4) & 1u;
-                    const bool need_of = first && ((ent >> 5) & 1u);
-                    const bool of_ok = !need_of || mbar_test(&out_free[ob], (ph >> (kOF + ob)) & 1u);
-                    if (of_ok && mbar_test(&w_full[sl], (uint32_t)(oq_j / kSlots) & 1u)) {
-                        if (need_of) ph ^= 1u << (kOF + ob);
-                        tc_fence_after();
-                        const uint64_t a0 = sdesc(smem0 + sl * kPanelBytes, 2048, 128);
-                        const uint64_t b0 = sdesc(wb0 + sl * kWBytes, kWK, 128);
-                        const uint32_t dz = tmem + 256 + 128 * ob;
-                        const uint32_t acc0 = first ? 0u : 1u;
-#pragma unroll
-                        for (int kk = 0; kk < kTile / 16; ++kk) {
-                            const uint64_t oa = (uint64_t)(kk * 2 * 2048) >> 4;
-                            const uint64_t ow = (uint64_t)(kk * 2 * kWK) >> 4;
-                            mma(dz, a0 + oa, b0 + ow, id_out, kk ? 1u : acc0);
-                        }
-                        mma_commit(&w_free[sl]);
-                        mma_commit(&panel_free[sl]);
-                        if (last) mma_commit(&out_full[ob]);
-                        oq >>= 8;
-                        --oq_n;
-                        ++oq_j;
-                        progressed = true;
-                    }
-                }
-                if (progressed) {
-                    idle0 = 0;
-                } else {
-                    const uint64_t now = gtime();
-                    if (idle0 == 0) {
-                        idle0 = now;
-                    } else if (now - idle0 > 2000000000ull) {
-                        atomicExch(a.status, SPIIR_DEV_TIMEOUT);
-                        *abort = 1;
-                        ok = false;
-                    }
-                    if (*abort) ok = false;
-                }
+                mma_commit(&state_full[g]);
+                issued = true;
+                // prefetch the template's next batch into the other buffer
+                // once that buffer's readers are certainly done
+                const int nb2 = J.b0 + 1, x2 = nb2 & 1;
+                if (nb2 < a.n_batches && (x2 ? held1 : held0) != nb2 && !((loading >> x2) & 1u) &&
+                    (x2 ? last1 : last0) <= last_pf - 3)
+                    start_load(x2, nb2);
             }
             // nothing may still run when the tensor memory is released, and no
             // copy may still be writing shared memory
@@ -888,15 +888,54 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             for (int x = 0; x < 2; ++x)
                 if ((loading >> x) & 1u) mbar_wait(&xs_full[x], (xs_ph >> x) & 1u, a.status);
         }
+    } else if (warp == kCarryWarps - 1) {
+        if (lane == 0) {
+            // ---------------- OUTPUT issuer ----------------
+            // OUTPUT of each job in job order (the first tile of a (template,
+            // batch) overwrites the accumulator) once its W is written and,
+            // for a first tile, the accumulator's previous epilogue is done.
+            // W complete implies the job's STATE has finished.
+            uint32_t of_ph = 0;                 // out_free phase per buffer
+            bool issued = false;
+            const uint32_t id_out = idesc(128, 2 * kNii, BF16, true, true);
+            const uint32_t smem0 = s32(smem), wb0 = s32(Wb);
+            for (CarryJobs ot(a); ot.valid; ot.next()) {
+                const CarryJob J = ot.cur();
+                const uint32_t sl = (uint32_t)J.s, ob = (uint32_t)(J.e & 1);
+                if (J.first_tile && J.e >= 2) {
+                    if (!mbar_wait_ab(&out_free[ob], (of_ph >> ob) & 1u, a.status, abort)) break;
+                    of_ph ^= 1u << ob;
+                }
+                if (!mbar_wait_ab(&w_full[sl], (uint32_t)(J.j / kSlots) & 1u, a.status, abort)) break;
+                tc_fence_after();
+                // D = R^T W over the tile's filters
+                const uint64_t a0 = sdesc(smem0 + sl * kPanelBytes, 2048, 128);
+                const uint64_t b0 = sdesc(wb0 + sl * kWBytes, kWK, 128);
+                const uint32_t dz = tmem + 256 + 128 * ob;
+                const uint32_t acc0 = J.first_tile ? 0u : 1u;
+#pragma unroll
+                for (int kk = 0; kk < kTile / 16; ++kk) {
+                    const uint64_t oa = (uint64_t)(kk * 2 * 2048) >> 4;
+                    const uint64_t ow = (uint64_t)(kk * 2 * kWK) >> 4;
+                    mma(dz, a0 + oa, b0 + ow, id_out, kk ? 1u : acc0);
+                }
+                mma_commit(&w_free[sl]);
+                mma_commit(&panel_free[sl]);
+                if (J.last_tile) mma_commit(&out_full[ob]);
+                issued = true;
+            }
+            if (issued) {
+                mma_commit(&drain_o);
+                mbar_wait(&drain_o, 0, a.status);
+            }
+        }
     } else if (warp <= 4) {
         // ---------------- power panels and epilogue ----------------
         // panel: thread = filter k: a_k^i, i < 64, as four chains of 16
         // powers (starting from a^0, a^16, a^32, a^48)
         const int k = threadIdx.x - 32;
-        // epilogue: thread = lane r of its warp's tensor-memory quadrant q;
-        // lanes r and r + 16 hold the re and im rows of power j = 16 q + r % 16
-        const bool hi = lane >= 16;
-        const int jj = (warp & 3) * 16 + (lane & 15);
+        // epilogue: each warp reads its tensor-memory quadrant q (powers
+        // 16 q .. 16 q + 15) as two 16-lane halves
         const uint32_t lane_base = ((uint32_t)((warp & 3) * 32)) << 16;
         struct Ep {
             int t, b0, e, j;
@@ -911,41 +950,30 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             const int nb = min(a.cpb, a.n_chunks - b * a.cpb);
             const int nii = S * nb * LJ;                // columns of this batch
             const uint32_t tb = tmem + lane_base + 256 + 128 * ob;
-            // z of stream 0 and 1 at this batch's first sample and power jj
+            // z of stream 0 and 1 at this batch's first sample
             float2 *zb0 = a.z + (int64_t)a.stream0 * a.z_stream_stride + (int64_t)J.t * a.z_row_stride +
-                          (int64_t)b * a.cpb * L + jj;
+                          (int64_t)b * a.cpb * L;
             float2 *zb1 = zb0 + a.z_stream_stride;
-            // 64 columns per tensor-memory round trip; of the 8 chunk columns in
-            // 16 of them the re-row lane writes the first four, the im-row lane
-            // the last four, each taking the other row from its partner lane
-            for (int hh = 0; hh < 2 * kNii / 64; ++hh) {
-                uint32_t v[4][16];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) tmem_ld16_nw(tb + 64 * hh + 16 * i, v[i]);
+            // chunk column c = 4 cb + t % 4 = (chunk S + stream) LJ + j2
+            const int tm = lane & 3, qo = tm / LJ, j2 = tm % LJ;
+#pragma unroll 1
+            for (int hf = 0; hf < 2; ++hf) {
+                // lanes 16 hf .. 16 hf + 15 of the quadrant: thread t gets the
+                // re row of power jj (lane t / 4) and its im row (lane t / 4 + 8),
+                // columns 2 (t % 4) and 2 (t % 4) + 1 of every 8
+                const int jj = (warp & 3) * 16 + 8 * hf + (lane >> 2);
+                uint32_t v[64];
+                tmem_ld16x256_x16(tb + ((uint32_t)(16 * hf) << 16), v);
                 tmem_wait_ld();
 #pragma unroll
-                for (int i4 = 0; i4 < 4; ++i4) {
-                    const int h = 4 * hh + i4;
-                    float own[8], oth[8];               // own and partner row, this lane's columns
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const float lo_v = __uint_as_float(v[i4][i]), hi_v = __uint_as_float(v[i4][8 + i]);
-                        own[i] = hi ? hi_v : lo_v;
-                        oth[i] = __shfl_xor_sync(0xffffffffu, hi ? lo_v : hi_v, 16);
-                    }
-#pragma unroll
-                    for (int cc = 0; cc < 4; ++cc) {
-                        const float rr = hi ? oth[2 * cc] : own[2 * cc];           // D[re j][2c]
-                        const float ri = hi ? oth[2 * cc + 1] : own[2 * cc + 1];   // D[re j][2c + 1]
-                        const float ir = hi ? own[2 * cc] : oth[2 * cc];           // D[im j][2c]
-                        const float ii = hi ? own[2 * cc + 1] : oth[2 * cc + 1];   // D[im j][2c + 1]
-                        if (8 * h + (hi ? 4 : 0) + cc < nii) {
-                            // c = (chunk S + stream) LJ + j2; the im-row lane's
-                            // columns are 4 / LJ steps on
-                            const int q = (8 * h + cc) / LJ + (hi ? 4 / LJ : 0);
-                            float2 *zp = ((q % S) ? zb1 : zb0) + (q / S) * L + kJ * ((8 * h + cc) % LJ);
-                            *zp = make_float2(a.scale * (rr - ii), a.scale * (ri + ir));
-                        }
+                for (int cb = 0; cb < 16; ++cb) {
+                    const int c = 4 * cb + tm;
+                    if (c < nii) {
+                        const int q = (4 * cb) / LJ + qo;
+                        float2 *zp = ((q % S) ? zb1 : zb0) + (q / S) * L + kJ * j2 + jj;
+                        const float r0 = __uint_as_float(v[4 * cb]), r1 = __uint_as_float(v[4 * cb + 1]);
+                        const float r2 = __uint_as_float(v[4 * cb + 2]), r3 = __uint_as_float(v[4 * cb + 3]);
+                        *zp = make_float2(a.scale * (r0 - r3), a.scale * (r1 + r2));
                     }
                 }
             }
@@ -1037,10 +1065,10 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                 }
 #pragma unroll
                 for (int ch = 0; ch < 4; ++ch) {
-                    // powers 16 ch + 8 ib .. + 7: re in row group 4 ch + ib, im two groups on
-                    const size_t off = (size_t)(k >> 3) * 2048 + (4 * ch + ib) * 128 + (k & 7) * 16;
+                    // powers 16 ch + 8 ib .. + 7: re in row group 4 ch + 2 ib, im in the next
+                    const size_t off = (size_t)(k >> 3) * 2048 + (4 * ch + 2 * ib) * 128 + (k & 7) * 16;
                     *reinterpret_cast<uint4 *>(P + off) = pack8<BF16>(vr[ch]);
-                    *reinterpret_cast<uint4 *>(P + off + 2 * 128) = pack8<BF16>(vi[ch]);
+                    *reinterpret_cast<uint4 *>(P + off + 128) = pack8<BF16>(vi[ch]);
                 }
             }
             fence_async_smem();
@@ -1064,7 +1092,7 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             const int sl = J.s;
             const int64_t slot = (int64_t)J.tile * kTile + k;
             const float2 ak = a.a[slot], aJ = a.aJ[slot], ck = a.c[slot], aLf = a.aLf[slot];
-            const double2 aLb = a.aLb[slot];
+            const float4 aLb = a.aLb[slot];
             // per job: aJ^i2 for the state sums, a^(kJ j2) a c for the outputs
             float2 pj[LJ], cj[LJ];
             pj[0] = make_float2(1.f, 0.f);
@@ -1082,8 +1110,8 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                 cji[i] = make_float2(cj[2 * i].y, cj[2 * i + 1].y);
                 ncji[i] = make_float2(-cj[2 * i].y, -cj[2 * i + 1].y);
             }
-            double2 v0 = a.v[(int64_t)a.stream0 * a.n_slots + slot];
-            double2 v1 = S > 1 ? a.v[(int64_t)(a.stream0 + 1) * a.n_slots + slot] : make_double2(0, 0);
+            float4 v0 = a.v[(int64_t)a.stream0 * a.n_slots + slot];
+            float4 v1 = S > 1 ? a.v[(int64_t)(a.stream0 + 1) * a.n_slots + slot] : make_float4(0, 0, 0, 0);
             if (!mbar_wait_ab(&state_full[grp], n_state & 1, a.status, abort)) return false;
             ++n_state;
             tc_fence_after();
@@ -1093,16 +1121,16 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             const int b = J.b0;
             const int nb = min(a.cpb, a.n_chunks - b * a.cpb);
             const int nsteps = S * nb;                          // (stream, chunk) steps
-            // Carry across this batch. The batch's starting state v is FP64;
-            // chunk states inside the batch are FP32:
+            // Carry across this batch. The batch's starting state v is
+            // double-float; chunk states inside the batch are FP32:
             //   v_c = a^(cL) v + d_c,  d_{c+1} = a^L d_c + U_c,  d_0 = 0,
-            // and the next batch starts from a^(nb L) v + d_nb in FP64.
+            // and the next batch starts from a^(nb L) v + d_nb in double-float.
             // per stream: a^(cL) v and d_c; the streams' chains interleave
             float2 p[S], dd[S];
 #pragma unroll
             for (int i = 0; i < S; ++i) {
-                const double2 vi = i ? v1 : v0;
-                p[i] = make_float2((float)vi.x, (float)vi.y);
+                const float4 vi = i ? v1 : v0;
+                p[i] = make_float2(vi.x, vi.y);
                 dd[i] = make_float2(0.f, 0.f);
             }
             // STATE columns: (chunk, stream, i2) -> (c S + s) LJ + i2, read 32
@@ -1172,26 +1200,23 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                     }
                 }
             }
-            // W is complete: the OUTPUT contraction may start while the state
-            // update below runs on the (slow) FP64 pipe
+            // W is complete: the OUTPUT contraction may start during the
+            // state update below
             fence_async_smem();
             mbar_arrive(&w_full[sl]);
-            // v <- a^(nb L) v + d_nb in FP64, per stream
-            double2 pw;
+            // v <- a^(nb L) v + d_nb in double-float, per stream
+            float4 pw;
             if (nb == a.cpb) {
                 pw = aLb;
             } else {
-                const double2 aL = a.aL[slot];
+                const float4 aL = a.aL[slot];
                 pw = aL;
-                for (int i = 1; i < nb; ++i)
-                    pw = make_double2(pw.x * aL.x - pw.y * aL.y, pw.x * aL.y + pw.y * aL.x);
+                for (int i = 1; i < nb; ++i) pw = cdf_mul_add(pw, aL, make_float2(0.f, 0.f));
             }
-            v0 = make_double2(fma(pw.x, v0.x, fma(-pw.y, v0.y, (double)dd[0].x)),
-                              fma(pw.x, v0.y, fma(pw.y, v0.x, (double)dd[0].y)));
+            v0 = cdf_mul_add(pw, v0, dd[0]);
             a.v[(int64_t)a.stream0 * a.n_slots + slot] = v0;
             if constexpr (S > 1) {
-                v1 = make_double2(fma(pw.x, v1.x, fma(-pw.y, v1.y, (double)dd[1].x)),
-                                  fma(pw.x, v1.y, fma(pw.y, v1.x, (double)dd[1].y)));
+                v1 = cdf_mul_add(pw, v1, dd[1]);
                 a.v[(int64_t)(a.stream0 + 1) * a.n_slots + slot] = v1;
             }
             return true;
@@ -1223,7 +1248,7 @@ struct TcBank {
     int32_t *tile_ptr = nullptr, *tmpl_of = nullptr;
     uint8_t *has_carry = nullptr;
     float2 *a = nullptr, *aJ = nullptr, *c = nullptr, *aLf = nullptr;
-    double2 *aL = nullptr, *v = nullptr, *aLb1 = nullptr, *aLb2 = nullptr;
+    float4 *aL = nullptr, *v = nullptr, *aLb1 = nullptr, *aLb2 = nullptr;   // double-float
     float *xbuf = nullptr, *stage = nullptr;
     float2 *z = nullptr;
     unsigned int *status = nullptr;
@@ -1289,6 +1314,12 @@ int64_t tc_bytes(const spiir_bank_desc *d, const TcPlan &p) {
     b += S * C * hank_bytes_of(p.L, p.K);
     b += (C * S * (p.L / kJ) / kNii + 2) * kXsegBytes;
     return b + 256;
+}
+
+// Double-float split of a complex double: {re hi, im hi, re lo, im lo}.
+float4 host_df(std::complex<double> x) {
+    const float rh = (float)x.real(), ih = (float)x.imag();
+    return make_float4(rh, ih, (float)(x.real() - (double)rh), (float)(x.imag() - (double)ih));
 }
 
 uint16_t host16(float x, bool bf16) {
@@ -1394,7 +1425,7 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
     // Carry tiles: 128 filter slots each, template-major.
     std::vector<int32_t> tile_ptr(p.T + 1, 0), tmpl_of;
     std::vector<float2> av(p.n_slots), aJv(p.n_slots), cv(p.n_slots);
-    std::vector<double2> aLv(p.n_slots), aLb1v(p.n_slots), aLb2v(p.n_slots);
+    std::vector<float4> aLv(p.n_slots), aLb1v(p.n_slots), aLb2v(p.n_slots);
     std::vector<float2> aLfv(p.n_slots);
     const int cpb1 = carry_cpb(1, p.L), cpb2 = carry_cpb(2, p.L);
     int tile = 0;
@@ -1420,15 +1451,15 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
                 av[slot] = make_float2(d->a_re[k], d->a_im[k]);
                 const auto pJ = pw(kJ);
                 aJv[slot] = make_float2((float)pJ.real(), (float)pJ.imag());
-                aLv[slot] = make_double2(aL.real(), aL.imag());
+                aLv[slot] = host_df(aL);
                 aLfv[slot] = make_float2((float)aL.real(), (float)aL.imag());
                 const auto b1 = pw(p.L * cpb1), b2 = pw(p.L * cpb2);
-                aLb1v[slot] = make_double2(b1.real(), b1.imag());
-                aLb2v[slot] = make_double2(b2.real(), b2.imag());
+                aLb1v[slot] = host_df(b1);
+                aLb2v[slot] = host_df(b2);
                 cv[slot] = make_float2((float)ck.real(), (float)ck.imag());
             } else {
                 av[slot] = aJv[slot] = cv[slot] = aLfv[slot] = make_float2(0.f, 0.f);
-                aLv[slot] = aLb1v[slot] = aLb2v[slot] = make_double2(0.0, 0.0);
+                aLv[slot] = aLb1v[slot] = aLb2v[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
         tile += nt;
@@ -1452,8 +1483,8 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
     if ((st = tc_upload(&b->aLb1, aLb1v, s))) return st;
     if ((st = tc_upload(&b->aLb2, aLb2v, s))) return st;
     const int64_t S = d->n_streams;
-    TC_CUDA(cudaMalloc((void **)&b->v, std::max<int64_t>(1, S * p.n_slots) * sizeof(double2)));
-    TC_CUDA(cudaMemsetAsync(b->v, 0, std::max<int64_t>(1, S * p.n_slots) * sizeof(double2), s));
+    TC_CUDA(cudaMalloc((void **)&b->v, std::max<int64_t>(1, S * p.n_slots) * sizeof(float4)));
+    TC_CUDA(cudaMemsetAsync(b->v, 0, std::max<int64_t>(1, S * p.n_slots) * sizeof(float4), s));
     TC_CUDA(cudaMalloc((void **)&b->xbuf, S * p.xbuf_stride * sizeof(float)));
     TC_CUDA(cudaMemsetAsync(b->xbuf, 0, S * p.xbuf_stride * sizeof(float), s));
     TC_CUDA(cudaMalloc((void **)&b->stage, S * p.ring_len * sizeof(float)));
@@ -1647,7 +1678,7 @@ spiir_status spiir_tc_push(TcBank *b, int s0, int count, const float *x, int64_t
 
 spiir_status spiir_tc_reset(TcBank *b, int s0, int count, cudaStream_t s) {
     if (b->n_slots)
-        TC_CUDA(cudaMemsetAsync(b->v + (int64_t)s0 * b->n_slots, 0, count * b->n_slots * sizeof(double2), s));
+        TC_CUDA(cudaMemsetAsync(b->v + (int64_t)s0 * b->n_slots, 0, count * b->n_slots * sizeof(float4), s));
     TC_CUDA(cudaMemsetAsync(b->xbuf + (int64_t)s0 * b->xbuf_stride, 0, count * b->xbuf_stride * sizeof(float), s));
     for (int q = s0; q < s0 + count; ++q) b->last_n[q] = 0;
     return SPIIR_OK;
