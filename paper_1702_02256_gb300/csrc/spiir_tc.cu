@@ -286,6 +286,7 @@ struct TcCarryArgs {
     const float4 *aLb;        // [slot] a_k^(L * cpb), double-float, cpb of this launch
     const float2 *c;          // [slot] a_k^(F-d_k) b_k
     float4 *v;                // [stream][n_slots] undelayed unit-filter state, double-float
+    const uint4 *panel;       // [tile] power panels (layout below), precomputed
     int64_t n_slots;
     const uint4 *xseg;        // staged STATE strain segments
     int32_t L, n_chunks, n_streams, stream0, cpb, n_batches;
@@ -774,7 +775,7 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < kSlots; ++i) {
-            mbar_init(&panel_full[i], 128);
+            mbar_init(&panel_full[i], 1);
             mbar_init(&panel_free[i], 1);
             mbar_init(&w_full[i], 128);
             mbar_init(&w_free[i], 1);
@@ -931,9 +932,10 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
         }
     } else if (warp <= 4) {
         // ---------------- power panels and epilogue ----------------
-        // panel: thread = filter k: a_k^i, i < 64, as four chains of 16
-        // powers (starting from a^0, a^16, a^32, a^48)
-        const int k = threadIdx.x - 32;
+        // panel: the tile's precomputed panel, one bulk copy into the slot
+        // (issued by the role's first thread; last_copy = its latest job)
+        const bool leader = threadIdx.x == 32;
+        int last_copy = -1;
         // epilogue: each warp reads its tensor-memory quadrant q (powers
         // 16 q .. 16 q + 15) as two 16-lane halves
         const uint32_t lane_base = ((uint32_t)((warp & 3) * 32)) << 16;
@@ -984,8 +986,6 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
         bool ok = true;
         carry_jobs(a, [&](const CarryJob &J) -> bool {
             const int sl = J.s;
-            const int64_t slot = (int64_t)J.tile * kTile + k;
-            const float2 ak = a.a[slot];
             // Epilogues five or more jobs back are taken first: the OUTPUT
             // that frees this job's slot may need their accumulator (first
             // tile of the (template, batch) two after them).
@@ -1033,46 +1033,12 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                     if (!(ok = panel_role_all(*abort == 0))) return false;
                 }
             }
-            unsigned char *P = smem + sl * kPanelBytes;
-            float2 a16 = ak;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a16 = cmul(a16, a16);
-            float2 p[4];
-            p[0] = make_float2(1.f, 0.f);
-#pragma unroll
-            for (int i = 1; i < 4; ++i) p[i] = cmul(p[i - 1], a16);
-            // chains (0, 1) and (2, 3) advance together in packed f32x2:
-            // re' = re ak.x - im ak.y, im' = re ak.y + im ak.x
-            float2 pr[2] = {make_float2(p[0].x, p[1].x), make_float2(p[2].x, p[3].x)};
-            float2 pi[2] = {make_float2(p[0].y, p[1].y), make_float2(p[2].y, p[3].y)};
-            const float2 akr = make_float2(ak.x, ak.x), aki = make_float2(ak.y, ak.y);
-            const float2 naki = make_float2(-ak.y, -ak.y);
-#pragma unroll
-            for (int ib = 0; ib < 2; ++ib) {
-                float vr[4][8], vi[4][8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-#pragma unroll
-                    for (int h2 = 0; h2 < 2; ++h2) {
-                        vr[2 * h2][q] = pr[h2].x;
-                        vr[2 * h2 + 1][q] = pr[h2].y;
-                        vi[2 * h2][q] = pi[h2].x;
-                        vi[2 * h2 + 1][q] = pi[h2].y;
-                        const float2 nr = __ffma2_rn(pi[h2], naki, __fmul2_rn(pr[h2], akr));
-                        pi[h2] = __ffma2_rn(pi[h2], akr, __fmul2_rn(pr[h2], aki));
-                        pr[h2] = nr;
-                    }
-                }
-#pragma unroll
-                for (int ch = 0; ch < 4; ++ch) {
-                    // powers 16 ch + 8 ib .. + 7: re in row group 4 ch + 2 ib, im in the next
-                    const size_t off = (size_t)(k >> 3) * 2048 + (4 * ch + 2 * ib) * 128 + (k & 7) * 16;
-                    *reinterpret_cast<uint4 *>(P + off) = pack8<BF16>(vr[ch]);
-                    *reinterpret_cast<uint4 *>(P + off + 128) = pack8<BF16>(vi[ch]);
-                }
+            if (leader) {
+                mbar_expect(&panel_full[sl], kPanelBytes);
+                bulk_load(smem + sl * kPanelBytes, a.panel + (size_t)J.tile * (kPanelBytes / 16), kPanelBytes,
+                          &panel_full[sl]);
+                last_copy = J.j;
             }
-            fence_async_smem();
-            mbar_arrive(&panel_full[sl]);
             return true;
         });
         if (ok && ep_n > 0) ok = epilogue(ep0);
@@ -1080,6 +1046,11 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
         if (ok && ep_n > 2) ok = epilogue(ep2);
         if (ok && ep_n > 3) ok = epilogue(ep3);
         if (ok && ep_n > 4) ok = epilogue(ep4);
+        // no copy may still be writing shared memory when the CTA exits (the
+        // STATE issuer has waited for every panel unless it gave up)
+        if (leader)
+            for (int j = max(0, last_copy - kSlots + 1); j <= last_copy; ++j)
+                mbar_wait(&panel_full[j % kSlots], (uint32_t)(j / kSlots) & 1u, a.status);
     } else if (warp <= 12) {
         // ---------------- carry groups ----------------
         const int grp = (warp - 5) >> 2;
@@ -1253,6 +1224,7 @@ struct TcBank {
     float2 *z = nullptr;
     unsigned int *status = nullptr;
     uint4 *hank = nullptr, *xseg = nullptr;   // staged strain operands
+    uint4 *panel = nullptr;                   // carry tiles' power panels
     int hank_bytes = 0;
     int n_sms = 1;
     std::vector<int64_t> last_n;
@@ -1307,6 +1279,7 @@ int64_t tc_bytes(const spiir_bank_desc *d, const TcPlan &p) {
     b += (int64_t)p.n_groups * p.n_slices * kSliceBytes;
     b += (int64_t)p.T * 4 + (p.T + 1) * 4 + p.T * 4;
     b += p.n_slots * (8 * 4 + 16 * 3);
+    b += (int64_t)p.n_tiles * kPanelBytes;
     b += S * p.n_slots * 16;
     b += S * p.xbuf_stride * 4 + S * p.ring_len * 4;
     b += S * (int64_t)p.T * p.ring_len * 8;
@@ -1427,6 +1400,7 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
     std::vector<float2> av(p.n_slots), aJv(p.n_slots), cv(p.n_slots);
     std::vector<float4> aLv(p.n_slots), aLb1v(p.n_slots), aLb2v(p.n_slots);
     std::vector<float2> aLfv(p.n_slots);
+    std::vector<int64_t> slot_k(p.n_slots, -1);   // filter of each carry slot (-1: padding)
     const int cpb1 = carry_cpb(1, p.L), cpb2 = carry_cpb(2, p.L);
     int tile = 0;
     for (int t = 0; t < p.T; ++t) {
@@ -1437,6 +1411,7 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
             const int64_t slot = (int64_t)tile * kTile + i;
             if (i < (int)fl[t].size()) {
                 const int64_t k = fl[t][i];
+                slot_k[slot] = k;
                 const std::complex<double> a(d->a_re[k], d->a_im[k]), bb(d->b_re[k], d->b_im[k]);
                 auto pw = [&](int n) {
                     std::complex<double> r(1, 0), x = a;
@@ -1466,6 +1441,33 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
     }
     tile_ptr[p.T] = tile;
     b->n_carry_ctas = (int)tmpl_of.size();
+    // Power panel of each tile (the layout the carry kernel copies into a
+    // slot): a_k^j, j < kJ, in FP64 and rounded once to the operand type.
+    std::vector<uint16_t> panel((size_t)tile * (kPanelBytes / 2));
+    {
+        auto pwork = [&](int64_t t0, int64_t t1) {
+            for (int64_t tl = t0; tl < t1; ++tl)
+                for (int kk = 0; kk < kTile; ++kk) {
+                    const int64_t k = slot_k[tl * kTile + kk];
+                    const std::complex<double> a =
+                        k >= 0 ? std::complex<double>(d->a_re[k], d->a_im[k]) : std::complex<double>(0, 0);
+                    std::complex<double> x(1, 0);
+                    // [k/8][m/8][k%8][m%8]: row group 2 (j/8) = Re, 2 (j/8) + 1 = Im
+                    uint16_t *P = panel.data() + (size_t)tl * (kPanelBytes / 2) + (kk >> 3) * 1024 + (kk & 7) * 8;
+                    for (int j = 0; j < kJ; ++j) {
+                        const int g = 2 * (j >> 3);
+                        P[g * 64 + (j & 7)] = host16((float)x.real(), b->bf16);
+                        P[(g + 1) * 64 + (j & 7)] = host16((float)x.imag(), b->bf16);
+                        x *= a;
+                    }
+                }
+        };
+        const int nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        std::vector<std::thread> th;
+        for (int i = 0; i < nth; ++i)
+            th.emplace_back(pwork, (int64_t)tile * i / nth, (int64_t)tile * (i + 1) / nth);
+        for (auto &x : th) x.join();
+    }
     std::vector<uint8_t> has_carry(p.T, 0);
     for (int t : tmpl_of) has_carry[t] = 1;
 
@@ -1482,6 +1484,9 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
     if ((st = tc_upload(&b->aLf, aLfv, s))) return st;
     if ((st = tc_upload(&b->aLb1, aLb1v, s))) return st;
     if ((st = tc_upload(&b->aLb2, aLb2v, s))) return st;
+    if ((st = tc_upload(&b->panel, std::vector<uint4>((uint4 *)panel.data(), (uint4 *)(panel.data() + panel.size())),
+                        s)))
+        return st;
     const int64_t S = d->n_streams;
     TC_CUDA(cudaMalloc((void **)&b->v, std::max<int64_t>(1, S * p.n_slots) * sizeof(float4)));
     TC_CUDA(cudaMemsetAsync(b->v, 0, std::max<int64_t>(1, S * p.n_slots) * sizeof(float4), s));
@@ -1618,6 +1623,7 @@ spiir_status spiir_tc_push(TcBank *b, int s0, int count, const float *x, int64_t
         ca.z_row_stride = b->ring_len;
         ca.z_stream_stride = (int64_t)b->T * b->ring_len;
         ca.status = b->status;
+        ca.panel = b->panel;
         const int grid = std::min(b->n_carry_ctas, b->n_sms);
         const int thr = kCarryWarps * 32;
         timer->begin(SPIIR_K_TC_CARRY, s);
@@ -1719,7 +1725,7 @@ void spiir_tc_destroy(TcBank *b) {
     if (!b) return;
     void *ptrs[] = {b->H, b->row_scale, b->tile_ptr, b->tmpl_of, b->has_carry, b->a, b->aJ, b->c,
                     b->aL, b->v, b->xbuf, b->stage, b->z, b->status, b->hank, b->xseg,
-                    b->aLf, b->aLb1, b->aLb2};
+                    b->aLf, b->aLb1, b->aLb2, b->panel};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     delete b;
