@@ -539,15 +539,16 @@ __global__ void __launch_bounds__(kFirThreads, 1) tc_fir_kernel(const TcFirArgs 
 
 // ---------------------------------------------------------------------------
 // Carry kernel: one CTA per SM, persistent over templates. A CTA's work is a
-// sequence of jobs (template, chunk batch, 128-filter tile) on three pipeline
-// slots (power panel and OUTPUT operand in shared memory) and two carry
+// sequence of jobs (template, chunk batch, 128-filter tile) on four power
+// panel slots and two OUTPUT-operand (W) slots in shared memory and two carry
 // groups, spread over warp roles:
 //   warp 0, lane 0   issues the STATE contractions in job order as soon as
 //                    each one's inputs are ready, and the strain-segment copies
 //   warp 13, lane 0  issues the OUTPUT contractions in job order (a separate
 //                    warp, on another scheduler: a single issuer sharing a
 //                    scheduler with the arithmetic warps was slow to react)
-//   warps 1-4        power panel of each job into its slot, and the epilogue
+//   warps 1-4        bulk copy of each job's precomputed power panel into
+//                    its slot (a panel copy runs up to four jobs ahead), and the epilogue
 //                    of each (template, batch): OUTPUT accumulators -> z,
 //                    taken while the next panel's slot is still in use (or
 //                    at the latest five jobs after its last tile)
@@ -573,10 +574,11 @@ __global__ void __launch_bounds__(kFirThreads, 1) tc_fir_kernel(const TcFirArgs 
 // ---------------------------------------------------------------------------
 
 constexpr int kCarryWarps = 14;
-constexpr int kSlots = 3;
+constexpr int kPanelSlots = 4;     // power panels in flight
+constexpr int kWSlots = 2;         // OUTPUT operands W in flight
 constexpr int kPanelBytes = kTile * 2 * kJ * 2;                 // 32 KB
 constexpr int kWBytes = kTile * 2 * kNii * 2;                   // 32 KB
-constexpr int kCarrySmem = kSlots * (kPanelBytes + kWBytes) + 2 * kXsegBytes;   // 208 KB
+constexpr int kCarrySmem = kPanelSlots * kPanelBytes + kWSlots * kWBytes + 2 * kXsegBytes;   // 208 KB
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *m) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s32(m)) : "memory");
@@ -664,10 +666,10 @@ struct CarryJob {
     int t, b0, tile;
     bool first_tile, last_tile;
     int j, e;   // job index and (template, batch) index within this CTA
-    int s, g;   // pipeline slot (panel, W) and carry group (STATE columns)
+    int s, w, g;   // panel slot, W slot and carry group (STATE columns)
 };
 
-// The job sequence of this CTA: jobs cycle through the three slots and
+// The job sequence of this CTA: jobs cycle through the panel and W slots and
 // alternate between the two carry groups. When a template has several
 // batches, the filter state v of a tile passes from one batch to the next,
 // so a tile keeps its carry group for all of them. Every listed template
@@ -692,7 +694,7 @@ struct CarryJobs {
     }
     __device__ CarryJob cur() const {
         const int g = multi ? ((tile - tile0) & 1) : (j & 1);
-        return CarryJob{t, b0, tile, tile == tile0, tile == tile1 - 1, j, e, j % kSlots, g};
+        return CarryJob{t, b0, tile, tile == tile0, tile == tile1 - 1, j, e, j % kPanelSlots, j % kWSlots, g};
     }
     __device__ void next() {
         ++j;
@@ -758,13 +760,13 @@ __device__ __forceinline__ float4 cdf_mul_add(float4 x, float4 y, float2 d) {
 template <bool BF16, int LJ, int S>
 __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcCarryArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t panel_full[kSlots], panel_free[kSlots], w_full[kSlots], w_free[kSlots],
+    __shared__ uint64_t panel_full[kPanelSlots], panel_free[kPanelSlots], w_full[kWSlots], w_free[kWSlots],
         state_full[2], state_free[2], out_full[2], out_free[2], xs_full[2], drain, drain_o;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
-    // slot s: panel at s * kPanelBytes, W at kSlots * kPanelBytes + s * kWBytes
-    unsigned char *Wb = smem + kSlots * kPanelBytes;
-    unsigned char *Xs = Wb + kSlots * kWBytes;                     // strain segments of batches b % 2
+    // panel slot s at s * kPanelBytes, W slot w at kPanelSlots * kPanelBytes + w * kWBytes
+    unsigned char *Wb = smem + kPanelSlots * kPanelBytes;
+    unsigned char *Xs = Wb + kWSlots * kWBytes;                    // strain segments of batches b % 2
     // OUTPUT operand W, MN-major [k/8][n/8][k%8][n%8] (n = column, k = filter):
     // 8-column groups 128 bytes apart, 8-filter groups kWK apart; column 2c =
     // Re w(c), 2c + 1 = Im w(c) of chunk column c = (stream, chunk, j2)
@@ -774,9 +776,11 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
     volatile int *abort = &s_abort;     // S (1 or 2) = a.n_streams
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kSlots; ++i) {
+        for (int i = 0; i < kPanelSlots; ++i) {
             mbar_init(&panel_full[i], 1);
             mbar_init(&panel_free[i], 1);
+        }
+        for (int i = 0; i < kWSlots; ++i) {
             mbar_init(&w_full[i], 128);
             mbar_init(&w_free[i], 1);
         }
@@ -805,7 +809,7 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             // STATE of each job in job order, as soon as its strain segment,
             // its carry group's STATE columns and its panel are ready; the
             // strain-segment copies. Phase parities and use flags are bits
-            // of ph; slot phases follow from the job index (use j / kSlots).
+            // of ph; slot phases follow from the job index (use j / kPanelSlots).
             constexpr uint32_t kSF = 0, kUsed = 2;
             uint32_t ph = 0, ph_d = 0;
             // strain-segment buffers (batch b in buffer b % 2): batch held or
@@ -813,8 +817,9 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             // and the phase of the next load's completion
             int held0 = -1, held1 = -1, last0 = -1000, last1 = -1000;
             uint32_t loading = 0, xs_ph = 0;
-            int last_pf = -1;   // latest job whose panel was ready: every STATE
-                                // up to three jobs before it has finished
+            int last_pf = -1;   // latest job whose panel was ready: every STATE up
+                                // to kPanelSlots jobs before it has finished (its
+                                // slot was freed by that job's OUTPUT)
             auto start_load = [&](int x, int batch) {
                 mbar_expect(&xs_full[x], kXsegBytes);
                 bulk_load(Xs + x * kXsegBytes, a.xseg + (size_t)batch * (kXsegBytes / 16), kXsegBytes,
@@ -832,9 +837,9 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                 const int xb = J.b0 & 1;
                 if ((xb ? held1 : held0) != J.b0 && !((loading >> xb) & 1u)) {
                     // the buffer's readers must be done before it is refilled:
-                    // certain three jobs on, else drain the tensor pipe (rare:
-                    // one-tile templates with several batches)
-                    if (issued && (xb ? last1 : last0) > last_pf - 3) {
+                    // certain kPanelSlots jobs on, else drain the tensor pipe
+                    // (rare: templates of one or two tiles with several batches)
+                    if (issued && (xb ? last1 : last0) > last_pf - kPanelSlots) {
                         mma_commit(&drain);
                         ok = mbar_wait_ab(&drain, ph_d, a.status, abort);
                         ph_d ^= 1u;
@@ -852,7 +857,8 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                     ph ^= 1u << (kSF + g);
                 }
                 ph |= 1u << (kUsed + g);
-                if (!(ok = mbar_wait_ab(&panel_full[sl], (uint32_t)(J.j / kSlots) & 1u, a.status, abort))) break;
+                if (!(ok = mbar_wait_ab(&panel_full[sl], (uint32_t)(J.j / kPanelSlots) & 1u, a.status, abort)))
+                    break;
                 last_pf = J.j;
                 if (xb) last1 = J.j;
                 else last0 = J.j;
@@ -877,7 +883,7 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                 // once that buffer's readers are certainly done
                 const int nb2 = J.b0 + 1, x2 = nb2 & 1;
                 if (nb2 < a.n_batches && (x2 ? held1 : held0) != nb2 && !((loading >> x2) & 1u) &&
-                    (x2 ? last1 : last0) <= last_pf - 3)
+                    (x2 ? last1 : last0) <= last_pf - kPanelSlots)
                     start_load(x2, nb2);
             }
             // nothing may still run when the tensor memory is released, and no
@@ -902,16 +908,16 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             const uint32_t smem0 = s32(smem), wb0 = s32(Wb);
             for (CarryJobs ot(a); ot.valid; ot.next()) {
                 const CarryJob J = ot.cur();
-                const uint32_t sl = (uint32_t)J.s, ob = (uint32_t)(J.e & 1);
+                const uint32_t sl = (uint32_t)J.s, wl = (uint32_t)J.w, ob = (uint32_t)(J.e & 1);
                 if (J.first_tile && J.e >= 2) {
                     if (!mbar_wait_ab(&out_free[ob], (of_ph >> ob) & 1u, a.status, abort)) break;
                     of_ph ^= 1u << ob;
                 }
-                if (!mbar_wait_ab(&w_full[sl], (uint32_t)(J.j / kSlots) & 1u, a.status, abort)) break;
+                if (!mbar_wait_ab(&w_full[wl], (uint32_t)(J.j / kWSlots) & 1u, a.status, abort)) break;
                 tc_fence_after();
                 // D = R^T W over the tile's filters
                 const uint64_t a0 = sdesc(smem0 + sl * kPanelBytes, 2048, 128);
-                const uint64_t b0 = sdesc(wb0 + sl * kWBytes, kWK, 128);
+                const uint64_t b0 = sdesc(wb0 + wl * kWBytes, kWK, 128);
                 const uint32_t dz = tmem + 256 + 128 * ob;
                 const uint32_t acc0 = J.first_tile ? 0u : 1u;
 #pragma unroll
@@ -920,7 +926,7 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                     const uint64_t ow = (uint64_t)(kk * 2 * kWK) >> 4;
                     mma(dz, a0 + oa, b0 + ow, id_out, kk ? 1u : acc0);
                 }
-                mma_commit(&w_free[sl]);
+                mma_commit(&w_free[wl]);
                 mma_commit(&panel_free[sl]);
                 if (J.last_tile) mma_commit(&out_full[ob]);
                 issued = true;
@@ -1012,7 +1018,7 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             // While this job's slot is still in use, take the epilogues whose
             // contractions have finished (bounded like every other wait; the
             // slot test suspends the threads for up to 1 us at a time).
-            const int use = J.j / kSlots;
+            const int use = J.j / kPanelSlots;
             if (use > 0) {
                 uint64_t t0 = 0;
                 while (!panel_role_all(mbar_try_ns(&panel_free[sl], (use - 1) & 1, 1000u))) {
@@ -1049,8 +1055,8 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
         // no copy may still be writing shared memory when the CTA exits (the
         // STATE issuer has waited for every panel unless it gave up)
         if (leader)
-            for (int j = max(0, last_copy - kSlots + 1); j <= last_copy; ++j)
-                mbar_wait(&panel_full[j % kSlots], (uint32_t)(j / kSlots) & 1u, a.status);
+            for (int j = max(0, last_copy - kPanelSlots + 1); j <= last_copy; ++j)
+                mbar_wait(&panel_full[j % kPanelSlots], (uint32_t)(j / kPanelSlots) & 1u, a.status);
     } else if (warp <= 12) {
         // ---------------- carry groups ----------------
         const int grp = (warp - 5) >> 2;
@@ -1060,7 +1066,7 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
         uint32_t n_state = 0;
         carry_jobs(a, [&](const CarryJob &J) -> bool {
             if (J.g != grp) return true;
-            const int sl = J.s;
+            const int wl = J.w;
             const int64_t slot = (int64_t)J.tile * kTile + k;
             const float2 ak = a.a[slot], aJ = a.aJ[slot], ck = a.c[slot], aLf = a.aLf[slot];
             const float4 aLb = a.aLb[slot];
@@ -1086,9 +1092,9 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             if (!mbar_wait_ab(&state_full[grp], n_state & 1, a.status, abort)) return false;
             ++n_state;
             tc_fence_after();
-            const int use = J.j / kSlots;
-            if (use > 0 && !mbar_wait_ab(&w_free[sl], (use - 1) & 1, a.status, abort)) return false;
-            unsigned char *W = Wb + sl * kWBytes;
+            const int use = J.j / kWSlots;
+            if (use > 0 && !mbar_wait_ab(&w_free[wl], (use - 1) & 1, a.status, abort)) return false;
+            unsigned char *W = Wb + wl * kWBytes;
             const int b = J.b0;
             const int nb = min(a.cpb, a.n_chunks - b * a.cpb);
             const int nsteps = S * nb;                          // (stream, chunk) steps
@@ -1174,7 +1180,7 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             // W is complete: the OUTPUT contraction may start during the
             // state update below
             fence_async_smem();
-            mbar_arrive(&w_full[sl]);
+            mbar_arrive(&w_full[wl]);
             // v <- a^(nb L) v + d_nb in double-float, per stream
             float4 pw;
             if (nb == a.cpb) {
