@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -124,10 +125,14 @@ def _peaks():
 
 def _source_hash(kernel_file: str) -> str:
     """First 16 hex digits of the sha256 of the kernel file followed by the
-    planner (spiir_api.cu): the traffic depends on both."""
+    planner (spiir_api.cu), comments and blank lines left out: the traffic
+    depends on the code of both, not on their comments."""
     h = hashlib.sha256()
     for f in (kernel_file, "spiir_api.cu"):
-        h.update(open(os.path.join(ROOT, "paper_1702_02256_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_1702_02256_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update("\n".join(ln.rstrip() for ln in src.splitlines() if ln.strip()).encode())
     return h.hexdigest()[:16]
 
 
@@ -298,7 +303,7 @@ def _measure(w, form, args, dev, dist, sampler, rank, ws):
     S = w["n_streams"]
     n = w["x"].shape[1]
     push_len = w["block_len"] * w["push_blocks"]
-    kw = dict(tune=args.tune) if form == "plain" else dict(mode=form, chunk_len=w["chunk_len"])
+    kw = dict(tune=args.tune) if form == "plain" else dict(mode=form, chunk_len=w["chunk_len"], carry=args.carry)
     if w.get("h_down") is not None:
         kw.update(h_down=w["h_down"], h_up=w["h_up"])
     b = spiir.Bank(bank, n_streams=S, block_len=w["block_len"], max_push_blocks=w["push_blocks"], **kw)
@@ -376,6 +381,12 @@ def _measure(w, form, args, dev, dist, sampler, rank, ws):
                 p50=float(np.percentile(lat, 50)), p99=float(np.percentile(lat, 99)),
                 e2e=ws * fs_per_step / e2e_s, h2d=int(S * n * 4),
                 d2h=int(S * bank.n_templates * n * 8), wall=(t_wall0, t_wall1))
+
+
+def _form_desc(form: str, args) -> str:
+    if form == "plain":
+        return "plain FP32 recursion"
+    return f"tensor-core block form ({form}, {args.carry} carry between chunk batches)"
 
 
 def _roofline(m, w, args, peaks, sms):
@@ -474,7 +485,7 @@ def run_ours(args):
             "n_filters": bank.n_filters,
             "n_streams": w["n_streams"],
             "samples_per_step": int(w["x"].shape[1]),
-            "form": "plain FP32 recursion" if form == "plain" else f"tensor-core block form ({form})",
+            "form": _form_desc(form, args),
             "kernel_variant": main["info"]["kernel_variant"],
             "variant_choice": {1: "autotuned at bank creation", 0: "default"}.get(
                 args.tune, f"forced {-args.tune - 1}") if form == "plain" else "n/a",
@@ -499,7 +510,7 @@ def run_ours(args):
     }
     if chosen:
         line["chosen"] = {
-            "form": f"tensor-core block form ({chosen['form']})",
+            "form": _form_desc(chosen["form"], args),
             "value": chosen["value"], "unit": UNIT, "ms_per_step": chosen["ms_per_step"],
             "real_time_templates": chosen["rtt"],
             "p50_block_latency_ms": chosen["p50"], "p99_block_latency_ms": chosen["p99"],
@@ -614,6 +625,9 @@ def main():
     ap.add_argument("--resampler", default="default", choices=["default", "paper"],
                     help="multi-rate: 32/32-tap 60 dB pair (default) or the paper's "
                          "384-tap 100 dB decimator with the 32-tap interpolator")
+    ap.add_argument("--carry", default="fp64", choices=["fp64", "df"],
+                    help="tensor-core forms: inter-batch state arithmetic, FP64 (default) or "
+                         "double-float pairs on the FP32 pipe")
     ap.add_argument("--tune", type=int, default=None,
                     help="plain-form kernel variant: 1 = autotune at bank creation, 0 = default, "
                          "-(v+1) = variant v (default: autotune for multirate, else 0)")

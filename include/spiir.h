@@ -56,7 +56,8 @@ typedef enum {
  * The TC_* forms are the block-parallel tensor-core form for single-rate
  * banks: over chunks of chunk_len samples the bank is a dense contraction of
  * the template impulse responses with a Toeplitz view of x, plus per-filter
- * power panels a_k^j applied to filter states carried between chunks in FP64.
+ * power panels a_k^j applied to filter states carried between chunks in FP64
+ * (or double-float, desc->carry).
  * TC_FP16 / TC_BF16 round the panel and strain operands to that type (FP32
  * accumulation). TC_BF16X2 (each operand split into a bf16 high and low part)
  * is reserved: this build returns SPIIR_EUNSUPPORTED for it. */
@@ -100,6 +101,13 @@ typedef struct {
     int32_t n_taps_up;            /* interpolator length: even, 2..64; 0 =
                                      n_taps (Sec. 2.2 pairs a long 100 dB
                                      decimator with a 32-tap interpolator) */
+    int32_t carry;                /* TC forms: arithmetic of the filter state
+                                     carried between chunk batches and of the
+                                     powers a_k^L: 0 = FP64 (default), 1 =
+                                     double-float pairs on the FP32 pipe
+                                     (about 48 significant bits; faster on
+                                     parts with a low FP64 rate). Ignored by
+                                     PLAIN_FP32; other values: EINVAL */
 } spiir_bank_desc;
 
 /* Read-only facts about a created bank. */

@@ -40,6 +40,7 @@
 #include <cstring>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "spiir_internal.h"
@@ -281,11 +282,11 @@ struct TcCarryArgs {
     int32_t n_carry;
     const float2 *a;          // [slot] a_k
     const float2 *aJ;         // [slot] a_k^kJ
-    const float4 *aL;         // [slot] a_k^L, double-float {re hi, im hi, re lo, im lo}
+    const uint4 *aL;          // [slot] a_k^L: FP64 double2 or double-float float4 (carry mode)
     const float2 *aLf;        // [slot] a_k^L rounded to FP32
-    const float4 *aLb;        // [slot] a_k^(L * cpb), double-float, cpb of this launch
+    const uint4 *aLb;         // [slot] a_k^(L * cpb), same type, cpb of this launch
     const float2 *c;          // [slot] a_k^(F-d_k) b_k
-    float4 *v;                // [stream][n_slots] undelayed unit-filter state, double-float
+    uint4 *v;                 // [stream][n_slots] undelayed unit-filter state, same type
     const uint4 *panel;       // [tile] power panels (layout below), precomputed
     int64_t n_slots;
     const uint4 *xseg;        // staged STATE strain segments
@@ -553,7 +554,7 @@ __global__ void __launch_bounds__(kFirThreads, 1) tc_fir_kernel(const TcFirArgs 
 //                    taken while the next panel's slot is still in use (or
 //                    at the latest five jobs after its last tile)
 //   warps 5-8, 9-12  carry groups 0 and 1: STATE (tensor memory) -> FP32
-//                    carry inside a batch, double-float from batch to batch
+//                    carry inside a batch, FP64 (or double-float) from batch to batch
 //                    -> OUTPUT operand W of the job's slot
 // Panel of a 128-filter tile: 128 rows m of powers, layout
 // [k/8][m/8][k%8][m%8], in row groups of 8: group 2 p holds Re a_k^j and
@@ -757,8 +758,18 @@ __device__ __forceinline__ float4 cdf_mul_add(float4 x, float4 y, float2 d) {
     return make_float4(re.x, im.x, re.y, im.y);
 }
 
-template <bool BF16, int LJ, int S>
+// The inter-batch anchor in either carry arithmetic: FP64 complex (double2)
+// or double-float (float4). Its FP32 value, x y + d, and x y.
+__device__ __forceinline__ float2 anchor_f32(const double2 &v) { return make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ float2 anchor_f32(const float4 &v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ double2 anchor_madd(double2 x, double2 y, float2 d) {
+    return make_double2(fma(x.x, y.x, fma(-x.y, y.y, (double)d.x)), fma(x.x, y.y, fma(x.y, y.x, (double)d.y)));
+}
+__device__ __forceinline__ float4 anchor_madd(float4 x, float4 y, float2 d) { return cdf_mul_add(x, y, d); }
+
+template <bool BF16, int LJ, int S, bool DF>
 __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcCarryArgs a) {
+    using Anchor = typename std::conditional<DF, float4, double2>::type;   // carry arithmetic
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t panel_full[kPanelSlots], panel_free[kPanelSlots], w_full[kWSlots], w_free[kWSlots],
         state_full[2], state_free[2], out_full[2], out_free[2], xs_full[2], drain, drain_o;
@@ -1069,7 +1080,8 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             const int wl = J.w;
             const int64_t slot = (int64_t)J.tile * kTile + k;
             const float2 ak = a.a[slot], aJ = a.aJ[slot], ck = a.c[slot], aLf = a.aLf[slot];
-            const float4 aLb = a.aLb[slot];
+            const Anchor aLb = reinterpret_cast<const Anchor *>(a.aLb)[slot];
+            Anchor *vs = reinterpret_cast<Anchor *>(a.v);
             // per job: aJ^i2 for the state sums, a^(kJ j2) a c for the outputs
             float2 pj[LJ], cj[LJ];
             pj[0] = make_float2(1.f, 0.f);
@@ -1087,8 +1099,8 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                 cji[i] = make_float2(cj[2 * i].y, cj[2 * i + 1].y);
                 ncji[i] = make_float2(-cj[2 * i].y, -cj[2 * i + 1].y);
             }
-            float4 v0 = a.v[(int64_t)a.stream0 * a.n_slots + slot];
-            float4 v1 = S > 1 ? a.v[(int64_t)(a.stream0 + 1) * a.n_slots + slot] : make_float4(0, 0, 0, 0);
+            Anchor v0 = vs[(int64_t)a.stream0 * a.n_slots + slot];
+            Anchor v1 = S > 1 ? vs[(int64_t)(a.stream0 + 1) * a.n_slots + slot] : Anchor{};
             if (!mbar_wait_ab(&state_full[grp], n_state & 1, a.status, abort)) return false;
             ++n_state;
             tc_fence_after();
@@ -1098,16 +1110,17 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             const int b = J.b0;
             const int nb = min(a.cpb, a.n_chunks - b * a.cpb);
             const int nsteps = S * nb;                          // (stream, chunk) steps
-            // Carry across this batch. The batch's starting state v is
-            // double-float; chunk states inside the batch are FP32:
+            // Carry across this batch. The batch's starting state v is an
+            // FP64 (or double-float) anchor; chunk states inside the batch are
+            // FP32 offsets from it:
             //   v_c = a^(cL) v + d_c,  d_{c+1} = a^L d_c + U_c,  d_0 = 0,
-            // and the next batch starts from a^(nb L) v + d_nb in double-float.
+            // and the next batch starts from a^(nb L) v + d_nb in the anchor's
+            // arithmetic.
             // per stream: a^(cL) v and d_c; the streams' chains interleave
             float2 p[S], dd[S];
 #pragma unroll
             for (int i = 0; i < S; ++i) {
-                const float4 vi = i ? v1 : v0;
-                p[i] = make_float2(vi.x, vi.y);
+                p[i] = anchor_f32(i ? v1 : v0);
                 dd[i] = make_float2(0.f, 0.f);
             }
             // STATE columns: (chunk, stream, i2) -> (c S + s) LJ + i2, read 32
@@ -1181,20 +1194,20 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             // state update below
             fence_async_smem();
             mbar_arrive(&w_full[wl]);
-            // v <- a^(nb L) v + d_nb in double-float, per stream
-            float4 pw;
+            // v <- a^(nb L) v + d_nb in the anchor's arithmetic, per stream
+            Anchor pw;
             if (nb == a.cpb) {
                 pw = aLb;
             } else {
-                const float4 aL = a.aL[slot];
+                const Anchor aL = reinterpret_cast<const Anchor *>(a.aL)[slot];
                 pw = aL;
-                for (int i = 1; i < nb; ++i) pw = cdf_mul_add(pw, aL, make_float2(0.f, 0.f));
+                for (int i = 1; i < nb; ++i) pw = anchor_madd(pw, aL, make_float2(0.f, 0.f));
             }
-            v0 = cdf_mul_add(pw, v0, dd[0]);
-            a.v[(int64_t)a.stream0 * a.n_slots + slot] = v0;
+            v0 = anchor_madd(pw, v0, dd[0]);
+            vs[(int64_t)a.stream0 * a.n_slots + slot] = v0;
             if constexpr (S > 1) {
-                v1 = cdf_mul_add(pw, v1, dd[1]);
-                a.v[(int64_t)(a.stream0 + 1) * a.n_slots + slot] = v1;
+                v1 = anchor_madd(pw, v1, dd[1]);
+                vs[(int64_t)(a.stream0 + 1) * a.n_slots + slot] = v1;
             }
             return true;
         });
@@ -1225,7 +1238,8 @@ struct TcBank {
     int32_t *tile_ptr = nullptr, *tmpl_of = nullptr;
     uint8_t *has_carry = nullptr;
     float2 *a = nullptr, *aJ = nullptr, *c = nullptr, *aLf = nullptr;
-    float4 *aL = nullptr, *v = nullptr, *aLb1 = nullptr, *aLb2 = nullptr;   // double-float
+    uint4 *aL = nullptr, *v = nullptr, *aLb1 = nullptr, *aLb2 = nullptr;   // FP64 or double-float
+    bool df = false;                          // double-float carry
     float *xbuf = nullptr, *stage = nullptr;
     float2 *z = nullptr;
     unsigned int *status = nullptr;
@@ -1295,10 +1309,36 @@ int64_t tc_bytes(const spiir_bank_desc *d, const TcPlan &p) {
     return b + 256;
 }
 
-// Double-float split of a complex double: {re hi, im hi, re lo, im lo}.
-float4 host_df(std::complex<double> x) {
-    const float rh = (float)x.real(), ih = (float)x.imag();
-    return make_float4(rh, ih, (float)(x.real() - (double)rh), (float)(x.imag() - (double)ih));
+// An anchor value as the carry kernel reads it: FP64 {re, im}, or the
+// double-float split {re hi, im hi, re lo, im lo}.
+uint4 host_anchor(std::complex<double> x, bool df) {
+    uint4 r;
+    if (df) {
+        const float rh = (float)x.real(), ih = (float)x.imag();
+        const float4 f = make_float4(rh, ih, (float)(x.real() - (double)rh), (float)(x.imag() - (double)ih));
+        std::memcpy(&r, &f, sizeof r);
+    } else {
+        const double2 f = make_double2(x.real(), x.imag());
+        std::memcpy(&r, &f, sizeof r);
+    }
+    return r;
+}
+
+// The carry kernel's instantiations, indexed 8 bf16 + 4 (L = 128) + 2 (two
+// streams) + (double-float carry).
+using CarryFn = void (*)(const TcCarryArgs);
+CarryFn carry_kernel(int i) {
+    static const CarryFn k[16] = {
+        tc_carry_kernel<false, 4, 1, false>, tc_carry_kernel<false, 4, 1, true>,
+        tc_carry_kernel<false, 4, 2, false>, tc_carry_kernel<false, 4, 2, true>,
+        tc_carry_kernel<false, 2, 1, false>, tc_carry_kernel<false, 2, 1, true>,
+        tc_carry_kernel<false, 2, 2, false>, tc_carry_kernel<false, 2, 2, true>,
+        tc_carry_kernel<true, 4, 1, false>,  tc_carry_kernel<true, 4, 1, true>,
+        tc_carry_kernel<true, 4, 2, false>,  tc_carry_kernel<true, 4, 2, true>,
+        tc_carry_kernel<true, 2, 1, false>,  tc_carry_kernel<true, 2, 1, true>,
+        tc_carry_kernel<true, 2, 2, false>,  tc_carry_kernel<true, 2, 2, true>,
+    };
+    return k[i];
 }
 
 uint16_t host16(float x, bool bf16) {
@@ -1340,6 +1380,7 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
     b->ring_len = p.ring_len;
     b->xbuf_stride = p.xbuf_stride;
     b->bf16 = d->mode != SPIIR_TC_FP16;
+    b->df = d->carry == 1;
     b->scale = scale;
     b->max_delay = p.max_delay;
     b->last_n.assign(d->n_streams, 0);
@@ -1404,7 +1445,7 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
     // Carry tiles: 128 filter slots each, template-major.
     std::vector<int32_t> tile_ptr(p.T + 1, 0), tmpl_of;
     std::vector<float2> av(p.n_slots), aJv(p.n_slots), cv(p.n_slots);
-    std::vector<float4> aLv(p.n_slots), aLb1v(p.n_slots), aLb2v(p.n_slots);
+    std::vector<uint4> aLv(p.n_slots), aLb1v(p.n_slots), aLb2v(p.n_slots);
     std::vector<float2> aLfv(p.n_slots);
     std::vector<int64_t> slot_k(p.n_slots, -1);   // filter of each carry slot (-1: padding)
     const int cpb1 = carry_cpb(1, p.L), cpb2 = carry_cpb(2, p.L);
@@ -1432,15 +1473,15 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
                 av[slot] = make_float2(d->a_re[k], d->a_im[k]);
                 const auto pJ = pw(kJ);
                 aJv[slot] = make_float2((float)pJ.real(), (float)pJ.imag());
-                aLv[slot] = host_df(aL);
+                aLv[slot] = host_anchor(aL, b->df);
                 aLfv[slot] = make_float2((float)aL.real(), (float)aL.imag());
                 const auto b1 = pw(p.L * cpb1), b2 = pw(p.L * cpb2);
-                aLb1v[slot] = host_df(b1);
-                aLb2v[slot] = host_df(b2);
+                aLb1v[slot] = host_anchor(b1, b->df);
+                aLb2v[slot] = host_anchor(b2, b->df);
                 cv[slot] = make_float2((float)ck.real(), (float)ck.imag());
             } else {
                 av[slot] = aJv[slot] = cv[slot] = aLfv[slot] = make_float2(0.f, 0.f);
-                aLv[slot] = aLb1v[slot] = aLb2v[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+                aLv[slot] = aLb1v[slot] = aLb2v[slot] = make_uint4(0u, 0u, 0u, 0u);
             }
         }
         tile += nt;
@@ -1494,8 +1535,8 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
                         s)))
         return st;
     const int64_t S = d->n_streams;
-    TC_CUDA(cudaMalloc((void **)&b->v, std::max<int64_t>(1, S * p.n_slots) * sizeof(float4)));
-    TC_CUDA(cudaMemsetAsync(b->v, 0, std::max<int64_t>(1, S * p.n_slots) * sizeof(float4), s));
+    TC_CUDA(cudaMalloc((void **)&b->v, std::max<int64_t>(1, S * p.n_slots) * sizeof(uint4)));
+    TC_CUDA(cudaMemsetAsync(b->v, 0, std::max<int64_t>(1, S * p.n_slots) * sizeof(uint4), s));
     TC_CUDA(cudaMalloc((void **)&b->xbuf, S * p.xbuf_stride * sizeof(float)));
     TC_CUDA(cudaMemsetAsync(b->xbuf, 0, S * p.xbuf_stride * sizeof(float), s));
     TC_CUDA(cudaMalloc((void **)&b->stage, S * p.ring_len * sizeof(float)));
@@ -1515,14 +1556,16 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
     int max_optin = 0;
     TC_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     {
-        const void *fns[10] = {(const void *)tc_fir_kernel<true>, (const void *)tc_fir_kernel<false>,
-                               (const void *)tc_carry_kernel<true, 2, 1>, (const void *)tc_carry_kernel<true, 4, 1>,
-                               (const void *)tc_carry_kernel<false, 2, 1>, (const void *)tc_carry_kernel<false, 4, 1>,
-                               (const void *)tc_carry_kernel<true, 2, 2>, (const void *)tc_carry_kernel<true, 4, 2>,
-                               (const void *)tc_carry_kernel<false, 2, 2>, (const void *)tc_carry_kernel<false, 4, 2>};
-        const int need[10] = {fir_smem_of(p.L, p.K), fir_smem_of(p.L, p.K), kCarrySmem, kCarrySmem,
-                              kCarrySmem, kCarrySmem, kCarrySmem, kCarrySmem, kCarrySmem, kCarrySmem};
-        for (int i = 0; i < 10; ++i) {
+        const void *fns[18];
+        int need[18];
+        fns[0] = (const void *)tc_fir_kernel<true>;
+        fns[1] = (const void *)tc_fir_kernel<false>;
+        need[0] = need[1] = fir_smem_of(p.L, p.K);
+        for (int i = 0; i < 16; ++i) {
+            fns[2 + i] = (const void *)carry_kernel(i);
+            need[2 + i] = kCarrySmem;
+        }
+        for (int i = 0; i < 18; ++i) {
             cudaFuncAttributes fa;
             TC_CUDA(cudaFuncGetAttributes(&fa, fns[i]));
             const int dyn_max = max_optin - (int)fa.sharedSizeBytes;
@@ -1634,23 +1677,7 @@ spiir_status spiir_tc_push(TcBank *b, int s0, int count, const float *x, int64_t
         const int thr = kCarryWarps * 32;
         timer->begin(SPIIR_K_TC_CARRY, s);
         const bool l2 = b->L == 2 * kJ, two = count == 2;
-        if (b->bf16) {
-            if (two) {
-                if (l2) tc_carry_kernel<true, 2, 2><<<grid, thr, kCarrySmem, s>>>(ca);
-                else tc_carry_kernel<true, 4, 2><<<grid, thr, kCarrySmem, s>>>(ca);
-            } else {
-                if (l2) tc_carry_kernel<true, 2, 1><<<grid, thr, kCarrySmem, s>>>(ca);
-                else tc_carry_kernel<true, 4, 1><<<grid, thr, kCarrySmem, s>>>(ca);
-            }
-        } else {
-            if (two) {
-                if (l2) tc_carry_kernel<false, 2, 2><<<grid, thr, kCarrySmem, s>>>(ca);
-                else tc_carry_kernel<false, 4, 2><<<grid, thr, kCarrySmem, s>>>(ca);
-            } else {
-                if (l2) tc_carry_kernel<false, 2, 1><<<grid, thr, kCarrySmem, s>>>(ca);
-                else tc_carry_kernel<false, 4, 1><<<grid, thr, kCarrySmem, s>>>(ca);
-            }
-        }
+        carry_kernel(8 * b->bf16 + 4 * l2 + 2 * two + b->df)<<<grid, thr, kCarrySmem, s>>>(ca);
         TC_CUDA(cudaGetLastError());
         timer->end(s);
     }
@@ -1690,7 +1717,7 @@ spiir_status spiir_tc_push(TcBank *b, int s0, int count, const float *x, int64_t
 
 spiir_status spiir_tc_reset(TcBank *b, int s0, int count, cudaStream_t s) {
     if (b->n_slots)
-        TC_CUDA(cudaMemsetAsync(b->v + (int64_t)s0 * b->n_slots, 0, count * b->n_slots * sizeof(float4), s));
+        TC_CUDA(cudaMemsetAsync(b->v + (int64_t)s0 * b->n_slots, 0, count * b->n_slots * sizeof(uint4), s));
     TC_CUDA(cudaMemsetAsync(b->xbuf + (int64_t)s0 * b->xbuf_stride, 0, count * b->xbuf_stride * sizeof(float), s));
     for (int q = s0; q < s0 + count; ++q) b->last_n[q] = 0;
     return SPIIR_OK;

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_PKG, "_build", "libspiir.so")
 OK, EINVAL, ENOMEM, EBUDGET, ECUDA, ETIMEOUT, ESTATE, EUNSUPPORTED = range(8)
 PLAIN_FP32, TC_FP16, TC_BF16, TC_BF16X2 = range(4)
 MODES = {"plain": PLAIN_FP32, "fp16": TC_FP16, "bf16": TC_BF16, "bf16x2": TC_BF16X2}
+CARRY = {"fp64": 0, "df": 1}     # tensor-core forms: inter-batch state arithmetic
 
 _c_void_p = ctypes.c_void_p
 _i32, _i64, _f32, _f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double
@@ -34,6 +35,7 @@ class BankDesc(ctypes.Structure):
         ("h_down", _c_void_p), ("h_up", _c_void_p),
         ("n_taps", _i32), ("align", _i32), ("snr_scale", _f32), ("mode", _i32),
         ("chunk_len", _i32), ("tune", _i32), ("hbm_budget_bytes", _i64), ("n_taps_up", _i32),
+        ("carry", _i32),
     ]
 
 
@@ -128,7 +130,7 @@ def make_desc(bank, n_streams: int = 1, block_len: int = 4096, max_push_blocks: 
               mode: str = "plain", chunk_len: int = 0, tune: int = 0,
               hbm_budget_bytes: int = 0, align: Optional[bool] = None,
               h_down: Optional[np.ndarray] = None, h_up: Optional[np.ndarray] = None,
-              snr_scale: float = 0.0):
+              snr_scale: float = 0.0, carry="fp64"):
     """Fill a BankDesc from an inputs.Bank. Returns (desc, keepalive arrays)."""
     keep = dict(
         a_re=_arr(bank.a_re, np.float32), a_im=_arr(bank.a_im, np.float32),
@@ -159,6 +161,7 @@ def make_desc(bank, n_streams: int = 1, block_len: int = 4096, max_push_blocks: 
     d.chunk_len = chunk_len
     d.tune = tune
     d.hbm_budget_bytes = hbm_budget_bytes
+    d.carry = CARRY[carry] if isinstance(carry, str) else int(carry)
     return d, keep
 
 

@@ -82,6 +82,11 @@ def test_validation_rejects_bad_descriptions():
     assert _status(mr, block_len=4096, h_down=spiir.kaiser_taps(514, 100.0), h_up=hu) == spiir.EINVAL
     assert _status(mr, block_len=4096, h_down=hd, h_up=spiir.kaiser_taps(66, 60.0)) == spiir.EINVAL
     assert _status(mr, block_len=4096, h_down=hd, h_up=spiir.kaiser_taps(31, 60.0)) == spiir.EINVAL
+    # carry arithmetic of the tensor-core forms: 0 = FP64, 1 = double-float,
+    # anything else is rejected before the form is looked at
+    assert _status(bank, carry="df") == spiir.OK
+    assert _status(bank, carry=2) == spiir.EINVAL
+    assert _status(bank, mode="fp16", carry=-1) == spiir.EINVAL
     d, _k = spiir.make_desc(bank)
     assert spiir.lib().spiir_bank_create(None, None, ctypes.byref(ctypes.c_void_p())) == spiir.EINVAL
     assert "NULL" in spiir.last_error()

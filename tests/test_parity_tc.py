@@ -77,6 +77,25 @@ def test_three_streams_pair_and_single(torch_cuda, oracle_mod):
         _check(z[s], ref, TOL_TC, 256)
 
 
+@pytest.mark.parametrize("mode,tol", [("fp16", TOL_TC), ("bf16", TOL_BF16)])
+def test_double_float_carry_matches_fp64(torch_cuda, oracle_mod, mode, tol):
+    """The double-float batch anchor (carry="df") against the default FP64
+    anchor: the FP32 chunk states both hand to the contractions agree, so the
+    SNR series agree far below the tolerance; and the double-float form
+    against the oracle. Two streams, pushes of 3 blocks of 1024 (12 chunks:
+    one full batch of 8 and a partial one, whose power a^(nb L) the kernel
+    builds in the anchor's arithmetic)."""
+    counts = [60, 128, 200, 256, 300, 1, 383]
+    bank = inputs.single_rate_bank(len(counts), counts, 700, seed=23)
+    x = inputs.strain(2, 4 * 3072, seed=14)
+    kw = dict(block_len=1024, push_blocks=3, n_streams=2, mode=mode, chunk_len=256)
+    z64 = gpu_snr(bank, x, **kw)
+    zdf = gpu_snr(bank, x, carry="df", **kw)
+    assert rel_rms(zdf, z64).max() <= 1e-6
+    for s in range(2):
+        _check(zdf[s], oracle_mod.spiir_single(bank, x[s]), tol, 256)
+
+
 def test_tc_matches_plain_path(torch_cuda):
     """Same bank through both forms: they agree to the TC tolerance."""
     bank = inputs.single_rate_bank(70, 64, 300, seed=3)
