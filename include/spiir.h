@@ -153,7 +153,8 @@ spiir_status spiir_push_block(spiir_bank_t bank, int32_t stream_id,
  * -1) into z_dev: complex64 [n_templates][n_samples] per stream, streams
  * outermost, the last n_samples samples of that push, z = snr_scale * sum.
  * Asynchronous device-to-device copy on cuda_stream.
- * Errors: EINVAL, ESTATE (nothing pushed on that stream yet). */
+ * Errors: EINVAL, ESTATE (nothing pushed on that stream since create, reset
+ * or state import). */
 spiir_status spiir_read_snr(spiir_bank_t bank, int32_t stream_id, void *z_dev,
                             int64_t n_samples, void *cuda_stream);
 
@@ -161,6 +162,36 @@ spiir_status spiir_read_snr(spiir_bank_t bank, int32_t stream_id, void *z_dev,
  * (or all, -1): the next push behaves like the first push of a new bank. */
 spiir_status spiir_state_reset(spiir_bank_t bank, int32_t stream_id,
                                void *cuda_stream);
+
+/* The SNR of Sec. 2.1 as the modulus of z over a per-template normalisation
+ * constant: out_dev[stream][template][i] = |z| / norm_dev[template] for the
+ * last n_samples samples of the most recent push of stream_id (or every
+ * stream, -1), float32, streams outermost. norm_dev: device float
+ * [n_templates] (the caller's constants, > 0), or NULL for |z|. Asynchronous
+ * on cuda_stream. Errors: EINVAL, ESTATE (no push since create, reset or
+ * state import). */
+spiir_status spiir_read_snr_abs(spiir_bank_t bank, int32_t stream_id, float *out_dev,
+                                int64_t n_samples, const float *norm_dev, void *cuda_stream);
+
+/* Checkpoint and resume. A state blob holds, per stream, everything a push
+ * depends on: the filter states (in filter order, so it does not depend on
+ * the kernel variant), the strain and resampler histories and the length of
+ * the last push. spiir_state_bytes: size of the blob of one stream (or all,
+ * -1), -1 on a bad argument. spiir_state_export writes it to host memory dst
+ * (at least that many bytes; the call waits for the copies). spiir_state_import
+ * reads a blob of the same number of streams into stream_id (or all, -1) of a
+ * bank created from the same description (same filters, rates, resampler,
+ * block length, maximum push and form; the tensor-core carry arithmetic may
+ * differ: its state is stored in FP64); later pushes then continue the
+ * stream as if it had never stopped. The output ring is not part of the
+ * state: read the SNR after the next push. Errors: EINVAL (NULL pointer,
+ * short buffer, blob of another description or form, stream count).
+ * The caller owns dst/src. */
+int64_t spiir_state_bytes(spiir_bank_t bank, int32_t stream_id);
+spiir_status spiir_state_export(spiir_bank_t bank, int32_t stream_id, void *dst, int64_t bytes,
+                                void *cuda_stream);
+spiir_status spiir_state_import(spiir_bank_t bank, int32_t stream_id, const void *src,
+                                int64_t bytes, void *cuda_stream);
 
 /* End-to-end call on host buffers: copy x_host [n_streams or 1][n_samples]
  * to the device, push, and copy the SNR back into z_host (layout of

@@ -121,6 +121,7 @@ struct Plan {
     std::vector<int32_t> task_out;
     std::vector<int32_t> comb_ptr, comb_rows;
     std::vector<int32_t> order;
+    std::vector<int64_t> slot_filter;   // filter of each slot (-1: padding)
     int64_t lds_rounds = 0, lds_wavefronts = 0;
     int64_t n_units = 0;
 };
@@ -448,6 +449,7 @@ spiir_status make_plan(const spiir_bank_desc *d, int variant, bool arrays, Plan 
     p.bre.assign(n_slots, 0.f);
     p.bim.assign(n_slots, 0.f);
     p.xoff.assign(n_slots, 0);
+    p.slot_filter.assign(n_slots, -1);
     int64_t slot_base = 0;
     for (auto &ib : item_bundles) {
         CtaItem ci;
@@ -526,6 +528,7 @@ spiir_status make_plan(const spiir_bank_desc *d, int variant, bool arrays, Plan 
                         }
                         int32_t xo;
                         if (pick >= 0) {
+                            p.slot_filter[s] = pick;
                             p.are[s] = d->a_re[pick];
                             p.aim[s] = d->a_im[pick];
                             p.bre[s] = d->b_re[pick];
@@ -617,6 +620,8 @@ struct spiir_bank {
     cudaStream_t cap = nullptr;             // private stream for graph capture
     std::vector<GraphEntry> graphs;
     std::vector<int64_t> last_n;
+    std::vector<char> out_valid;            // the output ring holds a push of the stream
+    uint64_t fingerprint = 0;               // of the description, for state import
     int64_t footprint = 0;
     int64_t n_filters = 0;
     TcBank *tc = nullptr;
@@ -869,6 +874,40 @@ spiir_status push_plain(spiir_bank *b, int s0, int count, const float *x, int64_
     return SPIIR_OK;
 }
 
+// FNV-1a over everything in a description that the filter state's meaning
+// and layout depend on (the carry arithmetic of the tensor-core forms is left
+// out: their state is exported in FP64).
+uint64_t desc_fingerprint(const spiir_bank_desc *d) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const void *p, size_t n) {
+        const unsigned char *c = (const unsigned char *)p;
+        for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+    };
+    const int32_t sc[] = {d->n_templates, d->n_levels, d->base_rate, d->block_len,
+                          d->max_push_blocks, d->n_taps ? d->n_taps : 32,
+                          d->n_taps_up ? d->n_taps_up : (d->n_taps ? d->n_taps : 32), d->align,
+                          (int32_t)(d->mode != SPIIR_PLAIN_FP32), d->mode == SPIIR_PLAIN_FP32 ? 0 :
+                          (d->chunk_len ? d->chunk_len : 256)};
+    mix(sc, sizeof sc);
+    mix(&d->n_filters, sizeof d->n_filters);
+    const int64_t n = d->n_filters;
+    if (n > 0) {
+        mix(d->a_re, n * sizeof(float));
+        mix(d->a_im, n * sizeof(float));
+        mix(d->b_re, n * sizeof(float));
+        mix(d->b_im, n * sizeof(float));
+        mix(d->delay, n * sizeof(int32_t));
+        mix(d->template_id, n * sizeof(int32_t));
+        if (d->level) mix(d->level, n * sizeof(int8_t));
+    }
+    if (d->h_down) {
+        const int nt = d->n_taps ? d->n_taps : 32, ntu = d->n_taps_up ? d->n_taps_up : nt;
+        mix(d->h_down, nt * sizeof(float));
+        mix(d->h_up, ntu * sizeof(float));
+    }
+    return h;
+}
+
 spiir_status build_bank(const spiir_bank_desc *desc, int variant, cudaStream_t s,
                         spiir_bank *b) {
     b->d = *desc;
@@ -892,6 +931,8 @@ spiir_status build_bank(const spiir_bank_desc *desc, int variant, cudaStream_t s
         lib_kaiser_taps(ntu, 60.0, b->h_up.data());
     }
     b->last_n.assign(desc->n_streams, 0);
+    b->out_valid.assign(desc->n_streams, 0);
+    b->fingerprint = desc_fingerprint(desc);
     if (!b->timer) b->timer = new KernelTimer();
     spiir_status st;
     if (desc->mode != SPIIR_PLAIN_FP32) {
@@ -995,16 +1036,24 @@ spiir_status spiir_push_block(spiir_bank_t b, int32_t stream_id, const float *x_
     if (b->tc) {
         spiir_status st = spiir_tc_push(b->tc, s0, cnt, x_dev, n_samples, n_samples, s, b->timer);
         if (st) return fail(st, "%s", spiir_tc_last_error());
-        for (int q = s0; q < s0 + cnt; ++q) b->last_n[q] = n_samples;
+        for (int q = s0; q < s0 + cnt; ++q) {
+            b->last_n[q] = n_samples;
+            b->out_valid[q] = 1;
+        }
         return SPIIR_OK;
     }
     bool same = true;
     for (int q = s0; q < s0 + cnt; ++q) same &= (b->last_n[q] == b->last_n[s0]);
-    if (same) return push_plain(b, s0, cnt, x_dev, n_samples, n_samples, s);
-    for (int q = 0; q < cnt; ++q) {
-        spiir_status st = push_plain(b, s0 + q, 1, x_dev + q * n_samples, n_samples, n_samples, s);
+    if (same) {
+        spiir_status st = push_plain(b, s0, cnt, x_dev, n_samples, n_samples, s);
         if (st) return st;
+    } else {
+        for (int q = 0; q < cnt; ++q) {
+            spiir_status st = push_plain(b, s0 + q, 1, x_dev + q * n_samples, n_samples, n_samples, s);
+            if (st) return st;
+        }
     }
+    for (int q = s0; q < s0 + cnt; ++q) b->out_valid[q] = 1;
     return SPIIR_OK;
 }
 
@@ -1019,6 +1068,8 @@ spiir_status spiir_read_snr(spiir_bank_t b, int32_t stream_id, void *z_dev, int6
     cudaStream_t s = (cudaStream_t)cuda_stream;
     for (int q = s0; q < s0 + cnt; ++q) {
         if (b->last_n[q] == 0) return fail(SPIIR_ESTATE, "nothing pushed on stream %d", q);
+        if (!b->out_valid[q])
+            return fail(SPIIR_ESTATE, "no push on stream %d since its state was imported", q);
         if (n_samples <= 0 || n_samples > b->last_n[q])
             return fail(SPIIR_EINVAL, "n_samples must be in [1, samples of the last push]");
     }
@@ -1061,7 +1112,182 @@ spiir_status spiir_state_reset(spiir_bank_t b, int32_t stream_id, void *cuda_str
             CUDA_TRY(cudaMemsetAsync(b->ubuf + (int64_t)s0 * p.ubuf_stream_stride, 0,
                                      cnt * p.ubuf_stream_stride * sizeof(float2), s));
     }
-    for (int q = s0; q < s0 + cnt; ++q) b->last_n[q] = 0;
+    for (int q = s0; q < s0 + cnt; ++q) {
+        b->last_n[q] = 0;
+        b->out_valid[q] = 0;
+    }
+    return SPIIR_OK;
+}
+
+// State blob: a header, then one record per stream: the length of its last
+// push, the filter states in filter order (plain: FP32 {re, im}; tensor-core:
+// FP64 {re, im}), the strain history (xbuf) and, for the plain form, the
+// upsampler histories (ubuf).
+struct StateHeader {
+    char magic[8];
+    uint32_t form, n_streams;
+    uint64_t fingerprint;
+    int64_t n_filters, xbuf_len, ubuf_len, elem_bytes;
+};
+constexpr char kStateMagic[8] = {'S', 'P', 'I', 'I', 'R', 'S', 'T', '1'};
+
+static void state_shape(spiir_bank_t b, StateHeader &h) {
+    std::memcpy(h.magic, kStateMagic, 8);
+    h.form = b->tc ? 1u : 0u;
+    h.fingerprint = b->fingerprint;
+    h.n_filters = b->n_filters;
+    h.xbuf_len = b->tc ? spiir_tc_xbuf_len(b->tc) : b->p.xbuf_stream_stride;
+    h.ubuf_len = b->tc ? 0 : b->p.ubuf_stream_stride;
+    h.elem_bytes = b->tc ? 16 : 8;
+}
+
+static int64_t state_record_bytes(const StateHeader &h) {
+    return 8 + h.n_filters * h.elem_bytes + h.xbuf_len * 4 + h.ubuf_len * 8;
+}
+
+int64_t spiir_state_bytes(spiir_bank_t b, int32_t stream_id) {
+    if (!b || stream_id < -1 || stream_id >= b->d.n_streams) return -1;
+    StateHeader h;
+    state_shape(b, h);
+    const int cnt = stream_id < 0 ? b->d.n_streams : 1;
+    return (int64_t)sizeof(StateHeader) + cnt * state_record_bytes(h);
+}
+
+spiir_status spiir_state_export(spiir_bank_t b, int32_t stream_id, void *dst, int64_t bytes,
+                                void *cuda_stream) {
+    if (!b) return fail(SPIIR_EINVAL, "bank is NULL");
+    if (!dst) return fail(SPIIR_EINVAL, "dst is NULL");
+    if (stream_id < -1 || stream_id >= b->d.n_streams)
+        return fail(SPIIR_EINVAL, "stream_id %d out of range", stream_id);
+    if (bytes < spiir_state_bytes(b, stream_id))
+        return fail(SPIIR_EINVAL, "buffer of %lld bytes, %lld needed", (long long)bytes,
+                    (long long)spiir_state_bytes(b, stream_id));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int s0 = stream_id < 0 ? 0 : stream_id;
+    const int cnt = stream_id < 0 ? b->d.n_streams : 1;
+    StateHeader h;
+    state_shape(b, h);
+    h.n_streams = (uint32_t)cnt;
+    char *out = (char *)dst;
+    std::memcpy(out, &h, sizeof h);
+    out += sizeof h;
+    for (int q = s0; q < s0 + cnt; ++q) {
+        int64_t last_n = b->last_n[q];
+        char *rec = out;
+        out += state_record_bytes(h);
+        double *v64 = nullptr;
+        float2 *v32 = nullptr;
+        float *xb = (float *)(rec + 8 + h.n_filters * h.elem_bytes);
+        if (b->tc) {
+            v64 = (double *)(rec + 8);
+            spiir_status st = spiir_tc_state_get(b->tc, q, v64, xb, &last_n, s);
+            if (st) return fail(st, "%s", spiir_tc_last_error());
+        } else {
+            const Plan &p = b->p;
+            std::vector<float2> raw(p.n_slots);
+            if (p.n_slots)
+                CUDA_TRY(cudaMemcpyAsync(raw.data(), b->state + (int64_t)q * p.n_slots,
+                                         p.n_slots * sizeof(float2), cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(cudaMemcpyAsync(xb, b->xbuf + (int64_t)q * p.xbuf_stream_stride,
+                                     p.xbuf_stream_stride * sizeof(float), cudaMemcpyDeviceToHost, s));
+            if (h.ubuf_len)
+                CUDA_TRY(cudaMemcpyAsync(xb + h.xbuf_len, b->ubuf + (int64_t)q * p.ubuf_stream_stride,
+                                         p.ubuf_stream_stride * sizeof(float2), cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(cudaStreamSynchronize(s));
+            v32 = (float2 *)(rec + 8);
+            for (int64_t sl = 0; sl < p.n_slots; ++sl)
+                if (p.slot_filter[sl] >= 0) v32[p.slot_filter[sl]] = raw[sl];
+        }
+        std::memcpy(rec, &last_n, 8);
+    }
+    return SPIIR_OK;
+}
+
+spiir_status spiir_state_import(spiir_bank_t b, int32_t stream_id, const void *src, int64_t bytes,
+                                void *cuda_stream) {
+    if (!b) return fail(SPIIR_EINVAL, "bank is NULL");
+    if (!src) return fail(SPIIR_EINVAL, "src is NULL");
+    if (stream_id < -1 || stream_id >= b->d.n_streams)
+        return fail(SPIIR_EINVAL, "stream_id %d out of range", stream_id);
+    const int s0 = stream_id < 0 ? 0 : stream_id;
+    const int cnt = stream_id < 0 ? b->d.n_streams : 1;
+    StateHeader want, got;
+    state_shape(b, want);
+    if (bytes < (int64_t)sizeof got) return fail(SPIIR_EINVAL, "state blob too short");
+    std::memcpy(&got, src, sizeof got);
+    if (std::memcmp(got.magic, kStateMagic, 8) != 0) return fail(SPIIR_EINVAL, "not a state blob");
+    if (got.form != want.form || got.fingerprint != want.fingerprint || got.n_filters != want.n_filters ||
+        got.xbuf_len != want.xbuf_len || got.ubuf_len != want.ubuf_len || got.elem_bytes != want.elem_bytes)
+        return fail(SPIIR_EINVAL, "state blob of another bank description or form");
+    if ((int)got.n_streams != cnt)
+        return fail(SPIIR_EINVAL, "blob holds %u streams, %d requested", got.n_streams, cnt);
+    if (bytes < (int64_t)sizeof got + cnt * state_record_bytes(got))
+        return fail(SPIIR_EINVAL, "state blob truncated");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const char *in = (const char *)src + sizeof got;
+    for (int q = s0; q < s0 + cnt; ++q) {
+        const char *rec = in;
+        in += state_record_bytes(got);
+        int64_t last_n;
+        std::memcpy(&last_n, rec, 8);
+        if (last_n < 0 || last_n > (int64_t)b->d.block_len * b->d.max_push_blocks ||
+            last_n % b->d.block_len != 0)
+            return fail(SPIIR_EINVAL, "state blob: bad push length");
+        const float *xb = (const float *)(rec + 8 + got.n_filters * got.elem_bytes);
+        if (b->tc) {
+            spiir_status st = spiir_tc_state_set(b->tc, q, (const double *)(rec + 8), xb, last_n, s);
+            if (st) return fail(st, "%s", spiir_tc_last_error());
+        } else {
+            const Plan &p = b->p;
+            const float2 *v32 = (const float2 *)(rec + 8);
+            std::vector<float2> raw(p.n_slots, make_float2(0.f, 0.f));
+            for (int64_t sl = 0; sl < p.n_slots; ++sl)
+                if (p.slot_filter[sl] >= 0) raw[sl] = v32[p.slot_filter[sl]];
+            if (p.n_slots)
+                CUDA_TRY(cudaMemcpyAsync(b->state + (int64_t)q * p.n_slots, raw.data(),
+                                         p.n_slots * sizeof(float2), cudaMemcpyHostToDevice, s));
+            CUDA_TRY(cudaMemcpyAsync(b->xbuf + (int64_t)q * p.xbuf_stream_stride, xb,
+                                     p.xbuf_stream_stride * sizeof(float), cudaMemcpyHostToDevice, s));
+            if (got.ubuf_len)
+                CUDA_TRY(cudaMemcpyAsync(b->ubuf + (int64_t)q * p.ubuf_stream_stride, xb + got.xbuf_len,
+                                         p.ubuf_stream_stride * sizeof(float2), cudaMemcpyHostToDevice, s));
+            CUDA_TRY(cudaStreamSynchronize(s));
+        }
+        b->last_n[q] = last_n;
+        b->out_valid[q] = 0;
+    }
+    return SPIIR_OK;
+}
+
+spiir_status spiir_read_snr_abs(spiir_bank_t b, int32_t stream_id, float *out_dev, int64_t n_samples,
+                                const float *norm_dev, void *cuda_stream) {
+    if (!b) return fail(SPIIR_EINVAL, "bank is NULL");
+    if (!out_dev) return fail(SPIIR_EINVAL, "out_dev is NULL");
+    if (stream_id < -1 || stream_id >= b->d.n_streams)
+        return fail(SPIIR_EINVAL, "stream_id %d out of range", stream_id);
+    const int s0 = stream_id < 0 ? 0 : stream_id;
+    const int cnt = stream_id < 0 ? b->d.n_streams : 1;
+    for (int q = s0; q < s0 + cnt; ++q) {
+        if (b->last_n[q] == 0) return fail(SPIIR_ESTATE, "nothing pushed on stream %d", q);
+        if (!b->out_valid[q])
+            return fail(SPIIR_ESTATE, "no push on stream %d since its state was imported", q);
+        if (n_samples <= 0 || n_samples > b->last_n[q])
+            return fail(SPIIR_EINVAL, "n_samples must be in [1, samples of the last push]");
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int T = b->d.n_templates;
+    for (int q = s0; q < s0 + cnt; ++q) {
+        const float2 *src;
+        int64_t ring;
+        if (b->tc) {
+            src = spiir_tc_output(b->tc, q, &ring);
+        } else {
+            ring = b->p.ring_len;
+            src = b->z + (int64_t)q * T * ring;
+        }
+        CUDA_TRY(spiir_launch_abs(src + b->last_n[q] - n_samples, ring, T, n_samples, norm_dev,
+                                  out_dev + (int64_t)(q - s0) * T * n_samples, s));
+    }
     return SPIIR_OK;
 }
 

@@ -196,6 +196,9 @@ cudaError_t spiir_launch_decimate(const DecimArgs &a, int n_streams, cudaStream_
 cudaError_t spiir_launch_recur(const RecurArgs &a, int variant, int n_ctas,
                                int n_streams, int smem_bytes, cudaStream_t s);
 cudaError_t spiir_launch_combine(const CombineArgs &a, int chunk, int n_streams, cudaStream_t s);
+// out[t][i] = |z[t][i]| / norm[t] (norm NULL: 1) for T rows of n samples, z rows ring apart.
+cudaError_t spiir_launch_abs(const float2 *z, int64_t ring, int T, int64_t n, const float *norm,
+                             float *out, cudaStream_t s);
 // Base-rate samples per combine time chunk, and the combine CTA's shared memory.
 int spiir_combine_chunk(int n_levels, int64_t push_max);
 int spiir_combine_smem(int n_levels, int chunk);

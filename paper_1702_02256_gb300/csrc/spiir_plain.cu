@@ -785,6 +785,35 @@ cudaError_t spiir_launch_recur(const RecurArgs &a, int variant, int n_ctas, int 
     return cudaGetLastError();
 }
 
+namespace {
+
+// |z| / norm_t, one thread per output sample (the SNR of Sec. 2.1 is the
+// modulus of z over the template's normalisation constant).
+__global__ void abs_kernel(const float2 *z, int64_t ring, int64_t n, const float *norm, float *out) {
+    const int t = blockIdx.y;
+    const float nt = norm ? norm[t] : 1.0f;
+    const float2 *zr = z + (int64_t)t * ring;
+    float *o = out + (int64_t)t * n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = zr[i];
+        o[i] = hypotf(v.x, v.y) / nt;
+    }
+}
+
+}  // namespace
+
+cudaError_t spiir_launch_abs(const float2 *z, int64_t ring, int T, int64_t n, const float *norm,
+                             float *out, cudaStream_t s) {
+    if (T <= 0 || n <= 0) return cudaSuccess;
+    const int bx = (int)std::min<int64_t>((n + 255) / 256, 64);
+    for (int t0 = 0; t0 < T; t0 += 65535) {
+        const int tn = std::min(65535, T - t0);
+        abs_kernel<<<dim3(bx, tn), 256, 0, s>>>(z + (int64_t)t0 * ring, ring, n, norm ? norm + t0 : nullptr,
+                                              out + (int64_t)t0 * n);
+    }
+    return cudaGetLastError();
+}
+
 int spiir_combine_chunk(int n_levels, int64_t push_max) {
     const int64_t c = std::max<int64_t>(2048, (int64_t)4 << (n_levels - 1));
     return (int)std::min<int64_t>(c, push_max);

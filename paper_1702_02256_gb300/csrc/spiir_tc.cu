@@ -1245,6 +1245,8 @@ struct TcBank {
     unsigned int *status = nullptr;
     uint4 *hank = nullptr, *xseg = nullptr;   // staged strain operands
     uint4 *panel = nullptr;                   // carry tiles' power panels
+    std::vector<int64_t> slot_k;              // filter of each carry slot (-1: padding)
+    int64_t n_filters = 0;
     int hank_bytes = 0;
     int n_sms = 1;
     std::vector<int64_t> last_n;
@@ -1488,6 +1490,7 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
     }
     tile_ptr[p.T] = tile;
     b->n_carry_ctas = (int)tmpl_of.size();
+    b->n_filters = d->n_filters;
     // Power panel of each tile (the layout the carry kernel copies into a
     // slot): a_k^j, j < kJ, in FP64 and rounded once to the operand type.
     std::vector<uint16_t> panel((size_t)tile * (kPanelBytes / 2));
@@ -1534,6 +1537,7 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
     if ((st = tc_upload(&b->panel, std::vector<uint4>((uint4 *)panel.data(), (uint4 *)(panel.data() + panel.size())),
                         s)))
         return st;
+    b->slot_k = std::move(slot_k);
     const int64_t S = d->n_streams;
     TC_CUDA(cudaMalloc((void **)&b->v, std::max<int64_t>(1, S * p.n_slots) * sizeof(uint4)));
     TC_CUDA(cudaMemsetAsync(b->v, 0, std::max<int64_t>(1, S * p.n_slots) * sizeof(uint4), s));
@@ -1720,6 +1724,55 @@ spiir_status spiir_tc_reset(TcBank *b, int s0, int count, cudaStream_t s) {
         TC_CUDA(cudaMemsetAsync(b->v + (int64_t)s0 * b->n_slots, 0, count * b->n_slots * sizeof(uint4), s));
     TC_CUDA(cudaMemsetAsync(b->xbuf + (int64_t)s0 * b->xbuf_stride, 0, count * b->xbuf_stride * sizeof(float), s));
     for (int q = s0; q < s0 + count; ++q) b->last_n[q] = 0;
+    return SPIIR_OK;
+}
+
+int64_t spiir_tc_xbuf_len(TcBank *b) { return b->xbuf_stride; }
+
+spiir_status spiir_tc_state_get(TcBank *b, int q, double *v, float *xbuf, int64_t *last_n, cudaStream_t s) {
+    std::vector<uint4> raw(b->n_slots);
+    if (b->n_slots)
+        TC_CUDA(cudaMemcpyAsync(raw.data(), b->v + (int64_t)q * b->n_slots, b->n_slots * sizeof(uint4),
+                                cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaMemcpyAsync(xbuf, b->xbuf + (int64_t)q * b->xbuf_stride, b->xbuf_stride * sizeof(float),
+                            cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaStreamSynchronize(s));
+    for (int64_t sl = 0; sl < b->n_slots; ++sl) {
+        const int64_t k = b->slot_k[sl];
+        if (k < 0) continue;
+        double re, im;
+        if (b->df) {
+            float4 f;
+            std::memcpy(&f, &raw[sl], sizeof f);
+            re = (double)f.x + (double)f.z;
+            im = (double)f.y + (double)f.w;
+        } else {
+            double2 f;
+            std::memcpy(&f, &raw[sl], sizeof f);
+            re = f.x;
+            im = f.y;
+        }
+        v[2 * k] = re;
+        v[2 * k + 1] = im;
+    }
+    *last_n = b->last_n[q];
+    return SPIIR_OK;
+}
+
+spiir_status spiir_tc_state_set(TcBank *b, int q, const double *v, const float *xbuf, int64_t last_n,
+                                cudaStream_t s) {
+    std::vector<uint4> raw(b->n_slots, make_uint4(0u, 0u, 0u, 0u));
+    for (int64_t sl = 0; sl < b->n_slots; ++sl) {
+        const int64_t k = b->slot_k[sl];
+        if (k >= 0) raw[sl] = host_anchor(std::complex<double>(v[2 * k], v[2 * k + 1]), b->df);
+    }
+    if (b->n_slots)
+        TC_CUDA(cudaMemcpyAsync(b->v + (int64_t)q * b->n_slots, raw.data(), b->n_slots * sizeof(uint4),
+                                cudaMemcpyHostToDevice, s));
+    TC_CUDA(cudaMemcpyAsync(b->xbuf + (int64_t)q * b->xbuf_stride, xbuf, b->xbuf_stride * sizeof(float),
+                            cudaMemcpyHostToDevice, s));
+    TC_CUDA(cudaStreamSynchronize(s));
+    b->last_n[q] = last_n;
     return SPIIR_OK;
 }
 

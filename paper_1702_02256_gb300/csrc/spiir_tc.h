@@ -20,5 +20,13 @@ float *spiir_tc_stage(TcBank *b);
 unsigned int *spiir_tc_status(TcBank *b);
 void spiir_tc_info(TcBank *b, spiir_bank_info *info);
 int64_t spiir_tc_footprint(const spiir_bank_desc *desc);
+// Filter state of stream q in filter order (FP64 {re, im} per filter, whatever
+// the carry arithmetic), its strain history (xbuf_len floats) and the length
+// of its last push. Synchronous on s.
+int64_t spiir_tc_xbuf_len(TcBank *b);
+spiir_status spiir_tc_state_get(TcBank *b, int q, double *v, float *xbuf, int64_t *last_n,
+                                cudaStream_t s);
+spiir_status spiir_tc_state_set(TcBank *b, int q, const double *v, const float *xbuf, int64_t last_n,
+                                cudaStream_t s);
 void spiir_tc_destroy(TcBank *b);
 const char *spiir_tc_last_error();

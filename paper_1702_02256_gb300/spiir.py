@@ -71,6 +71,10 @@ _SIGS = {
     "spiir_push_block": (_i32, [_c_void_p, _i32, _c_void_p, _i64, _c_void_p]),
     "spiir_read_snr": (_i32, [_c_void_p, _i32, _c_void_p, _i64, _c_void_p]),
     "spiir_state_reset": (_i32, [_c_void_p, _i32, _c_void_p]),
+    "spiir_read_snr_abs": (_i32, [_c_void_p, _i32, _c_void_p, _i64, _c_void_p, _c_void_p]),
+    "spiir_state_bytes": (_i64, [_c_void_p, _i32]),
+    "spiir_state_export": (_i32, [_c_void_p, _i32, _c_void_p, _i64, _c_void_p]),
+    "spiir_state_import": (_i32, [_c_void_p, _i32, _c_void_p, _i64, _c_void_p]),
     "spiir_push_block_host": (_i32, [_c_void_p, _i32, _c_void_p, _i64, _c_void_p, _c_void_p]),
     "spiir_bank_footprint": (_i64, [ctypes.POINTER(BankDesc)]),
     "spiir_bank_get_info": (_i32, [_c_void_p, ctypes.POINTER(BankInfo)]),
@@ -255,6 +259,33 @@ class Bank:
 
     def reset(self, stream_id: int = -1, stream=None):
         check(lib().spiir_state_reset(self._h, stream_id, _stream_handle(stream)))
+
+    def read_abs(self, n_samples: int, norm=None, stream_id: int = -1, out=None, stream=None):
+        """|z| / norm[t] of the last push: float32 CUDA tensor [n_streams, T, n]
+        (or [T, n]). norm: float32 CUDA tensor [T] or None."""
+        import torch
+        shape = ((self.n_streams if stream_id < 0 else 1), self.n_templates, n_samples)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32, device="cuda")
+        check(lib().spiir_read_snr_abs(self._h, stream_id, out.data_ptr(), n_samples,
+                                       None if norm is None else norm.data_ptr(),
+                                       _stream_handle(stream)))
+        return out if stream_id < 0 else out[0]
+
+    def export_state(self, stream_id: int = -1, stream=None) -> np.ndarray:
+        """Checkpoint: the state blob of one stream (or all) as uint8 host bytes."""
+        n = int(lib().spiir_state_bytes(self._h, stream_id))
+        if n < 0:
+            raise SpiirError(EINVAL, "bad stream_id")
+        buf = np.empty(n, np.uint8)
+        check(lib().spiir_state_export(self._h, stream_id, buf.ctypes.data, n, _stream_handle(stream)))
+        return buf
+
+    def import_state(self, blob, stream_id: int = -1, stream=None):
+        """Resume from a blob written by export_state (same description)."""
+        blob = np.ascontiguousarray(blob, np.uint8)
+        check(lib().spiir_state_import(self._h, stream_id, blob.ctypes.data, blob.size,
+                                       _stream_handle(stream)))
 
     def info(self) -> dict:
         inf = BankInfo()
