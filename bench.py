@@ -259,6 +259,46 @@ def run_sweep(args):
     return 0
 
 
+def run_ratesweep(args):
+    """Throughput against the number of rates (the paper's multi-rate table,
+    Table tab:multirate_speedup): 4096 templates whose 1024 filters are split
+    equally over R = 1, 2, 3, 4, 8 rates from 4096 Hz down (R = 1: all at full
+    rate), plain form, 1 s pushes of 4 s of strain. Reports the device time per
+    second of strain and its ratio to R = 1 (the paper's GPU row: 287, 220,
+    199, 143, 85 s, i.e. 1.30x, 1.44x, 2.01x, 3.38x)."""
+    import torch
+    from paper_1702_02256_gb300 import inputs
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    T, M = 4096, 1024
+    if args.tune is None:
+        args.tune = 1
+    rows = []
+    for R in (1, 2, 3, 4, 8):
+        counts = np.full((T, R), M // R, np.int64)
+        counts[:, 0] += M - counts.sum(axis=1)
+        bank = inputs.multi_rate_bank(T, R, seed=7, counts=counts)
+        w = dict(bank=bank, x=inputs.strain(1, 4 * 4096, seed=3), block_len=4096, push_blocks=1,
+                 n_streams=1, chunk_len=256, desc=f"{T} templates x {M} filters over {R} rates")
+        m = _measure(w, "plain", args, dev, None, None, 0, 1)
+        ms_per_s = m["ms_per_step"] / (w["x"].shape[1] / 4096.0)
+        rows.append({"rates": R, "filters_per_rate": [int(c) for c in counts[0]],
+                     "ms_per_second_of_strain": ms_per_s,
+                     "filter_samples_per_s": m["value"], "kernel_variant": m["info"]["kernel_variant"],
+                     "kernel_share": {k: round(v[0] / max(1e-9, sum(x[0] for x in m["kt"].values())), 4)
+                                      for k, v in m["kt"].items()}})
+    for r in rows:
+        r["time_ratio_vs_1_rate"] = rows[0]["ms_per_second_of_strain"] / r["ms_per_second_of_strain"]
+    line = {"metric": "device time per second of strain by number of rates (plain form)",
+            "value": rows[-1]["time_ratio_vs_1_rate"], "unit": "x faster than 1 rate",
+            "higher_is_better": True, "n_gpus": 1, "data": "synthetic", "rows": rows,
+            "config": {"workload": f"{T} templates x {M} filters split equally over 1-8 rates "
+                                   f"(4096 Hz down), delays 0-1023, 4 s in 1 s pushes, autotuned tiles",
+                       "paper_gpu_ratio": {"2": 287 / 220, "3": 287 / 199, "4": 287 / 143, "8": 287 / 85}}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -612,7 +652,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="single", choices=["single", "multirate", "tc", "serve", "sweep"])
+    ap.add_argument("--workload", default="single", choices=["single", "multirate", "tc", "serve", "sweep", "ratesweep"])
     ap.add_argument("--serve-kind", default="single", choices=["single", "multirate"],
                     help="serving: banks of the plain-form run (multi-rate is config 4)")
     ap.add_argument("--serve-blocks", type=int, default=24)
@@ -646,6 +686,8 @@ def main():
         return run_serve(args)
     if args.workload == "sweep":
         return run_sweep(args)
+    if args.workload == "ratesweep":
+        return run_ratesweep(args)
     return run_ours(args)
 
 
