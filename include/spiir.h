@@ -49,7 +49,7 @@ typedef enum {
     SPIIR_ETIMEOUT = 5,    /* a bounded device-side wait gave up; results of
                               that push are not valid, the bank stays usable */
     SPIIR_ESTATE = 6,      /* call out of order (read before any push, ...) */
-    SPIIR_EUNSUPPORTED = 7 /* valid request this build does not provide */
+    SPIIR_EUNSUPPORTED = 7 /* valid request this library does not provide */
 } spiir_status;
 
 /* Compute form. PLAIN_FP32 is the per-sample FP32 recursion (all n_levels).
@@ -60,7 +60,7 @@ typedef enum {
  * (or double-float, desc->carry).
  * TC_FP16 / TC_BF16 round the panel and strain operands to that type (FP32
  * accumulation). TC_BF16X2 (each operand split into a bf16 high and low part)
- * is reserved: this build returns SPIIR_EUNSUPPORTED for it. */
+ * is reserved: the library returns SPIIR_EUNSUPPORTED for it. */
 typedef enum {
     SPIIR_PLAIN_FP32 = 0,
     SPIIR_TC_FP16 = 1,
