@@ -20,7 +20,9 @@
 // of one round over the 32 shared-memory banks). Every lane accumulates its
 // filters' sum for T consecutive samples, then the lanes of a unit reduce
 // those T sums with a butterfly reduce-scatter (shuffles in a fixed order,
-// no atomics), which leaves each lane holding whole sums for T/G samples.
+// no atomics; a full-warp unit with T = 32 goes through the warp's shared-
+// memory rows instead), which leaves each lane holding whole sums for T/G
+// samples.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -295,7 +297,7 @@ struct OutCtx {
     int xw_log2, xw_rank, warp;
     int n_tiles;      // tiles in this segment (for the cross-warp hand-off)
     float *red;       // cross-warp buffers in shared memory
-    float2 *scratch;  // per-warp staging of small units' output rows
+    float2 *scratch;  // per-warp rows: small units' output staging, full-warp sums
 };
 
 // After the reduce-scatter for group size G a lane holds CH = max(T/G, 1)
@@ -307,7 +309,29 @@ struct OutCtx {
 template <int T, int G>
 __device__ __forceinline__ void reduce_write(float (&re)[T], float (&im)[T], int lane, int tl,
                                              int t0, int tile, const OutCtx &o) {
-    rs_round<T, T, G / 2>(re, im, lane);
+    if constexpr (T == 32 && G == 32) {
+        // A whole warp sums each of the 32 samples: through the warp's
+        // shared-memory rows (lane l stores its 32 sums in row l, then sums
+        // column l over the rows in lane order) this takes 32 stores, 32 loads
+        // and 31 adds per lane and value pair, about half the instructions of
+        // the five-round butterfly.
+        float2 *sc = o.scratch + o.warp * (32 * kRowPitch);
+#pragma unroll
+        for (int i = 0; i < T; ++i) sc[lane * kRowPitch + i] = make_float2(re[i], im[i]);
+        __syncwarp();
+        float ar = 0.f, ai = 0.f;
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            const float2 v = sc[q * kRowPitch + lane];
+            ar += v.x;
+            ai += v.y;
+        }
+        re[0] = ar;
+        im[0] = ai;
+        __syncwarp();
+    } else {
+        rs_round<T, T, G / 2>(re, im, lane);
+    }
     constexpr int NS = ilog2(G < T ? G : T);
     constexpr int NR = ilog2(G) - NS;
     constexpr int CH = (T / G) > 1 ? (T / G) : 1;
