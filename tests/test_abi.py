@@ -132,3 +132,29 @@ def test_workload_shapes_follow_recipes():
     hi = b.level < 6
     om = np.angle(b.a_re[hi] + 1j * b.a_im[hi].astype(np.float64))
     assert np.all(np.abs(om) >= math.pi / 2 - 1e-6)
+
+
+@pytest.mark.parametrize("c_name,cls", [("spiir_bank_desc", "BankDesc"), ("spiir_bank_info", "BankInfo"),
+                                         ("spiir_kernel_times", "KernelTimes")])
+def test_struct_layout_matches_the_c_header(tmp_path, c_name, cls):
+    """Every field of the ABI's structs sits at the same offset for a C
+    compiler (gcc on include/spiir.h) and for the ctypes binding."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    py = getattr(spiir, cls)
+    names = [f for f, _ in py._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"spiir.h\"\nint main(void) {\n"
+                   + "".join(f'    printf("{n} %zu\\n", offsetof({c_name}, {n}));\n' for n in names)
+                   + f'    printf("sizeof %zu\\n", sizeof({c_name}));\n    return 0;\n}}\n')
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                         text=True).stdout.splitlines())
+    for n in names:
+        assert int(out[n]) == getattr(py, n).offset, n
+    assert int(out["sizeof"]) == ctypes.sizeof(py)
