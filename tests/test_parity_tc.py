@@ -96,6 +96,25 @@ def test_double_float_carry_matches_fp64(torch_cuda, oracle_mod, mode, tol):
         _check(zdf[s], oracle_mod.spiir_single(bank, x[s]), tol, 256)
 
 
+@pytest.mark.parametrize("carry", ["fp64", "df"])
+def test_long_stream_does_not_drift(torch_cuda, oracle_mod, carry):
+    """32 s of strain in 1 s pushes (512 chunks, 32 carry batches per
+    stream) through filters with time constants up to 2000 samples: the
+    state carried from batch to batch (FP64 or double-float) keeps the error
+    within the tolerance to the end, and the last 4 s are no worse than
+    1.5x seconds 4-8 (after the start-up transient of the first chunks,
+    whose state term starts from zero)."""
+    bank = inputs.single_rate_bank(12, [64, 200, 3, 128, 256, 40, 90, 300, 17, 129, 77, 1], 1023, seed=41)
+    x = inputs.strain(1, 32 * 4096, seed=42)
+    z = gpu_snr(bank, x, push_blocks=1, mode="fp16", chunk_len=256, carry=carry)[0]
+    ref = oracle_mod.spiir_single(bank, x[0])
+    _check(z, ref, TOL_TC, 256)
+    w = 4 * 4096
+    early = rel_rms(z[:, w:2 * w], ref[:, w:2 * w]).max()
+    late = rel_rms(z[:, -w:], ref[:, -w:]).max()
+    assert late <= 1.5 * early, (early, late)
+
+
 def test_tc_matches_plain_path(torch_cuda):
     """Same bank through both forms: they agree to the TC tolerance."""
     bank = inputs.single_rate_bank(70, 64, 300, seed=3)
