@@ -214,15 +214,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 }
 
 template <bool BF16>
-__device__ __forceinline__ uint16_t to16(float x) {
-    if constexpr (BF16) {
-        return __bfloat16_as_ushort(__float2bfloat16_rn(x));
-    } else {
-        return __half_as_ushort(__float2half_rn(x));
-    }
-}
-
-template <bool BF16>
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
     if constexpr (BF16) {
         const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
