@@ -264,9 +264,17 @@ spiir_status spiir_kaiser_taps(int32_t n_taps, double atten_db, float *out);
 
 /* The rate-assignment rule of Sec. 2.2 on a base-rate pole a: the level
  * whose rate base_rate/2^i is the smallest that is >= twice the filter's band
- * edge |arg a| * base_rate / (2 pi). */
+ * edge |arg a| * base_rate / (2 pi). Returns -1 for n_levels outside [1, 30]
+ * or base_rate <= 0. */
 int32_t spiir_assign_level(float a_re, float a_im, int32_t base_rate,
                            int32_t n_levels);
+
+/* The same rule with a passband margin: the smallest available rate that is
+ * >= 2 f (1 + margin), keeping the band edge clear of the resamplers'
+ * transition band (margin = 0 is spiir_assign_level). Returns -1 for
+ * margin < 0 or not finite, n_levels outside [1, 30] or base_rate <= 0. */
+int32_t spiir_assign_level_margin(float a_re, float a_im, int32_t base_rate,
+                                  int32_t n_levels, float margin);
 
 /* One-shot filtering that allocates no device memory. The paper has no
  * counterpart: this is for callers that cannot call cudaMalloc, such as code

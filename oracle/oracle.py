@@ -52,6 +52,8 @@ def lib():
         _lib.spiir_oracle_kaiser_taps.argtypes = [i32, d, p]
         _lib.spiir_oracle_assign_level.restype = i32
         _lib.spiir_oracle_assign_level.argtypes = [d, d, i32, i32]
+        _lib.spiir_oracle_assign_level_margin.restype = i32
+        _lib.spiir_oracle_assign_level_margin.argtypes = [d, d, i32, i32, d]
         _lib.spiir_oracle_align_delay.restype = i64
         _lib.spiir_oracle_align_delay.argtypes = [i32, i32, i32, i32, i32]
         _lib.spiir_oracle_single.restype = ctypes.c_int
@@ -92,9 +94,15 @@ def kaiser_taps(n_taps: int = 32, atten_db: float = 60.0) -> np.ndarray:
     return out
 
 
-def assign_level(a_re: float, a_im: float, base_rate: int, n_levels: int) -> int:
-    return int(lib().spiir_oracle_assign_level(float(a_re), float(a_im),
-                                               int(base_rate), int(n_levels)))
+def assign_level(a_re: float, a_im: float, base_rate: int, n_levels: int,
+                 margin: float = 0.0) -> int:
+    """Sec. 2.2: the smallest available rate >= 2 f (1 + margin), f the band
+    edge |arg a| * base_rate / (2 pi); margin = 0 is the paper's rule."""
+    if margin == 0.0:
+        return int(lib().spiir_oracle_assign_level(float(a_re), float(a_im),
+                                                   int(base_rate), int(n_levels)))
+    return int(lib().spiir_oracle_assign_level_margin(float(a_re), float(a_im), int(base_rate),
+                                                      int(n_levels), float(margin)))
 
 
 def align_delay(level: int, n_levels: int, n_taps: int = 32, align: bool = True,

@@ -26,7 +26,9 @@
  *                            window parameter from Kaiser's published
  *                            attenuation formula, I0 by its power series.
  *   spiir_oracle_assign_level Sec. 2.2: the filter's band edge from arg(a),
- *                            its Nyquist rate rounded up to an available rate.
+ *                            its Nyquist rate rounded up to an available rate
+ *                            (spiir_oracle_assign_level_margin: with an
+ *                            optional passband margin).
  *
  * Readings where the paper is silent (stated once here, used throughout):
  *   - filter state starts at zero and x[n] = 0 for n < 0;
@@ -105,13 +107,24 @@ int spiir_oracle_kaiser_taps(int32_t n_taps, double atten_db, float *out) {
 /* Rate assignment (Sec. 2.2)                                          */
 /* ------------------------------------------------------------------ */
 
+int32_t spiir_oracle_assign_level_margin(double a_re, double a_im, int32_t base_rate,
+                                         int32_t n_levels, double margin);
+
 /* a is the base-rate pole. Its band edge is f = |arg a| * base_rate / (2 pi);
  * the filter needs a rate of at least 2 f (Nyquist); the chosen level is the
  * one with the smallest available rate base_rate / 2^i that is >= 2 f. */
 int32_t spiir_oracle_assign_level(double a_re, double a_im, int32_t base_rate,
                                   int32_t n_levels) {
+    return spiir_oracle_assign_level_margin(a_re, a_im, base_rate, n_levels, 0.0);
+}
+
+/* The same rule with a passband margin (an optional knob; the paper's rule
+ * is margin = 0): the rate must be at least 2 f (1 + margin), so that the
+ * band edge stays clear of the resamplers' transition band. */
+int32_t spiir_oracle_assign_level_margin(double a_re, double a_im, int32_t base_rate,
+                                         int32_t n_levels, double margin) {
     double f = fabs(atan2(a_im, a_re)) * (double)base_rate / (2.0 * ORACLE_PI);
-    double need = 2.0 * f;
+    double need = 2.0 * f * (1.0 + margin);
     for (int32_t i = n_levels - 1; i >= 0; --i) {
         double rate = (double)base_rate / (double)(1 << i);
         if (rate >= need) return i;

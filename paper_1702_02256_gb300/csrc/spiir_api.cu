@@ -1421,10 +1421,18 @@ spiir_status spiir_kaiser_taps(int32_t n_taps, double atten_db, float *out) {
 }
 
 int32_t spiir_assign_level(float a_re, float a_im, int32_t base_rate, int32_t n_levels) {
+    return spiir_assign_level_margin(a_re, a_im, base_rate, n_levels, 0.f);
+}
+
+int32_t spiir_assign_level_margin(float a_re, float a_im, int32_t base_rate, int32_t n_levels,
+                                  float margin) {
+    if (!(margin >= 0.f) || !std::isfinite(margin) || n_levels < 1 || n_levels > 30 || base_rate <= 0)
+        return -1;
     const double f = std::fabs(std::atan2((double)a_im, (double)a_re)) * base_rate / (2.0 * M_PI);
+    const double need = 2.0 * f * (1.0 + (double)margin);
     int32_t lv = 0;
     for (int32_t i = 0; i < n_levels; ++i)
-        if ((double)base_rate / (double)(1 << i) >= 2.0 * f) lv = i;
+        if ((double)base_rate / (double)(1 << i) >= need) lv = i;
     return lv;
 }
 

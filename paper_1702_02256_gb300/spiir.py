@@ -83,6 +83,7 @@ _SIGS = {
     "spiir_bank_destroy": (None, [_c_void_p]),
     "spiir_kaiser_taps": (_i32, [_i32, _f64, _c_void_p]),
     "spiir_assign_level": (_i32, [_f32, _f32, _i32, _i32]),
+    "spiir_assign_level_margin": (_i32, [_f32, _f32, _i32, _i32, _f32]),
     "spiir_last_error": (ctypes.c_char_p, []),
     "spiir_filter_noalloc": (_i32, [ctypes.POINTER(BankDesc), _c_void_p, _i64, _c_void_p, _c_void_p]),
     "spiir_bank_enable_timing": (_i32, [_c_void_p, _i32]),
@@ -126,8 +127,10 @@ def kaiser_taps(n_taps: int = 32, atten_db: float = 60.0) -> np.ndarray:
     return out
 
 
-def assign_level(a_re: float, a_im: float, base_rate: int, n_levels: int) -> int:
-    return int(lib().spiir_assign_level(a_re, a_im, base_rate, n_levels))
+def assign_level(a_re: float, a_im: float, base_rate: int, n_levels: int, margin: float = 0.0) -> int:
+    if margin == 0.0:
+        return int(lib().spiir_assign_level(a_re, a_im, base_rate, n_levels))
+    return int(lib().spiir_assign_level_margin(a_re, a_im, base_rate, n_levels, margin))
 
 
 def make_desc(bank, n_streams: int = 1, block_len: int = 4096, max_push_blocks: int = 1,

@@ -52,6 +52,21 @@ def test_assign_level_matches_oracle(oracle_mod):
                 float(ar), float(ai), 4096, L)
 
 
+def test_assign_level_margin_matches_oracle(oracle_mod):
+    rng = np.random.default_rng(1)
+    for _ in range(2000):
+        th = rng.uniform(-math.pi, math.pi)
+        r = rng.uniform(0.5, 1.0)
+        ar, ai = np.float32(r * math.cos(th)), np.float32(r * math.sin(th))
+        m = float(np.float32(rng.choice([0.0, 0.01, 0.05, 0.2, 1.0])))
+        for L in (1, 4, 7):
+            assert spiir.assign_level(ar, ai, 4096, L, margin=m) == oracle_mod.assign_level(
+                float(ar), float(ai), 4096, L, margin=m)
+    assert spiir.lib().spiir_assign_level_margin(0.5, 0.5, 4096, 7, -0.1) == -1
+    assert spiir.lib().spiir_assign_level_margin(0.5, 0.5, 4096, 0, 0.1) == -1
+    assert spiir.lib().spiir_assign_level(0.5, 0.5, 0, 7) == -1
+
+
 def _status(bank, **kw):
     d, _k = spiir.make_desc(bank, **kw)
     info = spiir.BankInfo()

@@ -345,6 +345,28 @@ def test_assign_level_table4(oracle_mod):
     assert oracle_mod.assign_level(0.99, 0.001, R0, L) == L - 1
 
 
+def test_assign_level_margin(oracle_mod):
+    """The margin knob: margin 0 is the paper's rule; a band edge at 95% of a
+    rate's Nyquist frequency stays at that rate for margins below 1/0.95 - 1
+    and moves one rate up above it (closed form); more margin never lowers
+    the rate."""
+    R0, L = 4096, 7
+    rng = np.random.default_rng(3)
+    for _ in range(500):
+        th = rng.uniform(-math.pi, math.pi)
+        ar, ai = 0.99 * math.cos(th), 0.99 * math.sin(th)
+        assert oracle_mod.assign_level(ar, ai, R0, L, margin=0.0) == oracle_mod.assign_level(ar, ai, R0, L)
+        levels = [oracle_mod.assign_level(ar, ai, R0, L, margin=m) for m in (0.0, 0.02, 0.1, 0.5, 1.0)]
+        assert all(b <= a for a, b in zip(levels, levels[1:])), levels
+    for lv in range(1, L):
+        f = 0.95 * (R0 >> lv) / 2.0                 # 95% of level lv's Nyquist frequency
+        arg = 2 * math.pi * f / R0
+        ar, ai = 0.99 * math.cos(arg), 0.99 * math.sin(arg)
+        edge = 1.0 / 0.95 - 1.0
+        assert oracle_mod.assign_level(ar, ai, R0, L, margin=0.5 * edge) == lv
+        assert oracle_mod.assign_level(ar, ai, R0, L, margin=1.5 * edge) == lv - 1
+
+
 def test_cost_model_golden():
     """The cost model the roofline uses (12 flops per filter-sample) and the
     paper's worked example of it: half the filters at R/2 saves 25%."""
