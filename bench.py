@@ -123,13 +123,14 @@ def _peaks():
         return {}
 
 
-def _source_hash(kernel_file: str) -> str:
+def _source_hash(kernel_file: str, csrc: str = "") -> str:
     """First 16 hex digits of the sha256 of the kernel file followed by the
     planner (spiir_api.cu), comments and blank lines left out: the traffic
     depends on the code of both, not on their comments."""
+    csrc = csrc or os.path.join(ROOT, "paper_1702_02256_gb300", "csrc")
     h = hashlib.sha256()
     for f in (kernel_file, "spiir_api.cu"):
-        src = open(os.path.join(ROOT, "paper_1702_02256_gb300", "csrc", f)).read()
+        src = open(os.path.join(csrc, f)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         src = re.sub(r"//[^\n]*", "", src)
         h.update("\n".join(ln.rstrip() for ln in src.splitlines() if ln.strip()).encode())
