@@ -134,6 +134,24 @@ def test_plan_multirate_and_footprint():
     assert _status(bank, hbm_budget_bytes=1) == spiir.OK  # budget is checked at create
 
 
+def test_tc_footprint_counts_panels_and_state():
+    """The block form's footprint (HBM admission) includes the precomputed
+    power panel of every 128-filter tile (32 KB) and 16 bytes of carried
+    state per tile slot and stream: adding one tile to one template adds at
+    least 32 KB + 128 x 16 B x streams."""
+    counts = [1, 128, 129, 300, 0, 5, 256, 64, 65, 1000]
+    base = inputs.single_rate_bank(len(counts), counts, 500, seed=1)
+    more = inputs.single_rate_bank(len(counts), counts[:-1] + [1000 + 128], 500, seed=1)
+    tiles = lambda c: sum(-(-k // 128) for k in c)
+    assert tiles(counts[:-1] + [1128]) == tiles(counts) + 1
+    for S in (1, 2):
+        kw = dict(mode="fp16", n_streams=S, block_len=4096, max_push_blocks=1)
+        f0, f1 = spiir.footprint(base, **kw), spiir.footprint(more, **kw)
+        assert f0 >= tiles(counts) * (32768 + 128 * 16 * S)
+        assert f1 - f0 >= 32768 + 128 * 16 * S
+    assert spiir.footprint(base, mode="fp16", n_streams=1) == spiir.footprint(base, mode="bf16", n_streams=1)
+
+
 def test_workload_shapes_follow_recipes():
     w = inputs.workload(0)
     assert w["bank"].n_filters == 256 and w["x"].shape == (1, 4096)
