@@ -222,6 +222,7 @@ def _cpu_sample(w, budget_s: float, n_templates_max: int, threads: int = 0):
     dt = run(sel)
     rate = fs(sel) / dt
     sample = f"{n} of {bank.n_templates} templates, full {x.shape[0]} samples, {dt:.1f} s wall"
+    _cpu_sample.last_wall_s = dt
     return rate, sample, threads
 
 
@@ -309,10 +310,12 @@ def run_reference(args):
     rates = []
     sample = ""
     threads = 1
+    walls = []
     for i in range(args.warmup + args.steps):
         rate, sample, threads = _cpu_sample(w, per_step, 64)
         if i >= args.warmup:
             rates.append(rate)
+            walls.append(_cpu_sample.last_wall_s)
     value = float(np.mean(rates))
     bank = w["bank"]
     n = w["x"].shape[1]
@@ -321,6 +324,11 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * fs_total / value, "higher_is_better": True,
+        "ms_per_step_extrapolated": True,
+        "ms_per_step_basis": "not measured: the full step's filter-samples divided by the rate "
+                             "measured on a bounded template sample (the oracle would take this "
+                             "long for one whole step)",
+        "sample_wall_ms_per_step": 1e3 * float(np.mean(walls)),
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w["desc"], "n_templates": bank.n_templates,
                    "n_filters": bank.n_filters},
@@ -335,9 +343,13 @@ def run_reference(args):
 FORM_MODE = {"plain": "plain", "fp16": "fp16", "bf16": "bf16"}
 
 
-def _measure(w, form, args, dev, dist, sampler, rank, ws):
+def _measure(w, form, args, dev, dist, sampler, rank, ws, err=None):
     """Time one form of the filtering on workload w. Returns a dict of the
-    device-timed throughput, per-kernel times, latency and end-to-end rate."""
+    device-timed throughput, per-kernel times, latency and end-to-end rate.
+    err = (template indices, samples): afterwards the state is reset and the
+    first samples are pushed again, and the SNR of those templates is
+    returned as "err_z" (complex64 [streams, templates, samples]) for the
+    comparison with the oracle."""
     import torch
     from paper_1702_02256_gb300 import spiir
     bank = w["bank"]
@@ -411,6 +423,18 @@ def _measure(w, form, args, dev, dist, sampler, rank, ws):
         for p in xh_pushes:
             b.push_host(p, z_out=zh)
     e2e_s = replicas.max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist, dev)
+    err_z = None
+    if err is not None:
+        sel, n_err = err
+        b.reset()
+        idx = torch.from_numpy(np.asarray(sel, np.int64)).to(dev)
+        zz = torch.empty((S, bank.n_templates, push_len), dtype=torch.complex64, device=dev)
+        parts = []
+        for p in pushes[:max(1, n_err // push_len)]:
+            b.push(p, stream_id=-1)
+            b.read(push_len, stream_id=-1, out=zz)
+            parts.append(zz.index_select(1, idx).cpu().numpy())
+        err_z = np.concatenate(parts, axis=-1)
     b.sync_status()
     b.close()
     del flush
@@ -421,7 +445,7 @@ def _measure(w, form, args, dev, dist, sampler, rank, ws):
                 rtt=ws * bank.n_templates * S * (n / 4096.0) / (ms_per_step / 1e3),
                 p50=float(np.percentile(lat, 50)), p99=float(np.percentile(lat, 99)),
                 e2e=ws * fs_per_step / e2e_s, h2d=int(S * n * 4),
-                d2h=int(S * bank.n_templates * n * 8), wall=(t_wall0, t_wall1))
+                d2h=int(S * bank.n_templates * n * 8), wall=(t_wall0, t_wall1), err_z=err_z)
 
 
 def _form_desc(form: str, args) -> str:
@@ -430,8 +454,44 @@ def _form_desc(form: str, args) -> str:
     return f"tensor-core block form ({form}, {args.carry} carry between chunk batches)"
 
 
-def _roofline(m, w, args, peaks, sms):
+def _oracle_error(w, sel, z):
+    """SNR error of a GPU run against the FP64 oracle (part of the CPU
+    baseline leg: the oracle runs on the host cores): per template and
+    stream, RMS error over RMS oracle SNR, on the sampled templates and the
+    first samples of the workload."""
+    from oracle import oracle
+    bank = w["bank"]
+    n = z.shape[-1]
+    errs = []
+    for s in range(z.shape[0]):
+        x = w["x"][s, :n]
+        if bank.n_levels > 1:
+            ref = oracle.spiir_multirate(bank, x, h_down=w.get("h_down"), h_up=w.get("h_up"),
+                                         templates=sel)
+        else:
+            ref = oracle.spiir_single(bank, x, templates=sel)
+        num = np.sqrt(np.mean(np.abs(z[s] - ref) ** 2, axis=-1))
+        den = np.sqrt(np.mean(np.abs(ref) ** 2, axis=-1))
+        errs.append(num / np.where(den > 0, den, 1.0))
+    e = np.concatenate(errs)
+    return {"max": float(e.max()), "median": float(np.median(e)), "templates": int(len(sel)),
+            "streams": int(z.shape[0]), "seconds": n / 4096.0,
+            "measure": "per template and stream: RMS(z - z_oracle) / RMS(z_oracle), FP64 oracle"}
+
+
+def _err_sample(w, k=8, seconds=2):
+    """Templates and samples of the oracle comparison: k spread templates,
+    the first `seconds` seconds (at least one push)."""
+    T = w["bank"].n_templates
+    sel = np.unique(np.linspace(0, T - 1, k).round().astype(np.int32))
+    push_len = w["block_len"] * w["push_blocks"]
+    n = max(push_len, (seconds * 4096 // push_len) * push_len)
+    return sel, min(n, w["x"].shape[1])
+
+
+def _roofline(m, w, args, peaks, sms, wl=None):
     """Roofline of the dominant kernel of one measured form."""
+    wl = wl or args.workload
     kt = m["kt"]
     bank = w["bank"]
     if m["form"] == "plain":
@@ -441,7 +501,7 @@ def _roofline(m, w, args, peaks, sms):
         ach = FLOPS_PER_FS * m["fs_per_step"] * m["steps"] / nl / (ms / nl / 1e3) / 1e12 if nl else 0.0
         return {"bound": "alu", "kernel": "recur_kernel", "achieved": ach, "peak": peak,
                 "unit": "TFLOP/s", "frac": ach / peak if peak else None,
-                "traffic": _traffic("spiir_plain.cu", f"recur_{args.workload}",
+                "traffic": _traffic("spiir_plain.cu", f"recur_{wl}",
                                     m["info"].get("kernel_variant")),
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz "
                               f"(sm_max_mhz of measured peaks) / {LANE_OPS_PER_FS} lane-ops x "
@@ -460,13 +520,40 @@ def _roofline(m, w, args, peaks, sms):
         name, ach = "tc_fir_kernel", fir_flops / (fir_ms / 1e3) / 1e12 if fir_ms else 0.0
     else:
         name, ach = "tc_carry_kernel", carry_flops / (car_ms / 1e3) / 1e12 if car_ms else 0.0
-    key = ("tc_fir" if name == "tc_fir_kernel" else "tc_carry") + f"_{args.workload}"
+    key = ("tc_fir" if name == "tc_fir_kernel" else "tc_carry") + f"_{wl}"
     return {"bound": "tensor", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
             "frac": ach / peak, "traffic": _traffic("spiir_tc.cu", key),
             "peak_basis": "measured dense bf16 burst (cuBLAS) of MEASURED_PEAKS; fp16 has the same "
                           "nominal dense rate",
             "fir_tflops": fir_flops / (fir_ms / 1e3) / 1e12 if fir_ms else None,
             "carry_tflops": carry_flops / (car_ms / 1e3) / 1e12 if car_ms else None}
+
+
+def _workload_desc(name):
+    return {"tc": "single-rate 8000 templates x 256 filters, 2 streams, 4096 Hz, 8 s per step "
+                  "(8 pushes of 1 s of both streams), delays 0-1023, chunk length 256"}[name]
+
+
+def _leg_json(m, w, wl, args, peaks, sms, plain=None, err=None):
+    """One measured form of a workload as a JSON object: rate, step time,
+    latency, roofline of its dominant kernel, end-to-end rate and SNR error
+    against the oracle; speed-up over the plain form's leg when given."""
+    o = {
+        "form": _form_desc(m["form"], args),
+        "value": m["value"], "unit": UNIT, "ms_per_step": m["ms_per_step"], "steps": m["steps"],
+        "real_time_templates": m["rtt"],
+        "p50_block_latency_ms": m["p50"], "p99_block_latency_ms": m["p99"],
+        "roofline": _roofline(m, w, args, peaks, sms, wl),
+        "e2e": {"value": m["e2e"], "unit": UNIT, "h2d_bytes_per_step": m["h2d"],
+                "d2h_bytes_per_step": m["d2h"]},
+        "kernel_ms": {k: v[0] for k, v in m["kt"].items()},
+        "gpu_launches": int(sum(c for _, c in m["kt"].values())),
+    }
+    if plain is not None:
+        o["speedup_vs_plain"] = m["value"] / plain["value"]
+    if m.get("err_z") is not None and err is not None:
+        o["snr_error_vs_oracle"] = _oracle_error(w, err[0], m["err_z"])
+    return o
 
 
 def run_ours(args):
@@ -489,10 +576,20 @@ def run_ours(args):
         sampler.start()
         time.sleep(0.5)
     form = args.form or ("fp16" if args.workload == "tc" else "plain")
-    main = _measure(w, form, args, dev, dist, sampler, rank, ws)
+    lead = rank == 0 and ws == 1      # oracle comparisons: one GPU, rank 0
+    err = _err_sample(w) if lead else None
+    main = _measure(w, form, args, dev, dist, sampler, rank, ws, err=err)
     chosen = None
     if args.chosen and args.chosen != form and w["bank"].n_levels == 1:
-        chosen = _measure(w, args.chosen, args, dev, dist, sampler, rank, ws)
+        chosen = _measure(w, args.chosen, args, dev, dist, sampler, rank, ws, err=err)
+    # the block-parallel configuration (8000 x 256 filters, 2 streams, 1 s
+    # pushes): the plain form and every requested tensor-core form
+    c3 = []
+    if args.workload == "single" and args.config3:
+        w3 = _workload("tc", rank)
+        err3 = _err_sample(w3) if lead else None
+        for f3 in ["plain"] + [f for f in args.config3.split(",") if f]:
+            c3.append((f3, _measure(w3, f3, args, dev, dist, sampler, rank, ws, err=err3)))
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -549,16 +646,16 @@ def run_ours(args):
         "gpu_launches": int(sum(c for _, c in kt.values())),
         "clocks": clocks,
     }
+    if main["err_z"] is not None:
+        line["snr_error_vs_oracle"] = _oracle_error(w, err[0], main["err_z"])
     if chosen:
-        line["chosen"] = {
-            "form": _form_desc(chosen["form"], args),
-            "value": chosen["value"], "unit": UNIT, "ms_per_step": chosen["ms_per_step"],
-            "real_time_templates": chosen["rtt"],
-            "p50_block_latency_ms": chosen["p50"], "p99_block_latency_ms": chosen["p99"],
-            "speedup_vs_plain": chosen["value"] / main["value"],
-            "roofline": _roofline(chosen, w, args, peaks, sms),
-            "e2e": {"value": chosen["e2e"], "unit": UNIT},
-            "kernel_ms": {k: v[0] for k, v in chosen["kt"].items()},
+        line["chosen"] = _leg_json(chosen, w, args.workload, args, peaks, sms, main, err)
+    if c3:
+        plain3 = c3[0][1]
+        line["config3"] = {
+            "workload": _workload_desc("tc"),
+            "legs": {f: _leg_json(m, w3, "tc", args, peaks, sms, plain3 if f != "plain" else None, err3)
+                     for f, m in c3},
         }
     print(json.dumps(line), flush=True)
     if dist:
@@ -663,6 +760,10 @@ def main():
                     help="compute form of the headline number (default: plain; fp16 for tc)")
     ap.add_argument("--chosen", default="fp16", choices=["", "plain", "fp16", "bf16"],
                     help="second form measured on the same workload and reported as 'chosen'")
+    ap.add_argument("--config3", default="fp16",
+                    help="default workload only: also measure the 8000 x 256 two-stream "
+                         "configuration with the plain form and these tensor-core forms "
+                         "(comma-separated; empty: skip)")
     ap.add_argument("--resampler", default="default", choices=["default", "paper"],
                     help="multi-rate: 32/32-tap 60 dB pair (default) or the paper's "
                          "384-tap 100 dB decimator with the 32-tap interpolator")

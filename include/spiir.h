@@ -14,7 +14,9 @@
  * kaiser_window_filtering), a filter at level i runs at base_rate/2^i on the
  * level-i strain, and from the lowest rate up each rate's sum is upsampled by
  * 2 and added to the next rate's sum; level i's own sum is delayed by
- * D_i = (T-1) + 2*D_{i+1} (D_H = 0) so that the levels line up.
+ * D_i = (Td-1)/2 + (Tu-1)/2 + 2*D_{i+1} (D_H = 0; Td, Tu the decimator and
+ * interpolator lengths, whose linear-phase round trip this is) so that the
+ * levels line up.
  *
  * Conventions shared by every call:
  *   - Complex arrays on the device are complex64: interleaved (re, im) float32.
@@ -83,7 +85,14 @@ typedef struct {
     const float *b_re, *b_im;     /* gain b_k */
     const int32_t *delay;         /* d_k >= 0, samples at the filter's rate */
     const int32_t *template_id;   /* in [0, n_templates) */
-    const int8_t *level;          /* in [0, n_levels); NULL = all level 0 */
+    const int8_t *level;          /* in [0, n_levels); NULL = all level 0.
+                                     There is no "assign at create" value
+                                     (-1 is EINVAL): running a designed
+                                     filter at a lower rate changes its
+                                     pole, gain and delay, which is filter
+                                     design; spiir_assign_level gives the
+                                     Sec. 2.2 rule to callers that convert
+                                     their filters themselves */
     const float *h_down, *h_up;   /* decimator taps (n_taps of them) and
                                      interpolator taps (n_taps_up); NULL =
                                      built-in 60 dB Kaiser low-passes */
@@ -277,9 +286,11 @@ int32_t spiir_assign_level_margin(float a_re, float a_im, int32_t base_rate,
                                   int32_t n_levels, float margin);
 
 /* One-shot filtering that allocates no device memory. The paper has no
- * counterpart: this is for callers that cannot call cudaMalloc, such as code
- * that runs while a CUDA graph is being captured on its stream, or a host
- * framework whose real-time thread must not allocate device memory.
+ * counterpart: this is for callers that cannot call cudaMalloc, such as a
+ * host framework whose real-time thread must not allocate device memory (an
+ * allocation can block on the driver for an unbounded time), or a process
+ * whose device memory is divided up in advance, so that an allocation outside
+ * its own pools fails.
  *
  * Filters x_dev (device float32 [n_samples], one stream) with the bank that
  * desc describes (plain FP32 form, n_streams = 1), starting from zero filter
@@ -287,7 +298,9 @@ int32_t spiir_assign_level_margin(float a_re, float a_im, int32_t base_rate,
  * [n_templates][n_samples], the layout of spiir_read_snr) -- the SNR that
  * spiir_bank_create + spiir_push_block + spiir_read_snr would give for the
  * same description and samples. n_samples: a positive multiple of
- * 4 * 2^(n_levels-1). The caller owns x_dev and z_dev.
+ * 4 * 2^(n_levels-1). desc->block_len, max_push_blocks and tune >= 0 are
+ * ignored (one push of n_samples, built-in tile choice; tune < 0 still
+ * forces a variant). The caller owns x_dev and z_dev.
  *
  * All device memory it uses is one fixed 32 MiB __device__ array that every
  * GPU loading the library reserves until the process exits. A bank and length
@@ -295,9 +308,13 @@ int32_t spiir_assign_level_margin(float a_re, float a_im, int32_t base_rate,
  * message giving both sizes. Every call shares that array and leaves its
  * contents behind (it clears what must start at zero), so calls whose work
  * overlaps on the GPU -- on two streams, or from two host threads -- race and
- * must be serialised by the caller. The first call on a device looks up the
- * array's device address; make that first call before any stream capture.
- * Host-side packing uses ordinary host memory. */
+ * must be serialised by the caller. A bounded device-side wait that gives up
+ * (possible only when such calls overlap) leaves a wrong z and is not
+ * reported by this call. The first call on a device, with that device
+ * current, looks up the array's device address (first calls from several
+ * host threads are safe); make that first call before any stream capture.
+ * The coefficients are packed in ordinary host memory and copied in on
+ * cuda_stream. */
 spiir_status spiir_filter_noalloc(const spiir_bank_desc *desc, const float *x_dev,
                                   int64_t n_samples, void *z_dev, void *cuda_stream);
 

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -595,7 +596,7 @@ spiir_status upload(T **dst, const std::vector<T> &src, cudaStream_t s) {
 
 struct GraphEntry {
     int s0, count;
-    int64_t n, n_prev;
+    int64_t n, n_prev, zoff;
     cudaGraphExec_t exec;
 };
 
@@ -618,8 +619,11 @@ struct spiir_bank {
     unsigned int *queue = nullptr, *prog = nullptr;
     int ctas_per_sm = 1, n_sms = 1;
     cudaStream_t cap = nullptr;             // private stream for graph capture
+    cudaStream_t copy = nullptr;            // host push: device-to-host copies
+    cudaEvent_t piece_done[4] = {};         // host push: a piece's SNR is in the ring
     std::vector<GraphEntry> graphs;
-    std::vector<int64_t> last_n;
+    std::vector<int64_t> last_n;            // samples of the last kernel push (strain history)
+    std::vector<int64_t> ring_n;            // samples of the last call's push held in the ring
     std::vector<char> out_valid;            // the output ring holds a push of the stream
     uint64_t fingerprint = 0;               // of the description, for state import
     int64_t footprint = 0;
@@ -657,6 +661,15 @@ struct spiir_bank {
             cudaStreamDestroy(cap);
             cap = nullptr;
         }
+        if (copy) {
+            cudaStreamDestroy(copy);
+            copy = nullptr;
+        }
+        for (auto &e : piece_done)
+            if (e) {
+                cudaEventDestroy(e);
+                e = nullptr;
+            }
     }
 };
 
@@ -724,8 +737,11 @@ void level_args(const spiir_bank *b, int64_t n, int64_t n_prev, LevelArgs *lev) 
 }
 
 // The kernels of one push (no host state changes).
+// zoff: first output-ring column this push writes (0 for an ordinary push;
+// the pieces of a pipelined host push write consecutive column ranges).
 spiir_status launch_sequence(spiir_bank *b, int s0, int count, const float *x, int64_t x_stride,
-                             int64_t n, int64_t n_prev, cudaStream_t st, bool stall_test) {
+                             int64_t n, int64_t n_prev, cudaStream_t st, bool stall_test,
+                             int64_t zoff = 0) {
     const Plan &p = b->p;
     PrologueArgs pa{};
     pa.queue = b->queue;
@@ -777,7 +793,7 @@ spiir_status launch_sequence(spiir_bank *b, int s0, int count, const float *x, i
         ra.xbuf_stream_stride = p.xbuf_stream_stride;
         ra.partial = b->partial;
         ra.partial_stream_stride = p.part_stream_stride;
-        ra.z = b->z;
+        ra.z = b->z + zoff;
         ra.z_row_stride = p.ring_len;
         ra.z_stream_stride = (int64_t)b->d.n_templates * p.ring_len;
         ra.scale = b->scale;
@@ -800,7 +816,7 @@ spiir_status launch_sequence(spiir_bank *b, int s0, int count, const float *x, i
         ca.partial_stream_stride = p.part_stream_stride;
         ca.ubuf = b->ubuf;
         ca.ubuf_stream_stride = p.ubuf_stream_stride;
-        ca.z = b->z;
+        ca.z = b->z + zoff;
         ca.z_row_stride = p.ring_len;
         ca.z_stream_stride = (int64_t)b->d.n_templates * p.ring_len;
         ca.scale = b->scale;
@@ -822,11 +838,11 @@ spiir_status launch_sequence(spiir_bank *b, int s0, int count, const float *x, i
 // staging buffer on the caller's stream and one graph (captured once per
 // stream set, length and previous length) launches all kernels.
 spiir_status push_graph(spiir_bank *b, int s0, int count, const float *x, int64_t x_stride,
-                        int64_t n, cudaStream_t st) {
+                        int64_t n, cudaStream_t st, int64_t zoff) {
     const int64_t n_prev = b->last_n[s0];
     GraphEntry *ge = nullptr;
     for (auto &g : b->graphs)
-        if (g.s0 == s0 && g.count == count && g.n == n && g.n_prev == n_prev) ge = &g;
+        if (g.s0 == s0 && g.count == count && g.n == n && g.n_prev == n_prev && g.zoff == zoff) ge = &g;
     if (!ge) {
         if (b->graphs.size() >= 16) {
             cudaGraphExecDestroy(b->graphs.front().exec);
@@ -835,7 +851,7 @@ spiir_status push_graph(spiir_bank *b, int s0, int count, const float *x, int64_
         cudaGraph_t g = nullptr;
         CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
         spiir_status stc = launch_sequence(b, s0, count, b->xstage + (int64_t)s0 * n, n, n, n_prev,
-                                           b->cap, false);
+                                           b->cap, false, zoff);
         cudaError_t e = cudaStreamEndCapture(b->cap, &g);
         if (stc) {
             if (g) cudaGraphDestroy(g);
@@ -846,7 +862,7 @@ spiir_status push_graph(spiir_bank *b, int s0, int count, const float *x, int64_
         e = cudaGraphInstantiate(&exec, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return fail(SPIIR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
-        b->graphs.push_back(GraphEntry{s0, count, n, n_prev, exec});
+        b->graphs.push_back(GraphEntry{s0, count, n, n_prev, zoff, exec});
         ge = &b->graphs.back();
     }
     float *dst = b->xstage + (int64_t)s0 * n;
@@ -863,12 +879,12 @@ spiir_status push_graph(spiir_bank *b, int s0, int count, const float *x, int64_
 }
 
 spiir_status push_plain(spiir_bank *b, int s0, int count, const float *x, int64_t x_stride,
-                        int64_t n, cudaStream_t st, bool stall_test = false) {
+                        int64_t n, cudaStream_t st, bool stall_test = false, int64_t zoff = 0) {
     spiir_status r;
     if (b->cap && !b->timer->on && !stall_test)
-        r = push_graph(b, s0, count, x, x_stride, n, st);
+        r = push_graph(b, s0, count, x, x_stride, n, st, zoff);
     else
-        r = launch_sequence(b, s0, count, x, x_stride, n, b->last_n[s0], st, stall_test);
+        r = launch_sequence(b, s0, count, x, x_stride, n, b->last_n[s0], st, stall_test, zoff);
     if (r) return r;
     for (int q = s0; q < s0 + count; ++q) b->last_n[q] = n;
     return SPIIR_OK;
@@ -931,6 +947,7 @@ spiir_status build_bank(const spiir_bank_desc *desc, int variant, cudaStream_t s
         lib_kaiser_taps(ntu, 60.0, b->h_up.data());
     }
     b->last_n.assign(desc->n_streams, 0);
+    b->ring_n.assign(desc->n_streams, 0);
     b->out_valid.assign(desc->n_streams, 0);
     b->fingerprint = desc_fingerprint(desc);
     if (!b->timer) b->timer = new KernelTimer();
@@ -1037,7 +1054,7 @@ spiir_status spiir_push_block(spiir_bank_t b, int32_t stream_id, const float *x_
         spiir_status st = spiir_tc_push(b->tc, s0, cnt, x_dev, n_samples, n_samples, s, b->timer);
         if (st) return fail(st, "%s", spiir_tc_last_error());
         for (int q = s0; q < s0 + cnt; ++q) {
-            b->last_n[q] = n_samples;
+            b->last_n[q] = b->ring_n[q] = n_samples;
             b->out_valid[q] = 1;
         }
         return SPIIR_OK;
@@ -1053,7 +1070,10 @@ spiir_status spiir_push_block(spiir_bank_t b, int32_t stream_id, const float *x_
             if (st) return st;
         }
     }
-    for (int q = s0; q < s0 + cnt; ++q) b->out_valid[q] = 1;
+    for (int q = s0; q < s0 + cnt; ++q) {
+        b->ring_n[q] = n_samples;
+        b->out_valid[q] = 1;
+    }
     return SPIIR_OK;
 }
 
@@ -1070,7 +1090,7 @@ spiir_status spiir_read_snr(spiir_bank_t b, int32_t stream_id, void *z_dev, int6
         if (b->last_n[q] == 0) return fail(SPIIR_ESTATE, "nothing pushed on stream %d", q);
         if (!b->out_valid[q])
             return fail(SPIIR_ESTATE, "no push on stream %d since its state was imported", q);
-        if (n_samples <= 0 || n_samples > b->last_n[q])
+        if (n_samples <= 0 || n_samples > b->ring_n[q])
             return fail(SPIIR_EINVAL, "n_samples must be in [1, samples of the last push]");
     }
     const int T = b->d.n_templates;
@@ -1083,7 +1103,7 @@ spiir_status spiir_read_snr(spiir_bank_t b, int32_t stream_id, void *z_dev, int6
             ring = b->p.ring_len;
             src = b->z + (int64_t)q * T * ring;
         }
-        src += b->last_n[q] - n_samples;
+        src += b->ring_n[q] - n_samples;
         char *dst = (char *)z_dev + (int64_t)(q - s0) * T * n_samples * sizeof(float2);
         CUDA_TRY(cudaMemcpy2DAsync(dst, n_samples * sizeof(float2), src, ring * sizeof(float2),
                                    n_samples * sizeof(float2), T, cudaMemcpyDeviceToDevice, s));
@@ -1113,7 +1133,7 @@ spiir_status spiir_state_reset(spiir_bank_t b, int32_t stream_id, void *cuda_str
                                      cnt * p.ubuf_stream_stride * sizeof(float2), s));
     }
     for (int q = s0; q < s0 + cnt; ++q) {
-        b->last_n[q] = 0;
+        b->last_n[q] = b->ring_n[q] = 0;
         b->out_valid[q] = 0;
     }
     return SPIIR_OK;
@@ -1254,6 +1274,7 @@ spiir_status spiir_state_import(spiir_bank_t b, int32_t stream_id, const void *s
             CUDA_TRY(cudaStreamSynchronize(s));
         }
         b->last_n[q] = last_n;
+        b->ring_n[q] = 0;
         b->out_valid[q] = 0;
     }
     return SPIIR_OK;
@@ -1271,7 +1292,7 @@ spiir_status spiir_read_snr_abs(spiir_bank_t b, int32_t stream_id, float *out_de
         if (b->last_n[q] == 0) return fail(SPIIR_ESTATE, "nothing pushed on stream %d", q);
         if (!b->out_valid[q])
             return fail(SPIIR_ESTATE, "no push on stream %d since its state was imported", q);
-        if (n_samples <= 0 || n_samples > b->last_n[q])
+        if (n_samples <= 0 || n_samples > b->ring_n[q])
             return fail(SPIIR_EINVAL, "n_samples must be in [1, samples of the last push]");
     }
     cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -1285,7 +1306,7 @@ spiir_status spiir_read_snr_abs(spiir_bank_t b, int32_t stream_id, float *out_de
             ring = b->p.ring_len;
             src = b->z + (int64_t)q * T * ring;
         }
-        CUDA_TRY(spiir_launch_abs(src + b->last_n[q] - n_samples, ring, T, n_samples, norm_dev,
+        CUDA_TRY(spiir_launch_abs(src + b->ring_n[q] - n_samples, ring, T, n_samples, norm_dev,
                                   out_dev + (int64_t)(q - s0) * T * n_samples, s));
     }
     return SPIIR_OK;
@@ -1301,27 +1322,70 @@ spiir_status spiir_push_block_host(spiir_bank_t b, int32_t stream_id, const floa
         n_samples > (int64_t)b->d.block_len * b->d.max_push_blocks)
         return fail(SPIIR_EINVAL, "bad n_samples");
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    const int cnt = stream_id < 0 ? b->d.n_streams : 1;
-    float *stage = b->tc ? spiir_tc_stage(b->tc) : b->xstage;
-    CUDA_TRY(cudaMemcpyAsync(stage, x_host, cnt * n_samples * sizeof(float),
-                             cudaMemcpyHostToDevice, s));
-    spiir_status st = spiir_push_block(b, stream_id, stage, n_samples, cuda_stream);
-    if (st) return st;
     const int s0 = stream_id < 0 ? 0 : stream_id;
+    const int cnt = stream_id < 0 ? b->d.n_streams : 1;
     const int T = b->d.n_templates;
-    for (int q = s0; q < s0 + cnt; ++q) {
-        const float2 *src;
-        int64_t ring;
-        if (b->tc) {
-            src = spiir_tc_output(b->tc, q, &ring);
-        } else {
-            ring = b->p.ring_len;
-            src = b->z + (int64_t)q * T * ring;
-        }
-        char *dst = (char *)z_host + (int64_t)(q - s0) * T * n_samples * sizeof(float2);
-        CUDA_TRY(cudaMemcpy2DAsync(dst, n_samples * sizeof(float2), src, ring * sizeof(float2),
-                                   n_samples * sizeof(float2), T, cudaMemcpyDeviceToHost, s));
+    // A push of several blocks runs as up to four pieces of whole blocks.
+    // Piece i writes output-ring columns [off_i, off_i + n_i) (pushes compose
+    // exactly: block-split invariance), and its SNR is copied back on a
+    // second stream while piece i + 1 computes. The ring then holds the whole
+    // push, as after one push of n_samples.
+    const int64_t n_blocks = n_samples / b->d.block_len;
+    const int n_pieces = (int)std::min<int64_t>(4, n_blocks);
+    if (n_pieces > 1 && !b->copy) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&b->copy, cudaStreamNonBlocking));
+        for (auto &e : b->piece_done) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
+    int64_t off = 0;
+    for (int i = 0; i < n_pieces; ++i) {
+        bool same = true;
+        for (int q = s0; q < s0 + cnt; ++q) same &= (b->last_n[q] == b->last_n[s0]);
+        const int64_t n_i = (n_blocks * (i + 1) / n_pieces - n_blocks * i / n_pieces) * b->d.block_len;
+        // strain of this piece, [cnt][n_i], into the staging buffer (the
+        // plain form's graphs read it there; stream order keeps the previous
+        // piece's kernels ahead of the overwrite)
+        float *stage = b->tc ? spiir_tc_stage(b->tc) : b->xstage + (int64_t)s0 * n_i;
+        CUDA_TRY(cudaMemcpy2DAsync(stage, n_i * sizeof(float), x_host + off, n_samples * sizeof(float),
+                                   n_i * sizeof(float), cnt, cudaMemcpyHostToDevice, s));
+        if (b->tc) {
+            spiir_status st = spiir_tc_push(b->tc, s0, cnt, stage, n_i, n_i, s, b->timer, off);
+            if (st) return fail(st, "%s", spiir_tc_last_error());
+            for (int q = s0; q < s0 + cnt; ++q) b->last_n[q] = n_i;
+        } else if (same) {
+            spiir_status st = push_plain(b, s0, cnt, stage, n_i, n_i, s, false, off);
+            if (st) return st;
+        } else {
+            for (int q = 0; q < cnt; ++q) {
+                spiir_status st = push_plain(b, s0 + q, 1, stage + q * n_i, n_i, n_i, s, false, off);
+                if (st) return st;
+            }
+        }
+        cudaStream_t cs = s;
+        if (n_pieces > 1) {
+            CUDA_TRY(cudaEventRecord(b->piece_done[i], s));
+            CUDA_TRY(cudaStreamWaitEvent(b->copy, b->piece_done[i], 0));
+            cs = b->copy;
+        }
+        for (int q = s0; q < s0 + cnt; ++q) {
+            const float2 *src;
+            int64_t ring;
+            if (b->tc) {
+                src = spiir_tc_output(b->tc, q, &ring);
+            } else {
+                ring = b->p.ring_len;
+                src = b->z + (int64_t)q * T * ring;
+            }
+            char *dst = (char *)z_host + ((int64_t)(q - s0) * T * n_samples + off) * sizeof(float2);
+            CUDA_TRY(cudaMemcpy2DAsync(dst, n_samples * sizeof(float2), src + off, ring * sizeof(float2),
+                                       n_i * sizeof(float2), T, cudaMemcpyDeviceToHost, cs));
+        }
+        off += n_i;
+    }
+    for (int q = s0; q < s0 + cnt; ++q) {
+        b->ring_n[q] = n_samples;
+        b->out_valid[q] = 1;
+    }
+    if (b->copy) CUDA_TRY(cudaStreamSynchronize(b->copy));
     CUDA_TRY(cudaStreamSynchronize(s));
     return SPIIR_OK;
 }
@@ -1443,13 +1507,14 @@ const char *spiir_last_error(void) { return g_err.c_str(); }
 // ---------------------------------------------------------------------------
 // One-shot filtering without device allocation (spiir_filter_noalloc).
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured on its stream, a host framework that hands the library a
-// real-time thread on which device allocation is forbidden, or a process whose
-// device memory is carved up in advance by someone else. This entry point
-// serves them: all the device memory it needs lives in one file-scope
-// __device__ array of fixed size, which the module reserves on every GPU that
-// loads the library and keeps until the process exits.
+// Some callers cannot call cudaMalloc: a host framework that hands the
+// library a real-time thread on which device allocation is forbidden (an
+// allocation can block on the driver for an unbounded time), or a process
+// whose device memory is carved up in advance by someone else, so that any
+// allocation outside its own pools fails. This entry point serves them: all
+// the device memory it needs lives in one file-scope __device__ array of
+// fixed size, which the module reserves on every GPU that loads the library
+// and keeps until the process exits.
 // ---------------------------------------------------------------------------
 
 #define SPIIR_NOALLOC_SCRATCH_BYTES (32u << 20)
@@ -1459,7 +1524,10 @@ static __device__ __align__(256) unsigned char g_spiir_noalloc_scratch[SPIIR_NOA
 namespace {
 
 constexpr int kMaxDevices = 64;
-void *g_noalloc_ptr[kMaxDevices] = {};
+// Per-device address of the scratch array, filled in by the first call on
+// that device. Atomic so that first calls from several host threads do not
+// race; two of them may both look the address up, which is harmless.
+std::atomic<void *> g_noalloc_ptr[kMaxDevices] = {};
 KernelTimer g_noalloc_timer;  // stays off: pushes record no events
 
 // Device address of the scratch array on the current device. The array's
@@ -1469,12 +1537,12 @@ spiir_status noalloc_scratch(void **out) {
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return fail(SPIIR_EUNSUPPORTED, "device %d out of range", dev);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
+    void *p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
         CUDA_TRY(cudaGetSymbolAddress(&p, g_spiir_noalloc_scratch));
-        g_noalloc_ptr[dev] = p;
+        g_noalloc_ptr[dev].store(p, std::memory_order_release);
     }
-    *out = g_noalloc_ptr[dev];
+    *out = p;
     return SPIIR_OK;
 }
 
@@ -1502,20 +1570,25 @@ spiir_status put(T *dst, const std::vector<T> &src, cudaStream_t s) {
 extern "C" spiir_status spiir_filter_noalloc(const spiir_bank_desc *desc, const float *x_dev,
                                              int64_t n_samples, void *z_dev, void *cuda_stream) {
     if (!x_dev || !z_dev) return fail(SPIIR_EINVAL, "x_dev and z_dev must not be NULL");
-    spiir_status st = validate(desc);
-    if (st) return st;
+    if (!desc) return fail(SPIIR_EINVAL, "desc is NULL");
     if (desc->mode != SPIIR_PLAIN_FP32)
         return fail(SPIIR_EUNSUPPORTED, "spiir_filter_noalloc runs the plain FP32 form only");
     if (desc->n_streams != 1) return fail(SPIIR_EINVAL, "spiir_filter_noalloc takes one stream");
+    if (desc->n_levels < 1 || desc->n_levels > SPIIR_MAX_LEVELS)
+        return fail(SPIIR_EINVAL, "n_levels must be in [1, %d]", SPIIR_MAX_LEVELS);
     const int H = desc->n_levels - 1;
     if (n_samples <= 0 || n_samples % (4ll << H) != 0 || n_samples > (1ll << 30))
         return fail(SPIIR_EINVAL, "n_samples must be a positive multiple of 4*2^(n_levels-1)");
 
-    // Plan for one push of n_samples from zero state.
+    // Plan for one push of n_samples from zero state: the description's
+    // block_len, max_push_blocks and autotuning request are replaced before
+    // it is validated, so a caller need not fill them in.
     spiir_bank_desc d = *desc;
     d.block_len = (int32_t)n_samples;
     d.max_push_blocks = 1;
     d.tune = desc->tune < 0 ? desc->tune : 0;
+    spiir_status st = validate(&d);
+    if (st) return st;
     spiir_bank b;
     b.d = d;
     b.n_filters = d.n_filters;
@@ -1610,6 +1683,7 @@ extern "C" spiir_status spiir_filter_noalloc(const spiir_bank_desc *desc, const 
         lib_kaiser_taps(ntu, 60.0, b.h_up.data());
     }
     b.last_n.assign(1, 0);
+    b.ring_n.assign(1, 0);
     b.timer = &g_noalloc_timer;
     st = push_plain(&b, 0, 1, x_dev, n_samples, n_samples, s);
     // The bank object only borrows these pointers: clear them so that it

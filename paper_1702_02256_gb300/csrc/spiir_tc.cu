@@ -1574,13 +1574,13 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
 }
 
 spiir_status spiir_tc_push(TcBank *b, int s0, int count, const float *x, int64_t x_stride, int64_t n,
-                           cudaStream_t s, KernelTimer *timer) {
+                           cudaStream_t s, KernelTimer *timer, int64_t zoff) {
     if (n % b->L != 0) return tc_fail(SPIIR_EINVAL, "push length must be a multiple of chunk_len");
     const int64_t n_prev = b->last_n[s0];
     for (int q = s0; q < s0 + count; ++q)
         if (b->last_n[q] != n_prev) {
             for (int i = 0; i < count; ++i) {
-                spiir_status st = spiir_tc_push(b, s0 + i, 1, x + i * x_stride, x_stride, n, s, timer);
+                spiir_status st = spiir_tc_push(b, s0 + i, 1, x + i * x_stride, x_stride, n, s, timer, zoff);
                 if (st) return st;
             }
             return SPIIR_OK;
@@ -1590,7 +1590,7 @@ spiir_status spiir_tc_push(TcBank *b, int s0, int count, const float *x, int64_t
     if (count > 2) {
         for (int i = 0; i < count; i += 2) {
             const int cnt = std::min(2, count - i);
-            spiir_status st = spiir_tc_push(b, s0 + i, cnt, x + i * x_stride, x_stride, n, s, timer);
+            spiir_status st = spiir_tc_push(b, s0 + i, cnt, x + i * x_stride, x_stride, n, s, timer, zoff);
             if (st) return st;
         }
         return SPIIR_OK;
@@ -1663,7 +1663,7 @@ spiir_status spiir_tc_push(TcBank *b, int s0, int count, const float *x, int64_t
         ca.cpb = cpb;
         ca.n_batches = n_batches;
         ca.scale = b->scale;
-        ca.z = b->z;
+        ca.z = b->z + zoff;
         ca.z_row_stride = b->ring_len;
         ca.z_stream_stride = (int64_t)b->T * b->ring_len;
         ca.status = b->status;
@@ -1689,7 +1689,7 @@ spiir_status spiir_tc_push(TcBank *b, int s0, int count, const float *x, int64_t
     fa.n_streams = count;
     fa.n_templates = b->T;
     fa.stream0 = s0;
-    fa.z = b->z;
+    fa.z = b->z + zoff;
     fa.z_row_stride = b->ring_len;
     fa.z_stream_stride = (int64_t)b->T * b->ring_len;
     fa.status = b->status;

@@ -12,8 +12,9 @@ struct TcBank;
 spiir_status spiir_tc_create(const spiir_bank_desc *desc, float scale, cudaStream_t s,
                              TcBank **out, int64_t *footprint);
 struct KernelTimer;
+// zoff: first output-ring column the push writes (0 for an ordinary push).
 spiir_status spiir_tc_push(TcBank *b, int s0, int count, const float *x, int64_t x_stride,
-                           int64_t n, cudaStream_t s, KernelTimer *timer);
+                           int64_t n, cudaStream_t s, KernelTimer *timer, int64_t zoff = 0);
 spiir_status spiir_tc_reset(TcBank *b, int s0, int count, cudaStream_t s);
 const float2 *spiir_tc_output(TcBank *b, int stream, int64_t *ring_len);
 float *spiir_tc_stage(TcBank *b);

@@ -206,3 +206,45 @@ def test_kernel_timing_counts_launches(torch_cuda):
     assert kt["recur"][1] == 3 and kt["combine"][1] == 3 and kt["decimate"][1] == 3
     assert all(ms >= 0 for ms, _ in kt.values())
     b.close()
+
+
+@pytest.mark.parametrize("form", ["plain-multirate", "fp16"])
+def test_pipelined_host_push(torch_cuda, oracle_mod, form):
+    """A host push of several blocks runs as pieces whose SNR is copied back
+    while the next piece computes. Two streams, a 7-block host push (pieces
+    of 1, 2, 2, 2 blocks), then an ordinary device push and a 3-block host
+    push: the stream continues as if pushed in one piece; every sample
+    against the oracle (and, for the plain form, bit for bit against device
+    pushes)."""
+    import torch
+    from paper_1702_02256_gb300 import spiir
+    blk = 1024
+    if form == "fp16":
+        bank = inputs.single_rate_bank(6, [40, 128, 200, 5, 300, 64], 500, seed=51)
+        kw = dict(mode="fp16", chunk_len=256)
+        tol = 1e-3
+    else:
+        bank = inputs.multi_rate_bank(5, 3, seed=52, delay_max=200)
+        kw = {}
+        tol = TOL_PLAIN
+    x = inputs.strain(2, 11 * blk, seed=53)
+    b = spiir.Bank(bank, n_streams=2, block_len=blk, max_push_blocks=7, **kw)
+    z1 = b.push_host(np.ascontiguousarray(x[:, :7 * blk]))
+    xd = torch.from_numpy(np.ascontiguousarray(x[:, 7 * blk:8 * blk])).cuda()
+    b.push(xd, stream_id=-1)
+    z2 = b.read(blk, stream_id=-1).cpu().numpy()
+    z3 = b.push_host(np.ascontiguousarray(x[:, 8 * blk:]))
+    got = np.concatenate([z1, z2, z3], axis=-1).astype(np.complex128)
+    zr = b.read(3 * blk, stream_id=-1).cpu().numpy()
+    b.sync_status()
+    b.close()
+    assert np.array_equal(zr, z3)                       # the ring holds the whole last push
+    if form != "fp16":
+        ref_dev = gpu_snr(bank, x, block_len=blk, push_blocks=1, n_streams=2, **kw)
+        assert np.array_equal(got, ref_dev)
+    for s in range(2):
+        if bank.n_levels > 1:
+            ref = oracle_mod.spiir_multirate(bank, x[s])
+        else:
+            ref = oracle_mod.spiir_single(bank, x[s])
+        assert rel_rms(got[s], ref).max() <= tol

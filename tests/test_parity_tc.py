@@ -13,7 +13,11 @@ from tests._util import TOL_TC, gpu_snr, rel_rms
 
 pytestmark = pytest.mark.gpu
 
+# Single-pass BF16 rounds both operands to 8 significant bits and misses the
+# stated 1e-3 (about 2.4e-3 measured); it is held to this looser bound, and
+# the test ids say so. Split BF16 (bf16x2) is held to 1e-3.
 TOL_BF16 = 1e-2
+BF16_IDS = ["fp16-1e-3", "bf16-single-pass-misses-1e-3-held-to-1e-2"]
 
 
 @pytest.fixture(scope="module")
@@ -32,7 +36,7 @@ def _check(z, ref, tol, L):
     return float(err.max())
 
 
-@pytest.mark.parametrize("mode,tol", [("fp16", TOL_TC), ("bf16", TOL_BF16)])
+@pytest.mark.parametrize("mode,tol", [("fp16", TOL_TC), ("bf16", TOL_BF16)], ids=BF16_IDS)
 def test_config3_scaled_two_streams(torch_cuda, oracle_mod, mode, tol):
     """Config-3 filters (256 per template, delays to 1023), 2 streams, 4 s pushed
     as 1 s blocks, chunk length 256."""
@@ -77,7 +81,7 @@ def test_three_streams_pair_and_single(torch_cuda, oracle_mod):
         _check(z[s], ref, TOL_TC, 256)
 
 
-@pytest.mark.parametrize("mode,tol", [("fp16", TOL_TC), ("bf16", TOL_BF16)])
+@pytest.mark.parametrize("mode,tol", [("fp16", TOL_TC), ("bf16", TOL_BF16)], ids=BF16_IDS)
 def test_double_float_carry_matches_fp64(torch_cuda, oracle_mod, mode, tol):
     """The double-float batch anchor (carry="df") against the default FP64
     anchor: the FP32 chunk states both hand to the contractions agree, so the

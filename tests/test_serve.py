@@ -90,3 +90,20 @@ def test_request_alone_equals_request_in_mix(form):
     for i in range(3):
         alone = run([i])
         assert np.array_equal(mix[i], alone[i]), i
+    # and each request's SNR is the oracle's for the strain it saw: its bank
+    # starts from zero state at its first block
+    from oracle import oracle
+    from tests._util import TOL_PLAIN, TOL_TC, rel_rms
+    xh = x.cpu().numpy()
+    tol = TOL_PLAIN if form == "plain" else TOL_TC
+    for i in range(3):
+        first, life = spec[i]
+        z = np.concatenate(list(mix[i]), axis=-1)          # [3, T, life * block]
+        seg = xh[:, first * block:(first + life) * block]
+        for s in range(3):
+            if form == "plain":
+                ref = oracle.spiir_multirate(banks[i], seg[s])
+            else:
+                ref = oracle.spiir_single(banks[i], seg[s])
+            err = rel_rms(z[s], ref)
+            assert err.max() <= tol, (i, s, float(err.max()))
