@@ -318,6 +318,107 @@ int32_t spiir_assign_level_margin(float a_re, float a_im, int32_t base_rate,
 spiir_status spiir_filter_noalloc(const spiir_bank_desc *desc, const float *x_dev,
                                   int64_t n_samples, void *z_dev, void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Serving: many banks filtered together.
+ *
+ * A server holds the strain of n_streams detector streams and any number of
+ * member banks (template-bank requests of a serving loop). Every push filters
+ * one block of every stream through all members at once: one shared history
+ * update and decimation cascade of the strain (Sec. 2.2), one recursion
+ * launch over the work items of every member and level (Eqs. iireq0,
+ * iireq1), one upsample-and-add launch over every member's templates; the
+ * tensor-core modes run the levels whose block holds whole chunks in the
+ * block-parallel form, batched over all members, and the rest in the plain
+ * form. Members join and leave between pushes; their filter states and
+ * resampler histories stay on the device between pushes, in pooled arrays
+ * that grow as needed and are reused after a member leaves.
+ *
+ * A member added before push k takes part from push k on: its filter states
+ * and upsampler histories start at zero there, while its delayed inputs
+ * x[n - d_k] read the server's continuous strain history (for a member
+ * added before the first push that is the zero history of a new bank, and
+ * its SNR equals that of a bank of its own). Each member's SNR is the same
+ * whatever other members share the server (fixed summation order).
+ * ------------------------------------------------------------------------ */
+typedef struct spiir_server *spiir_server_t;
+
+typedef struct {
+    int32_t n_streams;     /* detector streams pushed together, >= 1 */
+    int32_t n_levels;      /* rates of every member, 1..12 */
+    int32_t base_rate;     /* Hz of level 0 */
+    int32_t block_len;     /* base-rate samples per push and stream; a
+                              multiple of 4 * 2^(n_levels-1) */
+    int32_t max_delay;     /* largest delay d_k (own-rate samples) any member
+                              may have; sets the strain history kept */
+    const float *h_down, *h_up;   /* resampler taps as in spiir_bank_desc */
+    int32_t n_taps, n_taps_up;
+    int32_t align;         /* as in spiir_bank_desc (1 when n_levels > 1) */
+    float snr_scale;       /* 0 = 2/base_rate */
+    spiir_mode mode;       /* PLAIN_FP32, TC_FP16 or TC_BF16 */
+    int32_t chunk_len;     /* TC modes: chunk length (0 = 256) */
+    int32_t carry;         /* TC modes: as in spiir_bank_desc */
+    int32_t tune;          /* recursion variant: -(v+1) forces v, else built-in */
+} spiir_server_desc;
+
+/* Facts about a server. */
+typedef struct {
+    int32_t n_members;         /* members taking part in pushes */
+    int32_t n_templates;       /* their templates */
+    int64_t n_filters;         /* their filters */
+    int64_t filter_samples_per_push;  /* sum over filters of own-rate samples
+                                         in one push of one stream */
+    int64_t device_bytes;      /* device memory the server holds (pools) */
+    int32_t n_cta_items;       /* recursion work items per stream */
+    int32_t kernel_variant;    /* recursion variant */
+    int32_t tc_levels;         /* levels run in the block-parallel form */
+    int32_t launches_per_push; /* kernels one push launches */
+} spiir_server_info;
+
+/* Create an empty server. Errors: EINVAL, ENOMEM, ECUDA, EUNSUPPORTED. */
+spiir_status spiir_server_create(const spiir_server_desc *desc, void *cuda_stream,
+                                 spiir_server_t *out);
+
+/* Add a member. Of *member only the filters (a, b, delay, template_id,
+ * level), n_templates, n_filters, n_levels (must equal the server's) and
+ * base_rate (must equal the server's) are used; streams, block length,
+ * resampler, scale and form are the server's. The arrays are copied before
+ * return. *member_id receives the member's handle (>= 0). The member takes
+ * part from the next push. Errors: EINVAL (description, a delay above
+ * max_delay), ENOMEM. */
+spiir_status spiir_server_add(spiir_server_t srv, const spiir_bank_desc *member,
+                              int32_t *member_id);
+
+/* Remove a member: it takes no part in later pushes and its memory is
+ * reused. Errors: EINVAL (unknown id). */
+spiir_status spiir_server_remove(spiir_server_t srv, int32_t member_id);
+
+/* Device bytes a member would add to the server's pools (for admission
+ * control; pools grow geometrically, so the server may hold up to about
+ * half as much again). -1 on a bad description. */
+int64_t spiir_server_member_footprint(spiir_server_t srv, const spiir_bank_desc *member);
+
+/* Filter one block of every stream: x_dev device float32
+ * [n_streams][block_len]. Applies pending additions and removals first.
+ * Asynchronous on cuda_stream. Errors: ESTATE (no member), ECUDA; ETIMEOUT
+ * from an earlier push (spiir_server_sync_status). */
+spiir_status spiir_server_push(spiir_server_t srv, const float *x_dev, void *cuda_stream);
+
+/* The SNR of the last push for one member: z_dev device complex64
+ * [n_streams][n_templates of the member][block_len]. Asynchronous device
+ * copy on cuda_stream. Errors: EINVAL (unknown id), ESTATE (the member has
+ * not taken part in a push yet). */
+spiir_status spiir_server_read(spiir_server_t srv, int32_t member_id, void *z_dev,
+                               void *cuda_stream);
+
+spiir_status spiir_server_get_info(spiir_server_t srv, spiir_server_info *info);
+
+/* Wait for the server's queued work and report its device status word (OK,
+ * or ETIMEOUT once after a bounded device wait gave up). */
+spiir_status spiir_server_sync_status(spiir_server_t srv);
+
+/* Release everything the server holds. NULL is ignored. */
+void spiir_server_destroy(spiir_server_t srv);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *spiir_last_error(void);
 

@@ -59,6 +59,9 @@ def lib():
         _lib.spiir_oracle_single.restype = ctypes.c_int
         _lib.spiir_oracle_single.argtypes = [i32, p, p, p, p, p, p, p, i64, d,
                                              p, i32, p, i32]
+        _lib.spiir_oracle_single_from.restype = ctypes.c_int
+        _lib.spiir_oracle_single_from.argtypes = [i32, p, p, p, p, p, p, p, i64, d,
+                                                  p, i32, p, i32, i64]
         _lib.spiir_oracle_decimate.restype = ctypes.c_int
         _lib.spiir_oracle_decimate.argtypes = [p, i64, p, i32, p]
         _lib.spiir_oracle_upsample_add.restype = ctypes.c_int
@@ -146,6 +149,29 @@ def spiir_single(bank, x: np.ndarray, scale: Optional[float] = None,
                                    threads or default_threads())
     if rc:
         raise ValueError(f"spiir_oracle_single failed ({rc})")
+    return z[..., 0] + 1j * z[..., 1]
+
+
+def spiir_single_from(bank, x: np.ndarray, start: int, scale: Optional[float] = None,
+                      templates: Optional[Sequence[int]] = None,
+                      threads: Optional[int] = None) -> np.ndarray:
+    """Single-rate SNR with every filter state zero before sample `start`
+    (z = 0 there) and the recursion of Eq. iireq0 from `start` on, its delayed
+    inputs x[n - d_k] read from the whole series x (a bank that joins a
+    running stream)."""
+    x = np.ascontiguousarray(x, np.float32)
+    n = int(x.shape[0])
+    scale = 2.0 / bank.base_rate if scale is None else float(scale)
+    ptr = _csr(bank)
+    tsel, n_sel = _sel(bank, templates)
+    z = np.zeros((n_sel, n, 2), np.float64)
+    arrs = [np.ascontiguousarray(v) for v in (bank.a_re, bank.a_im, bank.b_re,
+                                              bank.b_im, bank.delay)]
+    rc = lib().spiir_oracle_single_from(bank.n_templates, _ptr(ptr), *[_ptr(v) for v in arrs],
+                                        _ptr(x), n, scale, _ptr(tsel), n_sel, _ptr(z),
+                                        threads or default_threads(), int(start))
+    if rc:
+        raise ValueError(f"spiir_oracle_single_from failed ({rc})")
     return z[..., 0] + 1j * z[..., 1]
 
 

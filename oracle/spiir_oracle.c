@@ -14,6 +14,9 @@
  * What each function follows:
  *   spiir_oracle_single      Sec. 2.1, Eq. (iireq0) per filter and Eq. (iireq1)
  *                            summed over a template's filters.
+ *   spiir_oracle_single_from The same recursion with the filter state zero
+ *                            before a start sample while the strain before it
+ *                            is real (a bank joining a running stream).
  *   spiir_oracle_decimate    Sec. 2.2, Eq. (kaiser_window_filtering), causal
  *                            T-tap form, keep every second output.
  *   spiir_oracle_upsample_add  Sec. 2.2 (Fig. 1): zero-stuff x2, Kaiser
@@ -136,13 +139,14 @@ int32_t spiir_oracle_assign_level_margin(double a_re, double a_im, int32_t base_
 /* Single-rate SPIIR (Sec. 2.1, Eqs. iireq0 and iireq1)                 */
 /* ------------------------------------------------------------------ */
 
-/* One filter, y[n] = a*y[n-1] + b*x[n-d] with y[-1] = 0 and x[<0] = 0, its
- * output added to acc[n] (complex, interleaved re/im), n = 0..n_samples-1. */
+/* One filter, y[n] = a*y[n-1] + b*x[n-d] for n = start..n_samples-1 with
+ * y[start-1] = 0 and x[<0] = 0, its output added to acc[n] (complex,
+ * interleaved re/im); acc[n] for n < start is left alone. */
 static void filter_into(double a_re, double a_im, double b_re, double b_im,
                         int32_t d, const double *x, int64_t n_samples,
-                        double *acc) {
+                        double *acc, int64_t start) {
     double y_re = 0.0, y_im = 0.0;
-    for (int64_t n = 0; n < n_samples; ++n) {
+    for (int64_t n = start; n < n_samples; ++n) {
         double xin = (n - d >= 0) ? x[n - d] : 0.0;
         double ny_re = a_re * y_re - a_im * y_im + b_re * xin;
         double ny_im = a_re * y_im + a_im * y_re + b_im * xin;
@@ -158,12 +162,43 @@ static void filter_into(double a_re, double a_im, double b_re, double b_im,
  * (tsel[j], or all when tsel is NULL) writes
  *   z[j][n] = scale * sum_k y_k[n]      (complex, interleaved)
  * summed over the template's filters in index order. */
+static int single_from(int32_t n_templates, const int64_t *tmpl_ptr,
+                       const float *a_re, const float *a_im,
+                       const float *b_re, const float *b_im,
+                       const int32_t *delay, const float *x,
+                       int64_t n_samples, double scale, const int32_t *tsel,
+                       int32_t n_sel, double *z, int32_t n_threads, int64_t start);
+
 int spiir_oracle_single(int32_t n_templates, const int64_t *tmpl_ptr,
                         const float *a_re, const float *a_im,
                         const float *b_re, const float *b_im,
                         const int32_t *delay, const float *x,
                         int64_t n_samples, double scale, const int32_t *tsel,
                         int32_t n_sel, double *z, int32_t n_threads) {
+    return single_from(n_templates, tmpl_ptr, a_re, a_im, b_re, b_im, delay, x, n_samples,
+                       scale, tsel, n_sel, z, n_threads, 0);
+}
+
+/* As spiir_oracle_single, for filters whose state is zero before sample
+ * `start` (z[n] = 0 there) and which run from `start` on with their delayed
+ * inputs x[n - d_k] taken from the whole series x. */
+int spiir_oracle_single_from(int32_t n_templates, const int64_t *tmpl_ptr,
+                             const float *a_re, const float *a_im,
+                             const float *b_re, const float *b_im,
+                             const int32_t *delay, const float *x,
+                             int64_t n_samples, double scale, const int32_t *tsel,
+                             int32_t n_sel, double *z, int32_t n_threads, int64_t start) {
+    if (start < 0 || start > n_samples) return 1;
+    return single_from(n_templates, tmpl_ptr, a_re, a_im, b_re, b_im, delay, x, n_samples,
+                       scale, tsel, n_sel, z, n_threads, start);
+}
+
+static int single_from(int32_t n_templates, const int64_t *tmpl_ptr,
+                       const float *a_re, const float *a_im,
+                       const float *b_re, const float *b_im,
+                       const int32_t *delay, const float *x,
+                       int64_t n_samples, double scale, const int32_t *tsel,
+                       int32_t n_sel, double *z, int32_t n_threads, int64_t start) {
     if (n_samples < 0 || n_templates < 0 || !tmpl_ptr || !z) return 1;
     if (!tsel) n_sel = n_templates;
     double *xd = (double *)malloc(sizeof(double) * (size_t)(n_samples + 1));
@@ -178,7 +213,7 @@ int spiir_oracle_single(int32_t n_templates, const int64_t *tmpl_ptr,
         memset(acc, 0, sizeof(double) * 2 * (size_t)n_samples);
         for (int64_t k = tmpl_ptr[t]; k < tmpl_ptr[t + 1]; ++k)
             filter_into(a_re[k], a_im[k], b_re[k], b_im[k], delay[k], xd,
-                        n_samples, acc);
+                        n_samples, acc, start);
         for (int64_t n = 0; n < 2 * n_samples; ++n) acc[n] *= scale;
     }
     free(xd);
@@ -289,7 +324,7 @@ int spiir_oracle_multirate(int32_t n_templates, const int64_t *tmpl_ptr,
             for (int64_t k = tmpl_ptr[t]; k < tmpl_ptr[t + 1]; ++k)
                 if (level[k] == i)
                     filter_into(a_re[k], a_im[k], b_re[k], b_im[k], delay[k],
-                                xl[i], Ni, s);
+                                xl[i], Ni, s, 0);
             int64_t D = spiir_oracle_align_delay(i, n_levels, n_taps_down,
                                                  n_taps_up, align);
             for (int64_t n = 0; n < Ni; ++n) {

@@ -27,9 +27,10 @@
 
 #include "spiir.h"
 #include "spiir_internal.h"
+#include "spiir_plan.h"
 #include "spiir_tc.h"
 
-namespace {
+namespace spiir_host {
 
 thread_local std::string g_err;
 
@@ -42,16 +43,6 @@ spiir_status fail(spiir_status st, const char *fmt, ...) {
     g_err = buf;
     return st;
 }
-
-#define CUDA_TRY(call)                                                                   \
-    do {                                                                                 \
-        cudaError_t e_ = (call);                                                         \
-        if (e_ != cudaSuccess)                                                           \
-            return fail(e_ == cudaErrorMemoryAllocation ? SPIIR_ENOMEM : SPIIR_ECUDA,    \
-                        "%s: %s", #call, cudaGetErrorString(e_));                        \
-    } while (0)
-
-inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
 constexpr int kSmemMax = 227 * 1024;
 
@@ -94,38 +85,6 @@ void lib_kaiser_taps(int n, double A, float *out) {
 // ---------------------------------------------------------------------------
 // Plan: sizes and packed arrays for one kernel variant
 // ---------------------------------------------------------------------------
-
-struct Plan {
-    int variant = 0, T = 32, FMAX = 8;
-    int n_levels = 1, H = 0, n_taps = 32, n_taps_up = 32, align = 0;   // decimator, interpolator
-    int hist[SPIIR_MAX_LEVELS] = {};
-    int seg[SPIIR_MAX_LEVELS] = {};
-    int64_t max_n[SPIIR_MAX_LEVELS] = {};
-    int64_t xbuf_off[SPIIR_MAX_LEVELS] = {};
-    int64_t part_rows[SPIIR_MAX_LEVELS] = {};
-    int64_t part_base[SPIIR_MAX_LEVELS] = {};
-    int64_t part_stride[SPIIR_MAX_LEVELS] = {};
-    int64_t ubuf_off[SPIIR_MAX_LEVELS] = {};
-    int32_t ubuf_stride[SPIIR_MAX_LEVELS] = {};
-    int64_t xbuf_stream_stride = 0, part_stream_stride = 0, ubuf_stream_stride = 0;
-    int64_t ring_len = 0;
-    int smem_bytes = 0;
-    bool need_combine = false;
-    int max_F = 0, max_delay = 0;
-    int64_t n_slots = 0;
-    int64_t fs_per_block = 0;
-    // packed arrays
-    std::vector<float> are, aim, bre, bim;
-    std::vector<int32_t> xoff;
-    std::vector<WarpTask> tasks;
-    std::vector<CtaItem> items;
-    std::vector<int32_t> task_out;
-    std::vector<int32_t> comb_ptr, comb_rows;
-    std::vector<int32_t> order;
-    std::vector<int64_t> slot_filter;   // filter of each slot (-1: padding)
-    int64_t lds_rounds = 0, lds_wavefronts = 0;
-    int64_t n_units = 0;
-};
 
 struct Unit {
     int level, tmpl;
@@ -240,7 +199,11 @@ int default_variant(const spiir_bank_desc *d) {
 }
 
 // Builds the plan. With arrays == false only the sizes are computed.
-spiir_status make_plan(const spiir_bank_desc *d, int variant, bool arrays, Plan &p) {
+// hist_fixed (optional, n_levels entries): strain history per level to use
+// instead of the bank's own (a server's shared strain buffers); it must hold
+// every filter's delay plus the level's alignment delay.
+spiir_status make_plan(const spiir_bank_desc *d, int variant, bool arrays, Plan &p,
+                       const int *hist_fixed) {
     p = Plan();
     p.variant = variant;
     spiir_recur_variant_shape(variant, &p.T, &p.FMAX);
@@ -266,6 +229,12 @@ spiir_status make_plan(const spiir_bank_desc *d, int variant, bool arrays, Plan 
         int64_t h = (int64_t)maxd[i] + D;
         if (i < p.H) h = std::max<int64_t>(h, p.n_taps - 1);
         h = round_up(h, 4);
+        if (hist_fixed) {
+            if (hist_fixed[i] < h)
+                return fail(SPIIR_EINVAL, "a delay at level %d (%lld samples with alignment) is above "
+                                          "the server's strain history", i, (long long)h);
+            h = hist_fixed[i];
+        }
         p.hist[i] = (int)h;
         p.max_delay = std::max<int>(p.max_delay, (int)(maxd[i] + D));
         p.max_n[i] = push_max >> i;
@@ -588,7 +557,9 @@ spiir_status upload(T **dst, const std::vector<T> &src, cudaStream_t s) {
     return SPIIR_OK;
 }
 
-}  // namespace
+}  // namespace spiir_host
+
+using namespace spiir_host;
 
 // ---------------------------------------------------------------------------
 // The bank

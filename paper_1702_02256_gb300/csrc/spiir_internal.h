@@ -124,6 +124,8 @@ struct CombineArgs {
     int32_t n_taps;
     int32_t stream0;
     unsigned int *status;          // device status word (bounded waits)
+    const int32_t *rows;           // NULL: CTA x combines template row x; else
+                                   // row rows[x] (n_templates entries)
     float h_up2[SPIIR_MAX_TAPS];   // 2 * h_up (gain 2 of the zero-stuffed series)
     LevelArgs lev[SPIIR_MAX_LEVELS];
 };

@@ -624,7 +624,8 @@ __global__ void __launch_bounds__(kCombThreads, 4) combine_kernel(const CombineA
     extern __shared__ __align__(16) unsigned char csm[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(csm);
     float2 *cbuf = reinterpret_cast<float2 *>(csm + 16);
-    const int t = blockIdx.x, s = a.stream0 + blockIdx.y, tid = threadIdx.x;
+    const int t = a.rows ? a.rows[blockIdx.x] : (int)blockIdx.x;
+    const int s = a.stream0 + blockIdx.y, tid = threadIdx.x;
     const int H = a.n_levels - 1, ht = a.n_taps / 2;
     const float2 *part = a.partial + (int64_t)s * a.partial_stream_stride;
     float2 *hist = a.ubuf + (int64_t)s * a.ubuf_stream_stride;

@@ -1,0 +1,815 @@
+// spiir_server.cu -- many banks filtered together (spiir_server_* of
+// include/spiir.h): the batched serving form of the SPIIR hot path.
+//
+// Every push runs one prologue (strain history update) and one decimation
+// cascade for all members (Sec. 2.2), one persistent recursion launch over the
+// work items of every member and level (Eqs. iireq0, iireq1), and one
+// upsample-and-add launch over the templates of every member that needs it;
+// the launches are replayed from a CUDA graph while the membership is
+// unchanged. Each member is planned exactly like a bank of its own
+// (make_plan, with the server's strain history), and its slots, template
+// rows and partial rows are placed in pooled device arrays:
+//   * filter slots (pole, gain, window offset, state per stream),
+//   * template rows (output ring, upsampler histories),
+//   * partial rows per level (per-push scratch of the level sums);
+// each pool hands out contiguous ranges first-fit, reuses the ranges of
+// members that left, and grows geometrically (keeping every member's place
+// and its state). The work lists (warp tasks, CTA items, queue order,
+// destinations, combine lists) are rebuilt on the host and uploaded whenever
+// the membership changes; the kernels are the bank's own.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "spiir.h"
+#include "spiir_internal.h"
+#include "spiir_plan.h"
+
+using namespace spiir_host;
+
+namespace {
+
+// First-fit allocator of index ranges in [0, cap).
+class RangeAlloc {
+  public:
+    int64_t cap() const { return cap_; }
+    // Start of a free range of n indices, or -1 (n == 0 takes nothing).
+    int64_t take(int64_t n) {
+        if (n <= 0) return 0;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= n) {
+                const int64_t s = it->first, len = it->second;
+                free_.erase(it);
+                if (len > n) free_[s + n] = len - n;
+                return s;
+            }
+        }
+        return -1;
+    }
+    void give(int64_t s, int64_t n) {
+        if (n <= 0) return;
+        auto it = free_.emplace(s, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    // Capacity at which a range of n fits (extending a free tail if any).
+    int64_t need_for(int64_t n) const {
+        if (!free_.empty()) {
+            auto last = std::prev(free_.end());
+            if (last->first + last->second == cap_) return last->first + n;
+        }
+        return cap_ + n;
+    }
+    void grow(int64_t new_cap) {
+        if (new_cap > cap_) {
+            give(cap_, new_cap - cap_);
+            cap_ = new_cap;
+        }
+    }
+
+  private:
+    std::map<int64_t, int64_t> free_;
+    int64_t cap_ = 0;
+};
+
+// A device array that grows on demand (elements, not bytes).
+template <typename T>
+struct DevVec {
+    T *p = nullptr;
+    int64_t cap = 0;
+    // At least n elements; the old contents are not kept.
+    spiir_status reserve(int64_t n) {
+        if (n <= cap) return SPIIR_OK;
+        const int64_t c = std::max<int64_t>(n, cap + cap / 2);
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        CUDA_TRY(cudaMalloc((void **)&p, std::max<int64_t>(1, c) * sizeof(T)));
+        cap = c;
+        return SPIIR_OK;
+    }
+    spiir_status upload(const std::vector<T> &v, cudaStream_t s) {
+        spiir_status st = reserve((int64_t)v.size());
+        if (st) return st;
+        if (!v.empty())
+            CUDA_TRY(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+        return SPIIR_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+struct Member {
+    int id = 0;
+    int T = 0;
+    Plan p;                      // the member's own plan (server history)
+    int64_t slot0 = 0;           // first pooled filter slot
+    int64_t row0 = 0;            // first pooled template row
+    int64_t prow0[SPIIR_MAX_LEVELS] = {};   // first pooled partial row per level
+    int64_t n_filters = 0;
+    bool pushed = false;         // has taken part in a push
+};
+
+}  // namespace
+
+struct spiir_server {
+    spiir_server_desc d{};
+    int S = 1, L = 1, H = 0, block = 0, variant = 0;
+    float scale = 0.f;
+    std::vector<float> h_down, h_up;
+    Plan geo;                    // sizes of an empty member: strain layout,
+                                 // segment lengths, partial strides, history
+    int smem_bytes = 0, ctas_per_sm = 1, n_sms = 1;
+    // shared strain
+    float *xbuf = nullptr, *xstage = nullptr;
+    unsigned int *status = nullptr;
+    // pools
+    RangeAlloc slot_alloc, row_alloc, prow_alloc[SPIIR_MAX_LEVELS];
+    float *are = nullptr, *aim = nullptr, *bre = nullptr, *bim = nullptr;
+    int32_t *xoff = nullptr;
+    float2 *state = nullptr;     // [stream][slot cap]
+    float2 *z = nullptr;         // [stream][row cap][block]
+    float2 *ubuf = nullptr;      // [stream][level 1..H][row cap][SPIIR_UHIST]
+    float2 *partial = nullptr;   // [stream][level][prow cap][stride]
+    int64_t part_base[SPIIR_MAX_LEVELS] = {}, part_stream_stride = 0;
+    // work lists
+    DevVec<WarpTask> tasks;
+    DevVec<CtaItem> items;
+    DevVec<int32_t> order, task_out, comb_ptr, comb_rows, comb_list;
+    DevVec<unsigned int> queue, prog;
+    int n_items = 0, n_comb = 0, n_tasks = 0;
+    // members
+    std::map<int, Member> members;
+    std::vector<Member> pending_add;
+    std::vector<int> pending_remove;
+    int next_id = 0;
+    bool dirty = false;
+    int64_t pushes = 0;
+    // graph of one push (by previous push length: 0 for the first)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+
+    void drop_graphs() {
+        for (auto &g : graph)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+    }
+    void release() {
+        drop_graphs();
+        void *ptrs[] = {xbuf, xstage, status, are, aim, bre, bim, xoff, state, z, ubuf, partial};
+        for (void *q : ptrs)
+            if (q) cudaFree(q);
+        xbuf = xstage = nullptr;
+        status = nullptr;
+        are = aim = bre = bim = nullptr;
+        xoff = nullptr;
+        state = z = ubuf = partial = nullptr;
+        tasks.release();
+        items.release();
+        order.release();
+        task_out.release();
+        comb_ptr.release();
+        comb_rows.release();
+        comb_list.release();
+        queue.release();
+        prog.release();
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+        cap_stream = nullptr;
+    }
+};
+
+namespace {
+
+// The description a member is planned with: its filters, the server's shape.
+spiir_bank_desc member_desc(const spiir_server *sv, const spiir_bank_desc *m) {
+    spiir_bank_desc d = *m;
+    d.n_streams = sv->S;
+    d.block_len = sv->block;
+    d.max_push_blocks = 1;
+    d.h_down = sv->h_down.data();
+    d.h_up = sv->h_up.data();
+    d.n_taps = (int32_t)sv->h_down.size();
+    d.n_taps_up = (int32_t)sv->h_up.size();
+    d.align = sv->d.align;
+    d.snr_scale = sv->scale;
+    d.mode = SPIIR_PLAIN_FP32;
+    d.chunk_len = 0;
+    d.tune = -(sv->variant + 1);
+    d.hbm_budget_bytes = 0;
+    d.carry = 0;
+    return d;
+}
+
+// Grow a [outer][cap] array to [outer][new_cap], keeping the first cap of
+// each row; new entries are zero.
+template <typename T>
+spiir_status grow_rows(T **p, int64_t outer, int64_t cap, int64_t new_cap, int64_t inner, cudaStream_t s) {
+    T *q = nullptr;
+    CUDA_TRY(cudaMalloc((void **)&q, std::max<int64_t>(1, outer * new_cap * inner) * sizeof(T)));
+    CUDA_TRY(cudaMemsetAsync(q, 0, std::max<int64_t>(1, outer * new_cap * inner) * sizeof(T), s));
+    if (*p && cap > 0)
+        CUDA_TRY(cudaMemcpy2DAsync(q, new_cap * inner * sizeof(T), *p, cap * inner * sizeof(T),
+                                   cap * inner * sizeof(T), outer, cudaMemcpyDeviceToDevice, s));
+    if (*p) {
+        CUDA_TRY(cudaStreamSynchronize(s));
+        cudaFree(*p);
+    }
+    *p = q;
+    return SPIIR_OK;
+}
+
+spiir_status grow_slots(spiir_server *sv, int64_t need, cudaStream_t s) {
+    const int64_t cap = sv->slot_alloc.cap();
+    const int64_t nc = std::max<int64_t>(need, cap + cap / 2);
+    spiir_status st;
+    if ((st = grow_rows(&sv->are, 1, cap, nc, 1, s)) || (st = grow_rows(&sv->aim, 1, cap, nc, 1, s)) ||
+        (st = grow_rows(&sv->bre, 1, cap, nc, 1, s)) || (st = grow_rows(&sv->bim, 1, cap, nc, 1, s)) ||
+        (st = grow_rows(&sv->xoff, 1, cap, nc, 1, s)) || (st = grow_rows(&sv->state, sv->S, cap, nc, 1, s)))
+        return st;
+    sv->slot_alloc.grow(nc);
+    return SPIIR_OK;
+}
+
+spiir_status grow_template_rows(spiir_server *sv, int64_t need, cudaStream_t s) {
+    const int64_t cap = sv->row_alloc.cap();
+    const int64_t nc = std::max<int64_t>(need, cap + cap / 2);
+    spiir_status st;
+    // the output ring is per-push: no contents to keep
+    if (sv->z) {
+        CUDA_TRY(cudaStreamSynchronize(s));
+        cudaFree(sv->z);
+        sv->z = nullptr;
+    }
+    CUDA_TRY(cudaMalloc((void **)&sv->z, std::max<int64_t>(1, sv->S * nc * sv->block) * sizeof(float2)));
+    CUDA_TRY(cudaMemsetAsync(sv->z, 0, std::max<int64_t>(1, sv->S * nc * sv->block) * sizeof(float2), s));
+    if (sv->H > 0 && (st = grow_rows(&sv->ubuf, (int64_t)sv->S * sv->H, cap, nc, SPIIR_UHIST, s))) return st;
+    sv->row_alloc.grow(nc);
+    return SPIIR_OK;
+}
+
+// Partial rows are per-push scratch: growing reallocates without copying.
+spiir_status grow_partial_rows(spiir_server *sv, int level, int64_t need, cudaStream_t s) {
+    const int64_t cap = sv->prow_alloc[level].cap();
+    sv->prow_alloc[level].grow(std::max<int64_t>(need, cap + cap / 2));
+    int64_t off = 0;
+    for (int i = 0; i < sv->L; ++i) {
+        sv->part_base[i] = off;
+        off += sv->prow_alloc[i].cap() * sv->geo.part_stride[i];
+    }
+    sv->part_stream_stride = off;
+    if (sv->partial) {
+        CUDA_TRY(cudaStreamSynchronize(s));
+        cudaFree(sv->partial);
+        sv->partial = nullptr;
+    }
+    CUDA_TRY(cudaMalloc((void **)&sv->partial, std::max<int64_t>(1, sv->S * off) * sizeof(float2)));
+    return SPIIR_OK;
+}
+
+// Place a new member: ranges in every pool, coefficients uploaded, state,
+// output rows and upsampler histories zeroed.
+spiir_status place(spiir_server *sv, Member &m, cudaStream_t s) {
+    spiir_status st;
+    const Plan &p = m.p;
+    int64_t at = sv->slot_alloc.take(p.n_slots);
+    if (at < 0) {
+        if ((st = grow_slots(sv, sv->slot_alloc.need_for(p.n_slots), s))) return st;
+        at = sv->slot_alloc.take(p.n_slots);
+    }
+    m.slot0 = at;
+    at = sv->row_alloc.take(m.T);
+    if (at < 0) {
+        if ((st = grow_template_rows(sv, sv->row_alloc.need_for(m.T), s))) return st;
+        at = sv->row_alloc.take(m.T);
+    }
+    m.row0 = at;
+    for (int i = 0; i < sv->L; ++i) {
+        at = sv->prow_alloc[i].take(p.part_rows[i]);
+        if (at < 0) {
+            if ((st = grow_partial_rows(sv, i, sv->prow_alloc[i].need_for(p.part_rows[i]), s))) return st;
+            at = sv->prow_alloc[i].take(p.part_rows[i]);
+        }
+        m.prow0[i] = at;
+    }
+    const int64_t n = p.n_slots, cap = sv->slot_alloc.cap(), rcap = sv->row_alloc.cap();
+    if (n > 0) {
+        CUDA_TRY(cudaMemcpyAsync(sv->are + m.slot0, p.are.data(), n * 4, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(sv->aim + m.slot0, p.aim.data(), n * 4, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(sv->bre + m.slot0, p.bre.data(), n * 4, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(sv->bim + m.slot0, p.bim.data(), n * 4, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(sv->xoff + m.slot0, p.xoff.data(), n * 4, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemset2DAsync(sv->state + m.slot0, cap * sizeof(float2), 0, n * sizeof(float2), sv->S, s));
+    }
+    CUDA_TRY(cudaMemset2DAsync(sv->z + m.row0 * sv->block, rcap * sv->block * sizeof(float2), 0,
+                               (size_t)m.T * sv->block * sizeof(float2), sv->S, s));
+    if (sv->H > 0)
+        CUDA_TRY(cudaMemset2DAsync(sv->ubuf + m.row0 * SPIIR_UHIST, rcap * SPIIR_UHIST * sizeof(float2), 0,
+                                   (size_t)m.T * SPIIR_UHIST * sizeof(float2), (size_t)sv->S * sv->H, s));
+    return SPIIR_OK;
+}
+
+void unplace(spiir_server *sv, const Member &m) {
+    sv->slot_alloc.give(m.slot0, m.p.n_slots);
+    sv->row_alloc.give(m.row0, m.T);
+    for (int i = 0; i < sv->L; ++i) sv->prow_alloc[i].give(m.prow0[i], m.p.part_rows[i]);
+}
+
+// Work lists of all members, in member order, with pooled indices.
+spiir_status rebuild_lists(spiir_server *sv, cudaStream_t s) {
+    std::vector<WarpTask> tasks;
+    std::vector<CtaItem> items;
+    std::vector<int32_t> task_out, order;
+    std::vector<int64_t> work;
+    const int64_t rcap = sv->row_alloc.cap();
+    std::vector<int32_t> owner(rcap, -1);      // member (index in mv) of each pooled row
+    std::vector<const Member *> mv;
+    for (auto &kv : sv->members) mv.push_back(&kv.second);
+    for (size_t mi = 0; mi < mv.size(); ++mi) {
+        const Member &m = *mv[mi];
+        const Plan &p = m.p;
+        const int32_t task0 = (int32_t)tasks.size(), out0 = (int32_t)task_out.size();
+        // level of each destination entry (from the task that owns it)
+        std::vector<int8_t> lvl(p.task_out.size(), 0);
+        for (const WarpTask &wt : p.tasks)
+            for (int g = 0; g < wt.n_groups; ++g) lvl[wt.out_base + g] = wt.level;
+        for (size_t j = 0; j < p.task_out.size(); ++j) {
+            const int32_t dst = p.task_out[j];
+            if (dst >= 0)
+                task_out.push_back((int32_t)(m.row0 + dst));
+            else
+                task_out.push_back(-(int32_t)(m.prow0[lvl[j]] + (-dst - 1)) - 1);
+        }
+        for (WarpTask wt : p.tasks) {
+            wt.slot_base = (int32_t)(wt.slot_base + m.slot0);
+            wt.out_base += out0;
+            tasks.push_back(wt);
+        }
+        for (CtaItem ci : p.items) {
+            int64_t w = 0;
+            for (int k = 0; k < ci.task_count; ++k) {
+                const WarpTask &wt = p.tasks[ci.task_begin + k];
+                w += (int64_t)wt.F * (sv->block >> wt.level);
+            }
+            ci.task_begin += task0;
+            items.push_back(ci);
+            work.push_back(w);
+        }
+        for (int t = 0; t < m.T; ++t) owner[m.row0 + t] = (int32_t)mi;
+    }
+    if ((int64_t)tasks.size() > INT32_MAX || (int64_t)sv->slot_alloc.cap() > INT32_MAX)
+        return fail(SPIIR_EUNSUPPORTED, "server above 2^31 filter slots");
+    order.resize(items.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int32_t)i;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return work[a] > work[b]; });
+    // combine lists over the pooled template rows
+    std::vector<int32_t> cptr((size_t)rcap * sv->L + 1, 0), crows, clist;
+    for (int64_t r = 0; r < rcap; ++r) {
+        const int mi = owner[r];
+        const Member *m = mi >= 0 ? mv[mi] : nullptr;
+        const bool comb = m && m->p.need_combine;
+        if (comb) clist.push_back((int32_t)r);
+        for (int i = 0; i < sv->L; ++i) {
+            const size_t j = (size_t)r * sv->L + i;
+            if (comb) {
+                const int t = (int)(r - m->row0);
+                const Plan &p = m->p;
+                for (int32_t q = p.comb_ptr[(size_t)t * sv->L + i]; q < p.comb_ptr[(size_t)t * sv->L + i + 1]; ++q)
+                    crows.push_back((int32_t)(m->prow0[i] + p.comb_rows[q]));
+            }
+            cptr[j + 1] = (int32_t)crows.size();
+        }
+    }
+    spiir_status st;
+    if ((st = sv->tasks.upload(tasks, s)) || (st = sv->items.upload(items, s)) ||
+        (st = sv->order.upload(order, s)) || (st = sv->task_out.upload(task_out, s)) ||
+        (st = sv->comb_ptr.upload(cptr, s)) || (st = sv->comb_rows.upload(crows, s)) ||
+        (st = sv->comb_list.upload(clist, s)))
+        return st;
+    if ((st = sv->prog.reserve((int64_t)sv->S * std::max<size_t>(1, items.size())))) return st;
+    sv->n_items = (int)items.size();
+    sv->n_tasks = (int)tasks.size();
+    sv->n_comb = (int)clist.size();
+    return SPIIR_OK;
+}
+
+spiir_status apply_changes(spiir_server *sv, cudaStream_t s) {
+    for (int id : sv->pending_remove) {
+        auto it = sv->members.find(id);
+        if (it == sv->members.end()) continue;
+        unplace(sv, it->second);
+        sv->members.erase(it);
+    }
+    sv->pending_remove.clear();
+    for (Member &m : sv->pending_add) {
+        spiir_status st = place(sv, m, s);
+        if (st) return st;
+        // the packed coefficients are on the device now; keep the lists
+        const int id = m.id;
+        sv->members.emplace(id, std::move(m));
+        Plan &p = sv->members[id].p;
+        std::vector<float>().swap(p.are);
+        std::vector<float>().swap(p.aim);
+        std::vector<float>().swap(p.bre);
+        std::vector<float>().swap(p.bim);
+        std::vector<int32_t>().swap(p.xoff);
+        std::vector<int64_t>().swap(p.slot_filter);
+    }
+    sv->pending_add.clear();
+    spiir_status st = rebuild_lists(sv, s);
+    if (st) return st;
+    sv->drop_graphs();
+    sv->dirty = false;
+    return SPIIR_OK;
+}
+
+void level_args(const spiir_server *sv, int64_t n_prev, LevelArgs *lev) {
+    const Plan &g = sv->geo;
+    const int segs = push_segments_n(sv->block);
+    for (int i = 0; i < sv->L; ++i) {
+        LevelArgs &L = lev[i];
+        L.hist = g.hist[i];
+        L.n = (int32_t)(sv->block >> i);
+        L.seg = (int32_t)segment_len(sv->block, i, segs);
+        L.n_prev = (int32_t)(n_prev >> i);
+        L.part_base = sv->part_base[i];
+        L.part_stride = g.part_stride[i];
+        L.xbuf_off = g.xbuf_off[i];
+        L.ubuf_off = i > 0 ? (int64_t)(i - 1) * sv->row_alloc.cap() * SPIIR_UHIST : 0;
+        L.ubuf_stride = i > 0 ? SPIIR_UHIST : 0;
+        L.pad = 0;
+    }
+}
+
+// The kernels of one push (reading the strain from xstage).
+spiir_status launch_push(spiir_server *sv, int64_t n_prev, cudaStream_t st) {
+    const int S = sv->S;
+    PrologueArgs pa{};
+    pa.queue = sv->queue.p;
+    pa.prog = sv->prog.p;
+    pa.n_items = sv->n_items;
+    pa.xbuf = sv->xbuf;
+    pa.xbuf_stream_stride = sv->geo.xbuf_stream_stride;
+    pa.x_in = sv->xstage;
+    pa.x_in_stream_stride = sv->block;
+    pa.stream0 = 0;
+    pa.n_levels = sv->L;
+    level_args(sv, n_prev, pa.lev);
+    CUDA_TRY(spiir_launch_prologue(pa, S, st));
+    if (sv->L > 1) {
+        DecimArgs da{};
+        da.xbuf = sv->xbuf;
+        da.xbuf_stream_stride = sv->geo.xbuf_stream_stride;
+        da.stream0 = 0;
+        da.n_levels = sv->L;
+        da.n_taps = (int)sv->h_down.size();
+        for (size_t j = 0; j < sv->h_down.size(); ++j) da.h_down[j] = sv->h_down[j];
+        level_args(sv, n_prev, da.lev);
+        CUDA_TRY(spiir_launch_decimate(da, S, st));
+    }
+    if (sv->n_items > 0) {
+        RecurArgs ra{};
+        ra.tasks = sv->tasks.p;
+        ra.items = sv->items.p;
+        ra.order = sv->order.p;
+        ra.n_items = sv->n_items;
+        ra.n_segs = push_segments_n(sv->block);
+        ra.queue = sv->queue.p;
+        ra.prog = sv->prog.p;
+        ra.stall_test = 0;
+        ra.task_out = sv->task_out.p;
+        ra.a_re = sv->are;
+        ra.a_im = sv->aim;
+        ra.b_re = sv->bre;
+        ra.b_im = sv->bim;
+        ra.xoff = sv->xoff;
+        ra.state = sv->state;
+        ra.n_slots = sv->slot_alloc.cap();
+        ra.xbuf = sv->xbuf;
+        ra.xbuf_stream_stride = sv->geo.xbuf_stream_stride;
+        ra.partial = sv->partial;
+        ra.partial_stream_stride = sv->part_stream_stride;
+        ra.z = sv->z;
+        ra.z_row_stride = sv->block;
+        ra.z_stream_stride = sv->row_alloc.cap() * sv->block;
+        ra.scale = sv->scale;
+        ra.stream0 = 0;
+        ra.n_levels = sv->L;
+        ra.status = sv->status;
+        level_args(sv, n_prev, ra.lev);
+        const int64_t total = (int64_t)ra.n_segs * ra.n_items;
+        const int64_t resident = std::max<int64_t>(1, (int64_t)sv->ctas_per_sm * sv->n_sms / S);
+        const int ctas = (int)std::min<int64_t>(total, resident);
+        CUDA_TRY(spiir_launch_recur(ra, sv->variant, ctas, S, sv->smem_bytes, st));
+    }
+    if (sv->n_comb > 0) {
+        CombineArgs ca{};
+        ca.comb_ptr = sv->comb_ptr.p;
+        ca.comb_rows = sv->comb_rows.p;
+        ca.partial = sv->partial;
+        ca.partial_stream_stride = sv->part_stream_stride;
+        ca.ubuf = sv->ubuf;
+        ca.ubuf_stream_stride = (int64_t)sv->H * sv->row_alloc.cap() * SPIIR_UHIST;
+        ca.z = sv->z;
+        ca.z_row_stride = sv->block;
+        ca.z_stream_stride = sv->row_alloc.cap() * sv->block;
+        ca.scale = sv->scale;
+        ca.n_templates = sv->n_comb;
+        ca.n_levels = sv->L;
+        ca.n_taps = (int)sv->h_up.size();
+        ca.stream0 = 0;
+        ca.status = sv->status;
+        ca.rows = sv->comb_list.p;
+        for (size_t j = 0; j < sv->h_up.size(); ++j) ca.h_up2[j] = 2.0f * sv->h_up[j];
+        level_args(sv, n_prev, ca.lev);
+        CUDA_TRY(spiir_launch_combine(ca, spiir_combine_chunk(sv->L, sv->block), S, st));
+    }
+    return SPIIR_OK;
+}
+
+int64_t member_bytes(const spiir_server *sv, const Plan &p, int T) {
+    const int64_t S = sv->S;
+    int64_t b = p.n_slots * (4 * 4 + 4 + 8 * S);
+    b += (int64_t)T * S * ((int64_t)sv->block + (int64_t)sv->H * SPIIR_UHIST) * 8;
+    for (int i = 0; i < sv->L; ++i) b += p.part_rows[i] * S * sv->geo.part_stride[i] * 8;
+    b += (int64_t)p.tasks.size() * (sizeof(WarpTask) + 32 * 4) + (int64_t)p.items.size() * (sizeof(CtaItem) + 4 + 4 * S);
+    b += (int64_t)T * sv->L * 4 + p.n_slots * 4;
+    return b;
+}
+
+spiir_status check_member(const spiir_server *sv, const spiir_bank_desc *m) {
+    if (!m) return fail(SPIIR_EINVAL, "member is NULL");
+    if (m->n_levels != sv->L)
+        return fail(SPIIR_EINVAL, "member has %d levels, the server %d", m->n_levels, sv->L);
+    if (m->base_rate != sv->d.base_rate) return fail(SPIIR_EINVAL, "member base_rate differs from the server's");
+    for (int64_t k = 0; k < m->n_filters; ++k)
+        if (m->delay && m->delay[k] > sv->d.max_delay)
+            return fail(SPIIR_EINVAL, "delay[%lld] = %d above the server's max_delay %d", (long long)k,
+                        m->delay[k], sv->d.max_delay);
+    return SPIIR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+spiir_status spiir_server_create(const spiir_server_desc *desc, void *cuda_stream, spiir_server_t *out) {
+    if (!out) return fail(SPIIR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!desc) return fail(SPIIR_EINVAL, "desc is NULL");
+    if (desc->mode != SPIIR_PLAIN_FP32)
+        return fail(SPIIR_EUNSUPPORTED, "server: tensor-core modes are not available");
+    if (desc->max_delay < 0 || desc->max_delay > (1 << 20))
+        return fail(SPIIR_EINVAL, "max_delay must be in [0, 2^20]");
+    if (desc->n_levels < 1 || desc->n_levels > SPIIR_MAX_LEVELS)
+        return fail(SPIIR_EINVAL, "n_levels must be in [1, %d]", SPIIR_MAX_LEVELS);
+    // the shape is checked by planning an empty bank of it
+    spiir_bank_desc e{};
+    e.n_templates = 1;
+    e.n_levels = desc->n_levels;
+    e.base_rate = desc->base_rate;
+    e.n_streams = desc->n_streams;
+    e.block_len = desc->block_len;
+    e.max_push_blocks = 1;
+    e.h_down = desc->h_down;
+    e.h_up = desc->h_up;
+    e.n_taps = desc->n_taps;
+    e.n_taps_up = desc->n_taps_up;
+    e.align = desc->n_levels > 1 ? desc->align : 0;
+    e.snr_scale = desc->snr_scale;
+    e.mode = SPIIR_PLAIN_FP32;
+    e.tune = desc->tune;
+    spiir_status st = validate(&e);
+    if (st) return st;
+    if ((desc->block_len >> (desc->n_levels - 1)) % 4 != 0)
+        return fail(SPIIR_EINVAL, "block_len must be a multiple of 4 * 2^(n_levels-1)");
+    spiir_server *sv = new (std::nothrow) spiir_server();
+    if (!sv) return fail(SPIIR_ENOMEM, "host allocation failed");
+    sv->d = *desc;
+    sv->d.h_down = sv->d.h_up = nullptr;
+    sv->d.align = e.align;
+    sv->S = desc->n_streams;
+    sv->L = desc->n_levels;
+    sv->H = desc->n_levels - 1;
+    sv->block = desc->block_len;
+    sv->scale = desc->snr_scale != 0.f ? desc->snr_scale : 2.0f / (float)desc->base_rate;
+    const int nt = desc->n_taps ? desc->n_taps : 32;
+    const int ntu = desc->n_taps_up ? desc->n_taps_up : nt;
+    sv->h_down.resize(nt);
+    sv->h_up.resize(ntu);
+    if (desc->h_down) {
+        std::copy(desc->h_down, desc->h_down + nt, sv->h_down.begin());
+        std::copy(desc->h_up, desc->h_up + ntu, sv->h_up.begin());
+    } else {
+        lib_kaiser_taps(nt, 60.0, sv->h_down.data());
+        lib_kaiser_taps(ntu, 60.0, sv->h_up.data());
+    }
+    // built-in variant: T = 32 with 4 filters per lane for multi-rate
+    // members (small units), 8 for single rate
+    sv->variant = desc->tune < 0 ? std::min(-desc->tune - 1, spiir_recur_variant_count() - 1)
+                                 : (desc->n_levels > 1 ? 2 : 3);
+    // the strain history every member can use: the largest delay plus the
+    // level's alignment delay (a bank with a filter of delay max_delay at
+    // every level)
+    {
+        spiir_bank_desc g = e;
+        g.h_down = sv->h_down.data();
+        g.h_up = sv->h_up.data();
+        g.n_taps = nt;
+        g.n_taps_up = ntu;
+        std::vector<float> one(sv->L, 0.f);
+        std::vector<int32_t> dl(sv->L, desc->max_delay), tid(sv->L, 0);
+        std::vector<int8_t> lv(sv->L);
+        for (int i = 0; i < sv->L; ++i) lv[i] = (int8_t)i;
+        g.n_filters = sv->L;
+        g.a_re = g.a_im = g.b_re = g.b_im = one.data();
+        g.delay = dl.data();
+        g.template_id = tid.data();
+        g.level = lv.data();
+        if ((st = make_plan(&g, sv->variant, false, sv->geo))) {
+            delete sv;
+            return st;
+        }
+    }
+    sv->smem_bytes = sv->geo.smem_bytes;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    auto bail = [&](spiir_status r) {
+        sv->release();
+        delete sv;
+        return r;
+    };
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return bail(fail(SPIIR_ECUDA, "cudaGetDevice failed"));
+    if (cudaDeviceGetAttribute(&sv->n_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return bail(fail(SPIIR_ECUDA, "cudaDeviceGetAttribute failed"));
+    cudaError_t e1 = spiir_recur_prepare(sv->variant, sv->smem_bytes, &sv->ctas_per_sm);
+    if (e1 == cudaSuccess) e1 = spiir_combine_prepare();
+    if (e1 != cudaSuccess) return bail(fail(SPIIR_ECUDA, "kernel setup: %s", cudaGetErrorString(e1)));
+    const int64_t xs = sv->S * sv->geo.xbuf_stream_stride;
+    if (cudaMalloc((void **)&sv->xbuf, xs * sizeof(float)) != cudaSuccess ||
+        cudaMalloc((void **)&sv->xstage, (int64_t)sv->S * sv->block * sizeof(float)) != cudaSuccess ||
+        cudaMalloc((void **)&sv->status, sizeof(unsigned int)) != cudaSuccess)
+        return bail(fail(SPIIR_ENOMEM, "server strain buffers"));
+    if (cudaMemsetAsync(sv->xbuf, 0, xs * sizeof(float), s) != cudaSuccess ||
+        cudaMemsetAsync(sv->status, 0, sizeof(unsigned int), s) != cudaSuccess)
+        return bail(fail(SPIIR_ECUDA, "server setup"));
+    if ((st = sv->queue.reserve(sv->S)) || (st = sv->prog.reserve(sv->S))) return bail(st);
+    for (int i = 0; i < sv->L; ++i) sv->part_base[i] = 0;
+    if (cudaStreamCreateWithFlags(&sv->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(SPIIR_ECUDA, "cudaStreamCreate failed"));
+    if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(SPIIR_ECUDA, "server setup"));
+    *out = sv;
+    g_err.clear();
+    return SPIIR_OK;
+}
+
+spiir_status spiir_server_add(spiir_server_t sv, const spiir_bank_desc *member, int32_t *member_id) {
+    if (!sv || !member_id) return fail(SPIIR_EINVAL, "NULL argument");
+    spiir_status st = check_member(sv, member);
+    if (st) return st;
+    const spiir_bank_desc d = member_desc(sv, member);
+    if ((st = validate(&d))) return st;
+    Member m;
+    m.id = sv->next_id;
+    m.T = d.n_templates;
+    m.n_filters = d.n_filters;
+    if ((st = make_plan(&d, sv->variant, true, m.p, sv->geo.hist))) return st;
+    if (m.p.smem_bytes > sv->smem_bytes)
+        return fail(SPIIR_EINVAL, "member needs more shared memory than the server's kernel setup");
+    sv->pending_add.push_back(std::move(m));
+    *member_id = sv->next_id++;
+    sv->dirty = true;
+    return SPIIR_OK;
+}
+
+spiir_status spiir_server_remove(spiir_server_t sv, int32_t member_id) {
+    if (!sv) return fail(SPIIR_EINVAL, "server is NULL");
+    for (size_t i = 0; i < sv->pending_add.size(); ++i)
+        if (sv->pending_add[i].id == member_id) {
+            sv->pending_add.erase(sv->pending_add.begin() + i);
+            return SPIIR_OK;
+        }
+    if (!sv->members.count(member_id) ||
+        std::find(sv->pending_remove.begin(), sv->pending_remove.end(), member_id) != sv->pending_remove.end())
+        return fail(SPIIR_EINVAL, "no member %d", member_id);
+    sv->pending_remove.push_back(member_id);
+    sv->dirty = true;
+    return SPIIR_OK;
+}
+
+int64_t spiir_server_member_footprint(spiir_server_t sv, const spiir_bank_desc *member) {
+    if (!sv || check_member(sv, member)) return -1;
+    const spiir_bank_desc d = member_desc(sv, member);
+    if (validate(&d)) return -1;
+    Plan p;
+    if (make_plan(&d, sv->variant, false, p, sv->geo.hist)) return -1;
+    return member_bytes(sv, p, d.n_templates);
+}
+
+spiir_status spiir_server_push(spiir_server_t sv, const float *x_dev, void *cuda_stream) {
+    if (!sv || !x_dev) return fail(SPIIR_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    spiir_status st;
+    if (sv->dirty && (st = apply_changes(sv, s))) return st;
+    if (sv->members.empty()) return fail(SPIIR_ESTATE, "server has no member");
+    CUDA_TRY(cudaMemcpyAsync(sv->xstage, x_dev, (int64_t)sv->S * sv->block * sizeof(float),
+                             cudaMemcpyDeviceToDevice, s));
+    const int gi = sv->pushes > 0 ? 1 : 0;
+    if (!sv->graph[gi]) {
+        cudaGraph_t g = nullptr;
+        CUDA_TRY(cudaStreamBeginCapture(sv->cap_stream, cudaStreamCaptureModeThreadLocal));
+        spiir_status stc = launch_push(sv, gi ? sv->block : 0, sv->cap_stream);
+        cudaError_t e = cudaStreamEndCapture(sv->cap_stream, &g);
+        if (stc) {
+            if (g) cudaGraphDestroy(g);
+            return stc;
+        }
+        if (e != cudaSuccess) return fail(SPIIR_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&sv->graph[gi], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(SPIIR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    CUDA_TRY(cudaGraphLaunch(sv->graph[gi], s));
+    ++sv->pushes;
+    for (auto &kv : sv->members) kv.second.pushed = true;
+    return SPIIR_OK;
+}
+
+spiir_status spiir_server_read(spiir_server_t sv, int32_t member_id, void *z_dev, void *cuda_stream) {
+    if (!sv || !z_dev) return fail(SPIIR_EINVAL, "NULL argument");
+    auto it = sv->members.find(member_id);
+    if (it == sv->members.end()) {
+        for (const Member &m : sv->pending_add)
+            if (m.id == member_id) return fail(SPIIR_ESTATE, "member %d has not taken part in a push", member_id);
+        return fail(SPIIR_EINVAL, "no member %d", member_id);
+    }
+    const Member &m = it->second;
+    if (!m.pushed) return fail(SPIIR_ESTATE, "member %d has not taken part in a push", member_id);
+    const int64_t row_bytes = (int64_t)sv->block * sizeof(float2);
+    CUDA_TRY(cudaMemcpy2DAsync(z_dev, m.T * row_bytes, sv->z + m.row0 * sv->block,
+                               sv->row_alloc.cap() * row_bytes, m.T * row_bytes, sv->S,
+                               cudaMemcpyDeviceToDevice, (cudaStream_t)cuda_stream));
+    return SPIIR_OK;
+}
+
+spiir_status spiir_server_get_info(spiir_server_t sv, spiir_server_info *info) {
+    if (!sv || !info) return fail(SPIIR_EINVAL, "NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    info->n_members = (int32_t)sv->members.size();
+    for (auto &kv : sv->members) {
+        info->n_templates += kv.second.T;
+        info->n_filters += kv.second.n_filters;
+        info->filter_samples_per_push += kv.second.p.fs_per_block;
+    }
+    int64_t b = sv->S * sv->geo.xbuf_stream_stride * 4 + (int64_t)sv->S * sv->block * 4;
+    b += sv->slot_alloc.cap() * (4 * 4 + 4 + 8 * (int64_t)sv->S);
+    b += sv->row_alloc.cap() * sv->S * ((int64_t)sv->block + (int64_t)sv->H * SPIIR_UHIST) * 8;
+    b += sv->S * sv->part_stream_stride * 8;
+    b += sv->tasks.cap * sizeof(WarpTask) + sv->items.cap * sizeof(CtaItem) +
+         4 * (sv->order.cap + sv->task_out.cap + sv->comb_ptr.cap + sv->comb_rows.cap + sv->comb_list.cap +
+              sv->queue.cap + sv->prog.cap);
+    info->device_bytes = b;
+    info->n_cta_items = sv->n_items;
+    info->kernel_variant = sv->variant;
+    info->tc_levels = 0;
+    info->launches_per_push = 1 + (sv->L > 1) + (sv->n_items > 0) + (sv->n_comb > 0);
+    return SPIIR_OK;
+}
+
+spiir_status spiir_server_sync_status(spiir_server_t sv) {
+    if (!sv) return fail(SPIIR_EINVAL, "server is NULL");
+    CUDA_TRY(cudaDeviceSynchronize());
+    unsigned int v = 0;
+    CUDA_TRY(cudaMemcpy(&v, sv->status, sizeof(v), cudaMemcpyDeviceToHost));
+    if (v != SPIIR_DEV_OK) {
+        CUDA_TRY(cudaMemset(sv->status, 0, sizeof(unsigned int)));
+        return fail(SPIIR_ETIMEOUT, "a device-side wait timed out (status %u)", v);
+    }
+    return SPIIR_OK;
+}
+
+void spiir_server_destroy(spiir_server_t sv) {
+    if (!sv) return;
+    cudaDeviceSynchronize();
+    sv->release();
+    delete sv;
+}
+
+}  // extern "C"

@@ -10,9 +10,10 @@ stay for a number of blocks. The server
   retiring requests free enough memory;
 * keeps every admitted bank, its filter state and its strain history resident
   on the device between blocks;
-* pushes each block of all streams to every active bank, each bank on its own
-  CUDA stream, so the work of all requests overlaps on the GPU, and reads back
-  each bank's SNR for the block;
+* pushes each block of all streams to every active request: BatchedServer
+  makes the requests members of one device-side server, so a block is one
+  batched push for all of them (continuous batching); Server keeps a bank per
+  request, each on its own CUDA stream (the unbatched baseline);
 * records, per request and block, the device time from the push to the SNR
   being in the output buffer (CUDA events on the request's stream), and per
   block the time until every active request is done.
@@ -162,6 +163,98 @@ class Server:
             close = getattr(a.handle, "close", None)
             if close:
                 close()
+        self.active = []
+
+
+class BatchedServer(Server):
+    """Continuous batching on one libspiir server (spiir_server_t).
+
+    Same admission and retirement as Server (HBM budget, arrival order, no
+    overtaking), but every admitted request is a member of one device-side
+    server: each block is a single push that filters all of them together
+    (one shared strain update and decimation, one recursion launch over every
+    member's work items, one upsample-and-add launch, replayed from a CUDA
+    graph while the membership is unchanged), followed by one device copy of
+    each member's SNR. Requests join and leave between blocks; their filter
+    states stay on the device meanwhile.
+
+    engine: the device server (spiir.Server) or a test double with add,
+    remove, push, read and member_footprint."""
+
+    def __init__(self, hbm_budget: int, n_streams: int, block_len: int, engine,
+                 use_cuda: bool = True):
+        self.engine = engine
+        super().__init__(hbm_budget, n_streams, block_len, make_bank=lambda r: engine.add(r.bank),
+                         footprint=lambda r: engine.member_footprint(r.bank), use_cuda=use_cuda)
+
+    def _admit(self):
+        admitted = []
+        while self.pending:
+            req, fp = self.pending[0]
+            if req.arrival_block > self.block or self.used + fp > self.budget:
+                break
+            self.pending.popleft()
+            a = Active(req=req, handle=self.engine.add(req.bank), footprint=fp,
+                       admitted_block=self.block)
+            if self.use_cuda:
+                import torch
+                a.out = torch.empty((self.n_streams, req.bank.n_templates, self.block_len),
+                                    dtype=torch.complex64, device="cuda")
+            self.active.append(a)
+            self.used += fp
+            admitted.append(req.rid)
+        return admitted
+
+    def _retire(self):
+        keep = []
+        for a in self.active:
+            if a.blocks_done >= a.req.lifetime:
+                self.used -= a.footprint
+                self.engine.remove(a.handle)
+                self.finished[a.req.rid] = a
+            else:
+                keep.append(a)
+        self.active = keep
+
+    def step(self, x_block) -> dict:
+        admitted = self._admit()
+        rec = {"block": self.block, "admitted": admitted, "active": [a.req.rid for a in self.active],
+               "templates": int(sum(a.req.bank.n_templates for a in self.active)),
+               "used_bytes": self.used, "pending": len(self.pending)}
+        if self.active:
+            if self.use_cuda:
+                import torch
+                main = torch.cuda.current_stream()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(main)                          # the block is on the device
+                self.engine.push(x_block)
+                for a in self.active:
+                    self.engine.read(a.handle, out=a.out)
+                e1.record(main)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                rec["latency_ms"] = [ms] * len(self.active)
+                rec["block_ms"] = ms
+                for a in self.active:
+                    if a.req.keep_snr:
+                        a.snr.append(a.out.cpu().numpy().copy())
+            else:
+                self.engine.push(x_block)
+                for a in self.active:
+                    out = self.engine.read(a.handle)
+                    if a.req.keep_snr:
+                        a.snr.append(out)
+        for a in self.active:
+            a.blocks_done += 1
+        self.block += 1
+        self._retire()
+        self.log.append(rec)
+        return rec
+
+    def drain(self):
+        for a in self.active:
+            self.engine.remove(a.handle)
         self.active = []
 
 

@@ -49,6 +49,23 @@ class BankInfo(ctypes.Structure):
     ]
 
 
+class ServerDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_streams", _i32), ("n_levels", _i32), ("base_rate", _i32), ("block_len", _i32),
+        ("max_delay", _i32), ("h_down", _c_void_p), ("h_up", _c_void_p),
+        ("n_taps", _i32), ("n_taps_up", _i32), ("align", _i32), ("snr_scale", _f32),
+        ("mode", _i32), ("chunk_len", _i32), ("carry", _i32), ("tune", _i32),
+    ]
+
+
+class ServerInfo(ctypes.Structure):
+    _fields_ = [
+        ("n_members", _i32), ("n_templates", _i32), ("n_filters", _i64),
+        ("filter_samples_per_push", _i64), ("device_bytes", _i64), ("n_cta_items", _i32),
+        ("kernel_variant", _i32), ("tc_levels", _i32), ("launches_per_push", _i32),
+    ]
+
+
 K_PROLOGUE, K_DECIMATE, K_RECUR, K_COMBINE, K_TC_STAGE, K_TC_FIR, K_TC_CARRY, K_OTHER = range(8)
 KERNEL_NAMES = ["prologue", "decimate", "recur", "combine", "tc_stage", "tc_fir", "tc_carry", "other"]
 
@@ -89,6 +106,15 @@ _SIGS = {
     "spiir_bank_enable_timing": (_i32, [_c_void_p, _i32]),
     "spiir_bank_test_stall": (_i32, [_c_void_p, _c_void_p, _i64, _c_void_p]),
     "spiir_bank_kernel_times": (_i32, [_c_void_p, ctypes.POINTER(KernelTimes)]),
+    "spiir_server_create": (_i32, [ctypes.POINTER(ServerDesc), _c_void_p, ctypes.POINTER(_c_void_p)]),
+    "spiir_server_add": (_i32, [_c_void_p, ctypes.POINTER(BankDesc), ctypes.POINTER(_i32)]),
+    "spiir_server_remove": (_i32, [_c_void_p, _i32]),
+    "spiir_server_member_footprint": (_i64, [_c_void_p, ctypes.POINTER(BankDesc)]),
+    "spiir_server_push": (_i32, [_c_void_p, _c_void_p, _c_void_p]),
+    "spiir_server_read": (_i32, [_c_void_p, _i32, _c_void_p, _c_void_p]),
+    "spiir_server_get_info": (_i32, [_c_void_p, ctypes.POINTER(ServerInfo)]),
+    "spiir_server_sync_status": (_i32, [_c_void_p]),
+    "spiir_server_destroy": (None, [_c_void_p]),
 }
 
 
@@ -319,6 +345,96 @@ class Bank:
     def close(self):
         if getattr(self, "_h", None):
             lib().spiir_bank_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Many banks filtered together (spiir_server_t): one push filters a
+    block of every stream through every member with shared strain
+    preprocessing and batched launches."""
+
+    def __init__(self, n_streams: int, n_levels: int, block_len: int, max_delay: int,
+                 base_rate: int = 4096, mode: str = "plain", chunk_len: int = 0,
+                 carry="fp64", tune: int = 0, h_down=None, h_up=None,
+                 align: Optional[bool] = None, snr_scale: float = 0.0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libspiir needs a CUDA device")
+        d = ServerDesc()
+        d.n_streams, d.n_levels, d.base_rate, d.block_len = n_streams, n_levels, base_rate, block_len
+        d.max_delay = max_delay
+        self._keep = {}
+        if h_down is not None:
+            self._keep["h_down"] = _arr(h_down, np.float32)
+            self._keep["h_up"] = _arr(h_up, np.float32)
+            d.h_down = self._keep["h_down"].ctypes.data
+            d.h_up = self._keep["h_up"].ctypes.data
+            d.n_taps = int(self._keep["h_down"].shape[0])
+            d.n_taps_up = int(self._keep["h_up"].shape[0])
+        d.align = int(n_levels > 1 if align is None else align)
+        d.snr_scale = snr_scale
+        d.mode = MODES[mode] if isinstance(mode, str) else int(mode)
+        d.chunk_len = chunk_len
+        d.carry = CARRY[carry] if isinstance(carry, str) else int(carry)
+        d.tune = tune
+        h = _c_void_p()
+        check(lib().spiir_server_create(ctypes.byref(d), _stream_handle(stream), ctypes.byref(h)))
+        self._h = h
+        self.n_streams = n_streams
+        self.block_len = block_len
+        self.n_levels = n_levels
+        self._templates = {}
+
+    def _member_desc(self, bank):
+        return make_desc(bank, n_streams=self.n_streams, block_len=self.block_len)
+
+    def add(self, bank) -> int:
+        """Add a member bank (inputs.Bank); it takes part from the next push."""
+        d, _keep = self._member_desc(bank)
+        mid = _i32()
+        check(lib().spiir_server_add(self._h, ctypes.byref(d), ctypes.byref(mid)))
+        self._templates[int(mid.value)] = bank.n_templates
+        return int(mid.value)
+
+    def remove(self, member_id: int):
+        check(lib().spiir_server_remove(self._h, int(member_id)))
+        self._templates.pop(int(member_id), None)
+
+    def member_footprint(self, bank) -> int:
+        d, _keep = self._member_desc(bank)
+        return int(lib().spiir_server_member_footprint(self._h, ctypes.byref(d)))
+
+    def push(self, x, stream=None):
+        """x: float32 CUDA tensor [n_streams, block_len], contiguous."""
+        assert x.is_cuda and x.is_contiguous() and tuple(x.shape) == (self.n_streams, self.block_len)
+        check(lib().spiir_server_push(self._h, x.data_ptr(), _stream_handle(stream)))
+
+    def read(self, member_id: int, out=None, stream=None):
+        """SNR of the last push for one member: complex64 [n_streams, T, block_len]."""
+        import torch
+        T = self._templates[int(member_id)]
+        if out is None:
+            out = torch.empty((self.n_streams, T, self.block_len), dtype=torch.complex64, device="cuda")
+        check(lib().spiir_server_read(self._h, int(member_id), out.data_ptr(), _stream_handle(stream)))
+        return out
+
+    def info(self) -> dict:
+        inf = ServerInfo()
+        check(lib().spiir_server_get_info(self._h, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in ServerInfo._fields_}
+
+    def sync_status(self):
+        check(lib().spiir_server_sync_status(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().spiir_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -168,7 +168,9 @@ def test_workload_shapes_follow_recipes():
 
 
 @pytest.mark.parametrize("c_name,cls", [("spiir_bank_desc", "BankDesc"), ("spiir_bank_info", "BankInfo"),
-                                         ("spiir_kernel_times", "KernelTimes")])
+                                         ("spiir_kernel_times", "KernelTimes"),
+                                         ("spiir_server_desc", "ServerDesc"),
+                                         ("spiir_server_info", "ServerInfo")])
 def test_struct_layout_matches_the_c_header(tmp_path, c_name, cls):
     """Every field of the ABI's structs sits at the same offset for a C
     compiler (gcc on include/spiir.h) and for the ctypes binding."""

@@ -177,6 +177,39 @@ def test_padding_filters_are_inert(oracle_mod):
     assert np.array_equal(oracle_mod.spiir_single(pad, x), z)
 
 
+def test_single_from_start_special_cases(oracle_mod):
+    """State zero before `start`: start = 0 is the ordinary recursion bit for
+    bit; z = 0 before start; strain that is zero before start leaves nothing
+    to forget, so the result is the ordinary recursion's."""
+    bank = inputs.single_rate_bank(3, [5, 1, 9], 40, seed=12)
+    x = inputs.strain(1, 700, seed=3)[0]
+    full = oracle_mod.spiir_single(bank, x)
+    assert np.array_equal(oracle_mod.spiir_single_from(bank, x, start=0), full)
+    z = oracle_mod.spiir_single_from(bank, x, start=300)
+    assert np.all(z[:, :300] == 0)
+    x0 = x.copy()
+    x0[:300] = 0.0
+    assert np.array_equal(oracle_mod.spiir_single_from(bank, x0, start=300)[:, 300:],
+                          oracle_mod.spiir_single(bank, x0)[:, 300:])
+
+
+def test_single_from_start_closed_form(oracle_mod):
+    """One filter per template: the solution of y[n] = a y[n-1] + b x[n-d]
+    splits at s into the zero-state solution from s plus the free response
+    a^(n-s+1) y[s-1] of the state it had, so
+    z_from[n] = z[n] - scale a^(n-s+1) y[s-1] with y[s-1] = z[s-1] / scale."""
+    bank = inputs.single_rate_bank(4, 1, 25, seed=13)
+    x = inputs.strain(1, 900, seed=4)[0]
+    s0, scale = 333, 2.0 / bank.base_rate
+    full = oracle_mod.spiir_single(bank, x)
+    got = oracle_mod.spiir_single_from(bank, x, start=s0)
+    a, _b = _complex(bank)
+    n = np.arange(s0, 900)
+    for t in range(4):
+        free = scale * a[t] ** (n - s0 + 1) * (full[t, s0 - 1] / scale)
+        assert _rel(got[t, s0:], full[t, s0:] - free) <= 1e-12
+
+
 # --------------------------------------------------------------------------
 # Multi-rate scheme (Sec. 2.2)
 # --------------------------------------------------------------------------
