@@ -398,9 +398,11 @@ spiir_status spiir_server_remove(spiir_server_t srv, int32_t member_id);
 int64_t spiir_server_member_footprint(spiir_server_t srv, const spiir_bank_desc *member);
 
 /* Filter one block of every stream: x_dev device float32
- * [n_streams][block_len]. Applies pending additions and removals first.
- * Asynchronous on cuda_stream. Errors: ESTATE (no member), ECUDA; ETIMEOUT
- * from an earlier push (spiir_server_sync_status). */
+ * [n_streams][block_len]. Applies pending additions and removals first. A
+ * push without members still takes the block into the strain history, so
+ * that members joining later read the continuous stream. Asynchronous on
+ * cuda_stream. Errors: ECUDA, ENOMEM; ETIMEOUT from an earlier push shows in
+ * spiir_server_sync_status. */
 spiir_status spiir_server_push(spiir_server_t srv, const float *x_dev, void *cuda_stream);
 
 /* The SNR of the last push for one member: z_dev device complex64

@@ -728,7 +728,6 @@ spiir_status spiir_server_push(spiir_server_t sv, const float *x_dev, void *cuda
     cudaStream_t s = (cudaStream_t)cuda_stream;
     spiir_status st;
     if (sv->dirty && (st = apply_changes(sv, s))) return st;
-    if (sv->members.empty()) return fail(SPIIR_ESTATE, "server has no member");
     CUDA_TRY(cudaMemcpyAsync(sv->xstage, x_dev, (int64_t)sv->S * sv->block * sizeof(float),
                              cudaMemcpyDeviceToDevice, s));
     const int gi = sv->pushes > 0 ? 1 : 0;

@@ -221,30 +221,32 @@ class BatchedServer(Server):
         rec = {"block": self.block, "admitted": admitted, "active": [a.req.rid for a in self.active],
                "templates": int(sum(a.req.bank.n_templates for a in self.active)),
                "used_bytes": self.used, "pending": len(self.pending)}
-        if self.active:
-            if self.use_cuda:
-                import torch
-                main = torch.cuda.current_stream()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(main)                          # the block is on the device
-                self.engine.push(x_block)
-                for a in self.active:
-                    self.engine.read(a.handle, out=a.out)
-                e1.record(main)
-                e1.synchronize()
+        # every block enters the server's strain history, with or without
+        # requests, so that a request joining later reads the continuous stream
+        if self.use_cuda:
+            import torch
+            main = torch.cuda.current_stream()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(main)                          # the block is on the device
+            self.engine.push(x_block)
+            for a in self.active:
+                self.engine.read(a.handle, out=a.out)
+            e1.record(main)
+            e1.synchronize()
+            if self.active:
                 ms = e0.elapsed_time(e1)
                 rec["latency_ms"] = [ms] * len(self.active)
                 rec["block_ms"] = ms
-                for a in self.active:
-                    if a.req.keep_snr:
-                        a.snr.append(a.out.cpu().numpy().copy())
-            else:
-                self.engine.push(x_block)
-                for a in self.active:
-                    out = self.engine.read(a.handle)
-                    if a.req.keep_snr:
-                        a.snr.append(out)
+            for a in self.active:
+                if a.req.keep_snr:
+                    a.snr.append(a.out.cpu().numpy().copy())
+        elif self.active:
+            self.engine.push(x_block)
+            for a in self.active:
+                out = self.engine.read(a.handle)
+                if a.req.keep_snr:
+                    a.snr.append(out)
         for a in self.active:
             a.blocks_done += 1
         self.block += 1

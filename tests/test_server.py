@@ -87,8 +87,6 @@ def _run(banks, spec, x, block, n_levels, max_delay, **kw):
                 ids[i] = srv.add(banks[i])
             if i in ids and b == first + life:
                 srv.remove(ids.pop(i))
-        if not ids:
-            continue
         srv.push(x[:, b * block:(b + 1) * block].contiguous())
         for i, mid in ids.items():
             outs[i].append(srv.read(mid).cpu().numpy())
