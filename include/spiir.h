@@ -337,8 +337,13 @@ spiir_status spiir_filter_noalloc(const spiir_bank_desc *desc, const float *x_de
  * and upsampler histories start at zero there, while its delayed inputs
  * x[n - d_k] read the server's continuous strain history (for a member
  * added before the first push that is the zero history of a new bank, and
- * its SNR equals that of a bank of its own). Each member's SNR is the same
- * whatever other members share the server (fixed summation order).
+ * its SNR equals that of a bank of its own). In the levels run in the block
+ * form the first chunk's FIR window reaches F samples back (F = max_delay + 1
+ * rounded up to 64), so there a late member's filters start F - d_k samples
+ * before its first sample: the start-up transients of the two forms differ
+ * by a term that decays with each filter's time constant. Each member's SNR
+ * is the same whatever other members share the server (fixed summation
+ * order).
  * ------------------------------------------------------------------------ */
 typedef struct spiir_server *spiir_server_t;
 

@@ -3,20 +3,29 @@
 //
 // Every push runs one prologue (strain history update) and one decimation
 // cascade for all members (Sec. 2.2), one persistent recursion launch over the
-// work items of every member and level (Eqs. iireq0, iireq1), and one
-// upsample-and-add launch over the templates of every member that needs it;
+// work items of every member and level that runs in the plain form (Eqs.
+// iireq0, iireq1), in the tensor-core modes one batched block-form launch
+// sequence per level (and pair of streams) over every member's filters at
+// that level, and one upsample-and-add launch over every member's templates;
 // the launches are replayed from a CUDA graph while the membership is
-// unchanged. Each member is planned exactly like a bank of its own
-// (make_plan, with the server's strain history), and its slots, template
-// rows and partial rows are placed in pooled device arrays:
-//   * filter slots (pole, gain, window offset, state per stream),
+// unchanged. Each member is planned like a bank of its own (make_plan with
+// the server's strain history; spiir_tc_pack per block-form level) and placed
+// in pooled device arrays:
+//   * plain filter slots (pole, gain, window offset, state per stream),
 //   * template rows (output ring, upsampler histories),
-//   * partial rows per level (per-push scratch of the level sums);
+//   * partial rows per level (per-push scratch of the level sums), the
+//     plain units' rows first, then 64 rows per impulse-response group,
+//   * per block-form level: impulse-response groups (64 templates) and carry
+//     tiles (128 filters: coefficients, power panel, FP64 state per stream);
 // each pool hands out contiguous ranges first-fit, reuses the ranges of
 // members that left, and grows geometrically (keeping every member's place
 // and its state). The work lists (warp tasks, CTA items, queue order,
-// destinations, combine lists) are rebuilt on the host and uploaded whenever
-// the membership changes; the kernels are the bank's own.
+// destinations, group and carry lists, combine lists) are rebuilt on the host
+// and uploaded whenever the membership changes; the kernels are the bank's.
+//
+// In the block form a level's alignment delay D_i (Sec. 2.2) is a delay of
+// the strain the level reads (its window starts D_i samples earlier), so the
+// FIR length stays the largest filter delay plus one.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,6 +36,7 @@
 #include "spiir.h"
 #include "spiir_internal.h"
 #include "spiir_plan.h"
+#include "spiir_tc.h"
 
 using namespace spiir_host;
 
@@ -115,15 +125,43 @@ struct DevVec {
     }
 };
 
+// A member's part at one block-form level.
+struct MemberTc {
+    bool used = false;           // the member has filters at this level
+    int64_t g0 = 0, ng = 0;      // impulse-response groups
+    int64_t t0 = 0, nt = 0;      // carry tiles
+    TcPack pk;                   // host packing (only has_carry kept once uploaded)
+};
+
 struct Member {
     int id = 0;
     int T = 0;
-    Plan p;                      // the member's own plan (server history)
+    Plan p;                      // plan of the member's plain-form levels
     int64_t slot0 = 0;           // first pooled filter slot
     int64_t row0 = 0;            // first pooled template row
     int64_t prow0[SPIIR_MAX_LEVELS] = {};   // first pooled partial row per level
+    MemberTc tc[SPIIR_MAX_LEVELS];
+    bool combine = false;        // its templates go through the combine pass
     int64_t n_filters = 0;
+    int64_t fs_per_push = 0;     // filter-samples of one push per stream
     bool pushed = false;         // has taken part in a push
+};
+
+// One block-form level of the server: pools and per-push lists.
+struct TcPool {
+    bool on = false;
+    int hist_read = 0;           // strain history before the push, minus D_i
+    RangeAlloc group_alloc, tile_alloc;
+    uint4 *H = nullptr;          // [group][slice][16 KB]
+    float *row_scale = nullptr;  // [group * 64 + r]
+    uint8_t *has_carry = nullptr;
+    int32_t *tile_ptr = nullptr, *tile_end = nullptr;
+    float2 *a = nullptr, *aJ = nullptr, *c = nullptr, *aLf = nullptr;   // [tile * 128 + k]
+    uint4 *aL = nullptr, *aLb1 = nullptr, *aLb2 = nullptr;
+    uint4 *v = nullptr;          // [stream][tile * 128 + k]
+    uint4 *panel = nullptr;      // [tile][32 KB]
+    DevVec<int32_t> groups, tmpl_of;
+    int n_groups = 0, n_carry = 0;
 };
 
 }  // namespace
@@ -136,6 +174,11 @@ struct spiir_server {
     Plan geo;                    // sizes of an empty member: strain layout,
                                  // segment lengths, partial strides, history
     int smem_bytes = 0, ctas_per_sm = 1, n_sms = 1;
+    // block form
+    bool tc_mode = false, bf16 = false, df = false;
+    int tcL = 256, tcF = 0, tcK = 0, n_slices = 0, n_tc_levels = 0;
+    TcPool tcp[SPIIR_MAX_LEVELS];
+    uint4 *hank = nullptr, *xseg = nullptr;
     // shared strain
     float *xbuf = nullptr, *xstage = nullptr;
     unsigned int *status = nullptr;
@@ -146,7 +189,7 @@ struct spiir_server {
     float2 *state = nullptr;     // [stream][slot cap]
     float2 *z = nullptr;         // [stream][row cap][block]
     float2 *ubuf = nullptr;      // [stream][level 1..H][row cap][SPIIR_UHIST]
-    float2 *partial = nullptr;   // [stream][level][prow cap][stride]
+    float2 *partial = nullptr;   // [stream][level][rows][stride]
     int64_t part_base[SPIIR_MAX_LEVELS] = {}, part_stream_stride = 0;
     // work lists
     DevVec<WarpTask> tasks;
@@ -164,6 +207,11 @@ struct spiir_server {
     // graph of one push (by previous push length: 0 for the first)
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int launches = 0;
+
+    // rows of partial level i before its block-form rows
+    int64_t tc_row_base(int i) const { return prow_alloc[i].cap(); }
+    int64_t level_rows(int i) const { return prow_alloc[i].cap() + 64 * tcp[i].group_alloc.cap(); }
 
     void drop_graphs() {
         for (auto &g : graph)
@@ -174,7 +222,7 @@ struct spiir_server {
     }
     void release() {
         drop_graphs();
-        void *ptrs[] = {xbuf, xstage, status, are, aim, bre, bim, xoff, state, z, ubuf, partial};
+        void *ptrs[] = {xbuf, xstage, status, are, aim, bre, bim, xoff, state, z, ubuf, partial, hank, xseg};
         for (void *q : ptrs)
             if (q) cudaFree(q);
         xbuf = xstage = nullptr;
@@ -182,6 +230,21 @@ struct spiir_server {
         are = aim = bre = bim = nullptr;
         xoff = nullptr;
         state = z = ubuf = partial = nullptr;
+        hank = xseg = nullptr;
+        for (auto &t : tcp) {
+            void *tp[] = {t.H, t.row_scale, t.has_carry, t.tile_ptr, t.tile_end, t.a, t.aJ, t.c, t.aLf,
+                          t.aL, t.aLb1, t.aLb2, t.v, t.panel};
+            for (void *q : tp)
+                if (q) cudaFree(q);
+            t.H = nullptr;
+            t.row_scale = nullptr;
+            t.has_carry = nullptr;
+            t.tile_ptr = t.tile_end = nullptr;
+            t.a = t.aJ = t.c = t.aLf = nullptr;
+            t.aL = t.aLb1 = t.aLb2 = t.v = t.panel = nullptr;
+            t.groups.release();
+            t.tmpl_of.release();
+        }
         tasks.release();
         items.release();
         order.release();
@@ -198,8 +261,9 @@ struct spiir_server {
 
 namespace {
 
-// The description a member is planned with: its filters, the server's shape.
-spiir_bank_desc member_desc(const spiir_server *sv, const spiir_bank_desc *m) {
+// The description a member's plain levels are planned with: its filters at
+// those levels, the server's shape.
+spiir_bank_desc plain_desc(const spiir_server *sv, const spiir_bank_desc *m) {
     spiir_bank_desc d = *m;
     d.n_streams = sv->S;
     d.block_len = sv->block;
@@ -218,8 +282,8 @@ spiir_bank_desc member_desc(const spiir_server *sv, const spiir_bank_desc *m) {
     return d;
 }
 
-// Grow a [outer][cap] array to [outer][new_cap], keeping the first cap of
-// each row; new entries are zero.
+// Grow a [outer][cap * inner] array to [outer][new_cap * inner], keeping the
+// first cap entries of each row; new entries are zero.
 template <typename T>
 spiir_status grow_rows(T **p, int64_t outer, int64_t cap, int64_t new_cap, int64_t inner, cudaStream_t s) {
     T *q = nullptr;
@@ -236,9 +300,10 @@ spiir_status grow_rows(T **p, int64_t outer, int64_t cap, int64_t new_cap, int64
     return SPIIR_OK;
 }
 
+int64_t grown(int64_t need, int64_t cap) { return std::max<int64_t>(need, cap + cap / 2); }
+
 spiir_status grow_slots(spiir_server *sv, int64_t need, cudaStream_t s) {
-    const int64_t cap = sv->slot_alloc.cap();
-    const int64_t nc = std::max<int64_t>(need, cap + cap / 2);
+    const int64_t cap = sv->slot_alloc.cap(), nc = grown(need, cap);
     spiir_status st;
     if ((st = grow_rows(&sv->are, 1, cap, nc, 1, s)) || (st = grow_rows(&sv->aim, 1, cap, nc, 1, s)) ||
         (st = grow_rows(&sv->bre, 1, cap, nc, 1, s)) || (st = grow_rows(&sv->bim, 1, cap, nc, 1, s)) ||
@@ -249,8 +314,7 @@ spiir_status grow_slots(spiir_server *sv, int64_t need, cudaStream_t s) {
 }
 
 spiir_status grow_template_rows(spiir_server *sv, int64_t need, cudaStream_t s) {
-    const int64_t cap = sv->row_alloc.cap();
-    const int64_t nc = std::max<int64_t>(need, cap + cap / 2);
+    const int64_t cap = sv->row_alloc.cap(), nc = grown(need, cap);
     spiir_status st;
     // the output ring is per-push: no contents to keep
     if (sv->z) {
@@ -265,14 +329,12 @@ spiir_status grow_template_rows(spiir_server *sv, int64_t need, cudaStream_t s) 
     return SPIIR_OK;
 }
 
-// Partial rows are per-push scratch: growing reallocates without copying.
-spiir_status grow_partial_rows(spiir_server *sv, int level, int64_t need, cudaStream_t s) {
-    const int64_t cap = sv->prow_alloc[level].cap();
-    sv->prow_alloc[level].grow(std::max<int64_t>(need, cap + cap / 2));
+// Partial rows are per-push scratch: a new layout reallocates without copying.
+spiir_status relayout_partial(spiir_server *sv, cudaStream_t s) {
     int64_t off = 0;
     for (int i = 0; i < sv->L; ++i) {
         sv->part_base[i] = off;
-        off += sv->prow_alloc[i].cap() * sv->geo.part_stride[i];
+        off += sv->level_rows(i) * sv->geo.part_stride[i];
     }
     sv->part_stream_stride = off;
     if (sv->partial) {
@@ -281,6 +343,91 @@ spiir_status grow_partial_rows(spiir_server *sv, int level, int64_t need, cudaSt
         sv->partial = nullptr;
     }
     CUDA_TRY(cudaMalloc((void **)&sv->partial, std::max<int64_t>(1, sv->S * off) * sizeof(float2)));
+    return SPIIR_OK;
+}
+
+spiir_status grow_groups(spiir_server *sv, TcPool &t, int64_t need, cudaStream_t s) {
+    const int64_t cap = t.group_alloc.cap(), nc = grown(need, cap);
+    spiir_status st;
+    const int64_t slice16 = (int64_t)sv->n_slices * (kTcSliceBytes / 16);
+    if ((st = grow_rows(&t.H, 1, cap, nc, slice16, s)) || (st = grow_rows(&t.row_scale, 1, cap, nc, 64, s)) ||
+        (st = grow_rows(&t.has_carry, 1, cap, nc, 64, s)) || (st = grow_rows(&t.tile_ptr, 1, cap, nc, 64, s)) ||
+        (st = grow_rows(&t.tile_end, 1, cap, nc, 64, s)))
+        return st;
+    t.group_alloc.grow(nc);
+    return relayout_partial(sv, s);
+}
+
+spiir_status grow_tiles(spiir_server *sv, TcPool &t, int64_t need, cudaStream_t s) {
+    const int64_t cap = t.tile_alloc.cap(), nc = grown(need, cap);
+    spiir_status st;
+    if ((st = grow_rows(&t.a, 1, cap, nc, kTcTile, s)) || (st = grow_rows(&t.aJ, 1, cap, nc, kTcTile, s)) ||
+        (st = grow_rows(&t.c, 1, cap, nc, kTcTile, s)) || (st = grow_rows(&t.aLf, 1, cap, nc, kTcTile, s)) ||
+        (st = grow_rows(&t.aL, 1, cap, nc, kTcTile, s)) || (st = grow_rows(&t.aLb1, 1, cap, nc, kTcTile, s)) ||
+        (st = grow_rows(&t.aLb2, 1, cap, nc, kTcTile, s)) ||
+        (st = grow_rows(&t.v, sv->S, cap, nc, kTcTile, s)) ||
+        (st = grow_rows(&t.panel, 1, cap, nc, kTcPanelBytes / 16, s)))
+        return st;
+    t.tile_alloc.grow(nc);
+    return SPIIR_OK;
+}
+
+template <typename T>
+spiir_status put(T *dst, const std::vector<T> &src, cudaStream_t s) {
+    if (!src.empty())
+        CUDA_TRY(cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return SPIIR_OK;
+}
+
+// Place a member's block-form part at level i.
+spiir_status place_tc(spiir_server *sv, Member &m, int i, cudaStream_t s) {
+    MemberTc &mt = m.tc[i];
+    TcPool &t = sv->tcp[i];
+    const TcPack &pk = mt.pk;
+    spiir_status st;
+    mt.ng = pk.n_groups;
+    mt.nt = pk.n_tiles;
+    int64_t at = t.group_alloc.take(mt.ng);
+    if (at < 0) {
+        if ((st = grow_groups(sv, t, t.group_alloc.need_for(mt.ng), s))) return st;
+        at = t.group_alloc.take(mt.ng);
+    }
+    mt.g0 = at;
+    at = t.tile_alloc.take(mt.nt);
+    if (at < 0) {
+        if ((st = grow_tiles(sv, t, t.tile_alloc.need_for(mt.nt), s))) return st;
+        at = t.tile_alloc.take(mt.nt);
+    }
+    mt.t0 = at;
+    const int64_t slice16 = (int64_t)sv->n_slices * (kTcSliceBytes / 16);
+    CUDA_TRY(cudaMemcpyAsync(t.H + mt.g0 * slice16, pk.H.data(), pk.H.size() * sizeof(uint16_t),
+                             cudaMemcpyHostToDevice, s));
+    // per row of the member's groups (rows past its templates are inert)
+    const int64_t nr = mt.ng * 64;
+    std::vector<float> rs(nr, 0.f);
+    std::vector<uint8_t> hc(nr, 0);
+    std::vector<int32_t> tp(nr, 0), te(nr, 0);
+    for (int r = 0; r < m.T; ++r) {
+        rs[r] = pk.row_scale[r];
+        hc[r] = pk.has_carry[r];
+        tp[r] = (int32_t)(mt.t0 + pk.tile_ptr[r]);
+        te[r] = (int32_t)(mt.t0 + pk.tile_ptr[r + 1]);
+    }
+    const int64_t r0 = mt.g0 * 64;
+    if ((st = put(t.row_scale + r0, rs, s)) || (st = put(t.has_carry + r0, hc, s)) ||
+        (st = put(t.tile_ptr + r0, tp, s)) || (st = put(t.tile_end + r0, te, s)))
+        return st;
+    const int64_t k0 = mt.t0 * kTcTile;
+    if ((st = put(t.a + k0, pk.a, s)) || (st = put(t.aJ + k0, pk.aJ, s)) || (st = put(t.c + k0, pk.c, s)) ||
+        (st = put(t.aLf + k0, pk.aLf, s)) || (st = put(t.aL + k0, pk.aL, s)) ||
+        (st = put(t.aLb1 + k0, pk.aLb1, s)) || (st = put(t.aLb2 + k0, pk.aLb2, s)))
+        return st;
+    if (mt.nt > 0) {
+        CUDA_TRY(cudaMemcpyAsync(t.panel + mt.t0 * (kTcPanelBytes / 16), pk.panel.data(),
+                                 pk.panel.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemset2DAsync(t.v + k0, t.tile_alloc.cap() * kTcTile * sizeof(uint4), 0,
+                                   mt.nt * kTcTile * sizeof(uint4), sv->S, s));
+    }
     return SPIIR_OK;
 }
 
@@ -304,11 +451,14 @@ spiir_status place(spiir_server *sv, Member &m, cudaStream_t s) {
     for (int i = 0; i < sv->L; ++i) {
         at = sv->prow_alloc[i].take(p.part_rows[i]);
         if (at < 0) {
-            if ((st = grow_partial_rows(sv, i, sv->prow_alloc[i].need_for(p.part_rows[i]), s))) return st;
+            sv->prow_alloc[i].grow(grown(sv->prow_alloc[i].need_for(p.part_rows[i]), sv->prow_alloc[i].cap()));
+            if ((st = relayout_partial(sv, s))) return st;
             at = sv->prow_alloc[i].take(p.part_rows[i]);
         }
         m.prow0[i] = at;
     }
+    for (int i = 0; i < sv->L; ++i)
+        if (m.tc[i].used && (st = place_tc(sv, m, i, s))) return st;
     const int64_t n = p.n_slots, cap = sv->slot_alloc.cap(), rcap = sv->row_alloc.cap();
     if (n > 0) {
         CUDA_TRY(cudaMemcpyAsync(sv->are + m.slot0, p.are.data(), n * 4, cudaMemcpyHostToDevice, s));
@@ -329,7 +479,13 @@ spiir_status place(spiir_server *sv, Member &m, cudaStream_t s) {
 void unplace(spiir_server *sv, const Member &m) {
     sv->slot_alloc.give(m.slot0, m.p.n_slots);
     sv->row_alloc.give(m.row0, m.T);
-    for (int i = 0; i < sv->L; ++i) sv->prow_alloc[i].give(m.prow0[i], m.p.part_rows[i]);
+    for (int i = 0; i < sv->L; ++i) {
+        sv->prow_alloc[i].give(m.prow0[i], m.p.part_rows[i]);
+        if (m.tc[i].used) {
+            sv->tcp[i].group_alloc.give(m.tc[i].g0, m.tc[i].ng);
+            sv->tcp[i].tile_alloc.give(m.tc[i].t0, m.tc[i].nt);
+        }
+    }
 }
 
 // Work lists of all members, in member order, with pooled indices.
@@ -379,20 +535,23 @@ spiir_status rebuild_lists(spiir_server *sv, cudaStream_t s) {
     order.resize(items.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = (int32_t)i;
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return work[a] > work[b]; });
-    // combine lists over the pooled template rows
+    // combine lists over the pooled template rows: the plain units' partial
+    // rows, then the template's block-form row of each block-form level
     std::vector<int32_t> cptr((size_t)rcap * sv->L + 1, 0), crows, clist;
     for (int64_t r = 0; r < rcap; ++r) {
         const int mi = owner[r];
         const Member *m = mi >= 0 ? mv[mi] : nullptr;
-        const bool comb = m && m->p.need_combine;
+        const bool comb = m && m->combine;
         if (comb) clist.push_back((int32_t)r);
         for (int i = 0; i < sv->L; ++i) {
             const size_t j = (size_t)r * sv->L + i;
             if (comb) {
                 const int t = (int)(r - m->row0);
                 const Plan &p = m->p;
-                for (int32_t q = p.comb_ptr[(size_t)t * sv->L + i]; q < p.comb_ptr[(size_t)t * sv->L + i + 1]; ++q)
-                    crows.push_back((int32_t)(m->prow0[i] + p.comb_rows[q]));
+                if (!p.comb_ptr.empty())
+                    for (int32_t q = p.comb_ptr[(size_t)t * sv->L + i]; q < p.comb_ptr[(size_t)t * sv->L + i + 1]; ++q)
+                        crows.push_back((int32_t)(m->prow0[i] + p.comb_rows[q]));
+                if (m->tc[i].used) crows.push_back((int32_t)(sv->tc_row_base(i) + m->tc[i].g0 * 64 + t));
             }
             cptr[j + 1] = (int32_t)crows.size();
         }
@@ -407,6 +566,23 @@ spiir_status rebuild_lists(spiir_server *sv, cudaStream_t s) {
     sv->n_items = (int)items.size();
     sv->n_tasks = (int)tasks.size();
     sv->n_comb = (int)clist.size();
+    // block-form lists: the groups of every member at the level, and the
+    // pooled rows of the templates that own carry tiles
+    for (int i = 0; i < sv->L; ++i) {
+        TcPool &t = sv->tcp[i];
+        if (!t.on) continue;
+        std::vector<int32_t> gl, tl;
+        for (const Member *m : mv) {
+            const MemberTc &mt = m->tc[i];
+            if (!mt.used) continue;
+            for (int64_t g = 0; g < mt.ng; ++g) gl.push_back((int32_t)(mt.g0 + g));
+            for (int r = 0; r < m->T && r < (int)mt.pk.has_carry.size(); ++r)
+                if (mt.pk.has_carry[r]) tl.push_back((int32_t)(mt.g0 * 64 + r));
+        }
+        if ((st = t.groups.upload(gl, s)) || (st = t.tmpl_of.upload(tl, s))) return st;
+        t.n_groups = (int)gl.size();
+        t.n_carry = (int)tl.size();
+    }
     return SPIIR_OK;
 }
 
@@ -424,13 +600,20 @@ spiir_status apply_changes(spiir_server *sv, cudaStream_t s) {
         // the packed coefficients are on the device now; keep the lists
         const int id = m.id;
         sv->members.emplace(id, std::move(m));
-        Plan &p = sv->members[id].p;
+        Member &mm = sv->members[id];
+        Plan &p = mm.p;
         std::vector<float>().swap(p.are);
         std::vector<float>().swap(p.aim);
         std::vector<float>().swap(p.bre);
         std::vector<float>().swap(p.bim);
         std::vector<int32_t>().swap(p.xoff);
         std::vector<int64_t>().swap(p.slot_filter);
+        for (auto &mt : mm.tc) {
+            // keep only which templates own tiles (for the carry lists)
+            std::vector<uint8_t> hc = std::move(mt.pk.has_carry);
+            mt.pk = TcPack();
+            mt.pk.has_carry = std::move(hc);
+        }
     }
     sv->pending_add.clear();
     spiir_status st = rebuild_lists(sv, s);
@@ -461,6 +644,7 @@ void level_args(const spiir_server *sv, int64_t n_prev, LevelArgs *lev) {
 // The kernels of one push (reading the strain from xstage).
 spiir_status launch_push(spiir_server *sv, int64_t n_prev, cudaStream_t st) {
     const int S = sv->S;
+    int launches = 0;
     PrologueArgs pa{};
     pa.queue = sv->queue.p;
     pa.prog = sv->prog.p;
@@ -473,6 +657,7 @@ spiir_status launch_push(spiir_server *sv, int64_t n_prev, cudaStream_t st) {
     pa.n_levels = sv->L;
     level_args(sv, n_prev, pa.lev);
     CUDA_TRY(spiir_launch_prologue(pa, S, st));
+    ++launches;
     if (sv->L > 1) {
         DecimArgs da{};
         da.xbuf = sv->xbuf;
@@ -483,6 +668,7 @@ spiir_status launch_push(spiir_server *sv, int64_t n_prev, cudaStream_t st) {
         for (size_t j = 0; j < sv->h_down.size(); ++j) da.h_down[j] = sv->h_down[j];
         level_args(sv, n_prev, da.lev);
         CUDA_TRY(spiir_launch_decimate(da, S, st));
+        ++launches;
     }
     if (sv->n_items > 0) {
         RecurArgs ra{};
@@ -518,6 +704,58 @@ spiir_status launch_push(spiir_server *sv, int64_t n_prev, cudaStream_t st) {
         const int64_t resident = std::max<int64_t>(1, (int64_t)sv->ctas_per_sm * sv->n_sms / S);
         const int ctas = (int)std::min<int64_t>(total, resident);
         CUDA_TRY(spiir_launch_recur(ra, sv->variant, ctas, S, sv->smem_bytes, st));
+        ++launches;
+    }
+    // block-form levels: each level's sums into its partial rows (unscaled;
+    // the combine pass applies the SNR scale), streams two at a time
+    for (int i = 0; i < sv->L; ++i) {
+        const TcPool &t = sv->tcp[i];
+        if (!t.on || t.n_groups == 0) continue;
+        for (int q0 = 0; q0 < S; q0 += 2) {
+            TcLaunch l{};
+            l.xbuf = sv->xbuf + sv->geo.xbuf_off[i];
+            l.xbuf_stride = sv->geo.xbuf_stream_stride;
+            l.hist = t.hist_read;
+            l.F = sv->tcF;
+            l.L = sv->tcL;
+            l.K = sv->tcK;
+            l.n_chunks = (sv->block >> i) / sv->tcL;
+            l.n_streams = std::min(2, S - q0);
+            l.stream0 = q0;
+            l.hank = sv->hank;
+            l.xseg = sv->xseg;
+            l.tile_ptr = t.tile_ptr;
+            l.tile_end = t.tile_end;
+            l.tmpl_of = t.tmpl_of.p;
+            l.n_carry = t.n_carry;
+            l.a = t.a;
+            l.aJ = t.aJ;
+            l.aLf = t.aLf;
+            l.c = t.c;
+            l.aL = t.aL;
+            l.aLb1 = t.aLb1;
+            l.aLb2 = t.aLb2;
+            l.panel = t.panel;
+            l.v = t.v;
+            l.n_slots = t.tile_alloc.cap() * kTcTile;
+            l.carry_scale = 1.0f;
+            l.H = t.H;
+            l.row_scale = t.row_scale;
+            l.has_carry = t.has_carry;
+            l.groups = t.groups.p;
+            l.n_groups = t.n_groups;
+            l.n_rows = (int)(64 * t.group_alloc.cap());
+            l.z = sv->partial + sv->part_base[i] + sv->tc_row_base(i) * sv->geo.part_stride[i];
+            l.z_row_stride = sv->geo.part_stride[i];
+            l.z_stream_stride = sv->part_stream_stride;
+            l.bf16 = sv->bf16;
+            l.df = sv->df;
+            l.status = sv->status;
+            l.n_sms = sv->n_sms;
+            spiir_status r = spiir_tc_launch(l, st, nullptr);
+            if (r) return fail(r, "%s", spiir_tc_last_error());
+            launches += 2 + (t.n_carry > 0);
+        }
     }
     if (sv->n_comb > 0) {
         CombineArgs ca{};
@@ -540,17 +778,26 @@ spiir_status launch_push(spiir_server *sv, int64_t n_prev, cudaStream_t st) {
         for (size_t j = 0; j < sv->h_up.size(); ++j) ca.h_up2[j] = 2.0f * sv->h_up[j];
         level_args(sv, n_prev, ca.lev);
         CUDA_TRY(spiir_launch_combine(ca, spiir_combine_chunk(sv->L, sv->block), S, st));
+        ++launches;
     }
+    sv->launches = launches;
     return SPIIR_OK;
 }
 
-int64_t member_bytes(const spiir_server *sv, const Plan &p, int T) {
+int64_t member_bytes(const spiir_server *sv, const Member &m) {
+    const Plan &p = m.p;
     const int64_t S = sv->S;
     int64_t b = p.n_slots * (4 * 4 + 4 + 8 * S);
-    b += (int64_t)T * S * ((int64_t)sv->block + (int64_t)sv->H * SPIIR_UHIST) * 8;
+    b += (int64_t)m.T * S * ((int64_t)sv->block + (int64_t)sv->H * SPIIR_UHIST) * 8;
     for (int i = 0; i < sv->L; ++i) b += p.part_rows[i] * S * sv->geo.part_stride[i] * 8;
     b += (int64_t)p.tasks.size() * (sizeof(WarpTask) + 32 * 4) + (int64_t)p.items.size() * (sizeof(CtaItem) + 4 + 4 * S);
-    b += (int64_t)T * sv->L * 4 + p.n_slots * 4;
+    b += (int64_t)m.T * sv->L * 4 + p.n_slots * 4;
+    for (int i = 0; i < sv->L; ++i) {
+        const MemberTc &mt = m.tc[i];
+        if (!mt.used) continue;
+        b += mt.pk.n_groups * ((int64_t)sv->n_slices * kTcSliceBytes + 64 * (4 + 1 + 8) + 64 * S * sv->geo.part_stride[i] * 8);
+        b += (int64_t)mt.pk.n_tiles * (kTcPanelBytes + kTcTile * (32 + 48 + 16 * S));
+    }
     return b;
 }
 
@@ -559,10 +806,75 @@ spiir_status check_member(const spiir_server *sv, const spiir_bank_desc *m) {
     if (m->n_levels != sv->L)
         return fail(SPIIR_EINVAL, "member has %d levels, the server %d", m->n_levels, sv->L);
     if (m->base_rate != sv->d.base_rate) return fail(SPIIR_EINVAL, "member base_rate differs from the server's");
+    if (m->n_filters > 0 && !m->delay) return fail(SPIIR_EINVAL, "filter arrays must not be NULL");
     for (int64_t k = 0; k < m->n_filters; ++k)
-        if (m->delay && m->delay[k] > sv->d.max_delay)
+        if (m->delay[k] > sv->d.max_delay)
             return fail(SPIIR_EINVAL, "delay[%lld] = %d above the server's max_delay %d", (long long)k,
                         m->delay[k], sv->d.max_delay);
+    return SPIIR_OK;
+}
+
+// Plan a member: its plain levels with make_plan, each block-form level with
+// spiir_tc_pack (arrays == false: sizes only, for the footprint).
+spiir_status build_member(const spiir_server *sv, const spiir_bank_desc *member, bool arrays, Member &m) {
+    spiir_status st = check_member(sv, member);
+    if (st) return st;
+    spiir_bank_desc d = plain_desc(sv, member);
+    if ((st = validate(&d))) return st;
+    m.T = d.n_templates;
+    m.n_filters = d.n_filters;
+    m.fs_per_push = 0;
+    for (int64_t k = 0; k < d.n_filters; ++k) m.fs_per_push += sv->block >> (d.level ? d.level[k] : 0);
+    // the plain levels' filters
+    std::vector<float> ar, ai, br, bi;
+    std::vector<int32_t> dl, tid;
+    std::vector<int8_t> lv;
+    bool any_tc = false;
+    for (int i = 0; i < sv->L; ++i) m.tc[i].used = false;
+    for (int64_t k = 0; k < d.n_filters; ++k) {
+        const int l = d.level ? d.level[k] : 0;
+        if (sv->tcp[l].on) {
+            m.tc[l].used = true;
+            any_tc = true;
+            continue;
+        }
+        ar.push_back(d.a_re[k]);
+        ai.push_back(d.a_im[k]);
+        br.push_back(d.b_re[k]);
+        bi.push_back(d.b_im[k]);
+        dl.push_back(d.delay[k]);
+        tid.push_back(d.template_id[k]);
+        lv.push_back((int8_t)l);
+    }
+    spiir_bank_desc dp = d;
+    dp.n_filters = (int64_t)ar.size();
+    dp.a_re = ar.data();
+    dp.a_im = ai.data();
+    dp.b_re = br.data();
+    dp.b_im = bi.data();
+    dp.delay = dl.data();
+    dp.template_id = tid.data();
+    dp.level = lv.data();
+    if ((st = make_plan(&dp, sv->variant, arrays, m.p, sv->geo.hist))) return st;
+    if (m.p.smem_bytes > sv->smem_bytes)
+        return fail(SPIIR_EINVAL, "member needs more shared memory than the server's kernel setup");
+    m.combine = m.p.need_combine || any_tc;
+    for (int i = 0; i < sv->L; ++i) {
+        if (!m.tc[i].used) continue;
+        if (arrays) {
+            if ((st = spiir_tc_pack(&d, i, sv->tcF, sv->tcL, 1.0, sv->bf16, sv->df, m.tc[i].pk)))
+                return fail(st, "%s", spiir_tc_last_error());
+        } else {
+            // sizes only: groups of 64 templates, tiles of 128 filters per template
+            std::vector<int64_t> cnt(m.T, 0);
+            for (int64_t k = 0; k < d.n_filters; ++k)
+                if ((d.level ? d.level[k] : 0) == i) cnt[d.template_id[k]]++;
+            m.tc[i].pk.n_groups = (m.T + 63) / 64;
+            int nt = 0;
+            for (int t = 0; t < m.T; ++t) nt += (int)((cnt[t] + kTcTile - 1) / kTcTile);
+            m.tc[i].pk.n_tiles = nt;
+        }
+    }
     return SPIIR_OK;
 }
 
@@ -574,12 +886,17 @@ spiir_status spiir_server_create(const spiir_server_desc *desc, void *cuda_strea
     if (!out) return fail(SPIIR_EINVAL, "out is NULL");
     *out = nullptr;
     if (!desc) return fail(SPIIR_EINVAL, "desc is NULL");
-    if (desc->mode != SPIIR_PLAIN_FP32)
-        return fail(SPIIR_EUNSUPPORTED, "server: tensor-core modes are not available");
+    if (desc->mode != SPIIR_PLAIN_FP32 && desc->mode != SPIIR_TC_FP16 && desc->mode != SPIIR_TC_BF16)
+        return fail(SPIIR_EUNSUPPORTED, "server: mode must be PLAIN_FP32, TC_FP16 or TC_BF16");
     if (desc->max_delay < 0 || desc->max_delay > (1 << 20))
         return fail(SPIIR_EINVAL, "max_delay must be in [0, 2^20]");
     if (desc->n_levels < 1 || desc->n_levels > SPIIR_MAX_LEVELS)
         return fail(SPIIR_EINVAL, "n_levels must be in [1, %d]", SPIIR_MAX_LEVELS);
+    if (desc->carry != 0 && desc->carry != 1) return fail(SPIIR_EINVAL, "carry must be 0 or 1");
+    const bool tc = desc->mode != SPIIR_PLAIN_FP32;
+    const int tcL = desc->chunk_len ? desc->chunk_len : 256;
+    if (tc && tcL != 128 && tcL != 256) return fail(SPIIR_EUNSUPPORTED, "chunk_len must be 128 or 256");
+    const int tcF = (int)(((int64_t)desc->max_delay + 1 + 63) / 64 * 64);
     // the shape is checked by planning an empty bank of it
     spiir_bank_desc e{};
     e.n_templates = 1;
@@ -625,9 +942,22 @@ spiir_status spiir_server_create(const spiir_server_desc *desc, void *cuda_strea
     // members (small units), 8 for single rate
     sv->variant = desc->tune < 0 ? std::min(-desc->tune - 1, spiir_recur_variant_count() - 1)
                                  : (desc->n_levels > 1 ? 2 : 3);
-    // the strain history every member can use: the largest delay plus the
-    // level's alignment delay (a bank with a filter of delay max_delay at
-    // every level)
+    // block form: the levels whose push holds whole chunks
+    sv->tc_mode = tc;
+    sv->bf16 = desc->mode == SPIIR_TC_BF16;
+    sv->df = desc->carry == 1;
+    sv->tcL = tcL;
+    sv->tcF = tcF;
+    sv->tcK = tcF + tcL;
+    sv->n_slices = sv->tcK / 64;
+    if (tc)
+        for (int i = 0; i < sv->L; ++i)
+            if ((sv->block >> i) >= tcL && (sv->block >> i) % tcL == 0) {
+                sv->tcp[i].on = true;
+                sv->n_tc_levels++;
+            }
+    // the strain history every member can use: the largest delay (the FIR
+    // length in the block form) plus the level's alignment delay
     {
         spiir_bank_desc g = e;
         g.h_down = sv->h_down.data();
@@ -635,7 +965,7 @@ spiir_status spiir_server_create(const spiir_server_desc *desc, void *cuda_strea
         g.n_taps = nt;
         g.n_taps_up = ntu;
         std::vector<float> one(sv->L, 0.f);
-        std::vector<int32_t> dl(sv->L, desc->max_delay), tid(sv->L, 0);
+        std::vector<int32_t> dl(sv->L, tc ? tcF : desc->max_delay), tid(sv->L, 0);
         std::vector<int8_t> lv(sv->L);
         for (int i = 0; i < sv->L; ++i) lv[i] = (int8_t)i;
         g.n_filters = sv->L;
@@ -648,6 +978,9 @@ spiir_status spiir_server_create(const spiir_server_desc *desc, void *cuda_strea
             return st;
         }
     }
+    for (int i = 0; i < sv->L; ++i)
+        if (sv->tcp[i].on)
+            sv->tcp[i].hist_read = sv->geo.hist[i] - (int)align_delay(i, sv->L, nt, ntu, sv->d.align);
     sv->smem_bytes = sv->geo.smem_bytes;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     auto bail = [&](spiir_status r) {
@@ -662,6 +995,19 @@ spiir_status spiir_server_create(const spiir_server_desc *desc, void *cuda_strea
     cudaError_t e1 = spiir_recur_prepare(sv->variant, sv->smem_bytes, &sv->ctas_per_sm);
     if (e1 == cudaSuccess) e1 = spiir_combine_prepare();
     if (e1 != cudaSuccess) return bail(fail(SPIIR_ECUDA, "kernel setup: %s", cudaGetErrorString(e1)));
+    if (sv->n_tc_levels > 0) {
+        if ((st = spiir_tc_prepare(sv->tcL, sv->tcK))) return bail(fail(st, "%s", spiir_tc_last_error()));
+        // staging buffers for the largest level (level 0 holds the most chunks)
+        int64_t cmax = 0;
+        for (int i = 0; i < sv->L; ++i)
+            if (sv->tcp[i].on) cmax = std::max<int64_t>(cmax, (sv->block >> i) / sv->tcL);
+        const int64_t hb = spiir_tc_hank_bytes(sv->tcL, sv->tcK);
+        const int cpb = spiir_tc_cpb(2, sv->tcL);
+        const int64_t nb = std::max<int64_t>((cmax + cpb - 1) / cpb + 1, cmax);
+        if (cudaMalloc((void **)&sv->hank, 2 * cmax * hb) != cudaSuccess ||
+            cudaMalloc((void **)&sv->xseg, nb * spiir_tc_xseg_bytes()) != cudaSuccess)
+            return bail(fail(SPIIR_ENOMEM, "server staging buffers"));
+    }
     const int64_t xs = sv->S * sv->geo.xbuf_stream_stride;
     if (cudaMalloc((void **)&sv->xbuf, xs * sizeof(float)) != cudaSuccess ||
         cudaMalloc((void **)&sv->xstage, (int64_t)sv->S * sv->block * sizeof(float)) != cudaSuccess ||
@@ -671,7 +1017,7 @@ spiir_status spiir_server_create(const spiir_server_desc *desc, void *cuda_strea
         cudaMemsetAsync(sv->status, 0, sizeof(unsigned int), s) != cudaSuccess)
         return bail(fail(SPIIR_ECUDA, "server setup"));
     if ((st = sv->queue.reserve(sv->S)) || (st = sv->prog.reserve(sv->S))) return bail(st);
-    for (int i = 0; i < sv->L; ++i) sv->part_base[i] = 0;
+    if ((st = relayout_partial(sv, s))) return bail(st);
     if (cudaStreamCreateWithFlags(&sv->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
         return bail(fail(SPIIR_ECUDA, "cudaStreamCreate failed"));
     if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(SPIIR_ECUDA, "server setup"));
@@ -682,17 +1028,10 @@ spiir_status spiir_server_create(const spiir_server_desc *desc, void *cuda_strea
 
 spiir_status spiir_server_add(spiir_server_t sv, const spiir_bank_desc *member, int32_t *member_id) {
     if (!sv || !member_id) return fail(SPIIR_EINVAL, "NULL argument");
-    spiir_status st = check_member(sv, member);
-    if (st) return st;
-    const spiir_bank_desc d = member_desc(sv, member);
-    if ((st = validate(&d))) return st;
     Member m;
     m.id = sv->next_id;
-    m.T = d.n_templates;
-    m.n_filters = d.n_filters;
-    if ((st = make_plan(&d, sv->variant, true, m.p, sv->geo.hist))) return st;
-    if (m.p.smem_bytes > sv->smem_bytes)
-        return fail(SPIIR_EINVAL, "member needs more shared memory than the server's kernel setup");
+    spiir_status st = build_member(sv, member, true, m);
+    if (st) return st;
     sv->pending_add.push_back(std::move(m));
     *member_id = sv->next_id++;
     sv->dirty = true;
@@ -715,12 +1054,10 @@ spiir_status spiir_server_remove(spiir_server_t sv, int32_t member_id) {
 }
 
 int64_t spiir_server_member_footprint(spiir_server_t sv, const spiir_bank_desc *member) {
-    if (!sv || check_member(sv, member)) return -1;
-    const spiir_bank_desc d = member_desc(sv, member);
-    if (validate(&d)) return -1;
-    Plan p;
-    if (make_plan(&d, sv->variant, false, p, sv->geo.hist)) return -1;
-    return member_bytes(sv, p, d.n_templates);
+    if (!sv) return -1;
+    Member m;
+    if (build_member(sv, member, false, m)) return -1;
+    return member_bytes(sv, m);
 }
 
 spiir_status spiir_server_push(spiir_server_t sv, const float *x_dev, void *cuda_stream) {
@@ -775,7 +1112,7 @@ spiir_status spiir_server_get_info(spiir_server_t sv, spiir_server_info *info) {
     for (auto &kv : sv->members) {
         info->n_templates += kv.second.T;
         info->n_filters += kv.second.n_filters;
-        info->filter_samples_per_push += kv.second.p.fs_per_block;
+        info->filter_samples_per_push += kv.second.fs_per_push;
     }
     int64_t b = sv->S * sv->geo.xbuf_stream_stride * 4 + (int64_t)sv->S * sv->block * 4;
     b += sv->slot_alloc.cap() * (4 * 4 + 4 + 8 * (int64_t)sv->S);
@@ -784,11 +1121,17 @@ spiir_status spiir_server_get_info(spiir_server_t sv, spiir_server_info *info) {
     b += sv->tasks.cap * sizeof(WarpTask) + sv->items.cap * sizeof(CtaItem) +
          4 * (sv->order.cap + sv->task_out.cap + sv->comb_ptr.cap + sv->comb_rows.cap + sv->comb_list.cap +
               sv->queue.cap + sv->prog.cap);
+    for (int i = 0; i < sv->L; ++i) {
+        const TcPool &t = sv->tcp[i];
+        if (!t.on) continue;
+        b += t.group_alloc.cap() * ((int64_t)sv->n_slices * kTcSliceBytes + 64 * 13);
+        b += t.tile_alloc.cap() * (kTcPanelBytes + kTcTile * (32 + 48 + 16 * (int64_t)sv->S));
+    }
     info->device_bytes = b;
     info->n_cta_items = sv->n_items;
     info->kernel_variant = sv->variant;
-    info->tc_levels = 0;
-    info->launches_per_push = 1 + (sv->L > 1) + (sv->n_items > 0) + (sv->n_comb > 0);
+    info->tc_levels = sv->n_tc_levels;
+    info->launches_per_push = sv->launches;
     return SPIIR_OK;
 }
 

@@ -257,6 +257,8 @@ struct TcFirArgs {
     const uint4 *H;           // [group][slice][16 KB] pre-tiled impulse responses
     const float *row_scale;   // per template: snr_scale * 2^-e_t
     const uint8_t *has_carry; // per template: z already holds the state term
+    const int32_t *groups;    // NULL: template groups 0 .. n_groups-1; else
+                              // the groups to run (n_groups entries)
     const uint4 *hank;        // staged Toeplitz sources
     int32_t hank_bytes;
     int32_t L, K;
@@ -269,6 +271,8 @@ struct TcFirArgs {
 
 struct TcCarryArgs {
     const int32_t *tile_ptr;  // [t], [t+1]: carry tiles of template t
+    const int32_t *tile_end;  // NULL, or [t]: end of template t's tiles
+                              // (tile_ptr[t] is then their start)
     const int32_t *tmpl_of;   // templates that own tiles
     int32_t n_carry;
     const float2 *a;          // [slot] a_k
@@ -395,7 +399,8 @@ __global__ void __launch_bounds__(kFirThreads, 1) tc_fir_kernel(const TcFirArgs 
         bool ok = true;
         for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++li) {
             const int c = it % a.n_chunks, sg = it / a.n_chunks;
-            const int ss = sg % a.n_streams, g = sg / a.n_streams;
+            const int ss = sg % a.n_streams;
+            const int g = a.groups ? a.groups[sg / a.n_streams] : sg / a.n_streams;
             const int hb = li & 1;
             if (li >= 2) {
                 ok = mbar_wait(&h_empty[hb], ((li >> 1) - 1) & 1, a.status);
@@ -462,7 +467,8 @@ __global__ void __launch_bounds__(kFirThreads, 1) tc_fir_kernel(const TcFirArgs 
         bool ok = true;
         for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++li) {
             const int c = it % a.n_chunks, sg = it / a.n_chunks;
-            const int ss = sg % a.n_streams, g = sg / a.n_streams;
+            const int ss = sg % a.n_streams;
+            const int g = a.groups ? a.groups[sg / a.n_streams] : sg / a.n_streams;
             const int ab = li & 1;
             ok = ok && mbar_wait(&acc_full[ab], (li >> 1) & 1, a.status);
             tc_fence_after();
@@ -679,7 +685,7 @@ struct CarryJobs {
         if (valid) {
             t = a->tmpl_of[ti];
             tile0 = a->tile_ptr[t];
-            tile1 = a->tile_ptr[t + 1];
+            tile1 = a->tile_end ? a->tile_end[t] : a->tile_ptr[t + 1];
             b0 = 0;
             tile = tile0;
         }
@@ -1350,6 +1356,276 @@ spiir_status tc_upload(T **dst, const std::vector<T> &src, cudaStream_t s) {
 
 }  // namespace
 
+int spiir_tc_hank_bytes(int L, int K) { return hank_bytes_of(L, K); }
+int spiir_tc_xseg_bytes() { return kXsegBytes; }
+int spiir_tc_cpb(int streams, int L) { return carry_cpb(streams, L); }
+
+spiir_status spiir_tc_pack(const spiir_bank_desc *d, int level, int F, int L, double row_mult, bool bf16,
+                           bool df, TcPack &pk) {
+    pk = TcPack();
+    const int T = d->n_templates;
+    const int K = F + L;
+    pk.T = T;
+    pk.F = F;
+    pk.L = L;
+    pk.K = K;
+    pk.n_groups = (T + kGroup - 1) / kGroup;
+    pk.n_slices = K / kKs;
+    // filters per template in input order
+    std::vector<std::vector<int64_t>> fl(T);
+    for (int64_t k = 0; k < d->n_filters; ++k) {
+        if (level >= 0 && (d->level ? d->level[k] : 0) != level) continue;
+        if (d->delay[k] >= F) return tc_fail(SPIIR_EINVAL, "tensor-core form: a delay is not below F");
+        fl[d->template_id[k]].push_back(k);
+    }
+
+    // Impulse responses h_t[q], q < K, in FP64; rows scaled by 2^e_t into the
+    // 16-bit range; tiles [group][slice][r/8][k/8][r%8][k%8].
+    pk.H.assign((size_t)pk.n_groups * pk.n_slices * (kSliceBytes / 2), 0);
+    pk.row_scale.assign(T, 0.f);
+    auto work = [&](int t0, int t1) {
+        std::vector<std::complex<double>> h(K);
+        for (int t = t0; t < t1; ++t) {
+            std::fill(h.begin(), h.end(), std::complex<double>(0, 0));
+            for (int64_t k : fl[t]) {
+                const std::complex<double> a(d->a_re[k], d->a_im[k]);
+                std::complex<double> pw(d->b_re[k], d->b_im[k]);
+                for (int q = d->delay[k]; q < K; ++q) {
+                    h[q] += pw;
+                    pw *= a;
+                }
+            }
+            double mx = 0.0;
+            for (int q = 0; q < K; ++q) mx = std::max(mx, std::max(std::fabs(h[q].real()), std::fabs(h[q].imag())));
+            int e = 0;
+            if (mx > 0.0) {
+                int ex;
+                std::frexp(mx, &ex);          // mx in [2^(ex-1), 2^ex)
+                e = 10 - ex;                  // max |h| * 2^e in [2^9, 2^10)
+            }
+            const double sc = std::ldexp(1.0, e);
+            pk.row_scale[t] = (float)(row_mult * std::ldexp(1.0, -e));
+            const int g = t / kGroup;
+            for (int comp = 0; comp < 2; ++comp) {
+                const int r = 2 * (t % kGroup) + comp;
+                for (int q = 0; q < K; ++q) {
+                    const double val = (comp ? h[q].imag() : h[q].real()) * sc;
+                    const int sl = q / kKs, kq = q % kKs;
+                    const size_t off = ((size_t)g * pk.n_slices + sl) * (kSliceBytes / 2) +
+                                       (size_t)(r >> 3) * 512 + (kq >> 3) * 64 + (r & 7) * 8 + (kq & 7);
+                    pk.H[off] = host16((float)val, bf16);
+                }
+            }
+        }
+    };
+    const int nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    {
+        std::vector<std::thread> th;
+        for (int i = 0; i < nth; ++i) {
+            const int t0 = (int)((int64_t)T * i / nth), t1 = (int)((int64_t)T * (i + 1) / nth);
+            th.emplace_back(work, t0, t1);
+        }
+        for (auto &x : th) x.join();
+    }
+
+    // Carry tiles: 128 filter slots each, template-major.
+    int n_tiles = 0;
+    for (int t = 0; t < T; ++t) n_tiles += (int)((fl[t].size() + kTile - 1) / kTile);
+    pk.n_tiles = n_tiles;
+    const int64_t n_slots = (int64_t)n_tiles * kTile;
+    pk.tile_ptr.assign(T + 1, 0);
+    pk.has_carry.assign(T, 0);
+    pk.a.assign(n_slots, make_float2(0.f, 0.f));
+    pk.aJ = pk.c = pk.aLf = pk.a;
+    pk.aL.assign(n_slots, make_uint4(0u, 0u, 0u, 0u));
+    pk.aLb1 = pk.aLb2 = pk.aL;
+    pk.slot_k.assign(n_slots, -1);
+    const int cpb1 = carry_cpb(1, L), cpb2 = carry_cpb(2, L);
+    int tile = 0;
+    for (int t = 0; t < T; ++t) {
+        pk.tile_ptr[t] = tile;
+        const int nt = (int)((fl[t].size() + kTile - 1) / kTile);
+        if (nt) pk.has_carry[t] = 1;
+        for (int i = 0; i < (int)fl[t].size(); ++i) {
+            const int64_t slot = (int64_t)tile * kTile + i;
+            const int64_t k = fl[t][i];
+            pk.slot_k[slot] = k;
+            const std::complex<double> a(d->a_re[k], d->a_im[k]), bb(d->b_re[k], d->b_im[k]);
+            auto pw = [&](int n) {
+                std::complex<double> r(1, 0), x = a;
+                while (n) {
+                    if (n & 1) r *= x;
+                    x *= x;
+                    n >>= 1;
+                }
+                return r;
+            };
+            const std::complex<double> aL = pw(L), ck = pw(F - d->delay[k]) * bb;
+            pk.a[slot] = make_float2(d->a_re[k], d->a_im[k]);
+            const auto pJ = pw(kJ);
+            pk.aJ[slot] = make_float2((float)pJ.real(), (float)pJ.imag());
+            pk.aL[slot] = host_anchor(aL, df);
+            pk.aLf[slot] = make_float2((float)aL.real(), (float)aL.imag());
+            pk.aLb1[slot] = host_anchor(pw(L * cpb1), df);
+            pk.aLb2[slot] = host_anchor(pw(L * cpb2), df);
+            pk.c[slot] = make_float2((float)ck.real(), (float)ck.imag());
+        }
+        tile += nt;
+    }
+    pk.tile_ptr[T] = tile;
+    // Power panel of each tile (the layout the carry kernel copies into a
+    // slot): a_k^j, j < kJ, in FP64 and rounded once to the operand type.
+    pk.panel.assign((size_t)n_tiles * (kPanelBytes / 2), 0);
+    {
+        auto pwork = [&](int64_t t0, int64_t t1) {
+            for (int64_t tl = t0; tl < t1; ++tl)
+                for (int kk = 0; kk < kTile; ++kk) {
+                    const int64_t k = pk.slot_k[tl * kTile + kk];
+                    const std::complex<double> a =
+                        k >= 0 ? std::complex<double>(d->a_re[k], d->a_im[k]) : std::complex<double>(0, 0);
+                    std::complex<double> x(1, 0);
+                    // [k/8][m/8][k%8][m%8]: row group 2 (j/8) = Re, 2 (j/8) + 1 = Im
+                    uint16_t *P = pk.panel.data() + (size_t)tl * (kPanelBytes / 2) + (kk >> 3) * 1024 + (kk & 7) * 8;
+                    for (int j = 0; j < kJ; ++j) {
+                        const int g = 2 * (j >> 3);
+                        P[g * 64 + (j & 7)] = host16((float)x.real(), bf16);
+                        P[(g + 1) * 64 + (j & 7)] = host16((float)x.imag(), bf16);
+                        x *= a;
+                    }
+                }
+        };
+        std::vector<std::thread> th;
+        for (int i = 0; i < nth; ++i)
+            th.emplace_back(pwork, (int64_t)n_tiles * i / nth, (int64_t)n_tiles * (i + 1) / nth);
+        for (auto &x : th) x.join();
+    }
+    return SPIIR_OK;
+}
+
+spiir_status spiir_tc_prepare(int L, int K) {
+    int dev = 0, max_optin = 0;
+    TC_CUDA(cudaGetDevice(&dev));
+    TC_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const void *fns[18];
+    int need[18];
+    fns[0] = (const void *)tc_fir_kernel<true>;
+    fns[1] = (const void *)tc_fir_kernel<false>;
+    need[0] = need[1] = fir_smem_of(L, K);
+    for (int i = 0; i < 16; ++i) {
+        fns[2 + i] = (const void *)carry_kernel(i);
+        need[2 + i] = kCarrySmem;
+    }
+    // kernel-wide limits shared by every bank: the device maximum
+    for (int i = 0; i < 18; ++i) {
+        cudaFuncAttributes fa;
+        TC_CUDA(cudaFuncGetAttributes(&fa, fns[i]));
+        const int dyn_max = max_optin - (int)fa.sharedSizeBytes;
+        if (need[i] > dyn_max)
+            return tc_fail(SPIIR_EUNSUPPORTED, "tensor-core form: shared memory above the device limit");
+        TC_CUDA(cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
+    }
+    return SPIIR_OK;
+}
+
+spiir_status spiir_tc_launch(const TcLaunch &l, cudaStream_t s, KernelTimer *timer) {
+    const int C = l.n_chunks, count = l.n_streams;
+    const int cpb = carry_cpb(count, l.L);
+    const int n_batches = (C + cpb - 1) / cpb;
+    const int hb = hank_bytes_of(l.L, l.K);
+    TcStageArgs sa{};
+    sa.xbuf = l.xbuf;
+    sa.xbuf_stride = l.xbuf_stride;
+    sa.hist = l.hist;
+    sa.F = l.F;
+    sa.L = l.L;
+    sa.K = l.K;
+    sa.n_chunks = C;
+    sa.n_streams = count;
+    sa.stream0 = l.stream0;
+    sa.cpb = cpb;
+    sa.n_batches = n_batches;
+    sa.hank = l.hank;
+    sa.hank_bytes = hb;
+    sa.xseg = l.xseg;
+    {
+        const int64_t chunks = (int64_t)count * C * (hb / 16) + (int64_t)n_batches * (kXsegBytes / 16);
+        const int grid = (int)std::min<int64_t>((chunks + 255) / 256, 8LL * l.n_sms);
+        if (timer) timer->begin(SPIIR_K_TC_STAGE, s);
+        if (l.bf16)
+            tc_stage_kernel<true><<<grid, 256, 0, s>>>(sa);
+        else
+            tc_stage_kernel<false><<<grid, 256, 0, s>>>(sa);
+        TC_CUDA(cudaGetLastError());
+        if (timer) timer->end(s);
+    }
+    // the carry kernel writes the state term into z; the FIR kernel adds to it
+    if (l.n_carry > 0) {
+        TcCarryArgs ca{};
+        ca.tile_ptr = l.tile_ptr;
+        ca.tile_end = l.tile_end;
+        ca.tmpl_of = l.tmpl_of;
+        ca.n_carry = l.n_carry;
+        ca.a = l.a;
+        ca.aJ = l.aJ;
+        ca.aL = l.aL;
+        ca.aLf = l.aLf;
+        ca.aLb = count == 1 ? l.aLb1 : l.aLb2;
+        ca.c = l.c;
+        ca.v = l.v;
+        ca.n_slots = l.n_slots;
+        ca.xseg = l.xseg;
+        ca.L = l.L;
+        ca.n_chunks = C;
+        ca.n_streams = count;
+        ca.stream0 = l.stream0;
+        ca.cpb = cpb;
+        ca.n_batches = n_batches;
+        ca.scale = l.carry_scale;
+        ca.z = l.z;
+        ca.z_row_stride = l.z_row_stride;
+        ca.z_stream_stride = l.z_stream_stride;
+        ca.status = l.status;
+        ca.panel = l.panel;
+        const int grid = std::min(l.n_carry, l.n_sms);
+        if (timer) timer->begin(SPIIR_K_TC_CARRY, s);
+        const bool l2 = l.L == 2 * kJ, two = count == 2;
+        carry_kernel(8 * l.bf16 + 4 * l2 + 2 * two + l.df)<<<grid, kCarryWarps * 32, kCarrySmem, s>>>(ca);
+        TC_CUDA(cudaGetLastError());
+        if (timer) timer->end(s);
+    }
+    if (l.n_groups > 0) {
+        TcFirArgs fa{};
+        fa.H = l.H;
+        fa.row_scale = l.row_scale;
+        fa.has_carry = l.has_carry;
+        fa.groups = l.groups;
+        fa.hank = l.hank;
+        fa.hank_bytes = hb;
+        fa.L = l.L;
+        fa.K = l.K;
+        fa.n_groups = l.n_groups;
+        fa.n_chunks = C;
+        fa.n_streams = count;
+        fa.n_templates = l.n_rows;
+        fa.stream0 = l.stream0;
+        fa.z = l.z;
+        fa.z_row_stride = l.z_row_stride;
+        fa.z_stream_stride = l.z_stream_stride;
+        fa.status = l.status;
+        const int items = l.n_groups * C * count;
+        const int grid = std::min(items, l.n_sms);
+        const int smem = fir_smem_of(l.L, l.K);
+        if (timer) timer->begin(SPIIR_K_TC_FIR, s);
+        if (l.bf16)
+            tc_fir_kernel<true><<<grid, kFirThreads, smem, s>>>(fa);
+        else
+            tc_fir_kernel<false><<<grid, kFirThreads, smem, s>>>(fa);
+        TC_CUDA(cudaGetLastError());
+        if (timer) timer->end(s);
+    }
+    return SPIIR_OK;
+}
+
 spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t s, TcBank **out,
                              int64_t *footprint) {
     *out = nullptr;
@@ -1381,154 +1657,31 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
     *footprint = bytes;
     *out = b;
 
-    // filters per template in input order
-    std::vector<std::vector<int64_t>> fl(p.T);
-    for (int64_t k = 0; k < d->n_filters; ++k) fl[d->template_id[k]].push_back(k);
-
-    // Impulse responses h_t[q], q < K, in FP64; rows scaled by 2^e_t into the
-    // 16-bit range; tiles [group][slice][r/8][k/8][r%8][k%8].
-    const int K = p.K;
-    std::vector<uint16_t> Hh((size_t)p.n_groups * p.n_slices * (kSliceBytes / 2), 0);
-    std::vector<float> row_scale(p.T, 0.f);
-    auto work = [&](int t0, int t1) {
-        std::vector<std::complex<double>> h(K);
-        for (int t = t0; t < t1; ++t) {
-            std::fill(h.begin(), h.end(), std::complex<double>(0, 0));
-            for (int64_t k : fl[t]) {
-                const std::complex<double> a(d->a_re[k], d->a_im[k]);
-                std::complex<double> pw(d->b_re[k], d->b_im[k]);
-                for (int q = d->delay[k]; q < K; ++q) {
-                    h[q] += pw;
-                    pw *= a;
-                }
-            }
-            double mx = 0.0;
-            for (int q = 0; q < K; ++q) mx = std::max(mx, std::max(std::fabs(h[q].real()), std::fabs(h[q].imag())));
-            int e = 0;
-            if (mx > 0.0) {
-                int ex;
-                std::frexp(mx, &ex);          // mx in [2^(ex-1), 2^ex)
-                e = 10 - ex;                  // max |h| * 2^e in [2^9, 2^10)
-            }
-            const double sc = std::ldexp(1.0, e);
-            row_scale[t] = (float)(scale * std::ldexp(1.0, -e));
-            const int g = t / kGroup;
-            for (int comp = 0; comp < 2; ++comp) {
-                const int r = 2 * (t % kGroup) + comp;
-                for (int q = 0; q < K; ++q) {
-                    const double val = (comp ? h[q].imag() : h[q].real()) * sc;
-                    const int sl = q / kKs, kq = q % kKs;
-                    const size_t off = ((size_t)g * p.n_slices + sl) * (kSliceBytes / 2) +
-                                       (size_t)(r >> 3) * 512 + (kq >> 3) * 64 + (r & 7) * 8 + (kq & 7);
-                    Hh[off] = host16((float)val, b->bf16);
-                }
-            }
-        }
-    };
-    {
-        const int nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-        std::vector<std::thread> th;
-        for (int i = 0; i < nth; ++i) {
-            const int t0 = (int)((int64_t)p.T * i / nth), t1 = (int)((int64_t)p.T * (i + 1) / nth);
-            th.emplace_back(work, t0, t1);
-        }
-        for (auto &x : th) x.join();
-    }
-
-    // Carry tiles: 128 filter slots each, template-major.
-    std::vector<int32_t> tile_ptr(p.T + 1, 0), tmpl_of;
-    std::vector<float2> av(p.n_slots), aJv(p.n_slots), cv(p.n_slots);
-    std::vector<uint4> aLv(p.n_slots), aLb1v(p.n_slots), aLb2v(p.n_slots);
-    std::vector<float2> aLfv(p.n_slots);
-    std::vector<int64_t> slot_k(p.n_slots, -1);   // filter of each carry slot (-1: padding)
-    const int cpb1 = carry_cpb(1, p.L), cpb2 = carry_cpb(2, p.L);
-    int tile = 0;
-    for (int t = 0; t < p.T; ++t) {
-        tile_ptr[t] = tile;
-        const int nt = (int)((fl[t].size() + kTile - 1) / kTile);
-        if (nt) tmpl_of.push_back(t);
-        for (int i = 0; i < nt * kTile; ++i) {
-            const int64_t slot = (int64_t)tile * kTile + i;
-            if (i < (int)fl[t].size()) {
-                const int64_t k = fl[t][i];
-                slot_k[slot] = k;
-                const std::complex<double> a(d->a_re[k], d->a_im[k]), bb(d->b_re[k], d->b_im[k]);
-                auto pw = [&](int n) {
-                    std::complex<double> r(1, 0), x = a;
-                    while (n) {
-                        if (n & 1) r *= x;
-                        x *= x;
-                        n >>= 1;
-                    }
-                    return r;
-                };
-                const std::complex<double> aL = pw(p.L), ck = pw(p.F - d->delay[k]) * bb;
-                av[slot] = make_float2(d->a_re[k], d->a_im[k]);
-                const auto pJ = pw(kJ);
-                aJv[slot] = make_float2((float)pJ.real(), (float)pJ.imag());
-                aLv[slot] = host_anchor(aL, b->df);
-                aLfv[slot] = make_float2((float)aL.real(), (float)aL.imag());
-                const auto b1 = pw(p.L * cpb1), b2 = pw(p.L * cpb2);
-                aLb1v[slot] = host_anchor(b1, b->df);
-                aLb2v[slot] = host_anchor(b2, b->df);
-                cv[slot] = make_float2((float)ck.real(), (float)ck.imag());
-            } else {
-                av[slot] = aJv[slot] = cv[slot] = aLfv[slot] = make_float2(0.f, 0.f);
-                aLv[slot] = aLb1v[slot] = aLb2v[slot] = make_uint4(0u, 0u, 0u, 0u);
-            }
-        }
-        tile += nt;
-    }
-    tile_ptr[p.T] = tile;
+    TcPack pk;
+    if ((st = spiir_tc_pack(d, -1, p.F, p.L, scale, b->bf16, b->df, pk))) return st;
+    std::vector<int32_t> tmpl_of;
+    for (int t = 0; t < p.T; ++t)
+        if (pk.has_carry[t]) tmpl_of.push_back(t);
     b->n_carry_ctas = (int)tmpl_of.size();
     b->n_filters = d->n_filters;
-    // Power panel of each tile (the layout the carry kernel copies into a
-    // slot): a_k^j, j < kJ, in FP64 and rounded once to the operand type.
-    std::vector<uint16_t> panel((size_t)tile * (kPanelBytes / 2));
-    {
-        auto pwork = [&](int64_t t0, int64_t t1) {
-            for (int64_t tl = t0; tl < t1; ++tl)
-                for (int kk = 0; kk < kTile; ++kk) {
-                    const int64_t k = slot_k[tl * kTile + kk];
-                    const std::complex<double> a =
-                        k >= 0 ? std::complex<double>(d->a_re[k], d->a_im[k]) : std::complex<double>(0, 0);
-                    std::complex<double> x(1, 0);
-                    // [k/8][m/8][k%8][m%8]: row group 2 (j/8) = Re, 2 (j/8) + 1 = Im
-                    uint16_t *P = panel.data() + (size_t)tl * (kPanelBytes / 2) + (kk >> 3) * 1024 + (kk & 7) * 8;
-                    for (int j = 0; j < kJ; ++j) {
-                        const int g = 2 * (j >> 3);
-                        P[g * 64 + (j & 7)] = host16((float)x.real(), b->bf16);
-                        P[(g + 1) * 64 + (j & 7)] = host16((float)x.imag(), b->bf16);
-                        x *= a;
-                    }
-                }
-        };
-        const int nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-        std::vector<std::thread> th;
-        for (int i = 0; i < nth; ++i)
-            th.emplace_back(pwork, (int64_t)tile * i / nth, (int64_t)tile * (i + 1) / nth);
-        for (auto &x : th) x.join();
-    }
-    std::vector<uint8_t> has_carry(p.T, 0);
-    for (int t : tmpl_of) has_carry[t] = 1;
-
-    if ((st = tc_upload(&b->H, std::vector<uint4>((uint4 *)Hh.data(), (uint4 *)(Hh.data() + Hh.size())), s)))
+    if ((st = tc_upload(&b->H, std::vector<uint4>((uint4 *)pk.H.data(), (uint4 *)(pk.H.data() + pk.H.size())), s)))
         return st;
-    if ((st = tc_upload(&b->row_scale, row_scale, s))) return st;
-    if ((st = tc_upload(&b->tile_ptr, tile_ptr, s))) return st;
+    if ((st = tc_upload(&b->row_scale, pk.row_scale, s))) return st;
+    if ((st = tc_upload(&b->tile_ptr, pk.tile_ptr, s))) return st;
     if ((st = tc_upload(&b->tmpl_of, tmpl_of, s))) return st;
-    if ((st = tc_upload(&b->has_carry, has_carry, s))) return st;
-    if ((st = tc_upload(&b->a, av, s))) return st;
-    if ((st = tc_upload(&b->aJ, aJv, s))) return st;
-    if ((st = tc_upload(&b->c, cv, s))) return st;
-    if ((st = tc_upload(&b->aL, aLv, s))) return st;
-    if ((st = tc_upload(&b->aLf, aLfv, s))) return st;
-    if ((st = tc_upload(&b->aLb1, aLb1v, s))) return st;
-    if ((st = tc_upload(&b->aLb2, aLb2v, s))) return st;
-    if ((st = tc_upload(&b->panel, std::vector<uint4>((uint4 *)panel.data(), (uint4 *)(panel.data() + panel.size())),
+    if ((st = tc_upload(&b->has_carry, pk.has_carry, s))) return st;
+    if ((st = tc_upload(&b->a, pk.a, s))) return st;
+    if ((st = tc_upload(&b->aJ, pk.aJ, s))) return st;
+    if ((st = tc_upload(&b->c, pk.c, s))) return st;
+    if ((st = tc_upload(&b->aL, pk.aL, s))) return st;
+    if ((st = tc_upload(&b->aLf, pk.aLf, s))) return st;
+    if ((st = tc_upload(&b->aLb1, pk.aLb1, s))) return st;
+    if ((st = tc_upload(&b->aLb2, pk.aLb2, s))) return st;
+    if ((st = tc_upload(&b->panel,
+                        std::vector<uint4>((uint4 *)pk.panel.data(), (uint4 *)(pk.panel.data() + pk.panel.size())),
                         s)))
         return st;
-    b->slot_k = std::move(slot_k);
+    b->slot_k = std::move(pk.slot_k);
     const int64_t S = d->n_streams;
     TC_CUDA(cudaMalloc((void **)&b->v, std::max<int64_t>(1, S * p.n_slots) * sizeof(uint4)));
     TC_CUDA(cudaMemsetAsync(b->v, 0, std::max<int64_t>(1, S * p.n_slots) * sizeof(uint4), s));
@@ -1547,28 +1700,7 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
     int dev = 0;
     TC_CUDA(cudaGetDevice(&dev));
     TC_CUDA(cudaDeviceGetAttribute(&b->n_sms, cudaDevAttrMultiProcessorCount, dev));
-    // kernel-wide limits shared by every bank: the device maximum, set once
-    int max_optin = 0;
-    TC_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    {
-        const void *fns[18];
-        int need[18];
-        fns[0] = (const void *)tc_fir_kernel<true>;
-        fns[1] = (const void *)tc_fir_kernel<false>;
-        need[0] = need[1] = fir_smem_of(p.L, p.K);
-        for (int i = 0; i < 16; ++i) {
-            fns[2 + i] = (const void *)carry_kernel(i);
-            need[2 + i] = kCarrySmem;
-        }
-        for (int i = 0; i < 18; ++i) {
-            cudaFuncAttributes fa;
-            TC_CUDA(cudaFuncGetAttributes(&fa, fns[i]));
-            const int dyn_max = max_optin - (int)fa.sharedSizeBytes;
-            if (need[i] > dyn_max)
-                return tc_fail(SPIIR_EUNSUPPORTED, "tensor-core form: shared memory above the device limit");
-            TC_CUDA(cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
-        }
-    }
+    if ((st = spiir_tc_prepare(p.L, p.K))) return st;
     TC_CUDA(cudaStreamSynchronize(s));
     return SPIIR_OK;
 }
@@ -1611,101 +1743,48 @@ spiir_status spiir_tc_push(TcBank *b, int s0, int count, const float *x, int64_t
     TC_CUDA(spiir_launch_prologue(pa, count, s));
     timer->end(s);
 
-    const int C = (int)(n / b->L);
-    const int cpb = carry_cpb(count, b->L);
-    const int n_batches = (C + cpb - 1) / cpb;
-    TcStageArgs sa{};
-    sa.xbuf = b->xbuf;
-    sa.xbuf_stride = b->xbuf_stride;
-    sa.hist = b->F;
-    sa.F = b->F;
-    sa.L = b->L;
-    sa.K = b->K;
-    sa.n_chunks = C;
-    sa.n_streams = count;
-    sa.stream0 = s0;
-    sa.cpb = cpb;
-    sa.n_batches = n_batches;
-    sa.hank = b->hank;
-    sa.hank_bytes = b->hank_bytes;
-    sa.xseg = b->xseg;
-    {
-        const int64_t chunks = (int64_t)count * C * (b->hank_bytes / 16) + (int64_t)n_batches * (kXsegBytes / 16);
-        const int grid = (int)std::min<int64_t>((chunks + 255) / 256, 8LL * b->n_sms);
-        timer->begin(SPIIR_K_TC_STAGE, s);
-        if (b->bf16)
-            tc_stage_kernel<true><<<grid, 256, 0, s>>>(sa);
-        else
-            tc_stage_kernel<false><<<grid, 256, 0, s>>>(sa);
-        TC_CUDA(cudaGetLastError());
-        timer->end(s);
-    }
-
-    // the carry kernel writes the state term into z; the FIR kernel adds to it
-    if (b->n_carry_ctas > 0) {
-        TcCarryArgs ca{};
-        ca.tile_ptr = b->tile_ptr;
-        ca.tmpl_of = b->tmpl_of;
-        ca.n_carry = b->n_carry_ctas;
-        ca.a = b->a;
-        ca.aJ = b->aJ;
-        ca.aL = b->aL;
-        ca.aLf = b->aLf;
-        ca.aLb = count == 1 ? b->aLb1 : b->aLb2;
-        ca.c = b->c;
-        ca.v = b->v;
-        ca.n_slots = b->n_slots;
-        ca.xseg = b->xseg;
-        ca.L = b->L;
-        ca.n_chunks = C;
-        ca.n_streams = count;
-        ca.stream0 = s0;
-        ca.cpb = cpb;
-        ca.n_batches = n_batches;
-        ca.scale = b->scale;
-        ca.z = b->z + zoff;
-        ca.z_row_stride = b->ring_len;
-        ca.z_stream_stride = (int64_t)b->T * b->ring_len;
-        ca.status = b->status;
-        ca.panel = b->panel;
-        const int grid = std::min(b->n_carry_ctas, b->n_sms);
-        const int thr = kCarryWarps * 32;
-        timer->begin(SPIIR_K_TC_CARRY, s);
-        const bool l2 = b->L == 2 * kJ, two = count == 2;
-        carry_kernel(8 * b->bf16 + 4 * l2 + 2 * two + b->df)<<<grid, thr, kCarrySmem, s>>>(ca);
-        TC_CUDA(cudaGetLastError());
-        timer->end(s);
-    }
-    TcFirArgs fa{};
-    fa.H = b->H;
-    fa.row_scale = b->row_scale;
-    fa.has_carry = b->has_carry;
-    fa.hank = b->hank;
-    fa.hank_bytes = b->hank_bytes;
-    fa.L = b->L;
-    fa.K = b->K;
-    fa.n_groups = b->n_groups;
-    fa.n_chunks = C;
-    fa.n_streams = count;
-    fa.n_templates = b->T;
-    fa.stream0 = s0;
-    fa.z = b->z + zoff;
-    fa.z_row_stride = b->ring_len;
-    fa.z_stream_stride = (int64_t)b->T * b->ring_len;
-    fa.status = b->status;
-    {
-        const int items = b->n_groups * C * count;
-        const int grid = std::min(items, b->n_sms);
-        const int smem = fir_smem_of(b->L, b->K);
-        timer->begin(SPIIR_K_TC_FIR, s);
-        if (b->bf16)
-            tc_fir_kernel<true><<<grid, kFirThreads, smem, s>>>(fa);
-        else
-            tc_fir_kernel<false><<<grid, kFirThreads, smem, s>>>(fa);
-        TC_CUDA(cudaGetLastError());
-        timer->end(s);
-    }
-
+    TcLaunch l{};
+    l.xbuf = b->xbuf;
+    l.xbuf_stride = b->xbuf_stride;
+    l.hist = b->F;
+    l.F = b->F;
+    l.L = b->L;
+    l.K = b->K;
+    l.n_chunks = (int)(n / b->L);
+    l.n_streams = count;
+    l.stream0 = s0;
+    l.hank = b->hank;
+    l.xseg = b->xseg;
+    l.tile_ptr = b->tile_ptr;
+    l.tile_end = nullptr;
+    l.tmpl_of = b->tmpl_of;
+    l.n_carry = b->n_carry_ctas;
+    l.a = b->a;
+    l.aJ = b->aJ;
+    l.aLf = b->aLf;
+    l.c = b->c;
+    l.aL = b->aL;
+    l.aLb1 = b->aLb1;
+    l.aLb2 = b->aLb2;
+    l.panel = b->panel;
+    l.v = b->v;
+    l.n_slots = b->n_slots;
+    l.carry_scale = b->scale;
+    l.H = b->H;
+    l.row_scale = b->row_scale;
+    l.has_carry = b->has_carry;
+    l.groups = nullptr;
+    l.n_groups = b->n_groups;
+    l.n_rows = b->T;
+    l.z = b->z + zoff;
+    l.z_row_stride = b->ring_len;
+    l.z_stream_stride = (int64_t)b->T * b->ring_len;
+    l.bf16 = b->bf16;
+    l.df = b->df;
+    l.status = b->status;
+    l.n_sms = b->n_sms;
+    spiir_status st = spiir_tc_launch(l, s, timer);
+    if (st) return st;
     for (int q = s0; q < s0 + count; ++q) b->last_n[q] = n;
     return SPIIR_OK;
 }

@@ -31,3 +31,74 @@ spiir_status spiir_tc_state_set(TcBank *b, int q, const double *v, const float *
                                 cudaStream_t s);
 void spiir_tc_destroy(TcBank *b);
 const char *spiir_tc_last_error();
+
+// ---------------------------------------------------------------------------
+// Building blocks shared with the server (spiir_server.cu)
+// ---------------------------------------------------------------------------
+
+// Sizes of the block-parallel form.
+constexpr int kTcGroup = 64;          // templates per impulse-response group (FIR rows / 2)
+constexpr int kTcTile = 128;          // filter slots per carry tile
+constexpr int kTcSliceBytes = 16384;  // one K slice of a group's impulse responses
+constexpr int kTcPanelBytes = 32768;  // one tile's power panel
+int spiir_tc_hank_bytes(int L, int K);            // Toeplitz source of one chunk
+int spiir_tc_xseg_bytes();                        // STATE strain segments of one batch
+int spiir_tc_cpb(int streams, int L);             // chunks per carry batch
+
+// Host-side packing of a set of single-rate filters (all of a bank, or one
+// level of a multi-rate bank) for a FIR length F and chunk length L: the
+// impulse-response groups, per-template row scales, the carry tiles and their
+// precomputed power panels, in the layouts the kernels read. Template t of
+// the set is FIR row 2 (t % 64) (+1) of group t / 64; its tiles are
+// tile_ptr[t] .. tile_ptr[t + 1] - 1.
+struct TcPack {
+    int T = 0, F = 0, L = 0, K = 0, n_groups = 0, n_slices = 0, n_tiles = 0;
+    std::vector<uint16_t> H;          // [group][slice][kTcSliceBytes / 2]
+    std::vector<float> row_scale;     // [T]: row_mult * 2^-e_t
+    std::vector<int32_t> tile_ptr;    // [T + 1]
+    std::vector<uint8_t> has_carry;   // [T]
+    std::vector<float2> a, aJ, c, aLf;      // [tile * 128 + lane]
+    std::vector<uint4> aL, aLb1, aLb2;      // [tile * 128 + lane]: FP64 or double-float
+    std::vector<int64_t> slot_k;            // filter of each slot (-1: padding)
+    std::vector<uint16_t> panel;      // [tile][kTcPanelBytes / 2]
+};
+// level < 0: every filter (single rate); else the filters with level[k] ==
+// level. Delays must be < F. row_mult scales every output row (the SNR scale,
+// or 1 for a level sum that a later pass scales).
+spiir_status spiir_tc_pack(const spiir_bank_desc *d, int level, int F, int L, double row_mult, bool bf16,
+                           bool df, TcPack &pk);
+
+// One batched launch sequence of the block-parallel form for up to two
+// streams: strain staging, the carry kernel (state term into z) and the FIR
+// kernel (adds the FIR term), over the groups and carry templates listed.
+struct TcLaunch {
+    // strain: xbuf + (stream0 + s) * xbuf_stride + hist is the push's first
+    // sample; hist >= F
+    const float *xbuf;
+    int64_t xbuf_stride;
+    int hist, F, L, K, n_chunks, n_streams, stream0;
+    uint4 *hank, *xseg;                // staging buffers
+    // carry
+    const int32_t *tile_ptr, *tile_end, *tmpl_of;
+    int n_carry;                       // templates listed in tmpl_of
+    const float2 *a, *aJ, *aLf, *c;
+    const uint4 *aL, *aLb1, *aLb2, *panel;
+    uint4 *v;                          // [stream][n_slots]
+    int64_t n_slots;
+    float carry_scale;
+    // FIR
+    const uint4 *H;
+    const float *row_scale;
+    const uint8_t *has_carry;
+    const int32_t *groups;             // NULL: groups 0 .. n_groups-1
+    int n_groups, n_rows;              // groups to run; rows addressable in z
+    // output rows (row t of stream s at z + s * z_stream_stride + t * z_row_stride)
+    float2 *z;
+    int64_t z_row_stride, z_stream_stride;
+    bool bf16, df;
+    unsigned int *status;
+    int n_sms;
+};
+spiir_status spiir_tc_launch(const TcLaunch &l, cudaStream_t s, KernelTimer *timer);
+// Sets the kernels' shared-memory limits (once per process and device).
+spiir_status spiir_tc_prepare(int L, int K);

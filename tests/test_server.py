@@ -157,3 +157,52 @@ def test_late_single_rate_member_against_the_oracle(torch_cuda, oracle_mod):
     z = _run([early, late], [(0, 5), (2, 3)], x, block, 1, 1023)
     ref = oracle_mod.spiir_single_from(late, xh[0], start=2 * block)
     assert rel_rms(z[1][0], ref[:, 2 * block:]).max() <= TOL_PLAIN
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("mode", ["fp16", "bf16"])
+def test_block_form_members_match_the_oracle(torch_cuda, oracle_mod, mode):
+    """Tensor-core server, 7 rates: levels 0-4 (4096-256 samples per block)
+    run in the block form batched over all members, levels 5-6 in the plain
+    form; members present from the first push against the FP64 oracle at the
+    block form's tolerance (fp16; single-pass bf16 at its looser bound)."""
+    import torch
+    from paper_1702_02256_gb300 import spiir
+    from tests._util import TOL_TC
+    tol = TOL_TC if mode == "fp16" else 1e-2
+    block = 4096
+    x = torch.from_numpy(inputs.strain(3, 3 * block, seed=65)).cuda()
+    xh = x.cpu().numpy()
+    banks = [inputs.multi_rate_bank(T, 7, seed=170 + T) for T in (3, 70, 5)]
+    srv = spiir.Server(3, 7, block, 1023, mode=mode, chunk_len=256)
+    ids = [srv.add(b) for b in banks]
+    out = {i: [] for i in ids}
+    for b in range(3):
+        srv.push(x[:, b * block:(b + 1) * block].contiguous())
+        for i in ids:
+            out[i].append(srv.read(i).cpu().numpy())
+    info = srv.info()
+    srv.sync_status()
+    srv.close()
+    assert info["tc_levels"] == 5
+    for i, bank in zip(ids, banks):
+        z = np.concatenate(out[i], axis=-1)
+        for s in range(3):
+            ref = oracle_mod.spiir_multirate(bank, xh[s])
+            assert rel_rms(z[s], ref).max() <= tol, (i, s)
+
+
+@pytest.mark.gpu
+def test_block_form_member_alone_equals_member_in_a_changing_mix(torch_cuda):
+    import torch
+    block = 2048
+    n_blocks = 7
+    x = torch.from_numpy(inputs.strain(3, n_blocks * block, seed=66)).cuda()
+    banks = [inputs.multi_rate_bank(T, 4, seed=190 + T, delay_max=900) for T in (5, 80, 3, 17, 130)]
+    spec = [(0, 7), (0, 3), (1, 5), (2, 5), (4, 3)]
+    kw = dict(mode="fp16", chunk_len=256)
+    mix = _run(banks, spec, x, block, 4, 900, **kw)
+    for i in range(len(banks)):
+        only = [(spec[j] if j == i else (n_blocks + 1, 0)) for j in range(len(banks))]
+        alone = _run(banks, only, x, block, 4, 900, **kw)
+        assert np.array_equal(mix[i], alone[i]), i
