@@ -402,6 +402,15 @@ spiir_status spiir_server_remove(spiir_server_t srv, int32_t member_id);
  * half as much again). -1 on a bad description. */
 int64_t spiir_server_member_footprint(spiir_server_t srv, const spiir_bank_desc *member);
 
+/* Apply the pending additions and removals now, so that the next push only
+ * filters: place the new members in the pools and upload their coefficients
+ * (on a stream of the server's, after the work of earlier pushes), rebuild
+ * the work lists and capture the next push's launches. Work is queued on
+ * cuda_stream, which the next push must follow (pass the same stream). A
+ * serving loop calls it between blocks, while it waits for the next block.
+ * Optional: a push applies pending changes itself. Errors: ENOMEM, ECUDA. */
+spiir_status spiir_server_prepare(spiir_server_t srv, void *cuda_stream);
+
 /* Filter one block of every stream: x_dev device float32
  * [n_streams][block_len]. Applies pending additions and removals first. A
  * push without members still takes the block into the strain history, so
@@ -422,6 +431,12 @@ spiir_status spiir_server_get_info(spiir_server_t srv, spiir_server_info *info);
 /* Wait for the server's queued work and report its device status word (OK,
  * or ETIMEOUT once after a bounded device wait gave up). */
 spiir_status spiir_server_sync_status(spiir_server_t srv);
+
+/* Tracing, as for banks: while enabled, pushes launch their kernels one by
+ * one (no graph) with a CUDA event pair around each; spiir_server_kernel_times
+ * waits for them and returns the per-kind sums since the previous call. */
+spiir_status spiir_server_enable_timing(spiir_server_t srv, int32_t enable);
+spiir_status spiir_server_kernel_times(spiir_server_t srv, spiir_kernel_times *out);
 
 /* Release everything the server holds. NULL is ignored. */
 void spiir_server_destroy(spiir_server_t srv);

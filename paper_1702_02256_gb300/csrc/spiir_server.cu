@@ -100,11 +100,16 @@ template <typename T>
 struct DevVec {
     T *p = nullptr;
     int64_t cap = 0;
-    // At least n elements; the old contents are not kept.
-    spiir_status reserve(int64_t n) {
+    // At least n elements; the old contents are not kept. The old array is
+    // freed once the work queued on s (which follows every push that read
+    // it) has finished.
+    spiir_status reserve(int64_t n, cudaStream_t s) {
         if (n <= cap) return SPIIR_OK;
         const int64_t c = std::max<int64_t>(n, cap + cap / 2);
-        if (p) cudaFree(p);
+        if (p) {
+            CUDA_TRY(cudaStreamSynchronize(s));
+            cudaFree(p);
+        }
         p = nullptr;
         cap = 0;
         CUDA_TRY(cudaMalloc((void **)&p, std::max<int64_t>(1, c) * sizeof(T)));
@@ -112,7 +117,7 @@ struct DevVec {
         return SPIIR_OK;
     }
     spiir_status upload(const std::vector<T> &v, cudaStream_t s) {
-        spiir_status st = reserve((int64_t)v.size());
+        spiir_status st = reserve((int64_t)v.size(), s);
         if (st) return st;
         if (!v.empty())
             CUDA_TRY(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
@@ -208,6 +213,12 @@ struct spiir_server {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int launches = 0;
+    // membership changes run on io after the last push (ev_push) and the
+    // next push waits for them (ev_io)
+    cudaStream_t io = nullptr;
+    cudaEvent_t ev_push = nullptr, ev_io = nullptr;
+    bool pushed_once = false, io_pending = false;
+    KernelTimer *timer = nullptr;
 
     // rows of partial level i before its block-form rows
     int64_t tc_row_base(int i) const { return prow_alloc[i].cap(); }
@@ -256,6 +267,16 @@ struct spiir_server {
         prog.release();
         if (cap_stream) cudaStreamDestroy(cap_stream);
         cap_stream = nullptr;
+        if (io) cudaStreamDestroy(io);
+        io = nullptr;
+        if (ev_push) cudaEventDestroy(ev_push);
+        if (ev_io) cudaEventDestroy(ev_io);
+        ev_push = ev_io = nullptr;
+        if (timer) {
+            timer->release();
+            delete timer;
+            timer = nullptr;
+        }
     }
 };
 
@@ -562,7 +583,7 @@ spiir_status rebuild_lists(spiir_server *sv, cudaStream_t s) {
         (st = sv->comb_ptr.upload(cptr, s)) || (st = sv->comb_rows.upload(crows, s)) ||
         (st = sv->comb_list.upload(clist, s)))
         return st;
-    if ((st = sv->prog.reserve((int64_t)sv->S * std::max<size_t>(1, items.size())))) return st;
+    if ((st = sv->prog.reserve((int64_t)sv->S * std::max<size_t>(1, items.size()), s))) return st;
     sv->n_items = (int)items.size();
     sv->n_tasks = (int)tasks.size();
     sv->n_comb = (int)clist.size();
@@ -586,7 +607,10 @@ spiir_status rebuild_lists(spiir_server *sv, cudaStream_t s) {
     return SPIIR_OK;
 }
 
-spiir_status apply_changes(spiir_server *sv, cudaStream_t s) {
+spiir_status apply_changes(spiir_server *sv) {
+    cudaStream_t s = sv->io;
+    // nothing may change under a push still in flight
+    if (sv->pushed_once) CUDA_TRY(cudaStreamWaitEvent(s, sv->ev_push, 0));
     for (int id : sv->pending_remove) {
         auto it = sv->members.find(id);
         if (it == sv->members.end()) continue;
@@ -618,8 +642,35 @@ spiir_status apply_changes(spiir_server *sv, cudaStream_t s) {
     sv->pending_add.clear();
     spiir_status st = rebuild_lists(sv, s);
     if (st) return st;
+    CUDA_TRY(cudaEventRecord(sv->ev_io, s));
+    sv->io_pending = true;
     sv->drop_graphs();
     sv->dirty = false;
+    return SPIIR_OK;
+}
+
+spiir_status launch_push(spiir_server *sv, int64_t n_prev, cudaStream_t st);
+
+// The graph of the next push (captured once per membership and per first or
+// later push).
+spiir_status ensure_graph(spiir_server *sv) {
+    const int gi = sv->pushes > 0 ? 1 : 0;
+    if (sv->graph[gi]) return SPIIR_OK;
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(sv->cap_stream, cudaStreamCaptureModeThreadLocal));
+    KernelTimer *keep = sv->timer;
+    sv->timer = nullptr;                 // no events inside the graph
+    spiir_status stc = launch_push(sv, gi ? sv->block : 0, sv->cap_stream);
+    sv->timer = keep;
+    cudaError_t e = cudaStreamEndCapture(sv->cap_stream, &g);
+    if (stc) {
+        if (g) cudaGraphDestroy(g);
+        return stc;
+    }
+    if (e != cudaSuccess) return fail(SPIIR_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&sv->graph[gi], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(SPIIR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
     return SPIIR_OK;
 }
 
@@ -656,7 +707,10 @@ spiir_status launch_push(spiir_server *sv, int64_t n_prev, cudaStream_t st) {
     pa.stream0 = 0;
     pa.n_levels = sv->L;
     level_args(sv, n_prev, pa.lev);
+    KernelTimer *tm = (sv->timer && sv->timer->on) ? sv->timer : nullptr;
+    if (tm) tm->begin(SPIIR_K_PROLOGUE, st);
     CUDA_TRY(spiir_launch_prologue(pa, S, st));
+    if (tm) tm->end(st);
     ++launches;
     if (sv->L > 1) {
         DecimArgs da{};
@@ -667,7 +721,9 @@ spiir_status launch_push(spiir_server *sv, int64_t n_prev, cudaStream_t st) {
         da.n_taps = (int)sv->h_down.size();
         for (size_t j = 0; j < sv->h_down.size(); ++j) da.h_down[j] = sv->h_down[j];
         level_args(sv, n_prev, da.lev);
+        if (tm) tm->begin(SPIIR_K_DECIMATE, st);
         CUDA_TRY(spiir_launch_decimate(da, S, st));
+        if (tm) tm->end(st);
         ++launches;
     }
     if (sv->n_items > 0) {
@@ -703,7 +759,9 @@ spiir_status launch_push(spiir_server *sv, int64_t n_prev, cudaStream_t st) {
         const int64_t total = (int64_t)ra.n_segs * ra.n_items;
         const int64_t resident = std::max<int64_t>(1, (int64_t)sv->ctas_per_sm * sv->n_sms / S);
         const int ctas = (int)std::min<int64_t>(total, resident);
+        if (tm) tm->begin(SPIIR_K_RECUR, st);
         CUDA_TRY(spiir_launch_recur(ra, sv->variant, ctas, S, sv->smem_bytes, st));
+        if (tm) tm->end(st);
         ++launches;
     }
     // block-form levels: each level's sums into its partial rows (unscaled;
@@ -752,7 +810,7 @@ spiir_status launch_push(spiir_server *sv, int64_t n_prev, cudaStream_t st) {
             l.df = sv->df;
             l.status = sv->status;
             l.n_sms = sv->n_sms;
-            spiir_status r = spiir_tc_launch(l, st, nullptr);
+            spiir_status r = spiir_tc_launch(l, st, tm);
             if (r) return fail(r, "%s", spiir_tc_last_error());
             launches += 2 + (t.n_carry > 0);
         }
@@ -777,7 +835,9 @@ spiir_status launch_push(spiir_server *sv, int64_t n_prev, cudaStream_t st) {
         ca.rows = sv->comb_list.p;
         for (size_t j = 0; j < sv->h_up.size(); ++j) ca.h_up2[j] = 2.0f * sv->h_up[j];
         level_args(sv, n_prev, ca.lev);
+        if (tm) tm->begin(SPIIR_K_COMBINE, st);
         CUDA_TRY(spiir_launch_combine(ca, spiir_combine_chunk(sv->L, sv->block), S, st));
+        if (tm) tm->end(st);
         ++launches;
     }
     sv->launches = launches;
@@ -1016,10 +1076,14 @@ spiir_status spiir_server_create(const spiir_server_desc *desc, void *cuda_strea
     if (cudaMemsetAsync(sv->xbuf, 0, xs * sizeof(float), s) != cudaSuccess ||
         cudaMemsetAsync(sv->status, 0, sizeof(unsigned int), s) != cudaSuccess)
         return bail(fail(SPIIR_ECUDA, "server setup"));
-    if ((st = sv->queue.reserve(sv->S)) || (st = sv->prog.reserve(sv->S))) return bail(st);
+    if ((st = sv->queue.reserve(sv->S, s)) || (st = sv->prog.reserve(sv->S, s))) return bail(st);
     if ((st = relayout_partial(sv, s))) return bail(st);
-    if (cudaStreamCreateWithFlags(&sv->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
-        return bail(fail(SPIIR_ECUDA, "cudaStreamCreate failed"));
+    if (cudaStreamCreateWithFlags(&sv->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&sv->io, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sv->ev_push, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sv->ev_io, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(SPIIR_ECUDA, "stream or event creation failed"));
+    sv->timer = new KernelTimer();
     if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(SPIIR_ECUDA, "server setup"));
     *out = sv;
     g_err.clear();
@@ -1060,31 +1124,57 @@ int64_t spiir_server_member_footprint(spiir_server_t sv, const spiir_bank_desc *
     return member_bytes(sv, m);
 }
 
+spiir_status spiir_server_prepare(spiir_server_t sv, void *cuda_stream) {
+    if (!sv) return fail(SPIIR_EINVAL, "server is NULL");
+    spiir_status st;
+    if (sv->dirty && (st = apply_changes(sv))) return st;
+    if (!(sv->timer && sv->timer->on) && (st = ensure_graph(sv))) return st;
+    if (sv->io_pending) {
+        CUDA_TRY(cudaStreamWaitEvent((cudaStream_t)cuda_stream, sv->ev_io, 0));
+        sv->io_pending = false;
+    }
+    return SPIIR_OK;
+}
+
 spiir_status spiir_server_push(spiir_server_t sv, const float *x_dev, void *cuda_stream) {
     if (!sv || !x_dev) return fail(SPIIR_EINVAL, "NULL argument");
     cudaStream_t s = (cudaStream_t)cuda_stream;
     spiir_status st;
-    if (sv->dirty && (st = apply_changes(sv, s))) return st;
+    if ((st = spiir_server_prepare(sv, cuda_stream))) return st;
     CUDA_TRY(cudaMemcpyAsync(sv->xstage, x_dev, (int64_t)sv->S * sv->block * sizeof(float),
                              cudaMemcpyDeviceToDevice, s));
-    const int gi = sv->pushes > 0 ? 1 : 0;
-    if (!sv->graph[gi]) {
-        cudaGraph_t g = nullptr;
-        CUDA_TRY(cudaStreamBeginCapture(sv->cap_stream, cudaStreamCaptureModeThreadLocal));
-        spiir_status stc = launch_push(sv, gi ? sv->block : 0, sv->cap_stream);
-        cudaError_t e = cudaStreamEndCapture(sv->cap_stream, &g);
-        if (stc) {
-            if (g) cudaGraphDestroy(g);
-            return stc;
-        }
-        if (e != cudaSuccess) return fail(SPIIR_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-        e = cudaGraphInstantiate(&sv->graph[gi], g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return fail(SPIIR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    if (sv->timer && sv->timer->on) {
+        if ((st = launch_push(sv, sv->pushes > 0 ? sv->block : 0, s))) return st;
+    } else {
+        CUDA_TRY(cudaGraphLaunch(sv->graph[sv->pushes > 0 ? 1 : 0], s));
     }
-    CUDA_TRY(cudaGraphLaunch(sv->graph[gi], s));
+    CUDA_TRY(cudaEventRecord(sv->ev_push, s));
+    sv->pushed_once = true;
     ++sv->pushes;
     for (auto &kv : sv->members) kv.second.pushed = true;
+    return SPIIR_OK;
+}
+
+spiir_status spiir_server_enable_timing(spiir_server_t sv, int32_t enable) {
+    if (!sv) return fail(SPIIR_EINVAL, "server is NULL");
+    sv->timer->flush();
+    sv->timer->on = enable != 0;
+    for (int k = 0; k < SPIIR_K_COUNT; ++k) {
+        sv->timer->ms[k] = 0.0;
+        sv->timer->launches[k] = 0;
+    }
+    return SPIIR_OK;
+}
+
+spiir_status spiir_server_kernel_times(spiir_server_t sv, spiir_kernel_times *out) {
+    if (!sv || !out) return fail(SPIIR_EINVAL, "NULL argument");
+    sv->timer->flush();
+    for (int k = 0; k < SPIIR_K_COUNT; ++k) {
+        out->ms[k] = sv->timer->ms[k];
+        out->launches[k] = sv->timer->launches[k];
+        sv->timer->ms[k] = 0.0;
+        sv->timer->launches[k] = 0;
+    }
     return SPIIR_OK;
 }
 

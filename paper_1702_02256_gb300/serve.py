@@ -224,8 +224,16 @@ class BatchedServer(Server):
         # every block enters the server's strain history, with or without
         # requests, so that a request joining later reads the continuous stream
         if self.use_cuda:
+            import time
             import torch
             main = torch.cuda.current_stream()
+            # membership changes (placement, uploads, work lists, graph) are
+            # made between blocks, before the block arrives
+            t0 = time.perf_counter()
+            prep = getattr(self.engine, "prepare", None)
+            if prep:
+                prep()
+            rec["prepare_ms"] = 1e3 * (time.perf_counter() - t0)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(main)                          # the block is on the device

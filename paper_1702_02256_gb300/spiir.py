@@ -111,6 +111,9 @@ _SIGS = {
     "spiir_server_remove": (_i32, [_c_void_p, _i32]),
     "spiir_server_member_footprint": (_i64, [_c_void_p, ctypes.POINTER(BankDesc)]),
     "spiir_server_push": (_i32, [_c_void_p, _c_void_p, _c_void_p]),
+    "spiir_server_prepare": (_i32, [_c_void_p, _c_void_p]),
+    "spiir_server_enable_timing": (_i32, [_c_void_p, _i32]),
+    "spiir_server_kernel_times": (_i32, [_c_void_p, ctypes.POINTER(KernelTimes)]),
     "spiir_server_read": (_i32, [_c_void_p, _i32, _c_void_p, _c_void_p]),
     "spiir_server_get_info": (_i32, [_c_void_p, ctypes.POINTER(ServerInfo)]),
     "spiir_server_sync_status": (_i32, [_c_void_p]),
@@ -410,10 +413,24 @@ class Server:
         d, _keep = self._member_desc(bank)
         return int(lib().spiir_server_member_footprint(self._h, ctypes.byref(d)))
 
+    def prepare(self, stream=None):
+        """Apply pending additions and removals ahead of the next push."""
+        check(lib().spiir_server_prepare(self._h, _stream_handle(stream)))
+
     def push(self, x, stream=None):
         """x: float32 CUDA tensor [n_streams, block_len], contiguous."""
         assert x.is_cuda and x.is_contiguous() and tuple(x.shape) == (self.n_streams, self.block_len)
         check(lib().spiir_server_push(self._h, x.data_ptr(), _stream_handle(stream)))
+
+    def enable_timing(self, on: bool = True):
+        check(lib().spiir_server_enable_timing(self._h, int(on)))
+
+    def kernel_times(self) -> dict:
+        """{kernel name: (ms summed, launches)} since the last call."""
+        kt = KernelTimes()
+        check(lib().spiir_server_kernel_times(self._h, ctypes.byref(kt)))
+        return {KERNEL_NAMES[k]: (kt.ms[k], int(kt.launches[k])) for k in range(8)
+                if kt.launches[k]}
 
     def read(self, member_id: int, out=None, stream=None):
         """SNR of the last push for one member: complex64 [n_streams, T, block_len]."""
