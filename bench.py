@@ -748,14 +748,20 @@ def _serve_search(kind, form, args, budget, batched=True):
         else:
             step = 8.5 / max(p99, 0.5)
             scale = scale * (min(4.0, max(1.25, step)) if hi is None else max(0.25, min(0.8, step)))
-    confirm = None
+    confirm, last = None, None
     if lo is not None and args.serve_confirm > 0:
-        for sc in (lo, 0.9 * lo):
-            confirm = _serve_trial(kind, form, sc, args.serve_confirm, 11, budget, batched)
-            confirm["scale"] = sc
-            if confirm.get("blocks", 0) and confirm["p99_block_latency_ms"] < 10.0:
+        sc = lo
+        for _ in range(3):
+            r = _serve_trial(kind, form, sc, args.serve_confirm, 7, budget, batched)
+            r["scale"] = sc
+            last = r
+            if r.get("blocks", 0) and r["p99_block_latency_ms"] < 10.0:
+                confirm = r
                 break
-    return {"search": trials, "at_slo": best, "confirm": confirm}
+            # the longer run saw a heavier load: rescale by its p99 (block
+            # time is close to proportional to the templates served)
+            sc *= 9.5 / max(r.get("p99_block_latency_ms", 20.0), 1.0)
+    return {"search": trials, "at_slo": best, "confirm": confirm or last}
 
 
 def _serve_summary(res):
@@ -830,9 +836,9 @@ def main():
                     help="serving: forms compared with the plain form (comma-separated)")
     ap.add_argument("--serve-blocks", type=int, default=16,
                     help="blocks per SLO-search run")
-    ap.add_argument("--serve-confirm", type=int, default=240,
+    ap.add_argument("--serve-confirm", type=int, default=210,
                     help="blocks of the confirmation run at the scale found (0: none)")
-    ap.add_argument("--serve-trials", type=int, default=6)
+    ap.add_argument("--serve-trials", type=int, default=5)
     ap.add_argument("--serving", type=int, default=1,
                     help="default workload only: add the serving comparison (configuration-4 "
                          "requests, batched server, plain and --serve-forms) to the line")
