@@ -451,7 +451,9 @@ def _measure(w, form, args, dev, dist, sampler, rank, ws, err=None):
 def _form_desc(form: str, args) -> str:
     if form == "plain":
         return "plain FP32 recursion"
-    return f"tensor-core block form ({form}, {args.carry} carry between chunk batches)"
+    carry = {"fp64": "FP64 state anchor per chunk batch", "df": "double-float state anchor per chunk batch",
+             "fp64chunk": "FP64 state at every chunk"}[args.carry]
+    return f"tensor-core block form ({form}, {carry})"
 
 
 def _oracle_error(w, sel, z):
@@ -854,9 +856,9 @@ def main():
     ap.add_argument("--resampler", default="default", choices=["default", "paper"],
                     help="multi-rate: 32/32-tap 60 dB pair (default) or the paper's "
                          "384-tap 100 dB decimator with the 32-tap interpolator")
-    ap.add_argument("--carry", default="fp64", choices=["fp64", "df"],
-                    help="tensor-core forms: inter-batch state arithmetic, FP64 (default) or "
-                         "double-float pairs on the FP32 pipe")
+    ap.add_argument("--carry", default="fp64", choices=["fp64", "df", "fp64chunk"],
+                    help="tensor-core forms: carried-state arithmetic: FP64 per chunk batch "
+                         "(default), double-float pairs on the FP32 pipe, or FP64 per chunk")
     ap.add_argument("--tune", type=int, default=None,
                     help="plain-form kernel variant: 1 = autotune at bank creation, 0 = default, "
                          "-(v+1) = variant v (default: autotune for multirate, else 0)")

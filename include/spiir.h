@@ -111,12 +111,15 @@ typedef struct {
                                      n_taps (Sec. 2.2 pairs a long 100 dB
                                      decimator with a 32-tap interpolator) */
     int32_t carry;                /* TC forms: arithmetic of the filter state
-                                     carried between chunk batches and of the
-                                     powers a_k^L: 0 = FP64 (default), 1 =
-                                     double-float pairs on the FP32 pipe
-                                     (about 48 significant bits; faster on
-                                     parts with a low FP64 rate). Ignored by
-                                     PLAIN_FP32; other values: EINVAL */
+                                     carried from chunk to chunk: 0 = FP64
+                                     at every batch of chunks, FP32 offsets
+                                     from it inside a batch (default); 1 =
+                                     the same with double-float pairs on the
+                                     FP32 pipe (about 48 significant bits;
+                                     faster on parts with a low FP64 rate);
+                                     2 = FP64 at every chunk (slowest).
+                                     Ignored by PLAIN_FP32; other values:
+                                     EINVAL */
 } spiir_bank_desc;
 
 /* Read-only facts about a created bank. */

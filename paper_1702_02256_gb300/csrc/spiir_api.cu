@@ -148,7 +148,8 @@ spiir_status validate(const spiir_bank_desc *d) {
     if (d->mode == SPIIR_TC_BF16X2)
         return fail(SPIIR_EUNSUPPORTED, "split-bf16 operands are not built; use SPIIR_TC_FP16");
     if (d->hbm_budget_bytes < 0) return fail(SPIIR_EINVAL, "hbm_budget_bytes must be >= 0");
-    if (d->carry != 0 && d->carry != 1) return fail(SPIIR_EINVAL, "carry must be 0 (FP64) or 1 (double-float)");
+    if (d->carry < 0 || d->carry > 2)
+        return fail(SPIIR_EINVAL, "carry must be 0 (FP64 per batch), 1 (double-float) or 2 (FP64 per chunk)");
     for (int64_t k = 0; k < d->n_filters; ++k) {
         if (d->template_id[k] < 0 || d->template_id[k] >= d->n_templates)
             return fail(SPIIR_EINVAL, "template_id[%lld] out of range", (long long)k);

@@ -808,6 +808,7 @@ spiir_status launch_push(spiir_server *sv, int64_t n_prev, cudaStream_t st) {
             l.z_stream_stride = sv->part_stream_stride;
             l.bf16 = sv->bf16;
             l.df = sv->df;
+            l.carry_mode = sv->d.carry;
             l.status = sv->status;
             l.n_sms = sv->n_sms;
             spiir_status r = spiir_tc_launch(l, st, tm);
@@ -952,7 +953,7 @@ spiir_status spiir_server_create(const spiir_server_desc *desc, void *cuda_strea
         return fail(SPIIR_EINVAL, "max_delay must be in [0, 2^20]");
     if (desc->n_levels < 1 || desc->n_levels > SPIIR_MAX_LEVELS)
         return fail(SPIIR_EINVAL, "n_levels must be in [1, %d]", SPIIR_MAX_LEVELS);
-    if (desc->carry != 0 && desc->carry != 1) return fail(SPIIR_EINVAL, "carry must be 0 or 1");
+    if (desc->carry < 0 || desc->carry > 2) return fail(SPIIR_EINVAL, "carry must be 0, 1 or 2");
     const bool tc = desc->mode != SPIIR_PLAIN_FP32;
     const int tcL = desc->chunk_len ? desc->chunk_len : 256;
     if (tc && tcL != 128 && tcL != 256) return fail(SPIIR_EUNSUPPORTED, "chunk_len must be 128 or 256");

@@ -764,8 +764,12 @@ __device__ __forceinline__ double2 anchor_madd(double2 x, double2 y, float2 d) {
 }
 __device__ __forceinline__ float4 anchor_madd(float4 x, float4 y, float2 d) { return cdf_mul_add(x, y, d); }
 
-template <bool BF16, int LJ, int S, bool DF>
+// MODE: arithmetic of the carried filter state. 0: FP64 anchor per chunk
+// batch with FP32 offsets inside it; 1: the same with a double-float anchor;
+// 2: FP64 state updated at every chunk.
+template <bool BF16, int LJ, int S, int MODE>
 __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcCarryArgs a) {
+    constexpr bool DF = MODE == 1, CH = MODE == 2;
     using Anchor = typename std::conditional<DF, float4, double2>::type;   // carry arithmetic
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t panel_full[kPanelSlots], panel_free[kPanelSlots], w_full[kWSlots], w_free[kWSlots],
@@ -1114,11 +1118,15 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             // and the next batch starts from a^(nb L) v + d_nb in the anchor's
             // arithmetic.
             // per stream: a^(cL) v and d_c; the streams' chains interleave
+            // (MODE 2: vc = the chunk's starting state in FP64, v_{c+1} = a^L v_c + U_c)
             float2 p[S], dd[S];
+            double2 vc[S];
+            const double2 aL64 = CH ? reinterpret_cast<const double2 *>(a.aL)[slot] : make_double2(0.0, 0.0);
 #pragma unroll
             for (int i = 0; i < S; ++i) {
                 p[i] = anchor_f32(i ? v1 : v0);
                 dd[i] = make_float2(0.f, 0.f);
+                if constexpr (CH) vc[i] = reinterpret_cast<const double2 &>(i ? v1 : v0);
             }
             // STATE columns: (chunk, stream, i2) -> (c S + s) LJ + i2, read 32
             // at a time (32 / LJ steps); step q = c S + s. Step q writes W columns 2 q LJ ..
@@ -1158,7 +1166,8 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                             ur = fmaf(pj[i2].x, gr, fmaf(-pj[i2].y, gi, ur));
                             ui = fmaf(pj[i2].x, gi, fmaf(pj[i2].y, gr, ui));
                         }
-                        const float2 vv = make_float2(p[ss].x + dd[ss].x, p[ss].y + dd[ss].y);
+                        const float2 vv = CH ? make_float2((float)vc[ss].x, (float)vc[ss].y)
+                                             : make_float2(p[ss].x + dd[ss].x, p[ss].y + dd[ss].y);
                         const float2 vx = make_float2(vv.x, vv.x), vy = make_float2(vv.y, vv.y);
 #pragma unroll
                         for (int i = 0; i < LJ / 2; ++i) {      // w = a^(kJ j2) a c vv
@@ -1169,9 +1178,14 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                             wi[2 * i] = m.x;
                             wi[2 * i + 1] = m.y;
                         }
-                        dd[ss] = make_float2(fmaf(aLf.x, dd[ss].x, fmaf(-aLf.y, dd[ss].y, ur)),
-                                             fmaf(aLf.x, dd[ss].y, fmaf(aLf.y, dd[ss].x, ui)));
-                        p[ss] = cmul(aLf, p[ss]);
+                        if constexpr (CH) {
+                            vc[ss] = make_double2(fma(aL64.x, vc[ss].x, fma(-aL64.y, vc[ss].y, (double)ur)),
+                                                  fma(aL64.x, vc[ss].y, fma(aL64.y, vc[ss].x, (double)ui)));
+                        } else {
+                            dd[ss] = make_float2(fmaf(aLf.x, dd[ss].x, fmaf(-aLf.y, dd[ss].y, ur)),
+                                                 fmaf(aLf.x, dd[ss].y, fmaf(aLf.y, dd[ss].x, ui)));
+                            p[ss] = cmul(aLf, p[ss]);
+                        }
                     } else {
                         // columns past this batch contribute nothing
 #pragma unroll
@@ -1191,6 +1205,12 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             // state update below
             fence_async_smem();
             mbar_arrive(&w_full[wl]);
+            if constexpr (CH) {
+                vs[(int64_t)a.stream0 * a.n_slots + slot] = reinterpret_cast<const Anchor &>(vc[0]);
+                if constexpr (S > 1)
+                    vs[(int64_t)(a.stream0 + 1) * a.n_slots + slot] = reinterpret_cast<const Anchor &>(vc[1]);
+                return true;
+            }
             // v <- a^(nb L) v + d_nb in the anchor's arithmetic, per stream
             Anchor pw;
             if (nb == a.cpb) {
@@ -1237,6 +1257,7 @@ struct TcBank {
     float2 *a = nullptr, *aJ = nullptr, *c = nullptr, *aLf = nullptr;
     uint4 *aL = nullptr, *v = nullptr, *aLb1 = nullptr, *aLb2 = nullptr;   // FP64 or double-float
     bool df = false;                          // double-float carry
+    int carry_mode = 0;                       // 0 FP64 per batch, 1 double-float, 2 FP64 per chunk
     float *xbuf = nullptr, *stage = nullptr;
     float2 *z = nullptr;
     unsigned int *status = nullptr;
@@ -1323,19 +1344,21 @@ uint4 host_anchor(std::complex<double> x, bool df) {
     return r;
 }
 
-// The carry kernel's instantiations, indexed 8 bf16 + 4 (L = 128) + 2 (two
-// streams) + (double-float carry).
+// The carry kernel's instantiations, indexed 12 bf16 + 6 (L = 128) + 3 (two
+// streams) + carry mode (0 FP64 anchor per batch, 1 double-float anchor, 2
+// FP64 per chunk).
 using CarryFn = void (*)(const TcCarryArgs);
+constexpr int kCarryFns = 24;
 CarryFn carry_kernel(int i) {
-    static const CarryFn k[16] = {
-        tc_carry_kernel<false, 4, 1, false>, tc_carry_kernel<false, 4, 1, true>,
-        tc_carry_kernel<false, 4, 2, false>, tc_carry_kernel<false, 4, 2, true>,
-        tc_carry_kernel<false, 2, 1, false>, tc_carry_kernel<false, 2, 1, true>,
-        tc_carry_kernel<false, 2, 2, false>, tc_carry_kernel<false, 2, 2, true>,
-        tc_carry_kernel<true, 4, 1, false>,  tc_carry_kernel<true, 4, 1, true>,
-        tc_carry_kernel<true, 4, 2, false>,  tc_carry_kernel<true, 4, 2, true>,
-        tc_carry_kernel<true, 2, 1, false>,  tc_carry_kernel<true, 2, 1, true>,
-        tc_carry_kernel<true, 2, 2, false>,  tc_carry_kernel<true, 2, 2, true>,
+    static const CarryFn k[kCarryFns] = {
+        tc_carry_kernel<false, 4, 1, 0>, tc_carry_kernel<false, 4, 1, 1>, tc_carry_kernel<false, 4, 1, 2>,
+        tc_carry_kernel<false, 4, 2, 0>, tc_carry_kernel<false, 4, 2, 1>, tc_carry_kernel<false, 4, 2, 2>,
+        tc_carry_kernel<false, 2, 1, 0>, tc_carry_kernel<false, 2, 1, 1>, tc_carry_kernel<false, 2, 1, 2>,
+        tc_carry_kernel<false, 2, 2, 0>, tc_carry_kernel<false, 2, 2, 1>, tc_carry_kernel<false, 2, 2, 2>,
+        tc_carry_kernel<true, 4, 1, 0>,  tc_carry_kernel<true, 4, 1, 1>,  tc_carry_kernel<true, 4, 1, 2>,
+        tc_carry_kernel<true, 4, 2, 0>,  tc_carry_kernel<true, 4, 2, 1>,  tc_carry_kernel<true, 4, 2, 2>,
+        tc_carry_kernel<true, 2, 1, 0>,  tc_carry_kernel<true, 2, 1, 1>,  tc_carry_kernel<true, 2, 1, 2>,
+        tc_carry_kernel<true, 2, 2, 0>,  tc_carry_kernel<true, 2, 2, 1>,  tc_carry_kernel<true, 2, 2, 2>,
     };
     return k[i];
 }
@@ -1506,17 +1529,17 @@ spiir_status spiir_tc_prepare(int L, int K) {
     int dev = 0, max_optin = 0;
     TC_CUDA(cudaGetDevice(&dev));
     TC_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    const void *fns[18];
-    int need[18];
+    const void *fns[2 + kCarryFns];
+    int need[2 + kCarryFns];
     fns[0] = (const void *)tc_fir_kernel<true>;
     fns[1] = (const void *)tc_fir_kernel<false>;
     need[0] = need[1] = fir_smem_of(L, K);
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < kCarryFns; ++i) {
         fns[2 + i] = (const void *)carry_kernel(i);
         need[2 + i] = kCarrySmem;
     }
     // kernel-wide limits shared by every bank: the device maximum
-    for (int i = 0; i < 18; ++i) {
+    for (int i = 0; i < 2 + kCarryFns; ++i) {
         cudaFuncAttributes fa;
         TC_CUDA(cudaFuncGetAttributes(&fa, fns[i]));
         const int dyn_max = max_optin - (int)fa.sharedSizeBytes;
@@ -1589,7 +1612,7 @@ spiir_status spiir_tc_launch(const TcLaunch &l, cudaStream_t s, KernelTimer *tim
         const int grid = std::min(l.n_carry, l.n_sms);
         if (timer) timer->begin(SPIIR_K_TC_CARRY, s);
         const bool l2 = l.L == 2 * kJ, two = count == 2;
-        carry_kernel(8 * l.bf16 + 4 * l2 + 2 * two + l.df)<<<grid, kCarryWarps * 32, kCarrySmem, s>>>(ca);
+        carry_kernel(12 * l.bf16 + 6 * l2 + 3 * two + l.carry_mode)<<<grid, kCarryWarps * 32, kCarrySmem, s>>>(ca);
         TC_CUDA(cudaGetLastError());
         if (timer) timer->end(s);
     }
@@ -1650,6 +1673,7 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
     b->xbuf_stride = p.xbuf_stride;
     b->bf16 = d->mode != SPIIR_TC_FP16;
     b->df = d->carry == 1;
+    b->carry_mode = d->carry;
     b->scale = scale;
     b->max_delay = p.max_delay;
     b->last_n.assign(d->n_streams, 0);
@@ -1781,6 +1805,7 @@ spiir_status spiir_tc_push(TcBank *b, int s0, int count, const float *x, int64_t
     l.z_stream_stride = (int64_t)b->T * b->ring_len;
     l.bf16 = b->bf16;
     l.df = b->df;
+    l.carry_mode = b->carry_mode;
     l.status = b->status;
     l.n_sms = b->n_sms;
     spiir_status st = spiir_tc_launch(l, s, timer);

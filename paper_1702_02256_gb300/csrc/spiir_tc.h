@@ -95,7 +95,8 @@ struct TcLaunch {
     // output rows (row t of stream s at z + s * z_stream_stride + t * z_row_stride)
     float2 *z;
     int64_t z_row_stride, z_stream_stride;
-    bool bf16, df;
+    bool bf16, df;                     // operand type; double-float anchor
+    int carry_mode;                    // 0 FP64 anchor per batch, 1 double-float, 2 FP64 per chunk
     unsigned int *status;
     int n_sms;
 };

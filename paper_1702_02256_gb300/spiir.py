@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "_build", "libspiir.so")
 OK, EINVAL, ENOMEM, EBUDGET, ECUDA, ETIMEOUT, ESTATE, EUNSUPPORTED = range(8)
 PLAIN_FP32, TC_FP16, TC_BF16, TC_BF16X2 = range(4)
 MODES = {"plain": PLAIN_FP32, "fp16": TC_FP16, "bf16": TC_BF16, "bf16x2": TC_BF16X2}
-CARRY = {"fp64": 0, "df": 1}     # tensor-core forms: inter-batch state arithmetic
+CARRY = {"fp64": 0, "df": 1, "fp64chunk": 2}   # tensor-core forms: carried-state arithmetic
 
 _c_void_p = ctypes.c_void_p
 _i32, _i64, _f32, _f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double

@@ -100,7 +100,7 @@ def test_double_float_carry_matches_fp64(torch_cuda, oracle_mod, mode, tol):
         _check(zdf[s], oracle_mod.spiir_single(bank, x[s]), tol, 256)
 
 
-@pytest.mark.parametrize("carry", ["fp64", "df"])
+@pytest.mark.parametrize("carry", ["fp64", "df", "fp64chunk"])
 def test_long_stream_does_not_drift(torch_cuda, oracle_mod, carry):
     """32 s of strain in 1 s pushes (512 chunks, 32 carry batches per
     stream) through filters with time constants up to 2000 samples: the
@@ -143,3 +143,19 @@ def test_tc_reset_and_host_entry(torch_cuda):
     b.sync_status()
     b.close()
     assert np.array_equal(first, zh)
+
+
+def test_fp64_every_chunk_matches_anchor_per_batch(torch_cuda, oracle_mod):
+    """carry = 2 updates the filter state in FP64 at every chunk instead of
+    anchoring it once per batch of chunks; the contractions see the state
+    rounded to FP32 either way, so the two agree far below the tolerance, and
+    both match the oracle. Two streams, partial batches (3 blocks of 1024)."""
+    counts = [60, 128, 200, 256, 300, 1, 383]
+    bank = inputs.single_rate_bank(len(counts), counts, 700, seed=23)
+    x = inputs.strain(2, 4 * 3072, seed=14)
+    kw = dict(block_len=1024, push_blocks=3, n_streams=2, mode="fp16", chunk_len=256)
+    z64 = gpu_snr(bank, x, **kw)
+    zch = gpu_snr(bank, x, carry="fp64chunk", **kw)
+    assert rel_rms(zch, z64).max() <= 1e-5
+    for s in range(2):
+        _check(zch[s], oracle_mod.spiir_single(bank, x[s]), TOL_TC, 256)
