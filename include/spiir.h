@@ -102,9 +102,14 @@ typedef struct {
     float snr_scale;              /* 0 = 2/base_rate (2*dt, Eq. iireq1) */
     spiir_mode mode;
     int32_t chunk_len;            /* TC forms: chunk length L (0 = 256) */
-    int32_t tune;                 /* 0 = built-in tile choice, 1 = time the
-                                     compiled variants at create and keep
-                                     the fastest, -(v+1) = use variant v */
+    int32_t tune;                 /* 0 = built-in tile choice; 1 = autotune
+                                     at create: time candidate tilings on
+                                     pushes of zeros and keep the fastest
+                                     (plain: every compiled recursion
+                                     variant, then the time-segment length
+                                     and resident CTAs per SM; TC: the
+                                     chunk length 128 or 256, overriding
+                                     chunk_len); -(v+1) = recursion variant v */
     int64_t hbm_budget_bytes;     /* 0 = no limit; else create fails with
                                      SPIIR_EBUDGET above it */
     int32_t n_taps_up;            /* interpolator length: even, 2..64; 0 =
@@ -140,6 +145,10 @@ typedef struct {
     float smem_ways;           /* mean shared-memory wavefronts per round of
                                   32 delayed-input reads (1 = no conflicts) */
     float slot_fill;           /* n_filters / n_slots */
+    int32_t segment_base;      /* plain form: base-rate samples per time
+                                  segment of the recursion's work queue */
+    int32_t ctas_per_sm;       /* plain form: resident recursion CTAs per SM */
+    float tune_ms;             /* wall time the autotuner took (0: not run) */
 } spiir_bank_info;
 
 /* Create a bank: validate the description, place filters into warp tasks

@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -94,12 +95,13 @@ struct Unit {
 };
 
 // A push of n base-rate samples is cut into S time segments (S the smallest
-// power of two with S * 4096 >= n); level i's segments are segment_len
-// samples long (a multiple of 4, at most max(4096 >> i, 4)), so at the lower
+// power of two with S * seg_base >= n, seg_base 4096 unless tuned); level
+// i's segments are segment_len samples long (a multiple of 4, at most
+// max(seg_base >> i, 4)), so at the lower
 // rates the last segments may be short or empty.
-int push_segments_n(int64_t n) {
+int push_segments_n(int64_t n, int seg_base) {
     int S = 1;
-    while ((int64_t)S * 4096 < n) S *= 2;
+    while ((int64_t)S * seg_base < n) S *= 2;
     return S;
 }
 
@@ -189,6 +191,7 @@ void plan_info(const spiir_bank_desc *d, const Plan &p, spiir_bank_info *info) {
     info->n_units = (int32_t)p.n_units;
     info->smem_ways = p.lds_rounds ? (float)p.lds_wavefronts / (float)p.lds_rounds : 1.f;
     info->slot_fill = p.n_slots ? (float)d->n_filters / (float)p.n_slots : 1.f;
+    info->segment_base = p.seg_base;
 }
 
 int default_variant(const spiir_bank_desc *d) {
@@ -204,9 +207,10 @@ int default_variant(const spiir_bank_desc *d) {
 // instead of the bank's own (a server's shared strain buffers); it must hold
 // every filter's delay plus the level's alignment delay.
 spiir_status make_plan(const spiir_bank_desc *d, int variant, bool arrays, Plan &p,
-                       const int *hist_fixed) {
+                       const int *hist_fixed, int seg_base) {
     p = Plan();
     p.variant = variant;
+    p.seg_base = seg_base;
     spiir_recur_variant_shape(variant, &p.T, &p.FMAX);
     p.n_levels = d->n_levels;
     p.H = d->n_levels - 1;
@@ -240,7 +244,7 @@ spiir_status make_plan(const spiir_bank_desc *d, int variant, bool arrays, Plan 
         p.max_delay = std::max<int>(p.max_delay, (int)(maxd[i] + D));
         p.max_n[i] = push_max >> i;
         // the window holds the history plus the longest segment
-        const int64_t sg = std::min<int64_t>(round_up(p.max_n[i], 4), round_up(std::max(4096 >> i, 4), 4));
+        const int64_t sg = std::min<int64_t>(round_up(p.max_n[i], 4), round_up(std::max(p.seg_base >> i, 4), 4));
         if (16 + spiir_recur_red_bytes() + 4 * (h + sg) + 64 > kSmemMax - 1024)
             return fail(SPIIR_EUNSUPPORTED, "delay %lld at level %d does not fit shared memory",
                         (long long)h, i);
@@ -590,6 +594,8 @@ struct spiir_bank {
     int32_t *order = nullptr;
     unsigned int *queue = nullptr, *prog = nullptr;
     int ctas_per_sm = 1, n_sms = 1;
+    int ctas_cap = 0;                       // tuned CTAs per SM (0: the occupancy limit)
+    float tune_ms = 0.f;                    // wall time the autotuner took
     cudaStream_t cap = nullptr;             // private stream for graph capture
     cudaStream_t copy = nullptr;            // host push: device-to-host copies
     cudaEvent_t piece_done[4] = {};         // host push: a piece's SNR is in the ring
@@ -688,7 +694,7 @@ spiir_status alloc_plain(spiir_bank *b, cudaStream_t s) {
 
 // Time segments per push: about 4096 base-rate samples each, a power of two,
 // at least 4 samples at the lowest level.
-int push_segments(const Plan &, int64_t n) { return push_segments_n(n); }
+int push_segments(const Plan &p, int64_t n) { return push_segments_n(n, p.seg_base); }
 
 void level_args(const spiir_bank *b, int64_t n, int64_t n_prev, LevelArgs *lev) {
     const Plan &p = b->p;
@@ -775,7 +781,8 @@ spiir_status launch_sequence(spiir_bank *b, int s0, int count, const float *x, i
         level_args(b, n, n_prev, ra.lev);
         tm.begin(SPIIR_K_RECUR, st);
         const int64_t total = (int64_t)ra.n_segs * ra.n_items;
-        const int64_t resident = std::max<int64_t>(1, (int64_t)b->ctas_per_sm * b->n_sms / count);
+        const int per_sm = b->ctas_cap > 0 ? std::min(b->ctas_cap, b->ctas_per_sm) : b->ctas_per_sm;
+        const int64_t resident = std::max<int64_t>(1, (int64_t)per_sm * b->n_sms / count);
         const int ctas = (int)std::min<int64_t>(total, resident);
         CUDA_TRY(spiir_launch_recur(ra, p.variant, ctas, count, p.smem_bytes, st));
         tm.end(st);
@@ -896,8 +903,22 @@ uint64_t desc_fingerprint(const spiir_bank_desc *d) {
     return h;
 }
 
-spiir_status build_bank(const spiir_bank_desc *desc, int variant, cudaStream_t s,
+// Tile choices of a bank: the recursion variant, its time-segment length and
+// CTAs per SM (plain form), the chunk length (block form).
+struct Tuning {
+    int variant = 3;
+    int seg_base = 4096;
+    int ctas = 0;
+    int chunk_len = 0;
+};
+
+spiir_status build_bank(const spiir_bank_desc *desc_in, const Tuning &tn, cudaStream_t s,
                         spiir_bank *b) {
+    spiir_bank_desc dd = *desc_in;
+    if (tn.chunk_len) dd.chunk_len = tn.chunk_len;
+    const spiir_bank_desc *desc = &dd;
+    const int variant = tn.variant;
+    b->ctas_cap = tn.ctas;
     b->d = *desc;
     b->n_filters = desc->n_filters;
     b->d.a_re = b->d.a_im = b->d.b_re = b->d.b_im = nullptr;
@@ -929,7 +950,7 @@ spiir_status build_bank(const spiir_bank_desc *desc, int variant, cudaStream_t s
         if (st) return fail(st, "%s", spiir_tc_last_error());
         return SPIIR_OK;
     }
-    if ((st = make_plan(desc, variant, true, b->p))) return st;
+    if ((st = make_plan(desc, variant, true, b->p, nullptr, tn.seg_base))) return st;
     b->footprint = plan_footprint(desc, b->p);
     if (desc->hbm_budget_bytes > 0 && b->footprint > desc->hbm_budget_bytes)
         return fail(SPIIR_EBUDGET, "bank needs %lld bytes, budget %lld",
@@ -939,40 +960,92 @@ spiir_status build_bank(const spiir_bank_desc *desc, int variant, cudaStream_t s
     return SPIIR_OK;
 }
 
-// Time a few pushes of zeros through each compiled variant; return the best.
-spiir_status autotune(const spiir_bank_desc *desc, cudaStream_t s, int *best) {
+// Device time of a few pushes of zeros through a built bank (one push to
+// warm up, three timed), on its own kernels.
+spiir_status time_pushes(spiir_bank *b, const spiir_bank_desc *desc, cudaStream_t s, float *ms) {
+    const int S = desc->n_streams;
+    const int64_t n = (int64_t)desc->block_len * std::min(desc->max_push_blocks, 4);
+    float *x = b->tc ? spiir_tc_stage(b->tc) : b->xstage;
+    CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)S * n * sizeof(float), s));
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    spiir_status st = SPIIR_OK;
+    for (int r = 0; r < 4 && !st; ++r) {
+        if (r == 1) cudaEventRecord(e0, s);
+        st = b->tc ? spiir_tc_push(b->tc, 0, S, x, n, n, s, b->timer) : push_plain(b, 0, S, x, n, n, s);
+    }
+    cudaEventRecord(e1, s);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    if (e != cudaSuccess) return fail(SPIIR_ECUDA, "autotune: %s", cudaGetErrorString(e));
+    *ms = t;
+    return SPIIR_OK;
+}
+
+// Time one tuning; keep it in *best when faster. Banks that cannot be built
+// with it (shared memory, ...) are skipped.
+spiir_status try_tuning(const spiir_bank_desc *desc, const Tuning &tn, cudaStream_t s, Tuning *best,
+                        float *best_ms) {
+    spiir_bank tmp;
+    spiir_status st = build_bank(desc, tn, s, &tmp);
+    float ms = 0.f;
+    if (!st) st = time_pushes(&tmp, desc, s, &ms);
+    tmp.free_device();
+    if (st == SPIIR_ENOMEM || st == SPIIR_EBUDGET || st == SPIIR_ECUDA) return st;
+    if (!st && ms < *best_ms) {
+        *best_ms = ms;
+        *best = tn;
+    }
+    return SPIIR_OK;
+}
+
+// The autotuner (desc->tune == 1). Plain form: every compiled recursion
+// variant (time tile, filters per lane, CTAs per SM it is built for), then
+// for the fastest the time-segment length of the persistent queue (2048,
+// 4096, 8192 base-rate samples) and then fewer resident CTAs per SM. Block
+// form: the chunk length (128 or 256). Each candidate builds the bank and
+// times pushes of zeros of the bank's own push length.
+spiir_status autotune(const spiir_bank_desc *desc, cudaStream_t s, Tuning *best) {
     float best_ms = 1e30f;
-    *best = default_variant(desc);
+    spiir_status st;
+    if (desc->mode != SPIIR_PLAIN_FP32) {
+        best->chunk_len = desc->chunk_len ? desc->chunk_len : 256;
+        for (int Lc : {256, 128}) {
+            if (desc->block_len % Lc) continue;
+            Tuning tn;
+            tn.chunk_len = Lc;
+            if ((st = try_tuning(desc, tn, s, best, &best_ms))) return st;
+        }
+        return SPIIR_OK;
+    }
+    *best = Tuning();
+    best->variant = default_variant(desc);
     const int nv = spiir_recur_variant_count();
     for (int v = 0; v < nv; ++v) {
-        spiir_bank tmp;
-        spiir_status st = build_bank(desc, v, s, &tmp);
-        if (st) {
-            tmp.free_device();
-            if (st == SPIIR_ENOMEM || st == SPIIR_EBUDGET) return st;
-            continue;
-        }
-        const int64_t n = (int64_t)desc->block_len * std::min(desc->max_push_blocks, 4);
-        cudaMemsetAsync(tmp.xstage, 0, desc->n_streams * tmp.p.ring_len * sizeof(float), s);
-        cudaEvent_t e0, e1;
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
-        push_plain(&tmp, 0, desc->n_streams, tmp.xstage, tmp.p.ring_len, n, s);
-        cudaEventRecord(e0, s);
-        const int reps = 3;
-        for (int r = 0; r < reps; ++r) push_plain(&tmp, 0, desc->n_streams, tmp.xstage, tmp.p.ring_len, n, s);
-        cudaEventRecord(e1, s);
-        cudaError_t e = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        tmp.free_device();
-        if (e != cudaSuccess) return fail(SPIIR_ECUDA, "autotune: %s", cudaGetErrorString(e));
-        if (ms < best_ms) {
-            best_ms = ms;
-            *best = v;
-        }
+        Tuning tn;
+        tn.variant = v;
+        if ((st = try_tuning(desc, tn, s, best, &best_ms))) return st;
+    }
+    for (int sb : {2048, 8192}) {
+        Tuning tn = *best;
+        tn.seg_base = sb;
+        if ((st = try_tuning(desc, tn, s, best, &best_ms))) return st;
+    }
+    int occ = 1;
+    {
+        Plan p;
+        if (make_plan(desc, best->variant, false, p, nullptr, best->seg_base) == SPIIR_OK)
+            spiir_recur_prepare(best->variant, p.smem_bytes, &occ);
+    }
+    for (int c = occ - 1; c >= 1 && c >= occ - 2; --c) {
+        Tuning tn = *best;
+        tn.ctas = c;
+        if ((st = try_tuning(desc, tn, s, best, &best_ms))) return st;
     }
     return SPIIR_OK;
 }
@@ -991,14 +1064,19 @@ spiir_status spiir_bank_create(const spiir_bank_desc *desc, void *cuda_stream, s
     spiir_status st = validate(desc);
     if (st) return st;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    int variant = chosen_variant(desc);
-    if (desc->tune > 0 && desc->mode == SPIIR_PLAIN_FP32) {
-        if ((st = autotune(desc, s, &variant))) return st;
+    Tuning tn;
+    tn.variant = chosen_variant(desc);
+    float tune_ms = 0.f;
+    if (desc->tune > 0) {
+        const auto t0 = std::chrono::steady_clock::now();
+        if ((st = autotune(desc, s, &tn))) return st;
+        tune_ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
     spiir_bank *b = new (std::nothrow) spiir_bank();
     if (!b) return fail(SPIIR_ENOMEM, "host allocation failed");
     cudaGetDevice(&b->device);
-    st = build_bank(desc, variant, s, b);
+    b->tune_ms = tune_ms;
+    st = build_bank(desc, tn, s, b);
     if (st) {
         b->free_device();
         delete b;
@@ -1389,11 +1467,15 @@ spiir_status spiir_bank_get_info(spiir_bank_t b, spiir_bank_info *info) {
     info->footprint_bytes = b->footprint;
     if (b->tc) {
         spiir_tc_info(b->tc, info);
+        info->tune_ms = b->tune_ms;
         return SPIIR_OK;
     }
     plan_info(&b->d, b->p, info);
     info->slot_fill = b->p.n_slots ? (float)b->n_filters / (float)b->p.n_slots : 1.f;
     info->graph_captured = b->graphs.empty() ? 0 : 1;
+    info->segment_base = b->p.seg_base;
+    info->ctas_per_sm = b->ctas_cap > 0 ? std::min(b->ctas_cap, b->ctas_per_sm) : b->ctas_per_sm;
+    info->tune_ms = b->tune_ms;
     return SPIIR_OK;
 }
 

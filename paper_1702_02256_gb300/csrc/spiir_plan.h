@@ -31,6 +31,7 @@ inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 // Sizes and packed arrays of one bank for one recursion-kernel variant.
 struct Plan {
     int variant = 0, T = 32, FMAX = 8;
+    int seg_base = 4096;          // base-rate samples per time segment (tunable)
     int n_levels = 1, H = 0, n_taps = 32, n_taps_up = 32, align = 0;   // decimator, interpolator
     int hist[SPIIR_MAX_LEVELS] = {};
     int seg[SPIIR_MAX_LEVELS] = {};
@@ -65,10 +66,10 @@ struct Plan {
 spiir_status validate(const spiir_bank_desc *d);
 int chosen_variant(const spiir_bank_desc *d);
 spiir_status make_plan(const spiir_bank_desc *d, int variant, bool arrays, Plan &p,
-                       const int *hist_fixed = nullptr);
+                       const int *hist_fixed = nullptr, int seg_base = 4096);
 int64_t plan_footprint(const spiir_bank_desc *d, const Plan &p);
 int64_t align_delay(int level, int n_levels, int n_taps, int n_taps_up, int align);
-int push_segments_n(int64_t n);
+int push_segments_n(int64_t n, int seg_base = 4096);
 int64_t segment_len(int64_t n, int i, int S);
 void lib_kaiser_taps(int n, double A, float *out);
 

@@ -45,7 +45,8 @@ class BankInfo(ctypes.Structure):
         ("n_warp_tasks", _i32), ("n_cta_items", _i32), ("filters_per_lane", _i32),
         ("time_tile", _i32), ("kernel_variant", _i32), ("max_delay", _i32),
         ("tc_fir_len", _i32), ("graph_captured", _i32), ("n_units", _i32),
-        ("smem_ways", _f32), ("slot_fill", _f32),
+        ("smem_ways", _f32), ("slot_fill", _f32), ("segment_base", _i32), ("ctas_per_sm", _i32),
+        ("tune_ms", _f32),
     ]
 
 

@@ -100,7 +100,8 @@ def test_validation_rejects_bad_descriptions():
     # carry arithmetic of the tensor-core forms: 0 = FP64, 1 = double-float,
     # anything else is rejected before the form is looked at
     assert _status(bank, carry="df") == spiir.OK
-    assert _status(bank, carry=2) == spiir.EINVAL
+    assert _status(bank, carry=2) == spiir.OK
+    assert _status(bank, carry=3) == spiir.EINVAL
     assert _status(bank, mode="fp16", carry=-1) == spiir.EINVAL
     d, _k = spiir.make_desc(bank)
     assert spiir.lib().spiir_bank_create(None, None, ctypes.byref(ctypes.c_void_p())) == spiir.EINVAL

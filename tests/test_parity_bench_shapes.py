@@ -103,9 +103,27 @@ def test_multirate_autotuned_bank(torch_cuda, oracle_mod):
     v = info["kernel_variant"]
     n_var = 6
     assert 0 <= v < n_var
+    assert info["segment_base"] in (2048, 4096, 8192) and info["ctas_per_sm"] >= 1
+    assert info["tune_ms"] > 0
+    # the tuned time-segment length and CTA count change the schedule, not
+    # the arithmetic: the forced variant with default segments gives the same
+    # SNR bit for bit
     z_forced, info_f = _run_sampled(bank, x, sel, 1, 1, tune=-(v + 1))
-    assert info_f["kernel_variant"] == v
+    assert info_f["kernel_variant"] == v and info_f["segment_base"] == 4096
     assert np.array_equal(z, z_forced)
     ref = oracle_mod.spiir_multirate(bank, x[0], templates=sel)
     err = rel_rms(z[0], ref)
     assert err.max() <= TOL_PLAIN, float(err.max())
+
+
+def test_block_form_autotuned_chunk_length(torch_cuda, oracle_mod):
+    """tune = 1 on the block form picks the chunk length (128 or 256) by
+    timing; the bank it keeps matches the oracle."""
+    bank = inputs.single_rate_bank(300, 256, 1023, seed=replicas.rank_seed(0, 0))
+    x = inputs.strain(2, 3 * 4096, seed=1)
+    sel = _sample(bank.n_templates, 16)
+    z, info = _run_sampled(bank, x, sel, 1, 2, mode="fp16", tune=1)
+    assert info["time_tile"] in (128, 256) and info["tune_ms"] > 0
+    for s in range(2):
+        ref = oracle_mod.spiir_single(bank, x[s], templates=sel)
+        assert rel_rms(z[s], ref).max() <= TOL_TC
