@@ -633,6 +633,10 @@ def run_ours(args):
             "time_tile": main["info"]["time_tile"],
             "l2": "flushed between timed steps (256 MB write, untimed)",
             "parallelism": f"{ws} independent bank replicas" if ws > 1 else "1 GPU",
+            "reduction": args.ablation,
+            "segment_base": main["info"].get("segment_base"),
+            "ctas_per_sm": main["info"].get("ctas_per_sm"),
+            "tune_ms": main["info"].get("tune_ms"),
         },
         "real_time_templates": main["rtt"],
         "p50_block_latency_ms": main["p50"],
@@ -866,7 +870,15 @@ def main():
                     help="template count (0 = the workload's full size); small cases for ncu")
     ap.add_argument("--seconds", type=int, default=0,
                     help="seconds of strain per step (0 = the workload's 16 s)")
+    ap.add_argument("--ablation", default="adopted",
+                    choices=["adopted", "shuffle", "smem", "atomics"],
+                    help="recursion kernel's reduction (rebuilds libspiir with that "
+                         "SPIIR_REDUCE_ABLATION): adopted, shuffle butterfly for every group, "
+                         "shared-memory column sums for every group, cross-warp atomics")
     args = ap.parse_args()
+    if args.ablation != "adopted" and args.impl == "ours":
+        from paper_1702_02256_gb300 import build as lib_build
+        os.environ["SPIIR_LIB"] = lib_build.build_ablation(args.ablation)
     if args.tune is None:
         args.tune = 1 if args.workload == "multirate" else 0
     if args.warmup < 3:

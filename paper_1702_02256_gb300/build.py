@@ -37,6 +37,48 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+# Reduction ablations of the recursion kernel (compile-time switch
+# SPIIR_REDUCE_ABLATION in csrc/spiir_plain.cu): name -> value.
+ABLATIONS = {"adopted": 0, "shuffle": 1, "smem": 2, "atomics": 3}
+
+
+def build_ablation(name: str, verbose: bool = False) -> str:
+    """libspiir.so with the recursion kernel's reduction switched to `name`
+    (see ABLATIONS), in _build/ablation_<name>/; only spiir_plain.cu is
+    recompiled, the other objects are the default build's."""
+    k = ABLATIONS[name]
+    build(verbose=verbose)
+    if k == 0:
+        return LIB
+    out = os.path.join(BUILD, f"ablation_{name}")
+    os.makedirs(out, exist_ok=True)
+    src = os.path.join(CSRC, "spiir_plain.cu")
+    obj = os.path.join(out, "spiir_plain.o")
+    lib = os.path.join(out, "libspiir.so")
+    headers = sorted(glob.glob(os.path.join(CSRC, "*.h"))) + [os.path.join(ROOT, "include", "spiir.h")]
+    if _stale(obj, [src] + headers):
+        r = subprocess.run([nvcc()] + ARCH + FLAGS + [f"-DSPIIR_REDUCE_ABLATION={k}", "-c", src, "-o", obj],
+                           capture_output=True, text=True)
+        if verbose or r.returncode:
+            sys.stderr.write(r.stdout + r.stderr)
+        if r.returncode:
+            raise RuntimeError(f"nvcc failed for the {name} ablation")
+    others = [os.path.join(BUILD, os.path.basename(f)[:-3] + ".o")
+              for f in sorted(glob.glob(os.path.join(CSRC, "*.cu"))) if not f.endswith("spiir_plain.cu")]
+    if _stale(lib, [obj] + others):
+        tmp = lib + f".tmp{os.getpid()}"
+        subprocess.check_call([nvcc()] + ARCH + ["-shared", "-o", tmp, obj] + others)
+        os.replace(tmp, lib)
+    return lib
+
+
+def build_ablations(names, verbose: bool = False) -> dict:
+    """build_ablation for several names, compiled in parallel."""
+    build(verbose=verbose)
+    with cf.ThreadPoolExecutor(max_workers=max(1, len(names))) as ex:
+        return dict(zip(names, ex.map(lambda n: build_ablation(n, verbose), names)))
+
+
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))

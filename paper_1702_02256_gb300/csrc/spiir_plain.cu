@@ -30,6 +30,23 @@
 
 #include "spiir_internal.h"
 
+// Reduction of a unit's per-lane sums, chosen at compile time so that the
+// paper's alternatives (Sec. 3.1.3: shuffle or shared-memory reduction,
+// cross-warp direct atomics) can be rebuilt and timed against the adopted
+// one:
+//   0  adopted: shared-memory column sums for full-warp units of 32-sample
+//      tiles, shuffle butterfly for smaller groups, ordered hand-off across
+//      the warps of a unit;
+//   1  shuffle butterfly for every group size;
+//   2  shared-memory column sums for every group of 2 or more lanes
+//      (32-sample tiles);
+//   3  as 0, but the warps of a multi-warp unit add their sums into the
+//      output row with atomics (the rows are zeroed before the kernel; the
+//      order of the additions, and so the last bits, vary from run to run).
+#ifndef SPIIR_REDUCE_ABLATION
+#define SPIIR_REDUCE_ABLATION 0
+#endif
+
 namespace {
 
 // ---------------------------------------------------------------------------
@@ -309,7 +326,34 @@ struct OutCtx {
 template <int T, int G>
 __device__ __forceinline__ void reduce_write(float (&re)[T], float (&im)[T], int lane, int tl,
                                              int t0, int tile, const OutCtx &o) {
-    if constexpr (T == 32 && G == 32) {
+    constexpr int kAbl = SPIIR_REDUCE_ABLATION;
+    if constexpr (kAbl == 2 && T == 32 && G >= 2 && G < 32) {
+        // shared-memory column sums for a group of G lanes: lane l of group g
+        // sums columns (l % G) CH .. (l % G) CH + CH - 1 over the group's rows
+        constexpr int CHs = T / G;
+        float2 *sc = o.scratch + o.warp * (32 * kRowPitch);
+#pragma unroll
+        for (int i = 0; i < T; ++i) sc[lane * kRowPitch + i] = make_float2(re[i], im[i]);
+        __syncwarp();
+        const int g0 = lane & ~(G - 1), c0 = (lane & (G - 1)) * CHs;
+        float ar[CHs], ai[CHs];
+#pragma unroll
+        for (int i = 0; i < CHs; ++i) ar[i] = ai[i] = 0.f;
+#pragma unroll
+        for (int q = 0; q < G; ++q)
+#pragma unroll
+            for (int i = 0; i < CHs; ++i) {
+                const float2 v = sc[(g0 + q) * kRowPitch + c0 + i];
+                ar[i] += v.x;
+                ai[i] += v.y;
+            }
+#pragma unroll
+        for (int i = 0; i < CHs; ++i) {
+            re[i] = ar[i];
+            im[i] = ai[i];
+        }
+        __syncwarp();
+    } else if constexpr (kAbl != 1 && T == 32 && G == 32) {
         // A whole warp sums each of the 32 samples: through the warp's
         // shared-memory rows (lane l stores its 32 sums in row l, then sums
         // column l over the rows in lane order) this takes 32 stores, 32 loads
@@ -335,7 +379,24 @@ __device__ __forceinline__ void reduce_write(float (&re)[T], float (&im)[T], int
     constexpr int NS = ilog2(G < T ? G : T);
     constexpr int NR = ilog2(G) - NS;
     constexpr int CH = (T / G) > 1 ? (T / G) : 1;
-    if constexpr (G == 32) {
+    if constexpr (G == 32 && kAbl == 3) {
+        if (o.xw_log2 > 0) {
+            // every warp of the unit adds its sums into the zeroed row (each
+            // rank has the unit's destination in this build)
+            if (!o.valid) return;
+            if ((lane & ((1 << NR) - 1)) != 0) return;
+            float2 *row = o.row + t0;
+            const int tc = ((lane & (G - 1)) >> NR) * CH;
+#pragma unroll
+            for (int i = 0; i < CH; ++i)
+                if (tc + i < tl) {
+                    atomicAdd(&row[tc + i].x, o.scale * re[i]);
+                    atomicAdd(&row[tc + i].y, o.scale * im[i]);
+                }
+            return;
+        }
+    }
+    if constexpr (G == 32 && kAbl != 3) {
         if (o.xw_log2 > 0) {
             const int nw = 1 << o.xw_log2;
             const int first = o.warp - o.xw_rank;
@@ -515,7 +576,7 @@ __global__ void __launch_bounds__(SPIIR_CTA_WARPS * 32, MINB) recur_kernel(const
                 o.red = red;
                 o.scratch = scratch;
                 const int grp = lane >> wt.g_log2;
-                if (grp < wt.n_groups && wt.xw_rank == 0) {
+                if (grp < wt.n_groups && (wt.xw_rank == 0 || SPIIR_REDUCE_ABLATION == 3)) {
                     const int dst = a.task_out[wt.out_base + grp];
                     o.valid = true;
                     if (dst >= 0) {
@@ -806,6 +867,18 @@ cudaError_t spiir_launch_decimate(const DecimArgs &a, int n_streams, cudaStream_
 
 cudaError_t spiir_launch_recur(const RecurArgs &a, int variant, int n_ctas, int n_streams,
                                int smem_bytes, cudaStream_t s) {
+#if SPIIR_REDUCE_ABLATION == 3
+    // the atomics build adds into its destination rows: zero them first
+    for (int q = 0; q < n_streams; ++q) {
+        cudaError_t e = cudaMemset2DAsync(a.z + (int64_t)(a.stream0 + q) * a.z_stream_stride,
+                                          a.z_row_stride * sizeof(float2), 0, (size_t)a.lev[0].n * sizeof(float2),
+                                          (size_t)(a.z_stream_stride / a.z_row_stride), s);
+        if (e == cudaSuccess && a.partial && a.partial_stream_stride)
+            e = cudaMemsetAsync(a.partial + (int64_t)(a.stream0 + q) * a.partial_stream_stride, 0,
+                                (size_t)a.partial_stream_stride * sizeof(float2), s);
+        if (e != cudaSuccess) return e;
+    }
+#endif
     kVariants[variant].fn<<<dim3(n_ctas, n_streams), SPIIR_CTA_WARPS * 32, smem_bytes, s>>>(a);
     return cudaGetLastError();
 }

@@ -123,13 +123,15 @@ _SIGS = {
 
 
 def lib():
-    """Load libspiir.so (built by __graft_entry__.build()); fail loudly if absent."""
+    """Load libspiir.so (built by __graft_entry__.build()); fail loudly if absent.
+    SPIIR_LIB, if set, names another build of it (a reduction ablation)."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise ImportError(f"{LIB_PATH} is missing: build it with "
+        path = os.environ.get("SPIIR_LIB", LIB_PATH)
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with "
                               "`python -c 'import __graft_entry__ as g; g.build()'`")
-        L = ctypes.CDLL(LIB_PATH)
+        L = ctypes.CDLL(path)
         for name, (res, args) in _SIGS.items():
             fn = getattr(L, name)
             fn.restype = res
