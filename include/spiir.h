@@ -453,6 +453,41 @@ spiir_status spiir_server_kernel_times(spiir_server_t srv, spiir_kernel_times *o
 /* Release everything the server holds. NULL is ignored. */
 void spiir_server_destroy(spiir_server_t srv);
 
+/* ------------------------------------------------------------------------
+ * Replicas: one bank split by templates over several devices.
+ *
+ * Templates are independent (Eqs. iireq0, iireq1), so the bank of desc is
+ * cut into contiguous template ranges of about equal filter-samples, one
+ * ordinary bank per listed device (a device may be listed more than once),
+ * with no exchange between devices. Each push copies the host strain to every
+ * device, the devices filter at the same time (one host thread each), and the
+ * SNR rows are gathered into one host array in template order.
+ * ------------------------------------------------------------------------ */
+typedef struct spiir_replicas *spiir_replicas_t;
+
+/* Create the replicas. devices: n_devices device ordinals (1 <= n_devices <=
+ * n_templates). desc as for spiir_bank_create (its arrays are copied).
+ * Errors: EINVAL (description, a device not present), ENOMEM, ECUDA, and any
+ * error of spiir_bank_create on a device. */
+spiir_status spiir_replicas_create(const spiir_bank_desc *desc, const int32_t *devices,
+                                   int32_t n_devices, spiir_replicas_t *out);
+
+/* Push n_samples of every stream from host memory x_host [n_streams][n_samples]
+ * (n_samples as for spiir_push_block) through every replica and write the SNR
+ * to host memory z_host: complex64 [n_streams][n_templates][n_samples], the
+ * layout of spiir_read_snr for the whole bank. Returns when z_host is written.
+ * The caller owns both buffers. Errors: EINVAL, and those of
+ * spiir_push_block_host on a device. */
+spiir_status spiir_replicas_push_host(spiir_replicas_t rp, const float *x_host, int64_t n_samples,
+                                      void *z_host);
+
+/* Replica i's device and template range [template0, template0 + n_templates). */
+spiir_status spiir_replicas_get(spiir_replicas_t rp, int32_t i, int32_t *device,
+                                int32_t *template0, int32_t *n_templates);
+
+/* Release every replica. NULL is ignored. */
+void spiir_replicas_destroy(spiir_replicas_t rp);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *spiir_last_error(void);
 

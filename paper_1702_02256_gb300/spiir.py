@@ -119,6 +119,11 @@ _SIGS = {
     "spiir_server_get_info": (_i32, [_c_void_p, ctypes.POINTER(ServerInfo)]),
     "spiir_server_sync_status": (_i32, [_c_void_p]),
     "spiir_server_destroy": (None, [_c_void_p]),
+    "spiir_replicas_create": (_i32, [ctypes.POINTER(BankDesc), _c_void_p, _i32, ctypes.POINTER(_c_void_p)]),
+    "spiir_replicas_push_host": (_i32, [_c_void_p, _c_void_p, _i64, _c_void_p]),
+    "spiir_replicas_get": (_i32, [_c_void_p, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                                  ctypes.POINTER(_i32)]),
+    "spiir_replicas_destroy": (None, [_c_void_p]),
 }
 
 
@@ -455,6 +460,52 @@ class Server:
     def close(self):
         if getattr(self, "_h", None):
             lib().spiir_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Replicas:
+    """One bank split by templates over several devices (spiir_replicas_t):
+    host strain in, host SNR of the whole bank out."""
+
+    def __init__(self, bank, devices, n_streams: int = 1, block_len: int = 4096,
+                 max_push_blocks: int = 1, **kw):
+        d, _keep = make_desc(bank, n_streams=n_streams, block_len=block_len,
+                             max_push_blocks=max_push_blocks, **kw)
+        devs = (ctypes.c_int32 * len(devices))(*devices)
+        h = _c_void_p()
+        check(lib().spiir_replicas_create(ctypes.byref(d), devs, len(devices), ctypes.byref(h)))
+        self._h = h
+        self.n_templates = bank.n_templates
+        self.n_streams = n_streams
+        self.n_replicas = len(devices)
+
+    def push_host(self, x, z_out=None):
+        """x: numpy float32 [n_streams, n]; returns complex64 [n_streams, T, n]."""
+        x = np.ascontiguousarray(x, np.float32)
+        n = int(x.shape[-1])
+        if z_out is None:
+            z_out = np.empty((self.n_streams, self.n_templates, n), np.complex64)
+        check(lib().spiir_replicas_push_host(self._h, x.ctypes.data, n, z_out.ctypes.data))
+        return z_out
+
+    def ranges(self):
+        """[(device, first template, templates)] per replica."""
+        out = []
+        for i in range(self.n_replicas):
+            dv, t0, nt = _i32(), _i32(), _i32()
+            check(lib().spiir_replicas_get(self._h, i, ctypes.byref(dv), ctypes.byref(t0), ctypes.byref(nt)))
+            out.append((dv.value, t0.value, nt.value))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().spiir_replicas_destroy(self._h)
             self._h = None
 
     def __del__(self):
