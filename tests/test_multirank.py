@@ -53,28 +53,32 @@ def test_two_rank_max_and_rate():
 def test_replicas_behind_the_abi_match_one_bank():
     """spiir_replicas on the device list [0, 0, 0] (three template ranges on
     one GPU: independent banks, nothing waits on another) gives the SNR of
-    one bank of all templates bit for bit, multi-rate and two streams, over
-    two host pushes; every range is non-empty and they tile the bank."""
+    one bank of all templates, multi-rate and two streams, over two host
+    pushes: to the last bits (the packer's slot order depends on which units
+    share a warp) and against the oracle; every range is non-empty and they
+    tile the bank."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import numpy as np
     from paper_1702_02256_gb300 import inputs, spiir
     bank = inputs.multi_rate_bank(40, 4, seed=21, delay_max=500)
-    # every (template, rate) has a filter of the largest delay, so that each
-    # range's strain history (largest delay per rate) is the whole bank's and
-    # the packer lays out each template's filters the same way
-    key = bank.template_id.astype(np.int64) * 4 + bank.level
-    first = np.r_[True, key[1:] != key[:-1]]
-    bank.delay[first] = 500
     x = inputs.strain(2, 2 * 2048, seed=22)
     one = spiir.Bank(bank, n_streams=2, block_len=2048)
     rep = spiir.Replicas(bank, [0, 0, 0], n_streams=2, block_len=2048)
     r = rep.ranges()
     assert [t0 for _, t0, _ in r] == [0, r[0][2], r[0][2] + r[1][2]] and sum(n for _, _, n in r) == 40
     assert all(n > 0 for _, _, n in r)
+    from oracle import oracle
+    from tests._util import TOL_PLAIN, rel_rms
+    got = []
     for k in range(2):
         xk = np.ascontiguousarray(x[:, k * 2048:(k + 1) * 2048])
-        assert np.array_equal(rep.push_host(xk), one.push_host(xk))
+        zr = rep.push_host(xk).astype(np.complex128)
+        assert rel_rms(zr, one.push_host(xk).astype(np.complex128)).max() <= 1e-6
+        got.append(zr)
     rep.close()
     one.close()
+    got = np.concatenate(got, axis=-1)
+    for s in range(2):
+        assert rel_rms(got[s], oracle.spiir_multirate(bank, x[s])).max() <= TOL_PLAIN
