@@ -597,7 +597,7 @@ struct spiir_bank {
     int ctas_cap = 0;                       // tuned CTAs per SM (0: the occupancy limit)
     float tune_ms = 0.f;                    // wall time the autotuner took
     cudaStream_t cap = nullptr;             // private stream for graph capture
-    cudaStream_t copy = nullptr;            // host push: device-to-host copies
+    cudaStream_t copy[2] = {nullptr, nullptr};   // host push: device-to-host copies
     cudaEvent_t piece_done[4] = {};         // host push: a piece's SNR is in the ring
     std::vector<GraphEntry> graphs;
     std::vector<int64_t> last_n;            // samples of the last kernel push (strain history)
@@ -639,10 +639,11 @@ struct spiir_bank {
             cudaStreamDestroy(cap);
             cap = nullptr;
         }
-        if (copy) {
-            cudaStreamDestroy(copy);
-            copy = nullptr;
-        }
+        for (auto &c : copy)
+            if (c) {
+                cudaStreamDestroy(c);
+                c = nullptr;
+            }
         for (auto &e : piece_done)
             if (e) {
                 cudaEventDestroy(e);
@@ -1377,13 +1378,14 @@ spiir_status spiir_push_block_host(spiir_bank_t b, int32_t stream_id, const floa
     const int T = b->d.n_templates;
     // A push of several blocks runs as up to four pieces of whole blocks.
     // Piece i writes output-ring columns [off_i, off_i + n_i) (pushes compose
-    // exactly: block-split invariance), and its SNR is copied back on a
-    // second stream while piece i + 1 computes. The ring then holds the whole
-    // push, as after one push of n_samples.
+    // exactly: block-split invariance), and its SNR is copied back while
+    // piece i + 1 computes, the template rows split over two copy streams
+    // (two copy engines: one device-to-host stream does not fill the link).
+    // The ring then holds the whole push, as after one push of n_samples.
     const int64_t n_blocks = n_samples / b->d.block_len;
     const int n_pieces = (int)std::min<int64_t>(4, n_blocks);
-    if (n_pieces > 1 && !b->copy) {
-        CUDA_TRY(cudaStreamCreateWithFlags(&b->copy, cudaStreamNonBlocking));
+    if (!b->copy[0]) {
+        for (auto &c : b->copy) CUDA_TRY(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
         for (auto &e : b->piece_done) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
     int64_t off = 0;
@@ -1410,12 +1412,9 @@ spiir_status spiir_push_block_host(spiir_bank_t b, int32_t stream_id, const floa
                 if (st) return st;
             }
         }
-        cudaStream_t cs = s;
-        if (n_pieces > 1) {
-            CUDA_TRY(cudaEventRecord(b->piece_done[i], s));
-            CUDA_TRY(cudaStreamWaitEvent(b->copy, b->piece_done[i], 0));
-            cs = b->copy;
-        }
+        const int n_cs = 2;
+        CUDA_TRY(cudaEventRecord(b->piece_done[i], s));
+        for (auto &c : b->copy) CUDA_TRY(cudaStreamWaitEvent(c, b->piece_done[i], 0));
         for (int q = s0; q < s0 + cnt; ++q) {
             const float2 *src;
             int64_t ring;
@@ -1425,9 +1424,15 @@ spiir_status spiir_push_block_host(spiir_bank_t b, int32_t stream_id, const floa
                 ring = b->p.ring_len;
                 src = b->z + (int64_t)q * T * ring;
             }
-            char *dst = (char *)z_host + ((int64_t)(q - s0) * T * n_samples + off) * sizeof(float2);
-            CUDA_TRY(cudaMemcpy2DAsync(dst, n_samples * sizeof(float2), src + off, ring * sizeof(float2),
-                                       n_i * sizeof(float2), T, cudaMemcpyDeviceToHost, cs));
+            for (int h = 0; h < n_cs; ++h) {
+                const int r0 = T * h / n_cs, r1 = T * (h + 1) / n_cs;
+                if (r1 <= r0) continue;
+                char *dst = (char *)z_host + ((int64_t)(q - s0) * T * n_samples + (int64_t)r0 * n_samples + off) *
+                                                 sizeof(float2);
+                CUDA_TRY(cudaMemcpy2DAsync(dst, n_samples * sizeof(float2), src + (int64_t)r0 * ring + off,
+                                           ring * sizeof(float2), n_i * sizeof(float2), r1 - r0,
+                                           cudaMemcpyDeviceToHost, b->copy[h]));
+            }
         }
         off += n_i;
     }
@@ -1435,7 +1440,8 @@ spiir_status spiir_push_block_host(spiir_bank_t b, int32_t stream_id, const floa
         b->ring_n[q] = n_samples;
         b->out_valid[q] = 1;
     }
-    if (b->copy) CUDA_TRY(cudaStreamSynchronize(b->copy));
+    for (auto &c : b->copy)
+        if (c) CUDA_TRY(cudaStreamSynchronize(c));
     CUDA_TRY(cudaStreamSynchronize(s));
     return SPIIR_OK;
 }
