@@ -340,7 +340,8 @@ spiir_status spiir_filter_noalloc(const spiir_bank_desc *desc, const float *x_de
  * launch over the work items of every member and level (Eqs. iireq0,
  * iireq1), one upsample-and-add launch over every member's templates; the
  * tensor-core modes run the levels whose block holds whole chunks in the
- * block-parallel form, batched over all members, and the rest in the plain
+ * block-parallel form, batched over all members (for each template with
+ * enough filters at the level, tc_min_filters), and the rest in the plain
  * form. Members join and leave between pushes; their filter states and
  * resampler histories stay on the device between pushes, in pooled arrays
  * that grow as needed and are reused after a member leaves.
@@ -375,6 +376,12 @@ typedef struct {
     int32_t chunk_len;     /* TC modes: chunk length (0 = 256) */
     int32_t carry;         /* TC modes: as in spiir_bank_desc */
     int32_t tune;          /* recursion variant: -(v+1) forces v, else built-in */
+    int32_t tc_min_filters;/* TC modes: a template runs a block-form level in
+                              the block form when it has at least this many
+                              filters there, else in the plain form (the
+                              block form's cost per template-sample does not
+                              shrink with the filter count); 0 = 24, 1 =
+                              every template with filters */
 } spiir_server_desc;
 
 /* Facts about a server. */

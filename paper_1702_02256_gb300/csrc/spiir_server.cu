@@ -132,7 +132,9 @@ struct DevVec {
 
 // A member's part at one block-form level.
 struct MemberTc {
-    bool used = false;           // the member has filters at this level
+    bool used = false;           // some of the member's templates run this level in the block form
+    std::vector<int32_t> row;    // per member template: its row among them, or -1 (plain form)
+    int nT = 0;                  // templates routed to the block form
     int64_t g0 = 0, ng = 0;      // impulse-response groups
     int64_t t0 = 0, nt = 0;      // carry tiles
     TcPack pk;                   // host packing (only has_carry kept once uploaded)
@@ -182,6 +184,7 @@ struct spiir_server {
     // block form
     bool tc_mode = false, bf16 = false, df = false;
     int tcL = 256, tcF = 0, tcK = 0, n_slices = 0, n_tc_levels = 0;
+    int tc_min = 24;             // filters a template needs at a level to run it in the block form
     TcPool tcp[SPIIR_MAX_LEVELS];
     uint4 *hank = nullptr, *xseg = nullptr;
     // shared strain
@@ -428,7 +431,7 @@ spiir_status place_tc(spiir_server *sv, Member &m, int i, cudaStream_t s) {
     std::vector<float> rs(nr, 0.f);
     std::vector<uint8_t> hc(nr, 0);
     std::vector<int32_t> tp(nr, 0), te(nr, 0);
-    for (int r = 0; r < m.T; ++r) {
+    for (int r = 0; r < mt.nT; ++r) {
         rs[r] = pk.row_scale[r];
         hc[r] = pk.has_carry[r];
         tp[r] = (int32_t)(mt.t0 + pk.tile_ptr[r]);
@@ -572,7 +575,8 @@ spiir_status rebuild_lists(spiir_server *sv, cudaStream_t s) {
                 if (!p.comb_ptr.empty())
                     for (int32_t q = p.comb_ptr[(size_t)t * sv->L + i]; q < p.comb_ptr[(size_t)t * sv->L + i + 1]; ++q)
                         crows.push_back((int32_t)(m->prow0[i] + p.comb_rows[q]));
-                if (m->tc[i].used) crows.push_back((int32_t)(sv->tc_row_base(i) + m->tc[i].g0 * 64 + t));
+                if (m->tc[i].used && m->tc[i].row[t] >= 0)
+                    crows.push_back((int32_t)(sv->tc_row_base(i) + m->tc[i].g0 * 64 + m->tc[i].row[t]));
             }
             cptr[j + 1] = (int32_t)crows.size();
         }
@@ -597,7 +601,7 @@ spiir_status rebuild_lists(spiir_server *sv, cudaStream_t s) {
             const MemberTc &mt = m->tc[i];
             if (!mt.used) continue;
             for (int64_t g = 0; g < mt.ng; ++g) gl.push_back((int32_t)(mt.g0 + g));
-            for (int r = 0; r < m->T && r < (int)mt.pk.has_carry.size(); ++r)
+            for (int r = 0; r < mt.nT && r < (int)mt.pk.has_carry.size(); ++r)
                 if (mt.pk.has_carry[r]) tl.push_back((int32_t)(mt.g0 * 64 + r));
         }
         if ((st = t.groups.upload(gl, s)) || (st = t.tmpl_of.upload(tl, s))) return st;
@@ -886,26 +890,44 @@ spiir_status build_member(const spiir_server *sv, const spiir_bank_desc *member,
     m.n_filters = d.n_filters;
     m.fs_per_push = 0;
     for (int64_t k = 0; k < d.n_filters; ++k) m.fs_per_push += sv->block >> (d.level ? d.level[k] : 0);
-    // the plain levels' filters
+    // Routing: at a block-form level a template runs in the block form when
+    // it has at least tc_min filters there (the block form's cost per
+    // template-sample is fixed by F + L, the plain recursion's grows with the
+    // filters), else with its other filters in the plain form.
+    const int thr = sv->tc_min;
+    bool any_tc = false;
+    for (int i = 0; i < sv->L; ++i) {
+        MemberTc &mt = m.tc[i];
+        mt.used = false;
+        mt.nT = 0;
+        mt.row.clear();
+        if (!sv->tcp[i].on) continue;
+        std::vector<int32_t> cnt(m.T, 0);
+        for (int64_t k = 0; k < d.n_filters; ++k)
+            if ((d.level ? d.level[k] : 0) == i) cnt[d.template_id[k]]++;
+        mt.row.assign(m.T, -1);
+        for (int t = 0; t < m.T; ++t)
+            if (cnt[t] > 0 && cnt[t] >= thr) mt.row[t] = mt.nT++;
+        mt.used = mt.nT > 0;
+        any_tc |= mt.used;
+    }
+    auto to_tc = [&](int64_t k) {
+        const int l = d.level ? d.level[k] : 0;
+        return m.tc[l].used && m.tc[l].row[d.template_id[k]] >= 0;
+    };
+    // the filters of the plain form
     std::vector<float> ar, ai, br, bi;
     std::vector<int32_t> dl, tid;
     std::vector<int8_t> lv;
-    bool any_tc = false;
-    for (int i = 0; i < sv->L; ++i) m.tc[i].used = false;
     for (int64_t k = 0; k < d.n_filters; ++k) {
-        const int l = d.level ? d.level[k] : 0;
-        if (sv->tcp[l].on) {
-            m.tc[l].used = true;
-            any_tc = true;
-            continue;
-        }
+        if (to_tc(k)) continue;
         ar.push_back(d.a_re[k]);
         ai.push_back(d.a_im[k]);
         br.push_back(d.b_re[k]);
         bi.push_back(d.b_im[k]);
         dl.push_back(d.delay[k]);
         tid.push_back(d.template_id[k]);
-        lv.push_back((int8_t)l);
+        lv.push_back((int8_t)(d.level ? d.level[k] : 0));
     }
     spiir_bank_desc dp = d;
     dp.n_filters = (int64_t)ar.size();
@@ -920,20 +942,42 @@ spiir_status build_member(const spiir_server *sv, const spiir_bank_desc *member,
     if (m.p.smem_bytes > sv->smem_bytes)
         return fail(SPIIR_EINVAL, "member needs more shared memory than the server's kernel setup");
     m.combine = m.p.need_combine || any_tc;
+    // each block-form level: its routed templates, renumbered
     for (int i = 0; i < sv->L; ++i) {
-        if (!m.tc[i].used) continue;
+        MemberTc &mt = m.tc[i];
+        if (!mt.used) continue;
+        std::vector<float> qr, qi, cr, ci;
+        std::vector<int32_t> qd, qt;
+        std::vector<int64_t> tcnt(mt.nT, 0);
+        for (int64_t k = 0; k < d.n_filters; ++k) {
+            if ((d.level ? d.level[k] : 0) != i || mt.row[d.template_id[k]] < 0) continue;
+            qr.push_back(d.a_re[k]);
+            qi.push_back(d.a_im[k]);
+            cr.push_back(d.b_re[k]);
+            ci.push_back(d.b_im[k]);
+            qd.push_back(d.delay[k]);
+            qt.push_back(mt.row[d.template_id[k]]);
+            tcnt[mt.row[d.template_id[k]]]++;
+        }
         if (arrays) {
-            if ((st = spiir_tc_pack(&d, i, sv->tcF, sv->tcL, 1.0, sv->bf16, sv->df, m.tc[i].pk)))
+            spiir_bank_desc dt = d;
+            dt.n_templates = mt.nT;
+            dt.n_filters = (int64_t)qr.size();
+            dt.a_re = qr.data();
+            dt.a_im = qi.data();
+            dt.b_re = cr.data();
+            dt.b_im = ci.data();
+            dt.delay = qd.data();
+            dt.template_id = qt.data();
+            dt.level = nullptr;
+            if ((st = spiir_tc_pack(&dt, -1, sv->tcF, sv->tcL, 1.0, sv->bf16, sv->df, mt.pk)))
                 return fail(st, "%s", spiir_tc_last_error());
         } else {
             // sizes only: groups of 64 templates, tiles of 128 filters per template
-            std::vector<int64_t> cnt(m.T, 0);
-            for (int64_t k = 0; k < d.n_filters; ++k)
-                if ((d.level ? d.level[k] : 0) == i) cnt[d.template_id[k]]++;
-            m.tc[i].pk.n_groups = (m.T + 63) / 64;
+            mt.pk.n_groups = (mt.nT + 63) / 64;
             int nt = 0;
-            for (int t = 0; t < m.T; ++t) nt += (int)((cnt[t] + kTcTile - 1) / kTcTile);
-            m.tc[i].pk.n_tiles = nt;
+            for (int t = 0; t < mt.nT; ++t) nt += (int)((tcnt[t] + kTcTile - 1) / kTcTile);
+            mt.pk.n_tiles = nt;
         }
     }
     return SPIIR_OK;
@@ -1008,6 +1052,7 @@ spiir_status spiir_server_create(const spiir_server_desc *desc, void *cuda_strea
     sv->bf16 = desc->mode == SPIIR_TC_BF16;
     sv->df = desc->carry == 1;
     sv->tcL = tcL;
+    sv->tc_min = desc->tc_min_filters > 0 ? desc->tc_min_filters : 24;
     sv->tcF = tcF;
     sv->tcK = tcF + tcL;
     sv->n_slices = sv->tcK / 64;

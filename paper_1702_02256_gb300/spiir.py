@@ -56,6 +56,7 @@ class ServerDesc(ctypes.Structure):
         ("max_delay", _i32), ("h_down", _c_void_p), ("h_up", _c_void_p),
         ("n_taps", _i32), ("n_taps_up", _i32), ("align", _i32), ("snr_scale", _f32),
         ("mode", _i32), ("chunk_len", _i32), ("carry", _i32), ("tune", _i32),
+        ("tc_min_filters", _i32),
     ]
 
 
@@ -373,7 +374,8 @@ class Server:
     def __init__(self, n_streams: int, n_levels: int, block_len: int, max_delay: int,
                  base_rate: int = 4096, mode: str = "plain", chunk_len: int = 0,
                  carry="fp64", tune: int = 0, h_down=None, h_up=None,
-                 align: Optional[bool] = None, snr_scale: float = 0.0, stream=None):
+                 align: Optional[bool] = None, snr_scale: float = 0.0, tc_min_filters: int = 0,
+                 stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libspiir needs a CUDA device")
@@ -394,6 +396,7 @@ class Server:
         d.chunk_len = chunk_len
         d.carry = CARRY[carry] if isinstance(carry, str) else int(carry)
         d.tune = tune
+        d.tc_min_filters = tc_min_filters
         h = _c_void_p()
         check(lib().spiir_server_create(ctypes.byref(d), _stream_handle(stream), ctypes.byref(h)))
         self._h = h

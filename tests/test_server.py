@@ -160,10 +160,11 @@ def test_late_single_rate_member_against_the_oracle(torch_cuda, oracle_mod):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("mode", ["fp16", "bf16"])
-def test_block_form_members_match_the_oracle(torch_cuda, oracle_mod, mode):
-    """Tensor-core server, 7 rates: levels 0-4 (4096-256 samples per block)
-    run in the block form batched over all members, levels 5-6 in the plain
+@pytest.mark.parametrize("mode,tc_min", [("fp16", 1), ("fp16", 24), ("bf16", 24)])
+def test_block_form_members_match_the_oracle(torch_cuda, oracle_mod, mode, tc_min):
+    """Tensor-core server, 7 rates: at levels 0-4 (4096-256 samples per
+    block) the templates with at least tc_min filters there run in the block
+    form batched over all members, the others (and levels 5-6) in the plain
     form; members present from the first push against the FP64 oracle at the
     block form's tolerance (fp16; single-pass bf16 at its looser bound)."""
     import torch
@@ -174,7 +175,7 @@ def test_block_form_members_match_the_oracle(torch_cuda, oracle_mod, mode):
     x = torch.from_numpy(inputs.strain(3, 3 * block, seed=65)).cuda()
     xh = x.cpu().numpy()
     banks = [inputs.multi_rate_bank(T, 7, seed=170 + T) for T in (3, 70, 5)]
-    srv = spiir.Server(3, 7, block, 1023, mode=mode, chunk_len=256)
+    srv = spiir.Server(3, 7, block, 1023, mode=mode, chunk_len=256, tc_min_filters=tc_min)
     ids = [srv.add(b) for b in banks]
     out = {i: [] for i in ids}
     for b in range(3):
@@ -200,7 +201,7 @@ def test_block_form_member_alone_equals_member_in_a_changing_mix(torch_cuda):
     x = torch.from_numpy(inputs.strain(3, n_blocks * block, seed=66)).cuda()
     banks = [inputs.multi_rate_bank(T, 4, seed=190 + T, delay_max=900) for T in (5, 80, 3, 17, 130)]
     spec = [(0, 7), (0, 3), (1, 5), (2, 5), (4, 3)]
-    kw = dict(mode="fp16", chunk_len=256)
+    kw = dict(mode="fp16", chunk_len=256, tc_min_filters=40)
     mix = _run(banks, spec, x, block, 4, 900, **kw)
     for i in range(len(banks)):
         only = [(spec[j] if j == i else (n_blocks + 1, 0)) for j in range(len(banks))]
