@@ -719,6 +719,8 @@ __global__ void __launch_bounds__(kCombThreads, 4) combine_kernel(const CombineA
         bool ok = true;
         if (bytes) {
             if (tid == 0) {
+                // the previous chunk's reads of the stage before this copy's writes
+                fence_proxy_async_smem();
                 mbar_arrive_expect_tx(mbar, bytes);
                 for (int i = 0; i <= H; ++i)
                     if (cptr[i + 1] > cptr[i]) {
