@@ -574,6 +574,7 @@ struct GraphEntry {
     int s0, count;
     int64_t n, n_prev, zoff;
     cudaGraphExec_t exec;
+    std::vector<int64_t> prev;   // block form: previous push length of every pushed stream
 };
 
 struct spiir_bank {
@@ -842,7 +843,7 @@ spiir_status push_graph(spiir_bank *b, int s0, int count, const float *x, int64_
         e = cudaGraphInstantiate(&exec, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return fail(SPIIR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
-        b->graphs.push_back(GraphEntry{s0, count, n, n_prev, zoff, exec});
+        b->graphs.push_back(GraphEntry{s0, count, n, n_prev, zoff, exec, {}});
         ge = &b->graphs.back();
     }
     float *dst = b->xstage + (int64_t)s0 * n;
@@ -855,6 +856,50 @@ spiir_status push_graph(spiir_bank *b, int s0, int count, const float *x, int64_
         }
     }
     CUDA_TRY(cudaGraphLaunch(ge->exec, st));
+    return SPIIR_OK;
+}
+
+// A block-form push replayed from a CUDA graph (captured once per stream
+// set, length, previous lengths and output offset): the strain is copied into
+// the bank's staging buffer, which the graph reads.
+spiir_status push_tc(spiir_bank *b, int s0, int count, const float *x, int64_t n, cudaStream_t st,
+                     int64_t zoff) {
+    std::vector<int64_t> &last = spiir_tc_last_n(b->tc);
+    if (!b->cap || b->timer->on) {
+        spiir_status r = spiir_tc_push(b->tc, s0, count, x, n, n, st, b->timer, zoff);
+        return r ? fail(r, "%s", spiir_tc_last_error()) : SPIIR_OK;
+    }
+    std::vector<int64_t> prev(last.begin() + s0, last.begin() + s0 + count);
+    GraphEntry *ge = nullptr;
+    for (auto &g : b->graphs)
+        if (g.s0 == s0 && g.count == count && g.n == n && g.zoff == zoff && g.prev == prev) ge = &g;
+    float *stage = spiir_tc_stage(b->tc);
+    if (!ge) {
+        if (b->graphs.size() >= 16) {
+            cudaGraphExecDestroy(b->graphs.front().exec);
+            b->graphs.erase(b->graphs.begin());
+        }
+        cudaGraph_t g = nullptr;
+        CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+        spiir_status stc = spiir_tc_push(b->tc, s0, count, stage, n, n, b->cap, b->timer, zoff);
+        cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+        // capturing ran the push's host logic: put its state back
+        std::copy(prev.begin(), prev.end(), last.begin() + s0);
+        if (stc) {
+            if (g) cudaGraphDestroy(g);
+            return fail(stc, "%s", spiir_tc_last_error());
+        }
+        if (e != cudaSuccess) return fail(SPIIR_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(SPIIR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        b->graphs.push_back(GraphEntry{s0, count, n, prev.empty() ? 0 : prev[0], zoff, exec, prev});
+        ge = &b->graphs.back();
+    }
+    if (x != stage) CUDA_TRY(cudaMemcpyAsync(stage, x, (size_t)count * n * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(cudaGraphLaunch(ge->exec, st));
+    for (int q = s0; q < s0 + count; ++q) last[q] = n;
     return SPIIR_OK;
 }
 
@@ -949,6 +994,7 @@ spiir_status build_bank(const spiir_bank_desc *desc_in, const Tuning &tn, cudaSt
     if (desc->mode != SPIIR_PLAIN_FP32) {
         st = spiir_tc_create(desc, b->scale, s, &b->tc, &b->footprint);
         if (st) return fail(st, "%s", spiir_tc_last_error());
+        CUDA_TRY(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
         return SPIIR_OK;
     }
     if ((st = make_plan(desc, variant, true, b->p, nullptr, tn.seg_base))) return st;
@@ -1102,8 +1148,8 @@ spiir_status spiir_push_block(spiir_bank_t b, int32_t stream_id, const float *x_
     const int s0 = stream_id < 0 ? 0 : stream_id;
     const int cnt = stream_id < 0 ? b->d.n_streams : 1;
     if (b->tc) {
-        spiir_status st = spiir_tc_push(b->tc, s0, cnt, x_dev, n_samples, n_samples, s, b->timer);
-        if (st) return fail(st, "%s", spiir_tc_last_error());
+        spiir_status st = push_tc(b, s0, cnt, x_dev, n_samples, s, 0);
+        if (st) return st;
         for (int q = s0; q < s0 + cnt; ++q) {
             b->last_n[q] = b->ring_n[q] = n_samples;
             b->out_valid[q] = 1;
@@ -1400,8 +1446,8 @@ spiir_status spiir_push_block_host(spiir_bank_t b, int32_t stream_id, const floa
         CUDA_TRY(cudaMemcpy2DAsync(stage, n_i * sizeof(float), x_host + off, n_samples * sizeof(float),
                                    n_i * sizeof(float), cnt, cudaMemcpyHostToDevice, s));
         if (b->tc) {
-            spiir_status st = spiir_tc_push(b->tc, s0, cnt, stage, n_i, n_i, s, b->timer, off);
-            if (st) return fail(st, "%s", spiir_tc_last_error());
+            spiir_status st = push_tc(b, s0, cnt, stage, n_i, s, off);
+            if (st) return st;
             for (int q = s0; q < s0 + cnt; ++q) b->last_n[q] = n_i;
         } else if (same) {
             spiir_status st = push_plain(b, s0, cnt, stage, n_i, n_i, s, false, off);
@@ -1474,6 +1520,7 @@ spiir_status spiir_bank_get_info(spiir_bank_t b, spiir_bank_info *info) {
     if (b->tc) {
         spiir_tc_info(b->tc, info);
         info->tune_ms = b->tune_ms;
+        info->graph_captured = b->graphs.empty() ? 0 : 1;
         return SPIIR_OK;
     }
     plan_info(&b->d, b->p, info);

@@ -1824,6 +1824,8 @@ spiir_status spiir_tc_reset(TcBank *b, int s0, int count, cudaStream_t s) {
 
 int64_t spiir_tc_xbuf_len(TcBank *b) { return b->xbuf_stride; }
 
+std::vector<int64_t> &spiir_tc_last_n(TcBank *b) { return b->last_n; }
+
 spiir_status spiir_tc_state_get(TcBank *b, int q, double *v, float *xbuf, int64_t *last_n, cudaStream_t s) {
     std::vector<uint4> raw(b->n_slots);
     if (b->n_slots)

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "spiir.h"
 
 struct TcBank;
@@ -25,6 +27,8 @@ int64_t spiir_tc_footprint(const spiir_bank_desc *desc);
 // the carry arithmetic), its strain history (xbuf_len floats) and the length
 // of its last push. Synchronous on s.
 int64_t spiir_tc_xbuf_len(TcBank *b);
+// Length of each stream's last push (host state a push reads and updates).
+std::vector<int64_t> &spiir_tc_last_n(TcBank *b);
 spiir_status spiir_tc_state_get(TcBank *b, int q, double *v, float *xbuf, int64_t *last_n,
                                 cudaStream_t s);
 spiir_status spiir_tc_state_set(TcBank *b, int q, const double *v, const float *xbuf, int64_t last_n,
