@@ -586,6 +586,15 @@ def run_ours(args):
         chosen = _measure(w, args.chosen, args, dev, dist, sampler, rank, ws, err=err)
     # the block-parallel configuration (8000 x 256 filters, 2 streams, 1 s
     # pushes): the plain form and every requested tensor-core form
+    # the multi-rate bank (4000 templates, 7 rates), autotuned, 16 s in 1 s pushes
+    c2 = None
+    if args.workload == "single" and args.config2:
+        w2 = _workload("multirate", rank)
+        err2 = _err_sample(w2) if lead else None
+        tune_keep = args.tune
+        args.tune = 1
+        c2 = ("plain", _measure(w2, "plain", args, dev, dist, sampler, rank, ws, err=err2))
+        args.tune = tune_keep
     c3 = []
     if args.workload == "single" and args.config3:
         w3 = _workload("tc", rank)
@@ -656,6 +665,16 @@ def run_ours(args):
         line["snr_error_vs_oracle"] = _oracle_error(w, err[0], main["err_z"])
     if chosen:
         line["chosen"] = _leg_json(chosen, w, args.workload, args, peaks, sms, main, err)
+    if c2:
+        line["config2"] = {
+            "workload": w2["desc"],
+            "variant_choice": "autotuned at bank creation",
+            "kernel_variant": c2[1]["info"]["kernel_variant"],
+            "segment_base": c2[1]["info"].get("segment_base"),
+            "ctas_per_sm": c2[1]["info"].get("ctas_per_sm"),
+            "tune_ms": c2[1]["info"].get("tune_ms"),
+            "legs": {"plain": _leg_json(c2[1], w2, "multirate", args, peaks, sms, None, err2)},
+        }
     if args.workload == "single" and args.serving and ws == 1:
         line["serving"] = _serve_line(args)
     if c3:
@@ -853,6 +872,9 @@ def main():
                     help="compute form of the headline number (default: plain; fp16 for tc)")
     ap.add_argument("--chosen", default="fp16", choices=["", "plain", "fp16", "bf16"],
                     help="second form measured on the same workload and reported as 'chosen'")
+    ap.add_argument("--config2", type=int, default=1,
+                    help="default workload only: also measure the multi-rate bank (4000 templates, "
+                         "7 rates, autotuned) with the plain form")
     ap.add_argument("--config3", default="fp16",
                     help="default workload only: also measure the 8000 x 256 two-stream "
                          "configuration with the plain form and these tensor-core forms "

@@ -207,3 +207,36 @@ def test_block_form_member_alone_equals_member_in_a_changing_mix(torch_cuda):
         only = [(spec[j] if j == i else (n_blocks + 1, 0)) for j in range(len(banks))]
         alone = _run(banks, only, x, block, 4, 900, **kw)
         assert np.array_equal(mix[i], alone[i]), i
+
+
+@pytest.mark.gpu
+def test_server_rejects_bad_requests(torch_cuda):
+    """Wrong rate count or a delay above max_delay: EINVAL at add; an unknown
+    member: EINVAL; a member that has not taken part in a push yet: ESTATE;
+    removing it before its first push leaves no trace; pushes without
+    members keep the strain moving."""
+    import torch
+    from paper_1702_02256_gb300 import spiir
+    srv = spiir.Server(2, 3, 1024, 200)
+    with pytest.raises(spiir.SpiirError) as e:
+        srv.add(inputs.multi_rate_bank(3, 4, seed=1, delay_max=100))
+    assert e.value.status == spiir.EINVAL
+    with pytest.raises(spiir.SpiirError) as e:
+        srv.add(inputs.multi_rate_bank(3, 3, seed=1, delay_max=300))
+    assert e.value.status == spiir.EINVAL and "max_delay" in str(e.value)
+    x = torch.zeros((2, 1024), dtype=torch.float32, device="cuda")
+    srv.push(x)
+    mid = srv.add(inputs.multi_rate_bank(3, 3, seed=2, delay_max=200))
+    with pytest.raises(spiir.SpiirError) as e:
+        srv.read(mid)
+    assert e.value.status == spiir.ESTATE
+    srv.remove(mid)
+    with pytest.raises(spiir.SpiirError) as e:
+        srv.remove(mid)
+    assert e.value.status == spiir.EINVAL
+    mid = srv.add(inputs.multi_rate_bank(3, 3, seed=3, delay_max=200))
+    srv.push(x)
+    assert srv.read(mid).shape == (2, 3, 1024)
+    assert srv.info()["n_members"] == 1
+    srv.sync_status()
+    srv.close()
