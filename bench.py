@@ -513,7 +513,8 @@ def _roofline(m, w, args, peaks, sms, wl=None):
     samples = S * w["x"].shape[1] * m["steps"]
     F = m["info"]["tc_fir_len"]
     L = w["chunk_len"]
-    fir_flops = 4.0 * (F + L) * bank.n_templates * samples        # 2 real rows x 2 flops x K
+    passes = 3 if m["form"] == "bf16x2" else 1                     # split bf16: hi*hi + hi*lo + lo*hi
+    fir_flops = passes * 4.0 * (F + L) * bank.n_templates * samples   # 2 real rows x 2 flops x K
     carry_flops = 12.0 * bank.n_filters * samples                 # 4M state + 8M output
     fir_ms, fir_n = kt.get("tc_fir", (0.0, 0))
     car_ms, car_n = kt.get("tc_carry", (0.0, 0))
@@ -526,7 +527,8 @@ def _roofline(m, w, args, peaks, sms, wl=None):
     return {"bound": "tensor", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
             "frac": ach / peak, "traffic": _traffic("spiir_tc.cu", key),
             "peak_basis": "measured dense bf16 burst (cuBLAS) of MEASURED_PEAKS; fp16 has the same "
-                          "nominal dense rate",
+                          "nominal dense rate" + ("; the split-bf16 FIR counts its three passes"
+                                                  if passes > 1 else ""),
             "fir_tflops": fir_flops / (fir_ms / 1e3) / 1e12 if fir_ms else None,
             "carry_tflops": carry_flops / (car_ms / 1e3) / 1e12 if car_ms else None}
 
@@ -868,14 +870,14 @@ def main():
                     help="default workload only: add the serving comparison (configuration-4 "
                          "requests, batched server, plain and --serve-forms) to the line")
     ap.add_argument("--serve-scale0", type=float, default=0.02)
-    ap.add_argument("--form", default="", choices=["", "plain", "fp16", "bf16"],
+    ap.add_argument("--form", default="", choices=["", "plain", "fp16", "bf16", "bf16x2"],
                     help="compute form of the headline number (default: plain; fp16 for tc)")
-    ap.add_argument("--chosen", default="fp16", choices=["", "plain", "fp16", "bf16"],
+    ap.add_argument("--chosen", default="fp16", choices=["", "plain", "fp16", "bf16", "bf16x2"],
                     help="second form measured on the same workload and reported as 'chosen'")
     ap.add_argument("--config2", type=int, default=1,
                     help="default workload only: also measure the multi-rate bank (4000 templates, "
                          "7 rates, autotuned) with the plain form")
-    ap.add_argument("--config3", default="fp16",
+    ap.add_argument("--config3", default="fp16,bf16x2",
                     help="default workload only: also measure the 8000 x 256 two-stream "
                          "configuration with the plain form and these tensor-core forms "
                          "(comma-separated; empty: skip)")

@@ -147,8 +147,6 @@ spiir_status validate(const spiir_bank_desc *d) {
         return fail(SPIIR_EINVAL, "unknown mode %d", (int)d->mode);
     if (d->mode != SPIIR_PLAIN_FP32 && d->n_levels != 1)
         return fail(SPIIR_EUNSUPPORTED, "tensor-core forms take single-rate banks");
-    if (d->mode == SPIIR_TC_BF16X2)
-        return fail(SPIIR_EUNSUPPORTED, "split-bf16 operands are not built; use SPIIR_TC_FP16");
     if (d->hbm_budget_bytes < 0) return fail(SPIIR_EINVAL, "hbm_budget_bytes must be >= 0");
     if (d->carry < 0 || d->carry > 2)
         return fail(SPIIR_EINVAL, "carry must be 0 (FP64 per batch), 1 (double-float) or 2 (FP64 per chunk)");

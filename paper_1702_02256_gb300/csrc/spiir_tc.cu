@@ -246,6 +246,8 @@ struct TcStageArgs {
     int32_t hist, F, L, K, n_chunks, n_streams, stream0;
     int32_t cpb, n_batches;   // carry: chunks per batch, batches
     uint4 *hank;              // [s][c][hank_bytes/16]  FIR Toeplitz source
+    uint4 *hank_lo;           // NULL, or the same layout: x - bf16(x), the low
+                              // part of a split-bf16 operand
     int32_t hank_bytes;
     uint4 *xseg;              // [batch][kXsegBytes/16] STATE strain segments
 };
@@ -320,6 +322,12 @@ __global__ void tc_stage_kernel(const TcStageArgs a) {
                 v[q] = (p < a.L + a.K - 1 && m >= n0 - a.F) ? x[m] : 0.f;
             }
             a.hank[i] = pack8<BF16>(v);
+            if (a.hank_lo) {
+                float lo[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) lo[q] = v[q] - __bfloat162float(__float2bfloat16_rn(v[q]));
+                a.hank_lo[i] = pack8<BF16>(lo);
+            }
         } else {
             // STATE segments of batch b: row n = (c, s, i2) (streams of a
             // chunk adjacent), K = i1:
@@ -1262,6 +1270,9 @@ struct TcBank {
     float2 *z = nullptr;
     unsigned int *status = nullptr;
     uint4 *hank = nullptr, *xseg = nullptr;   // staged strain operands
+    bool split = false;                       // split bf16: FIR in three passes
+    uint4 *H_lo = nullptr, *hank_lo = nullptr;
+    uint8_t *all_rows = nullptr;
     uint4 *panel = nullptr;                   // carry tiles' power panels
     std::vector<int64_t> slot_k;              // filter of each carry slot (-1: padding)
     int64_t n_filters = 0;
@@ -1326,6 +1337,8 @@ int64_t tc_bytes(const spiir_bank_desc *d, const TcPlan &p) {
     const int64_t C = p.max_n / p.L;
     b += S * C * hank_bytes_of(p.L, p.K);
     b += (C * S * (p.L / kJ) / kNii + 2) * kXsegBytes;
+    if (d->mode == SPIIR_TC_BF16X2)     // low parts of H and of the Toeplitz sources
+        b += (int64_t)p.n_groups * p.n_slices * kSliceBytes + S * C * hank_bytes_of(p.L, p.K) + p.T;
     return b + 256;
 }
 
@@ -1384,7 +1397,8 @@ int spiir_tc_xseg_bytes() { return kXsegBytes; }
 int spiir_tc_cpb(int streams, int L) { return carry_cpb(streams, L); }
 
 spiir_status spiir_tc_pack(const spiir_bank_desc *d, int level, int F, int L, double row_mult, bool bf16,
-                           bool df, TcPack &pk) {
+                           bool df, TcPack &pk, bool split) {
+    split = split && bf16;
     pk = TcPack();
     const int T = d->n_templates;
     const int K = F + L;
@@ -1405,6 +1419,7 @@ spiir_status spiir_tc_pack(const spiir_bank_desc *d, int level, int F, int L, do
     // Impulse responses h_t[q], q < K, in FP64; rows scaled by 2^e_t into the
     // 16-bit range; tiles [group][slice][r/8][k/8][r%8][k%8].
     pk.H.assign((size_t)pk.n_groups * pk.n_slices * (kSliceBytes / 2), 0);
+    if (split) pk.H_lo.assign(pk.H.size(), 0);
     pk.row_scale.assign(T, 0.f);
     auto work = [&](int t0, int t1) {
         std::vector<std::complex<double>> h(K);
@@ -1437,6 +1452,11 @@ spiir_status spiir_tc_pack(const spiir_bank_desc *d, int level, int F, int L, do
                     const size_t off = ((size_t)g * pk.n_slices + sl) * (kSliceBytes / 2) +
                                        (size_t)(r >> 3) * 512 + (kq >> 3) * 64 + (r & 7) * 8 + (kq & 7);
                     pk.H[off] = host16((float)val, bf16);
+                    if (split) {
+                        // hi + lo carries about 16 significant bits of h
+                        const double hi = (double)__bfloat162float(__ushort_as_bfloat16(pk.H[off]));
+                        pk.H_lo[off] = host16((float)(val - hi), true);
+                    }
                 }
             }
         }
@@ -1568,6 +1588,7 @@ spiir_status spiir_tc_launch(const TcLaunch &l, cudaStream_t s, KernelTimer *tim
     sa.cpb = cpb;
     sa.n_batches = n_batches;
     sa.hank = l.hank;
+    sa.hank_lo = l.H_lo ? l.hank_lo : nullptr;
     sa.hank_bytes = hb;
     sa.xseg = l.xseg;
     {
@@ -1638,13 +1659,23 @@ spiir_status spiir_tc_launch(const TcLaunch &l, cudaStream_t s, KernelTimer *tim
         const int items = l.n_groups * C * count;
         const int grid = std::min(items, l.n_sms);
         const int smem = fir_smem_of(l.L, l.K);
+        // split bf16: H x_hi, then H x_lo and H_lo x_hi added to z (the
+        // product of the two low parts, about 2^-16 of the result, is left out)
+        const int passes = l.H_lo ? 3 : 1;
         if (timer) timer->begin(SPIIR_K_TC_FIR, s);
-        if (l.bf16)
-            tc_fir_kernel<true><<<grid, kFirThreads, smem, s>>>(fa);
-        else
-            tc_fir_kernel<false><<<grid, kFirThreads, smem, s>>>(fa);
-        TC_CUDA(cudaGetLastError());
-        if (timer) timer->end(s);
+        for (int pass = 0; pass < passes; ++pass) {
+            if (pass > 0) {
+                fa.has_carry = l.all_rows;
+                fa.hank = pass == 1 ? l.hank_lo : l.hank;
+                fa.H = pass == 1 ? l.H : l.H_lo;
+            }
+            if (l.bf16)
+                tc_fir_kernel<true><<<grid, kFirThreads, smem, s>>>(fa);
+            else
+                tc_fir_kernel<false><<<grid, kFirThreads, smem, s>>>(fa);
+            TC_CUDA(cudaGetLastError());
+        }
+        if (timer) timer->end(s, passes);
     }
     return SPIIR_OK;
 }
@@ -1672,6 +1703,7 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
     b->ring_len = p.ring_len;
     b->xbuf_stride = p.xbuf_stride;
     b->bf16 = d->mode != SPIIR_TC_FP16;
+    b->split = d->mode == SPIIR_TC_BF16X2;
     b->df = d->carry == 1;
     b->carry_mode = d->carry;
     b->scale = scale;
@@ -1682,7 +1714,7 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
     *out = b;
 
     TcPack pk;
-    if ((st = spiir_tc_pack(d, -1, p.F, p.L, scale, b->bf16, b->df, pk))) return st;
+    if ((st = spiir_tc_pack(d, -1, p.F, p.L, scale, b->bf16, b->df, pk, b->split))) return st;
     std::vector<int32_t> tmpl_of;
     for (int t = 0; t < p.T; ++t)
         if (pk.has_carry[t]) tmpl_of.push_back(t);
@@ -1690,6 +1722,12 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
     b->n_filters = d->n_filters;
     if ((st = tc_upload(&b->H, std::vector<uint4>((uint4 *)pk.H.data(), (uint4 *)(pk.H.data() + pk.H.size())), s)))
         return st;
+    if (b->split) {
+        if ((st = tc_upload(&b->H_lo, std::vector<uint4>((uint4 *)pk.H_lo.data(),
+                                                         (uint4 *)(pk.H_lo.data() + pk.H_lo.size())), s)))
+            return st;
+        if ((st = tc_upload(&b->all_rows, std::vector<uint8_t>(std::max(1, p.T), 1), s))) return st;
+    }
     if ((st = tc_upload(&b->row_scale, pk.row_scale, s))) return st;
     if ((st = tc_upload(&b->tile_ptr, pk.tile_ptr, s))) return st;
     if ((st = tc_upload(&b->tmpl_of, tmpl_of, s))) return st;
@@ -1719,6 +1757,7 @@ spiir_status spiir_tc_create(const spiir_bank_desc *d, float scale, cudaStream_t
     b->hank_bytes = hank_bytes_of(p.L, p.K);
     const int64_t Cmax = p.max_n / p.L;
     TC_CUDA(cudaMalloc((void **)&b->hank, S * Cmax * b->hank_bytes));
+    if (b->split) TC_CUDA(cudaMalloc((void **)&b->hank_lo, S * Cmax * b->hank_bytes));
     const int64_t nbmax = (Cmax + carry_cpb(std::min<int64_t>(S, 2), p.L) - 1) / carry_cpb(std::min<int64_t>(S, 2), p.L) + 1;
     TC_CUDA(cudaMalloc((void **)&b->xseg, std::max<int64_t>(nbmax, Cmax) * kXsegBytes));
     int dev = 0;
@@ -1797,6 +1836,9 @@ spiir_status spiir_tc_push(TcBank *b, int s0, int count, const float *x, int64_t
     l.H = b->H;
     l.row_scale = b->row_scale;
     l.has_carry = b->has_carry;
+    l.H_lo = b->H_lo;
+    l.hank_lo = b->hank_lo;
+    l.all_rows = b->all_rows;
     l.groups = nullptr;
     l.n_groups = b->n_groups;
     l.n_rows = b->T;
@@ -1889,7 +1931,7 @@ void spiir_tc_info(TcBank *b, spiir_bank_info *info) {
     info->n_cta_items = b->n_groups;
     info->filters_per_lane = 0;
     info->time_tile = b->L;
-    info->kernel_variant = b->bf16 ? 2 : 1;
+    info->kernel_variant = b->split ? 3 : b->bf16 ? 2 : 1;
     info->max_delay = b->max_delay;
     info->tc_fir_len = b->F;
     info->graph_captured = 0;
@@ -1908,7 +1950,7 @@ void spiir_tc_destroy(TcBank *b) {
     if (!b) return;
     void *ptrs[] = {b->H, b->row_scale, b->tile_ptr, b->tmpl_of, b->has_carry, b->a, b->aJ, b->c,
                     b->aL, b->v, b->xbuf, b->stage, b->z, b->status, b->hank, b->xseg,
-                    b->aLf, b->aLb1, b->aLb2, b->panel};
+                    b->aLf, b->aLb1, b->aLb2, b->panel, b->H_lo, b->hank_lo, b->all_rows};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     delete b;

@@ -58,6 +58,7 @@ int spiir_tc_cpb(int streams, int L);             // chunks per carry batch
 struct TcPack {
     int T = 0, F = 0, L = 0, K = 0, n_groups = 0, n_slices = 0, n_tiles = 0;
     std::vector<uint16_t> H;          // [group][slice][kTcSliceBytes / 2]
+    std::vector<uint16_t> H_lo;       // split bf16 only: h - bf16(h), same layout
     std::vector<float> row_scale;     // [T]: row_mult * 2^-e_t
     std::vector<int32_t> tile_ptr;    // [T + 1]
     std::vector<uint8_t> has_carry;   // [T]
@@ -68,9 +69,10 @@ struct TcPack {
 };
 // level < 0: every filter (single rate); else the filters with level[k] ==
 // level. Delays must be < F. row_mult scales every output row (the SNR scale,
-// or 1 for a level sum that a later pass scales).
+// or 1 for a level sum that a later pass scales). split (with bf16): also the
+// low bf16 part of every impulse-response value, H_lo.
 spiir_status spiir_tc_pack(const spiir_bank_desc *d, int level, int F, int L, double row_mult, bool bf16,
-                           bool df, TcPack &pk);
+                           bool df, TcPack &pk, bool split = false);
 
 // One batched launch sequence of the block-parallel form for up to two
 // streams: strain staging, the carry kernel (state term into z) and the FIR
@@ -94,6 +96,12 @@ struct TcLaunch {
     const uint4 *H;
     const float *row_scale;
     const uint8_t *has_carry;
+    // split bf16 (H_lo non-NULL): the FIR runs three accumulating passes,
+    // H x + H x_lo + H_lo x, over the low parts H_lo and hank_lo (staged
+    // here); all_rows: n_rows ones, so that the later passes add to z
+    const uint4 *H_lo;
+    uint4 *hank_lo;
+    const uint8_t *all_rows;
     const int32_t *groups;             // NULL: groups 0 .. n_groups-1
     int n_groups, n_rows;              // groups to run; rows addressable in z
     // output rows (row t of stream s at z + s * z_stream_stride + t * z_row_stride)

@@ -15,7 +15,7 @@ def test_error_per_dtype(oracle_mod, capsys):
         pytest.skip("no CUDA device")
     w = inputs.workload(3, scale_templates=64, n_samples=4 * 4096)
     refs = [oracle_mod.spiir_single(w["bank"], w["x"][s]) for s in range(2)]
-    bounds = {"plain": TOL_PLAIN, "fp16": TOL_TC, "bf16": 1e-2}
+    bounds = {"plain": TOL_PLAIN, "fp16": TOL_TC, "bf16": 1e-2, "bf16x2": TOL_TC}
     lines = []
     for mode, tol in bounds.items():
         kw = {} if mode == "plain" else dict(mode=mode, chunk_len=256)

@@ -8,10 +8,11 @@ between) is checked per template and stream against the oracle's SNR over
 the whole series.
 
 * single-rate 1024 x 512 filters, delays 0-4095 (F = 4096, K = 4352 for the
-  block form), 16 s as one 16-block push: plain FP32 at 1e-5 and the fp16
-  block form at 1e-3;
+  block form), 16 s as one 16-block push: plain FP32 at 1e-5, the fp16 and
+  split-bf16 block forms at 1e-3;
 * 8000 x 256 filters, delays 0-1023, two streams, 8 s in 1 s pushes (16 carry
-  batches of 8 chunks per push and stream pair): plain at 1e-5, fp16 at 1e-3;
+  batches of 8 chunks per push and stream pair): plain at 1e-5, fp16 and
+  split bf16 at 1e-3;
 * the multi-rate 4000-template bank with the autotuner on (tune = 1): the
   variant it keeps is one of the compiled ones, gives the same SNR bit for
   bit as that variant forced, and matches the oracle at 1e-5.
@@ -64,26 +65,26 @@ def _config1_bank():
     return inputs.single_rate_bank(1024, 512, 4095, seed=replicas.rank_seed(0, 0))
 
 
-@pytest.mark.parametrize("form,tol", [("plain", TOL_PLAIN), ("fp16", TOL_TC)])
+@pytest.mark.parametrize("form,tol", [("plain", TOL_PLAIN), ("fp16", TOL_TC), ("bf16x2", TOL_TC)])
 def test_config1_bench_shape_16_block_push(torch_cuda, oracle_mod, form, tol):
     bank = _config1_bank()
     x = inputs.strain(1, 16 * 4096, seed=1)
     sel = _sample(bank.n_templates, 32)
-    kw = {} if form == "plain" else dict(mode="fp16", chunk_len=256)
+    kw = {} if form == "plain" else dict(mode=form, chunk_len=256)
     z, info = _run_sampled(bank, x, sel, 16, 1, **kw)
-    if form == "fp16":
+    if form != "plain":
         assert info["tc_fir_len"] == 4096       # delays up to 4095: K = 4352 lags
     ref = oracle_mod.spiir_single(bank, x[0], templates=sel)
     err = rel_rms(z[0], ref)
     assert err.max() <= tol, (form, float(err.max()))
 
 
-@pytest.mark.parametrize("form,tol", [("plain", TOL_PLAIN), ("fp16", TOL_TC)])
+@pytest.mark.parametrize("form,tol", [("plain", TOL_PLAIN), ("fp16", TOL_TC), ("bf16x2", TOL_TC)])
 def test_config3_bench_shape_8s_in_1s_pushes(torch_cuda, oracle_mod, form, tol):
     bank = inputs.single_rate_bank(8000, 256, 1023, seed=replicas.rank_seed(0, 0))
     x = inputs.strain(2, 8 * 4096, seed=1)
     sel = _sample(bank.n_templates, 24)
-    kw = {} if form == "plain" else dict(mode="fp16", chunk_len=256)
+    kw = {} if form == "plain" else dict(mode=form, chunk_len=256)
     z, info = _run_sampled(bank, x, sel, 1, 2, **kw)
     for s in range(2):
         ref = oracle_mod.spiir_single(bank, x[s], templates=sel)
