@@ -448,6 +448,50 @@ def _measure(w, form, args, dev, dist, sampler, rank, ws, err=None):
                 d2h=int(S * bank.n_templates * n * 8), wall=(t_wall0, t_wall1), err_z=err_z)
 
 
+_LINK = {}
+
+
+def _host_link(torch, dev):
+    """Device-to-host and host-to-device copy bandwidth of this GPU's host link
+    (GB/s): 256 MB between a device buffer and a pinned host buffer, best of 3
+    copies each way, CUDA events on a side stream. Measured once per run."""
+    if _LINK:
+        return _LINK
+    nbytes = 256 << 20
+    d = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    st = torch.cuda.Stream(dev)
+    out = {}
+    for name, dst, src in (("d2h_gbs", h, d), ("h2d_gbs", d, h)):
+        best = 0.0
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(st):
+                e0.record(st)
+                dst.copy_(src, non_blocking=True)
+                e1.record(st)
+            e1.synchronize()
+            best = max(best, nbytes / (e0.elapsed_time(e1) / 1e3) / 1e9)
+        out[name] = best
+    del d, h
+    _LINK.update(out)
+    return _LINK
+
+
+def _e2e_json(m, torch, dev):
+    """The end-to-end object: the host-buffer rate, its copy bytes, and the
+    bound the measured host link puts on it (each step's copies at the link's
+    rates, overlapped with the device step)."""
+    link = _host_link(torch, dev)
+    t_link = max(m["d2h"] / (link["d2h_gbs"] * 1e9), m["h2d"] / (link["h2d_gbs"] * 1e9),
+                 m["ms_per_step"] / 1e3)
+    bound = m["fs_per_step"] / t_link
+    return {"value": m["e2e"], "unit": UNIT, "h2d_bytes_per_step": m["h2d"],
+            "d2h_bytes_per_step": m["d2h"],
+            "host_link": {"d2h_gbs": round(link["d2h_gbs"], 1), "h2d_gbs": round(link["h2d_gbs"], 1)},
+            "link_bound": bound, "frac_of_link_bound": m["e2e"] / bound}
+
+
 def _form_desc(form: str, args) -> str:
     if form == "plain":
         return "plain FP32 recursion"
@@ -542,14 +586,14 @@ def _leg_json(m, w, wl, args, peaks, sms, plain=None, err=None):
     """One measured form of a workload as a JSON object: rate, step time,
     latency, roofline of its dominant kernel, end-to-end rate and SNR error
     against the oracle; speed-up over the plain form's leg when given."""
+    import torch
     o = {
         "form": _form_desc(m["form"], args),
         "value": m["value"], "unit": UNIT, "ms_per_step": m["ms_per_step"], "steps": m["steps"],
         "real_time_templates": m["rtt"],
         "p50_block_latency_ms": m["p50"], "p99_block_latency_ms": m["p99"],
         "roofline": _roofline(m, w, args, peaks, sms, wl),
-        "e2e": {"value": m["e2e"], "unit": UNIT, "h2d_bytes_per_step": m["h2d"],
-                "d2h_bytes_per_step": m["d2h"]},
+        "e2e": _e2e_json(m, torch, torch.cuda.current_device()),
         "kernel_ms": {k: v[0] for k, v in m["kt"].items()},
         "gpu_launches": int(sum(c for _, c in m["kt"].values())),
     }
@@ -658,8 +702,7 @@ def run_ours(args):
                          "sample": cpu_sample},
         "cpu_baseline_single_thread": {"value": cpu1_rate, "unit": UNIT, "cores": 1,
                                        "kind": "oracle", "sample": cpu1_sample},
-        "e2e": {"value": main["e2e"], "unit": UNIT, "h2d_bytes_per_step": main["h2d"],
-                "d2h_bytes_per_step": main["d2h"]},
+        "e2e": _e2e_json(main, torch, dev),
         "gpu_launches": int(sum(c for _, c in kt.values())),
         "clocks": clocks,
     }
