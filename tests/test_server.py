@@ -214,9 +214,12 @@ def test_server_rejects_bad_requests(torch_cuda):
     """Wrong rate count or a delay above max_delay: EINVAL at add; an unknown
     member: EINVAL; a member that has not taken part in a push yet: ESTATE;
     removing it before its first push leaves no trace; pushes without
-    members keep the strain moving."""
+    members keep the strain moving; split bf16 is a bank mode only."""
     import torch
     from paper_1702_02256_gb300 import spiir
+    with pytest.raises(spiir.SpiirError) as e:
+        spiir.Server(2, 3, 1024, 200, mode="bf16x2")
+    assert e.value.status == spiir.EUNSUPPORTED
     srv = spiir.Server(2, 3, 1024, 200)
     with pytest.raises(spiir.SpiirError) as e:
         srv.add(inputs.multi_rate_bank(3, 4, seed=1, delay_max=100))

@@ -32,6 +32,8 @@ def _bank(case):
         return bank, dict(mode="plain")
     if case == "fp16-fp64-carry":
         return bank, dict(mode="fp16", chunk_len=256)
+    if case == "bf16x2-fp64-carry":
+        return bank, dict(mode="bf16x2", chunk_len=256)
     return bank, dict(mode="fp16", chunk_len=256, carry="df")
 
 
@@ -43,7 +45,8 @@ def _pushes(b, xd, first, last):
     return out
 
 
-@pytest.mark.parametrize("case", ["plain-single", "plain-multirate", "fp16-fp64-carry", "fp16-df-carry"])
+@pytest.mark.parametrize("case", ["plain-single", "plain-multirate", "fp16-fp64-carry", "fp16-df-carry",
+                                  "bf16x2-fp64-carry"])
 def test_resume_continues_bitwise(torch_cuda, case):
     import torch
     from paper_1702_02256_gb300 import spiir
