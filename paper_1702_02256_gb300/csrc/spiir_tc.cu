@@ -100,20 +100,6 @@ __device__ __forceinline__ bool mbar_try(uint64_t *m, uint32_t ph) {
     return ok != 0;
 }
 
-// As mbar_try, with a hint (ns) for how long the thread may be suspended
-// while the phase is incomplete: a polling loop that does not take issue
-// slots from the warps doing the work.
-__device__ __forceinline__ bool mbar_try_ns(uint64_t *m, uint32_t ph, uint32_t ns) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(s32(m)), "r"(ph), "r"(ns)
-        : "memory");
-    return ok != 0;
-}
-
 // Bounded wait (~2 s): on timeout record it and report false.
 __device__ __forceinline__ bool mbar_wait(uint64_t *m, uint32_t ph, unsigned int *status) {
     if (mbar_try(m, ph)) return true;
@@ -550,17 +536,21 @@ __global__ void __launch_bounds__(kFirThreads, 1) tc_fir_kernel(const TcFirArgs 
 // groups, spread over warp roles:
 //   warp 0, lane 0   issues the STATE contractions in job order as soon as
 //                    each one's inputs are ready, and the strain-segment copies
-//   warp 13, lane 0  issues the OUTPUT contractions in job order (a separate
-//                    warp, on another scheduler: a single issuer sharing a
+//   last warp, lane 0  issues the OUTPUT contractions in job order (a
+//                    separate warp, on another scheduler: a single issuer sharing a
 //                    scheduler with the arithmetic warps was slow to react)
-//   warps 1-4        bulk copy of each job's precomputed power panel into
-//                    its slot (a panel copy runs up to four jobs ahead), and the epilogue
-//                    of each (template, batch): OUTPUT accumulators -> z,
-//                    taken while the next panel's slot is still in use (or
-//                    at the latest five jobs after its last tile)
-//   warps 5-8, 9-12  carry groups 0 and 1: STATE (tensor memory) -> FP32
-//                    carry inside a batch, FP64 (or double-float) from batch to batch
-//                    -> OUTPUT operand W of the job's slot
+//   next-to-last warp, lane 0  bulk copy of each job's precomputed power
+//                    panel into its slot (up to four jobs ahead)
+//   warps 1-4        the epilogue of each (template, batch) in order:
+//                    OUTPUT accumulators -> z (a separate role: taken by the
+//                    copying warps, the epilogues delayed the next panel)
+//   warps 5 ..       carry groups 0 and 1 of 4 S warps each, one thread per
+//                    filter and stream: STATE (tensor memory) -> FP32 carry
+//                    inside a batch, FP64 (or double-float) from batch to batch
+//                    -> OUTPUT operand W of the job's slot. With two streams a
+//                    filter's two chains run in two threads, which halves each
+//                    group's dependent chain per job (the groups' latency, not
+//                    the tensor pipe, sets the kernel's pace)
 // Panel of a 128-filter tile: 128 rows m of powers, layout
 // [k/8][m/8][k%8][m%8], in row groups of 8: group 2 p holds Re a_k^j and
 // group 2 p + 1 Im a_k^j for the powers j = 8 p .. 8 p + 7. STATE reads it
@@ -573,13 +563,16 @@ __global__ void __launch_bounds__(kFirThreads, 1) tc_fir_kernel(const TcFirArgs 
 // load (shape 16x256b) gives each epilogue thread all four terms of z(j, c).
 // Every hand-off between roles is an mbarrier: tcgen05.commit for
 // contractions, one arrive per thread for the 128-thread roles; every wait is
-// bounded and gives up at once when another role has given up (the panel role
-// agrees on it with a barrier reduction, so it leaves as a whole).
+// bounded and gives up at once when another role has given up (the epilogue
+// role agrees on it with a barrier reduction, so it leaves as a whole).
 // Tensor memory (512 columns): STATE of carry group g at 128 g (re 64, im 64
 // columns); OUTPUT of (template, batch) e at 256 + 128 (e % 2).
 // ---------------------------------------------------------------------------
 
-constexpr int kCarryWarps = 14;
+// Warps of the carry kernel for S streams: the two issuers, the panel
+// copier, the four epilogue warps and two carry groups of 4 S warps (one
+// thread per filter and stream).
+constexpr int carry_warps(int S) { return 7 + 8 * S; }
 constexpr int kPanelSlots = 4;     // power panels in flight
 constexpr int kWSlots = 2;         // OUTPUT operands W in flight
 constexpr int kPanelBytes = kTile * 2 * kJ * 2;                 // 32 KB
@@ -588,18 +581,6 @@ constexpr int kCarrySmem = kPanelSlots * kPanelBytes + kWSlots * kWBytes + 2 * k
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *m) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s32(m)) : "memory");
-}
-
-// Non-blocking test of an mbarrier phase.
-__device__ __forceinline__ bool mbar_test(uint64_t *m, uint32_t ph) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(s32(m)), "r"(ph)
-        : "memory");
-    return ok != 0;
 }
 
 // Bounded wait that also gives up when *abort is set; a timeout sets *abort.
@@ -650,11 +631,38 @@ __device__ __forceinline__ void tmem_ld16x256_x16(uint32_t taddr, uint32_t (&r)[
         : "memory");
 }
 
+// The same, 8 times along the columns (64 columns).
+__device__ __forceinline__ void tmem_ld16x256_x8(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x256b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+
+// 32 lanes x N consecutive columns (N = 2 or 4), without waiting.
+__device__ __forceinline__ void tmem_ld_n(uint32_t taddr, uint32_t (&r)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld_n(uint32_t taddr, uint32_t (&r)[2]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];"
+                 : "=r"(r[0]), "=r"(r[1])
+                 : "r"(taddr)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// The 128 threads of the panel role (named barrier 1): synchronise, and
+// The 128 threads of the epilogue role (named barrier 1): synchronise, and
 // agree on v (true only if every thread passes true), so that the role
 // leaves its loop as a whole.
 __device__ __forceinline__ bool panel_role_all(bool v) {
@@ -776,8 +784,9 @@ __device__ __forceinline__ float4 anchor_madd(float4 x, float4 y, float2 d) { re
 // batch with FP32 offsets inside it; 1: the same with a double-float anchor;
 // 2: FP64 state updated at every chunk.
 template <bool BF16, int LJ, int S, int MODE>
-__global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcCarryArgs a) {
+__global__ void __launch_bounds__(carry_warps(S) * 32, 1) tc_carry_kernel(const TcCarryArgs a) {
     constexpr bool DF = MODE == 1, CH = MODE == 2;
+    constexpr int kCarryWarps = carry_warps(S), kGW = 4 * S;   // warps, warps per carry group
     using Anchor = typename std::conditional<DF, float4, double2>::type;   // carry arithmetic
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t panel_full[kPanelSlots], panel_free[kPanelSlots], w_full[kWSlots], w_free[kWSlots],
@@ -801,12 +810,12 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             mbar_init(&panel_free[i], 1);
         }
         for (int i = 0; i < kWSlots; ++i) {
-            mbar_init(&w_full[i], 128);
+            mbar_init(&w_full[i], 32 * kGW);
             mbar_init(&w_free[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&state_full[i], 1);
-            mbar_init(&state_free[i], 128);
+            mbar_init(&state_free[i], 32 * kGW);
             mbar_init(&out_full[i], 1);
             mbar_init(&out_free[i], 128);
         }
@@ -956,21 +965,33 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                 mbar_wait(&drain_o, 0, a.status);
             }
         }
+    } else if (warp == kCarryWarps - 2) {
+        if (lane == 0) {
+            // ---------------- panel copies ----------------
+            // each job's precomputed power panel, one bulk copy into its slot
+            // as soon as the OUTPUT kPanelSlots jobs back has freed the slot
+            int last_copy = -1;
+            for (CarryJobs pt(a); pt.valid; pt.next()) {
+                const CarryJob J = pt.cur();
+                const int sl = J.s, use = J.j / kPanelSlots;
+                if (use > 0 && !mbar_wait_ab(&panel_free[sl], (use - 1) & 1, a.status, abort)) break;
+                mbar_expect(&panel_full[sl], kPanelBytes);
+                bulk_load(smem + sl * kPanelBytes, a.panel + (size_t)J.tile * (kPanelBytes / 16), kPanelBytes,
+                          &panel_full[sl]);
+                last_copy = J.j;
+            }
+            // no copy may still be writing shared memory when the CTA exits
+            for (int j = max(0, last_copy - kPanelSlots + 1); j <= last_copy; ++j)
+                mbar_wait(&panel_full[j % kPanelSlots], (uint32_t)(j / kPanelSlots) & 1u, a.status);
+        }
     } else if (warp <= 4) {
-        // ---------------- power panels and epilogue ----------------
-        // panel: the tile's precomputed panel, one bulk copy into the slot
-        // (issued by the role's first thread; last_copy = its latest job)
-        const bool leader = threadIdx.x == 32;
-        int last_copy = -1;
-        // epilogue: each warp reads its tensor-memory quadrant q (powers
-        // 16 q .. 16 q + 15) as two 16-lane halves
+        // ---------------- epilogue ----------------
+        // each (template, batch) in order, once its last OUTPUT has finished:
+        // OUTPUT accumulators -> z. Each warp reads its tensor-memory quadrant
+        // q (powers 16 q .. 16 q + 15) as two 16-lane halves.
         const uint32_t lane_base = ((uint32_t)((warp & 3) * 32)) << 16;
-        struct Ep {
-            int t, b0, e, j;
-        };
-        Ep ep0{}, ep1{}, ep2{}, ep3{}, ep4{};   // pending epilogues, oldest first (at most 5)
-        int ep_n = 0;
-        auto epilogue = [&](const Ep &J) -> bool {
+        carry_jobs(a, [&](const CarryJob &J) -> bool {
+            if (!J.last_tile) return true;
             const int ob = J.e & 1;
             if (!panel_role_all(mbar_wait_ab(&out_full[ob], (J.e >> 1) & 1, a.status, abort))) return false;
             tc_fence_after();
@@ -984,23 +1005,30 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             float2 *zb1 = zb0 + a.z_stream_stride;
             // chunk column c = 4 cb + t % 4 = (chunk S + stream) LJ + j2
             const int tm = lane & 3, qo = tm / LJ, j2 = tm % LJ;
+            // 8-column groups per load: all 16 at once, or two loads of 8
+            // where the larger carry groups leave fewer registers per thread
+            constexpr int kEp = S == 2 ? 8 : 16;
 #pragma unroll 1
-            for (int hf = 0; hf < 2; ++hf) {
+            for (int hp = 0; hp < 2 * (16 / kEp); ++hp) {
+                const int hf = hp / (16 / kEp), cp = hp % (16 / kEp);
                 // lanes 16 hf .. 16 hf + 15 of the quadrant: thread t gets the
                 // re row of power jj (lane t / 4) and its im row (lane t / 4 + 8),
                 // columns 2 (t % 4) and 2 (t % 4) + 1 of every 8
                 const int jj = (warp & 3) * 16 + 8 * hf + (lane >> 2);
-                uint32_t v[64];
-                tmem_ld16x256_x16(tb + ((uint32_t)(16 * hf) << 16), v);
+                uint32_t v[4 * kEp];
+                const uint32_t ta = tb + ((uint32_t)(16 * hf) << 16) + (uint32_t)(8 * kEp * cp);
+                if constexpr (kEp == 16) tmem_ld16x256_x16(ta, v);
+                else tmem_ld16x256_x8(ta, v);
                 tmem_wait_ld();
 #pragma unroll
-                for (int cb = 0; cb < 16; ++cb) {
+                for (int cl = 0; cl < kEp; ++cl) {
+                    const int cb = cp * kEp + cl;
                     const int c = 4 * cb + tm;
                     if (c < nii) {
                         const int q = (4 * cb) / LJ + qo;
                         float2 *zp = ((q % S) ? zb1 : zb0) + (q / S) * L + kJ * j2 + jj;
-                        const float r0 = __uint_as_float(v[4 * cb]), r1 = __uint_as_float(v[4 * cb + 1]);
-                        const float r2 = __uint_as_float(v[4 * cb + 2]), r3 = __uint_as_float(v[4 * cb + 3]);
+                        const float r0 = __uint_as_float(v[4 * cl]), r1 = __uint_as_float(v[4 * cl + 1]);
+                        const float r2 = __uint_as_float(v[4 * cl + 2]), r3 = __uint_as_float(v[4 * cl + 3]);
                         *zp = make_float2(a.scale * (r0 - r3), a.scale * (r1 + r2));
                     }
                 }
@@ -1008,78 +1036,13 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             tc_fence_before();
             mbar_arrive(&out_free[ob]);
             return true;
-        };
-        bool ok = true;
-        carry_jobs(a, [&](const CarryJob &J) -> bool {
-            const int sl = J.s;
-            // Epilogues five or more jobs back are taken first: the OUTPUT
-            // that frees this job's slot may need their accumulator (first
-            // tile of the (template, batch) two after them).
-            auto pop = [&]() {
-                ep0 = ep1;
-                ep1 = ep2;
-                ep2 = ep3;
-                ep3 = ep4;
-                --ep_n;
-            };
-            while (ep_n > 0 && ep0.j <= J.j - 5) {
-                if (!(ok = epilogue(ep0))) return false;
-                pop();
-            }
-            if (J.last_tile) {
-                const Ep n{J.t, J.b0, J.e, J.j};
-                if (ep_n == 0) ep0 = n;
-                else if (ep_n == 1) ep1 = n;
-                else if (ep_n == 2) ep2 = n;
-                else if (ep_n == 3) ep3 = n;
-                else ep4 = n;
-                ++ep_n;
-            }
-            // While this job's slot is still in use, take the epilogues whose
-            // contractions have finished (bounded like every other wait; the
-            // slot test suspends the threads for up to 1 us at a time).
-            const int use = J.j / kPanelSlots;
-            if (use > 0) {
-                uint64_t t0 = 0;
-                while (!panel_role_all(mbar_try_ns(&panel_free[sl], (use - 1) & 1, 1000u))) {
-                    if (ep_n > 0 && ep0.j < J.j &&
-                        panel_role_all(mbar_test(&out_full[ep0.e & 1], (ep0.e >> 1) & 1))) {
-                        if (!(ok = epilogue(ep0))) return false;
-                        pop();
-                        t0 = 0;
-                        continue;
-                    }
-                    const uint64_t now = gtime();
-                    if (t0 == 0) {
-                        t0 = now;
-                    } else if (now - t0 > 2000000000ull) {
-                        atomicExch(a.status, SPIIR_DEV_TIMEOUT);
-                        *abort = 1;
-                    }
-                    if (!(ok = panel_role_all(*abort == 0))) return false;
-                }
-            }
-            if (leader) {
-                mbar_expect(&panel_full[sl], kPanelBytes);
-                bulk_load(smem + sl * kPanelBytes, a.panel + (size_t)J.tile * (kPanelBytes / 16), kPanelBytes,
-                          &panel_full[sl]);
-                last_copy = J.j;
-            }
-            return true;
         });
-        if (ok && ep_n > 0) ok = epilogue(ep0);
-        if (ok && ep_n > 1) ok = epilogue(ep1);
-        if (ok && ep_n > 2) ok = epilogue(ep2);
-        if (ok && ep_n > 3) ok = epilogue(ep3);
-        if (ok && ep_n > 4) ok = epilogue(ep4);
-        // no copy may still be writing shared memory when the CTA exits (the
-        // STATE issuer has waited for every panel unless it gave up)
-        if (leader)
-            for (int j = max(0, last_copy - kPanelSlots + 1); j <= last_copy; ++j)
-                mbar_wait(&panel_full[j % kPanelSlots], (uint32_t)(j / kPanelSlots) & 1u, a.status);
-    } else if (warp <= 12) {
+    } else {
         // ---------------- carry groups ----------------
-        const int grp = (warp - 5) >> 2;
+        // group g = warps 5 + g kGW .. 5 + g kGW + kGW - 1; a thread owns
+        // filter k of the tile (its tensor-memory lane) in stream ss
+        const int grp = (warp - 5) / kGW;
+        const int ss = ((warp - 5) % kGW) >> 2;
         const int k = (warp & 3) * 32 + lane;                 // tensor-memory lane = filter
         const uint32_t lane_base = ((uint32_t)((warp & 3) * 32)) << 16;
         const uint32_t kofs = (uint32_t)(k >> 3) * kWK + (k & 7) * 16;
@@ -1090,7 +1053,7 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             const int64_t slot = (int64_t)J.tile * kTile + k;
             const float2 ak = a.a[slot], aJ = a.aJ[slot], ck = a.c[slot], aLf = a.aLf[slot];
             const Anchor aLb = reinterpret_cast<const Anchor *>(a.aLb)[slot];
-            Anchor *vs = reinterpret_cast<Anchor *>(a.v);
+            Anchor *vp = reinterpret_cast<Anchor *>(a.v) + (int64_t)(a.stream0 + ss) * a.n_slots + slot;
             // per job: aJ^i2 for the state sums, a^(kJ j2) a c for the outputs
             float2 pj[LJ], cj[LJ];
             pj[0] = make_float2(1.f, 0.f);
@@ -1108,104 +1071,137 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                 cji[i] = make_float2(cj[2 * i].y, cj[2 * i + 1].y);
                 ncji[i] = make_float2(-cj[2 * i].y, -cj[2 * i + 1].y);
             }
-            Anchor v0 = vs[(int64_t)a.stream0 * a.n_slots + slot];
-            Anchor v1 = S > 1 ? vs[(int64_t)(a.stream0 + 1) * a.n_slots + slot] : Anchor{};
+            Anchor v = *vp;
             if (!mbar_wait_ab(&state_full[grp], n_state & 1, a.status, abort)) return false;
             ++n_state;
             tc_fence_after();
-            const int use = J.j / kWSlots;
-            if (use > 0 && !mbar_wait_ab(&w_free[wl], (use - 1) & 1, a.status, abort)) return false;
-            unsigned char *W = Wb + wl * kWBytes;
             const int b = J.b0;
             const int nb = min(a.cpb, a.n_chunks - b * a.cpb);
-            const int nsteps = S * nb;                          // (stream, chunk) steps
             // Carry across this batch. The batch's starting state v is an
             // FP64 (or double-float) anchor; chunk states inside the batch are
             // FP32 offsets from it:
             //   v_c = a^(cL) v + d_c,  d_{c+1} = a^L d_c + U_c,  d_0 = 0,
             // and the next batch starts from a^(nb L) v + d_nb in the anchor's
-            // arithmetic.
-            // per stream: a^(cL) v and d_c; the streams' chains interleave
-            // (MODE 2: vc = the chunk's starting state in FP64, v_{c+1} = a^L v_c + U_c)
-            float2 p[S], dd[S];
-            double2 vc[S];
+            // arithmetic: p = a^(cL) v, dd = d_c (MODE 2: vc = the chunk's
+            // starting state in FP64, v_{c+1} = a^L v_c + U_c).
+            float2 p = anchor_f32(v), dd = make_float2(0.f, 0.f);
+            double2 vc = CH ? reinterpret_cast<const double2 &>(v) : make_double2(0.0, 0.0);
             const double2 aL64 = CH ? reinterpret_cast<const double2 *>(a.aL)[slot] : make_double2(0.0, 0.0);
-#pragma unroll
-            for (int i = 0; i < S; ++i) {
-                p[i] = anchor_f32(i ? v1 : v0);
-                dd[i] = make_float2(0.f, 0.f);
-                if constexpr (CH) vc[i] = reinterpret_cast<const double2 &>(i ? v1 : v0);
-            }
-            // STATE columns: (chunk, stream, i2) -> (c S + s) LJ + i2, read 32
-            // at a time (32 / LJ steps); step q = c S + s. Step q writes W columns 2 q LJ ..
-            // 2 q LJ + 2 LJ - 1: 4 LJ contiguous bytes at (k/8) kWK + q LJ / 4 * 128
-            // + (2 q LJ % 8) * 2 + (k%8) 16.
+            // Chunk c of this stream is STATE columns (c S + ss) LJ + i2 (re;
+            // im kNii further on) and W columns 2 (c S + ss) LJ .. + 2 LJ - 1:
+            // 4 LJ contiguous bytes at (k/8) kWK + n / 8 * 128 + (n % 8) * 2 +
+            // (k%8) 16, n = 2 (c S + ss) LJ.
             const uint32_t tb = tmem + lane_base + 128 * grp;
-            constexpr int kSteps = 16 / LJ;
+            constexpr int kMaxC = kNii / (S * LJ);
+            // Two streams: first every chunk's U = sum_i2 aJ^i2 G(i2), then the
+            // group's STATE columns are released and W is made, so that the
+            // group's next STATE contraction runs meanwhile. One stream: U and
+            // W chunk by chunk (its sixteen U would not fit the registers) and
+            // the columns are released at the last read.
+            constexpr bool kUFirst = S == 2;
+            constexpr int kR = (kUFirst ? 8 : 32) / LJ;    // chunks per tensor-memory round trip
+            auto load_round = [&](int pp, uint32_t(&rr)[kR * LJ], uint32_t(&ri)[kR * LJ]) {
+                if constexpr (S == 1) {          // the round's columns are contiguous
 #pragma unroll
-            for (int pp = 0; pp < kNii / 32; ++pp) {          // 32 columns per round trip
-                uint32_t rr[2][16], ri[2][16];
-                tmem_ld16_nw(tb + 32 * pp, rr[0]);
-                tmem_ld16_nw(tb + 32 * pp + 16, rr[1]);
-                tmem_ld16_nw(tb + kNii + 32 * pp, ri[0]);
-                tmem_ld16_nw(tb + kNii + 32 * pp + 16, ri[1]);
-                tmem_wait_ld();
-                if (pp == kNii / 32 - 1) {
-                    tc_fence_before();
-                    mbar_arrive(&state_free[grp]);
-                }
-#pragma unroll
-                for (int qq = 0; qq < 2 * kSteps; ++qq) {
-                    const int q = pp * 2 * kSteps + qq;
-                    const int n = 2 * q * LJ;
-                    const uint32_t off = kofs + (uint32_t)(n >> 3) * 128 + (n & 7) * 2;
-                    float wr[LJ], wi[LJ];
-                    if (q < nsteps) {
-                        const int ss = q % S;   // resolved at compile time (unrolled)
-                        // U = sum_i2 aJ^i2 G(i2)
-                        const int c0 = qq * LJ;
-                        float ur = __uint_as_float(rr[c0 >> 4][c0 & 15]);
-                        float ui = __uint_as_float(ri[c0 >> 4][c0 & 15]);
-#pragma unroll
-                        for (int i2 = 1; i2 < LJ; ++i2) {
-                            const int c = c0 + i2;
-                            const float gr = __uint_as_float(rr[c >> 4][c & 15]);
-                            const float gi = __uint_as_float(ri[c >> 4][c & 15]);
-                            ur = fmaf(pj[i2].x, gr, fmaf(-pj[i2].y, gi, ur));
-                            ui = fmaf(pj[i2].x, gi, fmaf(pj[i2].y, gr, ui));
-                        }
-                        const float2 vv = CH ? make_float2((float)vc[ss].x, (float)vc[ss].y)
-                                             : make_float2(p[ss].x + dd[ss].x, p[ss].y + dd[ss].y);
-                        const float2 vx = make_float2(vv.x, vv.x), vy = make_float2(vv.y, vv.y);
-#pragma unroll
-                        for (int i = 0; i < LJ / 2; ++i) {      // w = a^(kJ j2) a c vv
-                            const float2 r = __ffma2_rn(ncji[i], vy, __fmul2_rn(cjr[i], vx));
-                            const float2 m = __ffma2_rn(cji[i], vx, __fmul2_rn(cjr[i], vy));
-                            wr[2 * i] = r.x;
-                            wr[2 * i + 1] = r.y;
-                            wi[2 * i] = m.x;
-                            wi[2 * i + 1] = m.y;
-                        }
-                        if constexpr (CH) {
-                            vc[ss] = make_double2(fma(aL64.x, vc[ss].x, fma(-aL64.y, vc[ss].y, (double)ur)),
-                                                  fma(aL64.x, vc[ss].y, fma(aL64.y, vc[ss].x, (double)ui)));
-                        } else {
-                            dd[ss] = make_float2(fmaf(aLf.x, dd[ss].x, fmaf(-aLf.y, dd[ss].y, ur)),
-                                                 fmaf(aLf.x, dd[ss].y, fmaf(aLf.y, dd[ss].x, ui)));
-                            p[ss] = cmul(aLf, p[ss]);
-                        }
-                    } else {
-                        // columns past this batch contribute nothing
-#pragma unroll
-                        for (int j2 = 0; j2 < LJ; ++j2) wr[j2] = wi[j2] = 0.f;
+                    for (int i = 0; i < kR * LJ / 16; ++i) {
+                        const uint32_t col = (uint32_t)(pp * kR * LJ + 16 * i);
+                        tmem_ld16_nw(tb + col, reinterpret_cast<uint32_t(&)[16]>(rr[16 * i]));
+                        tmem_ld16_nw(tb + kNii + col, reinterpret_cast<uint32_t(&)[16]>(ri[16 * i]));
                     }
-                    if constexpr (LJ == 4) {
-                        *reinterpret_cast<uint4 *>(W + off) =
-                            make_uint4(pack2<BF16>(wr[0], wi[0]), pack2<BF16>(wr[1], wi[1]),
-                                       pack2<BF16>(wr[2], wi[2]), pack2<BF16>(wr[3], wi[3]));
+                } else {
+#pragma unroll
+                    for (int i = 0; i < kR; ++i) {
+                        const uint32_t col = (uint32_t)(((pp * kR + i) * S + ss) * LJ);
+                        tmem_ld_n(tb + col, reinterpret_cast<uint32_t(&)[LJ]>(rr[LJ * i]));
+                        tmem_ld_n(tb + kNii + col, reinterpret_cast<uint32_t(&)[LJ]>(ri[LJ * i]));
+                    }
+                }
+                tmem_wait_ld();
+            };
+            // U of the round's chunk i
+            auto u_of = [&](const uint32_t(&rr)[kR * LJ], const uint32_t(&ri)[kR * LJ], int i) {
+                float ur = __uint_as_float(rr[LJ * i]);
+                float ui = __uint_as_float(ri[LJ * i]);
+#pragma unroll
+                for (int i2 = 1; i2 < LJ; ++i2) {
+                    const float gr = __uint_as_float(rr[LJ * i + i2]);
+                    const float gi = __uint_as_float(ri[LJ * i + i2]);
+                    ur = fmaf(pj[i2].x, gr, fmaf(-pj[i2].y, gi, ur));
+                    ui = fmaf(pj[i2].x, gi, fmaf(pj[i2].y, gr, ui));
+                }
+                return make_float2(ur, ui);
+            };
+            // W of chunk c, then the carry to chunk c + 1
+            auto w_step = [&](unsigned char *W, int c, float2 Uc) {
+                const int n = 2 * (c * S + ss) * LJ;
+                const uint32_t off = kofs + (uint32_t)(n >> 3) * 128 + (n & 7) * 2;
+                float wr[LJ], wi[LJ];
+                if (c < nb) {
+                    const float2 vv = CH ? make_float2((float)vc.x, (float)vc.y)
+                                         : make_float2(p.x + dd.x, p.y + dd.y);
+                    const float2 vx = make_float2(vv.x, vv.x), vy = make_float2(vv.y, vv.y);
+#pragma unroll
+                    for (int i3 = 0; i3 < LJ / 2; ++i3) {      // w = a^(kJ j2) a c vv
+                        const float2 r = __ffma2_rn(ncji[i3], vy, __fmul2_rn(cjr[i3], vx));
+                        const float2 m = __ffma2_rn(cji[i3], vx, __fmul2_rn(cjr[i3], vy));
+                        wr[2 * i3] = r.x;
+                        wr[2 * i3 + 1] = r.y;
+                        wi[2 * i3] = m.x;
+                        wi[2 * i3 + 1] = m.y;
+                    }
+                    if constexpr (CH) {
+                        vc = make_double2(fma(aL64.x, vc.x, fma(-aL64.y, vc.y, (double)Uc.x)),
+                                          fma(aL64.x, vc.y, fma(aL64.y, vc.x, (double)Uc.y)));
                     } else {
-                        *reinterpret_cast<uint2 *>(W + off) =
-                            make_uint2(pack2<BF16>(wr[0], wi[0]), pack2<BF16>(wr[1], wi[1]));
+                        dd = make_float2(fmaf(aLf.x, dd.x, fmaf(-aLf.y, dd.y, Uc.x)),
+                                         fmaf(aLf.x, dd.y, fmaf(aLf.y, dd.x, Uc.y)));
+                        p = cmul(aLf, p);
+                    }
+                } else {
+                    // columns past this batch contribute nothing
+#pragma unroll
+                    for (int j2 = 0; j2 < LJ; ++j2) wr[j2] = wi[j2] = 0.f;
+                }
+                if constexpr (LJ == 4) {
+                    *reinterpret_cast<uint4 *>(W + off) =
+                        make_uint4(pack2<BF16>(wr[0], wi[0]), pack2<BF16>(wr[1], wi[1]),
+                                   pack2<BF16>(wr[2], wi[2]), pack2<BF16>(wr[3], wi[3]));
+                } else {
+                    *reinterpret_cast<uint2 *>(W + off) =
+                        make_uint2(pack2<BF16>(wr[0], wi[0]), pack2<BF16>(wr[1], wi[1]));
+                }
+            };
+            // W's slot is free once the OUTPUT two jobs back has finished
+            const int use = J.j / kWSlots;
+            unsigned char *W = Wb + wl * kWBytes;
+            if constexpr (kUFirst) {
+                float2 U[kMaxC];
+#pragma unroll
+                for (int pp = 0; pp < kMaxC / kR; ++pp) {
+                    uint32_t rr[kR * LJ], ri[kR * LJ];
+                    load_round(pp, rr, ri);
+#pragma unroll
+                    for (int i = 0; i < kR; ++i) U[pp * kR + i] = u_of(rr, ri, i);
+                }
+                tc_fence_before();
+                mbar_arrive(&state_free[grp]);
+                if (use > 0 && !mbar_wait_ab(&w_free[wl], (use - 1) & 1, a.status, abort)) return false;
+#pragma unroll
+                for (int c = 0; c < kMaxC; ++c) w_step(W, c, U[c]);
+            } else {
+                if (use > 0 && !mbar_wait_ab(&w_free[wl], (use - 1) & 1, a.status, abort)) return false;
+#pragma unroll
+                for (int pp = 0; pp < kMaxC / kR; ++pp) {
+                    uint32_t rr[kR * LJ], ri[kR * LJ];
+                    load_round(pp, rr, ri);
+                    if (pp == kMaxC / kR - 1) {
+                        tc_fence_before();
+                        mbar_arrive(&state_free[grp]);
+                    }
+#pragma unroll
+                    for (int i = 0; i < kR; ++i) {
+                        const int c = pp * kR + i;
+                        w_step(W, c, c < nb ? u_of(rr, ri, i) : make_float2(0.f, 0.f));
                     }
                 }
             }
@@ -1214,12 +1210,10 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
             fence_async_smem();
             mbar_arrive(&w_full[wl]);
             if constexpr (CH) {
-                vs[(int64_t)a.stream0 * a.n_slots + slot] = reinterpret_cast<const Anchor &>(vc[0]);
-                if constexpr (S > 1)
-                    vs[(int64_t)(a.stream0 + 1) * a.n_slots + slot] = reinterpret_cast<const Anchor &>(vc[1]);
+                *vp = reinterpret_cast<const Anchor &>(vc);
                 return true;
             }
-            // v <- a^(nb L) v + d_nb in the anchor's arithmetic, per stream
+            // v <- a^(nb L) v + d_nb in the anchor's arithmetic
             Anchor pw;
             if (nb == a.cpb) {
                 pw = aLb;
@@ -1228,12 +1222,7 @@ __global__ void __launch_bounds__(kCarryWarps * 32, 1) tc_carry_kernel(const TcC
                 pw = aL;
                 for (int i = 1; i < nb; ++i) pw = anchor_madd(pw, aL, make_float2(0.f, 0.f));
             }
-            v0 = anchor_madd(pw, v0, dd[0]);
-            vs[(int64_t)a.stream0 * a.n_slots + slot] = v0;
-            if constexpr (S > 1) {
-                v1 = anchor_madd(pw, v1, dd[1]);
-                vs[(int64_t)(a.stream0 + 1) * a.n_slots + slot] = v1;
-            }
+            *vp = anchor_madd(pw, v, dd);
             return true;
         });
     }
@@ -1633,7 +1622,7 @@ spiir_status spiir_tc_launch(const TcLaunch &l, cudaStream_t s, KernelTimer *tim
         const int grid = std::min(l.n_carry, l.n_sms);
         if (timer) timer->begin(SPIIR_K_TC_CARRY, s);
         const bool l2 = l.L == 2 * kJ, two = count == 2;
-        carry_kernel(12 * l.bf16 + 6 * l2 + 3 * two + l.carry_mode)<<<grid, kCarryWarps * 32, kCarrySmem, s>>>(ca);
+        carry_kernel(12 * l.bf16 + 6 * l2 + 3 * two + l.carry_mode)<<<grid, carry_warps(count) * 32, kCarrySmem, s>>>(ca);
         TC_CUDA(cudaGetLastError());
         if (timer) timer->end(s);
     }

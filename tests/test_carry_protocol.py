@@ -1,13 +1,16 @@
 """Discrete-event model of the carry kernel's mbarrier protocol (the
 block-parallel tensor-core form): four power-panel slots, two OUTPUT-operand
-(W) slots, two carry groups, separate STATE and OUTPUT issuers, panel copies
-by the panel role, epilogues forced five jobs back or taken while the next
-panel's slot is busy. The roles and their waits restate the kernel's; MMAs
-and copies complete at issue (once issued they wait on nothing), so every
-interleaving the random scheduler picks is a possible execution order. The
-model checks: no deadlock, no phase aliasing (a wait never sees its barrier
-two phases ahead), the strain-buffer refill margin (panel j ready implies
-OUTPUT j - 4 finished), and that each tile's batches are carried in order."""
+(W) slots, two carry groups, separate STATE and OUTPUT issuers, a panel
+copier, and an epilogue role that drains each (template, batch) in order.
+A carry group either releases its STATE columns after its last read, while
+it makes W (one stream), or reads every chunk's sum first and releases them
+before it waits for its W slot (two streams); both orders are checked. The
+roles and their waits restate the kernel's; MMAs and copies complete at
+issue (once issued they wait on nothing), so every interleaving the random
+scheduler picks is a possible execution order. The model checks: no
+deadlock, no phase aliasing (a wait never sees its barrier two phases
+ahead), the strain-buffer refill margin (panel j ready implies OUTPUT j - 4
+finished), and that each tile's batches are carried in order."""
 import random
 
 
@@ -42,7 +45,10 @@ def jobs(n_carry, grid, bid, tile_ptr, n_batches):
     return out
 
 
-def run(JOBS, seed):
+def run(JOBS, seed, u_first=False, drop=None):
+    """drop: a wait left out ('sfree' STATE issuer, 'ofree' OUTPUT issuer,
+    'wfull' OUTPUT issuer, 'pfree' copier, 'ofull' epilogue, 'wfree' and
+    'sfull' carry), to show that the model catches it."""
     B = {}
 
     def bar(n, c):
@@ -71,7 +77,9 @@ def run(JOBS, seed):
         for J in JOBS:
             g, s = J['g'], J['s']
             if used[g]:
-                yield W(f'sfree{g}', n_sf[g]); n_sf[g] += 1
+                if drop != 'sfree':
+                    yield W(f'sfree{g}', n_sf[g])
+                n_sf[g] += 1
             used[g] = True
             yield W(f'pfull{s}', J['j'] // KP)
             # panel J ready => OUTPUT(J - KP) complete (its slot was freed)
@@ -83,38 +91,32 @@ def run(JOBS, seed):
         for J in JOBS:
             ob, w, s = J['e'] & 1, J['w'], J['s']
             if J['first'] and J['e'] >= 2:
-                yield W(f'ofree{ob}', n_of[ob]); n_of[ob] += 1
-            yield W(f'wfull{w}', J['j'] // KW)
+                if drop != 'ofree':
+                    yield W(f'ofree{ob}', n_of[ob])
+                n_of[ob] += 1
+            if drop != 'wfull':
+                yield W(f'wfull{w}', J['j'] // KW)
             B[f'wfree{w}'].arrive(); B[f'pfree{s}'].arrive()
             if J['last']:
                 B[f'ofull{ob}'].arrive()
             out_done.add(J['j'])
 
-    def panel():
-        ep = []
-
-        def epilogue(E):
-            ob = E['e'] & 1
-            yield W(f'ofull{ob}', E['e'] >> 1)
-            B[f'ofree{ob}'].arrive(128)
+    def copier():
         for J in JOBS:
             s = J['s']
-            while ep and ep[0]['j'] <= J['j'] - 5:
-                yield from epilogue(ep.pop(0))
-            if J['last']:
-                ep.append(J)
-            assert len(ep) <= 5, len(ep)
             use = J['j'] // KP
-            if use > 0:
-                while not ready(f'pfree{s}', use - 1):
-                    e0 = ep[0] if ep else None
-                    if e0 is not None and e0['j'] < J['j'] and ready(f'ofull{e0["e"] & 1}', e0['e'] >> 1):
-                        yield from epilogue(ep.pop(0))
-                        continue
-                    yield ('poll',)
+            if use > 0 and drop != 'pfree':
+                yield W(f'pfree{s}', use - 1)
             B[f'pfull{s}'].arrive()
-        for E in ep:
-            yield from epilogue(E)
+
+    def epilogue():
+        for J in JOBS:
+            if not J['last']:
+                continue
+            ob = J['e'] & 1
+            if drop != 'ofull':
+                yield W(f'ofull{ob}', J['e'] >> 1)
+            B[f'ofree{ob}'].arrive(128)
 
     def carry(grp):
         n_state = 0
@@ -122,15 +124,20 @@ def run(JOBS, seed):
             if J['g'] != grp:
                 continue
             w = J['w']
-            yield W(f'sfull{grp}', n_state); n_state += 1
+            if drop != 'sfull':
+                yield W(f'sfull{grp}', n_state)
+            n_state += 1
             use = J['j'] // KW
-            if use > 0:
+            if u_first:
+                B[f'sfree{grp}'].arrive(128)
+            if use > 0 and drop != 'wfree':
                 yield W(f'wfree{w}', use - 1)
-            B[f'sfree{grp}'].arrive(128)
+            if not u_first:
+                B[f'sfree{grp}'].arrive(128)
             vlog.setdefault((J['t'], J['tile']), []).append(J['b0'])
             B[f'wfull{w}'].arrive(128)
 
-    roles = [state_issuer(), output_issuer(), panel(), carry(0), carry(1)]
+    roles = [state_issuer(), output_issuer(), copier(), epilogue(), carry(0), carry(1)]
     n = len(roles)
     st = [None] * n; done = [False] * n
     rng = random.Random(seed)
@@ -183,6 +190,32 @@ def test_carry_protocol_all_job_shapes():
                     for bid in range(min(grid, n_carry)):
                         J = jobs(n_carry, grid, bid, tp, nb)
                         for seed in range(6):
-                            run(J, seed)
+                            run(J, seed, u_first=bool(seed & 1))
                             cnt += 1
     assert cnt > 9000
+
+
+def test_carry_protocol_catches_each_missing_wait():
+    """The model is not vacuous: leaving out any one wait of any role breaks
+    one of its checks for some job shape and interleaving."""
+    shapes = []
+    for pat in [[1], [2], [3], [1, 2], [5, 1, 1, 4]]:
+        for n_carry in [3, 7]:
+            for nb in [1, 2, 5]:
+                tp = [0]
+                for i in range(n_carry):
+                    tp.append(tp[-1] + pat[i % len(pat)])
+                shapes.append(jobs(n_carry, 1, 0, tp, nb))
+    for drop in ['sfree', 'ofree', 'wfull', 'pfree', 'ofull', 'sfull', 'wfree']:
+        for u_first in (False, True):
+            caught = False
+            for J in shapes:
+                for seed in range(8):
+                    try:
+                        run(J, seed, u_first=u_first, drop=drop)
+                    except AssertionError:
+                        caught = True
+                        break
+                if caught:
+                    break
+            assert caught, (drop, u_first)
