@@ -89,13 +89,18 @@ __device__ __forceinline__ void mbar_init(uint64_t *m, uint32_t c) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s32(m)), "r"(c) : "memory");
 }
 
+// Test of an mbarrier phase that may suspend the thread until the phase
+// completes, for at most kSuspendNs (the hint): a waiting warp then takes no
+// issue slots from the warps doing the work, and the bounded waits below
+// still look at the clock and the abort flag between tries.
+constexpr uint32_t kSuspendNs = 100000;
 __device__ __forceinline__ bool mbar_try(uint64_t *m, uint32_t ph) {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
-        : "r"(s32(m)), "r"(ph)
+        : "r"(s32(m)), "r"(ph), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
