@@ -735,7 +735,7 @@ spiir_status launch_sequence(spiir_bank *b, int s0, int count, const float *x, i
     KernelTimer &tm = *b->timer;
     tm.begin(SPIIR_K_PROLOGUE, st);
     CUDA_TRY(spiir_launch_prologue(pa, count, st));
-    tm.end(st);
+    tm.end(st, kPrologueLaunches);
     if (p.n_levels > 1) {
         DecimArgs da{};
         da.xbuf = b->xbuf;

@@ -193,6 +193,8 @@ struct KernelTimer {
 };
 
 // Kernel launchers (spiir_plain.cu).
+// Kernels spiir_launch_prologue launches (history move, then the new samples).
+constexpr int kPrologueLaunches = 2;
 cudaError_t spiir_launch_prologue(const PrologueArgs &a, int n_streams, cudaStream_t s);
 cudaError_t spiir_launch_decimate(const DecimArgs &a, int n_streams, cudaStream_t s);
 cudaError_t spiir_launch_recur(const RecurArgs &a, int variant, int n_ctas,

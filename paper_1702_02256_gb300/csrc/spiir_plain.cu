@@ -122,6 +122,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *m, uint32_t parity,
 // Prologue: strain history + new base-rate samples
 // ---------------------------------------------------------------------------
 
+// One CTA per (level, stream) moves the level's history; the new base-rate
+// samples, whose places overlap the history's sources, are copied by the
+// next kernel with a grid wide enough for the push.
 __global__ void prologue_kernel(const PrologueArgs a) {
     const int lev = blockIdx.x;
     const int s = a.stream0 + blockIdx.y;
@@ -143,10 +146,14 @@ __global__ void prologue_kernel(const PrologueArgs a) {
             __syncthreads();
         }
     }
-    if (lev == 0) {
-        const float *src = a.x_in + (int64_t)blockIdx.y * a.x_in_stream_stride;
-        for (int k = threadIdx.x; k < L.n; k += blockDim.x) buf[hist + k] = src[k];
-    }
+}
+
+// The push's base-rate samples behind level 0's history, every stream.
+__global__ void prologue_copy_kernel(const PrologueArgs a) {
+    const LevelArgs L = a.lev[0];
+    float *buf = a.xbuf + (int64_t)(a.stream0 + blockIdx.y) * a.xbuf_stream_stride + L.xbuf_off + L.hist;
+    const float *src = a.x_in + (int64_t)blockIdx.y * a.x_in_stream_stride;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < L.n; k += gridDim.x * blockDim.x) buf[k] = src[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -858,7 +865,12 @@ cudaError_t spiir_recur_prepare(int v, int smem_bytes, int *ctas_per_sm) {
 int spiir_recur_red_bytes() { return kRedBytes + kScratchBytes; }
 
 cudaError_t spiir_launch_prologue(const PrologueArgs &a, int n_streams, cudaStream_t s) {
-    prologue_kernel<<<dim3(a.n_levels, n_streams), 256, 0, s>>>(a);
+    prologue_kernel<<<dim3(a.n_levels, n_streams), 512, 0, s>>>(a);
+    const int n = a.lev[0].n;
+    if (n > 0) {
+        const unsigned gx = (unsigned)std::min(1024, std::max(1, (n + 1023) / 1024));
+        prologue_copy_kernel<<<dim3(gx, n_streams), 256, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

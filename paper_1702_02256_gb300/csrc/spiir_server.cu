@@ -714,8 +714,8 @@ spiir_status launch_push(spiir_server *sv, int64_t n_prev, cudaStream_t st) {
     KernelTimer *tm = (sv->timer && sv->timer->on) ? sv->timer : nullptr;
     if (tm) tm->begin(SPIIR_K_PROLOGUE, st);
     CUDA_TRY(spiir_launch_prologue(pa, S, st));
-    if (tm) tm->end(st);
-    ++launches;
+    if (tm) tm->end(st, kPrologueLaunches);
+    launches += kPrologueLaunches;
     if (sv->L > 1) {
         DecimArgs da{};
         da.xbuf = sv->xbuf;

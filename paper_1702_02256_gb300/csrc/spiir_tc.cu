@@ -1798,7 +1798,7 @@ spiir_status spiir_tc_push(TcBank *b, int s0, int count, const float *x, int64_t
     pa.lev[0].xbuf_off = 0;
     timer->begin(SPIIR_K_TC_STAGE, s);
     TC_CUDA(spiir_launch_prologue(pa, count, s));
-    timer->end(s);
+    timer->end(s, kPrologueLaunches);
 
     TcLaunch l{};
     l.xbuf = b->xbuf;

@@ -204,6 +204,7 @@ def test_kernel_timing_counts_launches(torch_cuda):
         b.push(xd)
     kt = b.kernel_times()
     assert kt["recur"][1] == 3 and kt["combine"][1] == 3 and kt["decimate"][1] == 3
+    assert kt["prologue"][1] == 2 * 3        # history move + new-sample copy
     assert all(ms >= 0 for ms, _ in kt.values())
     b.close()
 
