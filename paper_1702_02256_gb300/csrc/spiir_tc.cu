@@ -131,6 +131,11 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
         : "memory");
 }
 
+// Bring [src, src + bytes) into L2 (16-byte aligned, a multiple of 16 bytes).
+__device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void fence_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -984,6 +989,17 @@ __global__ void __launch_bounds__(carry_warps(S) * 32, 1) tc_carry_kernel(const 
                 bulk_load(smem + sl * kPanelBytes, a.panel + (size_t)J.tile * (kPanelBytes / 16), kPanelBytes,
                           &panel_full[sl]);
                 last_copy = J.j;
+                if (J.b0 == 0) {
+                    // the tile's coefficients and states, which its carry
+                    // group reads when it starts the job, into L2 ahead of it
+                    const int64_t s0 = (int64_t)J.tile * kTile;
+                    prefetch_l2(a.a + s0, kTile * 8);
+                    prefetch_l2(a.aJ + s0, kTile * 8);
+                    prefetch_l2(a.c + s0, kTile * 8);
+                    prefetch_l2(a.aLf + s0, kTile * 8);
+                    prefetch_l2(a.aLb + s0, kTile * 16);
+                    for (int q = 0; q < S; ++q) prefetch_l2(a.v + (int64_t)(a.stream0 + q) * a.n_slots + s0, kTile * 16);
+                }
             }
             // no copy may still be writing shared memory when the CTA exits
             for (int j = max(0, last_copy - kPanelSlots + 1); j <= last_copy; ++j)
