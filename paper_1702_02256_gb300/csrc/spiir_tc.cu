@@ -1120,7 +1120,7 @@ __global__ void __launch_bounds__(carry_warps(S) * 32, 1) tc_carry_kernel(const 
             // W chunk by chunk (its sixteen U would not fit the registers) and
             // the columns are released at the last read.
             constexpr bool kUFirst = S == 2;
-            constexpr int kR = (kUFirst ? 8 : 32) / LJ;    // chunks per tensor-memory round trip
+            constexpr int kR = (kUFirst ? 16 : 32) / LJ;    // chunks per tensor-memory round trip
             auto load_round = [&](int pp, uint32_t(&rr)[kR * LJ], uint32_t(&ri)[kR * LJ]) {
                 if constexpr (S == 1) {          // the round's columns are contiguous
 #pragma unroll
