@@ -474,8 +474,6 @@ __global__ void __launch_bounds__(kFirThreads, 1) tc_fir_kernel(const TcFirArgs 
             const int ss = sg % a.n_streams;
             const int g = a.groups ? a.groups[sg / a.n_streams] : sg / a.n_streams;
             const int ab = li & 1;
-            ok = ok && mbar_wait(&acc_full[ab], (li >> 1) & 1, a.status);
-            tc_fence_after();
             const int t = g * kGroup + (r >> 1);
             const float sc = (t < a.n_templates) ? a.row_scale[t] : 0.f;
             float2 *zrow = a.z + (int64_t)(a.stream0 + ss) * a.z_stream_stride +
@@ -486,25 +484,30 @@ __global__ void __launch_bounds__(kFirThreads, 1) tc_fir_kernel(const TcFirArgs 
             // A lane writes the 8 samples of its 8 columns of a 16-column step:
             // column c is sample L - 1 - c, so they are the contiguous samples
             // from L - 8 - (16 cc + i0), moved as four 16-byte vectors. The
-            // state term (written by the carry kernel) is fetched two steps
-            // ahead so its global latency overlaps two steps.
+            // state term (written by the carry kernel) of the warp's next kD
+            // steps is in flight at any time, the first ones fetched before
+            // the accumulator is ready, so the global latency overlaps the
+            // contraction and the earlier steps.
             const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
             auto zv = [&](int cc) {
                 return reinterpret_cast<float4 *>(zrow + (L - 8 - (cc * 16 + i0)));
             };
-            float4 pf0[4], pf1[4];
+            constexpr int kD = 3;
+            float4 pf[kD][4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                pf0[i] = add ? zv(half)[i] : zero4;
-                pf1[i] = (add && half + 2 < L / 16) ? zv(half + 2)[i] : zero4;
-            }
+            for (int d = 0; d < kD; ++d)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) pf[d][i] = (add && half + 2 * d < L / 16) ? zv(half + 2 * d)[i] : zero4;
+            ok = ok && mbar_wait(&acc_full[ab], (li >> 1) & 1, a.status);
+            tc_fence_after();
             for (int cc = half; cc < L / 16; cc += 2) {
                 float4 prev[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    prev[i] = pf0[i];
-                    pf0[i] = pf1[i];
-                    pf1[i] = (add && cc + 4 < L / 16) ? zv(cc + 4)[i] : zero4;
+                    prev[i] = pf[0][i];
+#pragma unroll
+                    for (int d = 0; d + 1 < kD; ++d) pf[d][i] = pf[d + 1][i];
+                    pf[kD - 1][i] = (add && cc + 2 * kD < L / 16) ? zv(cc + 2 * kD)[i] : zero4;
                 }
                 float v[16];
                 tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + ab * 256 + cc * 16, v);
