@@ -325,8 +325,8 @@ __global__ void tc_stage_kernel(const TcStageArgs a) {
                 a.hank_lo[i] = pack8<BF16>(lo);
             }
         } else {
-            // STATE segments of batch b: row n = (c, s, i2) (streams of a
-            // chunk adjacent), K = i1:
+            // STATE segments of batch b: row n = (s, i2, c) (the chunks of a
+            // stream and power block adjacent), K = i1:
             // x_s[e_c - kJ i2 - i1], e_c = c L - F + L - 1; layout
             // [n/8][i1/8][n%8][i1%8]
             const int64_t j = i - hank_chunks;
@@ -334,9 +334,8 @@ __global__ void tc_stage_kernel(const TcStageArgs a) {
             constexpr int kKB = kJ / 8;
             const int n = (w / (8 * kKB)) * 8 + (w % 8), kb = (w / 8) % kKB;
             const int nb = min(a.cpb, a.n_chunks - b * a.cpb);
-            const int nii = a.n_streams * nb * LJ;
-            if (n < nii) {
-                const int q = n / LJ, i2 = n % LJ, cc = q / a.n_streams, ss = q % a.n_streams;
+            const int cc = n % a.cpb, i2 = (n / a.cpb) % LJ, ss = n / a.cpb / LJ;
+            if (ss < a.n_streams && cc < nb) {
                 const float *x = a.xbuf + (int64_t)(a.stream0 + ss) * a.xbuf_stride + a.hist;
                 const int e = (b * a.cpb + cc) * a.L - a.F + a.L - 1 - kJ * i2;
 #pragma unroll
@@ -612,18 +611,6 @@ __device__ __forceinline__ bool mbar_wait_ab(uint64_t *m, uint32_t ph, unsigned 
     return true;
 }
 
-// 32 lanes x 16 columns, without waiting (tmem_wait_ld completes the loads).
-__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%"
-        "15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr)
-        : "memory");
-}
-
 // 16 lanes x 256 bits, 16 times along the columns: thread t gets rows
 // t / 4 and t / 4 + 8, columns 2 (t % 4) and 2 (t % 4) + 1 of each 8.
 __device__ __forceinline__ void tmem_ld16x256_x16(uint32_t taddr, uint32_t (&r)[64]) {
@@ -657,16 +644,17 @@ __device__ __forceinline__ void tmem_ld16x256_x8(uint32_t taddr, uint32_t (&r)[3
         : "memory");
 }
 
-// 32 lanes x N consecutive columns (N = 2 or 4), without waiting.
-__device__ __forceinline__ void tmem_ld_n(uint32_t taddr, uint32_t (&r)[4]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+// 32 lanes x N consecutive columns (N = 4 or 8), without waiting.
+__device__ __forceinline__ void tmem_ld_n(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7])
                  : "r"(taddr)
                  : "memory");
 }
-__device__ __forceinline__ void tmem_ld_n(uint32_t taddr, uint32_t (&r)[2]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];"
-                 : "=r"(r[0]), "=r"(r[1])
+__device__ __forceinline__ void tmem_ld_n(uint32_t taddr, uint32_t (&r)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                  : "r"(taddr)
                  : "memory");
 }
@@ -1111,10 +1099,12 @@ __global__ void __launch_bounds__(carry_warps(S) * 32, 1) tc_carry_kernel(const 
             float2 p = anchor_f32(v), dd = make_float2(0.f, 0.f);
             double2 vc = CH ? reinterpret_cast<const double2 &>(v) : make_double2(0.0, 0.0);
             const double2 aL64 = CH ? reinterpret_cast<const double2 *>(a.aL)[slot] : make_double2(0.0, 0.0);
-            // Chunk c of this stream is STATE columns (c S + ss) LJ + i2 (re;
-            // im kNii further on) and W columns 2 (c S + ss) LJ .. + 2 LJ - 1:
-            // 4 LJ contiguous bytes at (k/8) kWK + n / 8 * 128 + (n % 8) * 2 +
-            // (k%8) 16, n = 2 (c S + ss) LJ.
+            // Chunk c's sums G(i2) for this stream are STATE columns
+            // (ss LJ + i2) kMaxC + c (re; im kNii further on): the chunks of a
+            // power block are adjacent, so the sums of two chunks form one
+            // packed f32x2 operand. Its W goes to columns 2 (c S + ss) LJ ..
+            // + 2 LJ - 1: 4 LJ contiguous bytes at (k/8) kWK + n / 8 * 128 +
+            // (n % 8) * 2 + (k%8) 16, n = 2 (c S + ss) LJ.
             const uint32_t tb = tmem + lane_base + 128 * grp;
             constexpr int kMaxC = kNii / (S * LJ);
             // Two streams: first every chunk's U = sum_i2 aJ^i2 G(i2), then the
@@ -1123,37 +1113,35 @@ __global__ void __launch_bounds__(carry_warps(S) * 32, 1) tc_carry_kernel(const 
             // W chunk by chunk (its sixteen U would not fit the registers) and
             // the columns are released at the last read.
             constexpr bool kUFirst = S == 2;
-            constexpr int kR = (kUFirst ? 16 : 32) / LJ;    // chunks per tensor-memory round trip
-            auto load_round = [&](int pp, uint32_t(&rr)[kR * LJ], uint32_t(&ri)[kR * LJ]) {
-                if constexpr (S == 1) {          // the round's columns are contiguous
+            constexpr int kR = 16 / LJ;                     // chunks per tensor-memory round trip
+            // a round: every power block's sums of chunks pp kR .. pp kR + kR - 1
+            auto load_round = [&](int pp, uint32_t(&rr)[LJ][kR], uint32_t(&ri)[LJ][kR]) {
 #pragma unroll
-                    for (int i = 0; i < kR * LJ / 16; ++i) {
-                        const uint32_t col = (uint32_t)(pp * kR * LJ + 16 * i);
-                        tmem_ld16_nw(tb + col, reinterpret_cast<uint32_t(&)[16]>(rr[16 * i]));
-                        tmem_ld16_nw(tb + kNii + col, reinterpret_cast<uint32_t(&)[16]>(ri[16 * i]));
-                    }
-                } else {
-#pragma unroll
-                    for (int i = 0; i < kR; ++i) {
-                        const uint32_t col = (uint32_t)(((pp * kR + i) * S + ss) * LJ);
-                        tmem_ld_n(tb + col, reinterpret_cast<uint32_t(&)[LJ]>(rr[LJ * i]));
-                        tmem_ld_n(tb + kNii + col, reinterpret_cast<uint32_t(&)[LJ]>(ri[LJ * i]));
-                    }
+                for (int i2 = 0; i2 < LJ; ++i2) {
+                    const uint32_t col = (uint32_t)((ss * LJ + i2) * kMaxC + pp * kR);
+                    tmem_ld_n(tb + col, rr[i2]);
+                    tmem_ld_n(tb + kNii + col, ri[i2]);
                 }
                 tmem_wait_ld();
             };
-            // U of the round's chunk i
-            auto u_of = [&](const uint32_t(&rr)[kR * LJ], const uint32_t(&ri)[kR * LJ], int i) {
-                float ur = __uint_as_float(rr[LJ * i]);
-                float ui = __uint_as_float(ri[LJ * i]);
+            // U of the round's chunks i, i + 1 (i even), two chunks per packed
+            // operation; each element takes the scalar order
+            // u = fma(Re aJ^i2, g, fma(-+Im aJ^i2, g', u)) over i2 = 1 ..
+            auto u_pair = [&](const uint32_t(&rr)[LJ][kR], const uint32_t(&ri)[LJ][kR], int i, float2 &u0,
+                              float2 &u1) {
+                float2 ur = make_float2(__uint_as_float(rr[0][i]), __uint_as_float(rr[0][i + 1]));
+                float2 ui = make_float2(__uint_as_float(ri[0][i]), __uint_as_float(ri[0][i + 1]));
 #pragma unroll
                 for (int i2 = 1; i2 < LJ; ++i2) {
-                    const float gr = __uint_as_float(rr[LJ * i + i2]);
-                    const float gi = __uint_as_float(ri[LJ * i + i2]);
-                    ur = fmaf(pj[i2].x, gr, fmaf(-pj[i2].y, gi, ur));
-                    ui = fmaf(pj[i2].x, gi, fmaf(pj[i2].y, gr, ui));
+                    const float2 gr = make_float2(__uint_as_float(rr[i2][i]), __uint_as_float(rr[i2][i + 1]));
+                    const float2 gi = make_float2(__uint_as_float(ri[i2][i]), __uint_as_float(ri[i2][i + 1]));
+                    const float2 px = make_float2(pj[i2].x, pj[i2].x), py = make_float2(pj[i2].y, pj[i2].y);
+                    const float2 npy = make_float2(-pj[i2].y, -pj[i2].y);
+                    ur = __ffma2_rn(px, gr, __ffma2_rn(npy, gi, ur));
+                    ui = __ffma2_rn(px, gi, __ffma2_rn(py, gr, ui));
                 }
-                return make_float2(ur, ui);
+                u0 = make_float2(ur.x, ui.x);
+                u1 = make_float2(ur.y, ui.y);
             };
             // W of chunk c, then the carry to chunk c + 1
             auto w_step = [&](unsigned char *W, int c, float2 Uc) {
@@ -1202,10 +1190,10 @@ __global__ void __launch_bounds__(carry_warps(S) * 32, 1) tc_carry_kernel(const 
                 float2 U[kMaxC];
 #pragma unroll
                 for (int pp = 0; pp < kMaxC / kR; ++pp) {
-                    uint32_t rr[kR * LJ], ri[kR * LJ];
+                    uint32_t rr[LJ][kR], ri[LJ][kR];
                     load_round(pp, rr, ri);
 #pragma unroll
-                    for (int i = 0; i < kR; ++i) U[pp * kR + i] = u_of(rr, ri, i);
+                    for (int i = 0; i < kR; i += 2) u_pair(rr, ri, i, U[pp * kR + i], U[pp * kR + i + 1]);
                 }
                 tc_fence_before();
                 mbar_arrive(&state_free[grp]);
@@ -1216,16 +1204,18 @@ __global__ void __launch_bounds__(carry_warps(S) * 32, 1) tc_carry_kernel(const 
                 if (use > 0 && !mbar_wait_ab(&w_free[wl], (use - 1) & 1, a.status, abort)) return false;
 #pragma unroll
                 for (int pp = 0; pp < kMaxC / kR; ++pp) {
-                    uint32_t rr[kR * LJ], ri[kR * LJ];
+                    uint32_t rr[LJ][kR], ri[LJ][kR];
                     load_round(pp, rr, ri);
                     if (pp == kMaxC / kR - 1) {
                         tc_fence_before();
                         mbar_arrive(&state_free[grp]);
                     }
 #pragma unroll
-                    for (int i = 0; i < kR; ++i) {
-                        const int c = pp * kR + i;
-                        w_step(W, c, c < nb ? u_of(rr, ri, i) : make_float2(0.f, 0.f));
+                    for (int i = 0; i < kR; i += 2) {
+                        float2 u0, u1;
+                        u_pair(rr, ri, i, u0, u1);
+                        w_step(W, pp * kR + i, u0);
+                        w_step(W, pp * kR + i + 1, u1);
                     }
                 }
             }
