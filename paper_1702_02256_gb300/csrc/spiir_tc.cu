@@ -22,13 +22,14 @@
 //          stored 8 times with one-sample shifts: every 8x8 core matrix
 //          (n-block g, k-block kb) is block g+kb, so both descriptor strides
 //          are 128 bytes and no Toeplitz matrix is ever built.
-//   STATE  G_k(c, i2) = sum_{i1<128} a_k^i1 x[e_c - 128 i2 - i1]: power panel
-//          R[k][i] = a_k^i (K-major, contraction over powers) times strain
-//          segments; U_k = sum_i2 a_k^(128 i2) G_k(c, i2).
-//   CARRY  (FP64, one thread per filter and stream) s = c_k v, v <- a^L v + U.
+//   STATE  G_k(c, i2) = sum_{i1<64} a_k^i1 x[e_c - 64 i2 - i1]: power panel
+//          R[k][i] = a_k^i, i < 64 (K-major, contraction over powers) times
+//          strain segments; U_k = sum_i2 a_k^(64 i2) G_k(c, i2).
+//   CARRY  (FP32 inside a batch of chunks, FP64 from batch to batch; one
+//          thread per filter and stream) s = c_k v, v <- a^L v + U.
 //   OUTPUT D[j1, (c, j2, re/im)] = sum_k R[k][j1] w_k(c, j2) with
-//          w = a_k^(128 j2) a_k s_k(c): the same panel R read MN-major
-//          (contraction over filters); added into z.
+//          w = a_k^(64 j2) a_k s_k(c): the same panel R read MN-major
+//          (contraction over filters); the FIR adds its term to it in z.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
