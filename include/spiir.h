@@ -70,7 +70,11 @@ typedef enum {
  * the SNR is small when the filters decay within a few FIR lengths (for
  * time constants log-uniform in 10-2000 samples and F = 1024, about 9% of
  * the RMS), so their rounding adds roughly that share of the single-pass
- * bf16 error. Banks only (the server takes PLAIN_FP32, TC_FP16, TC_BF16). */
+ * bf16 error. Banks only (the server takes PLAIN_FP32, TC_FP16, TC_BF16).
+ * The tensor-core modes take single-rate banks (n_levels = 1; a multi-rate
+ * bank is EUNSUPPORTED). Multi-rate banks run the block form at the rates
+ * whose block holds whole chunks through the server (spiir_server_*), where
+ * a member added before the first push has the SNR of a bank of its own. */
 typedef enum {
     SPIIR_PLAIN_FP32 = 0,
     SPIIR_TC_FP16 = 1,
