@@ -361,6 +361,14 @@ __global__ void tc_stage_kernel(const TcStageArgs a) {
 // the same time share impulse-response tiles in L2.
 // ---------------------------------------------------------------------------
 
+// Template group of the FIR items with group index sg / n_streams, the last
+// group first: the carry kernel ends on the highest templates, whose state
+// terms are then the likeliest to be still in L2 when the FIR reads them.
+__device__ __forceinline__ int fir_group(const TcFirArgs &a, int sg) {
+    const int gi = a.n_groups - 1 - sg / a.n_streams;
+    return a.groups ? a.groups[gi] : gi;
+}
+
 constexpr int kFirEpiWarps = 8;
 constexpr int kFirThreads = (2 + kFirEpiWarps) * 32;
 
@@ -404,7 +412,7 @@ __global__ void __launch_bounds__(kFirThreads, 1) tc_fir_kernel(const TcFirArgs 
         for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++li) {
             const int c = it % a.n_chunks, sg = it / a.n_chunks;
             const int ss = sg % a.n_streams;
-            const int g = a.groups ? a.groups[sg / a.n_streams] : sg / a.n_streams;
+            const int g = fir_group(a, sg);
             const int hb = li & 1;
             if (li >= 2) {
                 ok = mbar_wait(&h_empty[hb], ((li >> 1) - 1) & 1, a.status);
@@ -472,7 +480,7 @@ __global__ void __launch_bounds__(kFirThreads, 1) tc_fir_kernel(const TcFirArgs 
         for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++li) {
             const int c = it % a.n_chunks, sg = it / a.n_chunks;
             const int ss = sg % a.n_streams;
-            const int g = a.groups ? a.groups[sg / a.n_streams] : sg / a.n_streams;
+            const int g = fir_group(a, sg);
             const int ab = li & 1;
             const int t = g * kGroup + (r >> 1);
             const float sc = (t < a.n_templates) ? a.row_scale[t] : 0.f;
