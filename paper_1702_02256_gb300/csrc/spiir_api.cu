@@ -193,11 +193,24 @@ void plan_info(const spiir_bank_desc *d, const Plan &p, spiir_bank_info *info) {
 }
 
 int default_variant(const spiir_bank_desc *d) {
-    // T = 32, FMAX = 8: units above 256 filters span 2-4 warps, which gives the
-    // persistent scheduler twice as many independent chains as FMAX = 16, and
-    // the 32-sample tile halves the reduction's share per sample
-    (void)d;
-    return 3;
+    // By the mean number of filters in a bank's non-empty (template, rate)
+    // units (d is validated). Up to 128: T = 32 with 4 filters per lane and
+    // three CTAs per SM (variant 2), within 4% of the best compiled variant on
+    // single-rate banks of 4 to 128 filters per template and the fastest on
+    // multi-rate banks, whose units are small; 8 per lane loses up to 20%
+    // there (4-lane units at 32 filters). Larger units: T = 32, 8 filters per
+    // lane, two CTAs per SM (variant 3): units above 256 filters span 2-4
+    // warps, twice as many independent chains as with 16 per lane, and the
+    // 32-sample tile halves the reduction's share per sample.
+    if (d->n_filters <= 0) return 3;
+    std::vector<uint8_t> seen((size_t)d->n_templates * d->n_levels, 0);
+    int64_t units = 0;
+    for (int64_t k = 0; k < d->n_filters; ++k) {
+        const size_t u = (size_t)d->template_id[k] * d->n_levels + (d->level ? d->level[k] : 0);
+        units += seen[u] == 0;
+        seen[u] = 1;
+    }
+    return d->n_filters <= 128 * units ? 2 : 3;
 }
 
 // Builds the plan. With arrays == false only the sizes are computed.

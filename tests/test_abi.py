@@ -125,6 +125,23 @@ def test_plan_covers_every_filter(variant):
     assert 1.0 <= p["smem_ways"] <= 32.0
 
 
+def test_built_in_variant_follows_unit_size():
+    """Without tuning, banks whose (template, rate) units hold at most 128
+    filters on average run 4 filters per lane (variant 2), larger ones 8
+    (variant 3); a forced variant still wins."""
+    small = inputs.single_rate_bank(64, 32, 500, seed=4)
+    assert spiir.plan(small)["kernel_variant"] == 2
+    assert spiir.plan(inputs.single_rate_bank(8, 128, 500, seed=4))["kernel_variant"] == 2
+    assert spiir.plan(inputs.single_rate_bank(8, 129, 500, seed=4))["kernel_variant"] == 3
+    assert spiir.plan(inputs.single_rate_bank(16, 512, 4095, seed=4))["kernel_variant"] == 3
+    # multi-rate: the same filters spread over rates make smaller units
+    assert spiir.plan(inputs.multi_rate_bank(50, 7, seed=3))["kernel_variant"] == 2
+    # empty templates do not count as units
+    uneven = inputs.single_rate_bank(4, [0, 0, 300, 300], 500, seed=4)
+    assert spiir.plan(uneven)["kernel_variant"] == 3
+    assert spiir.plan(small, tune=-4)["kernel_variant"] == 3
+
+
 def test_plan_multirate_and_footprint():
     bank = inputs.multi_rate_bank(50, 7, seed=3)
     p = spiir.plan(bank, max_push_blocks=2)
