@@ -114,7 +114,11 @@ typedef struct {
     float snr_scale;              /* 0 = 2/base_rate (2*dt, Eq. iireq1) */
     spiir_mode mode;
     int32_t chunk_len;            /* TC forms: chunk length L (0 = 256) */
-    int32_t tune;                 /* 0 = built-in tile choice; 1 = autotune
+    int32_t tune;                 /* 0 = built-in tile choice (plain: 4
+                                     filters per lane when the non-empty
+                                     (template, level) units hold at most
+                                     128 filters on average, else 8; 32-
+                                     sample time tiles); 1 = autotune
                                      at create: time candidate tilings on
                                      pushes of zeros and keep the fastest
                                      (plain: every compiled recursion
