@@ -238,6 +238,27 @@ spiir_status spiir_push_block_host(spiir_bank_t bank, int32_t stream_id,
                                    const float *x_host, int64_t n_samples,
                                    void *z_host, void *cuda_stream);
 
+/* The same push, returning once its copies and kernels are queued: the SNR
+ * is in z_host, and x_host may be reused, only after spiir_bank_host_sync
+ * returns. Arguments and errors as for spiir_push_block_host; x_host and
+ * z_host must stay valid until then, and must be pinned for the copies to
+ * overlap anything. When the output ring holds two pushes of n_samples
+ * (block_len * max_push_blocks >= 2 * n_samples), consecutive asynchronous
+ * pushes write alternate halves of it, so a push's kernels run while the SNR
+ * of the push before it is still being copied out; otherwise each waits,
+ * on the device, for that copy. Every call that writes the ring (pushes,
+ * host pushes) waits on the device for the copies still reading it, so the
+ * calls may be mixed. spiir_read_snr and spiir_read_snr_abs read the last
+ * push wherever it sits in the ring. The SNR of the pushes of the tensor-core
+ * and plain forms is the same as from spiir_push_block_host, bit for bit. */
+spiir_status spiir_push_block_host_async(spiir_bank_t bank, int32_t stream_id,
+                                         const float *x_host, int64_t n_samples,
+                                         void *z_host, void *cuda_stream);
+
+/* Waits (on the host) until every asynchronous host push of the bank has its
+ * SNR in host memory. EINVAL for a NULL bank, ECUDA if a copy failed. */
+spiir_status spiir_bank_host_sync(spiir_bank_t bank);
+
 /* Device bytes a bank with this description would hold (filters, state,
  * history, scratch, output ring), for admission control. -1 on a bad desc. */
 int64_t spiir_bank_footprint(const spiir_bank_desc *desc);

@@ -611,9 +611,17 @@ struct spiir_bank {
     cudaStream_t cap = nullptr;             // private stream for graph capture
     cudaStream_t copy[2] = {nullptr, nullptr};   // host push: device-to-host copies
     cudaEvent_t piece_done[4] = {};         // host push: a piece's SNR is in the ring
+    // asynchronous host pushes alternate between ring columns [0, n) and
+    // [n, 2n) when the ring holds two pushes: half_free[h][c] is recorded on
+    // copy stream c after the last copy-back out of half h, which covered
+    // ring columns [half_lo[h], half_hi[h]); a later write there waits on it
+    cudaEvent_t half_free[2][2] = {};
+    int64_t half_lo[2] = {0, 0}, half_hi[2] = {0, 0};
+    int async_half = 0;                     // half the next asynchronous push writes
     std::vector<GraphEntry> graphs;
     std::vector<int64_t> last_n;            // samples of the last kernel push (strain history)
     std::vector<int64_t> ring_n;            // samples of the last call's push held in the ring
+    std::vector<int64_t> ring_base;         // ring column where that push starts
     std::vector<char> out_valid;            // the output ring holds a push of the stream
     uint64_t fingerprint = 0;               // of the description, for state import
     int64_t footprint = 0;
@@ -661,6 +669,12 @@ struct spiir_bank {
                 cudaEventDestroy(e);
                 e = nullptr;
             }
+        for (auto &h : half_free)
+            for (auto &e : h)
+                if (e) {
+                    cudaEventDestroy(e);
+                    e = nullptr;
+                }
     }
 };
 
@@ -998,6 +1012,7 @@ spiir_status build_bank(const spiir_bank_desc *desc_in, const Tuning &tn, cudaSt
     }
     b->last_n.assign(desc->n_streams, 0);
     b->ring_n.assign(desc->n_streams, 0);
+    b->ring_base.assign(desc->n_streams, 0);
     b->out_valid.assign(desc->n_streams, 0);
     b->fingerprint = desc_fingerprint(desc);
     if (!b->timer) b->timer = new KernelTimer();
@@ -1145,6 +1160,16 @@ spiir_status spiir_bank_create(const spiir_bank_desc *desc, void *cuda_stream, s
     return SPIIR_OK;
 }
 
+// Makes stream s wait until no asynchronous copy-back still reads ring
+// columns that overlap [lo, hi).
+static spiir_status fence_ring(spiir_bank *b, cudaStream_t s, int64_t lo, int64_t hi) {
+    for (int h = 0; h < 2; ++h)
+        if (b->half_hi[h] > lo && b->half_lo[h] < hi)
+            for (cudaEvent_t e : b->half_free[h])
+                if (e) CUDA_TRY(cudaStreamWaitEvent(s, e, 0));
+    return SPIIR_OK;
+}
+
 spiir_status spiir_push_block(spiir_bank_t b, int32_t stream_id, const float *x_dev,
                               int64_t n_samples, void *cuda_stream) {
     if (!b) return fail(SPIIR_EINVAL, "bank is NULL");
@@ -1158,6 +1183,8 @@ spiir_status spiir_push_block(spiir_bank_t b, int32_t stream_id, const float *x_
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const int s0 = stream_id < 0 ? 0 : stream_id;
     const int cnt = stream_id < 0 ? b->d.n_streams : 1;
+    if (spiir_status st = fence_ring(b, s, 0, n_samples)) return st;
+    for (int q = s0; q < s0 + cnt; ++q) b->ring_base[q] = 0;
     if (b->tc) {
         spiir_status st = push_tc(b, s0, cnt, x_dev, n_samples, s, 0);
         if (st) return st;
@@ -1211,7 +1238,7 @@ spiir_status spiir_read_snr(spiir_bank_t b, int32_t stream_id, void *z_dev, int6
             ring = b->p.ring_len;
             src = b->z + (int64_t)q * T * ring;
         }
-        src += b->ring_n[q] - n_samples;
+        src += b->ring_base[q] + b->ring_n[q] - n_samples;
         char *dst = (char *)z_dev + (int64_t)(q - s0) * T * n_samples * sizeof(float2);
         CUDA_TRY(cudaMemcpy2DAsync(dst, n_samples * sizeof(float2), src, ring * sizeof(float2),
                                    n_samples * sizeof(float2), T, cudaMemcpyDeviceToDevice, s));
@@ -1241,7 +1268,7 @@ spiir_status spiir_state_reset(spiir_bank_t b, int32_t stream_id, void *cuda_str
                                      cnt * p.ubuf_stream_stride * sizeof(float2), s));
     }
     for (int q = s0; q < s0 + cnt; ++q) {
-        b->last_n[q] = b->ring_n[q] = 0;
+        b->last_n[q] = b->ring_n[q] = b->ring_base[q] = 0;
         b->out_valid[q] = 0;
     }
     return SPIIR_OK;
@@ -1382,7 +1409,7 @@ spiir_status spiir_state_import(spiir_bank_t b, int32_t stream_id, const void *s
             CUDA_TRY(cudaStreamSynchronize(s));
         }
         b->last_n[q] = last_n;
-        b->ring_n[q] = 0;
+        b->ring_n[q] = b->ring_base[q] = 0;
         b->out_valid[q] = 0;
     }
     return SPIIR_OK;
@@ -1414,14 +1441,19 @@ spiir_status spiir_read_snr_abs(spiir_bank_t b, int32_t stream_id, float *out_de
             ring = b->p.ring_len;
             src = b->z + (int64_t)q * T * ring;
         }
-        CUDA_TRY(spiir_launch_abs(src + b->ring_n[q] - n_samples, ring, T, n_samples, norm_dev,
+        CUDA_TRY(spiir_launch_abs(src + b->ring_base[q] + b->ring_n[q] - n_samples, ring, T, n_samples, norm_dev,
                                   out_dev + (int64_t)(q - s0) * T * n_samples, s));
     }
     return SPIIR_OK;
 }
 
-spiir_status spiir_push_block_host(spiir_bank_t b, int32_t stream_id, const float *x_host,
-                                   int64_t n_samples, void *z_host, void *cuda_stream) {
+// The host-buffer push behind spiir_push_block_host (async = false: returns
+// once z_host holds the SNR) and spiir_push_block_host_async (returns once
+// the work is queued; the push goes into the ring half the previous
+// asynchronous push did not use when the ring holds two pushes, so its
+// kernels run while that push's SNR is still being copied out).
+static spiir_status host_push(spiir_bank_t b, int32_t stream_id, const float *x_host, int64_t n_samples,
+                       void *z_host, cudaStream_t s, bool async) {
     if (!b) return fail(SPIIR_EINVAL, "bank is NULL");
     if (!x_host || !z_host) return fail(SPIIR_EINVAL, "host buffers must not be NULL");
     if (stream_id < -1 || stream_id >= b->d.n_streams)
@@ -1429,22 +1461,30 @@ spiir_status spiir_push_block_host(spiir_bank_t b, int32_t stream_id, const floa
     if (n_samples <= 0 || n_samples % b->d.block_len != 0 ||
         n_samples > (int64_t)b->d.block_len * b->d.max_push_blocks)
         return fail(SPIIR_EINVAL, "bad n_samples");
-    cudaStream_t s = (cudaStream_t)cuda_stream;
     const int s0 = stream_id < 0 ? 0 : stream_id;
     const int cnt = stream_id < 0 ? b->d.n_streams : 1;
     const int T = b->d.n_templates;
+    int64_t ring_len = b->p.ring_len;
+    if (b->tc) spiir_tc_output(b->tc, 0, &ring_len);
+    const bool two = async && ring_len >= 2 * n_samples;
+    const int half = two ? b->async_half : 0;
+    const int64_t base = half ? n_samples : 0;    // first ring column of this push
     // A push of several blocks runs as up to four pieces of whole blocks.
-    // Piece i writes output-ring columns [off_i, off_i + n_i) (pushes compose
-    // exactly: block-split invariance), and its SNR is copied back while
-    // piece i + 1 computes, the template rows split over two copy streams
-    // (two copy engines: one device-to-host stream does not fill the link).
-    // The ring then holds the whole push, as after one push of n_samples.
+    // Piece i writes output-ring columns [base + off_i, base + off_i + n_i)
+    // (pushes compose exactly: block-split invariance), and its SNR is copied
+    // back while piece i + 1 computes, the template rows split over two copy
+    // streams (two copy engines: one device-to-host stream does not fill the
+    // link). The ring then holds the whole push, as after one push of n_samples.
     const int64_t n_blocks = n_samples / b->d.block_len;
     const int n_pieces = (int)std::min<int64_t>(4, n_blocks);
     if (!b->copy[0]) {
         for (auto &c : b->copy) CUDA_TRY(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
         for (auto &e : b->piece_done) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        for (auto &h : b->half_free)
+            for (auto &e : h) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
+    // no earlier asynchronous copy-back may still read what this push writes
+    if (spiir_status st = fence_ring(b, s, base, base + n_samples)) return st;
     int64_t off = 0;
     for (int i = 0; i < n_pieces; ++i) {
         bool same = true;
@@ -1457,15 +1497,15 @@ spiir_status spiir_push_block_host(spiir_bank_t b, int32_t stream_id, const floa
         CUDA_TRY(cudaMemcpy2DAsync(stage, n_i * sizeof(float), x_host + off, n_samples * sizeof(float),
                                    n_i * sizeof(float), cnt, cudaMemcpyHostToDevice, s));
         if (b->tc) {
-            spiir_status st = push_tc(b, s0, cnt, stage, n_i, s, off);
+            spiir_status st = push_tc(b, s0, cnt, stage, n_i, s, base + off);
             if (st) return st;
             for (int q = s0; q < s0 + cnt; ++q) b->last_n[q] = n_i;
         } else if (same) {
-            spiir_status st = push_plain(b, s0, cnt, stage, n_i, n_i, s, false, off);
+            spiir_status st = push_plain(b, s0, cnt, stage, n_i, n_i, s, false, base + off);
             if (st) return st;
         } else {
             for (int q = 0; q < cnt; ++q) {
-                spiir_status st = push_plain(b, s0 + q, 1, stage + q * n_i, n_i, n_i, s, false, off);
+                spiir_status st = push_plain(b, s0 + q, 1, stage + q * n_i, n_i, n_i, s, false, base + off);
                 if (st) return st;
             }
         }
@@ -1486,7 +1526,7 @@ spiir_status spiir_push_block_host(spiir_bank_t b, int32_t stream_id, const floa
                 if (r1 <= r0) continue;
                 char *dst = (char *)z_host + ((int64_t)(q - s0) * T * n_samples + (int64_t)r0 * n_samples + off) *
                                                  sizeof(float2);
-                CUDA_TRY(cudaMemcpy2DAsync(dst, n_samples * sizeof(float2), src + (int64_t)r0 * ring + off,
+                CUDA_TRY(cudaMemcpy2DAsync(dst, n_samples * sizeof(float2), src + (int64_t)r0 * ring + base + off,
                                            ring * sizeof(float2), n_i * sizeof(float2), r1 - r0,
                                            cudaMemcpyDeviceToHost, b->copy[h]));
             }
@@ -1495,11 +1535,39 @@ spiir_status spiir_push_block_host(spiir_bank_t b, int32_t stream_id, const floa
     }
     for (int q = s0; q < s0 + cnt; ++q) {
         b->ring_n[q] = n_samples;
+        b->ring_base[q] = base;
         b->out_valid[q] = 1;
+    }
+    if (async) {
+        for (int c = 0; c < 2; ++c) CUDA_TRY(cudaEventRecord(b->half_free[half][c], b->copy[c]));
+        b->half_lo[half] = base;
+        b->half_hi[half] = base + n_samples;
+        if (two) b->async_half ^= 1;
+        return SPIIR_OK;
     }
     for (auto &c : b->copy)
         if (c) CUDA_TRY(cudaStreamSynchronize(c));
     CUDA_TRY(cudaStreamSynchronize(s));
+    // every copy-back, asynchronous ones included, has finished
+    b->half_lo[0] = b->half_hi[0] = b->half_lo[1] = b->half_hi[1] = 0;
+    return SPIIR_OK;
+}
+
+spiir_status spiir_push_block_host(spiir_bank_t b, int32_t stream_id, const float *x_host,
+                                   int64_t n_samples, void *z_host, void *cuda_stream) {
+    return host_push(b, stream_id, x_host, n_samples, z_host, (cudaStream_t)cuda_stream, false);
+}
+
+spiir_status spiir_push_block_host_async(spiir_bank_t b, int32_t stream_id, const float *x_host,
+                                         int64_t n_samples, void *z_host, void *cuda_stream) {
+    return host_push(b, stream_id, x_host, n_samples, z_host, (cudaStream_t)cuda_stream, true);
+}
+
+spiir_status spiir_bank_host_sync(spiir_bank_t b) {
+    if (!b) return fail(SPIIR_EINVAL, "bank is NULL");
+    for (auto &c : b->copy)
+        if (c) CUDA_TRY(cudaStreamSynchronize(c));
+    b->half_lo[0] = b->half_hi[0] = b->half_lo[1] = b->half_hi[1] = 0;
     return SPIIR_OK;
 }
 

@@ -95,6 +95,8 @@ _SIGS = {
     "spiir_state_export": (_i32, [_c_void_p, _i32, _c_void_p, _i64, _c_void_p]),
     "spiir_state_import": (_i32, [_c_void_p, _i32, _c_void_p, _i64, _c_void_p]),
     "spiir_push_block_host": (_i32, [_c_void_p, _i32, _c_void_p, _i64, _c_void_p, _c_void_p]),
+    "spiir_push_block_host_async": (_i32, [_c_void_p, _i32, _c_void_p, _i64, _c_void_p, _c_void_p]),
+    "spiir_bank_host_sync": (_i32, [_c_void_p]),
     "spiir_bank_footprint": (_i64, [ctypes.POINTER(BankDesc)]),
     "spiir_bank_get_info": (_i32, [_c_void_p, ctypes.POINTER(BankInfo)]),
     "spiir_bank_plan": (_i32, [ctypes.POINTER(BankDesc), ctypes.POINTER(BankInfo)]),
@@ -297,6 +299,19 @@ class Bank:
         zp = z_out.data_ptr() if hasattr(z_out, "data_ptr") else z_out.ctypes.data
         check(lib().spiir_push_block_host(self._h, stream_id, xp, n, zp, _stream_handle(stream)))
         return z_out
+
+    def push_host_async(self, x, z_out, stream_id: int = -1, stream=None):
+        """As push_host, returning once the work is queued; z_out holds the
+        SNR (and x may change) after host_sync(). x and z_out: pinned CPU
+        torch tensors, kept alive by the caller until then."""
+        n = int(x.shape[-1])
+        check(lib().spiir_push_block_host_async(self._h, stream_id, x.data_ptr(), n, z_out.data_ptr(),
+                                                _stream_handle(stream)))
+        return z_out
+
+    def host_sync(self):
+        """Wait until every asynchronous host push has its SNR in host memory."""
+        check(lib().spiir_bank_host_sync(self._h))
 
     def reset(self, stream_id: int = -1, stream=None):
         check(lib().spiir_state_reset(self._h, stream_id, _stream_handle(stream)))

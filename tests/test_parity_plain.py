@@ -249,3 +249,57 @@ def test_pipelined_host_push(torch_cuda, oracle_mod, form):
         else:
             ref = oracle_mod.spiir_single(bank, x[s])
         assert rel_rms(got[s], ref).max() <= tol
+
+
+@pytest.mark.parametrize("form,ring_pushes", [("plain-multirate", 2), ("fp16", 2), ("fp16", 1)])
+def test_async_host_pushes(torch_cuda, oracle_mod, form, ring_pushes):
+    """Asynchronous host pushes of one block: with a ring of two pushes they
+    alternate ring halves (a push computes while the SNR of the one before it
+    is copied out), with a ring of one each waits for that copy. Six of them,
+    then a device push, a synchronous host push and two more asynchronous
+    ones, on two streams: every push's SNR equals, bit for bit, the same
+    pushes made synchronously on a bank of its own; a read returns the last
+    push; every sample against the oracle."""
+    import torch
+    from paper_1702_02256_gb300 import spiir
+    blk = 1024
+    if form == "fp16":
+        bank = inputs.single_rate_bank(6, [40, 128, 200, 5, 300, 64], 500, seed=61)
+        kw = dict(mode="fp16", chunk_len=256)
+        tol = 1e-3
+    else:
+        bank = inputs.multi_rate_bank(5, 3, seed=62, delay_max=200)
+        kw = {}
+        tol = TOL_PLAIN
+    n_blk = 10
+    x = inputs.strain(2, n_blk * blk, seed=63)
+    xb = [np.ascontiguousarray(x[:, i * blk:(i + 1) * blk]) for i in range(n_blk)]
+    r = spiir.Bank(bank, n_streams=2, block_len=blk, max_push_blocks=ring_pushes, **kw)
+    ref = [r.push_host(xi) for xi in xb]
+    r.close()
+    b = spiir.Bank(bank, n_streams=2, block_len=blk, max_push_blocks=ring_pushes, **kw)
+    xs = [torch.from_numpy(xi).pin_memory() for xi in xb]
+    zs = [torch.empty((2, bank.n_templates, blk), dtype=torch.complex64).pin_memory() for _ in range(n_blk)]
+    for i in range(6):
+        b.push_host_async(xs[i], zs[i])
+    b.push(xs[6].cuda(), stream_id=-1)          # waits on the device for the copies
+    zd = b.read(blk, stream_id=-1).cpu().numpy()
+    b.push_host(xb[7], z_out=zs[7])
+    b.push_host_async(xs[8], zs[8])
+    b.push_host_async(xs[9], zs[9])
+    last = b.read(blk, stream_id=-1).cpu().numpy()
+    b.host_sync()
+    b.sync_status()
+    b.close()
+    got = [z.numpy() for z in zs]
+    got[6] = zd
+    for i in range(n_blk):
+        assert np.array_equal(got[i], ref[i]), i
+    assert np.array_equal(last, got[9])
+    full = np.concatenate(got, axis=-1).astype(np.complex128)
+    for s in range(2):
+        if bank.n_levels > 1:
+            want = oracle_mod.spiir_multirate(bank, x[s])
+        else:
+            want = oracle_mod.spiir_single(bank, x[s])
+        assert rel_rms(full[s], want).max() <= tol
