@@ -107,6 +107,13 @@ def test_validation_rejects_bad_descriptions():
     assert spiir.lib().spiir_bank_create(None, None, ctypes.byref(ctypes.c_void_p())) == spiir.EINVAL
     assert "NULL" in spiir.last_error()
     assert spiir.lib().spiir_bank_footprint(None) == -1
+    # the queued host push and its sync refuse a NULL bank before any CUDA call
+    buf = np.zeros(4096, np.float32)
+    zb = np.zeros(2 * 4096, np.float32)
+    assert spiir.lib().spiir_push_block_host_async(None, -1, buf.ctypes.data, 4096, zb.ctypes.data,
+                                                   None) == spiir.EINVAL
+    assert "NULL" in spiir.last_error()
+    assert spiir.lib().spiir_bank_host_sync(None) == spiir.EINVAL
 
 
 @pytest.mark.parametrize("variant", [0, 1, 2, 3])
